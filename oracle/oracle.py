@@ -1,0 +1,268 @@
+"""ctypes front end of the FP64 CPU oracle (``sph_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` (to
+check the CUDA path) and by the cpu_baseline / reference leg of bench.py.  The
+product package never imports it.
+
+``build()`` compiles the C file with gcc (-O2 -ffp-contract=off -fopenmp) into
+``oracle/_build/libsph_oracle.so``; it is rebuilt when the source is newer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libsph_oracle.so")
+
+NAUX = 18
+AUX = {name: i for i, name in enumerate(
+    ["sigstar", "s", "nB", "nS", "nQ", "T", "muB", "muS", "muQ", "p", "e", "cs2", "theta", "Pi",
+     "u0", "nnb", "sigma", "status"])}
+ST_FALLBACK, ST_OUT_OF_TABLE, ST_NOCONV, ST_NONFINITE, ST_CS2_CAPPED, ST_SOLVE_FAIL = 1, 2, 4, 8, 16, 32
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fopenmp",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("milne", C.c_int), ("viscous", C.c_int), ("has_table", C.c_int),
+        ("h", C.c_double),
+        ("a0", C.c_double), ("a1", C.c_double), ("Tc_GeV", C.c_double), ("w_GeV", C.c_double),
+        ("chi", C.c_double * 3),
+        ("nT", C.c_int), ("nmu", C.c_int * 3),
+        ("T0", C.c_double), ("dT", C.c_double), ("mu0", C.c_double * 3), ("dmu", C.c_double * 3),
+        ("tp", C.c_void_p), ("ts", C.c_void_p), ("tnB", C.c_void_p), ("tnS", C.c_void_p), ("tnQ", C.c_void_p),
+        ("eta_over_s", C.c_double), ("zeta_peak", C.c_double), ("zeta_T_GeV", C.c_double),
+        ("zeta_w_GeV", C.c_double), ("tau_pi_coef", C.c_double), ("tau_Pi_ratio", C.c_double),
+        ("cs2_cap", C.c_double),
+        ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("pad", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d, i, l, p, u64 = C.c_double, C.c_int, C.c_long, C.c_void_p, C.c_uint64
+        P = C.POINTER(Params)
+        sig = {
+            "oc_W": (d, [d, d, i]), "oc_dWdr": (d, [d, d, i]),
+            "oc_cell_coords": (None, [l, i, p, d, p, p]),
+            "oc_morton": (u64, [i, p]),
+            "oc_sort_by_cell": (None, [l, i, p, d, p, p, p]),
+            "oc_neighbors_brute": (l, [l, i, p, d, l, p, p]),
+            "oc_neighbors_cells": (l, [l, i, p, d, l, p, p]),
+            "oc_eos_analytic": (None, [P, d, p, p, p, p]),
+            "oc_eos_invert_analytic": (i, [P, d, p, p, p]),
+            "oc_eos_table": (None, [P, p, p, p, p]),
+            "oc_eos_invert": (C.c_uint, [P, d, p, p]),
+            "oc_stage": (i, [P, l, d, p, p, p, p, p, p, p]),
+            "oc_observe": (None, [P, l, d, p, p, p, p]),
+            "oc_heun": (i, [P, l, p, d, i, p, p, p, p, p, p, p]),
+            "oc_totals": (None, [P, l, d, p, p, p, p]),
+            "oc_pi_pairs": (i, [i, p]),
+            "oc_pi_full": (None, [i, i, d, p, p, p]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
+    """Params for an inputs.Event; returns (params, keep-alive list of table arrays)."""
+    P = Params()
+    P.dim, P.milne, P.viscous = ev.dim, int(ev.milne), int(ev.transport.viscous)
+    P.h = ev.h
+    e = ev.eos
+    P.a0, P.a1, P.Tc_GeV, P.w_GeV = e.a0, e.a1, e.Tc_GeV, e.w_GeV
+    for q in range(3):
+        P.chi[q] = e.chi[q]
+    keep = []
+    if ev.table is not None:
+        t = ev.table
+        P.has_table = 1
+        P.nT = t.nT
+        for q in range(3):
+            P.nmu[q] = t.nmu[q]
+            P.mu0[q] = t.mu0[q]
+            P.dmu[q] = t.dmu[q]
+        P.T0, P.dT = t.T0, t.dT
+        arrs = [_f64(t.p), _f64(t.s), _f64(t.nB), _f64(t.nS), _f64(t.nQ)]
+        keep += arrs
+        P.tp, P.ts, P.tnB, P.tnS, P.tnQ = [a.ctypes.data for a in arrs]
+    tr = ev.transport
+    P.eta_over_s, P.zeta_peak, P.zeta_T_GeV, P.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
+    P.tau_pi_coef, P.tau_Pi_ratio, P.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
+    P.newton_tol, P.newton_maxit = newton_tol, newton_maxit
+    return P, keep
+
+
+def npi(dim: int) -> int:
+    return 3 if dim == 2 else 5
+
+
+def nv(dim: int) -> int:
+    return 2 * dim + 2 + npi(dim)
+
+
+def pack_state(ev) -> np.ndarray:
+    """y[nv][N]: x^i, u^i, S, Pi/sigma, pi^{ij}/sigma."""
+    return np.ascontiguousarray(np.vstack([ev.x, ev.u, ev.S[None], ev.Bv[None], ev.Pv]), dtype=np.float64)
+
+
+def W(r, h, dim):
+    return lib().oc_W(float(r), float(h), int(dim))
+
+
+def dWdr(r, h, dim):
+    return lib().oc_dWdr(float(r), float(h), int(dim))
+
+
+def cell_coords(x: np.ndarray, h: float):
+    x = _f64(x)
+    dim, n = x.shape
+    cc = np.zeros((dim, n), dtype=np.int32)
+    xmin = np.zeros(3)
+    lib().oc_cell_coords(n, dim, _ptr(x), h, _ptr(cc), _ptr(xmin))
+    return cc, xmin[:dim]
+
+
+def sort_by_cell(x: np.ndarray, h: float):
+    """(cell coords [dim][N] int32, Morton keys uint64, permutation sorting by (key, id))."""
+    x = _f64(x)
+    dim, n = x.shape
+    cc = np.zeros((dim, n), dtype=np.int32)
+    keys = np.zeros(n, dtype=np.uint64)
+    perm = np.zeros(n, dtype=np.int64)
+    lib().oc_sort_by_cell(n, dim, _ptr(x), h, _ptr(cc), _ptr(keys), _ptr(perm))
+    return cc, keys, perm
+
+
+def neighbors(x: np.ndarray, h: float, method: str = "cells"):
+    """Sorted (a, b) pairs with r_ab < 2h (self pairs included)."""
+    x = _f64(x)
+    dim, n = x.shape
+    fn = lib().oc_neighbors_cells if method == "cells" else lib().oc_neighbors_brute
+    cnt = fn(n, dim, _ptr(x), h, 0, None, None)
+    pa = np.zeros(max(cnt, 1), dtype=np.int32)
+    pb = np.zeros(max(cnt, 1), dtype=np.int32)
+    fn(n, dim, _ptr(x), h, cnt, _ptr(pa), _ptr(pb))
+    return pa[:cnt], pb[:cnt]
+
+
+def eos_invert(P: Params, s: float, n3):
+    out = np.zeros(11)
+    n3 = _f64(n3)
+    st = lib().oc_eos_invert(C.byref(P), float(s), _ptr(n3), _ptr(out))
+    return out, int(st)
+
+
+def eos_analytic(P: Params, T: float, mu3):
+    mu3 = _f64(mu3)
+    p = np.zeros(1)
+    sn = np.zeros(4)
+    H = np.zeros(16)
+    lib().oc_eos_analytic(C.byref(P), float(T), _ptr(mu3), _ptr(p), _ptr(sn), _ptr(H))
+    return p[0], sn, H.reshape(4, 4)
+
+
+def eos_table(P: Params, x4):
+    x4 = _f64(x4)
+    p = np.zeros(1)
+    sn = np.zeros(4)
+    J = np.zeros(16)
+    lib().oc_eos_table(C.byref(P), _ptr(x4), _ptr(p), _ptr(sn), _ptr(J))
+    return p[0], sn, J.reshape(4, 4)
+
+
+@dataclass
+class OracleRun:
+    """Holds an evolving state; ``step`` advances Heun steps, ``observe`` fills aux."""
+    ev: object
+    P: Params
+    keep: list
+    y: np.ndarray
+    Nq: np.ndarray
+    tau: float
+    work: float = 0.0
+    status_or: int = 0
+
+    @classmethod
+    def start(cls, ev, **kw):
+        P, keep = make_params(ev, **kw)
+        return cls(ev=ev, P=P, keep=keep, y=pack_state(ev), Nq=_f64(ev.Nq), tau=float(ev.tau0))
+
+    @property
+    def n(self):
+        return self.y.shape[1]
+
+    def step(self, nsteps: int):
+        n, dim = self.n, self.P.dim
+        aux = np.zeros((NAUX, n))
+        grad = np.zeros((dim * dim + dim, n))
+        st = np.zeros(n, dtype=np.uint32)
+        tau = C.c_double(self.tau)
+        work = C.c_double(self.work)
+        stor = C.c_uint(0)
+        lib().oc_heun(C.byref(self.P), n, C.byref(tau), float(self.ev.dtau), int(nsteps), _ptr(self.y),
+                      _ptr(self.Nq), _ptr(aux), _ptr(grad), _ptr(st), C.byref(stor), C.byref(work))
+        self.tau, self.work = tau.value, work.value
+        self.status_or |= stor.value
+        return aux
+
+    def stage(self, y=None, tau=None):
+        """One right-hand-side evaluation: (dydt, aux, grad, status, work_rate)."""
+        y = self.y if y is None else _f64(y)
+        tau = self.tau if tau is None else tau
+        n, dim = self.n, self.P.dim
+        dydt = np.zeros_like(y)
+        aux = np.zeros((NAUX, n))
+        grad = np.zeros((dim * dim + dim, n))
+        st = np.zeros(n, dtype=np.uint32)
+        wr = C.c_double(0.0)
+        lib().oc_stage(C.byref(self.P), n, float(tau), _ptr(y), _ptr(self.Nq), _ptr(dydt), _ptr(aux), _ptr(grad),
+                       _ptr(st), C.byref(wr))
+        return dydt, aux, grad, st, wr.value
+
+    def observe(self):
+        n = self.n
+        aux = np.zeros((NAUX, n))
+        st = np.zeros(n, dtype=np.uint32)
+        lib().oc_observe(C.byref(self.P), n, float(self.tau), _ptr(self.y), _ptr(self.Nq), _ptr(aux), _ptr(st))
+        return aux, st
+
+    def totals(self, aux=None):
+        if aux is None:
+            aux, _ = self.observe()
+        tot = np.zeros(5)
+        lib().oc_totals(C.byref(self.P), self.n, float(self.tau), _ptr(self.y), _ptr(self.Nq), _ptr(aux), _ptr(tot))
+        return {"E": tot[0], "S": tot[1], "N": tot[2:5].copy(), "work": self.work}

@@ -1,0 +1,1120 @@
+/*
+ * sph_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle of the SPH
+ * particle step of relativistic viscous BSQ hydrodynamics (arXiv 2511.22852,
+ * Sec. "Numerical solver: Smoothed particle hydrodynamics (SPH)").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load this library.  It shares
+ * no code, header, table or constant generator with the CUDA library, and the
+ * product path never calls it.
+ *
+ * Everything is written the plain way, in the paper's order:
+ *   1. neighbour pairs r_ab < 2h (brute force O(N^2) and a uniform cell list;
+ *      both must give the same set)                      -- Sec. "Kokkos and Cabana" (VerletList)
+ *   2. kernel sums sigma*_a = sum_b W_ab, s*_a = sum_b S_b W_ab,
+ *      n*_qa = sum_b N_qb W_ab; rest frame q = (q*) / (u^0 sqrt(-g))  -- eqs. refconv, sigmastar
+ *   3. EoS inversion (s, n_B, n_S, n_Q) -> (T, mu_B, mu_S, mu_Q) by Newton on the
+ *      quadrilinear table interpolant, with the closed-form EoS as backup  -- Sec. "EoS inverter"
+ *   4. SPH gradients: du^j/dx^k with the n = 0 form, the stress divergence with
+ *      the n = -1 form                                   -- eqs. sphderivativerel, generalsphderivative
+ *   5. equations of motion: the acceleration from the linear system
+ *      M du/dx0 = F, entropy production, minimal Israel-Stewart relaxation
+ *                                                        -- eqs. genform, unugeneral, dsdnrewr,
+ *                                                           min_bul_rel, min_she_rel
+ *   6. Heun (RK2) update.
+ *   7. totals: energy, entropy, charges, longitudinal work.
+ *
+ * The equations of motion are evaluated with generic 4x4 tensor algebra in a
+ * diagonal metric with explicit Christoffel symbols (Sec. "Notation"), i.e. the
+ * covariant formulas written out, not a specialised closed form.
+ *
+ * Compile with -ffp-contract=off so that the neighbour-acceptance test
+ * r^2 = dx*dx + dy*dy (+ dz*dz) < (2h)^2 rounds each product separately.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define HBARC 0.1973269804
+#define NAUX 18
+
+/* per-particle status bits */
+#define ST_FALLBACK 1u     /* table Newton failed, closed-form EoS used */
+#define ST_OUT_OF_TABLE 2u /* closed-form solution outside the table domain */
+#define ST_NOCONV 4u       /* no EoS solution */
+#define ST_NONFINITE 8u
+#define ST_CS2_CAPPED 16u
+#define ST_SOLVE_FAIL 32u  /* acceleration system singular */
+
+typedef struct {
+    int dim;     /* SPH dimensions: 2 (x, y) or 3 (x, y, eta|z) */
+    int milne;   /* 1: coordinates (tau, x, y, eta); 0: (t, x, y, z) */
+    int viscous; /* 0: ideal; 1: minimal Israel-Stewart shear + bulk */
+    int has_table;
+    double h;
+    /* closed-form EoS: p = T^4 [a0 + a1 (1 + tanh((T hc - Tc)/w))/2] + T^2 sum chi mu^2 / 2 */
+    double a0, a1, Tc_GeV, w_GeV;
+    double chi[3];
+    /* table: regular grid, row-major [T][muB][muS][muQ] */
+    int nT;
+    int nmu[3];
+    double T0, dT;
+    double mu0[3], dmu[3];
+    const double *tp, *ts, *tnB, *tnS, *tnQ;
+    /* transport */
+    double eta_over_s, zeta_peak, zeta_T_GeV, zeta_w_GeV;
+    double tau_pi_coef, tau_Pi_ratio, cs2_cap;
+    /* Newton */
+    double newton_tol;
+    int newton_maxit;
+    int pad;
+} oc_params;
+
+/* ------------------------------------------------------------------------ */
+/* cubic spline kernel (Sec. "Kernel function")                              */
+/* ------------------------------------------------------------------------ */
+static double sigma_d(int dim, double h)
+{
+    if (dim == 1) return 2.0 / (3.0 * h);
+    if (dim == 2) return 10.0 / (7.0 * M_PI * h * h);
+    return 1.0 / (M_PI * h * h * h);
+}
+
+double oc_W(double r, double h, int dim)
+{
+    double q = r / h;
+    double sd = sigma_d(dim, h);
+    if (q <= 1.0) return sd * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+    if (q <= 2.0) return sd * 0.25 * (2.0 - q) * (2.0 - q) * (2.0 - q);
+    return 0.0;
+}
+
+/* dW/dr: the gradient formula of the paper is (dW/dr) (r_a - r_b)/r */
+double oc_dWdr(double r, double h, int dim)
+{
+    double q = r / h;
+    double sd = sigma_d(dim, h);
+    if (q <= 1.0) return sd / h * (-3.0 * q + 2.25 * q * q);
+    if (q <= 2.0) return sd / h * (-0.75 * (2.0 - q) * (2.0 - q));
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* cells, Morton keys, neighbour pairs                                       */
+/* ------------------------------------------------------------------------ */
+static double r2_of(int dim, const double *x, long n, long a, long b)
+{
+    double r2 = 0.0;
+    for (int d = 0; d < dim; ++d) {
+        double dx = x[d * n + a] - x[d * n + b];
+        double sq = dx * dx;
+        r2 = r2 + sq;
+    }
+    return r2;
+}
+
+/* cell coordinates c_d = floor((x_d - min_a x_d) * (1/(2h))) */
+void oc_cell_coords(long n, int dim, const double *x, double h, int *cc, double *xmin_out)
+{
+    double inv_cell = 1.0 / (2.0 * h);
+    for (int d = 0; d < dim; ++d) {
+        double m = INFINITY;
+        for (long a = 0; a < n; ++a)
+            if (x[d * n + a] < m) m = x[d * n + a];
+        xmin_out[d] = m;
+        for (long a = 0; a < n; ++a) cc[d * n + a] = (int)floor((x[d * n + a] - m) * inv_cell);
+    }
+}
+
+/* Morton key: bit (dim*b + d) of the key is bit b of c_d */
+uint64_t oc_morton(int dim, const int *c)
+{
+    uint64_t key = 0;
+    int bits = dim == 2 ? 32 : 21;
+    for (int b = 0; b < bits; ++b)
+        for (int d = 0; d < dim; ++d) key |= (uint64_t)(((unsigned)c[d] >> b) & 1u) << (dim * b + d);
+    return key;
+}
+
+typedef struct {
+    uint64_t key;
+    long id;
+} keyid;
+
+static int cmp_keyid(const void *pa, const void *pb)
+{
+    const keyid *a = (const keyid *)pa, *b = (const keyid *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+/* Morton keys and the permutation that sorts particles by (key, id) */
+void oc_sort_by_cell(long n, int dim, const double *x, double h, int *cc, uint64_t *keys, long *perm)
+{
+    double xmin[3];
+    oc_cell_coords(n, dim, x, h, cc, xmin);
+    keyid *t = (keyid *)malloc(sizeof(keyid) * (size_t)(n > 0 ? n : 1));
+    for (long a = 0; a < n; ++a) {
+        int c[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) c[d] = cc[d * n + a];
+        keys[a] = oc_morton(dim, c);
+        t[a].key = keys[a];
+        t[a].id = a;
+    }
+    qsort(t, (size_t)n, sizeof(keyid), cmp_keyid);
+    for (long j = 0; j < n; ++j) perm[j] = t[j].id;
+    free(t);
+}
+
+/* all ordered pairs (a, b) with r_ab^2 < (2h)^2, self pairs included, sorted by (a, b) */
+long oc_neighbors_brute(long n, int dim, const double *x, double h, long cap, int *pa, int *pb)
+{
+    double two_h = 2.0 * h;
+    double supp2 = two_h * two_h;
+    long cnt = 0;
+    for (long a = 0; a < n; ++a)
+        for (long b = 0; b < n; ++b)
+            if (r2_of(dim, x, n, a, b) < supp2) {
+                if (cnt < cap) {
+                    pa[cnt] = (int)a;
+                    pb[cnt] = (int)b;
+                }
+                ++cnt;
+            }
+    return cnt;
+}
+
+/* uniform cell list: cells of side 2h, particles bucketed in id order */
+typedef struct {
+    int dim;
+    long n;
+    int nc[3];
+    long ncell;
+    int *cc;      /* [dim][n] */
+    long *start;  /* [ncell + 1] */
+    long *items;  /* [n] */
+} grid_t;
+
+static long lin_cell(const grid_t *g, const int *c)
+{
+    long l = 0;
+    for (int d = g->dim - 1; d >= 0; --d) l = l * g->nc[d] + c[d];
+    return l;
+}
+
+static void grid_build(grid_t *g, long n, int dim, const double *x, double h)
+{
+    double xmin[3];
+    g->dim = dim;
+    g->n = n;
+    g->cc = (int *)malloc(sizeof(int) * (size_t)(dim * (n > 0 ? n : 1)));
+    oc_cell_coords(n, dim, x, h, g->cc, xmin);
+    g->ncell = 1;
+    for (int d = 0; d < 3; ++d) g->nc[d] = 1;
+    for (int d = 0; d < dim; ++d) {
+        int m = 0;
+        for (long a = 0; a < n; ++a)
+            if (g->cc[d * n + a] > m) m = g->cc[d * n + a];
+        g->nc[d] = m + 1;
+        g->ncell *= g->nc[d];
+    }
+    g->start = (long *)calloc((size_t)g->ncell + 1, sizeof(long));
+    g->items = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    long *cell_of = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    for (long a = 0; a < n; ++a) {
+        int c[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) c[d] = g->cc[d * n + a];
+        cell_of[a] = lin_cell(g, c);
+        g->start[cell_of[a] + 1]++;
+    }
+    for (long c = 0; c < g->ncell; ++c) g->start[c + 1] += g->start[c];
+    long *fill = (long *)malloc(sizeof(long) * (size_t)g->ncell);
+    memcpy(fill, g->start, sizeof(long) * (size_t)g->ncell);
+    for (long a = 0; a < n; ++a) g->items[fill[cell_of[a]]++] = a;
+    free(fill);
+    free(cell_of);
+}
+
+static void grid_free(grid_t *g)
+{
+    free(g->cc);
+    free(g->start);
+    free(g->items);
+}
+
+/* visit every candidate b in the 3^dim cells around a's cell, in increasing b */
+typedef void (*pair_fn)(long a, long b, double r2, void *ctx);
+
+static int cmp_long(const void *pa, const void *pb)
+{
+    long a = *(const long *)pa, b = *(const long *)pb;
+    return (a > b) - (a < b);
+}
+
+static long grid_neighbors(const grid_t *g, const double *x, double supp2, long a, long *buf)
+{
+    long n = g->n, cnt = 0;
+    int dim = g->dim;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+        lo[d] = g->cc[d * n + a] - 1;
+        hi[d] = g->cc[d * n + a] + 1;
+        if (lo[d] < 0) lo[d] = 0;
+        if (hi[d] > g->nc[d] - 1) hi[d] = g->nc[d] - 1;
+    }
+    int c[3];
+    for (c[2] = lo[2]; c[2] <= hi[2]; ++c[2])
+        for (c[1] = lo[1]; c[1] <= hi[1]; ++c[1])
+            for (c[0] = lo[0]; c[0] <= hi[0]; ++c[0]) {
+                long l = lin_cell(g, c);
+                for (long k = g->start[l]; k < g->start[l + 1]; ++k) {
+                    long b = g->items[k];
+                    if (r2_of(dim, x, n, a, b) < supp2) buf[cnt++] = b;
+                }
+            }
+    qsort(buf, (size_t)cnt, sizeof(long), cmp_long);
+    return cnt;
+}
+
+long oc_neighbors_cells(long n, int dim, const double *x, double h, long cap, int *pa, int *pb)
+{
+    grid_t g;
+    grid_build(&g, n, dim, x, h);
+    double two_h = 2.0 * h;
+    double supp2 = two_h * two_h;
+    long *buf = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    long cnt = 0;
+    for (long a = 0; a < n; ++a) {
+        long m = grid_neighbors(&g, x, supp2, a, buf);
+        for (long k = 0; k < m; ++k) {
+            if (cnt < cap) {
+                pa[cnt] = (int)a;
+                pb[cnt] = (int)buf[k];
+            }
+            ++cnt;
+        }
+    }
+    free(buf);
+    grid_free(&g);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* equation of state                                                         */
+/* ------------------------------------------------------------------------ */
+static void an_f(const oc_params *P, double T, double *f, double *fp, double *fpp)
+{
+    double x = T * HBARC;
+    double th = tanh((x - P->Tc_GeV) / P->w_GeV);
+    double sech2 = 1.0 - th * th;
+    double k = HBARC / P->w_GeV;
+    *f = P->a0 + P->a1 * (1.0 + th) / 2.0;
+    *fp = P->a1 / 2.0 * sech2 * k;
+    *fpp = -P->a1 * sech2 * th * k * k;
+}
+
+/* closed form: p, (s, n) and H = d(s, n)/d(T, mu) */
+void oc_eos_analytic(const oc_params *P, double T, const double *mu, double *p, double *sn, double *H)
+{
+    double f, fp, fpp;
+    an_f(P, T, &f, &fp, &fpp);
+    double cm2 = 0.0;
+    for (int q = 0; q < 3; ++q) cm2 += P->chi[q] * mu[q] * mu[q];
+    *p = T * T * T * T * f + T * T * cm2 / 2.0;
+    sn[0] = 4.0 * T * T * T * f + T * T * T * T * fp + T * cm2;
+    for (int q = 0; q < 3; ++q) sn[1 + q] = P->chi[q] * T * T * mu[q];
+    if (H) {
+        memset(H, 0, sizeof(double) * 16);
+        H[0] = 12.0 * T * T * f + 8.0 * T * T * T * fp + T * T * T * T * fpp + cm2;
+        for (int q = 0; q < 3; ++q) {
+            H[0 * 4 + 1 + q] = 2.0 * P->chi[q] * T * mu[q];
+            H[(1 + q) * 4 + 0] = 2.0 * P->chi[q] * T * mu[q];
+            H[(1 + q) * 4 + 1 + q] = P->chi[q] * T * T;
+        }
+    }
+}
+
+/* closed-form inversion: mu_q = n_q/(chi_q T^2) reduces it to one equation in T,
+   g(T) = 4 T^3 f + T^4 f' + sum_q n_q^2/(chi_q T^3) - s = 0, solved on its upper
+   branch by a bracketed, bisection-safeguarded Newton iteration. */
+static void an_g(const oc_params *P, double T, double s, const double *n, double *g, double *gp)
+{
+    double f, fp, fpp;
+    an_f(P, T, &f, &fp, &fpp);
+    double c = 0.0;
+    for (int q = 0; q < 3; ++q)
+        if (P->chi[q] > 0.0) c += n[q] * n[q] / P->chi[q];
+    *g = 4.0 * T * T * T * f + T * T * T * T * fp + c / (T * T * T) - s;
+    *gp = 12.0 * T * T * f + 8.0 * T * T * T * fp + T * T * T * T * fpp - 3.0 * c / (T * T * T * T);
+}
+
+int oc_eos_invert_analytic(const oc_params *P, double s, const double *n, double *T_out, double *mu_out)
+{
+    if (!(s > 0.0) || !isfinite(s)) return ST_NOCONV;
+    for (int q = 0; q < 3; ++q) {
+        if (!isfinite(n[q])) return ST_NONFINITE;
+        if (!(P->chi[q] > 0.0) && n[q] != 0.0) return ST_NOCONV;
+    }
+    double Thi = cbrt(s / (4.0 * P->a0));
+    double g, gp;
+    an_g(P, Thi, s, n, &g, &gp);
+    double Tlo = Thi, gprev = g;
+    int found = (g <= 0.0);
+    if (found) Tlo = Thi;
+    for (int k = 0; k < 400 && !found; ++k) {
+        Tlo = 0.8 * Tlo;
+        double gl, gpl;
+        an_g(P, Tlo, s, n, &gl, &gpl);
+        if (gl <= 0.0) {
+            found = 1;
+            break;
+        }
+        if (gl > gprev) return ST_NOCONV; /* passed the minimum of g: no root */
+        gprev = gl;
+    }
+    if (!found) return ST_NOCONV;
+    double T = Thi;
+    if (g == 0.0) {
+        Tlo = Thi;
+    }
+    for (int it = 0; it < 200; ++it) {
+        an_g(P, T, s, n, &g, &gp);
+        if (g == 0.0) break;
+        if (g > 0.0) Thi = T;
+        else Tlo = T;
+        double Tn = T - g / gp;
+        if (!(gp > 0.0) || !(Tn > Tlo && Tn < Thi)) Tn = 0.5 * (Tlo + Thi);
+        if (fabs(Tn - T) <= 4e-16 * T) {
+            T = Tn;
+            break;
+        }
+        T = Tn;
+    }
+    *T_out = T;
+    for (int q = 0; q < 3; ++q) mu_out[q] = P->chi[q] > 0.0 ? n[q] / (P->chi[q] * T * T) : 0.0;
+    return 0;
+}
+
+/* quadrilinear interpolation of the table (value and gradient), plain 16-corner sum */
+static long tab_node(const oc_params *P, int iT, int iB, int iS, int iQ)
+{
+    return (((long)iT * P->nmu[0] + iB) * P->nmu[1] + iS) * P->nmu[2] + iQ;
+}
+
+static void tab_locate(double v, double v0, double dv, int nv, int *i, double *t)
+{
+    double r = (v - v0) / dv;
+    int k = (int)floor(r);
+    if (k < 0) k = 0;
+    if (k > nv - 2) k = nv - 2;
+    *i = k;
+    *t = r - (double)k;
+}
+
+/* out: value of p, s, nB, nS, nQ at x; J[4][4] = d(s,nB,nS,nQ)/d(T,muB,muS,muQ) */
+void oc_eos_table(const oc_params *P, const double *x, double *pv, double *sn, double *J)
+{
+    int idx[4];
+    double t[4], inv[4];
+    tab_locate(x[0], P->T0, P->dT, P->nT, &idx[0], &t[0]);
+    inv[0] = 1.0 / P->dT;
+    for (int q = 0; q < 3; ++q) {
+        tab_locate(x[1 + q], P->mu0[q], P->dmu[q], P->nmu[q], &idx[1 + q], &t[1 + q]);
+        inv[1 + q] = 1.0 / P->dmu[q];
+    }
+    const double *fld[5] = {P->ts, P->tnB, P->tnS, P->tnQ, P->tp};
+    double val[5] = {0, 0, 0, 0, 0};
+    double der[4][4];
+    memset(der, 0, sizeof(der));
+    for (int c = 0; c < 16; ++c) {
+        int bit[4] = {(c >> 3) & 1, (c >> 2) & 1, (c >> 1) & 1, c & 1};
+        double w[4], dw[4];
+        for (int k = 0; k < 4; ++k) {
+            w[k] = bit[k] ? t[k] : 1.0 - t[k];
+            dw[k] = (bit[k] ? 1.0 : -1.0) * inv[k];
+        }
+        long node = tab_node(P, idx[0] + bit[0], idx[1] + bit[1], idx[2] + bit[2], idx[3] + bit[3]);
+        double wall = w[0] * w[1] * w[2] * w[3];
+        for (int f = 0; f < 5; ++f) val[f] += wall * fld[f][node];
+        for (int k = 0; k < 4; ++k) {
+            double wk = dw[k];
+            for (int m = 0; m < 4; ++m)
+                if (m != k) wk *= w[m];
+            for (int f = 0; f < 4; ++f) der[f][k] += wk * fld[f][node];
+        }
+    }
+    if (pv) *pv = val[4];
+    for (int f = 0; f < 4; ++f) sn[f] = val[f];
+    if (J)
+        for (int f = 0; f < 4; ++f)
+            for (int k = 0; k < 4; ++k) J[f * 4 + k] = der[f][k];
+}
+
+/* Gaussian elimination with partial pivoting, A (m x m, row major) x = b; returns 0 on success */
+static int gauss_solve(int m, double *A, double *b)
+{
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < m; ++r)
+            if (fabs(A[r * m + c]) > fabs(A[piv * m + c])) piv = r;
+        if (!(fabs(A[piv * m + c]) > 0.0) || !isfinite(A[piv * m + c])) return -1;
+        if (piv != c) {
+            for (int k = 0; k < m; ++k) {
+                double tmp = A[c * m + k];
+                A[c * m + k] = A[piv * m + k];
+                A[piv * m + k] = tmp;
+            }
+            double tmp = b[c];
+            b[c] = b[piv];
+            b[piv] = tmp;
+        }
+        for (int r = c + 1; r < m; ++r) {
+            double f = A[r * m + c] / A[c * m + c];
+            for (int k = c; k < m; ++k) A[r * m + k] -= f * A[c * m + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < m; ++k) acc -= A[r * m + k] * b[k];
+        b[r] = acc / A[r * m + r];
+    }
+    return 0;
+}
+
+static int in_table(const oc_params *P, const double *x)
+{
+    if (!(x[0] >= P->T0 && x[0] <= P->T0 + (P->nT - 1) * P->dT)) return 0;
+    for (int q = 0; q < 3; ++q)
+        if (!(x[1 + q] >= P->mu0[q] && x[1 + q] <= P->mu0[q] + (P->nmu[q] - 1) * P->dmu[q])) return 0;
+    return 1;
+}
+
+static void clamp_table(const oc_params *P, double *x)
+{
+    double hiT = P->T0 + (P->nT - 1) * P->dT;
+    if (x[0] < P->T0) x[0] = P->T0;
+    if (x[0] > hiT) x[0] = hiT;
+    for (int q = 0; q < 3; ++q) {
+        double lo = P->mu0[q], hi = P->mu0[q] + (P->nmu[q] - 1) * P->dmu[q];
+        if (x[1 + q] < lo) x[1 + q] = lo;
+        if (x[1 + q] > hi) x[1 + q] = hi;
+    }
+}
+
+static double resid_inf(const oc_params *P, const double *x, double s, const double *n, double *r, double *J)
+{
+    double sn[4];
+    oc_eos_table(P, x, NULL, sn, J);
+    double tgt[4] = {s, n[0], n[1], n[2]};
+    double m = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        r[k] = (sn[k] - tgt[k]) / s;
+        if (fabs(r[k]) > m || !isfinite(r[k])) m = isfinite(r[k]) ? fabs(r[k]) : INFINITY;
+    }
+    if (J)
+        for (int k = 0; k < 16; ++k) J[k] /= s;
+    return m;
+}
+
+/* damped Newton on the table interpolant, started from x; 0 = converged */
+static int table_newton(const oc_params *P, double s, const double *n, double *x)
+{
+    double r[4], J[16];
+    double rn = resid_inf(P, x, s, n, r, J);
+    for (int it = 0; it < P->newton_maxit; ++it) {
+        if (rn <= P->newton_tol) {
+            /* one polishing step, taken only if it does not increase the residual */
+            double A[16], d[4], xn[4], rr[4];
+            memcpy(A, J, sizeof(A));
+            for (int k = 0; k < 4; ++k) d[k] = -r[k];
+            if (gauss_solve(4, A, d) == 0) {
+                for (int k = 0; k < 4; ++k) xn[k] = x[k] + d[k];
+                clamp_table(P, xn);
+                double rnn = resid_inf(P, xn, s, n, rr, NULL);
+                if (rnn <= rn) memcpy(x, xn, sizeof(xn));
+            }
+            return 0;
+        }
+        double A[16], d[4];
+        memcpy(A, J, sizeof(A));
+        for (int k = 0; k < 4; ++k) d[k] = -r[k];
+        if (gauss_solve(4, A, d) != 0) return -1;
+        double lam = 1.0, xn[4], rr[4], Jn[16], rnn = INFINITY;
+        for (int ls = 0; ls <= 8; ++ls) {
+            for (int k = 0; k < 4; ++k) xn[k] = x[k] + lam * d[k];
+            clamp_table(P, xn);
+            rnn = resid_inf(P, xn, s, n, rr, Jn);
+            if (rnn < rn) break;
+            lam *= 0.5;
+        }
+        memcpy(x, xn, sizeof(xn));
+        memcpy(r, rr, sizeof(rr));
+        memcpy(J, Jn, sizeof(Jn));
+        rn = rnn;
+    }
+    return rn <= P->newton_tol ? 0 : -1;
+}
+
+/* out[0..10]: T, muB, muS, muQ, p, e, p_s, p_nB, p_nS, p_nQ, cs2 (after the cap) */
+unsigned oc_eos_invert(const oc_params *P, double s, const double *n, double *out)
+{
+    unsigned st = 0;
+    for (int k = 0; k < 11; ++k) out[k] = 0.0;
+    if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) return ST_NONFINITE | ST_NOCONV;
+    double x[4];
+    int r = oc_eos_invert_analytic(P, s, n, &x[0], &x[1]);
+    if (r != 0) return (unsigned)r | ST_NOCONV;
+    double p, H[16], sn[4];
+    int use_table = 0;
+    if (P->has_table) {
+        if (in_table(P, x)) {
+            double xt[4];
+            memcpy(xt, x, sizeof(xt));
+            if (table_newton(P, s, n, xt) == 0) {
+                memcpy(x, xt, sizeof(xt));
+                use_table = 1;
+            } else {
+                st |= ST_FALLBACK;
+            }
+        } else {
+            st |= ST_OUT_OF_TABLE;
+        }
+    }
+    if (use_table) {
+        oc_eos_table(P, x, &p, sn, H);
+    } else {
+        oc_eos_analytic(P, x[0], &x[1], &p, sn, H);
+    }
+    double e = x[0] * s + x[1] * n[0] + x[2] * n[1] + x[3] * n[2] - p;
+    /* (p_s, p_n) = H^{-T} (s, n): dp = s dT + n.dmu with (dT, dmu) = H^{-1} (ds, dn) */
+    /* only the charge directions the EoS couples to take part (chi_q = 0 and no table:
+       n_q = 0 identically and p_{n_q} = 0) */
+    int act[4], m = 0;
+    for (int k = 0; k < 4; ++k)
+        if (k == 0 || use_table || P->chi[k - 1] > 0.0) act[m++] = k;
+    double A[16], zr[4], z[4] = {0, 0, 0, 0}, tgt[4] = {s, n[0], n[1], n[2]};
+    for (int i = 0; i < m; ++i) {
+        zr[i] = tgt[act[i]];
+        for (int j = 0; j < m; ++j) A[i * m + j] = H[act[j] * 4 + act[i]];
+    }
+    if (gauss_solve(m, A, zr) != 0) return st | ST_NOCONV;
+    for (int i = 0; i < m; ++i) z[act[i]] = zr[i];
+    double cs2 = (s * z[0] + n[0] * z[1] + n[1] * z[2] + n[2] * z[3]) / (e + p);
+    if (cs2 > P->cs2_cap) {
+        double f = P->cs2_cap / cs2;
+        for (int k = 0; k < 4; ++k) z[k] *= f;
+        cs2 = P->cs2_cap;
+        st |= ST_CS2_CAPPED;
+    }
+    out[0] = x[0];
+    out[1] = x[1];
+    out[2] = x[2];
+    out[3] = x[3];
+    out[4] = p;
+    out[5] = e;
+    for (int k = 0; k < 4; ++k) out[6 + k] = z[k];
+    out[10] = cs2;
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* geometry: diagonal metric, Christoffel symbols (Sec. "Notation")          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double g[4], gi[4], dg[4]; /* g_mu mu, g^mu mu, d g_mu mu / dx0 */
+    double G[4][4][4];         /* Gamma^a_{bc} */
+    double sqrtg;
+} geom_t;
+
+static void make_geom(int milne, double tau, geom_t *G)
+{
+    memset(G, 0, sizeof(*G));
+    G->g[0] = 1.0;
+    G->g[1] = G->g[2] = G->g[3] = -1.0;
+    G->sqrtg = 1.0;
+    if (milne) {
+        G->g[3] = -tau * tau;
+        G->dg[3] = -2.0 * tau;
+        G->G[0][3][3] = tau;
+        G->G[3][0][3] = 1.0 / tau;
+        G->G[3][3][0] = 1.0 / tau;
+        G->sqrtg = tau;
+    }
+    for (int m = 0; m < 4; ++m) G->gi[m] = 1.0 / G->g[m];
+}
+
+/* stored independent shear components, 4D index pairs (1 = x, 2 = y, 3 = eta|z) */
+static int npi_of(int dim) { return dim == 2 ? 3 : 5; }
+static const int PI2[3][2] = {{1, 1}, {1, 2}, {2, 2}};
+static const int PI3[5][2] = {{1, 1}, {1, 2}, {1, 3}, {2, 2}, {2, 3}};
+
+/* full contravariant pi^{mu nu} from the stored spatial components using
+   transversality u_mu pi^{mu nu} = 0 and tracelessness g_mu nu pi^{mu nu} = 0 */
+static void pi_full(int dim, const geom_t *G, const double *u, const double *stored, double pi[4][4])
+{
+    memset(pi, 0, sizeof(double) * 16);
+    int np = npi_of(dim);
+    for (int k = 0; k < np; ++k) {
+        int i = dim == 2 ? PI2[k][0] : PI3[k][0], j = dim == 2 ? PI2[k][1] : PI3[k][1];
+        pi[i][j] = pi[j][i] = stored[k];
+    }
+    double ul[4];
+    for (int m = 0; m < 4; ++m) ul[m] = G->g[m] * u[m];
+    /* pi^{33}: unknown in the trace; pi^{00} = sum_jk u_j u_k pi^{jk} / u_0^2 */
+    double known = 0.0;
+    for (int j = 1; j < 4; ++j)
+        for (int k = 1; k < 4; ++k)
+            if (!(j == 3 && k == 3)) known += ul[j] * ul[k] * pi[j][k];
+    known /= ul[0] * ul[0];
+    for (int i = 1; i < 3; ++i) known += G->g[i] * pi[i][i];
+    double coef = ul[3] * ul[3] / (ul[0] * ul[0]) + G->g[3];
+    pi[3][3] = -known / coef;
+    for (int i = 1; i < 4; ++i) {
+        double acc = 0.0;
+        for (int j = 1; j < 4; ++j) acc += ul[j] * pi[j][i];
+        pi[0][i] = pi[i][0] = -acc / ul[0];
+    }
+    double acc = 0.0;
+    for (int j = 1; j < 4; ++j) acc += ul[j] * pi[j][0];
+    pi[0][0] = -acc / ul[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* equations of motion at one particle                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int dim, viscous;
+    double u[4];        /* contravariant, u[0] = u^0 */
+    double dudx[4][4];  /* dudx[k][j] = d_k u^j (spatial k, j) */
+    double s, n[3], sigma, T, mu[3], p, e, ps, pn[3];
+    double Pi, Bv;
+    double pi[4][4], Pv[4][4]; /* pi^{mu nu} and pi^{mu nu}/sigma */
+    double eta, zeta, taupi, tauPi;
+} ppart;
+
+typedef struct {
+    double dP[4];       /* d/dx0 of P^i = sqrt(-g) T^{0i} / sigma* */
+    double dS, dBv;
+    double dPv[4][4];
+    double theta;
+} prates;
+
+/* every rate as a function of a trial acceleration a^i = du^i/dx0 (linear in a) */
+static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
+{
+    const double *u = q->u;
+    double u0 = u[0];
+    double v[4] = {1.0, u[1] / u0, u[2] / u0, u[3] / u0};
+    /* du^0/dx0 from u.u = 1 (paper's eq. unu) */
+    double acc = 0.0;
+    for (int i = 1; i < 4; ++i) acc += 2.0 * G->g[i] * u[i] * a[i] + u[i] * u[i] * G->dg[i];
+    double du0 = -acc / (2.0 * u0);
+    double dudt[4] = {du0, a[1], a[2], a[3]};
+    /* partial derivatives d[mu][nu] = d_mu u^nu */
+    double d[4][4];
+    memset(d, 0, sizeof(d));
+    for (int k = 1; k < 4; ++k) {
+        double s0 = 0.0;
+        for (int j = 1; j < 4; ++j) {
+            d[k][j] = q->dudx[k][j];
+            s0 += G->g[j] * u[j] * q->dudx[k][j];
+        }
+        d[k][0] = -s0 / u0;
+    }
+    for (int nu = 0; nu < 4; ++nu) {
+        double conv = 0.0;
+        for (int k = 1; k < 4; ++k) conv += v[k] * d[k][nu];
+        d[0][nu] = dudt[nu] - conv;
+    }
+    double nab[4][4];
+    for (int m = 0; m < 4; ++m)
+        for (int nu = 0; nu < 4; ++nu) {
+            double c = 0.0;
+            for (int l = 0; l < 4; ++l) c += G->G[nu][m][l] * u[l];
+            nab[m][nu] = d[m][nu] + c;
+        }
+    double theta = 0.0;
+    for (int m = 0; m < 4; ++m) theta += nab[m][m];
+    double Du[4];
+    for (int nu = 0; nu < 4; ++nu) {
+        double c = 0.0;
+        for (int m = 0; m < 4; ++m) c += u[m] * nab[m][nu];
+        Du[nu] = c;
+    }
+    double sig[4][4];
+    for (int m = 0; m < 4; ++m)
+        for (int nu = 0; nu < 4; ++nu) {
+            double Delta = (m == nu ? G->gi[m] : 0.0) - u[m] * u[nu];
+            sig[m][nu] = 0.5 * (G->gi[m] * nab[m][nu] + G->gi[nu] * nab[nu][m]) - 0.5 * (u[m] * Du[nu] + u[nu] * Du[m]) -
+                         Delta * theta / 3.0;
+        }
+    R->theta = theta;
+    double dsig = -q->sigma * theta / u0;
+    memset(R->dPv, 0, sizeof(R->dPv));
+    if (q->viscous) {
+        double pisig = 0.0;
+        for (int m = 0; m < 4; ++m)
+            for (int nu = 0; nu < 4; ++nu) pisig += q->pi[m][nu] * G->g[m] * G->g[nu] * sig[m][nu];
+        R->dS = (-q->Pi * theta + pisig) / (u0 * q->sigma * q->T);
+        R->dBv = -(q->Pi + q->zeta * theta) / (q->tauPi * u0 * q->sigma);
+        double alow[4];
+        for (int al = 0; al < 4; ++al) alow[al] = G->g[al] * Du[al];
+        for (int i = 1; i < 4; ++i)
+            for (int j = 1; j < 4; ++j) {
+                double chr = 0.0;
+                for (int m = 0; m < 4; ++m)
+                    for (int l = 0; l < 4; ++l) chr += u[m] * (G->G[i][m][l] * q->pi[l][j] + G->G[j][m][l] * q->pi[i][l]);
+                double pja = 0.0, pia = 0.0;
+                for (int al = 0; al < 4; ++al) {
+                    pja += q->pi[j][al] * alow[al];
+                    pia += q->pi[i][al] * alow[al];
+                }
+                double coup = u[i] * pja + u[j] * pia;
+                double rhs = (-q->pi[i][j] + 2.0 * q->eta * sig[i][j] - 4.0 / 3.0 * q->taupi * q->pi[i][j] * theta) / q->taupi;
+                double dpi = (rhs - chr - coup) / u0;
+                R->dPv[i][j] = dpi / q->sigma - q->pi[i][j] * dsig / (q->sigma * q->sigma);
+            }
+    } else {
+        R->dS = 0.0;
+        R->dBv = 0.0;
+    }
+    double ds = q->sigma * R->dS + (q->s / q->sigma) * dsig;
+    double dPi = q->sigma * R->dBv + q->Bv * dsig;
+    double dw = (q->T + q->ps) * ds + dPi;
+    for (int c = 0; c < 3; ++c) dw += (q->mu[c] + q->pn[c]) * (q->n[c] / q->sigma) * dsig;
+    double w = q->e + q->p + q->Pi;
+    for (int i = 1; i < 4; ++i) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int j = 1; j < 4; ++j) {
+            t1 += G->dg[j] * u[j] * q->Pv[j][i] + G->g[j] * a[j] * q->Pv[j][i] + G->g[j] * u[j] * R->dPv[j][i];
+            t2 += G->g[j] * u[j] * q->Pv[j][i];
+        }
+        double dpi0 = -t1 / (u0 * u0) + 2.0 * t2 * du0 / (u0 * u0 * u0);
+        R->dP[i] = (u[i] / q->sigma) * dw + (w / q->sigma) * a[i] - (w * u[i] / (q->sigma * q->sigma)) * dsig + dpi0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* one stage: neighbours, densities, EoS, gradients, rates                   */
+/* ------------------------------------------------------------------------ */
+static int nv_of(int dim) { return 2 * dim + 2 + npi_of(dim); }
+
+/* y layout [nv][n]: x^1..x^dim, u^1..u^dim, S, Pi/sigma, pi^{ij}/sigma (stored comps)
+   aux layout [NAUX][n]: sigma*, s, nB, nS, nQ, T, muB, muS, muQ, p, e, cs2, theta, Pi,
+                         u0, neighbour count, sigma, status
+   grad layout [dim*dim + dim][n]: d_k u^j (k major), F^i                              */
+static void densities_eos(const oc_params *P, long n, double tau, const double *y, const double *Nq, grid_t *g,
+                          double *aux, unsigned *status)
+{
+    int dim = P->dim;
+    double two_h = 2.0 * P->h;
+    double supp2 = two_h * two_h;
+    geom_t G;
+    make_geom(P->milne, tau, &G);
+#pragma omp parallel
+    {
+        long *buf = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 64)
+        for (long a = 0; a < n; ++a) {
+            long m = grid_neighbors(g, y, supp2, a, buf);
+            double sig = 0.0, ss = 0.0, nn[3] = {0, 0, 0};
+            for (long k = 0; k < m; ++k) {
+                long b = buf[k];
+                double r = sqrt(r2_of(dim, y, n, a, b));
+                double W = oc_W(r, P->h, dim);
+                sig += W;
+                ss += y[(2 * dim) * n + b] * W;
+                for (int c = 0; c < 3; ++c) nn[c] += Nq[c * n + b] * W;
+            }
+            double uu = 0.0;
+            for (int i = 0; i < dim; ++i) {
+                double ui = y[(dim + i) * n + a];
+                uu += -G.g[1 + i] * ui * ui;
+            }
+            double u0 = sqrt(1.0 + uu);
+            double vol = u0 * G.sqrtg;
+            aux[0 * n + a] = sig;
+            aux[1 * n + a] = ss / vol;
+            for (int c = 0; c < 3; ++c) aux[(2 + c) * n + a] = nn[c] / vol;
+            aux[14 * n + a] = u0;
+            aux[15 * n + a] = (double)m;
+            aux[16 * n + a] = sig / vol;
+            double out[11];
+            double nr[3] = {aux[2 * n + a], aux[3 * n + a], aux[4 * n + a]};
+            unsigned st = oc_eos_invert(P, aux[1 * n + a], nr, out);
+            for (int k = 0; k < 4; ++k) aux[(5 + k) * n + a] = out[k];
+            aux[9 * n + a] = out[4];
+            aux[10 * n + a] = out[5];
+            aux[11 * n + a] = out[10];
+            status[a] = st;
+            aux[17 * n + a] = (double)st;
+        }
+        free(buf);
+    }
+}
+
+/* EoS derivative outputs are kept aside for the rates */
+typedef struct {
+    double ps, pn[3];
+} eosder_t;
+
+int oc_stage(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *dydt, double *aux,
+             double *grad, unsigned *status, double *work_rate)
+{
+    int dim = P->dim, np = npi_of(dim), nv = nv_of(dim);
+    double two_h = 2.0 * P->h;
+    double supp2 = two_h * two_h;
+    geom_t G;
+    make_geom(P->milne, tau, &G);
+    grid_t g;
+    grid_build(&g, n, dim, y, P->h);
+    densities_eos(P, n, tau, y, Nq, &g, aux, status);
+
+    /* EoS derivatives again (kept out of aux), transport, full pi, X^{ji}/sigma*^2 */
+    eosder_t *ed = (eosder_t *)malloc(sizeof(eosder_t) * (size_t)(n > 0 ? n : 1));
+    double *Xs = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
+    double *us = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *pif = (double *)malloc(sizeof(double) * 16 * (size_t)(n > 0 ? n : 1));
+    double *Tfull = (double *)malloc(sizeof(double) * 16 * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+    for (long a = 0; a < n; ++a) {
+        double out[11];
+        double nr[3] = {aux[2 * n + a], aux[3 * n + a], aux[4 * n + a]};
+        oc_eos_invert(P, aux[1 * n + a], nr, out);
+        ed[a].ps = out[6];
+        for (int c = 0; c < 3; ++c) ed[a].pn[c] = out[7 + c];
+        double u[4] = {aux[14 * n + a], 0, 0, 0};
+        for (int i = 0; i < dim; ++i) u[1 + i] = y[(dim + i) * n + a];
+        double sigma = aux[16 * n + a];
+        double Pi = P->viscous ? sigma * y[(2 * dim + 1) * n + a] : 0.0;
+        double st[5] = {0, 0, 0, 0, 0};
+        if (P->viscous)
+            for (int k = 0; k < np; ++k) st[k] = sigma * y[(2 * dim + 2 + k) * n + a];
+        double pi[4][4];
+        pi_full(dim, &G, u, st, pi);
+        memcpy(&pif[16 * a], pi, sizeof(pi));
+        aux[13 * n + a] = Pi;
+        double p = aux[9 * n + a], e = aux[10 * n + a];
+        double sstar = aux[0 * n + a];
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) {
+                double X = -(p + Pi) * (j == i ? G.gi[1 + j] : 0.0) + pi[1 + j][1 + i] - (u[1 + j] / u[0]) * pi[0][1 + i];
+                Xs[9 * a + 3 * j + i] = X / (sstar * sstar);
+            }
+        for (int j = 0; j < 3; ++j) us[3 * a + j] = u[1 + j] / sstar;
+        for (int m = 0; m < 4; ++m)
+            for (int l = 0; l < 4; ++l) {
+                double Delta = (m == l ? G.gi[m] : 0.0) - u[m] * u[l];
+                Tfull[16 * a + 4 * m + l] = e * u[m] * u[l] - (p + Pi) * Delta + pi[m][l];
+            }
+    }
+
+    /* gradients */
+#pragma omp parallel
+    {
+        long *buf = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 64)
+        for (long a = 0; a < n; ++a) {
+            long m = grid_neighbors(&g, y, supp2, a, buf);
+            double du[3][3], F[3];
+            memset(du, 0, sizeof(du));
+            memset(F, 0, sizeof(F));
+            for (long k = 0; k < m; ++k) {
+                long b = buf[k];
+                double r2 = r2_of(dim, y, n, a, b);
+                if (r2 == 0.0) continue; /* grad W = 0 at r = 0 */
+                double r = sqrt(r2);
+                double dWdr = oc_dWdr(r, P->h, dim);
+                double gw[3] = {0, 0, 0};
+                for (int d = 0; d < dim; ++d) gw[d] = dWdr * (y[d * n + a] - y[d * n + b]) / r;
+                for (int kk = 0; kk < dim; ++kk)
+                    for (int j = 0; j < dim; ++j) du[kk][j] += us[3 * b + j] * gw[kk];
+                for (int i = 0; i < dim; ++i)
+                    for (int j = 0; j < dim; ++j) F[i] += (Xs[9 * a + 3 * j + i] + Xs[9 * b + 3 * j + i]) * gw[j];
+            }
+            for (int kk = 0; kk < dim; ++kk)
+                for (int j = 0; j < dim; ++j) grad[(kk * dim + j) * n + a] = du[kk][j];
+            for (int i = 0; i < dim; ++i) grad[(dim * dim + i) * n + a] = -G.sqrtg * F[i];
+        }
+        free(buf);
+    }
+
+    /* equations of motion */
+#pragma omp parallel for schedule(static)
+    for (long a = 0; a < n; ++a) {
+        ppart q;
+        memset(&q, 0, sizeof(q));
+        q.dim = dim;
+        q.viscous = P->viscous;
+        q.u[0] = aux[14 * n + a];
+        for (int i = 0; i < dim; ++i) q.u[1 + i] = y[(dim + i) * n + a];
+        for (int k = 0; k < dim; ++k)
+            for (int j = 0; j < dim; ++j) q.dudx[1 + k][1 + j] = grad[(k * dim + j) * n + a];
+        q.s = aux[1 * n + a];
+        for (int c = 0; c < 3; ++c) q.n[c] = aux[(2 + c) * n + a];
+        q.sigma = aux[16 * n + a];
+        q.T = aux[5 * n + a];
+        for (int c = 0; c < 3; ++c) q.mu[c] = aux[(6 + c) * n + a];
+        q.p = aux[9 * n + a];
+        q.e = aux[10 * n + a];
+        q.ps = ed[a].ps;
+        for (int c = 0; c < 3; ++c) q.pn[c] = ed[a].pn[c];
+        q.Pi = aux[13 * n + a];
+        q.Bv = P->viscous ? y[(2 * dim + 1) * n + a] : 0.0;
+        memcpy(q.pi, &pif[16 * a], sizeof(q.pi));
+        for (int m = 0; m < 4; ++m)
+            for (int l = 0; l < 4; ++l) q.Pv[m][l] = q.pi[m][l] / q.sigma;
+        if (P->viscous) {
+            q.eta = P->eta_over_s * q.s;
+            double dTg = q.T * HBARC - P->zeta_T_GeV;
+            q.zeta = P->zeta_peak * exp(-dTg * dTg / (2.0 * P->zeta_w_GeV * P->zeta_w_GeV)) * q.s;
+            q.taupi = P->tau_pi_coef * q.eta / (q.e + q.p);
+            q.tauPi = P->tau_Pi_ratio * q.taupi;
+        }
+        /* F^i: minus the SPH stress divergence, plus the Christoffel source */
+        double F[4] = {0, 0, 0, 0};
+        for (int i = 0; i < dim; ++i) {
+            double src = 0.0;
+            for (int m = 0; m < 4; ++m)
+                for (int l = 0; l < 4; ++l) src += G.G[1 + i][m][l] * Tfull[16 * a + 4 * m + l];
+            F[1 + i] = grad[(dim * dim + i) * n + a] - G.sqrtg * src / aux[0 * n + a];
+        }
+        /* M_ij = dP^i(e_j) - dP^i(0), c^i = dP^i(0); solve M a = F - c */
+        double zero[4] = {0, 0, 0, 0};
+        prates R0;
+        lhs_of(&q, &G, zero, &R0);
+        double M[9], rhs[3];
+        for (int j = 0; j < dim; ++j) {
+            double ej[4] = {0, 0, 0, 0};
+            ej[1 + j] = 1.0;
+            prates Rj;
+            lhs_of(&q, &G, ej, &Rj);
+            for (int i = 0; i < dim; ++i) M[i * dim + j] = Rj.dP[1 + i] - R0.dP[1 + i];
+        }
+        for (int i = 0; i < dim; ++i) rhs[i] = F[1 + i] - R0.dP[1 + i];
+        double acc4[4] = {0, 0, 0, 0};
+        if (gauss_solve(dim, M, rhs) == 0) {
+            for (int i = 0; i < dim; ++i) acc4[1 + i] = rhs[i];
+        } else {
+            status[a] |= ST_SOLVE_FAIL;
+            aux[17 * n + a] = (double)status[a];
+        }
+        prates R;
+        lhs_of(&q, &G, acc4, &R);
+        aux[12 * n + a] = R.theta;
+        for (int i = 0; i < dim; ++i) dydt[i * n + a] = q.u[1 + i] / q.u[0];
+        for (int i = 0; i < dim; ++i) dydt[(dim + i) * n + a] = acc4[1 + i];
+        dydt[(2 * dim) * n + a] = R.dS;
+        dydt[(2 * dim + 1) * n + a] = P->viscous ? R.dBv : 0.0;
+        for (int k = 0; k < np; ++k) {
+            int i = dim == 2 ? PI2[k][0] : PI3[k][0], j = dim == 2 ? PI2[k][1] : PI3[k][1];
+            dydt[(2 * dim + 2 + k) * n + a] = P->viscous ? R.dPv[i][j] : 0.0;
+        }
+    }
+    (void)nv;
+    /* longitudinal work rate: sum_a sqrt(-g) Gamma^0_{mu nu} T^{mu nu} / sigma* (serial, fixed order) */
+    double wr = 0.0;
+    for (long a = 0; a < n; ++a) {
+        double src = 0.0;
+        for (int m = 0; m < 4; ++m)
+            for (int l = 0; l < 4; ++l) src += G.G[0][m][l] * Tfull[16 * a + 4 * m + l];
+        wr += G.sqrtg * src / aux[0 * n + a];
+    }
+    *work_rate = wr;
+    free(ed);
+    free(Xs);
+    free(us);
+    free(pif);
+    free(Tfull);
+    grid_free(&g);
+    return 0;
+}
+
+/* densities and EoS only, at the current state (for read-out) */
+void oc_observe(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *aux, unsigned *status)
+{
+    grid_t g;
+    grid_build(&g, n, P->dim, y, P->h);
+    densities_eos(P, n, tau, y, Nq, &g, aux, status);
+    for (long a = 0; a < n; ++a) aux[13 * n + a] = P->viscous ? aux[16 * n + a] * y[(2 * P->dim + 1) * n + a] : 0.0;
+    grid_free(&g);
+}
+
+/* Heun: y1 = y0 + dt f(t, y0); y = ((y0 + y1) + dt f(t + dt, y1)) / 2.
+   work accumulates the longitudinal work integral with the same quadrature. */
+int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, double *y, const double *Nq, double *aux,
+            double *grad, unsigned *status, unsigned *status_or, double *work)
+{
+    int nv = nv_of(P->dim);
+    size_t sz = sizeof(double) * (size_t)nv * (size_t)(n > 0 ? n : 1);
+    double *k = (double *)malloc(sz);
+    double *y1 = (double *)malloc(sz);
+    unsigned acc = 0;
+    for (int step = 0; step < nsteps; ++step) {
+        double wr0, wr1;
+        oc_stage(P, n, *tau, y, Nq, k, aux, grad, status, &wr0);
+        for (long a = 0; a < n; ++a) acc |= status[a];
+        for (long i = 0; i < (long)nv * n; ++i) y1[i] = y[i] + dtau * k[i];
+        oc_stage(P, n, *tau + dtau, y1, Nq, k, aux, grad, status, &wr1);
+        for (long a = 0; a < n; ++a) acc |= status[a];
+        for (long i = 0; i < (long)nv * n; ++i) y[i] = 0.5 * ((y[i] + y1[i]) + dtau * k[i]);
+        *work += 0.5 * dtau * (wr0 + wr1);
+        *tau = *tau + dtau;
+    }
+    *status_or = acc;
+    free(k);
+    free(y1);
+    return 0;
+}
+
+/* totals at the current state: [0] E = sum sqrt(-g) T^{00}/sigma*, [1] sum S, [2..4] sum N_q
+   (serial sums in particle order); needs aux from oc_observe */
+void oc_totals(const oc_params *P, long n, double tau, const double *y, const double *Nq, const double *aux, double *tot)
+{
+    int dim = P->dim, np = npi_of(dim);
+    geom_t G;
+    make_geom(P->milne, tau, &G);
+    double E = 0.0, S = 0.0, N[3] = {0, 0, 0};
+    for (long a = 0; a < n; ++a) {
+        double u[4] = {aux[14 * n + a], 0, 0, 0};
+        for (int i = 0; i < dim; ++i) u[1 + i] = y[(dim + i) * n + a];
+        double sigma = aux[16 * n + a];
+        double st[5] = {0, 0, 0, 0, 0};
+        if (P->viscous)
+            for (int k = 0; k < np; ++k) st[k] = sigma * y[(2 * dim + 2 + k) * n + a];
+        double pi[4][4];
+        pi_full(dim, &G, u, st, pi);
+        double Pi = aux[13 * n + a];
+        double p = aux[9 * n + a], e = aux[10 * n + a];
+        double T00 = (e + p + Pi) * u[0] * u[0] - (p + Pi) * G.gi[0] + pi[0][0];
+        E += G.sqrtg * T00 / aux[0 * n + a];
+        S += y[(2 * dim) * n + a];
+        for (int c = 0; c < 3; ++c) N[c] += Nq[c * n + a];
+    }
+    tot[0] = E;
+    tot[1] = S;
+    for (int c = 0; c < 3; ++c) tot[2 + c] = N[c];
+}
+
+/* the stored-shear index pairs, for the Python side */
+int oc_pi_pairs(int dim, int *ij)
+{
+    int np = npi_of(dim);
+    for (int k = 0; k < np; ++k) {
+        ij[2 * k] = dim == 2 ? PI2[k][0] : PI3[k][0];
+        ij[2 * k + 1] = dim == 2 ? PI2[k][1] : PI3[k][1];
+    }
+    return np;
+}
+
+/* full pi^{mu nu} reconstruction, exported for tests (transversality, trace) */
+void oc_pi_full(int dim, int milne, double tau, const double *u4, const double *stored, double *out16)
+{
+    geom_t G;
+    make_geom(milne, tau, &G);
+    double pi[4][4];
+    pi_full(dim, &G, u4, stored, pi);
+    memcpy(out16, pi, sizeof(pi));
+}

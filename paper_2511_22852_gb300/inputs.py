@@ -1,0 +1,295 @@
+"""Seeded synthetic inputs for the SPH particle step.
+
+This module only *synthesises inputs*: particle lattices, hotspot entropy
+profiles, random charge fractions, the Gubser initial state and the node values
+of a tabulated equation of state.  It holds none of the arithmetic of the step
+itself (no kernel sums, no EoS inversion, no equations of motion), so the CUDA
+path and the CPU oracle can both consume what it produces without sharing any
+of the method's code.
+
+Units everywhere: lengths and times in fm, temperatures and chemical potentials
+in fm^-1, entropy and charge densities in fm^-3, energy densities and pressures
+in fm^-4 (hbar*c = 0.1973269804 GeV fm converts GeV <-> fm^-1).
+
+Workloads (shapes follow the paper's test setups, Sec. "Code validation" and
+Sec. "Convergence Tests"):
+  * ``gubser_ideal_2p1``      -- ideal conformal 2+1D Gubser flow, 51x51 lattice.
+  * ``viscous_bsq_2p1``       -- 2+1D viscous BSQ event: 200 Gaussian hotspots in a
+                                 7 fm disc, ~40k particles, synthetic 4D EoS table.
+  * ``synthetic_eos_table``   -- node values of p, s, n_B, n_S, n_Q on a regular
+                                 (T, mu_B, mu_S, mu_Q) grid (the paper's online-inverter
+                                 input, Sec. "Equation of state").
+  * ``bjorken_lattice_2p1``   -- uniform lattice (longitudinal Bjorken flow test).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HBARC = 0.1973269804  # GeV fm
+
+# ---------------------------------------------------------------------------
+# counter-based generator (SplitMix64), so every input is reproducible bit for
+# bit on any machine and numpy version
+# ---------------------------------------------------------------------------
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n outputs of SplitMix64 started at counter ``offset`` for ``seed``."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+# ---------------------------------------------------------------------------
+# parameter records
+# ---------------------------------------------------------------------------
+@dataclass
+class AnalyticEoS:
+    """p(T, mu) = T^4 [a0 + a1 (1 + tanh((T - Tc)/w))/2] + T^2 sum_q chi_q mu_q^2 / 2.
+
+    Tc and w are in GeV (the tanh argument is evaluated in GeV); T, mu in fm^-1.
+    a1 = 0 and chi = 0 give the conformal EoS p = eps/3 with eps = 3 a0 T^4.
+    """
+    a0: float
+    a1: float = 0.0
+    Tc_GeV: float = 0.155
+    w_GeV: float = 0.02
+    chi: tuple = (0.0, 0.0, 0.0)
+
+
+@dataclass
+class EoSTable:
+    """Regular (T, mu_B, mu_S, mu_Q) grid, axis values in fm^-1, row-major with mu_Q fastest."""
+    T0: float
+    dT: float
+    nT: int
+    mu0: tuple
+    dmu: tuple
+    nmu: tuple
+    p: np.ndarray
+    s: np.ndarray
+    nB: np.ndarray
+    nS: np.ndarray
+    nQ: np.ndarray
+
+
+@dataclass
+class Transport:
+    viscous: bool = False
+    eta_over_s: float = 0.0
+    zeta_peak: float = 0.0        # peak of zeta/s
+    zeta_T_GeV: float = 0.155     # temperature of the peak
+    zeta_w_GeV: float = 0.02      # Gaussian standard deviation
+    tau_pi_coef: float = 5.0      # tau_pi = coef * eta / (eps + p)
+    tau_Pi_ratio: float = 1.0     # tau_Pi = ratio * tau_pi
+    cs2_cap: float = 1.0          # causal cap on c_s^2 in the acceleration system
+
+
+@dataclass
+class Event:
+    """One event: SoA particle arrays plus run parameters."""
+    name: str
+    dim: int
+    milne: bool
+    h: float
+    tau0: float
+    dtau: float
+    nsteps: int
+    x: np.ndarray            # [dim][N] positions (fm; eta is dimensionless)
+    u: np.ndarray            # [dim][N] contravariant spatial u^i
+    S: np.ndarray            # [N] entropy per particle
+    Nq: np.ndarray           # [3][N] B, S, Q charge per particle
+    Bv: np.ndarray           # [N]  Pi / sigma
+    Pv: np.ndarray           # [npi][N] pi^{ij} / sigma (xx, xy, yy for dim 2)
+    eos: AnalyticEoS
+    table: EoSTable | None
+    transport: Transport
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.S.shape[0])
+
+
+# ---------------------------------------------------------------------------
+# forward closed-form EoS, used here only to synthesise inputs (table nodes,
+# initial entropy amplitudes).  The step's own EoS code lives elsewhere.
+# ---------------------------------------------------------------------------
+def _analytic_p_s_n(eos: AnalyticEoS, T: np.ndarray, mu: np.ndarray):
+    T = np.asarray(T, dtype=np.float64)
+    x = T * HBARC
+    arg = (x - eos.Tc_GeV) / eos.w_GeV
+    th = np.tanh(arg)
+    f = eos.a0 + eos.a1 * (1.0 + th) / 2.0
+    fp = eos.a1 / 2.0 * (1.0 - th * th) * HBARC / eos.w_GeV
+    chi = np.asarray(eos.chi, dtype=np.float64).reshape(3, *([1] * T.ndim))
+    mu = np.asarray(mu, dtype=np.float64)
+    sum_chi_mu2 = np.sum(chi * mu * mu, axis=0)
+    p = T ** 4 * f + T * T * sum_chi_mu2 / 2.0
+    s = 4.0 * T ** 3 * f + T ** 4 * fp + T * sum_chi_mu2
+    n = chi * T * T * mu
+    return p, s, n
+
+
+def synthetic_eos_table(eos: AnalyticEoS, nT=64, nmu=32, T_GeV=(0.05, 0.8), mu_GeV=0.45) -> EoSTable:
+    """Tabulate the closed-form EoS on the grid T in [0.05, 0.8] GeV, mu in [-0.45, 0.45] GeV."""
+    T0 = T_GeV[0] / HBARC
+    dT = (T_GeV[1] - T_GeV[0]) / (nT - 1) / HBARC
+    m0 = -mu_GeV / HBARC
+    dm = 2.0 * mu_GeV / (nmu - 1) / HBARC
+    T = T0 + dT * np.arange(nT)
+    mu = m0 + dm * np.arange(nmu)
+    TT, MB, MS, MQ = np.meshgrid(T, mu, mu, mu, indexing="ij")
+    p, s, n = _analytic_p_s_n(eos, TT, np.stack([MB, MS, MQ]))
+    c = np.ascontiguousarray
+    return EoSTable(T0=T0, dT=dT, nT=nT, mu0=(m0, m0, m0), dmu=(dm, dm, dm), nmu=(nmu, nmu, nmu),
+                    p=c(p), s=c(s), nB=c(n[0]), nS=c(n[1]), nQ=c(n[2]))
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+BJ_EOS = AnalyticEoS(a0=0.3, a1=2.5, Tc_GeV=0.155, w_GeV=0.02, chi=(0.3, 0.5, 0.4))
+# the same family with a 0.04 GeV crossover: c_s^2 <= 0.41 everywhere (causal), used by the
+# energy-balance test where the c_s^2 cap must not engage
+CAUSAL_EOS = AnalyticEoS(a0=0.3, a1=2.5, Tc_GeV=0.155, w_GeV=0.04, chi=(0.3, 0.5, 0.4))
+GUBSER_FSTAR = 11.0
+
+
+def gubser_T_u(tau, x, y, q=1.0, T0_GeV=0.4, tau0=1.0):
+    """Ideal Gubser flow (H0 = 0): T in fm^-1 and (u^tau, u^x, u^y), with T(tau0, r=0) = T0."""
+    r2 = x * x + y * y
+    r = np.sqrt(r2)
+
+    def cosh_rho(t, rr2):
+        sh = (q * q * (t * t - rr2) - 1.0) / (2.0 * q * t)
+        return np.sqrt(1.0 + sh * sh)
+
+    T = (T0_GeV / HBARC) * (tau0 / tau) * (cosh_rho(tau0, 0.0) / cosh_rho(tau, r2)) ** (2.0 / 3.0)
+    den = np.sqrt(1.0 + 2.0 * q * q * (tau * tau + r2) + q ** 4 * (tau * tau - r2) ** 2)
+    utau = (1.0 + q * q * (tau * tau + r2)) / den
+    ur = 2.0 * q * q * r * tau / den
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ux = np.where(r > 0, ur * x / np.where(r > 0, r, 1.0), 0.0)
+        uy = np.where(r > 0, ur * y / np.where(r > 0, r, 1.0), 0.0)
+    return T, utau, ux, uy
+
+
+def gubser_ideal_2p1(n_side=51, half_width=5.0, h=0.5, tau0=1.0, dtau=0.01, nsteps=60) -> Event:
+    """Config: ideal conformal 2+1D boost-invariant Gubser flow (q = 1/fm, T0 = 0.4 GeV at tau0 = 1 fm)."""
+    g = np.linspace(-half_width, half_width, n_side)
+    dx = g[1] - g[0]
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x, y = X.ravel().copy(), Y.ravel().copy()
+    T, utau, ux, uy = gubser_T_u(tau0, x, y)
+    eos = AnalyticEoS(a0=GUBSER_FSTAR / 3.0)
+    _, s, _ = _analytic_p_s_n(eos, T, np.zeros((3, x.size)))
+    S = s * utau * tau0 * dx * dx
+    n = x.size
+    return Event(name="gubser_ideal_2p1", dim=2, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=np.stack([x, y]), u=np.stack([ux, uy]), S=S, Nq=np.zeros((3, n)),
+                 Bv=np.zeros(n), Pv=np.zeros((3, n)), eos=eos, table=None,
+                 transport=Transport(viscous=False), meta={"dx": dx})
+
+
+def disc_lattice(R: float, n_target: int):
+    """Square lattice with spacing sqrt(pi R^2 / n_target), points with x^2 + y^2 <= R^2."""
+    dx = math.sqrt(math.pi * R * R / n_target)
+    m = int(math.ceil(R / dx)) + 1
+    g = dx * np.arange(-m, m + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    keep = (X * X + Y * Y) <= R * R
+    return X[keep].copy(), Y[keep].copy(), dx
+
+
+def viscous_bsq_2p1(n_target=40000, R=7.0, n_hot=200, sigma_hot=0.4, T_max_GeV=0.5,
+                    charge_frac=0.01, tau0=0.6, dtau=0.005, tau_end=8.0, h=0.3,
+                    seed_hot=1, seed_charge=2, with_table=True, table_shape=(64, 32)) -> Event:
+    """Config: viscous 2+1D BSQ single event (eta/s = 0.08, Gaussian zeta/s, synthetic 4D EoS table).
+
+    Entropy: sum of ``n_hot`` Gaussian hotspots (sigma 0.4 fm) with centres uniform in the disc,
+    scaled so that max s = s(T_max, mu = 0).  Charges n_q = eps_q s with eps_q ~ U(-charge_frac,
+    charge_frac) (the literal +-10 % has no EoS solution for hot particles; see the design notes).
+    """
+    x, y, dx = disc_lattice(R, n_target)
+    u = uniform01(seed_hot, 2 * n_hot)
+    rc = R * np.sqrt(u[:n_hot])
+    ph = 2.0 * math.pi * u[n_hot:]
+    cx, cy = rc * np.cos(ph), rc * np.sin(ph)
+    s_raw = np.zeros_like(x)
+    for k in range(n_hot):
+        s_raw += np.exp(-((x - cx[k]) ** 2 + (y - cy[k]) ** 2) / (2.0 * sigma_hot ** 2))
+    _, s_max, _ = _analytic_p_s_n(BJ_EOS, np.array(T_max_GeV / HBARC), np.zeros(3))
+    s = s_raw * (float(s_max) / s_raw.max())
+    n = x.size
+    eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
+    nq = eps * s[None, :]
+    vol = tau0 * dx * dx
+    table = synthetic_eos_table(BJ_EOS, nT=table_shape[0], nmu=table_shape[1]) if with_table else None
+    nsteps = int(round((tau_end - tau0) / dtau))
+    return Event(name="viscous_bsq_2p1", dim=2, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=np.stack([x, y]), u=np.zeros((2, n)), S=s * vol, Nq=nq * vol,
+                 Bv=np.zeros(n), Pv=np.zeros((3, n)), eos=BJ_EOS, table=table,
+                 transport=Transport(viscous=True, eta_over_s=0.08, zeta_peak=0.05,
+                                     zeta_T_GeV=0.155, zeta_w_GeV=0.02),
+                 meta={"dx": dx, "hotspots": np.stack([cx, cy])})
+
+
+def bjorken_lattice_2p1(T0_GeV=0.16, n_side=41, dx=0.1, h=0.3, tau0=0.6, dtau=0.005, nsteps=100,
+                        viscous=True, with_table=False) -> Event:
+    """Uniform-temperature square lattice at rest: interior particles follow longitudinal
+    (Bjorken) boost-invariant flow until the edge rarefaction arrives."""
+    g = dx * (np.arange(n_side) - (n_side - 1) / 2.0)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x, y = X.ravel().copy(), Y.ravel().copy()
+    n = x.size
+    _, s, _ = _analytic_p_s_n(BJ_EOS, np.full(n, T0_GeV / HBARC), np.zeros((3, n)))
+    table = synthetic_eos_table(BJ_EOS) if with_table else None
+    return Event(name="bjorken_lattice_2p1", dim=2, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=np.stack([x, y]), u=np.zeros((2, n)), S=s * tau0 * dx * dx, Nq=np.zeros((3, n)),
+                 Bv=np.zeros(n), Pv=np.zeros((3, n)), eos=BJ_EOS, table=table,
+                 transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0,
+                                     zeta_peak=0.05 if viscous else 0.0),
+                 meta={"dx": dx})
+
+
+def random_points(n: int, dim: int, extent: float, seed: int) -> np.ndarray:
+    """[dim][n] uniform points in [-extent, extent]^dim (neighbour-search tests)."""
+    return (2.0 * uniform01(seed, dim * n).reshape(dim, n) - 1.0) * extent
+
+
+def smooth_blob_2p1(half_width=4.0, dx=0.1, h=0.3, T_peak_GeV=0.45, T_floor_GeV=0.06, sigma=1.2,
+                    ecc=0.25, charge_frac=0.01, tau0=0.6, dtau=0.005, nsteps=200, viscous=True,
+                    with_table=True, seed_charge=7, eos: AnalyticEoS = None) -> Event:
+    """Smooth elliptic Gaussian temperature profile on a square lattice that reaches a cold floor
+    well inside the lattice edge (no free surface at high pressure): the energy-balance test case."""
+    g = dx * np.arange(-int(round(half_width / dx)), int(round(half_width / dx)) + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x, y = X.ravel().copy(), Y.ravel().copy()
+    n = x.size
+    eos = BJ_EOS if eos is None else eos
+    prof = np.exp(-(x * x / (1.0 + ecc) + y * y / (1.0 - ecc)) / (2.0 * sigma * sigma))
+    T = (T_floor_GeV + (T_peak_GeV - T_floor_GeV) * prof) / HBARC
+    _, s, _ = _analytic_p_s_n(eos, T, np.zeros((3, n)))
+    eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
+    vol = tau0 * dx * dx
+    table = synthetic_eos_table(eos) if with_table else None
+    return Event(name="smooth_blob_2p1", dim=2, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=np.stack([x, y]), u=np.zeros((2, n)), S=s * vol, Nq=eps * s[None, :] * vol,
+                 Bv=np.zeros(n), Pv=np.zeros((3, n)), eos=eos, table=table,
+                 transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0,
+                                     zeta_peak=0.05 if viscous else 0.0),
+                 meta={"dx": dx})

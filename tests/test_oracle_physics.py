@@ -1,0 +1,146 @@
+"""Physics pins of the oracle's whole step (CPU only).
+
+* Ideal conformal Gubser flow against the closed form T(tau, r), u^r(tau, r)
+  (Sec. "Code validation", eqs. vGubser_T, Gubser_utau, Gubser_ur with H0 = 0),
+  with second-order convergence under refinement.
+* Longitudinal (Bjorken) boost-invariant flow with minimal Israel-Stewart shear
+  and bulk relaxation (eqs. min_bul_rel, min_she_rel): interior particles of a
+  uniform lattice against an independent ODE integration.
+* Exact per-particle conservation of S and N_q for ideal flow (Sec. "Exact
+  conservation"), second law for viscous flow, and the energy balance of Milne
+  coordinates (E(tau) + longitudinal work = E(tau0)).
+* Transversality and tracelessness of the reconstructed shear tensor.
+"""
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+from oracle import oracle as O
+from paper_2511_22852_gb300 import inputs as I
+
+
+def _gubser_error(n_side, h, dtau, nsteps):
+    ev = I.gubser_ideal_2p1(n_side=n_side, h=h, dtau=dtau, nsteps=nsteps)
+    run = O.OracleRun.start(ev)
+    run.step(ev.nsteps)
+    aux, st = run.observe()
+    x, y = run.y[0], run.y[1]
+    m = np.sqrt(x * x + y * y) <= 3.0
+    Tg, ut, ux, uy = I.gubser_T_u(run.tau, x, y)
+    errT = np.abs(aux[O.AUX["T"]][m] - Tg[m]) / Tg[m]
+    erru = np.abs(run.y[2][m] - ux[m]).max()
+    return run, errT, erru
+
+
+def test_gubser_ideal_against_closed_form():
+    run, errT, erru = _gubser_error(51, 0.5, 0.01, 60)
+    assert abs(run.tau - 1.6) < 1e-12
+    assert run.status_or == 0
+    # SPH smoothing error of h = 0.5 fm on this profile is ~3 % already at tau0
+    assert errT.max() < 0.035 and errT.mean() < 0.02
+    assert erru < 0.08
+    # second order in h: halving h and dx (and dtau) cuts the error by ~4
+    run2, errT2, erru2 = _gubser_error(101, 0.25, 0.005, 120)
+    assert errT2.max() < 0.3 * errT.max()
+    assert erru2 < 0.4 * erru
+
+
+def _eos_fns(E):
+    hc = I.HBARC
+
+    def thermo(T):
+        x = T * hc
+        th = np.tanh((x - E.Tc_GeV) / E.w_GeV)
+        s2 = 1 - th * th
+        k = hc / E.w_GeV
+        f = E.a0 + E.a1 * (1 + th) / 2
+        fp = E.a1 / 2 * s2 * k
+        fpp = -E.a1 * s2 * th * k * k
+        return T ** 4 * f, 4 * T ** 3 * f + T ** 4 * fp, 12 * T ** 2 * f + 8 * T ** 3 * fp + T ** 4 * fpp
+
+    return thermo
+
+
+@pytest.mark.parametrize("T0", [0.16, 0.3])
+def test_bjorken_viscous_against_ode(T0):
+    ev = I.bjorken_lattice_2p1(T0_GeV=T0, n_side=41, nsteps=100)
+    tr = ev.transport
+    thermo = _eos_fns(ev.eos)
+
+    def rhs(tau, Y):
+        T, Pi, Phi = Y  # Phi = -tau^2 pi^{eta eta} = pi^{xx} + pi^{yy}
+        p, s, dsdT = thermo(T)
+        e = T * s - p
+        eta = tr.eta_over_s * s
+        zeta = tr.zeta_peak * np.exp(-(T * I.HBARC - tr.zeta_T_GeV) ** 2 / (2 * tr.zeta_w_GeV ** 2)) * s
+        taupi = tr.tau_pi_coef * eta / (e + p)
+        tauPi = tr.tau_Pi_ratio * taupi
+        dT = -(e + p + Pi - Phi) / tau / (T * dsdT)
+        dPi = -(Pi + zeta / tau) / tauPi - Pi / tau
+        dPhi = (-Phi + 4 * eta / (3 * tau)) / taupi - 4 * Phi / (3 * tau)
+        return [dT, dPi, dPhi]
+
+    run = O.OracleRun.start(ev)
+    c = int(np.argmin(ev.x[0] ** 2 + ev.x[1] ** 2))
+    aux0, _ = run.observe()
+    run.step(ev.nsteps)
+    aux, _ = run.observe()
+    sol = solve_ivp(rhs, (ev.tau0, run.tau), [aux0[O.AUX["T"]][c], 0.0, 0.0], rtol=1e-12, atol=1e-14)
+    Tode, Piode, Phiode = sol.y[:, -1]
+    sigma = aux[O.AUX["sigma"]][c]
+    assert abs(aux[O.AUX["T"]][c] / Tode - 1) < 1e-6
+    assert abs(aux[O.AUX["Pi"]][c] - Piode) < 2e-3 * abs(Piode)
+    pixx, pixy, piyy = sigma * run.y[6][c], sigma * run.y[7][c], sigma * run.y[8][c]
+    assert abs(pixx - Phiode / 2) < 1e-4 * abs(Phiode) and abs(piyy - Phiode / 2) < 1e-4 * abs(Phiode)
+    assert abs(pixy) < 1e-10 * abs(Phiode)
+
+
+def test_ideal_exact_per_particle_conservation():
+    ev = I.smooth_blob_2p1(viscous=False, half_width=2.5, nsteps=20)
+    run = O.OracleRun.start(ev)
+    S0, N0 = run.y[4].copy(), run.Nq.copy()
+    run.step(20)
+    assert np.array_equal(run.y[4], S0)  # dS/dtau = 0 exactly for ideal flow
+    assert np.array_equal(run.Nq, N0)
+    assert np.all(np.isfinite(run.y))
+
+
+def test_viscous_second_law_and_energy_balance():
+    """Causal EoS variant (no c_s^2 cap active): E + work conserved, total S non-decreasing."""
+    ev = I.smooth_blob_2p1(viscous=True, eos=I.CAUSAL_EOS, half_width=4.0)
+    run = O.OracleRun.start(ev)
+    aux0, st0 = run.observe()
+    t0 = run.totals(aux0)
+    S = [t0["S"]]
+    for _ in range(4):
+        run.step(25)
+        aux, st = run.observe()
+        tt = run.totals(aux)
+        S.append(tt["S"])
+        assert abs((tt["E"] + tt["work"]) / t0["E"] - 1) < 1e-3
+        assert np.array_equal(tt["N"], t0["N"])
+    assert run.status_or & (O.ST_NOCONV | O.ST_SOLVE_FAIL | O.ST_CS2_CAPPED) == 0
+    assert np.all(np.diff(S) > 0) and S[-1] / S[0] - 1 > 0.01
+
+
+def test_shear_reconstruction_properties():
+    import ctypes as C
+    rng = np.random.default_rng(8)
+    for dim, milne in [(2, 1), (2, 0), (3, 1), (3, 0)]:
+        for _ in range(10):
+            tau = rng.uniform(0.5, 3.0)
+            u = np.zeros(4)
+            u[1:1 + dim] = rng.normal(0, 0.8, dim)
+            if milne:
+                u[3] /= tau  # u^eta
+            g = np.array([1, -1, -1, -(tau * tau if milne else 1.0)])
+            u[0] = np.sqrt(1 - np.sum(g[1:] * u[1:] ** 2))
+            stored = rng.normal(0, 1, 5)
+            out = np.zeros(16)
+            O.lib().oc_pi_full(dim, milne, tau, u.ctypes.data_as(C.c_void_p), stored.ctypes.data_as(C.c_void_p),
+                               out.ctypes.data_as(C.c_void_p))
+            pi = out.reshape(4, 4)
+            ul = g * u
+            assert np.allclose(ul @ pi, 0, atol=1e-12 * np.abs(pi).max())
+            assert abs(np.sum(g * np.diag(pi))) < 1e-12 * np.abs(pi).max()
+            assert np.allclose(pi, pi.T)
