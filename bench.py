@@ -1,0 +1,296 @@
+"""Benchmark: SPH particle-steps/s of the viscous 2+1D BSQ single event (FP64).
+
+Workload: 40k particles in a 7 fm disc (200 seeded Gaussian hotspots, sigma
+0.4 fm), Milne 2+1D boost invariant, minimal Israel-Stewart shear + bulk
+(eta/s = 0.08, Gaussian zeta/s), synthetic 64 x 32^3 FP64 EoS table, h = 0.3 fm,
+dtau = 0.005 fm.  One step = one full Heun (RK2) step of the event: both stages,
+each with cell list, kernel sums, EoS inversion, gradients, equations of motion
+and update.  particle-steps/s = particles x steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one independent event per rank (replicas, weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+--impl reference times the CPU oracle (FP64 C, all host cores) on the same event.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH particle-steps/s"
+UNIT = "particle-steps/s"
+WORKLOAD = "viscous 2+1D BSQ single event, FP64: 40k particles, 64x32^3 EoS table, h=0.3 fm, dtau=0.005 fm"
+
+# algorithmic FP64 flops per accepted neighbour pair (fused multiply-add = 2):
+#   density : distance 5, sqrt 1, q 1, kernel polynomial 5, five accumulations 10          = 22
+#   gradient: distance 5, sqrt 1, q 1, kernel-derivative polynomial 3, 1/r and factor 2,
+#             dW vector 2, sum of dW 2, stress divergence 8, velocity gradient 8          = 32
+FLOPS_PER_PAIR = {"density": 22.0, "gradient": 32.0}
+# FP64 vector peak of GB300 (nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock)
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def cpu_baseline(ev, target_s=15.0):
+    """The CPU oracle, as it stands, on a bounded sample: whole Heun steps of the same event."""
+    from oracle import oracle as O
+    run = O.OracleRun.start(ev)
+    t = time.perf_counter()
+    run.step(1)
+    t1 = time.perf_counter() - t
+    nsteps = max(1, min(60, int(target_s / max(t1, 1e-3))))
+    t = time.perf_counter()
+    run.step(nsteps)
+    dt = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": ev.n * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} Heun steps of the full {ev.n}-particle event after 1 untimed step "
+                      f"({dt:.1f} s, FP64 C oracle, OpenMP over particles)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2511_22852_gb300 import inputs as I
+    ev = I.viscous_bsq_2p1()
+    run = O.OracleRun.start(ev)
+    for _ in range(args.warmup):
+        run.step(1)
+    t = time.perf_counter()
+    run.step(args.steps)
+    dt = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    val = ev.n * args.steps / dt
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "particles": ev.n, "l2": "host run (no GPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} Heun steps of the full {ev.n}-particle event"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2511_22852_gb300 import binding as Bd
+    from paper_2511_22852_gb300 import build_lib
+    from paper_2511_22852_gb300 import inputs as I
+
+    if rank == 0 or not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    if ws > 1:
+        dist.barrier()
+    # one independent event per rank (replicas): rank r uses hotspot/charge seeds shifted by r
+    ev = I.viscous_bsq_2p1(seed_hot=1 + 1000 * rank, seed_charge=2 + 1000 * rank)
+    stream = torch.cuda.Stream()
+    g = Bd.GpuEvent(ev, use_graph=True, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        g.step(1)
+    torch.cuda.synchronize()
+    # L2 (129 MB) flush between timed steps: a 256 MiB write, outside the timed events
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_before = g.totals()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                e0[k].record(stream)
+                g.step(1)
+                e1[k].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    t_after = g.totals()
+    launches = t_after["kernel_launches"] - t_before["kernel_launches"]
+    status_or = t_after["status_or"]
+    clocks = clk.summary()
+
+    tt = torch.tensor([dev_ms, float(ev.n * args.steps)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        mx = tt[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt[1:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        dev_ms_max, units = float(mx.item()), float(sm.item())
+    else:
+        dev_ms_max, units = dev_ms, float(ev.n * args.steps)
+    value = units / (dev_ms_max / 1e3)
+
+    out = None
+    if rank == 0:
+        # --- per-kernel device times (profile mode: CUDA events around each kernel group,
+        #     on the event's stream), same workload, for the roofline of the dominant kernel
+        gp = Bd.GpuEvent(ev, use_graph=False, stream=stream.cuda_stream, profile=True)
+        gp.step(2)
+        gp_times0 = gp.kernel_times()
+        p0 = gp.totals()["pairs"]
+        kp = max(4, min(args.steps, 40))
+        with torch.cuda.stream(stream):
+            for k in range(kp):
+                flush.fill_(float(k))
+                gp.step(1)
+        torch.cuda.synchronize()
+        p1 = gp.totals()["pairs"]
+        times = {k: (v[0] - gp_times0[k][0], v[1] - gp_times0[k][1]) for k, v in gp.kernel_times().items()}
+        gp.free()
+        pairs_incl_self = (p1 - p0)  # summed over both stages of kp steps
+        dom = max(times, key=lambda k: times[k][0])
+        grp_pairs = {"density": pairs_incl_self, "gradient": pairs_incl_self - 2 * kp * ev.n}
+        roof = None
+        if dom in FLOPS_PER_PAIR:
+            flops = FLOPS_PER_PAIR[dom] * grp_pairs[dom]
+            ms = times[dom][0]
+            achieved = flops / (ms / 1e3) / 1e9
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dom,
+                    "peak_source": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s at 2070 MHz)",
+                    "avg_launch_ms": ms / times[dom][1],
+                    "flops_per_launch": flops / times[dom][1]}
+        total_ms = sum(v[0] for v in times.values())
+        kernel_share = {k: round(v[0] / total_ms, 4) for k, v in times.items()}
+
+        # --- end to end through the C ABI with host buffers: each step copies the state in
+        #     from pinned host memory, steps, and reads the state back
+        ge = Bd.GpuEvent(ev, use_graph=True, stream=stream.cuda_stream)
+        st = ge.read(("X", "U", "S", "BV", "PV"))
+        pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in st.items()}
+        ge.step(1)
+        torch.cuda.synchronize()
+        ke = max(3, min(args.steps, 30))
+        bytes_state = sum(v.nbytes for v in pinned.values())
+        t = time.perf_counter()
+        for _ in range(ke):
+            ge.write_state(x=pinned["X"], u=pinned["U"], S=pinned["S"], Bv=pinned["BV"], Pv=pinned["PV"])
+            ge.step(1)
+            o = ge.read(("X", "U", "S", "BV", "PV"))
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t
+        ge.free()
+        e2e = {"value": ev.n * ke / te, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+               "d2h_bytes_per_step": sum(v.nbytes for v in o.values()), "steps": ke}
+
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "particles": ev.n, "l2": "flushed (256 MiB write) between timed steps",
+                          "parallelism": f"replicas x{ws}", "cuda_graph": True},
+               "roofline": roof, "kernel_share": kernel_share,
+               "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+               "wall_s_timed": t_wall, "status_or": int(status_or)}
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(ev)
+        print(json.dumps(out), flush=True)
+    g.free()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

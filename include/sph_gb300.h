@@ -1,0 +1,232 @@
+/*
+ * sph_gb300.h -- C ABI of the GB300 (sm_103a) SPH particle step for relativistic
+ * viscous BSQ hydrodynamics, following arXiv 2511.22852 (CCAKE 2.0).
+ *
+ * What the library computes, per Runge-Kutta stage (Sec. "Numerical solver:
+ * Smoothed particle hydrodynamics (SPH)"):
+ *   a1/a2  Morton-sorted cell list with cells of side 2h (the kernel support) and a
+ *          stable sort of the particles by (cell key, original id);
+ *   a3     kernel sums sigma*_a = sum_b W_ab, s*_a = sum_b S_b W_ab,
+ *          n*_qa = sum_b N_qb W_ab (eqs. sigmastar, refconv), rest-frame
+ *          densities q = q* / (u^0 sqrt(-g));
+ *   a4     EoS inversion (s, n_B, n_S, n_Q) -> (T, mu_B, mu_S, mu_Q) by Newton
+ *          iteration on the tabulated 4D EoS, the closed-form EoS as backup
+ *          (Sec. "Equation of state", "EoS inverter");
+ *   a5     SPH gradients (eqs. sphderivativerel, generalsphderivative);
+ *   a6     the acceleration from the linear system M du/dx0 = F (eq. unugeneral),
+ *          entropy production (eq. dsdnrewr), minimal Israel-Stewart bulk and
+ *          shear relaxation (eqs. min_bul_rel, min_she_rel);
+ *   a7     Heun (RK2) update;
+ *   a8     conservation totals (energy, entropy, charges, longitudinal work).
+ * All of it runs in hand-written CUDA kernels on one GPU; nothing falls back to
+ * the CPU.
+ *
+ * Units: lengths and times in fm (eta dimensionless), T and mu in fm^-1,
+ * densities s, n_q in fm^-3, p and e in fm^-4 (hbar c = 0.1973269804 GeV fm).
+ *
+ * Conventions for every call:
+ *   - the return value is an sph_status, SPH_OK = 0; nothing throws across the ABI;
+ *   - on an error, sph_last_error() returns a message for the calling thread;
+ *   - handles are opaque; one event handle is used by one host thread at a time;
+ *   - the library owns all device memory it allocates; the caller owns every
+ *     buffer it passes in and may free it as soon as the call returns.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, unsupported option) */
+    SPH_ERR_OOM = 2,        /* device allocation failed */
+    SPH_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    SPH_ERR_EOS_RANGE = 4,  /* a particle outside the table when the policy makes that fatal */
+    SPH_ERR_EOS_NOCONV = 5, /* no EoS solution for a particle, policy fatal */
+    SPH_ERR_NONFINITE = 6,  /* a non-finite state value, policy fatal */
+    SPH_ERR_TIMEOUT = 7,    /* a bounded host wait on the device gave up */
+    SPH_ERR_STATE = 8       /* call out of order, or the particles outgrew the cell table */
+} sph_status;
+
+/* per-particle status bits (read with SPH_F_STATUS; OR-ed over an event in sph_totals) */
+#define SPH_PST_FALLBACK 1u     /* table Newton did not converge: closed-form EoS used */
+#define SPH_PST_OUT_OF_TABLE 2u /* the solution lies outside the table: closed-form EoS used */
+#define SPH_PST_NOCONV 4u       /* no EoS solution at all */
+#define SPH_PST_NONFINITE 8u    /* non-finite density or state */
+#define SPH_PST_CS2_CAPPED 16u  /* c_s^2 > cap: dp/ds, dp/dn scaled down in the acceleration system */
+#define SPH_PST_SOLVE_FAIL 32u  /* the acceleration system was singular */
+/* A particle with NOCONV or NONFINITE from the EoS is frozen for that stage: it moves
+ * ballistically (dx/dt = v), every other rate is zero, and it contributes p = e = 0 to its
+ * neighbours' pressure gradient. */
+
+/* ---------------------------------------------------------------------------
+ * Equation of state (Sec. "Equation of state"; closed forms of the kind of
+ * Sec. "Modified EoS to permit lower eps_min").
+ *
+ * Closed form, always present (and the backup when a table is given):
+ *   p(T, mu) = T^4 [a0 + a1 (1 + tanh((T hbar c - Tc)/w)) / 2] + T^2 sum_q chi_q mu_q^2 / 2,
+ * Tc and w in GeV.  a1 = 0, chi = 0 is the conformal EoS p = e/3.
+ *
+ * Optional table (has_table = 1): p, s, n_B, n_S, n_Q on the regular grid
+ * T_i = T0 + i dT (i < nT), mu_q,j = mu0[q] + j dmu[q] (j < nmu[q]); each array
+ * holds nT*nmu[0]*nmu[1]*nmu[2] doubles, row-major [T][mu_B][mu_S][mu_Q]
+ * (mu_Q fastest), in HOST memory.  The library copies them to the device,
+ * interleaved per node; the caller keeps ownership of its arrays.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double a0, a1, Tc_GeV, w_GeV;
+    double chi[3];
+    int32_t has_table;
+    int32_t nT;
+    int32_t nmu[3];
+    int32_t newton_maxit; /* table Newton iterations (<= 0: 30) */
+    double T0, dT;
+    double mu0[3], dmu[3];
+    const double *p, *s, *nB, *nS, *nQ;
+    double newton_tol; /* max |residual| / s for convergence (<= 0: 1e-12) */
+} sph_eos_desc;
+
+typedef struct sph_eos sph_eos;
+typedef struct sph_event sph_event;
+
+/* Creates an EoS handle.  Errors: SPH_ERR_ARG (null pointers, a table dimension
+ * < 2, non-positive spacing, a0 <= 0), SPH_ERR_OOM, SPH_ERR_CUDA.  The handle is
+ * reference counted: events keep it alive; sph_free_eos drops the caller's reference. */
+sph_status sph_set_eos_table(sph_eos **out, const sph_eos_desc *desc);
+void sph_free_eos(sph_eos *eos);
+
+/* ---------------------------------------------------------------------------
+ * Event: N SPH particles with unit SPH mass (Sec. "SPH interpretation of a
+ * fluid element": m_b = 1, sigma* = 1/V*), dynamical variables of eq.
+ * dynamicalvariables: position x^i, u^i, S = s/sigma, Pi/sigma, pi^{ij}/sigma,
+ * N_q = n_q/sigma.
+ *
+ * Coordinates: milne = 1 is (tau, x, y, eta) with sqrt(-g) = tau, milne = 0 is
+ * Cartesian (t, x, y, z).  dim = 2 is transverse (x, y) only (with milne = 1:
+ * boost-invariant 2+1D).  This version implements dim = 2; other values return
+ * SPH_ERR_ARG.
+ *
+ * Arrays (SoA, doubles): x[dim*n] (x^1 for all particles, then x^2, ...),
+ * u[dim*n] (contravariant u^i), S[n], Nq[3*n] (B, S, Q), Bv[n] = Pi/sigma (may be
+ * NULL: zero), Pv[npi*n] = pi^{ij}/sigma for (xx, xy, yy) when dim = 2 (may be
+ * NULL: zero).  Host pointers, or device pointers when on_device = 1 (for example
+ * torch tensors' data_ptr()).  The library copies them; the caller keeps them.
+ *
+ * Transport: eta = eta_over_s * s; zeta = zeta_peak exp(-(T hbar c - zeta_T)^2 /
+ * (2 zeta_w^2)) s; tau_pi = tau_pi_coef eta / (e + p); tau_Pi = tau_Pi_ratio tau_pi.
+ * viscous = 0 evolves an ideal fluid.  cs2_cap bounds c_s^2 inside the
+ * acceleration system (<= 0: 1).  fatal_mask: per-particle status bits that
+ * make sph_step fail (0: none).  stream: a cudaStream_t, or NULL to let the
+ * library create one.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t dim, milne, viscous, on_device;
+    int64_t n;
+    double h, tau0, dtau;
+    const double *x, *u, *S, *Nq, *Bv, *Pv;
+    double eta_over_s, zeta_peak, zeta_T_GeV, zeta_w_GeV;
+    double tau_pi_coef, tau_Pi_ratio, cs2_cap;
+    uint32_t fatal_mask;
+    int32_t use_graph; /* 1: replay sph_step through a captured CUDA graph */
+    void *stream;
+    int32_t profile;   /* 1: time every kernel group with CUDA events (no graph; see sph_kernel_times) */
+    int32_t pad;
+} sph_event_desc;
+
+/* Copies the particles to device memory (sorted by cell on the first stage) and
+ * binds the EoS.  Errors: SPH_ERR_ARG (n < 0, h <= 0, dtau <= 0, dim != 2, null
+ * arrays for n > 0), SPH_ERR_OOM, SPH_ERR_CUDA.  n = 0 gives an empty event on
+ * which every call succeeds and does nothing. */
+sph_status sph_init_event(sph_event **out, const sph_event_desc *desc, const sph_eos *eos);
+void sph_free_event(sph_event *ev);
+
+/* Advances nsteps full Heun steps (2 stages each) of size dtau on the event's
+ * stream.  Asynchronous unless flags & SPH_SYNC; with SPH_SYNC the call waits
+ * (bounded by the event's timeout, SPH_ERR_TIMEOUT if exceeded) and checks the
+ * per-particle status against fatal_mask.  nsteps < 0: SPH_ERR_ARG. */
+#define SPH_SYNC 1u
+sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags);
+
+/* ---------------------------------------------------------------------------
+ * Read-out, in the ORIGINAL particle order of sph_init_event.  A field is copied
+ * when its mask bit is set; its destination must then be non-NULL and hold the
+ * stated number of doubles (or uint32/int32).  Derived fields (SIGMA_STAR ...
+ * STATUS) are evaluated at the current state (cell list, kernel sums and EoS
+ * inversion are rerun if the state changed since the last read).
+ * Destinations are host memory unless on_device = 1.  The call synchronises the
+ * event's stream.
+ * ------------------------------------------------------------------------- */
+#define SPH_F_X (1ull << 0)          /* x[dim*n] */
+#define SPH_F_U (1ull << 1)          /* u[dim*n] */
+#define SPH_F_S (1ull << 2)          /* S[n] */
+#define SPH_F_NQ (1ull << 3)         /* Nq[3*n] */
+#define SPH_F_BV (1ull << 4)         /* Bv[n] */
+#define SPH_F_PV (1ull << 5)         /* Pv[npi*n] */
+#define SPH_F_SIGMA_STAR (1ull << 6) /* sigstar[n] */
+#define SPH_F_S_DENS (1ull << 7)     /* s[n] (rest frame) */
+#define SPH_F_N_DENS (1ull << 8)     /* nq[3*n] (rest frame) */
+#define SPH_F_T (1ull << 9)          /* T[n] */
+#define SPH_F_MU (1ull << 10)        /* mu[3*n] */
+#define SPH_F_P (1ull << 11)         /* p[n] */
+#define SPH_F_E (1ull << 12)         /* e[n] */
+#define SPH_F_PI_BULK (1ull << 13)   /* Pi[n] */
+#define SPH_F_STATUS (1ull << 14)    /* status[n] (uint32) */
+#define SPH_F_NNB (1ull << 15)       /* neighbour count including self, nnb[n] (int32) */
+#define SPH_F_CELL (1ull << 16)      /* cell coordinates cell[dim*n] (int32) */
+
+typedef struct {
+    double *x, *u, *S, *Nq, *Bv, *Pv;
+    double *sigstar, *s, *nq, *T, *mu, *p, *e, *Pi;
+    uint32_t *status;
+    int32_t *nnb, *cell;
+    int32_t on_device;
+} sph_field_bufs;
+
+typedef struct {
+    double tau;
+    double E;      /* sum_a sqrt(-g) T^{00}_a / sigma*_a */
+    double S;      /* sum_a S_a */
+    double N[3];   /* sum_a N_qa (fixed-order sums: bitwise constant) */
+    double work;   /* int dtau sum_a sqrt(-g) Gamma^0_{mu nu} T^{mu nu} / sigma* (Milne) */
+    uint32_t status_or;
+    int32_t pad;
+    int64_t steps;
+    int64_t pairs;          /* accepted neighbour pairs (self pairs included) summed over all stages */
+    int64_t kernel_launches; /* kernels launched by sph_step so far (graph replays included) */
+} sph_totals;
+
+sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *out, sph_totals *tot);
+
+/* Overwrites the evolved state (x, u, S, Bv, Pv; Nq unchanged) from buffers in the
+ * original particle order (mask bits SPH_F_X .. SPH_F_PV; others ignored), e.g. to
+ * resume from a checkpoint read with sph_read_fields.  Errors: SPH_ERR_ARG. */
+sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *in);
+
+/* Per-kernel-group device time of an event created with profile = 1: for group k < *count
+ * (count <= max), names[32*k ..] gets a NUL-terminated name, ms[k] the summed milliseconds and
+ * launches[k] the number of launches since creation.  Groups: cells, permute, density, eos,
+ * gradient, eom, work.  SPH_ERR_STATE if profiling is off. */
+sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *sph_last_error(void);
+
+/* Test support (not part of the stepping interface): all ordered neighbour pairs
+ * (a, b) with r_ab < 2h at the current positions, in original ids, sorted by
+ * (a, b), self pairs included.  Writes min(count, cap) pairs; *count gets the total. */
+sph_status sph_debug_neighbors(sph_event *ev, int64_t cap, int32_t *pa, int32_t *pb, int64_t *count);
+
+/* Test support: one right-hand-side evaluation at the current state, without
+ * advancing it.  rates[nv*n] (nv = 2 dim + 2 + npi) and grad[(dim*dim + dim)*n]
+ * (d_k u^j, then F^i) in original order, host buffers; either may be NULL. */
+sph_status sph_debug_rates(sph_event *ev, double *rates, double *grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_GB300_H */

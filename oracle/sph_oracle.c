@@ -944,6 +944,13 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     /* equations of motion */
 #pragma omp parallel for schedule(static)
     for (long a = 0; a < n; ++a) {
+        if (status[a] & (ST_NOCONV | ST_NONFINITE)) {
+            /* no EoS solution: the particle is frozen for this stage, moving ballistically */
+            double u0 = aux[14 * n + a];
+            for (int k = 0; k < nv; ++k) dydt[k * n + a] = 0.0;
+            for (int i = 0; i < dim; ++i) dydt[i * n + a] = y[(dim + i) * n + a] / u0;
+            continue;
+        }
         ppart q;
         memset(&q, 0, sizeof(q));
         q.dim = dim;
@@ -1013,7 +1020,6 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
             dydt[(2 * dim + 2 + k) * n + a] = P->viscous ? R.dPv[i][j] : 0.0;
         }
     }
-    (void)nv;
     /* longitudinal work rate: sum_a sqrt(-g) Gamma^0_{mu nu} T^{mu nu} / sigma* (serial, fixed order) */
     double wr = 0.0;
     for (long a = 0; a < n; ++a) {

@@ -1,0 +1,293 @@
+"""Thin ctypes binding of the C ABI in ``include/sph_gb300.h``.
+
+The names are the C names (``sph_set_eos_table``, ``sph_init_event``,
+``sph_step``, ``sph_read_fields``, ...); this module only marshals arguments.
+Every step of the SPH path runs in the CUDA library: if the library is not
+built (``__graft_entry__.build()`` or ``python -m paper_2511_22852_gb300.build_lib``),
+loading fails with an error -- there is no CPU fallback.
+
+``GpuEvent`` wraps one event built from ``inputs.Event`` for tests and the
+benchmark.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_lib
+
+# ---------------------------------------------------------------------------
+SPH_OK, SPH_ERR_ARG, SPH_ERR_OOM, SPH_ERR_CUDA, SPH_ERR_EOS_RANGE, SPH_ERR_EOS_NOCONV, SPH_ERR_NONFINITE, \
+    SPH_ERR_TIMEOUT, SPH_ERR_STATE = range(9)
+STATUS_NAMES = ["SPH_OK", "SPH_ERR_ARG", "SPH_ERR_OOM", "SPH_ERR_CUDA", "SPH_ERR_EOS_RANGE", "SPH_ERR_EOS_NOCONV",
+                "SPH_ERR_NONFINITE", "SPH_ERR_TIMEOUT", "SPH_ERR_STATE"]
+PST_FALLBACK, PST_OUT_OF_TABLE, PST_NOCONV, PST_NONFINITE, PST_CS2_CAPPED, PST_SOLVE_FAIL = 1, 2, 4, 8, 16, 32
+SPH_SYNC = 1
+
+F = {name: 1 << i for i, name in enumerate(
+    ["X", "U", "S", "NQ", "BV", "PV", "SIGMA_STAR", "S_DENS", "N_DENS", "T", "MU", "P", "E", "PI_BULK", "STATUS",
+     "NNB", "CELL"])}
+
+EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_event", "sph_step", "sph_read_fields",
+           "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times"]
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else code}: {msg}")
+        self.code = code
+
+
+class EosDesc(C.Structure):
+    _fields_ = [("a0", C.c_double), ("a1", C.c_double), ("Tc_GeV", C.c_double), ("w_GeV", C.c_double),
+                ("chi", C.c_double * 3), ("has_table", C.c_int32), ("nT", C.c_int32), ("nmu", C.c_int32 * 3),
+                ("newton_maxit", C.c_int32), ("T0", C.c_double), ("dT", C.c_double), ("mu0", C.c_double * 3),
+                ("dmu", C.c_double * 3), ("p", C.c_void_p), ("s", C.c_void_p), ("nB", C.c_void_p),
+                ("nS", C.c_void_p), ("nQ", C.c_void_p), ("newton_tol", C.c_double)]
+
+
+class EventDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("milne", C.c_int32), ("viscous", C.c_int32), ("on_device", C.c_int32),
+                ("n", C.c_int64), ("h", C.c_double), ("tau0", C.c_double), ("dtau", C.c_double),
+                ("x", C.c_void_p), ("u", C.c_void_p), ("S", C.c_void_p), ("Nq", C.c_void_p), ("Bv", C.c_void_p),
+                ("Pv", C.c_void_p), ("eta_over_s", C.c_double), ("zeta_peak", C.c_double),
+                ("zeta_T_GeV", C.c_double), ("zeta_w_GeV", C.c_double), ("tau_pi_coef", C.c_double),
+                ("tau_Pi_ratio", C.c_double), ("cs2_cap", C.c_double), ("fatal_mask", C.c_uint32),
+                ("use_graph", C.c_int32), ("stream", C.c_void_p), ("profile", C.c_int32), ("pad", C.c_int32)]
+
+
+class FieldBufs(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ["x", "u", "S", "Nq", "Bv", "Pv", "sigstar", "s", "nq", "T", "mu", "p",
+                                          "e", "Pi", "status", "nnb", "cell"]] + [("on_device", C.c_int32)]
+
+
+class Totals(C.Structure):
+    _fields_ = [("tau", C.c_double), ("E", C.c_double), ("S", C.c_double), ("N", C.c_double * 3),
+                ("work", C.c_double), ("status_or", C.c_uint32), ("pad", C.c_int32), ("steps", C.c_int64),
+                ("pairs", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return build_lib.LIB
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build()")
+        _lib = C.CDLL(path)
+        vp, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+        sig = {
+            "sph_set_eos_table": (i32, [C.POINTER(vp), C.POINTER(EosDesc)]),
+            "sph_free_eos": (None, [vp]),
+            "sph_init_event": (i32, [C.POINTER(vp), C.POINTER(EventDesc), vp]),
+            "sph_free_event": (None, [vp]),
+            "sph_step": (i32, [vp, i32, u32]),
+            "sph_read_fields": (i32, [vp, C.c_uint64, C.POINTER(FieldBufs), C.POINTER(Totals)]),
+            "sph_write_state": (i32, [vp, C.c_uint64, C.POINTER(FieldBufs)]),
+            "sph_last_error": (C.c_char_p, []),
+            "sph_debug_neighbors": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
+            "sph_debug_rates": (i32, [vp, vp, vp]),
+            "sph_kernel_times": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+def _check(code):
+    if code != SPH_OK:
+        raise SphError(code, lib().sph_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())  # torch tensor
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# the C entry points under their own names
+def sph_set_eos_table(desc: EosDesc):
+    h = C.c_void_p()
+    _check(lib().sph_set_eos_table(C.byref(h), C.byref(desc)))
+    return h
+
+
+def sph_free_eos(h):
+    lib().sph_free_eos(h)
+
+
+def sph_init_event(desc: EventDesc, eos):
+    h = C.c_void_p()
+    _check(lib().sph_init_event(C.byref(h), C.byref(desc), eos))
+    return h
+
+
+def sph_free_event(h):
+    lib().sph_free_event(h)
+
+
+def sph_step(h, nsteps: int, flags: int = 0):
+    _check(lib().sph_step(h, int(nsteps), int(flags)))
+
+
+def sph_read_fields(h, mask: int, bufs: FieldBufs | None, tot: Totals | None):
+    _check(lib().sph_read_fields(h, C.c_uint64(mask), C.byref(bufs) if bufs is not None else None,
+                                 C.byref(tot) if tot is not None else None))
+
+
+def sph_write_state(h, mask: int, bufs: FieldBufs):
+    _check(lib().sph_write_state(h, C.c_uint64(mask), C.byref(bufs)))
+
+
+def sph_debug_neighbors(h, cap: int, pa, pb):
+    cnt = C.c_int64(0)
+    _check(lib().sph_debug_neighbors(h, int(cap), _ptr(pa), _ptr(pb), C.byref(cnt)))
+    return cnt.value
+
+
+def sph_debug_rates(h, rates, grad):
+    _check(lib().sph_debug_rates(h, _ptr(rates), _ptr(grad)))
+
+
+def sph_kernel_times(h):
+    """{group: (milliseconds, launches)} of an event created with profile = 1."""
+    names = C.create_string_buffer(32 * 16)
+    ms = np.zeros(16)
+    nl = np.zeros(16, dtype=np.int64)
+    cnt = C.c_int32(0)
+    _check(lib().sph_kernel_times(h, 16, names, ms.ctypes.data, nl.ctypes.data, C.byref(cnt)))
+    raw = names.raw
+    return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
+
+
+# ---------------------------------------------------------------------------
+def eos_desc(eos, table=None, newton_tol=1e-12, newton_maxit=30):
+    """(EosDesc, keep-alive list) from inputs.AnalyticEoS / inputs.EoSTable."""
+    d = EosDesc()
+    d.a0, d.a1, d.Tc_GeV, d.w_GeV = eos.a0, eos.a1, eos.Tc_GeV, eos.w_GeV
+    for q in range(3):
+        d.chi[q] = eos.chi[q]
+    d.newton_tol, d.newton_maxit = newton_tol, newton_maxit
+    keep = []
+    if table is not None:
+        d.has_table = 1
+        d.nT, d.T0, d.dT = table.nT, table.T0, table.dT
+        for q in range(3):
+            d.nmu[q], d.mu0[q], d.dmu[q] = table.nmu[q], table.mu0[q], table.dmu[q]
+        arrs = [_f64(table.p), _f64(table.s), _f64(table.nB), _f64(table.nS), _f64(table.nQ)]
+        keep += arrs
+        d.p, d.s, d.nB, d.nS, d.nQ = [a.ctypes.data for a in arrs]
+    return d, keep
+
+
+class GpuEvent:
+    """One event on the GPU, built from an ``inputs.Event``."""
+
+    def __init__(self, ev, use_graph=True, fatal_mask=0, eos_handle=None, stream=None, profile=False):
+        self.ev = ev
+        self.dim, self.n = ev.dim, ev.n
+        self.npi = 3 if ev.dim == 2 else 5
+        self.nv = 2 * ev.dim + 2 + self.npi
+        self._own_eos = eos_handle is None
+        if eos_handle is None:
+            ed, keep = eos_desc(ev.eos, ev.table)
+            eos_handle = sph_set_eos_table(ed)
+        self.eos = eos_handle
+        d = EventDesc()
+        d.dim, d.milne, d.viscous, d.on_device = ev.dim, int(ev.milne), int(ev.transport.viscous), 0
+        d.n, d.h, d.tau0, d.dtau = ev.n, ev.h, ev.tau0, ev.dtau
+        self._keep = [_f64(ev.x), _f64(ev.u), _f64(ev.S), _f64(ev.Nq), _f64(ev.Bv), _f64(ev.Pv)]
+        d.x, d.u, d.S, d.Nq, d.Bv, d.Pv = [a.ctypes.data if a.size else None for a in self._keep]
+        tr = ev.transport
+        d.eta_over_s, d.zeta_peak, d.zeta_T_GeV, d.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
+        d.tau_pi_coef, d.tau_Pi_ratio, d.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
+        d.fatal_mask, d.use_graph = fatal_mask, int(use_graph)
+        d.stream = stream
+        d.profile = int(profile)
+        self.h = sph_init_event(d, self.eos)
+
+    def step(self, nsteps: int, sync: bool = False):
+        sph_step(self.h, nsteps, SPH_SYNC if sync else 0)
+
+    def read(self, names=("X", "U", "S", "NQ", "BV", "PV")):
+        """Fields in original particle order, as numpy arrays."""
+        shapes = {"X": (self.dim, "x"), "U": (self.dim, "u"), "S": (1, "S"), "NQ": (3, "Nq"), "BV": (1, "Bv"),
+                  "PV": (self.npi, "Pv"), "SIGMA_STAR": (1, "sigstar"), "S_DENS": (1, "s"), "N_DENS": (3, "nq"),
+                  "T": (1, "T"), "MU": (3, "mu"), "P": (1, "p"), "E": (1, "e"), "PI_BULK": (1, "Pi"),
+                  "STATUS": (1, "status"), "NNB": (1, "nnb"), "CELL": (self.dim, "cell")}
+        b = FieldBufs()
+        out, mask = {}, 0
+        for nm in names:
+            rows, attr = shapes[nm]
+            dt = np.uint32 if nm == "STATUS" else (np.int32 if nm in ("NNB", "CELL") else np.float64)
+            arr = np.zeros((rows, self.n), dtype=dt)
+            out[nm] = arr if rows > 1 else arr[0]
+            setattr(b, attr, arr.ctypes.data)
+            mask |= F[nm]
+        sph_read_fields(self.h, mask, b, None)
+        return out
+
+    def totals(self):
+        t = Totals()
+        sph_read_fields(self.h, 0, None, t)
+        return {"tau": t.tau, "E": t.E, "S": t.S, "N": np.array(t.N[:]), "work": t.work,
+                "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs, "kernel_launches": t.kernel_launches}
+
+    def kernel_times(self):
+        return sph_kernel_times(self.h)
+
+    def neighbors(self):
+        cnt = sph_debug_neighbors(self.h, 0, None, None)
+        pa = np.zeros(max(cnt, 1), dtype=np.int32)
+        pb = np.zeros(max(cnt, 1), dtype=np.int32)
+        sph_debug_neighbors(self.h, cnt, pa, pb)
+        return pa[:cnt], pb[:cnt]
+
+    def rates(self):
+        r = np.zeros((self.nv, self.n))
+        g = np.zeros((6, self.n))
+        sph_debug_rates(self.h, r, g)
+        return r, g
+
+    def write_state(self, x=None, u=None, S=None, Bv=None, Pv=None):
+        b = FieldBufs()
+        keep, mask = [], 0
+        for nm, arr, attr in [("X", x, "x"), ("U", u, "u"), ("S", S, "S"), ("BV", Bv, "Bv"), ("PV", Pv, "Pv")]:
+            if arr is not None:
+                a = _f64(arr)
+                keep.append(a)
+                setattr(b, attr, a.ctypes.data)
+                mask |= F[nm]
+        sph_write_state(self.h, mask, b)
+
+    def free(self):
+        if self.h is not None:
+            sph_free_event(self.h)
+            self.h = None
+        if self._own_eos and self.eos is not None:
+            sph_free_eos(self.eos)
+            self.eos = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

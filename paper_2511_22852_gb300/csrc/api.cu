@@ -1,0 +1,794 @@
+// api.cu -- the C ABI of include/sph_gb300.h: EoS and event handles, the
+// per-stage launch sequence, CUDA-graph replay of whole steps, and read-out in
+// the original particle order.
+//
+// One Heun step (two stages) on device buffers A/B (state), C/D (stage state):
+//   stage 1: bbox(A) -> cells -> permute A -> B -> density(B) -> eos(B) ->
+//            gradient(B) -> eom: C = B + dt f(B)
+//   stage 2: bbox(C) -> cells -> permute C -> D and B -> A -> density(D) ->
+//            eos(D) -> gradient(D) -> eom: A = ((A + D) + dt f(D)) / 2
+// so the state is back in A after every step and the whole step can be captured
+// once as a CUDA graph and replayed; tau and the work integral live in device
+// memory and are advanced by the last kernel of the step.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sph_gb300.h"
+#include "sph_internal.cuh"
+
+using namespace sphg;
+
+static thread_local std::string g_err;
+
+static sph_status fail(sph_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(SPH_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct sph_eos {
+    EosDev dev;
+    double *d_sn = nullptr, *d_p = nullptr;
+    int refs = 1;
+};
+
+struct sph_event {
+    sph_eos *eos = nullptr;
+    int n = 0, dim = 2, milne = 1, viscous = 0, npi = 3, nv = 9, B = 6;
+    double h = 0.3, dtau = 0.01, tau0 = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevScalars *sc = nullptr;
+    double *Y[2] = {nullptr, nullptr}, *Y1[2] = {nullptr, nullptr}, *Nq[2] = {nullptr, nullptr};
+    int *id[2] = {nullptr, nullptr};
+    double *Nq_orig = nullptr;
+    CellBufs cb{};
+    double *dens = nullptr, *eosf = nullptr, *gin = nullptr, *gout = nullptr;
+    uint32_t *status = nullptr;
+    int *nnb = nullptr;
+    double *wpart = nullptr;
+    int nwblk = 1;
+    double *scratch = nullptr;  // read-out staging, rates, totals contributions
+    double *ntot = nullptr;     // fixed-order sums of the charges (constant), + scratch
+    double *tot = nullptr;      // totals scratch
+    TransportDev tr{};
+    uint32_t fatal_mask = 0;
+    bool use_graph = false, graph_ready = false, observed = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long host_steps = 0;
+    long long launches = 0;
+    double timeout_s = 600.0;
+    std::vector<void *> allocs;
+    // profile mode: CUDA events around every kernel group of a step
+    bool profile = false;
+    std::vector<cudaEvent_t> pev;  // 2 per (group, stage)
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// kernel groups timed in profile mode
+enum { G_CELLS = 0, G_PERMUTE, G_DENSITY, G_EOS, G_GRADIENT, G_EOM, G_WORK, G_COUNT };
+static const char *kGroupNames[G_COUNT] = {"cells", "permute", "density", "eos", "gradient", "eom", "work"};
+// kernels per stage: bbox (2), cells/scan/scatter/rank (4), permute, density, eos, gradient, eom, work
+constexpr int kKernelsPerStage = 12;
+
+static inline void mark(sph_event *ev, int group, int stage, int end)
+{
+    if (!ev->profile) return;
+    cudaEventRecord(ev->pev[(size_t)((group * 2 + (stage - 1)) * 2 + end)], ev->stream);
+}
+
+static EvView make_view(const sph_event *ev)
+{
+    EvView v;
+    v.n = ev->n;
+    v.dim = ev->dim;
+    v.milne = ev->milne;
+    v.nv = ev->nv;
+    v.B = ev->B;
+    v.h = ev->h;
+    v.inv_h = 1.0 / ev->h;
+    double two_h = 2.0 * ev->h;
+    v.supp2 = two_h * two_h;
+    v.inv_cell = 1.0 / (2.0 * ev->h);
+    v.sigma_d = ev->dim == 2 ? 10.0 / (7.0 * kPi * ev->h * ev->h) : 1.0 / (kPi * ev->h * ev->h * ev->h);
+    v.dtau = ev->dtau;
+    v.sc = ev->sc;
+    v.eos = ev->eos->dev;
+    v.tr = ev->tr;
+    return v;
+}
+
+static sph_status dalloc(sph_event *ev, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPH_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    ev->allocs.push_back(*p);
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch sequences
+static void enqueue_sort(sph_event *ev, const EvView &v, const double *ysrc, const int *idsrc)
+{
+    launch_bbox(v, ysrc, ev->stream);
+    launch_cells(v, ysrc, idsrc, ev->cb, ev->stream);
+}
+
+static void enqueue_step(sph_event *ev)
+{
+    EvView v = make_view(ev);
+    cudaStream_t st = ev->stream;
+    // stage 1
+    mark(ev, G_CELLS, 1, 0);
+    enqueue_sort(ev, v, ev->Y[0], ev->id[0]);
+    mark(ev, G_CELLS, 1, 1);
+    mark(ev, G_PERMUTE, 1, 0);
+    {
+        const double *src[2] = {ev->Y[0], ev->Nq[0]};
+        double *dst[2] = {ev->Y[1], ev->Nq[1]};
+        int rows[2] = {ev->nv, 3};
+        launch_permute(v, ev->cb.perm, src, dst, rows, 2, ev->id[0], ev->id[1], st);
+    }
+    mark(ev, G_PERMUTE, 1, 1);
+    mark(ev, G_DENSITY, 1, 0);
+    launch_density(v, ev->Y[1], ev->Nq[1], ev->cb, ev->dens, ev->nnb, st);
+    mark(ev, G_DENSITY, 1, 1);
+    mark(ev, G_EOS, 1, 0);
+    launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, st);
+    mark(ev, G_EOS, 1, 1);
+    mark(ev, G_GRADIENT, 1, 0);
+    launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
+    mark(ev, G_GRADIENT, 1, 1);
+    mark(ev, G_EOM, 1, 0);
+    launch_eom(v, 1, 0, ev->Y[1], ev->dens, ev->eosf, ev->gout, ev->Y1[0], nullptr, ev->status, st);
+    mark(ev, G_EOM, 1, 1);
+    mark(ev, G_WORK, 1, 0);
+    launch_work_finish(v, 1, ev->wpart, ev->nwblk, st);
+    mark(ev, G_WORK, 1, 1);
+    // stage 2
+    mark(ev, G_CELLS, 2, 0);
+    enqueue_sort(ev, v, ev->Y1[0], ev->id[1]);
+    mark(ev, G_CELLS, 2, 1);
+    mark(ev, G_PERMUTE, 2, 0);
+    {
+        const double *src[3] = {ev->Y1[0], ev->Y[1], ev->Nq[1]};
+        double *dst[3] = {ev->Y1[1], ev->Y[0], ev->Nq[0]};
+        int rows[3] = {ev->nv, ev->nv, 3};
+        launch_permute(v, ev->cb.perm, src, dst, rows, 3, ev->id[1], ev->id[0], st);
+    }
+    mark(ev, G_PERMUTE, 2, 1);
+    mark(ev, G_DENSITY, 2, 0);
+    launch_density(v, ev->Y1[1], ev->Nq[0], ev->cb, ev->dens, ev->nnb, st);
+    mark(ev, G_DENSITY, 2, 1);
+    mark(ev, G_EOS, 2, 0);
+    launch_eos(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, st);
+    mark(ev, G_EOS, 2, 1);
+    mark(ev, G_GRADIENT, 2, 0);
+    launch_gradient(v, 2, ev->Y1[1], ev->gin, ev->cb, ev->gout, st);
+    mark(ev, G_GRADIENT, 2, 1);
+    mark(ev, G_EOM, 2, 0);
+    launch_eom(v, 2, 1, ev->Y1[1], ev->dens, ev->eosf, ev->gout, ev->Y[0], nullptr, ev->status, st);
+    mark(ev, G_EOM, 2, 1);
+    mark(ev, G_WORK, 2, 0);
+    launch_work_finish(v, 2, ev->wpart, ev->nwblk, st);
+    mark(ev, G_WORK, 2, 1);
+}
+
+// profile mode: wait for the step and add the group times
+static sph_status collect_profile(sph_event *ev)
+{
+    CK(cudaStreamSynchronize(ev->stream));
+    for (int g = 0; g < G_COUNT; ++g)
+        for (int s = 0; s < 2; ++s) {
+            float ms = 0.0f;
+            size_t k = (size_t)((g * 2 + s) * 2);
+            CK(cudaEventElapsedTime(&ms, ev->pev[k], ev->pev[k + 1]));
+            ev->prof_ms[g] += ms;
+            ev->prof_n[g] += 1;
+        }
+    return SPH_OK;
+}
+
+// cell list, densities and EoS at the current state, into the B buffers (sorted)
+static void enqueue_observe(sph_event *ev)
+{
+    EvView v = make_view(ev);
+    cudaStream_t st = ev->stream;
+    enqueue_sort(ev, v, ev->Y[0], ev->id[0]);
+    const double *src[2] = {ev->Y[0], ev->Nq[0]};
+    double *dst[2] = {ev->Y[1], ev->Nq[1]};
+    int rows[2] = {ev->nv, 3};
+    launch_permute(v, ev->cb.perm, src, dst, rows, 2, ev->id[0], ev->id[1], st);
+    launch_density(v, ev->Y[1], ev->Nq[1], ev->cb, ev->dens, ev->nnb, st);
+    launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, st);
+}
+
+static sph_status wait_stream(sph_event *ev)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(ev->stream);
+        if (e == cudaSuccess) return SPH_OK;
+        if (e != cudaErrorNotReady) return fail(SPH_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > ev->timeout_s) return fail(SPH_ERR_TIMEOUT, "device did not finish within the wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 20 : 500));
+    }
+}
+
+static sph_status check_device_flags(sph_event *ev, DevScalars *hs)
+{
+    CK(cudaMemcpyAsync(hs, ev->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ev->stream));
+    sph_status s = wait_stream(ev);
+    if (s != SPH_OK) return s;
+    if (hs->err_flags & ERR_CELL_OVERFLOW)
+        return fail(SPH_ERR_STATE, "particles spread beyond the cell table fixed at sph_init_event");
+    uint32_t bad = hs->status_or & ev->fatal_mask;
+    if (bad & PST_NONFINITE) return fail(SPH_ERR_NONFINITE, "non-finite state or rate");
+    if (bad & PST_NOCONV) return fail(SPH_ERR_EOS_NOCONV, "EoS inversion without solution");
+    if (bad & (PST_OUT_OF_TABLE | PST_FALLBACK)) return fail(SPH_ERR_EOS_RANGE, "particle outside the EoS table");
+    if (bad) return fail(SPH_ERR_STATE, "fatal per-particle status");
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *sph_last_error(void) { return g_err.c_str(); }
+
+sph_status sph_set_eos_table(sph_eos **out, const sph_eos_desc *d)
+{
+    if (!out || !d) return fail(SPH_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (!(d->a0 > 0.0) || !(d->w_GeV > 0.0) || d->a1 < 0.0) return fail(SPH_ERR_ARG, "closed-form EoS needs a0 > 0, w > 0, a1 >= 0");
+    for (int q = 0; q < 3; ++q)
+        if (d->chi[q] < 0.0) return fail(SPH_ERR_ARG, "chi must be >= 0");
+    sph_eos *e = new (std::nothrow) sph_eos();
+    if (!e) return fail(SPH_ERR_OOM, "host allocation");
+    EosDev &E = e->dev;
+    memset(&E, 0, sizeof(E));
+    E.a0 = d->a0;
+    E.a1 = d->a1;
+    E.Tc_GeV = d->Tc_GeV;
+    E.w_GeV = d->w_GeV;
+    for (int q = 0; q < 3; ++q) E.chi[q] = d->chi[q];
+    E.tol = d->newton_tol > 0.0 ? d->newton_tol : 1e-12;
+    E.maxit = d->newton_maxit > 0 ? d->newton_maxit : 30;
+    E.has_table = d->has_table ? 1 : 0;
+    if (E.has_table) {
+        if (!d->p || !d->s || !d->nB || !d->nS || !d->nQ) {
+            delete e;
+            return fail(SPH_ERR_ARG, "table arrays must be non-null");
+        }
+        if (d->nT < 2 || d->nmu[0] < 2 || d->nmu[1] < 2 || d->nmu[2] < 2 || !(d->dT > 0.0) || !(d->dmu[0] > 0.0) ||
+            !(d->dmu[1] > 0.0) || !(d->dmu[2] > 0.0)) {
+            delete e;
+            return fail(SPH_ERR_ARG, "table needs >= 2 nodes per axis and positive spacings");
+        }
+        E.nT = d->nT;
+        E.T0 = d->T0;
+        E.dT = d->dT;
+        E.inv_dT = 1.0 / d->dT;
+        E.Tmax = d->T0 + (d->nT - 1) * d->dT;
+        for (int q = 0; q < 3; ++q) {
+            E.nmu[q] = d->nmu[q];
+            E.mu0[q] = d->mu0[q];
+            E.dmu[q] = d->dmu[q];
+            E.inv_dmu[q] = 1.0 / d->dmu[q];
+            E.mumax[q] = d->mu0[q] + (d->nmu[q] - 1) * d->dmu[q];
+        }
+        size_t nn = (size_t)d->nT * d->nmu[0] * d->nmu[1] * d->nmu[2];
+        std::vector<double> sn(4 * nn);
+        for (size_t i = 0; i < nn; ++i) {
+            sn[4 * i] = d->s[i];
+            sn[4 * i + 1] = d->nB[i];
+            sn[4 * i + 2] = d->nS[i];
+            sn[4 * i + 3] = d->nQ[i];
+        }
+        cudaError_t c1 = cudaMalloc(&e->d_sn, sizeof(double) * 4 * nn);
+        cudaError_t c2 = cudaMalloc(&e->d_p, sizeof(double) * nn);
+        if (c1 != cudaSuccess || c2 != cudaSuccess) {
+            cudaGetLastError();
+            if (e->d_sn) cudaFree(e->d_sn);
+            if (e->d_p) cudaFree(e->d_p);
+            delete e;
+            return fail(SPH_ERR_OOM, "cudaMalloc of the EoS table failed");
+        }
+        cudaError_t c3 = cudaMemcpy(e->d_sn, sn.data(), sizeof(double) * 4 * nn, cudaMemcpyHostToDevice);
+        cudaError_t c4 = cudaMemcpy(e->d_p, d->p, sizeof(double) * nn, cudaMemcpyHostToDevice);
+        if (c3 != cudaSuccess || c4 != cudaSuccess) {
+            cudaFree(e->d_sn);
+            cudaFree(e->d_p);
+            delete e;
+            return fail(SPH_ERR_CUDA, "copy of the EoS table failed");
+        }
+        E.sn = e->d_sn;
+        E.p = e->d_p;
+    }
+    *out = e;
+    return SPH_OK;
+}
+
+void sph_free_eos(sph_eos *e)
+{
+    if (!e) return;
+    if (--e->refs > 0) return;
+    if (e->d_sn) cudaFree(e->d_sn);
+    if (e->d_p) cudaFree(e->d_p);
+    delete e;
+}
+
+void sph_free_event(sph_event *ev)
+{
+    if (!ev) return;
+    if (ev->stream) cudaStreamSynchronize(ev->stream);
+    if (ev->gexec) cudaGraphExecDestroy(ev->gexec);
+    if (ev->graph) cudaGraphDestroy(ev->graph);
+    for (cudaEvent_t e : ev->pev) cudaEventDestroy(e);
+    for (void *p : ev->allocs) cudaFree(p);
+    if (ev->own_stream && ev->stream) cudaStreamDestroy(ev->stream);
+    sph_free_eos(ev->eos);
+    delete ev;
+}
+
+sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eos *eos)
+{
+    if (!out || !d || !eos) return fail(SPH_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (d->dim != 2) return fail(SPH_ERR_ARG, "this version implements dim = 2");
+    if (d->n < 0 || d->n > 0x7FFFFFFF) return fail(SPH_ERR_ARG, "n out of range");
+    if (!(d->h > 0.0) || !(d->dtau > 0.0)) return fail(SPH_ERR_ARG, "h and dtau must be positive");
+    if (d->milne && !(d->tau0 > 0.0)) return fail(SPH_ERR_ARG, "Milne coordinates need tau0 > 0");
+    if (d->n > 0 && (!d->x || !d->u || !d->S || !d->Nq)) return fail(SPH_ERR_ARG, "null particle array");
+    if (d->viscous && (!(d->tau_pi_coef > 0.0) || !(d->tau_Pi_ratio > 0.0) || !(d->eta_over_s > 0.0)))
+        return fail(SPH_ERR_ARG, "viscous run needs eta_over_s, tau_pi_coef, tau_Pi_ratio > 0");
+    sph_event *ev = new (std::nothrow) sph_event();
+    if (!ev) return fail(SPH_ERR_OOM, "host allocation");
+    ev->eos = const_cast<sph_eos *>(eos);
+    ev->eos->refs++;
+    ev->n = (int)d->n;
+    ev->dim = d->dim;
+    ev->milne = d->milne ? 1 : 0;
+    ev->viscous = d->viscous ? 1 : 0;
+    ev->npi = 3;
+    ev->nv = 2 * ev->dim + 2 + ev->npi;
+    ev->h = d->h;
+    ev->dtau = d->dtau;
+    ev->tau0 = d->tau0;
+    ev->fatal_mask = d->fatal_mask;
+    ev->profile = d->profile != 0;
+    ev->use_graph = d->use_graph != 0 && !ev->profile;
+    if (ev->profile) {
+        ev->pev.resize(G_COUNT * 2 * 2);
+        for (auto &e : ev->pev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                e = nullptr;
+                sph_free_event(ev);
+                return fail(SPH_ERR_CUDA, "cudaEventCreate failed");
+            }
+    }
+    ev->tr.viscous = ev->viscous;
+    ev->tr.eta_over_s = d->eta_over_s;
+    ev->tr.zeta_peak = d->zeta_peak;
+    ev->tr.zeta_T_GeV = d->zeta_T_GeV;
+    ev->tr.zeta_w_GeV = d->zeta_w_GeV > 0.0 ? d->zeta_w_GeV : 1.0;
+    ev->tr.tau_pi_coef = d->tau_pi_coef;
+    ev->tr.tau_Pi_ratio = d->tau_Pi_ratio;
+    ev->tr.cs2_cap = d->cs2_cap > 0.0 ? d->cs2_cap : 1.0;
+    if (const char *t = getenv("SPH_WAIT_LIMIT_S")) ev->timeout_s = atof(t);
+    auto bail = [&](sph_status s) {
+        std::string keep = g_err;
+        sph_free_event(ev);
+        g_err = keep;
+        return s;
+    };
+    if (d->stream) {
+        ev->stream = (cudaStream_t)d->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ev->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(SPH_ERR_CUDA, "cudaStreamCreate failed"));
+        }
+        ev->own_stream = true;
+    }
+    const int n = ev->n;
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    // cell table: 2^B cells per axis, four times the initial extent
+    std::vector<double> hx((size_t)ev->dim * N, 0.0);
+    if (n > 0) {
+        cudaMemcpyKind k = d->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        if (cudaMemcpy(hx.data(), d->x, sizeof(double) * ev->dim * n, k) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(SPH_ERR_ARG, "cannot read positions"));
+        }
+    }
+    int ncmax = 1;
+    for (int dd = 0; dd < ev->dim; ++dd) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = 0; i < n; ++i) {
+            double xv = hx[(size_t)dd * n + i];
+            if (!std::isfinite(xv)) return bail(fail(SPH_ERR_NONFINITE, "non-finite position"));
+            lo = std::min(lo, xv);
+            hi = std::max(hi, xv);
+        }
+        if (n > 0) ncmax = std::max(ncmax, (int)std::floor((hi - lo) / (2.0 * ev->h)) + 1);
+    }
+    int B = 3;
+    while ((1 << B) < 4 * ncmax && B < 15) ++B;
+    if ((1 << B) < ncmax) return bail(fail(SPH_ERR_ARG, "domain too large for the cell table"));
+    ev->B = B;
+    ev->cb.nb = 1 << (2 * B);
+    sph_status s;
+#define AL(ptr, bytes)                                                    \
+    do {                                                                  \
+        if ((s = dalloc(ev, (void **)&(ptr), (bytes))) != SPH_OK) return bail(s); \
+    } while (0)
+    const size_t dv = sizeof(double) * N;
+    AL(ev->sc, sizeof(DevScalars));
+    for (int b = 0; b < 2; ++b) {
+        AL(ev->Y[b], dv * ev->nv);
+        AL(ev->Y1[b], dv * ev->nv);
+        AL(ev->Nq[b], dv * 3);
+        AL(ev->id[b], sizeof(int) * N);
+    }
+    AL(ev->Nq_orig, dv * 3);
+    AL(ev->cb.key, sizeof(uint32_t) * N);
+    AL(ev->cb.tmp, sizeof(uint32_t) * N);
+    AL(ev->cb.perm, sizeof(uint32_t) * N);
+    AL(ev->cb.cnt, sizeof(uint32_t) * (size_t)ev->cb.nb);
+    AL(ev->cb.start, sizeof(uint32_t) * (size_t)ev->cb.nb);
+    AL(ev->cb.cursor, sizeof(uint32_t) * (size_t)ev->cb.nb);
+    AL(ev->dens, dv * kNDens);
+    AL(ev->eosf, dv * kNEos);
+    AL(ev->gin, dv * kNGin);
+    AL(ev->gout, dv * kNGout);
+    AL(ev->status, sizeof(uint32_t) * N);
+    AL(ev->nnb, sizeof(int) * N);
+    ev->nwblk = eom_block_count(n > 0 ? n : 1);
+    AL(ev->wpart, sizeof(double) * (size_t)ev->nwblk);
+    AL(ev->scratch, dv * std::max(ev->nv, kNEos));
+    AL(ev->ntot, sizeof(double) * (8 + 3 * 256));
+    AL(ev->tot, sizeof(double) * (8 + 3 * 256));
+#undef AL
+    cudaStream_t st = ev->stream;
+    if (n > 0) {
+        cudaMemcpyKind k = d->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        size_t dn = sizeof(double) * n;
+        CK(cudaMemcpyAsync(ev->Y[0], d->x, dn * ev->dim, k, st));
+        CK(cudaMemcpyAsync(ev->Y[0] + (size_t)ev->dim * n, d->u, dn * ev->dim, k, st));
+        CK(cudaMemcpyAsync(ev->Y[0] + (size_t)2 * ev->dim * n, d->S, dn, k, st));
+        if (d->Bv) CK(cudaMemcpyAsync(ev->Y[0] + (size_t)(2 * ev->dim + 1) * n, d->Bv, dn, k, st));
+        else CK(cudaMemsetAsync(ev->Y[0] + (size_t)(2 * ev->dim + 1) * n, 0, dn, st));
+        if (d->Pv) CK(cudaMemcpyAsync(ev->Y[0] + (size_t)(2 * ev->dim + 2) * n, d->Pv, dn * ev->npi, k, st));
+        else CK(cudaMemsetAsync(ev->Y[0] + (size_t)(2 * ev->dim + 2) * n, 0, dn * ev->npi, st));
+        CK(cudaMemcpyAsync(ev->Nq[0], d->Nq, dn * 3, k, st));
+        CK(cudaMemcpyAsync(ev->Nq_orig, d->Nq, dn * 3, k, st));
+        std::vector<int> iota(n);
+        for (int i = 0; i < n; ++i) iota[i] = i;
+        CK(cudaMemcpyAsync(ev->id[0], iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        if (!ev->viscous) {  // an ideal fluid carries no dissipative state
+            CK(cudaMemsetAsync(ev->Y[0] + (size_t)(2 * ev->dim + 1) * n, 0, dn * (1 + ev->npi), st));
+        }
+        launch_sum_fixed(ev->Nq_orig, n, 3, ev->ntot, st);
+    }
+    DevScalars hs;
+    memset(&hs, 0, sizeof(hs));
+    hs.tau = d->tau0;
+    CK(cudaMemcpyAsync(ev->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    *out = ev;
+    return SPH_OK;
+}
+
+sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (nsteps < 0) return fail(SPH_ERR_ARG, "nsteps < 0");
+    if (ev->n == 0 || nsteps == 0) return SPH_OK;
+    if (ev->use_graph && !ev->graph_ready) {
+        CK(cudaStreamBeginCapture(ev->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(ev);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ev->stream, &g);
+        if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        ev->graph = g;
+        CK(cudaGraphInstantiate(&ev->gexec, g, 0));
+        ev->graph_ready = true;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        if (ev->use_graph) {
+            CK(cudaGraphLaunch(ev->gexec, ev->stream));
+        } else {
+            enqueue_step(ev);
+            if (ev->profile) {
+                sph_status s = collect_profile(ev);
+                if (s != SPH_OK) return s;
+            }
+        }
+    }
+    CK(cudaGetLastError());
+    ev->host_steps += nsteps;
+    ev->launches += (long long)nsteps * 2 * kKernelsPerStage;
+    ev->observed = false;
+    if (flags & SPH_SYNC) {
+        DevScalars hs;
+        return check_device_flags(ev, &hs);
+    }
+    return SPH_OK;
+}
+
+static sph_status copy_out(sph_event *ev, void *dst, const void *src, size_t bytes, int on_device)
+{
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ev->stream));
+    return wait_stream(ev);
+}
+
+sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o, sph_totals *tot)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (mask && !o) return fail(SPH_ERR_ARG, "null buffers");
+    const int n = ev->n;
+    const size_t dn = sizeof(double) * (size_t)n;
+    cudaStream_t st = ev->stream;
+    const uint64_t derived = SPH_F_SIGMA_STAR | SPH_F_S_DENS | SPH_F_N_DENS | SPH_F_T | SPH_F_MU | SPH_F_P | SPH_F_E |
+                             SPH_F_PI_BULK | SPH_F_STATUS | SPH_F_NNB | SPH_F_CELL;
+    if (n > 0 && ((mask & derived) || tot) && !ev->observed) {
+        enqueue_observe(ev);
+        CK(cudaGetLastError());
+        ev->observed = true;
+    }
+    struct Row {
+        uint64_t bit;
+        double *dst;
+        const double *src;
+        int rows;
+        int state;  // 1: from the state buffer (id[0]); 0: derived (id[1])
+    };
+    double *dens = ev->dens, *eo = ev->eosf;
+    const size_t N = (size_t)n;
+    std::vector<Row> rows = {
+        {SPH_F_X, o ? o->x : nullptr, ev->Y[0], ev->dim, 1},
+        {SPH_F_U, o ? o->u : nullptr, ev->Y[0] + ev->dim * N, ev->dim, 1},
+        {SPH_F_S, o ? o->S : nullptr, ev->Y[0] + 2 * ev->dim * N, 1, 1},
+        {SPH_F_NQ, o ? o->Nq : nullptr, ev->Nq[0], 3, 1},
+        {SPH_F_BV, o ? o->Bv : nullptr, ev->Y[0] + (2 * ev->dim + 1) * N, 1, 1},
+        {SPH_F_PV, o ? o->Pv : nullptr, ev->Y[0] + (2 * ev->dim + 2) * N, ev->npi, 1},
+        {SPH_F_SIGMA_STAR, o ? o->sigstar : nullptr, dens, 1, 0},
+        {SPH_F_S_DENS, o ? o->s : nullptr, dens + N, 1, 0},
+        {SPH_F_N_DENS, o ? o->nq : nullptr, dens + 2 * N, 3, 0},
+        {SPH_F_T, o ? o->T : nullptr, eo, 1, 0},
+        {SPH_F_MU, o ? o->mu : nullptr, eo + N, 3, 0},
+        {SPH_F_P, o ? o->p : nullptr, eo + 4 * N, 1, 0},
+        {SPH_F_E, o ? o->e : nullptr, eo + 5 * N, 1, 0},
+    };
+    for (auto &r : rows) {
+        if (!(mask & r.bit)) continue;
+        if (!r.dst) return fail(SPH_ERR_ARG, "requested field has a null destination");
+        if (n == 0) continue;
+        launch_scatter_orig(r.src, ev->scratch, r.state ? ev->id[0] : ev->id[1], n, r.rows, st);
+        sph_status s = copy_out(ev, r.dst, ev->scratch, dn * r.rows, o->on_device);
+        if (s != SPH_OK) return s;
+    }
+    if (mask & SPH_F_PI_BULK) {
+        if (!o->Pi) return fail(SPH_ERR_ARG, "requested field has a null destination");
+        if (n > 0) {
+            // Pi = sigma * (Pi/sigma) with sigma = sigma* / (u^0 sqrt(-g)), on the host side of the copy
+            std::vector<double> bv(n), sg(n), u0(n);
+            launch_scatter_orig(ev->Y[1] + (2 * ev->dim + 1) * N, ev->scratch, ev->id[1], n, 1, st);
+            sph_status s = copy_out(ev, bv.data(), ev->scratch, dn, 0);
+            if (s != SPH_OK) return s;
+            launch_scatter_orig(dens, ev->scratch, ev->id[1], n, 1, st);
+            if ((s = copy_out(ev, sg.data(), ev->scratch, dn, 0)) != SPH_OK) return s;
+            launch_scatter_orig(dens + 5 * N, ev->scratch, ev->id[1], n, 1, st);
+            if ((s = copy_out(ev, u0.data(), ev->scratch, dn, 0)) != SPH_OK) return s;
+            DevScalars hs;
+            CK(cudaMemcpy(&hs, ev->sc, sizeof(hs), cudaMemcpyDeviceToHost));
+            double sqrtg = ev->milne ? hs.tau : 1.0;
+            std::vector<double> Pi(n);
+            for (int i = 0; i < n; ++i) Pi[i] = ev->viscous ? sg[i] / (u0[i] * sqrtg) * bv[i] : 0.0;
+            CK(cudaMemcpy(o->Pi, Pi.data(), dn, o->on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+        }
+    }
+    if (mask & SPH_F_STATUS) {
+        if (!o->status) return fail(SPH_ERR_ARG, "requested field has a null destination");
+        if (n > 0) {
+            launch_scatter_orig_u32(ev->status, (uint32_t *)ev->scratch, ev->id[1], n, st);
+            sph_status s = copy_out(ev, o->status, ev->scratch, sizeof(uint32_t) * n, o->on_device);
+            if (s != SPH_OK) return s;
+        }
+    }
+    if (mask & SPH_F_NNB) {
+        if (!o->nnb) return fail(SPH_ERR_ARG, "requested field has a null destination");
+        if (n > 0) {
+            launch_scatter_orig_u32((const uint32_t *)ev->nnb, (uint32_t *)ev->scratch, ev->id[1], n, st);
+            sph_status s = copy_out(ev, o->nnb, ev->scratch, sizeof(int) * n, o->on_device);
+            if (s != SPH_OK) return s;
+        }
+    }
+    if (mask & SPH_F_CELL) {
+        if (!o->cell) return fail(SPH_ERR_ARG, "requested field has a null destination");
+        if (n > 0) {
+            EvView v = make_view(ev);
+            launch_cell_coords(v, ev->Y[1], ev->id[1], (int *)ev->scratch, st);
+            sph_status s = copy_out(ev, o->cell, ev->scratch, sizeof(int) * ev->dim * n, o->on_device);
+            if (s != SPH_OK) return s;
+        }
+    }
+    if (tot) {
+        memset(tot, 0, sizeof(*tot));
+        DevScalars hs;
+        if (n > 0) {
+            EvView v = make_view(ev);
+            launch_totals(v, ev->Y[1], ev->Nq[1], ev->id[1], dens, eo, ev->scratch, st);
+            launch_sum_fixed(ev->scratch, n, 2, ev->tot, st);
+            double h2[2], hn[3];
+            CK(cudaMemcpyAsync(h2, ev->tot, sizeof(h2), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hn, ev->ntot, sizeof(hn), cudaMemcpyDeviceToHost, st));
+            sph_status s = check_device_flags(ev, &hs);
+            if (s != SPH_OK && s != SPH_ERR_EOS_RANGE && s != SPH_ERR_EOS_NOCONV && s != SPH_ERR_NONFINITE) return s;
+            tot->E = h2[0];
+            tot->S = h2[1];
+            for (int q = 0; q < 3; ++q) tot->N[q] = hn[q];
+        } else {
+            CK(cudaMemcpy(&hs, ev->sc, sizeof(hs), cudaMemcpyDeviceToHost));
+        }
+        tot->tau = hs.tau;
+        tot->work = hs.work;
+        tot->status_or = hs.status_or;
+        tot->steps = hs.steps;
+        tot->pairs = (int64_t)hs.pairs;
+        tot->kernel_launches = ev->launches;
+    }
+    return wait_stream(ev);
+}
+
+sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count)
+{
+    if (!ev || !count) return fail(SPH_ERR_ARG, "null argument");
+    if (!ev->profile) return fail(SPH_ERR_STATE, "event was not created with profile = 1");
+    int m = std::min<int>(max, G_COUNT);
+    for (int g = 0; g < m; ++g) {
+        if (names) {
+            strncpy(names + 32 * g, kGroupNames[g], 31);
+            names[32 * g + 31] = 0;
+        }
+        if (ms) ms[g] = ev->prof_ms[g];
+        if (launches) launches[g] = ev->prof_n[g];
+    }
+    *count = m;
+    return SPH_OK;
+}
+
+sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *in)
+{
+    if (!ev || !in) return fail(SPH_ERR_ARG, "null argument");
+    const int n = ev->n;
+    if (n == 0) return SPH_OK;
+    const size_t N = (size_t)n;
+    // the state buffer is in sorted order; bring it back to the original order first
+    cudaStream_t st = ev->stream;
+    launch_scatter_orig(ev->Y[0], ev->scratch, ev->id[0], n, ev->nv, st);
+    CK(cudaMemcpyAsync(ev->Y[0], ev->scratch, sizeof(double) * ev->nv * N, cudaMemcpyDeviceToDevice, st));
+    launch_scatter_orig(ev->Nq[0], ev->scratch, ev->id[0], n, 3, st);
+    CK(cudaMemcpyAsync(ev->Nq[0], ev->scratch, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st));
+    std::vector<int> iota(n);
+    for (int i = 0; i < n; ++i) iota[i] = i;
+    CK(cudaMemcpyAsync(ev->id[0], iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    cudaMemcpyKind k = in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    struct Row {
+        uint64_t bit;
+        const double *src;
+        size_t off;
+        int rows;
+    } rows[] = {
+        {SPH_F_X, in->x, 0, ev->dim},
+        {SPH_F_U, in->u, (size_t)ev->dim, ev->dim},
+        {SPH_F_S, in->S, (size_t)2 * ev->dim, 1},
+        {SPH_F_BV, in->Bv, (size_t)2 * ev->dim + 1, 1},
+        {SPH_F_PV, in->Pv, (size_t)2 * ev->dim + 2, ev->npi},
+    };
+    for (auto &r : rows) {
+        if (!(mask & r.bit)) continue;
+        if (!r.src) return fail(SPH_ERR_ARG, "masked field has a null source");
+        CK(cudaMemcpyAsync(ev->Y[0] + r.off * N, r.src, sizeof(double) * r.rows * N, k, st));
+    }
+    ev->observed = false;
+    return wait_stream(ev);
+}
+
+sph_status sph_debug_neighbors(sph_event *ev, int64_t cap, int32_t *pa, int32_t *pb, int64_t *count)
+{
+    if (!ev || !count) return fail(SPH_ERR_ARG, "null argument");
+    const int n = ev->n;
+    *count = 0;
+    if (n == 0) return SPH_OK;
+    enqueue_observe(ev);
+    ev->observed = true;
+    EvView v = make_view(ev);
+    cudaStream_t st = ev->stream;
+    int *d_cnt = nullptr;
+    long long *d_off = nullptr;
+    CK(cudaMalloc(&d_cnt, sizeof(int) * n));
+    CK(cudaMalloc(&d_off, sizeof(long long) * (n + 1)));
+    launch_neighbors_list(v, ev->Y[1], ev->id[1], ev->cb, nullptr, d_cnt, nullptr, st);
+    launch_scan_counts(d_cnt, d_off, n, st);
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, d_off + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    sph_status s = wait_stream(ev);
+    if (s != SPH_OK) return s;
+    int *d_pa = nullptr, *d_pb = nullptr;
+    CK(cudaMalloc(&d_pa, sizeof(int) * (total > 0 ? total : 1)));
+    CK(cudaMalloc(&d_pb, sizeof(int) * (total > 0 ? total : 1)));
+    launch_neighbors_list(v, ev->Y[1], ev->id[1], ev->cb, d_off, d_pa, d_pb, st);
+    std::vector<int> ha(total), hb(total);
+    if (total > 0) {
+        CK(cudaMemcpyAsync(ha.data(), d_pa, sizeof(int) * total, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hb.data(), d_pb, sizeof(int) * total, cudaMemcpyDeviceToHost, st));
+    }
+    s = wait_stream(ev);
+    cudaFree(d_cnt);
+    cudaFree(d_off);
+    cudaFree(d_pa);
+    cudaFree(d_pb);
+    if (s != SPH_OK) return s;
+    std::vector<long long> key(total);
+    for (long long i = 0; i < total; ++i) key[i] = ((long long)ha[i] << 32) | (unsigned)hb[i];
+    std::sort(key.begin(), key.end());
+    long long m = std::min<long long>(total, cap);
+    for (long long i = 0; i < m; ++i) {
+        pa[i] = (int)(key[i] >> 32);
+        pb[i] = (int)(key[i] & 0xFFFFFFFFLL);
+    }
+    *count = total;
+    return SPH_OK;
+}
+
+sph_status sph_debug_rates(sph_event *ev, double *rates, double *grad)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    const int n = ev->n;
+    if (n == 0) return SPH_OK;
+    enqueue_observe(ev);
+    ev->observed = true;
+    EvView v = make_view(ev);
+    cudaStream_t st = ev->stream;
+    launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
+    const size_t N = (size_t)n;
+    // rates go to Y1[1] (unused outside a step), then to the original order
+    launch_eom(v, 1, 2, ev->Y[1], ev->dens, ev->eosf, ev->gout, nullptr, ev->Y1[1], ev->status, st);
+    if (rates) {
+        launch_scatter_orig(ev->Y1[1], ev->scratch, ev->id[1], n, ev->nv, st);
+        sph_status s = copy_out(ev, rates, ev->scratch, sizeof(double) * ev->nv * N, 0);
+        if (s != SPH_OK) return s;
+    }
+    if (grad) {
+        launch_scatter_orig(ev->gout, ev->scratch, ev->id[1], n, kNGout, st);
+        sph_status s = copy_out(ev, grad, ev->scratch, sizeof(double) * kNGout * N, 0);
+        if (s != SPH_OK) return s;
+    }
+    return SPH_OK;
+}
+
+}  // extern "C"

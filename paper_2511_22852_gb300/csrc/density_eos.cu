@@ -1,0 +1,476 @@
+// density_eos.cu -- kernel-sum densities (row a3) and the EoS inversion (row a4).
+//
+// Density pass (eqs. sigmastar, refconv): one thread per particle in sorted
+// order walks the 3x3 cells around its own; consecutive threads of a warp sit
+// in the same or adjacent cells, so the candidate loads are shared through L1.
+// The acceptance test r^2 < (2h)^2 rounds every product separately, so the
+// neighbour set is identical to a plain FP64 evaluation on any platform.
+//
+// EoS pass (Sec. "EoS inverter", online inversion done on the device):
+//   1. closed-form EoS solved for T on its upper branch (mu_q = n_q/(chi_q T^2)),
+//      bracketed Newton with bisection safeguard;
+//   2. if that point lies in the table, damped Newton on the quadrilinear
+//      interpolant of (s, n_B, n_S, n_Q), residual scaled by s, 4x4 Jacobian from
+//      the same 16-corner stencil, one polishing step after convergence;
+//      otherwise (or without convergence) the closed form is kept and flagged;
+//   3. p, e = T s + mu.n - p, and (dp/ds, dp/dn_q) = H^-T (s, n) with H the
+//      Jacobian d(s, n)/d(T, mu) of the EoS used; c_s^2 above the cap scales
+//      them down (flagged).
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+namespace {
+
+__global__ void __launch_bounds__(128) k_density2(EvView v, const double *__restrict__ y, const double *__restrict__ Nq,
+                                                  const uint32_t *__restrict__ start, const uint32_t *__restrict__ cnt,
+                                                  double *__restrict__ dens, int *__restrict__ nnb)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= v.n) return;
+    const int n = v.n;
+    const double *X = y, *Y = y + n, *S = y + 4 * (size_t)n;
+    const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
+    double xa = X[a], ya = Y[a];
+    double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+    int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+    int lim = 1 << v.B;
+    double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
+    int c = 0;
+    for (int oy = -1; oy <= 1; ++oy) {
+        int ny = cy + oy;
+        if (ny < 0 || ny >= lim) continue;
+        for (int ox = -1; ox <= 1; ++ox) {
+            int nx = cx + ox;
+            if (nx < 0 || nx >= lim) continue;
+            uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+            uint32_t b0 = start[k], b1 = b0 + cnt[k];
+            for (uint32_t b = b0; b < b1; ++b) {
+                double r2 = dist2_2d(xa - X[b], ya - Y[b]);
+                if (r2 < v.supp2) {
+                    double q = r2 > 0.0 ? r2 * rsqrt_nr(r2) * v.inv_h : 0.0;
+                    double w = kernel_w(q);
+                    sg += w;
+                    ss = fma(S[b], w, ss);
+                    sb = fma(NB[b], w, sb);
+                    sS = fma(NS[b], w, sS);
+                    sq = fma(NQ[b], w, sq);
+                    ++c;
+                }
+            }
+        }
+    }
+    double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
+    double u0 = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+    double sd = v.sigma_d;
+    unsigned int tot = __reduce_add_sync(__activemask(), (unsigned int)c);
+    if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) atomicAdd(&v.sc->pairs, (unsigned long long)tot);
+    dens[a] = sd * sg;
+    dens[(size_t)n + a] = sd * ss;  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
+    dens[2 * (size_t)n + a] = sd * sb;
+    dens[3 * (size_t)n + a] = sd * sS;
+    dens[4 * (size_t)n + a] = sd * sq;
+    dens[5 * (size_t)n + a] = u0;
+    nnb[a] = c;
+}
+
+// ---------------------------------------------------------------------------
+// closed-form EoS
+__device__ __forceinline__ void an_shape(const EosDev &E, double T, double &f, double &fp, double &fpp)
+{
+    double k = kHbarc / E.w_GeV;
+    double th = tanh((T * kHbarc - E.Tc_GeV) / E.w_GeV);
+    double sech2 = fma(-th, th, 1.0);
+    f = E.a0 + 0.5 * E.a1 * (1.0 + th);
+    fp = 0.5 * E.a1 * sech2 * k;
+    fpp = -E.a1 * sech2 * th * k * k;
+}
+
+__device__ void an_eval(const EosDev &E, double T, const double *mu, double &p, double sn[4], double H[4][4])
+{
+    double f, fp, fpp;
+    an_shape(E, T, f, fp, fpp);
+    double cm2 = E.chi[0] * mu[0] * mu[0] + E.chi[1] * mu[1] * mu[1] + E.chi[2] * mu[2] * mu[2];
+    double T2 = T * T, T3 = T2 * T, T4 = T2 * T2;
+    p = T4 * f + 0.5 * T2 * cm2;
+    sn[0] = 4.0 * T3 * f + T4 * fp + T * cm2;
+    for (int q = 0; q < 3; ++q) sn[1 + q] = E.chi[q] * T2 * mu[q];
+    H[0][0] = 12.0 * T2 * f + 8.0 * T3 * fp + T4 * fpp + cm2;
+    for (int q = 0; q < 3; ++q) {
+        double c = 2.0 * E.chi[q] * T * mu[q];
+        H[0][1 + q] = c;
+        H[1 + q][0] = c;
+        for (int r = 0; r < 3; ++r) H[1 + q][1 + r] = (q == r) ? E.chi[q] * T2 : 0.0;
+    }
+}
+
+// g(T) = s(T, mu(T)) - s_target with mu_q(T) = n_q/(chi_q T^2)
+__device__ __forceinline__ void an_g(const EosDev &E, double T, double s, double c, double &g, double &gp)
+{
+    double f, fp, fpp;
+    an_shape(E, T, f, fp, fpp);
+    double T2 = T * T, T3 = T2 * T, T4 = T2 * T2;
+    g = 4.0 * T3 * f + T4 * fp + c / T3 - s;
+    gp = 12.0 * T2 * f + 8.0 * T3 * fp + T4 * fpp - 3.0 * c / T4;
+}
+
+__device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double &T, double *mu)
+{
+    if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) return PST_NONFINITE | PST_NOCONV;
+    if (!(s > 0.0)) return PST_NOCONV;
+    double c = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        if (E.chi[q] > 0.0) c += n[q] * n[q] / E.chi[q];
+        else if (n[q] != 0.0) return PST_NOCONV;
+    }
+    double Thi = cbrt(s / (4.0 * E.a0));
+    double g, gp;
+    an_g(E, Thi, s, c, g, gp);
+    double Tlo = Thi;
+    if (g > 0.0) {
+        double gprev = g;
+        bool found = false;
+        for (int k = 0; k < 400; ++k) {
+            Tlo *= 0.8;
+            double gl, gpl;
+            an_g(E, Tlo, s, c, gl, gpl);
+            if (gl <= 0.0) {
+                found = true;
+                break;
+            }
+            if (gl > gprev) return PST_NOCONV;
+            gprev = gl;
+        }
+        if (!found) return PST_NOCONV;
+    }
+    double t = Thi;
+    for (int it = 0; it < 200; ++it) {
+        an_g(E, t, s, c, g, gp);
+        if (g == 0.0) break;
+        if (g > 0.0) Thi = t;
+        else Tlo = t;
+        double tn = t - g / gp;
+        if (!(gp > 0.0) || !(tn > Tlo && tn < Thi)) tn = 0.5 * (Tlo + Thi);
+        if (fabs(tn - t) <= 4e-16 * t) {
+            t = tn;
+            break;
+        }
+        t = tn;
+    }
+    T = t;
+    for (int q = 0; q < 3; ++q) mu[q] = E.chi[q] > 0.0 ? n[q] / (E.chi[q] * t * t) : 0.0;
+    return 0u;
+}
+
+// ---------------------------------------------------------------------------
+// table: quadrilinear interpolation evaluated as four bilinear (mu_S, mu_Q)
+// patches combined over (T, mu_B), carrying all four partial derivatives
+__device__ __forceinline__ void locate(double x, double x0, double inv, int nx, int &i, double &t)
+{
+    double r = (x - x0) * inv;
+    int k = (int)floor(r);
+    k = max(0, min(k, nx - 2));
+    i = k;
+    t = r - (double)k;
+}
+
+// sn: interpolated (s, nB, nS, nQ); J[f][k] = d sn_f / d x_k; p optional
+__device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double J[4][4], double *p)
+{
+    int iT, iB, iS, iQ;
+    double tT, tB, tS, tQ;
+    locate(x[0], E.T0, E.inv_dT, E.nT, iT, tT);
+    locate(x[1], E.mu0[0], E.inv_dmu[0], E.nmu[0], iB, tB);
+    locate(x[2], E.mu0[1], E.inv_dmu[1], E.nmu[1], iS, tS);
+    locate(x[3], E.mu0[2], E.inv_dmu[2], E.nmu[2], iQ, tQ);
+    const int n3 = E.nmu[2], n23 = E.nmu[1] * E.nmu[2], n123 = E.nmu[0] * n23;
+    for (int f = 0; f < 4; ++f) {
+        sn[f] = 0.0;
+        for (int k = 0; k < 4; ++k) J[f][k] = 0.0;
+    }
+    double pv = 0.0;
+    for (int bT = 0; bT < 2; ++bT)
+        for (int bB = 0; bB < 2; ++bB) {
+            double wT = bT ? tT : 1.0 - tT, wB = bB ? tB : 1.0 - tB;
+            double dT = bT ? E.inv_dT : -E.inv_dT, dB = bB ? E.inv_dmu[0] : -E.inv_dmu[0];
+            size_t base = (size_t)(iT + bT) * n123 + (size_t)(iB + bB) * n23 + (size_t)iS * n3 + iQ;
+            const double2 *c00 = reinterpret_cast<const double2 *>(E.sn + 4 * base);
+            const double2 *c01 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + 1));
+            const double2 *c10 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + n3));
+            const double2 *c11 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + n3 + 1));
+            double v00[4], v01[4], v10[4], v11[4];
+            double2 t;
+            t = __ldg(c00); v00[0] = t.x; v00[1] = t.y; t = __ldg(c00 + 1); v00[2] = t.x; v00[3] = t.y;
+            t = __ldg(c01); v01[0] = t.x; v01[1] = t.y; t = __ldg(c01 + 1); v01[2] = t.x; v01[3] = t.y;
+            t = __ldg(c10); v10[0] = t.x; v10[1] = t.y; t = __ldg(c10 + 1); v10[2] = t.x; v10[3] = t.y;
+            t = __ldg(c11); v11[0] = t.x; v11[1] = t.y; t = __ldg(c11 + 1); v11[2] = t.x; v11[3] = t.y;
+            double wTB = wT * wB;
+            for (int f = 0; f < 4; ++f) {
+                double a0 = v00[f] + tQ * (v01[f] - v00[f]);  // mu_S lower face
+                double a1 = v10[f] + tQ * (v11[f] - v10[f]);  // mu_S upper face
+                double val = a0 + tS * (a1 - a0);
+                double dS = (a1 - a0) * E.inv_dmu[1];
+                double dQ = ((v01[f] - v00[f]) + tS * ((v11[f] - v10[f]) - (v01[f] - v00[f]))) * E.inv_dmu[2];
+                sn[f] = fma(wTB, val, sn[f]);
+                J[f][0] = fma(dT * wB, val, J[f][0]);
+                J[f][1] = fma(wT * dB, val, J[f][1]);
+                J[f][2] = fma(wTB, dS, J[f][2]);
+                J[f][3] = fma(wTB, dQ, J[f][3]);
+            }
+            if (p) {
+                double p00 = __ldg(E.p + base), p01 = __ldg(E.p + base + 1), p10 = __ldg(E.p + base + n3),
+                       p11 = __ldg(E.p + base + n3 + 1);
+                double a0 = p00 + tQ * (p01 - p00), a1 = p10 + tQ * (p11 - p10);
+                pv = fma(wTB, a0 + tS * (a1 - a0), pv);
+            }
+        }
+    if (p) *p = pv;
+}
+
+// Gaussian elimination with partial pivoting on an m x m system (m <= 4)
+__device__ bool solve_small(int m, double A[4][4], double b[4])
+{
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        double best = fabs(A[c][c]);
+        for (int r = c + 1; r < m; ++r)
+            if (fabs(A[r][c]) > best) {
+                best = fabs(A[r][c]);
+                piv = r;
+            }
+        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (piv != c) {
+            for (int k = 0; k < 4; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        double inv = 1.0 / A[c][c];
+        for (int r = c + 1; r < m; ++r) {
+            double f = A[r][c] * inv;
+            for (int k = c; k < m; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
+            b[r] = fma(-f, b[c], b[r]);
+        }
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < m; ++k) acc = fma(-A[r][k], b[k], acc);
+        b[r] = acc / A[r][r];
+    }
+    return true;
+}
+
+__device__ __forceinline__ void clamp4(const EosDev &E, double *x)
+{
+    x[0] = fmin(fmax(x[0], E.T0), E.Tmax);
+    for (int q = 0; q < 3; ++q) x[1 + q] = fmin(fmax(x[1 + q], E.mu0[q]), E.mumax[q]);
+}
+
+__device__ double resid(const EosDev &E, const double *x, double s, const double *n, double r[4], double J[4][4])
+{
+    double sn[4];
+    tab_eval(E, x, sn, J, nullptr);
+    double inv_s = 1.0 / s;
+    double tgt[4] = {s, n[0], n[1], n[2]};
+    double m = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        r[k] = (sn[k] - tgt[k]) * inv_s;
+        m = isfinite(r[k]) ? fmax(m, fabs(r[k])) : __longlong_as_double(0x7FF0000000000000LL);
+        for (int j = 0; j < 4; ++j) J[k][j] *= inv_s;
+    }
+    return m;
+}
+
+__device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x)
+{
+    double r[4], J[4][4];
+    double rn = resid(E, x, s, n, r, J);
+    for (int it = 0; it < E.maxit; ++it) {
+        double A[4][4], d[4];
+        for (int i = 0; i < 4; ++i) {
+            d[i] = -r[i];
+            for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
+        }
+        if (rn <= E.tol) {
+            if (solve_small(4, A, d)) {  // one polishing step if it does not increase the residual
+                double xn[4], rr[4], Jn[4][4];
+                for (int k = 0; k < 4; ++k) xn[k] = x[k] + d[k];
+                clamp4(E, xn);
+                if (resid(E, xn, s, n, rr, Jn) <= rn)
+                    for (int k = 0; k < 4; ++k) x[k] = xn[k];
+            }
+            return true;
+        }
+        if (!solve_small(4, A, d)) return false;
+        double lam = 1.0, xn[4], rr[4], Jn[4][4], rnn = 0.0;
+        for (int ls = 0; ls <= 8; ++ls) {
+            for (int k = 0; k < 4; ++k) xn[k] = fma(lam, d[k], x[k]);
+            clamp4(E, xn);
+            rnn = resid(E, xn, s, n, rr, Jn);
+            if (rnn < rn) break;
+            lam *= 0.5;
+        }
+        for (int k = 0; k < 4; ++k) {
+            x[k] = xn[k];
+            r[k] = rr[k];
+            for (int j = 0; j < 4; ++j) J[k][j] = Jn[k][j];
+        }
+        rn = rnn;
+    }
+    return rn <= E.tol;
+}
+
+struct EosOut {
+    double T, mu[3], p, e, ps, pn[3], cs2;
+    uint32_t st;
+};
+
+__device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const double *n)
+{
+    EosOut o;
+    o.T = 0.0;
+    for (int q = 0; q < 3; ++q) o.mu[q] = 0.0, o.pn[q] = 0.0;
+    o.p = o.e = o.ps = o.cs2 = 0.0;
+    double x[4];
+    o.st = an_invert(E, s, n, x[0], x + 1);
+    if (o.st) return o;
+    bool use_table = false;
+    if (E.has_table) {
+        bool inside = x[0] >= E.T0 && x[0] <= E.Tmax;
+        for (int q = 0; q < 3; ++q) inside = inside && x[1 + q] >= E.mu0[q] && x[1 + q] <= E.mumax[q];
+        if (inside) {
+            double xt[4] = {x[0], x[1], x[2], x[3]};
+            if (tab_newton(E, s, n, xt)) {
+                for (int k = 0; k < 4; ++k) x[k] = xt[k];
+                use_table = true;
+            } else {
+                o.st |= PST_FALLBACK;
+            }
+        } else {
+            o.st |= PST_OUT_OF_TABLE;
+        }
+    }
+    double p, H[4][4], sn[4];
+    if (use_table) tab_eval(E, x, sn, H, &p);
+    else an_eval(E, x[0], x + 1, p, sn, H);
+    double e = x[0] * s + x[1] * n[0] + x[2] * n[1] + x[3] * n[2] - p;
+    // (p_s, p_n) = H^-T (s, n) over the directions the EoS couples to
+    int act[4], m = 0;
+    for (int k = 0; k < 4; ++k)
+        if (k == 0 || use_table || E.chi[k - 1] > 0.0) act[m++] = k;
+    double A[4][4], z[4];
+    double tgt[4] = {s, n[0], n[1], n[2]};
+    for (int i = 0; i < 4; ++i) {
+        z[i] = i < m ? tgt[act[i]] : 0.0;
+        for (int j = 0; j < 4; ++j) A[i][j] = (i < m && j < m) ? H[act[j]][act[i]] : 0.0;
+    }
+    if (!solve_small(m, A, z)) {
+        o.st |= PST_NOCONV;
+        return o;
+    }
+    double zz[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < m; ++i) zz[act[i]] = z[i];
+    double cs2 = (s * zz[0] + n[0] * zz[1] + n[1] * zz[2] + n[2] * zz[3]) / (e + p);
+    if (cs2 > cs2_cap) {
+        double f = cs2_cap / cs2;
+        for (int k = 0; k < 4; ++k) zz[k] *= f;
+        cs2 = cs2_cap;
+        o.st |= PST_CS2_CAPPED;
+    }
+    o.T = x[0];
+    for (int q = 0; q < 3; ++q) o.mu[q] = x[1 + q], o.pn[q] = zz[1 + q];
+    o.p = p;
+    o.e = e;
+    o.ps = zz[0];
+    o.cs2 = cs2;
+    return o;
+}
+
+// EoS pass, 2+1D: rest-frame densities, inversion, and the per-particle inputs of the
+// gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{tau i},
+// and u^j / sigma*; plus the longitudinal work rate (p + Pi + tau^2 pi^{eta eta}) / sigma*
+__global__ void __launch_bounds__(128) k_eos2(EvView v, int stage, const double *__restrict__ y,
+                                              double *__restrict__ dens, double *__restrict__ eos,
+                                              double *__restrict__ gin, uint32_t *__restrict__ status,
+                                              double *__restrict__ wpart)
+{
+    __shared__ double red[4];
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = v.n;
+    double wcontrib = 0.0;
+    if (a < n) {
+        double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+        double sqrtg = v.milne ? tau : 1.0;
+        double sig_star = dens[a];
+        double u0 = dens[5 * (size_t)n + a];
+        double vol = u0 * sqrtg;
+        double s = dens[(size_t)n + a] / vol;
+        double nq[3] = {dens[2 * (size_t)n + a] / vol, dens[3 * (size_t)n + a] / vol, dens[4 * (size_t)n + a] / vol};
+        dens[(size_t)n + a] = s;
+        for (int q = 0; q < 3; ++q) dens[(2 + q) * (size_t)n + a] = nq[q];
+        EosOut o = eos_invert(v.eos, v.tr.cs2_cap, s, nq);
+        status[a] = o.st;
+        warp_or(&v.sc->status_or, o.st);
+        eos[a] = o.T;
+        for (int q = 0; q < 3; ++q) eos[(1 + q) * (size_t)n + a] = o.mu[q];
+        eos[4 * (size_t)n + a] = o.p;
+        eos[5 * (size_t)n + a] = o.e;
+        eos[6 * (size_t)n + a] = o.ps;
+        for (int q = 0; q < 3; ++q) eos[(7 + q) * (size_t)n + a] = o.pn[q];
+        eos[10 * (size_t)n + a] = o.cs2;
+        double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
+        double vx = ux / u0, vy = uy / u0;
+        double sigma = sig_star / vol;
+        double Pi = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
+        if (v.tr.viscous) {
+            Pi = sigma * y[5 * (size_t)n + a];
+            pxx = sigma * y[6 * (size_t)n + a];
+            pxy = sigma * y[7 * (size_t)n + a];
+            pyy = sigma * y[8 * (size_t)n + a];
+        }
+        double ptx = vx * pxx + vy * pxy;  // pi^{tau x}
+        double pty = vx * pxy + vy * pyy;  // pi^{tau y}
+        double inv2 = 1.0 / (sig_star * sig_star);
+        double P = o.p + Pi;
+        gin[a] = (P + pxx - vx * ptx) * inv2;                     // X^{xx}
+        gin[(size_t)n + a] = (pxy - vx * pty) * inv2;             // X^{xy}  (j = x, i = y)
+        gin[2 * (size_t)n + a] = (pxy - vy * ptx) * inv2;         // X^{yx}  (j = y, i = x)
+        gin[3 * (size_t)n + a] = (P + pyy - vy * pty) * inv2;     // X^{yy}
+        gin[4 * (size_t)n + a] = ux / sig_star;
+        gin[5 * (size_t)n + a] = uy / sig_star;
+        if (v.milne) {
+            double ptt = vx * ptx + vy * pty;
+            double t2pee = ptt - pxx - pyy;  // tau^2 pi^{eta eta} from tracelessness
+            wcontrib = (P + t2pee) / sig_star;
+        }
+    }
+    // deterministic block sum of the work rate
+    for (int o = 16; o > 0; o >>= 1) wcontrib += __shfl_xor_sync(0xFFFFFFFFu, wcontrib, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wcontrib;
+    __syncthreads();
+    if (threadIdx.x == 0) wpart[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                    cudaStream_t st)
+{
+    k_density2<<<nblk(v.n, 128), 128, 0, st>>>(v, y, Nq, cb.start, cb.cnt, dens, nnb);
+}
+
+void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
+                uint32_t *status, double *wpart, cudaStream_t st)
+{
+    k_eos2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart);
+}
+
+int eom_block_count(int n) { return nblk(n, 128); }
+
+}  // namespace sphg

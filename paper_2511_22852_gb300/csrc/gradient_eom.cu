@@ -1,0 +1,337 @@
+// gradient_eom.cu -- SPH gradients (row a5), equations of motion with minimal
+// Israel-Stewart sources (row a6), Heun update (row a7) and the reductions of
+// the conservation totals (row a8).
+//
+// Gradient pass (eqs. sphderivativerel, generalsphderivative with the sigma
+// exponents of the n-form corrected so that n = 0 reproduces eq.
+// sphderivativerel): per particle a
+//   d_k u^j  = sum_b (u^j_b / sigma*_b) d_k W_ab                        (n = 0)
+//   F^i      = -sqrt(-g) sum_b sum_j (X^{ji}_a/sigma*_a^2 + X^{ji}_b/sigma*_b^2) d_j W_ab   (n = -1)
+// where X^{ji} = T^{ji} - v^j T^{0i} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{0i}
+// (2+1D), so that F^i is the rate of the lab momentum per particle
+// P^i = sqrt(-g) T^{0i} / sigma*.  The a-part of the n = -1 sum factorises:
+// X_a sum_b dW_ab, so each pair costs 8 fused multiply-adds.
+//
+// Equations of motion, 2+1D Milne (boost invariant) or Cartesian: every rate is
+// affine in the unknown acceleration a^i = du^i/dx^0 (entropy production eq.
+// dsdnrewr, bulk eq. min_bul_rel, shear eq. min_she_rel, continuity
+// D sigma = -sigma theta), so dP^i/dx^0 = M^i_j a^j + c^i is assembled with
+// affine arithmetic (exact coefficients, no differencing) and M a = F - c is
+// solved per particle by Cramer's rule -- the D x D system of eq. unugeneral.
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+namespace {
+
+__global__ void __launch_bounds__(128) k_gradient2(EvView v, int stage, const double *__restrict__ y,
+                                                   const double *__restrict__ gin, const uint32_t *__restrict__ start,
+                                                   const uint32_t *__restrict__ cnt, double *__restrict__ gout)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= v.n) return;
+    const int n = v.n;
+    const double *X = y, *Y = y + n;
+    const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
+    const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
+    double xa = X[a], ya = Y[a];
+    double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+    int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+    int lim = 1 << v.B;
+    double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
+    double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
+    for (int oy = -1; oy <= 1; ++oy) {
+        int ny = cy + oy;
+        if (ny < 0 || ny >= lim) continue;
+        for (int ox = -1; ox <= 1; ++ox) {
+            int nx = cx + ox;
+            if (nx < 0 || nx >= lim) continue;
+            uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+            uint32_t b0 = start[k], b1 = b0 + cnt[k];
+            for (uint32_t b = b0; b < b1; ++b) {
+                double dx = xa - X[b], dy = ya - Y[b];
+                double r2 = dist2_2d(dx, dy);
+                if (r2 < v.supp2 && r2 > 0.0) {
+                    double ir = rsqrt_nr(r2);
+                    double q = r2 * ir * v.inv_h;
+                    double fac = kernel_dw(q) * ir;  // (dW/dr)/r without sigma_d/h
+                    double gx = fac * dx, gy = fac * dy;
+                    Gx += gx;
+                    Gy += gy;
+                    Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));
+                    Hy = fma(Xxy[b], gx, fma(Xyy[b], gy, Hy));
+                    double ubx = Ux[b], uby = Uy[b];
+                    dxux = fma(ubx, gx, dxux);
+                    dxuy = fma(uby, gx, dxuy);
+                    dyux = fma(ubx, gy, dyux);
+                    dyuy = fma(uby, gy, dyuy);
+                }
+            }
+        }
+    }
+    double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+    double sqrtg = v.milne ? tau : 1.0;
+    double c = v.sigma_d * v.inv_h;
+    gout[a] = c * dxux;
+    gout[(size_t)n + a] = c * dxuy;
+    gout[2 * (size_t)n + a] = c * dyux;
+    gout[3 * (size_t)n + a] = c * dyuy;
+    double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
+    double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
+    gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
+    gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+}
+
+__global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, const double *__restrict__ ys,
+                                              const double *__restrict__ dens, const double *__restrict__ eos,
+                                              const double *__restrict__ gout, double *__restrict__ yout,
+                                              double *__restrict__ rates, uint32_t *__restrict__ status)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= v.n) return;
+    const size_t n = (size_t)v.n;
+    double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+    double hub = v.milne ? 1.0 / tau : 0.0;      // Gamma^eta_{eta tau}
+    double sqrtg = v.milne ? tau : 1.0;
+    double ux = ys[2 * n + a], uy = ys[3 * n + a];
+    double sig_star = dens[a], s = dens[n + a], nq0 = dens[2 * n + a], nq1 = dens[3 * n + a], nq2 = dens[4 * n + a];
+    double g = dens[5 * n + a];
+    double T = eos[a], mu0 = eos[n + a], mu1 = eos[2 * n + a], mu2 = eos[3 * n + a];
+    double p = eos[4 * n + a], e = eos[5 * n + a], ps = eos[6 * n + a];
+    double pn0 = eos[7 * n + a], pn1 = eos[8 * n + a], pn2 = eos[9 * n + a];
+    double dxux = gout[a], dxuy = gout[n + a], dyux = gout[2 * n + a], dyuy = gout[3 * n + a];
+    double Fx = gout[4 * n + a], Fy = gout[5 * n + a];
+    double sigma = sig_star / (g * sqrtg);
+    double ig = 1.0 / g, isg = 1.0 / sigma;
+    double vx = ux * ig, vy = uy * ig;
+    const bool visc = v.tr.viscous != 0;
+    double Bv = 0.0, Pvxx = 0.0, Pvxy = 0.0, Pvyy = 0.0;
+    if (visc) {
+        Bv = ys[5 * n + a];
+        Pvxx = ys[6 * n + a];
+        Pvxy = ys[7 * n + a];
+        Pvyy = ys[8 * n + a];
+    }
+    double Pi = sigma * Bv, pxx = sigma * Pvxx, pxy = sigma * Pvxy, pyy = sigma * Pvyy;
+    const double dt = v.dtau;
+    const int nv = v.nv;
+    if (status[a] & (PST_NOCONV | PST_NONFINITE)) {
+        // no EoS solution: the particle is frozen for this stage (ballistic motion only)
+        for (int k = 0; k < nv; ++k) {
+            double fk = k == 0 ? vx : (k == 1 ? vy : 0.0);
+            if (mode == 0) yout[k * n + a] = ys[k * n + a] + dt * fk;
+            else if (mode == 1) yout[k * n + a] = 0.5 * ((yout[k * n + a] + ys[k * n + a]) + dt * fk);
+            else rates[k * n + a] = fk;
+        }
+        return;
+    }
+
+    const Aff ax = {0.0, 1.0, 0.0}, ay = {0.0, 0.0, 1.0};
+    Aff dg = vx * ax + vy * ay;                                  // d u^0 / dx^0
+    double dgx = (ux * dxux + uy * dxuy) * ig;                   // d_x u^0
+    double dgy = (ux * dyux + uy * dyuy) * ig;                   // d_y u^0
+    Aff th = dg + (dxux + dyuy + g * hub - (vx * dgx + vy * dgy));  // theta = nabla_mu u^mu
+    Aff dsg = (-sigma * ig) * th;                                // d sigma / dx^0
+
+    Aff dS = aff(0.0), dBv = aff(0.0), dPxx = aff(0.0), dPxy = aff(0.0), dPyy = aff(0.0);
+    if (visc) {
+        const double third = 1.0 / 3.0;
+        // sigma^{ij} = -(d_i u^j + d_j u^i)/2 - u^0 (u^i a^j + u^j a^i)/2 + (delta^{ij} + u^i u^j) theta/3
+        Aff sxx = aff(-dxux) - (g * ux) * ax + (third * (1.0 + ux * ux)) * th;
+        Aff sxy = aff(-0.5 * (dxuy + dyux)) - (0.5 * g) * (ux * ay + uy * ax) + (third * ux * uy) * th;
+        Aff syy = aff(-dyuy) - (g * uy) * ay + (third * (1.0 + uy * uy)) * th;
+        Aff see = aff(-g * hub) + third * th;                    // tau^2 sigma^{eta eta} (z z if Cartesian)
+        Aff svx = vx * sxx + vy * sxy, svy = vx * sxy + vy * syy;
+        Aff vsv = vx * svx + vy * svy;
+        double pvx = vx * pxx + vy * pxy, pvy = vx * pxy + vy * pyy;  // pi^{0i}
+        double vpv = vx * pvx + vy * pvy;                             // pi^{00}
+        double pee = vpv - pxx - pyy;                                 // tau^2 pi^{eta eta}
+        Aff pisig = vpv * vsv - 2.0 * (pvx * svx + pvy * svy) + pxx * sxx + 2.0 * pxy * sxy + pyy * syy + pee * see;
+        double eta = v.tr.eta_over_s * s;
+        double dTg = T * kHbarc - v.tr.zeta_T_GeV;
+        double zeta = v.tr.zeta_peak * exp(-dTg * dTg / (2.0 * v.tr.zeta_w_GeV * v.tr.zeta_w_GeV)) * s;
+        double taupi = v.tr.tau_pi_coef * eta / (e + p);
+        double tauPi = v.tr.tau_Pi_ratio * taupi;
+        dS = (ig * isg / T) * (pisig - Pi * th);
+        dBv = (-ig * isg / tauPi) * (zeta * th + Pi);
+        // pi^{j alpha} a_alpha with the lowered four-acceleration (u^0 du^0/dx^0, -u^0 a^i)
+        Aff pax = g * (pvx * dg - (pxx * ax + pxy * ay));
+        Aff pay = g * (pvy * dg - (pxy * ax + pyy * ay));
+        double itp = 1.0 / taupi, f43 = 4.0 / 3.0;
+        Aff dpxx = ig * (itp * (2.0 * eta * sxx - f43 * taupi * pxx * th + (-pxx)) - 2.0 * ux * pax);
+        Aff dpxy = ig * (itp * (2.0 * eta * sxy - f43 * taupi * pxy * th + (-pxy)) - (ux * pay + uy * pax));
+        Aff dpyy = ig * (itp * (2.0 * eta * syy - f43 * taupi * pyy * th + (-pyy)) - 2.0 * uy * pay);
+        double isg2 = isg * isg;
+        dPxx = isg * dpxx - (pxx * isg2) * dsg;
+        dPxy = isg * dpxy - (pxy * isg2) * dsg;
+        dPyy = isg * dpyy - (pyy * isg2) * dsg;
+    }
+    Aff ds = sigma * dS + (s * isg) * dsg;
+    Aff dPi = sigma * dBv + Bv * dsg;
+    Aff dw = (T + ps) * ds + (((mu0 + pn0) * nq0 + (mu1 + pn1) * nq1 + (mu2 + pn2) * nq2) * isg) * dsg + dPi;
+    double w = e + p + Pi;
+    double ig2 = ig * ig, ig3 = ig2 * ig;
+    double Px0 = ux * Pvxx + uy * Pvxy, Py0 = ux * Pvxy + uy * Pvyy;
+    Aff dPx = (ux * isg) * dw + (w * isg) * ax - (w * ux * isg * isg) * dsg +
+              ig2 * (Pvxx * ax + Pvxy * ay + ux * dPxx + uy * dPxy) - (2.0 * Px0 * ig3) * dg;
+    Aff dPy = (uy * isg) * dw + (w * isg) * ay - (w * uy * isg * isg) * dsg +
+              ig2 * (Pvxy * ax + Pvyy * ay + ux * dPxy + uy * dPyy) - (2.0 * Py0 * ig3) * dg;
+    double r0 = Fx - dPx.c, r1 = Fy - dPy.c;
+    double det = dPx.x * dPy.y - dPx.y * dPy.x;
+    uint32_t st = 0;
+    double acx = 0.0, acy = 0.0;
+    if (isfinite(det) && det != 0.0) {
+        double idet = 1.0 / det;
+        acx = (r0 * dPy.y - dPx.y * r1) * idet;
+        acy = (dPx.x * r1 - dPy.x * r0) * idet;
+    } else {
+        st |= PST_SOLVE_FAIL;
+    }
+    double f[9];
+    f[0] = vx;
+    f[1] = vy;
+    f[2] = acx;
+    f[3] = acy;
+    f[4] = at(dS, acx, acy);
+    f[5] = at(dBv, acx, acy);
+    f[6] = at(dPxx, acx, acy);
+    f[7] = at(dPxy, acx, acy);
+    f[8] = at(dPyy, acx, acy);
+    bool fin = true;
+    for (int k = 0; k < 9; ++k) fin = fin && isfinite(f[k]);
+    if (!fin) st |= PST_NONFINITE;
+    if (st) {
+        status[a] |= st;
+        atomicOr(&v.sc->status_or, st);
+    }
+    if (mode == 0) {
+        for (int k = 0; k < nv; ++k) yout[k * n + a] = ys[k * n + a] + dt * f[k];
+    } else if (mode == 1) {
+        for (int k = 0; k < nv; ++k) yout[k * n + a] = 0.5 * ((yout[k * n + a] + ys[k * n + a]) + dt * f[k]);
+    } else {
+        for (int k = 0; k < nv; ++k) rates[k * n + a] = f[k];
+    }
+}
+
+// stage work rate: fixed-order tree sum of the per-block partials; stage 2
+// closes the step (Heun quadrature of the work integral, tau += dtau)
+__global__ void __launch_bounds__(256) k_work_finish(EvView v, int stage, const double *__restrict__ wpart, int nblk)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 256) acc += wpart[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+        (void)tau;
+        v.sc->wr[stage - 1] = v.milne ? sh[0] : 0.0;
+        if (stage == 2) {
+            v.sc->work += 0.5 * v.dtau * (v.sc->wr[0] + v.sc->wr[1]);
+            v.sc->tau = v.sc->tau + v.dtau;
+            v.sc->steps += 1;
+        }
+    }
+}
+
+// per-particle totals contributions in ORIGINAL order: [0] sqrt(-g) T^{00}/sigma*, [1] S
+__global__ void k_totals2(EvView v, const double *__restrict__ y, const int *__restrict__ id,
+                          const double *__restrict__ dens, const double *__restrict__ eos, double *__restrict__ contrib)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= v.n) return;
+    const size_t n = (size_t)v.n;
+    double tau = v.sc->tau;
+    double sqrtg = v.milne ? tau : 1.0;
+    double sig_star = dens[a], g = dens[5 * n + a];
+    double sigma = sig_star / (g * sqrtg);
+    double ux = y[2 * n + a], uy = y[3 * n + a];
+    double vx = ux / g, vy = uy / g;
+    double Pi = 0.0, ptt = 0.0;
+    if (v.tr.viscous) {
+        Pi = sigma * y[5 * n + a];
+        double pxx = sigma * y[6 * n + a], pxy = sigma * y[7 * n + a], pyy = sigma * y[8 * n + a];
+        ptt = vx * (vx * pxx + vy * pxy) + vy * (vx * pxy + vy * pyy);
+    }
+    double p = eos[4 * n + a], e = eos[5 * n + a];
+    double T00 = (e + p + Pi) * g * g - (p + Pi) + ptt;
+    int o = id[a];
+    contrib[o] = sqrtg * T00 / sig_star;
+    contrib[n + o] = y[4 * n + a];
+}
+
+// fixed-order sums of nfield rows of n values: block partials over fixed chunks,
+// then one block sums the partials in order
+__global__ void __launch_bounds__(256) k_sum_rows(const double *__restrict__ vals, int n, int nfield,
+                                                  double *__restrict__ part, int chunk)
+{
+    __shared__ double sh[256];
+    int f = blockIdx.y;
+    int b = blockIdx.x;
+    double acc = 0.0;
+    int lo = b * chunk, hi = min(lo + chunk, n);
+    for (int i = lo + threadIdx.x; i < hi; i += 256) acc += vals[(size_t)f * n + i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)f * gridDim.x + b] = sh[0];
+}
+
+__global__ void k_sum_final(const double *__restrict__ part, int nb, int nfield, double *out)
+{
+    int f = threadIdx.x;
+    if (f >= nfield) return;
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += part[(size_t)f * nb + b];
+    out[f] = acc;
+}
+
+inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+void launch_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
+                     cudaStream_t st)
+{
+    k_gradient2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, y, gin, cb.start, cb.cnt, gout);
+}
+
+void launch_eom(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,
+                const double *gout, double *yout, double *rates, uint32_t *status, cudaStream_t st)
+{
+    k_eom2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, mode, ys, dens, eos, gout, yout, rates, status);
+}
+
+void launch_work_finish(const EvView &v, int stage, const double *wpart, int nb, cudaStream_t st)
+{
+    k_work_finish<<<1, 256, 0, st>>>(v, stage, wpart, nb);
+}
+
+void launch_totals(const EvView &v, const double *y, const double *Nq, const int *id, const double *dens,
+                   const double *eos, double *contrib, cudaStream_t st)
+{
+    (void)Nq;
+    k_totals2<<<nblk(v.n, 256), 256, 0, st>>>(v, y, id, dens, eos, contrib);
+}
+
+// out[f] = fixed-order sum of vals[f*n .. f*n + n); scratch after out (needs nfield*256 doubles)
+void launch_sum_fixed(const double *vals, int n, int nfield, double *out, cudaStream_t st)
+{
+    int chunk = 4096;
+    int nb = max(1, min(256, nblk(n, chunk)));
+    chunk = max(1, nblk(n, nb));
+    nb = max(1, nblk(n, chunk));
+    double *part = out + 8;
+    dim3 grid(nb, nfield);
+    k_sum_rows<<<grid, 256, 0, st>>>(vals, n, nfield, part, chunk);
+    k_sum_final<<<1, 32, 0, st>>>(part, nb, nfield, out);
+}
+
+}  // namespace sphg

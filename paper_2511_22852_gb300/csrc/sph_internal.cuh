@@ -1,0 +1,190 @@
+// sph_internal.cuh -- device-side data layout and helpers of the GB300 SPH step.
+//
+// Layout in HBM (structure of arrays, FP64, particles in Morton-sorted cell
+// order, ping-pong buffers for the per-stage permutation):
+//   y[nv][n]      state: x^i, u^i, S, Pi/sigma, pi^{ij}/sigma (xx, xy, yy)
+//   Nq[3][n]      charges per particle (constant without diffusion)
+//   id[n]         original particle index of each sorted slot
+//   dens[6][n]    sigma*, s, n_B, n_S, n_Q, u^0                 (density pass)
+//   eos[11][n]    T, mu_B, mu_S, mu_Q, p, e, p_s, p_nB, p_nS, p_nQ, c_s^2
+//   gin[6][n]     X^{ji}/sigma*^2 (xx, xy, yx, yy), u^x/sigma*, u^y/sigma*
+//   gout[6][n]    d_x u^x, d_x u^y, d_y u^x, d_y u^y, F^x, F^y  (gradient pass)
+// The bucket table of the cell list is indexed by the Morton key of the cell
+// coordinates (B bits per dimension, fixed at event creation).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sphg {
+
+constexpr double kHbarc = 0.1973269804;  // GeV fm
+constexpr double kPi = 3.14159265358979323846;
+
+// per-particle status bits (same values as SPH_PST_* in the public header)
+constexpr uint32_t PST_FALLBACK = 1u, PST_OUT_OF_TABLE = 2u, PST_NOCONV = 4u, PST_NONFINITE = 8u,
+                   PST_CS2_CAPPED = 16u, PST_SOLVE_FAIL = 32u;
+// event-level device error bits
+constexpr uint32_t ERR_CELL_OVERFLOW = 1u;
+
+constexpr int kNDens = 6, kNEos = 11, kNGin = 6, kNGout = 6;
+
+// scalars that change while stepping live in device memory, so a captured
+// CUDA graph can be replayed without re-instantiation
+struct DevScalars {
+    double tau;
+    double work;       // accumulated longitudinal work integral
+    double wr[2];      // work rate of stage 1 and stage 2 of the current step
+    long long xmin_enc[3];
+    unsigned int status_or;
+    unsigned int err_flags;
+    long long steps;
+    unsigned long long pairs;  // accepted neighbour pairs (self included), summed over stages
+};
+
+struct EosDev {
+    // closed form
+    double a0, a1, Tc_GeV, w_GeV, chi[3];
+    // table: sn[node] = {s, nB, nS, nQ}, p[node]; node = ((iT*n1 + iB)*n2 + iS)*n3 + iQ
+    int has_table, nT, nmu[3], maxit;
+    double T0, dT, mu0[3], dmu[3], inv_dT, inv_dmu[3], Tmax, mumax[3];
+    const double *sn;
+    const double *p;
+    double tol;
+};
+
+struct TransportDev {
+    int viscous;
+    double eta_over_s, zeta_peak, zeta_T_GeV, zeta_w_GeV, tau_pi_coef, tau_Pi_ratio, cs2_cap;
+};
+
+// everything a kernel of one event needs, passed by value
+struct EvView {
+    int n, dim, milne, nv, B;
+    double h, inv_h, supp2, inv_cell, sigma_d, dtau;
+    DevScalars *sc;
+    EosDev eos;
+    TransportDev tr;
+};
+
+// ---------------------------------------------------------------------------
+// order-preserving map of doubles to signed 64-bit integers (for atomicMin)
+__device__ __forceinline__ long long enc_double(double x)
+{
+    long long i = __double_as_longlong(x);
+    return i >= 0 ? i : (i ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__host__ __device__ __forceinline__ double dec_double(long long i)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(i >= 0 ? i : (i ^ 0x7FFFFFFFFFFFFFFFLL));
+#else
+    long long j = i >= 0 ? i : (i ^ 0x7FFFFFFFFFFFFFFFLL);
+    double d;
+    memcpy(&d, &j, 8);
+    return d;
+#endif
+}
+
+// Morton key: bit (2b + d) of the key is bit b of coordinate d
+__host__ __device__ __forceinline__ uint32_t spread2(uint32_t v)
+{
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton2(uint32_t cx, uint32_t cy) { return spread2(cx) | (spread2(cy) << 1); }
+
+// cell coordinate floor((x - xmin) * (1/(2h))): a single rounded subtraction and
+// product, the same two operations on every platform
+__device__ __forceinline__ int cell_coord(double x, double xmin, double inv_cell)
+{
+    return (int)floor(__dmul_rn(__dsub_rn(x, xmin), inv_cell));
+}
+
+// r^2 with each product rounded separately (no fused multiply-add), so the
+// neighbour decision r^2 < (2h)^2 is bit-for-bit reproducible
+__device__ __forceinline__ double dist2_2d(double dx, double dy) { return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)); }
+
+// 1/sqrt(x) for x > 0: single-precision seed, then two Newton-Raphson steps
+// y <- y (3 - x y^2) / 2 in double precision (quadratic convergence: ~1e-7 ->
+// ~1e-14 -> below one ulp of rounding noise)
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    double xh = 0.5 * x;
+    y = y * fma(-xh * y, y, 1.5);
+    y = y * fma(-xh * y, y, 1.5);
+    return y;
+}
+
+// cubic spline kernel (Sec. "Kernel function") as functions of q = r/h:
+// W = sigma_d w(q), dW/dr = sigma_d/h w'(q)
+__device__ __forceinline__ double kernel_w(double q)
+{
+    if (q <= 1.0) return fma(q * q, fma(0.75, q, -1.5), 1.0);
+    double t = 2.0 - q;
+    return 0.25 * t * t * t;
+}
+__device__ __forceinline__ double kernel_dw(double q)
+{
+    if (q <= 1.0) return q * fma(2.25, q, -3.0);
+    double t = 2.0 - q;
+    return -0.75 * t * t;
+}
+
+// affine form c + ax*a_x + ay*a_y in the unknown acceleration (a_x, a_y)
+struct Aff {
+    double c, x, y;
+};
+__device__ __forceinline__ Aff aff(double c) { return {c, 0.0, 0.0}; }
+__device__ __forceinline__ Aff operator+(Aff a, Aff b) { return {a.c + b.c, a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ Aff operator-(Aff a, Aff b) { return {a.c - b.c, a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ Aff operator-(Aff a) { return {-a.c, -a.x, -a.y}; }
+__device__ __forceinline__ Aff operator*(double s, Aff a) { return {s * a.c, s * a.x, s * a.y}; }
+__device__ __forceinline__ Aff operator*(Aff a, double s) { return {s * a.c, s * a.x, s * a.y}; }
+__device__ __forceinline__ Aff operator+(Aff a, double s) { return {a.c + s, a.x, a.y}; }
+__device__ __forceinline__ double at(Aff a, double ax, double ay) { return fma(a.x, ax, fma(a.y, ay, a.c)); }
+
+// warp-aggregated OR into a global word
+__device__ __forceinline__ void warp_or(unsigned int *dst, unsigned int v)
+{
+    unsigned int m = __reduce_or_sync(__activemask(), v);
+    if (m && (threadIdx.x & 31) == (__ffs(__activemask()) - 1)) atomicOr(dst, m);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (implemented in cells.cu, density_eos.cu, gradient_eom.cu)
+struct CellBufs {
+    uint32_t *key, *cnt, *start, *cursor, *tmp, *perm;
+    int nb;  // number of buckets = 1 << (dim * B)
+};
+
+void launch_bbox(const EvView &v, const double *y, cudaStream_t st);
+void launch_cells(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st);
+void launch_permute(const EvView &v, const uint32_t *perm, const double *const *src, double *const *dst,
+                    const int *nrows, int ngroups, const int *id_in, int *id_out, cudaStream_t st);
+void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                    cudaStream_t st);
+void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
+                uint32_t *status, double *wpart, cudaStream_t st);
+void launch_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
+                     cudaStream_t st);
+// mode 0: y1 = y + dt f(y); mode 1: y0 = ((y0 + y1) + dt f(y1)) / 2 in place; mode 2: rates only
+void launch_eom(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,
+                const double *gout, double *yout, double *rates, uint32_t *status, cudaStream_t st);
+void launch_work_finish(const EvView &v, int stage, const double *wpart, int nblk, cudaStream_t st);
+void launch_neighbors_list(const EvView &v, const double *y, const int *id, CellBufs cb, const long long *offs,
+                           int *pa, int *pb, cudaStream_t st);
+void launch_scan_counts(const int *cnt, long long *offs, int n, cudaStream_t st);
+void launch_totals(const EvView &v, const double *y, const double *Nq, const int *id, const double *dens,
+                   const double *eos, double *contrib, cudaStream_t st);
+void launch_sum_fixed(const double *vals, int n, int nfield, double *out, cudaStream_t st);
+void launch_scatter_orig(const double *src, double *dst, const int *id, int n, int nrows, cudaStream_t st);
+void launch_scatter_orig_u32(const uint32_t *src, uint32_t *dst, const int *id, int n, cudaStream_t st);
+void launch_cell_coords(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
+int eom_block_count(int n);
+
+}  // namespace sphg

@@ -1,0 +1,292 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: bit-exact for cell coordinates, neighbour counts and neighbour sets;
+1e-11 (normwise: max |gpu - oracle| / max |oracle| per field) after one Heun
+step and for the right-hand side; 1e-8 over a full evolution.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2511_22852_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-11
+TOL_EVOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def Bd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_22852_gb300 import binding, build_lib
+    build_lib.build()
+    return binding
+
+
+def relerr(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    den = np.max(np.abs(b)) if b.size else 1.0
+    if den == 0.0:
+        return float(np.max(np.abs(a))) if a.size else 0.0
+    return float(np.max(np.abs(a - b)) / den)
+
+
+def state_errors(g, run):
+    st = g.read(("X", "U", "S", "BV", "PV"))
+    y = run.y
+    return {"x": relerr(st["X"], y[0:2]), "u": relerr(st["U"], y[2:4]), "S": relerr(st["S"], y[4]),
+            "Bv": relerr(st["BV"], y[5]), "Pv": relerr(st["PV"], y[6:9])}
+
+
+CASES = {
+    "gubser": lambda: I.gubser_ideal_2p1(),
+    "bsq_small": lambda: I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20),
+    "blob_causal": lambda: I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS),
+    "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_cells_and_neighbours_bit_exact(Bd, case):
+    ev = CASES[case]()
+    g = Bd.GpuEvent(ev, use_graph=False)
+    f = g.read(("CELL", "NNB"))
+    cc, _ = O.cell_coords(ev.x, ev.h)
+    assert np.array_equal(f["CELL"], cc)
+    pa, pb = g.neighbors()
+    oa, ob = O.neighbors(ev.x, ev.h, "cells")
+    assert np.array_equal(pa, oa) and np.array_equal(pb, ob)
+    assert np.array_equal(f["NNB"], np.bincount(oa, minlength=ev.n))
+    g.free()
+
+
+def test_neighbours_random_and_boundary_points(Bd):
+    for n, seed in [(700, 31), (1, 32), (2, 33)]:
+        ev = I.bjorken_lattice_2p1(n_side=3, viscous=False)
+        x = I.random_points(n, 2, 1.7, seed)
+        ev.x, ev.u = x, np.zeros((2, n))
+        ev.S, ev.Nq, ev.Bv, ev.Pv = np.ones(n), np.zeros((3, n)), np.zeros(n), np.zeros((3, n))
+        g = Bd.GpuEvent(ev, use_graph=False)
+        pa, pb = g.neighbors()
+        oa, ob = O.neighbors(x, ev.h, "brute")
+        assert np.array_equal(pa, oa) and np.array_equal(pb, ob)
+        g.free()
+    # particles exactly on cell faces and pairs exactly at r = 2h (dyadic coordinates)
+    h = 0.3125
+    two_h = 2 * h
+    pts = np.array([(0.0, 0.0), (two_h, 0.0), (0.0, two_h), (2 * two_h, two_h), (0.25, 0.375),
+                    (0.25 + two_h, 0.375), (1.0, 1.0), (1.375, 1.5), (1.0, 1.0)]).T.copy()
+    ev = I.bjorken_lattice_2p1(n_side=3, viscous=False, h=h)
+    n = pts.shape[1]
+    ev.x, ev.u = pts, np.zeros((2, n))
+    ev.S, ev.Nq, ev.Bv, ev.Pv = np.ones(n), np.zeros((3, n)), np.zeros(n), np.zeros((3, n))
+    g = Bd.GpuEvent(ev, use_graph=False)
+    pa, pb = g.neighbors()
+    oa, ob = O.neighbors(pts, h, "brute")
+    assert np.array_equal(pa, oa) and np.array_equal(pb, ob)
+    g.free()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_densities_and_eos(Bd, case):
+    ev = CASES[case]()
+    g = Bd.GpuEvent(ev, use_graph=False)
+    f = g.read(("SIGMA_STAR", "S_DENS", "N_DENS", "T", "MU", "P", "E", "STATUS"))
+    run = O.OracleRun.start(ev)
+    aux, st = run.observe()
+    A = O.AUX
+    assert relerr(f["SIGMA_STAR"], aux[A["sigstar"]]) < 1e-13
+    assert relerr(f["S_DENS"], aux[A["s"]]) < 1e-13
+    if np.any(aux[A["nB"]]):
+        assert relerr(f["N_DENS"], aux[A["nB"]:A["nQ"] + 1]) < 1e-13
+    assert relerr(f["T"], aux[A["T"]]) < 1e-12
+    assert relerr(f["P"], aux[A["p"]]) < 1e-12
+    assert relerr(f["E"], aux[A["e"]]) < 1e-12
+    if np.any(aux[A["muB"]]):
+        assert relerr(f["MU"], aux[A["muB"]:A["muQ"] + 1]) < 1e-10
+    # same EoS branch (table / closed form) for every particle
+    branch = Bd.PST_FALLBACK | Bd.PST_OUT_OF_TABLE | Bd.PST_NOCONV
+    assert np.array_equal(f["STATUS"] & branch, st & branch)
+    g.free()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rates(Bd, case):
+    ev = CASES[case]()
+    if case == "bsq_small":  # start from a flowing, viscous state
+        run0 = O.OracleRun.start(ev)
+        run0.step(20)
+        ev.x, ev.u, ev.S = run0.y[0:2].copy(), run0.y[2:4].copy(), run0.y[4].copy()
+        ev.Bv, ev.Pv, ev.tau0 = run0.y[5].copy(), run0.y[6:9].copy(), run0.tau
+    g = Bd.GpuEvent(ev, use_graph=False)
+    r, grad = g.rates()
+    run = O.OracleRun.start(ev)
+    dydt, aux, ograd, st, wr = run.stage()
+    names = ["x", "y", "ux", "uy", "S", "Bv", "Pxx", "Pxy", "Pyy"]
+    for k, nm in enumerate(names):
+        if not np.any(dydt[k]) and not np.any(r[k]):
+            continue
+        assert relerr(r[k], dydt[k]) < TOL_STEP, (nm, relerr(r[k], dydt[k]))
+    assert relerr(grad[0:4], ograd[0:4]) < TOL_STEP
+    assert relerr(grad[4:6], ograd[4:6]) < TOL_STEP
+    g.free()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("graph", [False, True])
+def test_one_heun_step(Bd, case, graph):
+    ev = CASES[case]()
+    g = Bd.GpuEvent(ev, use_graph=graph)
+    g.step(1, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(1)
+    errs = state_errors(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    t = g.totals()
+    assert abs(t["tau"] - run.tau) < 1e-14 and t["steps"] == 1
+    g.free()
+
+
+def test_graph_and_stream_launches_are_bitwise_identical(Bd):
+    ev = CASES["bsq_small"]()
+    a = Bd.GpuEvent(ev, use_graph=True)
+    b = Bd.GpuEvent(ev, use_graph=False)
+    a.step(5)
+    b.step(5)
+    fa, fb = a.read(), b.read()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    a.free()
+    b.free()
+
+
+@pytest.mark.parametrize("case,nsteps", [("gubser", 60), ("bsq_small", 150), ("blob_causal", 100)])
+def test_evolution(Bd, case, nsteps):
+    ev = CASES[case]()
+    g = Bd.GpuEvent(ev, use_graph=True)
+    g.step(nsteps, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(nsteps)
+    errs = state_errors(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    t = g.totals()
+    ot = run.totals()
+    assert abs(t["E"] / ot["E"] - 1) < TOL_EVOL and abs(t["work"] / max(ot["work"], 1e-300) - 1) < TOL_EVOL
+    g.free()
+
+
+def test_full_size_viscous_bsq_one_step(Bd):
+    """The 40k-particle viscous BSQ event in the launch configuration the benchmark times."""
+    ev = I.viscous_bsq_2p1()
+    assert 39000 < ev.n < 41000
+    g = Bd.GpuEvent(ev, use_graph=True)
+    g.step(1, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(1)
+    errs = state_errors(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    f = g.read(("T", "STATUS"))
+    aux, st = run.observe()
+    assert relerr(f["T"], aux[O.AUX["T"]]) < 1e-12
+    g.free()
+
+
+def test_ideal_invariants_bitwise(Bd):
+    ev = I.gubser_ideal_2p1()
+    g = Bd.GpuEvent(ev)
+    t0 = g.totals()
+    g.step(30, sync=True)
+    f = g.read(("S", "NQ"))
+    assert np.array_equal(f["S"], ev.S) and np.array_equal(f["NQ"], ev.Nq)
+    ev2 = I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20)
+    g2 = Bd.GpuEvent(ev2)
+    t0 = g2.totals()
+    g2.step(40, sync=True)
+    t1 = g2.totals()
+    assert np.array_equal(t0["N"], t1["N"])  # charge totals bitwise constant
+    assert t1["S"] > t0["S"]  # second law
+    g.free()
+    g2.free()
+
+
+def test_resume_from_read_state_is_bitwise(Bd):
+    ev = CASES["bsq_small"]()
+    a = Bd.GpuEvent(ev)
+    a.step(10, sync=True)
+    ref = a.read()
+    b = Bd.GpuEvent(ev)
+    b.step(5, sync=True)
+    mid = b.read()
+    tau_mid = b.totals()["tau"]
+    ev2 = CASES["bsq_small"]()
+    ev2.x, ev2.u, ev2.S, ev2.Bv, ev2.Pv, ev2.tau0 = mid["X"], mid["U"], mid["S"], mid["BV"], mid["PV"], tau_mid
+    c = Bd.GpuEvent(ev2)
+    c.step(5, sync=True)
+    out = c.read()
+    for k in ref:
+        assert np.array_equal(out[k], ref[k]), k
+    # write_state into an existing event gives the same
+    b.write_state(x=mid["X"], u=mid["U"], S=mid["S"], Bv=mid["BV"], Pv=mid["PV"])
+    b.step(5, sync=True)
+    for k, v in b.read().items():
+        assert np.array_equal(v, ref[k]), k
+    for e in (a, b, c):
+        e.free()
+
+
+def test_edge_cases_and_errors(Bd):
+    # empty event: every call succeeds
+    ev = I.bjorken_lattice_2p1(n_side=3, viscous=False)
+    ev0 = I.bjorken_lattice_2p1(n_side=3, viscous=False)
+    n = 0
+    ev0.x, ev0.u, ev0.S = np.zeros((2, n)), np.zeros((2, n)), np.zeros(n)
+    ev0.Nq, ev0.Bv, ev0.Pv = np.zeros((3, n)), np.zeros(n), np.zeros((3, n))
+    g0 = Bd.GpuEvent(ev0)
+    g0.step(3, sync=True)
+    assert g0.read()["S"].size == 0
+    assert g0.totals()["steps"] == 0
+    g0.free()
+    # a single particle: its own neighbour only; runs
+    ev1 = I.bjorken_lattice_2p1(n_side=1, viscous=False)
+    g1 = Bd.GpuEvent(ev1)
+    g1.step(2, sync=True)
+    assert g1.read(("NNB",))["NNB"][0] == 1
+    g1.free()
+    # non-finite position
+    bad = I.bjorken_lattice_2p1(n_side=3, viscous=False)
+    bad.x[0, 4] = np.nan
+    with pytest.raises(Bd.SphError) as e:
+        Bd.GpuEvent(bad)
+    assert e.value.code == Bd.SPH_ERR_NONFINITE
+    # invalid arguments
+    g = Bd.GpuEvent(ev)
+    with pytest.raises(Bd.SphError) as e:
+        Bd.sph_step(g.h, -1, 0)
+    assert e.value.code == Bd.SPH_ERR_ARG
+    g.free()
+    bad2 = I.bjorken_lattice_2p1(n_side=3, viscous=False)
+    bad2.dtau = 0.0
+    with pytest.raises(Bd.SphError) as e:
+        Bd.GpuEvent(bad2)
+    assert e.value.code == Bd.SPH_ERR_ARG
+
+
+def test_infeasible_charges_are_flagged(Bd):
+    """The literal +-10 % charge fraction: no EoS solution for hot particles -- flagged, no hang,
+    and fatal when the caller's policy says so."""
+    ev = I.viscous_bsq_2p1(n_target=1500, R=2.2, n_hot=12, charge_frac=0.1)
+    g = Bd.GpuEvent(ev)
+    f = g.read(("STATUS",))
+    run = O.OracleRun.start(ev)
+    aux, st = run.observe()
+    assert np.any(st & O.ST_NOCONV)
+    assert np.array_equal(f["STATUS"] & Bd.PST_NOCONV, st & O.ST_NOCONV)
+    g.free()
+    g = Bd.GpuEvent(ev, fatal_mask=Bd.PST_NOCONV)
+    with pytest.raises(Bd.SphError) as e:
+        g.step(1, sync=True)
+    assert e.value.code == Bd.SPH_ERR_EOS_NOCONV
+    g.free()
