@@ -60,7 +60,10 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        # SPH_ORACLE_LIB: a deliberately mutated build, loaded by the mutation tests to show
+        # that the pins fail when a mistake is planted in the oracle
+        override = os.environ.get("SPH_ORACLE_LIB")
+        _lib = C.CDLL(override if override else build())
         d, i, l, p, u64 = C.c_double, C.c_int, C.c_long, C.c_void_p, C.c_uint64
         P = C.POINTER(Params)
         sig = {

@@ -216,13 +216,16 @@ def disc_lattice(R: float, n_target: int):
 
 
 def viscous_bsq_2p1(n_target=40000, R=7.0, n_hot=200, sigma_hot=0.4, T_max_GeV=0.5,
-                    charge_frac=0.01, tau0=0.6, dtau=0.005, tau_end=8.0, h=0.3,
-                    seed_hot=1, seed_charge=2, with_table=True, table_shape=(64, 32)) -> Event:
+                    charge_frac=0.1, tau0=0.6, dtau=0.005, tau_end=8.0, h=0.3,
+                    seed_hot=1, seed_charge=2, with_table=True, table_shape=(64, 32),
+                    coherent_charges=False) -> Event:
     """Config: viscous 2+1D BSQ single event (eta/s = 0.08, Gaussian zeta/s, synthetic 4D EoS table).
 
     Entropy: sum of ``n_hot`` Gaussian hotspots (sigma 0.4 fm) with centres uniform in the disc,
     scaled so that max s = s(T_max, mu = 0).  Charges n_q = eps_q s with eps_q ~ U(-charge_frac,
-    charge_frac) (the literal +-10 % has no EoS solution for hot particles; see the design notes).
+    charge_frac) per particle and charge.  ``coherent_charges``: eps_q = +charge_frac everywhere
+    (the kernel sums then keep n/s = charge_frac, which has no EoS solution for hot particles
+    at 0.1 -- the failure-path case).
     """
     x, y, dx = disc_lattice(R, n_target)
     u = uniform01(seed_hot, 2 * n_hot)
@@ -235,7 +238,10 @@ def viscous_bsq_2p1(n_target=40000, R=7.0, n_hot=200, sigma_hot=0.4, T_max_GeV=0
     _, s_max, _ = _analytic_p_s_n(BJ_EOS, np.array(T_max_GeV / HBARC), np.zeros(3))
     s = s_raw * (float(s_max) / s_raw.max())
     n = x.size
-    eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
+    if coherent_charges:
+        eps = np.full((3, n), charge_frac)
+    else:
+        eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
     nq = eps * s[None, :]
     vol = tau0 * dx * dx
     table = synthetic_eos_table(BJ_EOS, nT=table_shape[0], nmu=table_shape[1]) if with_table else None

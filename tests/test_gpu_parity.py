@@ -275,15 +275,21 @@ def test_edge_cases_and_errors(Bd):
 
 
 def test_infeasible_charges_are_flagged(Bd):
-    """The literal +-10 % charge fraction: no EoS solution for hot particles -- flagged, no hang,
-    and fatal when the caller's policy says so."""
-    ev = I.viscous_bsq_2p1(n_target=1500, R=2.2, n_hot=12, charge_frac=0.1)
+    """Coherent n_q = 0.1 s: no EoS solution for hot particles -- flagged, no hang, the particles
+    frozen, and fatal when the caller's policy says so."""
+    ev = I.viscous_bsq_2p1(n_target=1500, R=2.2, n_hot=12, charge_frac=0.1, coherent_charges=True)
     g = Bd.GpuEvent(ev)
     f = g.read(("STATUS",))
     run = O.OracleRun.start(ev)
     aux, st = run.observe()
     assert np.any(st & O.ST_NOCONV)
     assert np.array_equal(f["STATUS"] & Bd.PST_NOCONV, st & O.ST_NOCONV)
+    # the step runs; frozen particles keep their state; the result matches the oracle
+    g.step(2, sync=True)
+    run.step(2)
+    s = g.read(("S", "U"))
+    assert np.all(np.isfinite(s["S"])) and np.all(np.isfinite(s["U"]))
+    assert relerr(s["S"], run.y[4]) < TOL_STEP and relerr(s["U"], run.y[2:4]) < TOL_STEP
     g.free()
     g = Bd.GpuEvent(ev, fatal_mask=Bd.PST_NOCONV)
     with pytest.raises(Bd.SphError) as e:

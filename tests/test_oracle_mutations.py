@@ -1,0 +1,104 @@
+"""Each oracle pin must catch a plausible mistake planted in the oracle.
+
+A mutation rewrites one expression of a temporary copy of ``oracle/sph_oracle.c``
+(a dropped term, a wrong sign, a transposed operand, a wrong constant); the copy
+is compiled and the named pin is run against it in a subprocess: the pin must
+fail.  The unmutated oracle passes the same pins (the other test files).
+
+Not listed: the sign of the Christoffel term of the shear equation, which is identically
+zero for the transverse components evolved in boost-invariant 2+1D (an equivalent mutant).
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
+
+# (name, original text, mutated text, pin that must fail)
+MUTATIONS = [
+    ("kernel_norm", "return 10.0 / (7.0 * M_PI * h * h);", "return 10.0 / (7.0 * h * h);",
+     "test_oracle_kernel_neighbors.py::test_kernel_normalisation"),
+    ("kernel_grad_coef", "return sd / h * (-3.0 * q + 2.25 * q * q);", "return sd / h * (-3.0 * q + 2.5 * q * q);",
+     "test_oracle_kernel_neighbors.py::test_kernel_shape_and_gradient"),
+    ("support_inclusive", "if (r2_of(dim, x, n, a, b) < supp2) {", "if (r2_of(dim, x, n, a, b) <= supp2) {",
+     "test_oracle_kernel_neighbors.py::test_boundary_cases"),
+    ("morton_axis_swap", "<< (dim * b + d);", "<< (dim * b + (dim - 1 - d));",
+     "test_oracle_kernel_neighbors.py::test_morton_keys_by_hand"),
+    ("rest_frame_gamma", "double vol = u0 * G.sqrtg;", "double vol = G.sqrtg;",
+     "test_oracle_physics.py::test_gubser_ideal_against_closed_form"),
+    ("eos_drop_fprime", "sn[0] = 4.0 * T * T * T * f + T * T * T * T * fp + T * cm2;",
+     "sn[0] = 4.0 * T * T * T * f + T * cm2;", "test_oracle_eos.py::test_analytic_thermodynamic_identities"),
+    ("eos_jacobian_transposed", "for (int j = 0; j < m; ++j) A[i * m + j] = H[act[j] * 4 + act[i]];",
+     "for (int j = 0; j < m; ++j) A[i * m + j] = H[act[i] * 4 + act[j]];",
+     "test_oracle_eos.py::test_eos_derivatives_by_finite_difference"),
+    ("table_weight_index", "w[k] = bit[k] ? t[k] : 1.0 - t[k];", "w[k] = bit[k] ? 1.0 - t[k] : t[k];",
+     "test_oracle_eos.py::test_table_nodes_and_jacobian"),
+    ("bulk_sign", "R->dBv = -(q->Pi + q->zeta * theta)", "R->dBv = -(q->Pi - q->zeta * theta)",
+     "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
+    ("shear_drop_theta_term", " - 4.0 / 3.0 * q->taupi * q->pi[i][j] * theta) / q->taupi;", ") / q->taupi;",
+     "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
+    ("entropy_drop_bulk", "R->dS = (-q->Pi * theta + pisig)", "R->dS = (pisig)",
+     "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
+    pytest.param("shear_drop_accel_coupling", "double dpi = (rhs - chr - coup) / u0;", "double dpi = (rhs - chr) / u0;",
+                 "test_oracle_physics.py::test_viscous_second_law_and_energy_balance",
+                 marks=pytest.mark.xfail(strict=True, reason="parity unpinned: the projection coupling "
+                                         "u^i pi^{j alpha} a_alpha of the shear equation is second order and "
+                                         "no current pin resolves it (a viscous Gubser pin would)"),
+                 id="shear_drop_accel_coupling"),
+    ("momentum_drop_pi0i", "R->dP[i] = (u[i] / q->sigma) * dw + (w / q->sigma) * a[i] - (w * u[i] / (q->sigma * q->sigma)) * dsig + dpi0;",
+     "R->dP[i] = (u[i] / q->sigma) * dw + (w / q->sigma) * a[i] - (w * u[i] / (q->sigma * q->sigma)) * dsig;",
+     "test_oracle_physics.py::test_viscous_second_law_and_energy_balance"),
+    ("force_sign", "grad[(dim * dim + i) * n + a] = -G.sqrtg * F[i];", "grad[(dim * dim + i) * n + a] = G.sqrtg * F[i];",
+     "test_oracle_physics.py::test_gubser_ideal_against_closed_form"),
+    ("heun_drop_slope", "y[i] = 0.5 * ((y[i] + y1[i]) + dtau * k[i]);", "y[i] = 0.5 * (y[i] + y1[i]);",
+     "test_oracle_physics.py::test_gubser_ideal_against_closed_form"),
+    ("work_missing_sqrtg", "wr += G.sqrtg * src / aux[0 * n + a];", "wr += src / aux[0 * n + a];",
+     "test_oracle_physics.py::test_viscous_second_law_and_energy_balance"),
+    ("transversality_sign", "pi[0][i] = pi[i][0] = -acc / ul[0];", "pi[0][i] = pi[i][0] = acc / ul[0];",
+     "test_oracle_physics.py::test_shear_reconstruction_properties"),
+    ("enthalpy_drop_dw", "R->dP[i] = (u[i] / q->sigma) * dw +", "R->dP[i] = 0.0 * dw +",
+     "test_oracle_physics.py::test_gubser_ideal_against_closed_form"),
+]
+
+
+def _spec(m):
+    return m.values if hasattr(m, "values") else m
+
+
+def _run_mutant(workdir, name, orig, mut, pin):
+    src = open(SRC).read()
+    if src.count(orig) != 1:
+        return ("anchor", f"mutation anchor not unique/absent: {orig}")
+    cfile = os.path.join(workdir, f"{name}.c")
+    sofile = os.path.join(workdir, f"{name}.so")
+    open(cfile, "w").write(src.replace(orig, mut))
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                           "-shared", "-o", sofile, cfile, "-lm"])
+    env = dict(os.environ, SPH_ORACLE_LIB=sofile, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", pin)], env=env, capture_output=True, text=True, cwd=ROOT,
+                       timeout=900)
+    return (r.returncode, r.stdout[-2000:])
+
+
+@pytest.fixture(scope="module")
+def results():
+    """All mutants compiled and run concurrently (each pin in its own process)."""
+    with tempfile.TemporaryDirectory() as d:
+        workers = max(2, (os.cpu_count() or 4) // 2)
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            futs = {_spec(m)[0]: ex.submit(_run_mutant, d, *_spec(m)) for m in MUTATIONS}
+            yield {k: f.result() for k, f in futs.items()}
+
+
+@pytest.mark.parametrize("name,orig,mut,pin", MUTATIONS,
+                         ids=[m[0] if isinstance(m, tuple) else None for m in MUTATIONS])
+def test_pin_catches_planted_mistake(results, name, orig, mut, pin):
+    code, out = results[name]
+    assert code != "anchor", out
+    assert code != 0, f"pin {pin} did not catch mutation {name}:\n{out}"
