@@ -213,6 +213,26 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
  * gradient, eom, work.  SPH_ERR_STATE if profiling is off. */
 sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count);
 
+/* ---------------------------------------------------------------------------
+ * Densities without device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory -- a serving loop that has
+ * handed all free HBM to its own pool, or code running while another thread captures a
+ * CUDA graph in global mode (where cudaMalloc is illegal).  It runs the cell list and the
+ * kernel sums (rows a1-a3) exactly as the stepping path does and returns, in the input
+ * order, out[0*n..] = sigma*, out[1*n..] = s, out[2..4 *n..] = n_B, n_S, n_Q (rest frame,
+ * divided by u^0 sqrt(-g), sqrt(-g) = tau if milne else 1).
+ * x[2*n], u[2*n], S[n], Nq[3*n], out[5*n] are DEVICE buffers owned by the caller; dim = 2.
+ * Every temporary lives in one fixed file-scope device array (9,699,584 bytes, held by
+ * every GPU that loads the library until exit); the call allocates nothing and frees
+ * nothing.  Limits: n <= SPH_NOALLOC_MAX_PARTICLES (else SPH_ERR_ARG) and at most 256
+ * cells of side 2h per axis (else SPH_ERR_STATE).  Work runs on `stream` (NULL: the
+ * legacy default stream) and the call returns after it finished.  All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the caller.  The
+ * first call on a device looks up the array's address; make it before any stream capture. */
+#define SPH_NOALLOC_MAX_PARTICLES 65536
+sph_status sph_density_noalloc(const double *x, const double *u, const double *S, const double *Nq, int64_t n,
+                               double h, double tau, int32_t milne, double *out, void *stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *sph_last_error(void);
 

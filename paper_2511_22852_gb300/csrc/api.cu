@@ -33,6 +33,8 @@ static sph_status fail(sph_status s, const std::string &msg)
     return s;
 }
 
+void sphg::set_last_error(const char *msg) { g_err = msg; }
+
 #define CK(call)                                                                                   \
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \

@@ -186,5 +186,7 @@ void launch_scatter_orig(const double *src, double *dst, const int *id, int n, i
 void launch_scatter_orig_u32(const uint32_t *src, uint32_t *dst, const int *id, int n, cudaStream_t st);
 void launch_cell_coords(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
 int eom_block_count(int n);
+// sets the message returned by sph_last_error() for the calling thread
+void set_last_error(const char *msg);
 
 }  // namespace sphg
