@@ -37,6 +37,10 @@ WORKLOAD = "viscous 2+1D BSQ single event, FP64: 40k particles, 64x32^3 EoS tabl
 #   gradient: distance 5, sqrt 1, q 1, kernel-derivative polynomial 3, 1/r and factor 2,
 #             dW vector 2, sum of dW 2, stress divergence 8, velocity gradient 8          = 32
 FLOPS_PER_PAIR = {"density": 22.0, "gradient": 32.0}
+# EoS inversion, per unit of work actually done (counted on the device):
+#   table residual + Jacobian evaluation (quadrilinear, 4 fields x 4 patches with derivatives,
+#   scaling) 460; 4x4 Gaussian elimination with pivoting 64; closed-form g(T), g'(T) 26
+FLOPS_EOS = (460.0, 64.0, 26.0)
 # FP64 vector peak of GB300 (nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock)
 FP64_PEAK_GFLOPS = 1250.0
 
@@ -193,6 +197,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
     t_after = g.totals()
+    # diagnostic only (not the reported value): the same steps without the L2 flush in between
+    with torch.cuda.stream(stream):
+        for k in range(min(args.steps, 50)):
+            e0[k].record(stream)
+            g.step(1)
+            e1[k].record(stream)
+    torch.cuda.synchronize()
+    noflush_ms = sum(a.elapsed_time(b) for a, b in zip(e0[:min(args.steps, 50)], e1[:min(args.steps, 50)]))
+    noflush_ms /= min(args.steps, 50)
     launches = t_after["kernel_launches"] - t_before["kernel_launches"]
     status_or = t_after["status_or"]
     clocks = clk.summary()
@@ -215,29 +228,35 @@ def run_ours(args):
         gp = Bd.GpuEvent(ev, use_graph=False, stream=stream.cuda_stream, profile=True)
         gp.step(2)
         gp_times0 = gp.kernel_times()
-        p0 = gp.totals()["pairs"]
+        tot0 = gp.totals()
+        p0 = tot0["pairs"]
         kp = max(4, min(args.steps, 40))
         with torch.cuda.stream(stream):
             for k in range(kp):
                 flush.fill_(float(k))
                 gp.step(1)
         torch.cuda.synchronize()
-        p1 = gp.totals()["pairs"]
+        tot1 = gp.totals()
+        p1 = tot1["pairs"]
         times = {k: (v[0] - gp_times0[k][0], v[1] - gp_times0[k][1]) for k, v in gp.kernel_times().items()}
         gp.free()
         pairs_incl_self = (p1 - p0)  # summed over both stages of kp steps
         dom = max(times, key=lambda k: times[k][0])
-        grp_pairs = {"density": pairs_incl_self, "gradient": pairs_incl_self - 2 * kp * ev.n}
-        roof = None
-        if dom in FLOPS_PER_PAIR:
-            flops = FLOPS_PER_PAIR[dom] * grp_pairs[dom]
-            ms = times[dom][0]
-            achieved = flops / (ms / 1e3) / 1e9
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dom,
-                    "peak_source": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s at 2070 MHz)",
-                    "avg_launch_ms": ms / times[dom][1],
-                    "flops_per_launch": flops / times[dom][1]}
+        ew = [b - a for a, b in zip(tot0["eos_work"], tot1["eos_work"])]
+        flops = {"density": FLOPS_PER_PAIR["density"] * pairs_incl_self,
+                 "gradient": FLOPS_PER_PAIR["gradient"] * (pairs_incl_self - 2 * kp * ev.n),
+                 "eos": sum(f * w for f, w in zip(FLOPS_EOS, ew))}
+        rooflines = {}
+        for k in flops:
+            ms = times[k][0]
+            achieved = flops[k] / (ms / 1e3) / 1e9
+            rooflines[k] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": k,
+                            "peak_source": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s at 2070 MHz)",
+                            "avg_launch_ms": ms / times[k][1], "flops_per_launch": flops[k] / times[k][1]}
+        rooflines["eos"]["work_per_launch"] = {"table_evals": ew[0] / times["eos"][1], "solves": ew[1] / times["eos"][1],
+                                               "closed_form_evals": ew[2] / times["eos"][1]}
+        roof = rooflines.get(dom)
         total_ms = sum(v[0] for v in times.values())
         kernel_share = {k: round(v[0] / total_ms, 4) for k, v in times.items()}
 
@@ -266,9 +285,11 @@ def run_ours(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": WORKLOAD, "particles": ev.n, "l2": "flushed (256 MiB write) between timed steps",
                           "parallelism": f"replicas x{ws}", "cuda_graph": True},
-               "roofline": roof, "kernel_share": kernel_share,
+               "roofline": roof, "kernel_share": kernel_share, "kernel_rooflines": rooflines,
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-               "wall_s_timed": t_wall, "status_or": int(status_or)}
+               "wall_s_timed": t_wall, "status_or": int(status_or),
+               "diagnostics": {"ms_per_step_without_l2_flush": noflush_ms,
+                               "profile_mode_group_ms_per_step": total_ms / kp}}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ev)
         print(json.dumps(out), flush=True)

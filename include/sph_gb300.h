@@ -178,12 +178,17 @@ sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags);
 #define SPH_F_STATUS (1ull << 14)    /* status[n] (uint32) */
 #define SPH_F_NNB (1ull << 15)       /* neighbour count including self, nnb[n] (int32) */
 #define SPH_F_CELL (1ull << 16)      /* cell coordinates cell[dim*n] (int32) */
+#define SPH_F_GUESS (1ull << 17)     /* EoS warm start guess[4*n]: the previous stage's table solution
+                                        (T, mu_B, mu_S, mu_Q), T = 0 where the table was not used;
+                                        part of the evolved state (read it and write it back for a
+                                        bitwise resume) */
 
 typedef struct {
     double *x, *u, *S, *Nq, *Bv, *Pv;
     double *sigstar, *s, *nq, *T, *mu, *p, *e, *Pi;
     uint32_t *status;
     int32_t *nnb, *cell;
+    double *guess;
     int32_t on_device;
 } sph_field_bufs;
 
@@ -198,13 +203,16 @@ typedef struct {
     int64_t steps;
     int64_t pairs;          /* accepted neighbour pairs (self pairs included) summed over all stages */
     int64_t kernel_launches; /* kernels launched by sph_step so far (graph replays included) */
+    int64_t eos_work[3];     /* EoS work done: table residual+Jacobian evaluations, 4x4 solves,
+                                closed-form evaluations (all stages and read-outs) */
 } sph_totals;
 
 sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *out, sph_totals *tot);
 
-/* Overwrites the evolved state (x, u, S, Bv, Pv; Nq unchanged) from buffers in the
- * original particle order (mask bits SPH_F_X .. SPH_F_PV; others ignored), e.g. to
- * resume from a checkpoint read with sph_read_fields.  Errors: SPH_ERR_ARG. */
+/* Overwrites the evolved state (x, u, S, Bv, Pv, the EoS warm start; Nq unchanged) from
+ * buffers in the original particle order (mask bits SPH_F_X .. SPH_F_PV and SPH_F_GUESS;
+ * others ignored), e.g. to resume from a checkpoint read with sph_read_fields.  Fields not
+ * in the mask keep their values.  Errors: SPH_ERR_ARG. */
 sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *in);
 
 /* Per-kernel-group device time of an event created with profile = 1: for group k < *count
@@ -222,7 +230,7 @@ sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms,
  * order, out[0*n..] = sigma*, out[1*n..] = s, out[2..4 *n..] = n_B, n_S, n_Q (rest frame,
  * divided by u^0 sqrt(-g), sqrt(-g) = tau if milne else 1).
  * x[2*n], u[2*n], S[n], Nq[3*n], out[5*n] are DEVICE buffers owned by the caller; dim = 2.
- * Every temporary lives in one fixed file-scope device array (9,699,584 bytes, held by
+ * Every temporary lives in one fixed file-scope device array (10,223,872 bytes, held by
  * every GPU that loads the library until exit); the call allocates nothing and frees
  * nothing.  Limits: n <= SPH_NOALLOC_MAX_PARTICLES (else SPH_ERR_ARG) and at most 256
  * cells of side 2h per axis (else SPH_ERR_STATE).  Work runs on `stream` (NULL: the

@@ -77,9 +77,10 @@ def lib():
             "oc_eos_invert_analytic": (i, [P, d, p, p, p]),
             "oc_eos_table": (None, [P, p, p, p, p]),
             "oc_eos_invert": (C.c_uint, [P, d, p, p]),
-            "oc_stage": (i, [P, l, d, p, p, p, p, p, p, p]),
-            "oc_observe": (None, [P, l, d, p, p, p, p]),
-            "oc_heun": (i, [P, l, p, d, i, p, p, p, p, p, p, p]),
+            "oc_eos_invert_ws": (C.c_uint, [P, d, p, p, p, p]),
+            "oc_stage": (i, [P, l, d, p, p, p, p, p, p, p, p, p]),
+            "oc_observe": (None, [P, l, d, p, p, p, p, p]),
+            "oc_heun": (i, [P, l, p, d, i, p, p, p, p, p, p, p, p]),
             "oc_totals": (None, [P, l, d, p, p, p, p]),
             "oc_pi_pairs": (i, [i, p]),
             "oc_pi_full": (None, [i, i, d, p, p, p]),
@@ -218,11 +219,13 @@ class OracleRun:
     tau: float
     work: float = 0.0
     status_or: int = 0
+    guess: np.ndarray = None  # [4][N] warm start of the EoS Newton (previous table solution, T = 0: none)
 
     @classmethod
     def start(cls, ev, **kw):
         P, keep = make_params(ev, **kw)
-        return cls(ev=ev, P=P, keep=keep, y=pack_state(ev), Nq=_f64(ev.Nq), tau=float(ev.tau0))
+        return cls(ev=ev, P=P, keep=keep, y=pack_state(ev), Nq=_f64(ev.Nq), tau=float(ev.tau0),
+                   guess=np.zeros((4, ev.n)))
 
     @property
     def n(self):
@@ -237,13 +240,14 @@ class OracleRun:
         work = C.c_double(self.work)
         stor = C.c_uint(0)
         lib().oc_heun(C.byref(self.P), n, C.byref(tau), float(self.ev.dtau), int(nsteps), _ptr(self.y),
-                      _ptr(self.Nq), _ptr(aux), _ptr(grad), _ptr(st), C.byref(stor), C.byref(work))
+                      _ptr(self.Nq), _ptr(aux), _ptr(grad), _ptr(st), C.byref(stor), C.byref(work), _ptr(self.guess))
         self.tau, self.work = tau.value, work.value
         self.status_or |= stor.value
         return aux
 
     def stage(self, y=None, tau=None):
-        """One right-hand-side evaluation: (dydt, aux, grad, status, work_rate)."""
+        """One right-hand-side evaluation: (dydt, aux, grad, status, work_rate), warm-started from
+        the current guess (which is not updated)."""
         y = self.y if y is None else _f64(y)
         tau = self.tau if tau is None else tau
         n, dim = self.n, self.P.dim
@@ -252,15 +256,18 @@ class OracleRun:
         grad = np.zeros((dim * dim + dim, n))
         st = np.zeros(n, dtype=np.uint32)
         wr = C.c_double(0.0)
+        gout = np.zeros((4, n))
         lib().oc_stage(C.byref(self.P), n, float(tau), _ptr(y), _ptr(self.Nq), _ptr(dydt), _ptr(aux), _ptr(grad),
-                       _ptr(st), C.byref(wr))
+                       _ptr(st), C.byref(wr), _ptr(self.guess), _ptr(gout))
         return dydt, aux, grad, st, wr.value
 
     def observe(self):
+        """Densities and EoS at the current state (warm-started from the guess, which is not updated)."""
         n = self.n
         aux = np.zeros((NAUX, n))
         st = np.zeros(n, dtype=np.uint32)
-        lib().oc_observe(C.byref(self.P), n, float(self.tau), _ptr(self.y), _ptr(self.Nq), _ptr(aux), _ptr(st))
+        lib().oc_observe(C.byref(self.P), n, float(self.tau), _ptr(self.y), _ptr(self.Nq), _ptr(aux), _ptr(st),
+                         _ptr(self.guess))
         return aux, st
 
     def totals(self, aux=None):

@@ -557,31 +557,50 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
     return rn <= P->newton_tol ? 0 : -1;
 }
 
-/* out[0..10]: T, muB, muS, muQ, p, e, p_s, p_nB, p_nS, p_nQ, cs2 (after the cap) */
-unsigned oc_eos_invert(const oc_params *P, double s, const double *n, double *out)
+/* out[0..10]: T, muB, muS, muQ, p, e, p_s, p_nB, p_nS, p_nQ, cs2 (after the cap).
+   guess: the previous stage's table solution (T, muB, muS, muQ) of this particle, T <= 0
+   for none (may be NULL).  Order of attempts (SURVEY reading A16):
+     1. table Newton warm-started from the guess, if the guess lies in the table;
+     2. otherwise (or if 1. does not converge) the closed-form solution, then table Newton
+        started there if it lies in the table; else the closed form (flagged).
+   used_table (may be NULL) receives 1 when the table produced the result. */
+unsigned oc_eos_invert_ws(const oc_params *P, double s, const double *n, const double *guess, double *out,
+                          int *used_table)
 {
     unsigned st = 0;
     for (int k = 0; k < 11; ++k) out[k] = 0.0;
+    if (used_table) *used_table = 0;
     if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) return ST_NONFINITE | ST_NOCONV;
     double x[4];
-    int r = oc_eos_invert_analytic(P, s, n, &x[0], &x[1]);
-    if (r != 0) return (unsigned)r | ST_NOCONV;
     double p, H[16], sn[4];
     int use_table = 0;
-    if (P->has_table) {
-        if (in_table(P, x)) {
-            double xt[4];
-            memcpy(xt, x, sizeof(xt));
-            if (table_newton(P, s, n, xt) == 0) {
-                memcpy(x, xt, sizeof(xt));
-                use_table = 1;
-            } else {
-                st |= ST_FALLBACK;
-            }
-        } else {
-            st |= ST_OUT_OF_TABLE;
+    if (P->has_table && guess && guess[0] > 0.0 && in_table(P, guess)) {
+        double xt[4];
+        memcpy(xt, guess, sizeof(xt));
+        if (table_newton(P, s, n, xt) == 0) {
+            memcpy(x, xt, sizeof(xt));
+            use_table = 1;
         }
     }
+    if (!use_table) {
+        int r = oc_eos_invert_analytic(P, s, n, &x[0], &x[1]);
+        if (r != 0) return (unsigned)r | ST_NOCONV;
+        if (P->has_table) {
+            if (in_table(P, x)) {
+                double xt[4];
+                memcpy(xt, x, sizeof(xt));
+                if (table_newton(P, s, n, xt) == 0) {
+                    memcpy(x, xt, sizeof(xt));
+                    use_table = 1;
+                } else {
+                    st |= ST_FALLBACK;
+                }
+            } else {
+                st |= ST_OUT_OF_TABLE;
+            }
+        }
+    }
+    if (used_table) *used_table = use_table;
     if (use_table) {
         oc_eos_table(P, x, &p, sn, H);
     } else {
@@ -617,6 +636,11 @@ unsigned oc_eos_invert(const oc_params *P, double s, const double *n, double *ou
     for (int k = 0; k < 4; ++k) out[6 + k] = z[k];
     out[10] = cs2;
     return st;
+}
+
+unsigned oc_eos_invert(const oc_params *P, double s, const double *n, double *out)
+{
+    return oc_eos_invert_ws(P, s, n, NULL, out, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -806,7 +830,7 @@ static int nv_of(int dim) { return 2 * dim + 2 + npi_of(dim); }
                          u0, neighbour count, sigma, status
    grad layout [dim*dim + dim][n]: d_k u^j (k major), F^i                              */
 static void densities_eos(const oc_params *P, long n, double tau, const double *y, const double *Nq, grid_t *g,
-                          double *aux, unsigned *status)
+                          double *aux, unsigned *status, const double *guess_in, double *guess_out)
 {
     int dim = P->dim;
     double two_h = 2.0 * P->h;
@@ -843,7 +867,13 @@ static void densities_eos(const oc_params *P, long n, double tau, const double *
             aux[16 * n + a] = sig / vol;
             double out[11];
             double nr[3] = {aux[2 * n + a], aux[3 * n + a], aux[4 * n + a]};
-            unsigned st = oc_eos_invert(P, aux[1 * n + a], nr, out);
+            double gs[4] = {0, 0, 0, 0};
+            if (guess_in)
+                for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
+            int used = 0;
+            unsigned st = oc_eos_invert_ws(P, aux[1 * n + a], nr, gs, out, &used);
+            if (guess_out)
+                for (int k = 0; k < 4; ++k) guess_out[k * n + a] = used ? out[k] : 0.0;
             for (int k = 0; k < 4; ++k) aux[(5 + k) * n + a] = out[k];
             aux[9 * n + a] = out[4];
             aux[10 * n + a] = out[5];
@@ -861,7 +891,7 @@ typedef struct {
 } eosder_t;
 
 int oc_stage(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *dydt, double *aux,
-             double *grad, unsigned *status, double *work_rate)
+             double *grad, unsigned *status, double *work_rate, const double *guess_in, double *guess_out)
 {
     int dim = P->dim, np = npi_of(dim), nv = nv_of(dim);
     double two_h = 2.0 * P->h;
@@ -870,7 +900,7 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     make_geom(P->milne, tau, &G);
     grid_t g;
     grid_build(&g, n, dim, y, P->h);
-    densities_eos(P, n, tau, y, Nq, &g, aux, status);
+    densities_eos(P, n, tau, y, Nq, &g, aux, status, guess_in, guess_out);
 
     /* EoS derivatives again (kept out of aux), transport, full pi, X^{ji}/sigma*^2 */
     eosder_t *ed = (eosder_t *)malloc(sizeof(eosder_t) * (size_t)(n > 0 ? n : 1));
@@ -882,7 +912,10 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     for (long a = 0; a < n; ++a) {
         double out[11];
         double nr[3] = {aux[2 * n + a], aux[3 * n + a], aux[4 * n + a]};
-        oc_eos_invert(P, aux[1 * n + a], nr, out);
+        double gs[4] = {0, 0, 0, 0};
+        if (guess_in)
+            for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
+        oc_eos_invert_ws(P, aux[1 * n + a], nr, gs, out, NULL);
         ed[a].ps = out[6];
         for (int c = 0; c < 3; ++c) ed[a].pn[c] = out[7 + c];
         double u[4] = {aux[14 * n + a], 0, 0, 0};
@@ -1039,11 +1072,12 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
 }
 
 /* densities and EoS only, at the current state (for read-out) */
-void oc_observe(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *aux, unsigned *status)
+void oc_observe(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *aux, unsigned *status,
+                const double *guess)
 {
     grid_t g;
     grid_build(&g, n, P->dim, y, P->h);
-    densities_eos(P, n, tau, y, Nq, &g, aux, status);
+    densities_eos(P, n, tau, y, Nq, &g, aux, status, guess, NULL);
     for (long a = 0; a < n; ++a) aux[13 * n + a] = P->viscous ? aux[16 * n + a] * y[(2 * P->dim + 1) * n + a] : 0.0;
     grid_free(&g);
 }
@@ -1051,19 +1085,20 @@ void oc_observe(const oc_params *P, long n, double tau, const double *y, const d
 /* Heun: y1 = y0 + dt f(t, y0); y = ((y0 + y1) + dt f(t + dt, y1)) / 2.
    work accumulates the longitudinal work integral with the same quadrature. */
 int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, double *y, const double *Nq, double *aux,
-            double *grad, unsigned *status, unsigned *status_or, double *work)
+            double *grad, unsigned *status, unsigned *status_or, double *work, double *guess)
 {
     int nv = nv_of(P->dim);
     size_t sz = sizeof(double) * (size_t)nv * (size_t)(n > 0 ? n : 1);
     double *k = (double *)malloc(sz);
     double *y1 = (double *)malloc(sz);
+    double *g1 = (double *)calloc((size_t)4 * (size_t)(n > 0 ? n : 1), sizeof(double));
     unsigned acc = 0;
     for (int step = 0; step < nsteps; ++step) {
         double wr0, wr1;
-        oc_stage(P, n, *tau, y, Nq, k, aux, grad, status, &wr0);
+        oc_stage(P, n, *tau, y, Nq, k, aux, grad, status, &wr0, guess, g1);
         for (long a = 0; a < n; ++a) acc |= status[a];
         for (long i = 0; i < (long)nv * n; ++i) y1[i] = y[i] + dtau * k[i];
-        oc_stage(P, n, *tau + dtau, y1, Nq, k, aux, grad, status, &wr1);
+        oc_stage(P, n, *tau + dtau, y1, Nq, k, aux, grad, status, &wr1, g1, guess);
         for (long a = 0; a < n; ++a) acc |= status[a];
         for (long i = 0; i < (long)nv * n; ++i) y[i] = 0.5 * ((y[i] + y1[i]) + dtau * k[i]);
         *work += 0.5 * dtau * (wr0 + wr1);
@@ -1072,6 +1107,7 @@ int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, do
     *status_or = acc;
     free(k);
     free(y1);
+    free(g1);
     return 0;
 }
 

@@ -28,7 +28,7 @@ SPH_SYNC = 1
 
 F = {name: 1 << i for i, name in enumerate(
     ["X", "U", "S", "NQ", "BV", "PV", "SIGMA_STAR", "S_DENS", "N_DENS", "T", "MU", "P", "E", "PI_BULK", "STATUS",
-     "NNB", "CELL"])}
+     "NNB", "CELL", "GUESS"])}
 
 EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_event", "sph_step", "sph_read_fields",
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times"]
@@ -60,13 +60,13 @@ class EventDesc(C.Structure):
 
 class FieldBufs(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ["x", "u", "S", "Nq", "Bv", "Pv", "sigstar", "s", "nq", "T", "mu", "p",
-                                          "e", "Pi", "status", "nnb", "cell"]] + [("on_device", C.c_int32)]
+                                          "e", "Pi", "status", "nnb", "cell", "guess"]] + [("on_device", C.c_int32)]
 
 
 class Totals(C.Structure):
     _fields_ = [("tau", C.c_double), ("E", C.c_double), ("S", C.c_double), ("N", C.c_double * 3),
                 ("work", C.c_double), ("status_or", C.c_uint32), ("pad", C.c_int32), ("steps", C.c_int64),
-                ("pairs", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("pairs", C.c_int64), ("kernel_launches", C.c_int64), ("eos_work", C.c_int64 * 3)]
 
 
 _lib = None
@@ -232,7 +232,7 @@ class GpuEvent:
         shapes = {"X": (self.dim, "x"), "U": (self.dim, "u"), "S": (1, "S"), "NQ": (3, "Nq"), "BV": (1, "Bv"),
                   "PV": (self.npi, "Pv"), "SIGMA_STAR": (1, "sigstar"), "S_DENS": (1, "s"), "N_DENS": (3, "nq"),
                   "T": (1, "T"), "MU": (3, "mu"), "P": (1, "p"), "E": (1, "e"), "PI_BULK": (1, "Pi"),
-                  "STATUS": (1, "status"), "NNB": (1, "nnb"), "CELL": (self.dim, "cell")}
+                  "STATUS": (1, "status"), "NNB": (1, "nnb"), "CELL": (self.dim, "cell"), "GUESS": (4, "guess")}
         b = FieldBufs()
         out, mask = {}, 0
         for nm in names:
@@ -249,7 +249,8 @@ class GpuEvent:
         t = Totals()
         sph_read_fields(self.h, 0, None, t)
         return {"tau": t.tau, "E": t.E, "S": t.S, "N": np.array(t.N[:]), "work": t.work,
-                "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs, "kernel_launches": t.kernel_launches}
+                "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs, "kernel_launches": t.kernel_launches,
+                "eos_work": tuple(t.eos_work[:])}
 
     def kernel_times(self):
         return sph_kernel_times(self.h)
@@ -267,10 +268,11 @@ class GpuEvent:
         sph_debug_rates(self.h, r, g)
         return r, g
 
-    def write_state(self, x=None, u=None, S=None, Bv=None, Pv=None):
+    def write_state(self, x=None, u=None, S=None, Bv=None, Pv=None, guess=None):
         b = FieldBufs()
         keep, mask = [], 0
-        for nm, arr, attr in [("X", x, "x"), ("U", u, "u"), ("S", S, "S"), ("BV", Bv, "Bv"), ("PV", Pv, "Pv")]:
+        for nm, arr, attr in [("X", x, "x"), ("U", u, "u"), ("S", S, "S"), ("BV", Bv, "Bv"), ("PV", Pv, "Pv"),
+                              ("GUESS", guess, "guess")]:
             if arr is not None:
                 a = _f64(arr)
                 keep.append(a)

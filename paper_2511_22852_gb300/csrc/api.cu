@@ -59,6 +59,9 @@ struct sph_event {
     double *Nq_orig = nullptr;
     CellBufs cb{};
     double *dens = nullptr, *eosf = nullptr, *gin = nullptr, *gout = nullptr;
+    // EoS warm start: wguess (state order, carried across stages), guess_in (this stage's
+    // sorted order), wguess_obs (written by read-out evaluations, which leave wguess alone)
+    double *wguess = nullptr, *guess_in = nullptr, *wguess_obs = nullptr;
     uint32_t *status = nullptr;
     int *nnb = nullptr;
     double *wpart = nullptr;
@@ -107,6 +110,7 @@ static EvView make_view(const sph_event *ev)
     double two_h = 2.0 * ev->h;
     v.supp2 = two_h * two_h;
     v.inv_cell = 1.0 / (2.0 * ev->h);
+    v.supp2_hi = prefilter_bound(ev->h, ev->B);
     v.sigma_d = ev->dim == 2 ? 10.0 / (7.0 * kPi * ev->h * ev->h) : 1.0 / (kPi * ev->h * ev->h * ev->h);
     v.dtau = ev->dtau;
     v.sc = ev->sc;
@@ -145,17 +149,17 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_CELLS, 1, 1);
     mark(ev, G_PERMUTE, 1, 0);
     {
-        const double *src[2] = {ev->Y[0], ev->Nq[0]};
-        double *dst[2] = {ev->Y[1], ev->Nq[1]};
-        int rows[2] = {ev->nv, 3};
-        launch_permute(v, ev->cb.perm, src, dst, rows, 2, ev->id[0], ev->id[1], st);
+        const double *src[3] = {ev->Y[0], ev->Nq[0], ev->wguess};
+        double *dst[3] = {ev->Y[1], ev->Nq[1], ev->guess_in};
+        int rows[3] = {ev->nv, 3, 4};
+        launch_permute(v, ev->cb.perm, src, dst, rows, 3, ev->id[0], ev->id[1], st);
     }
     mark(ev, G_PERMUTE, 1, 1);
     mark(ev, G_DENSITY, 1, 0);
     launch_density(v, ev->Y[1], ev->Nq[1], ev->cb, ev->dens, ev->nnb, st);
     mark(ev, G_DENSITY, 1, 1);
     mark(ev, G_EOS, 1, 0);
-    launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, st);
+    launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
     mark(ev, G_EOS, 1, 1);
     mark(ev, G_GRADIENT, 1, 0);
     launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
@@ -172,17 +176,17 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_CELLS, 2, 1);
     mark(ev, G_PERMUTE, 2, 0);
     {
-        const double *src[3] = {ev->Y1[0], ev->Y[1], ev->Nq[1]};
-        double *dst[3] = {ev->Y1[1], ev->Y[0], ev->Nq[0]};
-        int rows[3] = {ev->nv, ev->nv, 3};
-        launch_permute(v, ev->cb.perm, src, dst, rows, 3, ev->id[1], ev->id[0], st);
+        const double *src[4] = {ev->Y1[0], ev->Y[1], ev->Nq[1], ev->wguess};
+        double *dst[4] = {ev->Y1[1], ev->Y[0], ev->Nq[0], ev->guess_in};
+        int rows[4] = {ev->nv, ev->nv, 3, 4};
+        launch_permute(v, ev->cb.perm, src, dst, rows, 4, ev->id[1], ev->id[0], st);
     }
     mark(ev, G_PERMUTE, 2, 1);
     mark(ev, G_DENSITY, 2, 0);
     launch_density(v, ev->Y1[1], ev->Nq[0], ev->cb, ev->dens, ev->nnb, st);
     mark(ev, G_DENSITY, 2, 1);
     mark(ev, G_EOS, 2, 0);
-    launch_eos(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, st);
+    launch_eos(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
     mark(ev, G_EOS, 2, 1);
     mark(ev, G_GRADIENT, 2, 0);
     launch_gradient(v, 2, ev->Y1[1], ev->gin, ev->cb, ev->gout, st);
@@ -216,12 +220,12 @@ static void enqueue_observe(sph_event *ev)
     EvView v = make_view(ev);
     cudaStream_t st = ev->stream;
     enqueue_sort(ev, v, ev->Y[0], ev->id[0]);
-    const double *src[2] = {ev->Y[0], ev->Nq[0]};
-    double *dst[2] = {ev->Y[1], ev->Nq[1]};
-    int rows[2] = {ev->nv, 3};
-    launch_permute(v, ev->cb.perm, src, dst, rows, 2, ev->id[0], ev->id[1], st);
+    const double *src[3] = {ev->Y[0], ev->Nq[0], ev->wguess};
+    double *dst[3] = {ev->Y[1], ev->Nq[1], ev->guess_in};
+    int rows[3] = {ev->nv, 3, 4};
+    launch_permute(v, ev->cb.perm, src, dst, rows, 3, ev->id[0], ev->id[1], st);
     launch_density(v, ev->Y[1], ev->Nq[1], ev->cb, ev->dens, ev->nnb, st);
-    launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, st);
+    launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess_obs, st);
 }
 
 static sph_status wait_stream(sph_event *ev)
@@ -457,6 +461,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     AL(ev->cb.key, sizeof(uint32_t) * N);
     AL(ev->cb.tmp, sizeof(uint32_t) * N);
     AL(ev->cb.perm, sizeof(uint32_t) * N);
+    AL(ev->cb.fpos, sizeof(float2) * N);
     AL(ev->cb.cnt, sizeof(uint32_t) * (size_t)ev->cb.nb);
     AL(ev->cb.start, sizeof(uint32_t) * (size_t)ev->cb.nb);
     AL(ev->cb.cursor, sizeof(uint32_t) * (size_t)ev->cb.nb);
@@ -464,6 +469,9 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     AL(ev->eosf, dv * kNEos);
     AL(ev->gin, dv * kNGin);
     AL(ev->gout, dv * kNGout);
+    AL(ev->wguess, dv * 4);
+    AL(ev->guess_in, dv * 4);
+    AL(ev->wguess_obs, dv * 4);
     AL(ev->status, sizeof(uint32_t) * N);
     AL(ev->nnb, sizeof(int) * N);
     ev->nwblk = eom_block_count(n > 0 ? n : 1);
@@ -485,6 +493,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
         else CK(cudaMemsetAsync(ev->Y[0] + (size_t)(2 * ev->dim + 2) * n, 0, dn * ev->npi, st));
         CK(cudaMemcpyAsync(ev->Nq[0], d->Nq, dn * 3, k, st));
         CK(cudaMemcpyAsync(ev->Nq_orig, d->Nq, dn * 3, k, st));
+        CK(cudaMemsetAsync(ev->wguess, 0, dn * 4, st));
         std::vector<int> iota(n);
         for (int i = 0; i < n; ++i) iota[i] = i;
         CK(cudaMemcpyAsync(ev->id[0], iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
@@ -577,6 +586,7 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         {SPH_F_NQ, o ? o->Nq : nullptr, ev->Nq[0], 3, 1},
         {SPH_F_BV, o ? o->Bv : nullptr, ev->Y[0] + (2 * ev->dim + 1) * N, 1, 1},
         {SPH_F_PV, o ? o->Pv : nullptr, ev->Y[0] + (2 * ev->dim + 2) * N, ev->npi, 1},
+        {SPH_F_GUESS, o ? o->guess : nullptr, ev->wguess, 4, 1},
         {SPH_F_SIGMA_STAR, o ? o->sigstar : nullptr, dens, 1, 0},
         {SPH_F_S_DENS, o ? o->s : nullptr, dens + N, 1, 0},
         {SPH_F_N_DENS, o ? o->nq : nullptr, dens + 2 * N, 3, 0},
@@ -661,6 +671,9 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         tot->status_or = hs.status_or;
         tot->steps = hs.steps;
         tot->pairs = (int64_t)hs.pairs;
+        tot->eos_work[0] = (int64_t)hs.eos_resid;
+        tot->eos_work[1] = (int64_t)hs.eos_solve;
+        tot->eos_work[2] = (int64_t)hs.eos_g;
         tot->kernel_launches = ev->launches;
     }
     return wait_stream(ev);
@@ -695,6 +708,8 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
     CK(cudaMemcpyAsync(ev->Y[0], ev->scratch, sizeof(double) * ev->nv * N, cudaMemcpyDeviceToDevice, st));
     launch_scatter_orig(ev->Nq[0], ev->scratch, ev->id[0], n, 3, st);
     CK(cudaMemcpyAsync(ev->Nq[0], ev->scratch, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st));
+    launch_scatter_orig(ev->wguess, ev->scratch, ev->id[0], n, 4, st);
+    CK(cudaMemcpyAsync(ev->wguess, ev->scratch, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, st));
     std::vector<int> iota(n);
     for (int i = 0; i < n; ++i) iota[i] = i;
     CK(cudaMemcpyAsync(ev->id[0], iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
@@ -715,6 +730,10 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
         if (!(mask & r.bit)) continue;
         if (!r.src) return fail(SPH_ERR_ARG, "masked field has a null source");
         CK(cudaMemcpyAsync(ev->Y[0] + r.off * N, r.src, sizeof(double) * r.rows * N, k, st));
+    }
+    if (mask & SPH_F_GUESS) {
+        if (!in->guess) return fail(SPH_ERR_ARG, "masked field has a null source");
+        CK(cudaMemcpyAsync(ev->wguess, in->guess, sizeof(double) * 4 * N, k, st));
     }
     ev->observed = false;
     return wait_stream(ev);

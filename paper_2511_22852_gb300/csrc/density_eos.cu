@@ -1,14 +1,17 @@
 // density_eos.cu -- kernel-sum densities (row a3) and the EoS inversion (row a4).
 //
-// Density pass (eqs. sigmastar, refconv): one thread per particle in sorted
-// order walks the 3x3 cells around its own; consecutive threads of a warp sit
-// in the same or adjacent cells, so the candidate loads are shared through L1.
-// The acceptance test r^2 < (2h)^2 rounds every product separately, so the
-// neighbour set is identical to a plain FP64 evaluation on any platform.
+// Density pass (eqs. sigmastar, refconv): one warp per particle (sorted order)
+// walks the 3x3 cells around its own; a single-precision prefilter with a proven
+// error margin discards far candidates, the survivors are compacted so the FP64
+// work runs on full warps.  The acceptance test r^2 < (2h)^2 is evaluated in FP64
+// with every product rounded separately, so the neighbour set is identical to a
+// plain FP64 evaluation on any platform.
 //
 // EoS pass (Sec. "EoS inverter", online inversion done on the device):
-//   1. closed-form EoS solved for T on its upper branch (mu_q = n_q/(chi_q T^2)),
-//      bracketed Newton with bisection safeguard;
+//   0. damped Newton on the quadrilinear table interpolant warm-started from this
+//      particle's previous-stage table solution, when there is one in the table;
+//   1. otherwise: closed-form EoS solved for T on its upper branch
+//      (mu_q = n_q/(chi_q T^2)), bracketed Newton with bisection safeguard;
 //   2. if that point lies in the table, damped Newton on the quadrilinear
 //      interpolant of (s, n_B, n_S, n_Q), residual scaled by s, 4x4 Jacobian from
 //      the same 16-corner stencil, one polishing step after convergence;
@@ -22,56 +25,109 @@ namespace sphg {
 
 namespace {
 
-__global__ void __launch_bounds__(128) k_density2(EvView v, const double *__restrict__ y, const double *__restrict__ Nq,
-                                                  const uint32_t *__restrict__ start, const uint32_t *__restrict__ cnt,
-                                                  double *__restrict__ dens, int *__restrict__ nnb)
+// single-precision positions relative to the bounding-box minimum (prefilter input)
+__global__ void k_fpos(EvView v, const double *__restrict__ y, float2 *__restrict__ fpos)
 {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= v.n) return;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= v.n) return;
+    double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+    fpos[j] = make_float2(__double2float_rn(__dsub_rn(y[j], xmin0)), __double2float_rn(__dsub_rn(y[v.n + j], xmin1)));
+}
+
+constexpr int kWarps = 4;  // warps (particles in flight) per block of the neighbour passes
+
+// Density pass, one warp per particle.  For each of the 3x3 cells the lanes take 32
+// candidates at a time through a single-precision prefilter; survivors are compacted
+// (ballot) into a per-warp queue and, 32 at a time, go through the exact FP64 test
+// r^2 < (2h)^2 and the kernel sum with every lane busy.  Per-lane partial sums are
+// combined by a butterfly reduction: the order is fixed, so results are reproducible.
+__global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double *__restrict__ y,
+                                                          const float2 *__restrict__ fpos,
+                                                          const double *__restrict__ Nq,
+                                                          const uint32_t *__restrict__ start,
+                                                          const uint32_t *__restrict__ cnt,
+                                                          double *__restrict__ dens, int *__restrict__ nnb)
+{
+    __shared__ int queue[kWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarps + wid;
+    if (a >= v.n) return;  // warp-uniform
+    int *q = queue[wid];
     const int n = v.n;
     const double *X = y, *Y = y + n, *S = y + 4 * (size_t)n;
     const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
-    double xa = X[a], ya = Y[a];
-    double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
-    int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
-    int lim = 1 << v.B;
+    const double xa = X[a], ya = Y[a];
+    const float2 fa = fpos[a];
+    const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+    const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+    const int lim = 1 << v.B;
+    const unsigned lt = (1u << lane) - 1u;
     double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
-    int c = 0;
+    int c = 0, qn = 0;
+    auto pair = [&](int b) {
+        double r2 = dist2_2d(xa - X[b], ya - Y[b]);
+        if (r2 < v.supp2) {
+            double q = r2 > 0.0 ? r2 * rsqrt_nr(r2) * v.inv_h : 0.0;
+            double w = kernel_w(q);
+            sg += w;
+            ss = fma(S[b], w, ss);
+            sb = fma(NB[b], w, sb);
+            sS = fma(NS[b], w, sS);
+            sq = fma(NQ[b], w, sq);
+            ++c;
+        }
+    };
     for (int oy = -1; oy <= 1; ++oy) {
-        int ny = cy + oy;
+        const int ny = cy + oy;
         if (ny < 0 || ny >= lim) continue;
         for (int ox = -1; ox <= 1; ++ox) {
-            int nx = cx + ox;
+            const int nx = cx + ox;
             if (nx < 0 || nx >= lim) continue;
-            uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
-            uint32_t b0 = start[k], b1 = b0 + cnt[k];
-            for (uint32_t b = b0; b < b1; ++b) {
-                double r2 = dist2_2d(xa - X[b], ya - Y[b]);
-                if (r2 < v.supp2) {
-                    double q = r2 > 0.0 ? r2 * rsqrt_nr(r2) * v.inv_h : 0.0;
-                    double w = kernel_w(q);
-                    sg += w;
-                    ss = fma(S[b], w, ss);
-                    sb = fma(NB[b], w, sb);
-                    sS = fma(NS[b], w, sS);
-                    sq = fma(NQ[b], w, sq);
-                    ++c;
+            const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+            const uint32_t b0 = start[k], b1 = b0 + cnt[k];
+            for (uint32_t base = b0; base < b1; base += 32) {
+                const uint32_t b = base + lane;
+                bool cand = false;
+                if (b < b1) {
+                    const float2 fb = fpos[b];
+                    const float dx = fa.x - fb.x, dy = fa.y - fb.y;
+                    cand = fmaf(dx, dx, dy * dy) <= v.supp2_hi;
+                }
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+                if (cand) q[qn + __popc(m & lt)] = (int)b;
+                qn += __popc(m);
+                __syncwarp();
+                if (qn >= 32) {
+                    pair(q[lane]);
+                    qn -= 32;
+                    __syncwarp();
+                    if (lane < qn) q[lane] = q[32 + lane];
+                    __syncwarp();
                 }
             }
         }
     }
-    double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
-    double u0 = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
-    double sd = v.sigma_d;
-    unsigned int tot = __reduce_add_sync(__activemask(), (unsigned int)c);
-    if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) atomicAdd(&v.sc->pairs, (unsigned long long)tot);
-    dens[a] = sd * sg;
-    dens[(size_t)n + a] = sd * ss;  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
-    dens[2 * (size_t)n + a] = sd * sb;
-    dens[3 * (size_t)n + a] = sd * sS;
-    dens[4 * (size_t)n + a] = sd * sq;
-    dens[5 * (size_t)n + a] = u0;
-    nnb[a] = c;
+    if (lane < qn) pair(q[lane]);
+    for (int o = 16; o > 0; o >>= 1) {
+        sg += __shfl_xor_sync(0xFFFFFFFFu, sg, o);
+        ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+        sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+        sS += __shfl_xor_sync(0xFFFFFFFFu, sS, o);
+        sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    }
+    if (lane == 0) {
+        const double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
+        const double sd = v.sigma_d;
+        dens[a] = sd * sg;
+        dens[(size_t)n + a] = sd * ss;  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
+        dens[2 * (size_t)n + a] = sd * sb;
+        dens[3 * (size_t)n + a] = sd * sS;
+        dens[4 * (size_t)n + a] = sd * sq;
+        dens[5 * (size_t)n + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+        nnb[a] = c;
+        atomicAdd(&v.sc->pairs, (unsigned long long)c);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -104,6 +160,11 @@ __device__ void an_eval(const EosDev &E, double T, const double *mu, double &p, 
     }
 }
 
+// work counters of one inversion (reported as algorithmic work by the benchmark)
+struct EosWork {
+    unsigned resid, solve, g;
+};
+
 // g(T) = s(T, mu(T)) - s_target with mu_q(T) = n_q/(chi_q T^2)
 __device__ __forceinline__ void an_g(const EosDev &E, double T, double s, double c, double &g, double &gp)
 {
@@ -114,7 +175,7 @@ __device__ __forceinline__ void an_g(const EosDev &E, double T, double s, double
     gp = 12.0 * T2 * f + 8.0 * T3 * fp + T4 * fpp - 3.0 * c / T4;
 }
 
-__device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double &T, double *mu)
+__device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double &T, double *mu, EosWork &w)
 {
     if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) return PST_NONFINITE | PST_NOCONV;
     if (!(s > 0.0)) return PST_NOCONV;
@@ -126,6 +187,7 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
     double Thi = cbrt(s / (4.0 * E.a0));
     double g, gp;
     an_g(E, Thi, s, c, g, gp);
+    ++w.g;
     double Tlo = Thi;
     if (g > 0.0) {
         double gprev = g;
@@ -134,6 +196,7 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
             Tlo *= 0.8;
             double gl, gpl;
             an_g(E, Tlo, s, c, gl, gpl);
+            ++w.g;
             if (gl <= 0.0) {
                 found = true;
                 break;
@@ -146,6 +209,7 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
     double t = Thi;
     for (int it = 0; it < 200; ++it) {
         an_g(E, t, s, c, g, gp);
+        ++w.g;
         if (g == 0.0) break;
         if (g > 0.0) Thi = t;
         else Tlo = t;
@@ -227,38 +291,52 @@ __device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double 
     if (p) *p = pv;
 }
 
-// Gaussian elimination with partial pivoting on an m x m system (m <= 4)
-__device__ bool solve_small(int m, double A[4][4], double b[4])
+// 4x4 Gaussian elimination with partial pivoting, fully unrolled so every index is a
+// compile-time constant and the system stays in registers.  Row swaps are conditional
+// moves.  Returns false on a zero or non-finite pivot.
+__device__ __forceinline__ bool solve4(double A[4][4], double b[4])
 {
-    for (int c = 0; c < m; ++c) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
         int piv = c;
         double best = fabs(A[c][c]);
-        for (int r = c + 1; r < m; ++r)
-            if (fabs(A[r][c]) > best) {
-                best = fabs(A[r][c]);
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            double v = fabs(A[r][c]);
+            if (v > best) {
+                best = v;
                 piv = r;
             }
+        }
         if (!(best > 0.0) || !isfinite(best)) return false;
-        if (piv != c) {
-            for (int k = 0; k < 4; ++k) {
-                double t = A[c][k];
-                A[c][k] = A[piv][k];
-                A[piv][k] = t;
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            if (piv == r) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double t = A[c][k];
+                    A[c][k] = A[r][k];
+                    A[r][k] = t;
+                }
+                double t = b[c];
+                b[c] = b[r];
+                b[r] = t;
             }
-            double t = b[c];
-            b[c] = b[piv];
-            b[piv] = t;
         }
         double inv = 1.0 / A[c][c];
-        for (int r = c + 1; r < m; ++r) {
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
             double f = A[r][c] * inv;
-            for (int k = c; k < m; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
+#pragma unroll
+            for (int k = c; k < 4; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
             b[r] = fma(-f, b[c], b[r]);
         }
     }
-    for (int r = m - 1; r >= 0; --r) {
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
         double acc = b[r];
-        for (int k = r + 1; k < m; ++k) acc = fma(-A[r][k], b[k], acc);
+#pragma unroll
+        for (int k = r + 1; k < 4; ++k) acc = fma(-A[r][k], b[k], acc);
         b[r] = acc / A[r][r];
     }
     return true;
@@ -285,40 +363,43 @@ __device__ double resid(const EosDev &E, const double *x, double s, const double
     return m;
 }
 
-__device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x)
+// Damped Newton on the table interpolant.  The Jacobian is factorised in place (it is
+// not needed after the step); each line-search trial overwrites r and J with their values
+// at the trial point, so the accepted point's residual and Jacobian are ready for the
+// next iteration (the same sequence as a copy-on-accept scheme, with fewer registers).
+__device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x, EosWork &w)
 {
     double r[4], J[4][4];
     double rn = resid(E, x, s, n, r, J);
+    ++w.resid;
     for (int it = 0; it < E.maxit; ++it) {
-        double A[4][4], d[4];
-        for (int i = 0; i < 4; ++i) {
-            d[i] = -r[i];
-            for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
-        }
+        double d[4] = {-r[0], -r[1], -r[2], -r[3]};
         if (rn <= E.tol) {
-            if (solve_small(4, A, d)) {  // one polishing step if it does not increase the residual
-                double xn[4], rr[4], Jn[4][4];
-                for (int k = 0; k < 4; ++k) xn[k] = x[k] + d[k];
+            ++w.solve;
+            if (solve4(J, d)) {  // one polishing step if it does not increase the residual
+                double xn[4] = {x[0] + d[0], x[1] + d[1], x[2] + d[2], x[3] + d[3]};
                 clamp4(E, xn);
-                if (resid(E, xn, s, n, rr, Jn) <= rn)
+                ++w.resid;
+                if (resid(E, xn, s, n, r, J) <= rn)
+#pragma unroll
                     for (int k = 0; k < 4; ++k) x[k] = xn[k];
             }
             return true;
         }
-        if (!solve_small(4, A, d)) return false;
-        double lam = 1.0, xn[4], rr[4], Jn[4][4], rnn = 0.0;
+        ++w.solve;
+        if (!solve4(J, d)) return false;
+        double lam = 1.0, xn[4], rnn = 0.0;
         for (int ls = 0; ls <= 8; ++ls) {
+#pragma unroll
             for (int k = 0; k < 4; ++k) xn[k] = fma(lam, d[k], x[k]);
             clamp4(E, xn);
-            rnn = resid(E, xn, s, n, rr, Jn);
+            rnn = resid(E, xn, s, n, r, J);
+            ++w.resid;
             if (rnn < rn) break;
             lam *= 0.5;
         }
-        for (int k = 0; k < 4; ++k) {
-            x[k] = xn[k];
-            r[k] = rr[k];
-            for (int j = 0; j < 4; ++j) J[k][j] = Jn[k][j];
-        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = xn[k];
         rn = rnn;
     }
     return rn <= E.tol;
@@ -329,63 +410,94 @@ struct EosOut {
     uint32_t st;
 };
 
-__device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const double *n)
+__device__ __forceinline__ bool inside_table(const EosDev &E, const double *x)
+{
+    bool in = x[0] >= E.T0 && x[0] <= E.Tmax;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) in = in && x[1 + q] >= E.mu0[q] && x[1 + q] <= E.mumax[q];
+    return in;
+}
+
+// guess: this particle's table solution of the previous stage (T <= 0: none).  Attempts:
+// table Newton from the guess; else the closed form, then table Newton from it; else the
+// closed form (flagged).  used_table tells whether the table produced the result.
+__device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const double *n, const double *guess,
+                             bool &used_table, EosWork &w)
 {
     EosOut o;
     o.T = 0.0;
     for (int q = 0; q < 3; ++q) o.mu[q] = 0.0, o.pn[q] = 0.0;
     o.p = o.e = o.ps = o.cs2 = 0.0;
+    o.st = 0u;
+    used_table = false;
+    if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) {
+        o.st = PST_NONFINITE | PST_NOCONV;
+        return o;
+    }
     double x[4];
-    o.st = an_invert(E, s, n, x[0], x + 1);
-    if (o.st) return o;
     bool use_table = false;
-    if (E.has_table) {
-        bool inside = x[0] >= E.T0 && x[0] <= E.Tmax;
-        for (int q = 0; q < 3; ++q) inside = inside && x[1 + q] >= E.mu0[q] && x[1 + q] <= E.mumax[q];
-        if (inside) {
-            double xt[4] = {x[0], x[1], x[2], x[3]};
-            if (tab_newton(E, s, n, xt)) {
-                for (int k = 0; k < 4; ++k) x[k] = xt[k];
-                use_table = true;
-            } else {
-                o.st |= PST_FALLBACK;
-            }
-        } else {
-            o.st |= PST_OUT_OF_TABLE;
+    if (E.has_table && guess[0] > 0.0 && inside_table(E, guess)) {
+        double xt[4] = {guess[0], guess[1], guess[2], guess[3]};
+        if (tab_newton(E, s, n, xt, w)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = xt[k];
+            use_table = true;
         }
     }
+    if (!use_table) {
+        o.st = an_invert(E, s, n, x[0], x + 1, w);
+        if (o.st) return o;
+        if (E.has_table) {
+            if (inside_table(E, x)) {
+                double xt[4] = {x[0], x[1], x[2], x[3]};
+                if (tab_newton(E, s, n, xt, w)) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x[k] = xt[k];
+                    use_table = true;
+                } else {
+                    o.st |= PST_FALLBACK;
+                }
+            } else {
+                o.st |= PST_OUT_OF_TABLE;
+            }
+        }
+    }
+    used_table = use_table;
     double p, H[4][4], sn[4];
     if (use_table) tab_eval(E, x, sn, H, &p);
     else an_eval(E, x[0], x + 1, p, sn, H);
     double e = x[0] * s + x[1] * n[0] + x[2] * n[1] + x[3] * n[2] - p;
-    // (p_s, p_n) = H^-T (s, n) over the directions the EoS couples to
-    int act[4], m = 0;
-    for (int k = 0; k < 4; ++k)
-        if (k == 0 || use_table || E.chi[k - 1] > 0.0) act[m++] = k;
-    double A[4][4], z[4];
-    double tgt[4] = {s, n[0], n[1], n[2]};
+    // (p_s, p_n) = H^-T (s, n) over the directions the EoS couples to; an uncoupled charge
+    // direction (no table, chi_q = 0) becomes an identity row with zero right-hand side
+    double A[4][4], z[4] = {s, n[0], n[1], n[2]};
+#pragma unroll
     for (int i = 0; i < 4; ++i) {
-        z[i] = i < m ? tgt[act[i]] : 0.0;
-        for (int j = 0; j < 4; ++j) A[i][j] = (i < m && j < m) ? H[act[j]][act[i]] : 0.0;
+        const bool act_i = i == 0 || use_table || E.chi[i - 1] > 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool act_j = j == 0 || use_table || E.chi[j - 1] > 0.0;
+            A[i][j] = (act_i && act_j) ? H[j][i] : (i == j ? 1.0 : 0.0);
+        }
+        if (!act_i) z[i] = 0.0;
     }
-    if (!solve_small(m, A, z)) {
+    ++w.solve;
+    if (!solve4(A, z)) {
         o.st |= PST_NOCONV;
         return o;
     }
-    double zz[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = 0; i < m; ++i) zz[act[i]] = z[i];
-    double cs2 = (s * zz[0] + n[0] * zz[1] + n[1] * zz[2] + n[2] * zz[3]) / (e + p);
+    double cs2 = (s * z[0] + n[0] * z[1] + n[1] * z[2] + n[2] * z[3]) / (e + p);
     if (cs2 > cs2_cap) {
         double f = cs2_cap / cs2;
-        for (int k = 0; k < 4; ++k) zz[k] *= f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) z[k] *= f;
         cs2 = cs2_cap;
         o.st |= PST_CS2_CAPPED;
     }
     o.T = x[0];
-    for (int q = 0; q < 3; ++q) o.mu[q] = x[1 + q], o.pn[q] = zz[1 + q];
+    for (int q = 0; q < 3; ++q) o.mu[q] = x[1 + q], o.pn[q] = z[1 + q];
     o.p = p;
     o.e = e;
-    o.ps = zz[0];
+    o.ps = z[0];
     o.cs2 = cs2;
     return o;
 }
@@ -393,15 +505,17 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
 // EoS pass, 2+1D: rest-frame densities, inversion, and the per-particle inputs of the
 // gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{tau i},
 // and u^j / sigma*; plus the longitudinal work rate (p + Pi + tau^2 pi^{eta eta}) / sigma*
-__global__ void __launch_bounds__(128) k_eos2(EvView v, int stage, const double *__restrict__ y,
-                                              double *__restrict__ dens, double *__restrict__ eos,
-                                              double *__restrict__ gin, uint32_t *__restrict__ status,
-                                              double *__restrict__ wpart)
+__global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const double *__restrict__ y,
+                                             double *__restrict__ dens, double *__restrict__ eos,
+                                             double *__restrict__ gin, uint32_t *__restrict__ status,
+                                             double *__restrict__ wpart, const double *__restrict__ guess_in,
+                                             double *__restrict__ guess_out)
 {
-    __shared__ double red[4];
+    __shared__ double red[2];
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = v.n;
     double wcontrib = 0.0;
+    unsigned wres = 0u, wsol = 0u, wg = 0u;
     if (a < n) {
         double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
         double sqrtg = v.milne ? tau : 1.0;
@@ -412,7 +526,18 @@ __global__ void __launch_bounds__(128) k_eos2(EvView v, int stage, const double 
         double nq[3] = {dens[2 * (size_t)n + a] / vol, dens[3 * (size_t)n + a] / vol, dens[4 * (size_t)n + a] / vol};
         dens[(size_t)n + a] = s;
         for (int q = 0; q < 3; ++q) dens[(2 + q) * (size_t)n + a] = nq[q];
-        EosOut o = eos_invert(v.eos, v.tr.cs2_cap, s, nq);
+        double gs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gs[k] = guess_in[(size_t)k * n + a];
+        bool used = false;
+        EosWork w = {0u, 0u, 0u};
+        EosOut o = eos_invert(v.eos, v.tr.cs2_cap, s, nq, gs, used, w);
+        wres = w.resid + 1u;  // + the final evaluation of p, (s, n) and H at the solution
+        wsol = w.solve;
+        wg = w.g;
+        guess_out[a] = used ? o.T : 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) guess_out[(size_t)(1 + q) * n + a] = used ? o.mu[q] : 0.0;
         status[a] = o.st;
         warp_or(&v.sc->status_or, o.st);
         eos[a] = o.T;
@@ -448,11 +573,19 @@ __global__ void __launch_bounds__(128) k_eos2(EvView v, int stage, const double 
             wcontrib = (P + t2pee) / sig_star;
         }
     }
-    // deterministic block sum of the work rate
+    // work counters (warp-aggregated) and the deterministic block sum of the work rate
+    wres = __reduce_add_sync(0xFFFFFFFFu, wres);
+    wsol = __reduce_add_sync(0xFFFFFFFFu, wsol);
+    wg = __reduce_add_sync(0xFFFFFFFFu, wg);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&v.sc->eos_resid, (unsigned long long)wres);
+        atomicAdd(&v.sc->eos_solve, (unsigned long long)wsol);
+        atomicAdd(&v.sc->eos_g, (unsigned long long)wg);
+    }
     for (int o = 16; o > 0; o >>= 1) wcontrib += __shfl_xor_sync(0xFFFFFFFFu, wcontrib, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wcontrib;
     __syncthreads();
-    if (threadIdx.x == 0) wpart[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+    if (threadIdx.x == 0) wpart[blockIdx.x] = red[0] + red[1];
 }
 
 inline int nblk(int n, int t) { return (n + t - 1) / t; }
@@ -462,15 +595,17 @@ inline int nblk(int n, int t) { return (n + t - 1) / t; }
 void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                     cudaStream_t st)
 {
-    k_density2<<<nblk(v.n, 128), 128, 0, st>>>(v, y, Nq, cb.start, cb.cnt, dens, nnb);
+    k_fpos<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos);
+    k_density2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb);
 }
 
 void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
-                uint32_t *status, double *wpart, cudaStream_t st)
+                uint32_t *status, double *wpart, const double *guess_in, double *guess_out, cudaStream_t st)
 {
-    k_eos2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart);
+    k_eos2<<<nblk(v.n, 64), 64, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart, guess_in,
+                                         guess_out);
 }
 
-int eom_block_count(int n) { return nblk(n, 128); }
+int eom_block_count(int n) { return nblk(n, 64); }
 
 }  // namespace sphg

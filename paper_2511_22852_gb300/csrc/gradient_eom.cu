@@ -24,62 +24,108 @@ namespace sphg {
 
 namespace {
 
-__global__ void __launch_bounds__(128) k_gradient2(EvView v, int stage, const double *__restrict__ y,
-                                                   const double *__restrict__ gin, const uint32_t *__restrict__ start,
-                                                   const uint32_t *__restrict__ cnt, double *__restrict__ gout)
+constexpr int kWarps = 4;  // warps (particles in flight) per block
+
+// Gradient pass, one warp per particle: single-precision prefilter of the candidates in
+// the 3x3 cells, ballot-compaction of the survivors into a per-warp queue, the exact FP64
+// test and the pair arithmetic 32 pairs at a time on full warps, then a fixed-order
+// butterfly reduction of the per-lane partial sums.
+__global__ void __launch_bounds__(32 * kWarps) k_gradient2(EvView v, int stage, const double *__restrict__ y,
+                                                           const float2 *__restrict__ fpos,
+                                                           const double *__restrict__ gin,
+                                                           const uint32_t *__restrict__ start,
+                                                           const uint32_t *__restrict__ cnt, double *__restrict__ gout)
 {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= v.n) return;
+    __shared__ int queue[kWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarps + wid;
+    if (a >= v.n) return;  // warp-uniform
+    int *q = queue[wid];
     const int n = v.n;
     const double *X = y, *Y = y + n;
     const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
     const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
-    double xa = X[a], ya = Y[a];
-    double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
-    int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
-    int lim = 1 << v.B;
+    const double xa = X[a], ya = Y[a];
+    const float2 fa = fpos[a];
+    const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+    const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+    const int lim = 1 << v.B;
+    const unsigned lt = (1u << lane) - 1u;
     double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
     double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
+    int qn = 0;
+    auto pair = [&](int b) {
+        const double dx = xa - X[b], dy = ya - Y[b];
+        const double r2 = dist2_2d(dx, dy);
+        if (r2 < v.supp2 && r2 > 0.0) {
+            const double ir = rsqrt_nr(r2);
+            const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;  // (dW/dr)/r without sigma_d/h
+            const double gx = fac * dx, gy = fac * dy;
+            Gx += gx;
+            Gy += gy;
+            Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));
+            Hy = fma(Xxy[b], gx, fma(Xyy[b], gy, Hy));
+            const double ubx = Ux[b], uby = Uy[b];
+            dxux = fma(ubx, gx, dxux);
+            dxuy = fma(uby, gx, dxuy);
+            dyux = fma(ubx, gy, dyux);
+            dyuy = fma(uby, gy, dyuy);
+        }
+    };
     for (int oy = -1; oy <= 1; ++oy) {
-        int ny = cy + oy;
+        const int ny = cy + oy;
         if (ny < 0 || ny >= lim) continue;
         for (int ox = -1; ox <= 1; ++ox) {
-            int nx = cx + ox;
+            const int nx = cx + ox;
             if (nx < 0 || nx >= lim) continue;
-            uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
-            uint32_t b0 = start[k], b1 = b0 + cnt[k];
-            for (uint32_t b = b0; b < b1; ++b) {
-                double dx = xa - X[b], dy = ya - Y[b];
-                double r2 = dist2_2d(dx, dy);
-                if (r2 < v.supp2 && r2 > 0.0) {
-                    double ir = rsqrt_nr(r2);
-                    double q = r2 * ir * v.inv_h;
-                    double fac = kernel_dw(q) * ir;  // (dW/dr)/r without sigma_d/h
-                    double gx = fac * dx, gy = fac * dy;
-                    Gx += gx;
-                    Gy += gy;
-                    Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));
-                    Hy = fma(Xxy[b], gx, fma(Xyy[b], gy, Hy));
-                    double ubx = Ux[b], uby = Uy[b];
-                    dxux = fma(ubx, gx, dxux);
-                    dxuy = fma(uby, gx, dxuy);
-                    dyux = fma(ubx, gy, dyux);
-                    dyuy = fma(uby, gy, dyuy);
+            const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+            const uint32_t b0 = start[k], b1 = b0 + cnt[k];
+            for (uint32_t base = b0; base < b1; base += 32) {
+                const uint32_t b = base + lane;
+                bool cand = false;
+                if (b < b1) {
+                    const float2 fb = fpos[b];
+                    const float dx = fa.x - fb.x, dy = fa.y - fb.y;
+                    cand = fmaf(dx, dx, dy * dy) <= v.supp2_hi;
+                }
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+                if (cand) q[qn + __popc(m & lt)] = (int)b;
+                qn += __popc(m);
+                __syncwarp();
+                if (qn >= 32) {
+                    pair(q[lane]);
+                    qn -= 32;
+                    __syncwarp();
+                    if (lane < qn) q[lane] = q[32 + lane];
+                    __syncwarp();
                 }
             }
         }
     }
-    double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-    double sqrtg = v.milne ? tau : 1.0;
-    double c = v.sigma_d * v.inv_h;
-    gout[a] = c * dxux;
-    gout[(size_t)n + a] = c * dxuy;
-    gout[2 * (size_t)n + a] = c * dyux;
-    gout[3 * (size_t)n + a] = c * dyuy;
-    double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
-    double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
-    gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
-    gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+    if (lane < qn) pair(q[lane]);
+    for (int o = 16; o > 0; o >>= 1) {
+        Gx += __shfl_xor_sync(0xFFFFFFFFu, Gx, o);
+        Gy += __shfl_xor_sync(0xFFFFFFFFu, Gy, o);
+        Hx += __shfl_xor_sync(0xFFFFFFFFu, Hx, o);
+        Hy += __shfl_xor_sync(0xFFFFFFFFu, Hy, o);
+        dxux += __shfl_xor_sync(0xFFFFFFFFu, dxux, o);
+        dxuy += __shfl_xor_sync(0xFFFFFFFFu, dxuy, o);
+        dyux += __shfl_xor_sync(0xFFFFFFFFu, dyux, o);
+        dyuy += __shfl_xor_sync(0xFFFFFFFFu, dyuy, o);
+    }
+    if (lane == 0) {
+        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+        const double sqrtg = v.milne ? tau : 1.0;
+        const double c = v.sigma_d * v.inv_h;
+        gout[a] = c * dxux;
+        gout[(size_t)n + a] = c * dxuy;
+        gout[2 * (size_t)n + a] = c * dyux;
+        gout[3 * (size_t)n + a] = c * dyuy;
+        const double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
+        const double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
+        gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
+        gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, const double *__restrict__ ys,
@@ -300,7 +346,7 @@ inline int nblk(int n, int t) { return (n + t - 1) / t; }
 void launch_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
                      cudaStream_t st)
 {
-    k_gradient2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, y, gin, cb.start, cb.cnt, gout);
+    k_gradient2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout);
 }
 
 void launch_eom(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,

@@ -11,7 +11,7 @@
 // Limits and sharing rules:
 //   * at most kMaxParticles particles and 2^kMaxBits cells of side 2h per axis;
 //     larger inputs are rejected with SPH_ERR_ARG / SPH_ERR_STATE, never truncated;
-//   * every GPU that loads the library holds the array (9,699,584 bytes) until exit;
+//   * every GPU that loads the library holds the array (10,223,872 bytes) until exit;
 //   * all calls share the one array: calls that overlap on the GPU (two streams,
 //     two host threads) race on it -- serialise them;
 //   * the first call on a device looks up the array's device address (once per
@@ -45,7 +45,8 @@ constexpr size_t kOffCursor = align256(kOffStart + sizeof(uint32_t) * kBuckets);
 constexpr size_t kOffY = align256(kOffCursor + sizeof(uint32_t) * kBuckets);      // 5 rows: x, y, ux, uy, S
 constexpr size_t kOffNq = align256(kOffY + sizeof(double) * 5 * kMaxParticles);    // 3 rows
 constexpr size_t kOffDens = align256(kOffNq + sizeof(double) * 3 * kMaxParticles); // 6 rows
-constexpr size_t kScratchBytes = align256(kOffDens + sizeof(double) * 6 * kMaxParticles);
+constexpr size_t kOffFpos = align256(kOffDens + sizeof(double) * 6 * kMaxParticles);
+constexpr size_t kScratchBytes = align256(kOffFpos + sizeof(float2) * kMaxParticles);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -118,6 +119,7 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     cb.cnt = reinterpret_cast<uint32_t *>(b + kOffCnt);
     cb.start = reinterpret_cast<uint32_t *>(b + kOffStart);
     cb.cursor = reinterpret_cast<uint32_t *>(b + kOffCursor);
+    cb.fpos = reinterpret_cast<float2 *>(b + kOffFpos);
     cb.nb = kBuckets;
     int *id_in = reinterpret_cast<int *>(b + kOffIdIn);
     int *id_out = reinterpret_cast<int *>(b + kOffIdOut);
@@ -138,6 +140,7 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     double two_h = 2.0 * h;
     v.supp2 = two_h * two_h;
     v.inv_cell = 1.0 / (2.0 * h);
+    v.supp2_hi = prefilter_bound(h, kMaxBits);
     v.sigma_d = 10.0 / (7.0 * kPi * h * h);
     v.sc = sc;
 

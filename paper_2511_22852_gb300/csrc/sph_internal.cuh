@@ -9,6 +9,8 @@
 //   eos[11][n]    T, mu_B, mu_S, mu_Q, p, e, p_s, p_nB, p_nS, p_nQ, c_s^2
 //   gin[6][n]     X^{ji}/sigma*^2 (xx, xy, yx, yy), u^x/sigma*, u^y/sigma*
 //   gout[6][n]    d_x u^x, d_x u^y, d_y u^x, d_y u^y, F^x, F^y  (gradient pass)
+//   guess[4][n]   warm start of the EoS Newton: the particle's previous table solution
+//                 (T, mu_B, mu_S, mu_Q), T = 0 when the table was not used
 // The bucket table of the cell list is indexed by the Morton key of the cell
 // coordinates (B bits per dimension, fixed at event creation).
 #pragma once
@@ -39,6 +41,9 @@ struct DevScalars {
     unsigned int err_flags;
     long long steps;
     unsigned long long pairs;  // accepted neighbour pairs (self included), summed over stages
+    // EoS work actually done, summed over stages: table residual+Jacobian evaluations,
+    // 4x4 solves, closed-form g(T) evaluations
+    unsigned long long eos_resid, eos_solve, eos_g;
 };
 
 struct EosDev {
@@ -61,6 +66,7 @@ struct TransportDev {
 struct EvView {
     int n, dim, milne, nv, B;
     double h, inv_h, supp2, inv_cell, sigma_d, dtau;
+    float supp2_hi;  // single-precision prefilter bound, >= (2h)^2 plus the worst rounding error
     DevScalars *sc;
     EosDev eos;
     TransportDev tr;
@@ -159,8 +165,29 @@ __device__ __forceinline__ void warp_or(unsigned int *dst, unsigned int v)
 // launchers (implemented in cells.cu, density_eos.cu, gradient_eom.cu)
 struct CellBufs {
     uint32_t *key, *cnt, *start, *cursor, *tmp, *perm;
-    int nb;  // number of buckets = 1 << (dim * B)
+    float2 *fpos;  // sorted positions relative to the bounding-box minimum, single precision
+    int nb;        // number of buckets = 1 << (dim * B)
 };
+
+// Bound for the single-precision candidate prefilter of the neighbour passes.  With
+// positions p = fl(x - xmin) in [0, L], L = 2^B * 2h (beyond it the cell table overflows
+// and the step fails), |fl(p) - p| <= L u and |fl(pa - pb) - (pa - pb)| <= 2 L u + 4h u
+// (u = 2^-24); for a true neighbour (|dx_d| <= 2h) the squared distance summed over two
+// axes then errs by at most 4 (2h) e + 2 e^2 + 4 u (2h)^2 with e the difference error.
+// Twice that margin is added, so the prefilter never rejects a pair the exact
+// double-precision test r^2 < (2h)^2 accepts; the exact test decides every pair.
+inline float prefilter_bound(double h, int B)
+{
+    const double u = 1.0 / 16777216.0;
+    const double two_h = 2.0 * h;
+    const double L = (double)(1 << B) * two_h;
+    const double e = 2.0 * L * u + 2.0 * two_h * u + L * u;
+    const double err = 4.0 * two_h * e + 2.0 * e * e + 4.0 * u * two_h * two_h;
+    const double hi = two_h * two_h + 2.0 * err;
+    float f = (float)hi;
+    while ((double)f < hi) f = nextafterf(f, 1e30f);
+    return f;
+}
 
 void launch_bbox(const EvView &v, const double *y, cudaStream_t st);
 void launch_cells(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st);
@@ -169,7 +196,7 @@ void launch_permute(const EvView &v, const uint32_t *perm, const double *const *
 void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                     cudaStream_t st);
 void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
-                uint32_t *status, double *wpart, cudaStream_t st);
+                uint32_t *status, double *wpart, const double *guess_in, double *guess_out, cudaStream_t st);
 void launch_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
                      cudaStream_t st);
 // mode 0: y1 = y + dt f(y); mode 1: y0 = ((y0 + y1) + dt f(y1)) / 2 in place; mode 2: rates only

@@ -219,22 +219,37 @@ def test_resume_from_read_state_is_bitwise(Bd):
     ref = a.read()
     b = Bd.GpuEvent(ev)
     b.step(5, sync=True)
-    mid = b.read()
+    mid = b.read(("X", "U", "S", "NQ", "BV", "PV", "GUESS"))
     tau_mid = b.totals()["tau"]
+    assert np.all(mid["GUESS"][0] > 0)  # every particle's EoS came from the table
     ev2 = CASES["bsq_small"]()
     ev2.x, ev2.u, ev2.S, ev2.Bv, ev2.Pv, ev2.tau0 = mid["X"], mid["U"], mid["S"], mid["BV"], mid["PV"], tau_mid
     c = Bd.GpuEvent(ev2)
+    c.write_state(guess=mid["GUESS"])  # the EoS warm start is part of the evolved state
     c.step(5, sync=True)
     out = c.read()
     for k in ref:
         assert np.array_equal(out[k], ref[k]), k
     # write_state into an existing event gives the same
-    b.write_state(x=mid["X"], u=mid["U"], S=mid["S"], Bv=mid["BV"], Pv=mid["PV"])
+    b.write_state(x=mid["X"], u=mid["U"], S=mid["S"], Bv=mid["BV"], Pv=mid["PV"], guess=mid["GUESS"])
     b.step(5, sync=True)
     for k, v in b.read().items():
         assert np.array_equal(v, ref[k]), k
     for e in (a, b, c):
         e.free()
+
+
+def test_warm_start_matches_oracle_over_steps(Bd):
+    """The carried EoS warm start: after several steps the GPU guess equals the oracle's."""
+    ev = CASES["bsq_small"]()
+    g = Bd.GpuEvent(ev)
+    g.step(3, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(3)
+    gs = g.read(("GUESS",))["GUESS"]
+    assert np.array_equal(gs[0] > 0, run.guess[0] > 0)
+    assert relerr(gs, run.guess) < TOL_STEP
+    g.free()
 
 
 def test_edge_cases_and_errors(Bd):

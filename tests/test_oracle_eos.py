@@ -170,3 +170,28 @@ def test_acausal_band_is_capped(bsq):
     _, sn, _ = O.eos_analytic(P, T, np.zeros(3))
     out, st = O.eos_invert(P, sn[0], [0, 0, 0])
     assert not st & O.ST_CS2_CAPPED and 0.3 < out[10] < 0.6
+
+
+def test_warm_started_inversion_reaches_the_same_root(bsq):
+    """Newton from the previous stage's solution converges to the root the cold
+    start (closed form, then table) finds; a guess outside the table falls back to the cold path."""
+    import ctypes as C
+    ev, P, _ = bsq
+    t = ev.table
+    rng = np.random.default_rng(9)
+    for _ in range(30):
+        T = t.T0 + rng.uniform(3, t.nT - 4) * t.dT
+        mu = rng.uniform(-0.2, 0.2, 3) * T
+        p, sn, _ = O.eos_table(P, np.array([T, *mu]))
+        cold, st = O.eos_invert(P, sn[0], sn[1:])
+        guess = np.array([T * (1 + rng.uniform(-0.02, 0.02)), *(mu + rng.uniform(-0.02, 0.02, 3) * T)])
+        for gs in [guess, np.array([t.T0 * 0.5, 0, 0, 0]), np.zeros(4)]:
+            out = np.zeros(11)
+            used = C.c_int(0)
+            nn = np.ascontiguousarray(sn[1:])
+            st2 = O.lib().oc_eos_invert_ws(C.byref(P), float(sn[0]), nn.ctypes.data_as(C.c_void_p),
+                                           gs.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p),
+                                           C.byref(used))
+            assert used.value == 1 and st2 == st
+            assert np.all(np.abs(out[:4] - cold[:4]) <= 1e-13 * T)
+            assert abs(out[4] / cold[4] - 1) < 1e-13
