@@ -107,6 +107,28 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
+def combine_ranks(dev_ms: float, units: float, device=None):
+    """(max over ranks of the timed device milliseconds, sum over ranks of the particle-steps).
+
+    Replicas: every rank advances its own event, so the job's work is the sum and its time the
+    slowest rank's.  Without an initialised process group this is the identity."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(dev_ms), float(units)
+    t = torch.tensor([float(dev_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def replica_event(rank: int):
+    """The event of one rank: the 40k-particle viscous BSQ workload with rank-shifted seeds."""
+    from paper_2511_22852_gb300 import inputs as I
+    return I.viscous_bsq_2p1(seed_hot=1 + 1000 * rank, seed_charge=2 + 1000 * rank)
+
+
 def cpu_baseline(ev, target_s=15.0):
     """The CPU oracle, as it stands, on a bounded sample: whole Heun steps of the same event."""
     from oracle import oracle as O
@@ -168,7 +190,7 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     # one independent event per rank (replicas): rank r uses hotspot/charge seeds shifted by r
-    ev = I.viscous_bsq_2p1(seed_hot=1 + 1000 * rank, seed_charge=2 + 1000 * rank)
+    ev = replica_event(rank)
     stream = torch.cuda.Stream()
     g = Bd.GpuEvent(ev, use_graph=True, stream=stream.cuda_stream)
     for _ in range(args.warmup):
@@ -210,15 +232,7 @@ def run_ours(args):
     status_or = t_after["status_or"]
     clocks = clk.summary()
 
-    tt = torch.tensor([dev_ms, float(ev.n * args.steps)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        mx = tt[:1].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt[1:].clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        dev_ms_max, units = float(mx.item()), float(sm.item())
-    else:
-        dev_ms_max, units = dev_ms, float(ev.n * args.steps)
+    dev_ms_max, units = combine_ranks(dev_ms, float(ev.n * args.steps), device="cuda")
     value = units / (dev_ms_max / 1e3)
 
     out = None
