@@ -108,12 +108,13 @@ void sph_free_eos(sph_eos *eos);
  *
  * Coordinates: milne = 1 is (tau, x, y, eta) with sqrt(-g) = tau, milne = 0 is
  * Cartesian (t, x, y, z).  dim = 2 is transverse (x, y) only (with milne = 1:
- * boost-invariant 2+1D).  This version implements dim = 2; other values return
- * SPH_ERR_ARG.
+ * boost-invariant 2+1D); dim = 3 adds eta (Milne, distances Euclidean in (x, y, eta))
+ * or z.  Other values return SPH_ERR_ARG.
  *
  * Arrays (SoA, doubles): x[dim*n] (x^1 for all particles, then x^2, ...),
  * u[dim*n] (contravariant u^i), S[n], Nq[3*n] (B, S, Q), Bv[n] = Pi/sigma (may be
- * NULL: zero), Pv[npi*n] = pi^{ij}/sigma for (xx, xy, yy) when dim = 2 (may be
+ * NULL: zero), Pv[npi*n] = pi^{ij}/sigma for (xx, xy, yy) when dim = 2 (npi = 3) and
+ * (xx, xy, x3, yy, y3) when dim = 3 (npi = 5; pi^{33} follows from tracelessness) (may be
  * NULL: zero).  Host pointers, or device pointers when on_device = 1 (for example
  * torch tensors' data_ptr()).  The library copies them; the caller keeps them.
  *
@@ -135,11 +136,20 @@ typedef struct {
     int32_t use_graph; /* 1: replay sph_step through a captured CUDA graph */
     void *stream;
     int32_t profile;   /* 1: time every kernel group with CUDA events (no graph; see sph_kernel_times) */
-    int32_t pad;
+    int32_t precision; /* SPH_FP64 or SPH_MIXED (see below) */
 } sph_event_desc;
 
+/* Precision of the step.  SPH_FP64: every operation in double precision.  SPH_MIXED (dim = 2):
+ * the neighbour passes (kernel sums and gradients) run in single precision with positions
+ * relative to their cell's origin and compensated (two-sum) accumulation, combined in double
+ * precision per particle; the neighbour set stays exactly that of the FP64 test (a proven float
+ * error band, the FP64 test inside it); the EoS inversion, equations of motion, Heun update and
+ * reductions stay FP64.  Results differ from SPH_FP64 at the ~1e-7 relative level. */
+#define SPH_FP64 0
+#define SPH_MIXED 1
+
 /* Copies the particles to device memory (sorted by cell on the first stage) and
- * binds the EoS.  Errors: SPH_ERR_ARG (n < 0, h <= 0, dtau <= 0, dim != 2, null
+ * binds the EoS.  Errors: SPH_ERR_ARG (n < 0, h <= 0, dtau <= 0, dim not 2 or 3, null
  * arrays for n > 0), SPH_ERR_OOM, SPH_ERR_CUDA.  n = 0 gives an empty event on
  * which every call succeeds and does nothing. */
 sph_status sph_init_event(sph_event **out, const sph_event_desc *desc, const sph_eos *eos);
@@ -205,6 +215,7 @@ typedef struct {
     int64_t kernel_launches; /* kernels launched by sph_step so far (graph replays included) */
     int64_t eos_work[3];     /* EoS work done: table residual+Jacobian evaluations, 4x4 solves,
                                 closed-form evaluations (all stages and read-outs) */
+    int64_t shell_tests;     /* SPH_MIXED: candidates decided by the exact FP64 test */
 } sph_totals;
 
 sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *out, sph_totals *tot);
@@ -251,7 +262,7 @@ sph_status sph_debug_neighbors(sph_event *ev, int64_t cap, int32_t *pa, int32_t 
 
 /* Test support: one right-hand-side evaluation at the current state, without
  * advancing it.  rates[nv*n] (nv = 2 dim + 2 + npi) and grad[(dim*dim + dim)*n]
- * (d_k u^j, then F^i) in original order, host buffers; either may be NULL. */
+ * (d_k u^j with k major, then F^i) in original order, host buffers; either may be NULL. */
 sph_status sph_debug_rates(sph_event *ev, double *rates, double *grad);
 
 #ifdef __cplusplus

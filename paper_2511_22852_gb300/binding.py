@@ -25,6 +25,7 @@ STATUS_NAMES = ["SPH_OK", "SPH_ERR_ARG", "SPH_ERR_OOM", "SPH_ERR_CUDA", "SPH_ERR
                 "SPH_ERR_NONFINITE", "SPH_ERR_TIMEOUT", "SPH_ERR_STATE"]
 PST_FALLBACK, PST_OUT_OF_TABLE, PST_NOCONV, PST_NONFINITE, PST_CS2_CAPPED, PST_SOLVE_FAIL = 1, 2, 4, 8, 16, 32
 SPH_SYNC = 1
+SPH_FP64, SPH_MIXED = 0, 1
 
 F = {name: 1 << i for i, name in enumerate(
     ["X", "U", "S", "NQ", "BV", "PV", "SIGMA_STAR", "S_DENS", "N_DENS", "T", "MU", "P", "E", "PI_BULK", "STATUS",
@@ -55,7 +56,7 @@ class EventDesc(C.Structure):
                 ("Pv", C.c_void_p), ("eta_over_s", C.c_double), ("zeta_peak", C.c_double),
                 ("zeta_T_GeV", C.c_double), ("zeta_w_GeV", C.c_double), ("tau_pi_coef", C.c_double),
                 ("tau_Pi_ratio", C.c_double), ("cs2_cap", C.c_double), ("fatal_mask", C.c_uint32),
-                ("use_graph", C.c_int32), ("stream", C.c_void_p), ("profile", C.c_int32), ("pad", C.c_int32)]
+                ("use_graph", C.c_int32), ("stream", C.c_void_p), ("profile", C.c_int32), ("precision", C.c_int32)]
 
 
 class FieldBufs(C.Structure):
@@ -66,7 +67,8 @@ class FieldBufs(C.Structure):
 class Totals(C.Structure):
     _fields_ = [("tau", C.c_double), ("E", C.c_double), ("S", C.c_double), ("N", C.c_double * 3),
                 ("work", C.c_double), ("status_or", C.c_uint32), ("pad", C.c_int32), ("steps", C.c_int64),
-                ("pairs", C.c_int64), ("kernel_launches", C.c_int64), ("eos_work", C.c_int64 * 3)]
+                ("pairs", C.c_int64), ("kernel_launches", C.c_int64), ("eos_work", C.c_int64 * 3),
+                ("shell_tests", C.c_int64)]
 
 
 _lib = None
@@ -201,7 +203,8 @@ def eos_desc(eos, table=None, newton_tol=1e-12, newton_maxit=30):
 class GpuEvent:
     """One event on the GPU, built from an ``inputs.Event``."""
 
-    def __init__(self, ev, use_graph=True, fatal_mask=0, eos_handle=None, stream=None, profile=False):
+    def __init__(self, ev, use_graph=True, fatal_mask=0, eos_handle=None, stream=None, profile=False,
+                 precision=SPH_FP64):
         self.ev = ev
         self.dim, self.n = ev.dim, ev.n
         self.npi = 3 if ev.dim == 2 else 5
@@ -222,6 +225,7 @@ class GpuEvent:
         d.fatal_mask, d.use_graph = fatal_mask, int(use_graph)
         d.stream = stream
         d.profile = int(profile)
+        d.precision = int(precision)
         self.h = sph_init_event(d, self.eos)
 
     def step(self, nsteps: int, sync: bool = False):
@@ -250,7 +254,7 @@ class GpuEvent:
         sph_read_fields(self.h, 0, None, t)
         return {"tau": t.tau, "E": t.E, "S": t.S, "N": np.array(t.N[:]), "work": t.work,
                 "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs, "kernel_launches": t.kernel_launches,
-                "eos_work": tuple(t.eos_work[:])}
+                "eos_work": tuple(t.eos_work[:]), "shell_tests": t.shell_tests}
 
     def kernel_times(self):
         return sph_kernel_times(self.h)
@@ -264,7 +268,7 @@ class GpuEvent:
 
     def rates(self):
         r = np.zeros((self.nv, self.n))
-        g = np.zeros((6, self.n))
+        g = np.zeros((self.dim * self.dim + self.dim, self.n))
         sph_debug_rates(self.h, r, g)
         return r, g
 

@@ -50,6 +50,10 @@ struct sph_eos {
 struct sph_event {
     sph_eos *eos = nullptr;
     int n = 0, dim = 2, milne = 1, viscous = 0, npi = 3, nv = 9, B = 6;
+    int B3[3] = {0, 0, 0};          // 3D: cell-coordinate bits per axis
+    int ngin = kNGin, ngout = kNGout;  // rows of the gradient-pass inputs and outputs
+    std::vector<uint32_t> spread_host;
+    uint32_t *spread = nullptr;     // 3D: generalized Morton spread tables (3 x 1024)
     double h = 0.3, dtau = 0.01, tau0 = 0.0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -71,6 +75,7 @@ struct sph_event {
     double *tot = nullptr;      // totals scratch
     TransportDev tr{};
     uint32_t fatal_mask = 0;
+    int mixed = 0;
     bool use_graph = false, graph_ready = false, observed = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -105,12 +110,17 @@ static EvView make_view(const sph_event *ev)
     v.milne = ev->milne;
     v.nv = ev->nv;
     v.B = ev->B;
+    for (int d = 0; d < 3; ++d) v.B3[d] = ev->B3[d];
+    v.spread = ev->spread;
     v.h = ev->h;
     v.inv_h = 1.0 / ev->h;
     double two_h = 2.0 * ev->h;
     v.supp2 = two_h * two_h;
     v.inv_cell = 1.0 / (2.0 * ev->h);
-    v.supp2_hi = prefilter_bound(ev->h, ev->B);
+    v.supp2_hi = prefilter_bound(ev->h, ev->B, ev->dim);
+    v.mixed = ev->mixed;
+    v.cell_f = (float)(2.0 * ev->h);
+    mixed_shell(ev->h, v.shell_lo, v.shell_hi);
     v.sigma_d = ev->dim == 2 ? 10.0 / (7.0 * kPi * ev->h * ev->h) : 1.0 / (kPi * ev->h * ev->h * ev->h);
     v.dtau = ev->dtau;
     v.sc = ev->sc;
@@ -360,7 +370,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
 {
     if (!out || !d || !eos) return fail(SPH_ERR_ARG, "null argument");
     *out = nullptr;
-    if (d->dim != 2) return fail(SPH_ERR_ARG, "this version implements dim = 2");
+    if (d->dim != 2 && d->dim != 3) return fail(SPH_ERR_ARG, "dim must be 2 or 3");
     if (d->n < 0 || d->n > 0x7FFFFFFF) return fail(SPH_ERR_ARG, "n out of range");
     if (!(d->h > 0.0) || !(d->dtau > 0.0)) return fail(SPH_ERR_ARG, "h and dtau must be positive");
     if (d->milne && !(d->tau0 > 0.0)) return fail(SPH_ERR_ARG, "Milne coordinates need tau0 > 0");
@@ -375,12 +385,23 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     ev->dim = d->dim;
     ev->milne = d->milne ? 1 : 0;
     ev->viscous = d->viscous ? 1 : 0;
-    ev->npi = 3;
+    ev->npi = ev->dim == 2 ? 3 : 5;
     ev->nv = 2 * ev->dim + 2 + ev->npi;
+    ev->ngin = ev->dim == 2 ? kNGin : 12;
+    ev->ngout = ev->dim == 2 ? kNGout : 12;
     ev->h = d->h;
     ev->dtau = d->dtau;
     ev->tau0 = d->tau0;
     ev->fatal_mask = d->fatal_mask;
+    if (d->precision != SPH_FP64 && d->precision != SPH_MIXED) {
+        sph_free_event(ev);
+        return fail(SPH_ERR_ARG, "precision must be SPH_FP64 or SPH_MIXED");
+    }
+    if (d->precision == SPH_MIXED && d->dim != 2) {
+        sph_free_event(ev);
+        return fail(SPH_ERR_ARG, "the mixed-precision form is implemented for dim = 2");
+    }
+    ev->mixed = d->precision == SPH_MIXED ? 1 : 0;
     ev->profile = d->profile != 0;
     ev->use_graph = d->use_graph != 0 && !ev->profile;
     if (ev->profile) {
@@ -428,7 +449,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
             return bail(fail(SPH_ERR_ARG, "cannot read positions"));
         }
     }
-    int ncmax = 1;
+    int ncmax = 1, nc[3] = {1, 1, 1};
     for (int dd = 0; dd < ev->dim; ++dd) {
         double lo = INFINITY, hi = -INFINITY;
         for (int i = 0; i < n; ++i) {
@@ -437,13 +458,43 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
             lo = std::min(lo, xv);
             hi = std::max(hi, xv);
         }
-        if (n > 0) ncmax = std::max(ncmax, (int)std::floor((hi - lo) / (2.0 * ev->h)) + 1);
+        if (n > 0) nc[dd] = (int)std::floor((hi - lo) / (2.0 * ev->h)) + 1;
+        ncmax = std::max(ncmax, nc[dd]);
     }
-    int B = 3;
-    while ((1 << B) < 4 * ncmax && B < 15) ++B;
-    if ((1 << B) < ncmax) return bail(fail(SPH_ERR_ARG, "domain too large for the cell table"));
-    ev->B = B;
-    ev->cb.nb = 1 << (2 * B);
+    if (ev->dim == 2) {
+        int B = 3;
+        while ((1 << B) < 4 * ncmax && B < 15) ++B;
+        if ((1 << B) < ncmax) return bail(fail(SPH_ERR_ARG, "domain too large for the cell table"));
+        ev->B = B;
+        ev->cb.nb = 1 << (2 * B);
+    } else {
+        // per-axis bits: room for 4x the initial extent (2x when that exceeds 2^24 buckets)
+        for (int margin = 4; margin >= 1; margin /= 2) {
+            int tot = 0;
+            for (int dd = 0; dd < 3; ++dd) {
+                int b = 2;
+                while ((1 << b) < margin * nc[dd] && b < 10) ++b;
+                ev->B3[dd] = b;
+                tot += b;
+            }
+            if (tot <= 24 || margin == 1) break;
+        }
+        int tot = ev->B3[0] + ev->B3[1] + ev->B3[2];
+        for (int dd = 0; dd < 3; ++dd)
+            if ((1 << ev->B3[dd]) < nc[dd] || tot > 24) return bail(fail(SPH_ERR_ARG, "domain too large for the cell table"));
+        ev->B = std::max(ev->B3[0], std::max(ev->B3[1], ev->B3[2]));
+        ev->cb.nb = 1 << tot;
+        // generalized Morton key: bit b of axis d goes to the next free key bit, axes in turn
+        ev->spread_host.assign(3 * 1024, 0u);
+        int pos = 0;
+        for (int b = 0; b < 10; ++b)
+            for (int dd = 0; dd < 3; ++dd)
+                if (b < ev->B3[dd]) {
+                    for (int c = 0; c < (1 << ev->B3[dd]); ++c)
+                        if ((c >> b) & 1) ev->spread_host[(size_t)dd * 1024 + c] |= 1u << pos;
+                    ++pos;
+                }
+    }
     sph_status s;
 #define AL(ptr, bytes)                                                    \
     do {                                                                  \
@@ -461,14 +512,17 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     AL(ev->cb.key, sizeof(uint32_t) * N);
     AL(ev->cb.tmp, sizeof(uint32_t) * N);
     AL(ev->cb.perm, sizeof(uint32_t) * N);
-    AL(ev->cb.fpos, sizeof(float2) * N);
+    if (ev->dim == 2) AL(ev->cb.fpos, sizeof(float2) * N);
+    else AL(ev->cb.fpos3, sizeof(float4) * N);
+    AL(ev->cb.part, sizeof(uint32_t) * (size_t)(ev->cb.nb / 4096 + 2));
+    if (ev->dim == 3) AL(ev->spread, sizeof(uint32_t) * 3 * 1024);
     AL(ev->cb.cnt, sizeof(uint32_t) * (size_t)ev->cb.nb);
     AL(ev->cb.start, sizeof(uint32_t) * (size_t)ev->cb.nb);
     AL(ev->cb.cursor, sizeof(uint32_t) * (size_t)ev->cb.nb);
     AL(ev->dens, dv * kNDens);
     AL(ev->eosf, dv * kNEos);
-    AL(ev->gin, dv * kNGin);
-    AL(ev->gout, dv * kNGout);
+    AL(ev->gin, dv * ev->ngin);
+    AL(ev->gout, dv * ev->ngout);
     AL(ev->wguess, dv * 4);
     AL(ev->guess_in, dv * 4);
     AL(ev->wguess_obs, dv * 4);
@@ -476,7 +530,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     AL(ev->nnb, sizeof(int) * N);
     ev->nwblk = eom_block_count(n > 0 ? n : 1);
     AL(ev->wpart, sizeof(double) * (size_t)ev->nwblk);
-    AL(ev->scratch, dv * std::max(ev->nv, kNEos));
+    AL(ev->scratch, dv * std::max(std::max(ev->nv, kNEos), ev->ngout));
     AL(ev->ntot, sizeof(double) * (8 + 3 * 256));
     AL(ev->tot, sizeof(double) * (8 + 3 * 256));
 #undef AL
@@ -503,6 +557,8 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
         }
         launch_sum_fixed(ev->Nq_orig, n, 3, ev->ntot, st);
     }
+    if (ev->dim == 3)
+        CK(cudaMemcpyAsync(ev->spread, ev->spread_host.data(), sizeof(uint32_t) * 3 * 1024, cudaMemcpyHostToDevice, st));
     DevScalars hs;
     memset(&hs, 0, sizeof(hs));
     hs.tau = d->tau0;
@@ -674,6 +730,7 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         tot->eos_work[0] = (int64_t)hs.eos_resid;
         tot->eos_work[1] = (int64_t)hs.eos_solve;
         tot->eos_work[2] = (int64_t)hs.eos_g;
+        tot->shell_tests = (int64_t)hs.shell_tests;
         tot->kernel_launches = ev->launches;
     }
     return wait_stream(ev);
@@ -805,8 +862,8 @@ sph_status sph_debug_rates(sph_event *ev, double *rates, double *grad)
         if (s != SPH_OK) return s;
     }
     if (grad) {
-        launch_scatter_orig(ev->gout, ev->scratch, ev->id[1], n, kNGout, st);
-        sph_status s = copy_out(ev, grad, ev->scratch, sizeof(double) * kNGout * N, 0);
+        launch_scatter_orig(ev->gout, ev->scratch, ev->id[1], n, ev->ngout, st);
+        sph_status s = copy_out(ev, grad, ev->scratch, sizeof(double) * ev->ngout * N, 0);
         if (s != SPH_OK) return s;
     }
     return SPH_OK;

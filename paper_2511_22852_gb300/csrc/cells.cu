@@ -87,6 +87,95 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ cnt,
     }
 }
 
+// multi-block exclusive scan of large bucket tables: chunk sums, a scan of the chunk sums
+// (one block), then each chunk rescanned with its offset
+constexpr int kScanChunk = 4096;  // 256 threads x 16 buckets
+
+__global__ void __launch_bounds__(256) k_scan_part(const uint32_t *__restrict__ cnt, uint32_t *part, int nb)
+{
+    __shared__ uint32_t sh[256];
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * 16;
+    uint32_t acc = 0;
+    for (int k = 0; k < 16; ++k)
+        if (base + k < nb) acc += cnt[base + k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *part, int np)
+{
+    // np <= 4096: four consecutive values per thread, then a block scan of the thread sums
+    __shared__ uint32_t warp_tot[32];
+    const int t = threadIdx.x;
+    uint32_t v[4], local = 0;
+    for (int k = 0; k < 4; ++k) {
+        int i = 4 * t + k;
+        v[k] = i < np ? part[i] : 0u;
+        local += v[k];
+    }
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t up = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((t & 31) >= o) incl += up;
+    }
+    if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+    __syncthreads();
+    if (t < 32) {
+        uint32_t w = warp_tot[t], wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t up = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (t >= o) wi += up;
+        }
+        warp_tot[t] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[t >> 5] + incl - local;
+    for (int k = 0; k < 4; ++k) {
+        int i = 4 * t + k;
+        if (i < np) part[i] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ part,
+                                                    uint32_t *start, uint32_t *cursor, int nb)
+{
+    __shared__ uint32_t warp_tot[8];
+    const int t = threadIdx.x;
+    const int base = blockIdx.x * kScanChunk + t * 16;
+    uint32_t local = 0;
+    for (int k = 0; k < 16; ++k)
+        if (base + k < nb) local += cnt[base + k];
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t up = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((t & 31) >= o) incl += up;
+    }
+    if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+    __syncthreads();
+    if (t < 32) {
+        uint32_t w = t < 8 ? warp_tot[t] : 0u, wi = w;
+        for (int o = 1; o < 8; o <<= 1) {
+            uint32_t up = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (t >= o) wi += up;
+        }
+        if (t < 8) warp_tot[t] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = part[blockIdx.x] + warp_tot[t >> 5] + incl - local;
+    for (int k = 0; k < 16; ++k)
+        if (base + k < nb) {
+            start[base + k] = run;
+            cursor[base + k] = run;
+            run += cnt[base + k];
+        }
+}
+
 __global__ void k_scatter(int n, const uint32_t *__restrict__ key, uint32_t *cursor, uint32_t *tmp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,11 +315,24 @@ void launch_bbox(const EvView &v, const double *y, cudaStream_t st)
     k_bbox<<<blocks, 256, 0, st>>>(v, y);
 }
 
+void launch_scan_buckets(CellBufs cb, cudaStream_t st)
+{
+    if (cb.nb <= 65536 || !cb.part) {
+        k_scan<<<1, 1024, 0, st>>>(cb.cnt, cb.start, cb.cursor, cb.nb);
+    } else {
+        const int np = (cb.nb + kScanChunk - 1) / kScanChunk;
+        k_scan_part<<<np, 256, 0, st>>>(cb.cnt, cb.part, cb.nb);
+        k_scan_top<<<1, 1024, 0, st>>>(cb.part, np);
+        k_scan_apply<<<np, 256, 0, st>>>(cb.cnt, cb.part, cb.start, cb.cursor, cb.nb);
+    }
+}
+
 void launch_cells(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st)
 {
     cudaMemsetAsync(cb.cnt, 0, sizeof(uint32_t) * (size_t)cb.nb, st);
-    k_cells<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.key, cb.cnt);
-    k_scan<<<1, 1024, 0, st>>>(cb.cnt, cb.start, cb.cursor, cb.nb);
+    if (v.dim == 3) launch_cells3(v, y, id, cb, st);
+    else k_cells<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.key, cb.cnt);
+    launch_scan_buckets(cb, st);
     k_scatter<<<nblk(v.n, 256), 256, 0, st>>>(v.n, cb.key, cb.cursor, cb.tmp);
     k_rank<<<nblk(v.n, 128), 128, 0, st>>>(v.n, cb.key, cb.start, cb.cnt, cb.tmp, id, cb.perm);
 }
@@ -252,6 +354,10 @@ void launch_neighbors_list(const EvView &v, const double *y, const int *id, Cell
                            int *pa, int *pb, cudaStream_t st)
 {
     // offs == nullptr: pa receives the per-particle counts
+    if (v.dim == 3) {
+        launch_neighbors_list3(v, y, id, cb, offs, pa, pb, st);
+        return;
+    }
     k_neighbors<<<nblk(v.n, 128), 128, 0, st>>>(v, y, id, cb.start, cb.cnt, offs, offs ? nullptr : pa, pa, pb);
 }
 
@@ -272,6 +378,10 @@ void launch_scatter_orig_u32(const uint32_t *src, uint32_t *dst, const int *id, 
 
 void launch_cell_coords(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st)
 {
+    if (v.dim == 3) {
+        launch_cell_coords3(v, y, id, cell_orig, st);
+        return;
+    }
     k_cell_coords<<<nblk(v.n, 256), 256, 0, st>>>(v, y, id, cell_orig);
 }
 

@@ -1,0 +1,383 @@
+// eos_device.cuh -- device code of the EoS inversion (row a4), shared by the 2+1D and
+// 3+1D EoS passes: closed-form EoS, quadrilinear table interpolation with derivatives,
+// the damped table Newton, and the warm-started inversion (Sec. "EoS inverter").
+#pragma once
+#include "sph_internal.cuh"
+
+namespace sphg {
+namespace {
+
+// closed-form EoS
+__device__ __forceinline__ void an_shape(const EosDev &E, double T, double &f, double &fp, double &fpp)
+{
+    double k = kHbarc / E.w_GeV;
+    double th = tanh((T * kHbarc - E.Tc_GeV) / E.w_GeV);
+    double sech2 = fma(-th, th, 1.0);
+    f = E.a0 + 0.5 * E.a1 * (1.0 + th);
+    fp = 0.5 * E.a1 * sech2 * k;
+    fpp = -E.a1 * sech2 * th * k * k;
+}
+
+__device__ void an_eval(const EosDev &E, double T, const double *mu, double &p, double sn[4], double H[4][4])
+{
+    double f, fp, fpp;
+    an_shape(E, T, f, fp, fpp);
+    double cm2 = E.chi[0] * mu[0] * mu[0] + E.chi[1] * mu[1] * mu[1] + E.chi[2] * mu[2] * mu[2];
+    double T2 = T * T, T3 = T2 * T, T4 = T2 * T2;
+    p = T4 * f + 0.5 * T2 * cm2;
+    sn[0] = 4.0 * T3 * f + T4 * fp + T * cm2;
+    for (int q = 0; q < 3; ++q) sn[1 + q] = E.chi[q] * T2 * mu[q];
+    H[0][0] = 12.0 * T2 * f + 8.0 * T3 * fp + T4 * fpp + cm2;
+    for (int q = 0; q < 3; ++q) {
+        double c = 2.0 * E.chi[q] * T * mu[q];
+        H[0][1 + q] = c;
+        H[1 + q][0] = c;
+        for (int r = 0; r < 3; ++r) H[1 + q][1 + r] = (q == r) ? E.chi[q] * T2 : 0.0;
+    }
+}
+
+// work counters of one inversion (reported as algorithmic work by the benchmark)
+struct EosWork {
+    unsigned resid, solve, g;
+};
+
+// g(T) = s(T, mu(T)) - s_target with mu_q(T) = n_q/(chi_q T^2)
+__device__ __forceinline__ void an_g(const EosDev &E, double T, double s, double c, double &g, double &gp)
+{
+    double f, fp, fpp;
+    an_shape(E, T, f, fp, fpp);
+    double T2 = T * T, T3 = T2 * T, T4 = T2 * T2;
+    g = 4.0 * T3 * f + T4 * fp + c / T3 - s;
+    gp = 12.0 * T2 * f + 8.0 * T3 * fp + T4 * fpp - 3.0 * c / T4;
+}
+
+__device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double &T, double *mu, EosWork &w)
+{
+    if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) return PST_NONFINITE | PST_NOCONV;
+    if (!(s > 0.0)) return PST_NOCONV;
+    double c = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        if (E.chi[q] > 0.0) c += n[q] * n[q] / E.chi[q];
+        else if (n[q] != 0.0) return PST_NOCONV;
+    }
+    double Thi = cbrt(s / (4.0 * E.a0));
+    double g, gp;
+    an_g(E, Thi, s, c, g, gp);
+    ++w.g;
+    double Tlo = Thi;
+    if (g > 0.0) {
+        double gprev = g;
+        bool found = false;
+        for (int k = 0; k < 400; ++k) {
+            Tlo *= 0.8;
+            double gl, gpl;
+            an_g(E, Tlo, s, c, gl, gpl);
+            ++w.g;
+            if (gl <= 0.0) {
+                found = true;
+                break;
+            }
+            if (gl > gprev) return PST_NOCONV;
+            gprev = gl;
+        }
+        if (!found) return PST_NOCONV;
+    }
+    double t = Thi;
+    for (int it = 0; it < 200; ++it) {
+        an_g(E, t, s, c, g, gp);
+        ++w.g;
+        if (g == 0.0) break;
+        if (g > 0.0) Thi = t;
+        else Tlo = t;
+        double tn = t - g / gp;
+        if (!(gp > 0.0) || !(tn > Tlo && tn < Thi)) tn = 0.5 * (Tlo + Thi);
+        if (fabs(tn - t) <= 4e-16 * t) {
+            t = tn;
+            break;
+        }
+        t = tn;
+    }
+    T = t;
+    for (int q = 0; q < 3; ++q) mu[q] = E.chi[q] > 0.0 ? n[q] / (E.chi[q] * t * t) : 0.0;
+    return 0u;
+}
+
+// ---------------------------------------------------------------------------
+// table: quadrilinear interpolation evaluated as four bilinear (mu_S, mu_Q)
+// patches combined over (T, mu_B), carrying all four partial derivatives
+__device__ __forceinline__ void locate(double x, double x0, double inv, int nx, int &i, double &t)
+{
+    double r = (x - x0) * inv;
+    int k = (int)floor(r);
+    k = max(0, min(k, nx - 2));
+    i = k;
+    t = r - (double)k;
+}
+
+// sn: interpolated (s, nB, nS, nQ); J[f][k] = d sn_f / d x_k; p optional
+__device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double J[4][4], double *p)
+{
+    int iT, iB, iS, iQ;
+    double tT, tB, tS, tQ;
+    locate(x[0], E.T0, E.inv_dT, E.nT, iT, tT);
+    locate(x[1], E.mu0[0], E.inv_dmu[0], E.nmu[0], iB, tB);
+    locate(x[2], E.mu0[1], E.inv_dmu[1], E.nmu[1], iS, tS);
+    locate(x[3], E.mu0[2], E.inv_dmu[2], E.nmu[2], iQ, tQ);
+    const int n3 = E.nmu[2], n23 = E.nmu[1] * E.nmu[2], n123 = E.nmu[0] * n23;
+    for (int f = 0; f < 4; ++f) {
+        sn[f] = 0.0;
+        for (int k = 0; k < 4; ++k) J[f][k] = 0.0;
+    }
+    double pv = 0.0;
+    for (int bT = 0; bT < 2; ++bT)
+        for (int bB = 0; bB < 2; ++bB) {
+            double wT = bT ? tT : 1.0 - tT, wB = bB ? tB : 1.0 - tB;
+            double dT = bT ? E.inv_dT : -E.inv_dT, dB = bB ? E.inv_dmu[0] : -E.inv_dmu[0];
+            size_t base = (size_t)(iT + bT) * n123 + (size_t)(iB + bB) * n23 + (size_t)iS * n3 + iQ;
+            const double2 *c00 = reinterpret_cast<const double2 *>(E.sn + 4 * base);
+            const double2 *c01 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + 1));
+            const double2 *c10 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + n3));
+            const double2 *c11 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + n3 + 1));
+            double v00[4], v01[4], v10[4], v11[4];
+            double2 t;
+            t = __ldg(c00); v00[0] = t.x; v00[1] = t.y; t = __ldg(c00 + 1); v00[2] = t.x; v00[3] = t.y;
+            t = __ldg(c01); v01[0] = t.x; v01[1] = t.y; t = __ldg(c01 + 1); v01[2] = t.x; v01[3] = t.y;
+            t = __ldg(c10); v10[0] = t.x; v10[1] = t.y; t = __ldg(c10 + 1); v10[2] = t.x; v10[3] = t.y;
+            t = __ldg(c11); v11[0] = t.x; v11[1] = t.y; t = __ldg(c11 + 1); v11[2] = t.x; v11[3] = t.y;
+            double wTB = wT * wB;
+            for (int f = 0; f < 4; ++f) {
+                double a0 = v00[f] + tQ * (v01[f] - v00[f]);  // mu_S lower face
+                double a1 = v10[f] + tQ * (v11[f] - v10[f]);  // mu_S upper face
+                double val = a0 + tS * (a1 - a0);
+                double dS = (a1 - a0) * E.inv_dmu[1];
+                double dQ = ((v01[f] - v00[f]) + tS * ((v11[f] - v10[f]) - (v01[f] - v00[f]))) * E.inv_dmu[2];
+                sn[f] = fma(wTB, val, sn[f]);
+                J[f][0] = fma(dT * wB, val, J[f][0]);
+                J[f][1] = fma(wT * dB, val, J[f][1]);
+                J[f][2] = fma(wTB, dS, J[f][2]);
+                J[f][3] = fma(wTB, dQ, J[f][3]);
+            }
+            if (p) {
+                double p00 = __ldg(E.p + base), p01 = __ldg(E.p + base + 1), p10 = __ldg(E.p + base + n3),
+                       p11 = __ldg(E.p + base + n3 + 1);
+                double a0 = p00 + tQ * (p01 - p00), a1 = p10 + tQ * (p11 - p10);
+                pv = fma(wTB, a0 + tS * (a1 - a0), pv);
+            }
+        }
+    if (p) *p = pv;
+}
+
+// 4x4 Gaussian elimination with partial pivoting, fully unrolled so every index is a
+// compile-time constant and the system stays in registers.  Row swaps are conditional
+// moves.  Returns false on a zero or non-finite pivot.
+__device__ __forceinline__ bool solve4(double A[4][4], double b[4])
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        double best = fabs(A[c][c]);
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            double v = fabs(A[r][c]);
+            if (v > best) {
+                best = v;
+                piv = r;
+            }
+        }
+        if (!(best > 0.0) || !isfinite(best)) return false;
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            if (piv == r) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double t = A[c][k];
+                    A[c][k] = A[r][k];
+                    A[r][k] = t;
+                }
+                double t = b[c];
+                b[c] = b[r];
+                b[r] = t;
+            }
+        }
+        double inv = 1.0 / A[c][c];
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            double f = A[r][c] * inv;
+#pragma unroll
+            for (int k = c; k < 4; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
+            b[r] = fma(-f, b[c], b[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+        double acc = b[r];
+#pragma unroll
+        for (int k = r + 1; k < 4; ++k) acc = fma(-A[r][k], b[k], acc);
+        b[r] = acc / A[r][r];
+    }
+    return true;
+}
+
+__device__ __forceinline__ void clamp4(const EosDev &E, double *x)
+{
+    x[0] = fmin(fmax(x[0], E.T0), E.Tmax);
+    for (int q = 0; q < 3; ++q) x[1 + q] = fmin(fmax(x[1 + q], E.mu0[q]), E.mumax[q]);
+}
+
+__device__ double resid(const EosDev &E, const double *x, double s, const double *n, double r[4], double J[4][4])
+{
+    double sn[4];
+    tab_eval(E, x, sn, J, nullptr);
+    double inv_s = 1.0 / s;
+    double tgt[4] = {s, n[0], n[1], n[2]};
+    double m = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        r[k] = (sn[k] - tgt[k]) * inv_s;
+        m = isfinite(r[k]) ? fmax(m, fabs(r[k])) : __longlong_as_double(0x7FF0000000000000LL);
+        for (int j = 0; j < 4; ++j) J[k][j] *= inv_s;
+    }
+    return m;
+}
+
+// Damped Newton on the table interpolant.  The Jacobian is factorised in place (it is
+// not needed after the step); each line-search trial overwrites r and J with their values
+// at the trial point, so the accepted point's residual and Jacobian are ready for the
+// next iteration (the same sequence as a copy-on-accept scheme, with fewer registers).
+__device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x, EosWork &w)
+{
+    double r[4], J[4][4];
+    double rn = resid(E, x, s, n, r, J);
+    ++w.resid;
+    for (int it = 0; it < E.maxit; ++it) {
+        double d[4] = {-r[0], -r[1], -r[2], -r[3]};
+        if (rn <= E.tol) {
+            ++w.solve;
+            if (solve4(J, d)) {  // one polishing step if it does not increase the residual
+                double xn[4] = {x[0] + d[0], x[1] + d[1], x[2] + d[2], x[3] + d[3]};
+                clamp4(E, xn);
+                ++w.resid;
+                if (resid(E, xn, s, n, r, J) <= rn)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x[k] = xn[k];
+            }
+            return true;
+        }
+        ++w.solve;
+        if (!solve4(J, d)) return false;
+        double lam = 1.0, xn[4], rnn = 0.0;
+        for (int ls = 0; ls <= 8; ++ls) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xn[k] = fma(lam, d[k], x[k]);
+            clamp4(E, xn);
+            rnn = resid(E, xn, s, n, r, J);
+            ++w.resid;
+            if (rnn < rn) break;
+            lam *= 0.5;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = xn[k];
+        rn = rnn;
+    }
+    return rn <= E.tol;
+}
+
+struct EosOut {
+    double T, mu[3], p, e, ps, pn[3], cs2;
+    uint32_t st;
+};
+
+__device__ __forceinline__ bool inside_table(const EosDev &E, const double *x)
+{
+    bool in = x[0] >= E.T0 && x[0] <= E.Tmax;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) in = in && x[1 + q] >= E.mu0[q] && x[1 + q] <= E.mumax[q];
+    return in;
+}
+
+// guess: this particle's table solution of the previous stage (T <= 0: none).  Attempts:
+// table Newton from the guess; else the closed form, then table Newton from it; else the
+// closed form (flagged).  used_table tells whether the table produced the result.
+__device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const double *n, const double *guess,
+                             bool &used_table, EosWork &w)
+{
+    EosOut o;
+    o.T = 0.0;
+    for (int q = 0; q < 3; ++q) o.mu[q] = 0.0, o.pn[q] = 0.0;
+    o.p = o.e = o.ps = o.cs2 = 0.0;
+    o.st = 0u;
+    used_table = false;
+    if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) {
+        o.st = PST_NONFINITE | PST_NOCONV;
+        return o;
+    }
+    double x[4];
+    bool use_table = false;
+    if (E.has_table && guess[0] > 0.0 && inside_table(E, guess)) {
+        double xt[4] = {guess[0], guess[1], guess[2], guess[3]};
+        if (tab_newton(E, s, n, xt, w)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = xt[k];
+            use_table = true;
+        }
+    }
+    if (!use_table) {
+        o.st = an_invert(E, s, n, x[0], x + 1, w);
+        if (o.st) return o;
+        if (E.has_table) {
+            if (inside_table(E, x)) {
+                double xt[4] = {x[0], x[1], x[2], x[3]};
+                if (tab_newton(E, s, n, xt, w)) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x[k] = xt[k];
+                    use_table = true;
+                } else {
+                    o.st |= PST_FALLBACK;
+                }
+            } else {
+                o.st |= PST_OUT_OF_TABLE;
+            }
+        }
+    }
+    used_table = use_table;
+    double p, H[4][4], sn[4];
+    if (use_table) tab_eval(E, x, sn, H, &p);
+    else an_eval(E, x[0], x + 1, p, sn, H);
+    double e = x[0] * s + x[1] * n[0] + x[2] * n[1] + x[3] * n[2] - p;
+    // (p_s, p_n) = H^-T (s, n) over the directions the EoS couples to; an uncoupled charge
+    // direction (no table, chi_q = 0) becomes an identity row with zero right-hand side
+    double A[4][4], z[4] = {s, n[0], n[1], n[2]};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool act_i = i == 0 || use_table || E.chi[i - 1] > 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool act_j = j == 0 || use_table || E.chi[j - 1] > 0.0;
+            A[i][j] = (act_i && act_j) ? H[j][i] : (i == j ? 1.0 : 0.0);
+        }
+        if (!act_i) z[i] = 0.0;
+    }
+    ++w.solve;
+    if (!solve4(A, z)) {
+        o.st |= PST_NOCONV;
+        return o;
+    }
+    double cs2 = (s * z[0] + n[0] * z[1] + n[1] * z[2] + n[2] * z[3]) / (e + p);
+    if (cs2 > cs2_cap) {
+        double f = cs2_cap / cs2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) z[k] *= f;
+        cs2 = cs2_cap;
+        o.st |= PST_CS2_CAPPED;
+    }
+    o.T = x[0];
+    for (int q = 0; q < 3; ++q) o.mu[q] = x[1 + q], o.pn[q] = z[1 + q];
+    o.p = p;
+    o.e = e;
+    o.ps = z[0];
+    o.cs2 = cs2;
+    return o;
+}
+
+
+}  // namespace
+}  // namespace sphg

@@ -346,12 +346,24 @@ inline int nblk(int n, int t) { return (n + t - 1) / t; }
 void launch_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
                      cudaStream_t st)
 {
+    if (v.dim == 3) {
+        launch_gradient3(v, stage, y, gin, cb, gout, st);
+        return;
+    }
+    if (v.mixed) {
+        launch_gradient2m(v, stage, y, gin, cb, gout, st);
+        return;
+    }
     k_gradient2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout);
 }
 
 void launch_eom(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,
                 const double *gout, double *yout, double *rates, uint32_t *status, cudaStream_t st)
 {
+    if (v.dim == 3) {
+        launch_eom3(v, stage, mode, ys, dens, eos, gout, yout, rates, status, st);
+        return;
+    }
     k_eom2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, mode, ys, dens, eos, gout, yout, rates, status);
 }
 
@@ -364,6 +376,10 @@ void launch_totals(const EvView &v, const double *y, const double *Nq, const int
                    const double *eos, double *contrib, cudaStream_t st)
 {
     (void)Nq;
+    if (v.dim == 3) {
+        launch_totals3(v, y, id, dens, eos, contrib, st);
+        return;
+    }
     k_totals2<<<nblk(v.n, 256), 256, 0, st>>>(v, y, id, dens, eos, contrib);
 }
 

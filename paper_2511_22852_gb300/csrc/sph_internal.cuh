@@ -44,6 +44,7 @@ struct DevScalars {
     // EoS work actually done, summed over stages: table residual+Jacobian evaluations,
     // 4x4 solves, closed-form g(T) evaluations
     unsigned long long eos_resid, eos_solve, eos_g;
+    unsigned long long shell_tests;  // mixed form: candidates that needed the exact FP64 test
 };
 
 struct EosDev {
@@ -65,8 +66,13 @@ struct TransportDev {
 // everything a kernel of one event needs, passed by value
 struct EvView {
     int n, dim, milne, nv, B;
+    int B3[3];                // 3D: bits of the cell coordinate per axis
+    const uint32_t *spread;   // 3D: spread[d * 1024 + c] = key bits of cell coordinate c on axis d
     double h, inv_h, supp2, inv_cell, sigma_d, dtau;
     float supp2_hi;  // single-precision prefilter bound, >= (2h)^2 plus the worst rounding error
+    int mixed;                 // 1: neighbour passes in FP32 with compensated sums (2D)
+    float cell_f;              // mixed: cell side 2h in single precision
+    float shell_lo, shell_hi;  // mixed: float r^2 below lo is inside, above hi outside, else FP64 test
     DevScalars *sc;
     EosDev eos;
     TransportDev tr;
@@ -165,8 +171,10 @@ __device__ __forceinline__ void warp_or(unsigned int *dst, unsigned int v)
 // launchers (implemented in cells.cu, density_eos.cu, gradient_eom.cu)
 struct CellBufs {
     uint32_t *key, *cnt, *start, *cursor, *tmp, *perm;
-    float2 *fpos;  // sorted positions relative to the bounding-box minimum, single precision
-    int nb;        // number of buckets = 1 << (dim * B)
+    float2 *fpos;   // 2D: sorted positions relative to the bounding-box minimum, single precision
+    float4 *fpos3;  // 3D: the same with three coordinates
+    uint32_t *part; // scan partial sums (multi-block scan of large bucket tables)
+    int nb;         // number of buckets: 1 << (2 B) in 2D, 1 << (B3[0] + B3[1] + B3[2]) in 3D
 };
 
 // Bound for the single-precision candidate prefilter of the neighbour passes.  With
@@ -176,13 +184,13 @@ struct CellBufs {
 // axes then errs by at most 4 (2h) e + 2 e^2 + 4 u (2h)^2 with e the difference error.
 // Twice that margin is added, so the prefilter never rejects a pair the exact
 // double-precision test r^2 < (2h)^2 accepts; the exact test decides every pair.
-inline float prefilter_bound(double h, int B)
+inline float prefilter_bound(double h, int B, int dim = 2)
 {
     const double u = 1.0 / 16777216.0;
     const double two_h = 2.0 * h;
     const double L = (double)(1 << B) * two_h;
     const double e = 2.0 * L * u + 2.0 * two_h * u + L * u;
-    const double err = 4.0 * two_h * e + 2.0 * e * e + 4.0 * u * two_h * two_h;
+    const double err = 2.0 * dim * two_h * e + dim * e * e + (dim + 2) * u * two_h * two_h;
     const double hi = two_h * two_h + 2.0 * err;
     float f = (float)hi;
     while ((double)f < hi) f = nextafterf(f, 1e30f);
@@ -213,6 +221,48 @@ void launch_scatter_orig(const double *src, double *dst, const int *id, int n, i
 void launch_scatter_orig_u32(const uint32_t *src, uint32_t *dst, const int *id, int n, cudaStream_t st);
 void launch_cell_coords(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
 int eom_block_count(int n);
+
+// mixed-precision 2D neighbour passes (mixed2d.cu); dispatched when v.mixed
+void launch_density2m(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                      cudaStream_t st);
+void launch_gradient2m(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
+                       cudaStream_t st);
+
+// Shell of the mixed-form neighbour decision.  Cell-relative positions are floats in
+// [0, 2h] (error <= 2h u each, u = 2^-24); the separation (r_a - r_b) - o 2h (|o| <= 1,
+// 2h itself rounded) errs by e <= 6 (2h) u per axis; for |dx_d| <= 2h the float r^2
+// (fmaf) errs by at most 2 dim (2h) e + dim e^2 + 2 u (2h)^2 <= 26 (2h)^2 u in 2D.  Twice
+// that margin on each side: outside [lo, hi] the float decision equals the exact one.
+inline void mixed_shell(double h, float &lo, float &hi)
+{
+    const double u = 1.0 / 16777216.0;
+    const double s2 = 4.0 * h * h;
+    const double err = 52.0 * s2 * u;
+    float l = (float)(s2 - err), g = (float)(s2 + err);
+    while ((double)l > s2 - err) l = nextafterf(l, 0.0f);
+    while ((double)g < s2 + err) g = nextafterf(g, 1e30f);
+    lo = l;
+    hi = g;
+}
+
+// 3D versions (step3d.cu); the launchers above dispatch to them when v.dim == 3
+void launch_cells3(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st);
+void launch_density3(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                     cudaStream_t st);
+void launch_eos3(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
+                 uint32_t *status, double *wpart, const double *guess_in, double *guess_out, cudaStream_t st);
+void launch_gradient3(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
+                      cudaStream_t st);
+void launch_eom3(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,
+                 const double *gout, double *yout, double *rates, uint32_t *status, cudaStream_t st);
+void launch_totals3(const EvView &v, const double *y, const int *id, const double *dens, const double *eos,
+                    double *contrib, cudaStream_t st);
+void launch_neighbors_list3(const EvView &v, const double *y, const int *id, CellBufs cb, const long long *offs,
+                            int *pa, int *pb, cudaStream_t st);
+void launch_cell_coords3(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
+// exclusive scan of cnt into start and cursor, any number of buckets
+void launch_scan_buckets(CellBufs cb, cudaStream_t st);
+
 // sets the message returned by sph_last_error() for the calling thread
 void set_last_error(const char *msg);
 

@@ -299,3 +299,92 @@ def smooth_blob_2p1(half_width=4.0, dx=0.1, h=0.3, T_peak_GeV=0.45, T_floor_GeV=
                  transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0,
                                      zeta_peak=0.05 if viscous else 0.0),
                  meta={"dx": dx})
+
+
+def lattice_3d(half_widths, spacings):
+    """[3][N] points of a box lattice centred on the origin (x, y, and eta or z)."""
+    axes = [d * (np.arange(int(round(2 * hw / d)) + 1) - int(round(2 * hw / d)) / 2.0)
+            for hw, d in zip(half_widths, spacings)]
+    G = np.meshgrid(*axes, indexing="ij")
+    return np.stack([g.ravel() for g in G]).copy()
+
+
+def bjorken_lattice_3p1(T0_GeV=0.16, half_widths=(0.8, 0.8, 0.4), spacings=(0.1, 0.1, 0.05), h=0.3,
+                        tau0=0.6, dtau=0.005, nsteps=40, viscous=True) -> Event:
+    """Uniform temperature at rest on a 3D Milne lattice (x, y, eta): interior particles follow
+    longitudinal Bjorken flow until the edge rarefaction arrives."""
+    x = lattice_3d(half_widths, spacings)
+    n = x.shape[1]
+    _, s, _ = _analytic_p_s_n(BJ_EOS, np.full(n, T0_GeV / HBARC), np.zeros((3, n)))
+    vol = tau0 * spacings[0] * spacings[1] * spacings[2]
+    return Event(name="bjorken_lattice_3p1", dim=3, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=x, u=np.zeros((3, n)), S=s * vol, Nq=np.zeros((3, n)), Bv=np.zeros(n), Pv=np.zeros((5, n)),
+                 eos=BJ_EOS, table=None,
+                 transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0,
+                                     zeta_peak=0.05 if viscous else 0.0),
+                 meta={"spacings": spacings})
+
+
+def smooth_blob_3d(milne=True, half_widths=(1.6, 1.6, 1.2), spacings=(0.16, 0.16, 0.12), h=0.3,
+                   T_peak_GeV=0.4, T_floor_GeV=0.07, sigma=(0.8, 0.6, 0.5), charge_frac=0.1, tau0=0.6,
+                   dtau=0.005, nsteps=20, viscous=True, with_table=True, eos: AnalyticEoS = None, seed_charge=11,
+                   flow=0.0) -> Event:
+    """Smooth anisotropic Gaussian temperature profile on a 3D lattice, Milne (x, y, eta) or
+    Cartesian (x, y, z), optional initial radial flow u^i = flow * x^i (transverse) to exercise
+    the acceleration and shear terms."""
+    eos = BJ_EOS if eos is None else eos
+    x = lattice_3d(half_widths, spacings)
+    n = x.shape[1]
+    prof = np.exp(-sum(x[d] ** 2 / (2.0 * sigma[d] ** 2) for d in range(3)))
+    T = (T_floor_GeV + (T_peak_GeV - T_floor_GeV) * prof) / HBARC
+    _, s, _ = _analytic_p_s_n(eos, T, np.zeros((3, n)))
+    eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
+    u = np.zeros((3, n))
+    u[0], u[1] = flow * x[0], flow * x[1]
+    gamma = np.sqrt(1.0 + u[0] ** 2 + u[1] ** 2)
+    vol = (tau0 if milne else 1.0) * spacings[0] * spacings[1] * spacings[2]
+    table = synthetic_eos_table(eos) if with_table else None
+    return Event(name="smooth_blob_3d", dim=3, milne=milne, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=x, u=u, S=s * gamma * vol, Nq=eps * (s * gamma * vol)[None, :], Bv=np.zeros(n),
+                 Pv=np.zeros((5, n)), eos=eos, table=table,
+                 transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0,
+                                     zeta_peak=0.05 if viscous else 0.0),
+                 meta={"spacings": spacings})
+
+
+def viscous_bsq_3p1(dx=0.124, deta=0.1, R=7.0, n_hot=200, sigma_hot=0.4, eta_sigma=1.5, eta_max=5.0,
+                    T_max_GeV=0.5, charge_frac=0.1, tau0=0.6, dtau=0.005, h=0.3, seed_hot=1, seed_charge=2,
+                    with_table=True) -> Event:
+    """Config: 3+1D hyperbolic (tau, x, y, eta_s) viscous BSQ event: the transverse hotspot
+    profile of the 2+1D event times exp(-eta^2/(2 sigma_eta^2)) for |eta| <= eta_max, on a
+    lattice dx = dy = 0.124 fm, d_eta = 0.1 (about 10^6 particles at the defaults)."""
+    m = int(math.ceil(R / dx)) + 1
+    g = dx * np.arange(-m, m + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    keep = (X * X + Y * Y) <= R * R
+    xt, yt = X[keep], Y[keep]
+    ke = int(round(eta_max / deta))
+    etas = deta * np.arange(-ke, ke + 1)
+    u = uniform01(seed_hot, 2 * n_hot)
+    rc = R * np.sqrt(u[:n_hot])
+    ph = 2.0 * math.pi * u[n_hot:]
+    cx, cy = rc * np.cos(ph), rc * np.sin(ph)
+    s_t = np.zeros_like(xt)
+    for k in range(n_hot):
+        s_t += np.exp(-((xt - cx[k]) ** 2 + (yt - cy[k]) ** 2) / (2.0 * sigma_hot ** 2))
+    _, s_max, _ = _analytic_p_s_n(BJ_EOS, np.array(T_max_GeV / HBARC), np.zeros(3))
+    s_t *= float(s_max) / s_t.max()
+    x = np.repeat(xt[None, :], etas.size, axis=0).ravel()
+    y = np.repeat(yt[None, :], etas.size, axis=0).ravel()
+    eta = np.repeat(etas[:, None], xt.size, axis=1).ravel()
+    s = np.repeat(s_t[None, :], etas.size, axis=0).ravel() * np.exp(-eta ** 2 / (2.0 * eta_sigma ** 2))
+    n = x.size
+    eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
+    vol = tau0 * dx * dx * deta
+    table = synthetic_eos_table(BJ_EOS) if with_table else None
+    return Event(name="viscous_bsq_3p1", dim=3, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=20,
+                 x=np.stack([x, y, eta]), u=np.zeros((3, n)), S=s * vol, Nq=eps * (s * vol)[None, :],
+                 Bv=np.zeros(n), Pv=np.zeros((5, n)), eos=BJ_EOS, table=table,
+                 transport=Transport(viscous=True, eta_over_s=0.08, zeta_peak=0.05, zeta_T_GeV=0.155,
+                                     zeta_w_GeV=0.02),
+                 meta={"dx": dx, "deta": deta})

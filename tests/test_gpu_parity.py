@@ -47,6 +47,83 @@ CASES = {
     "blob_causal": lambda: I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS),
     "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
 }
+CASES3 = {
+    "blob3_milne": lambda: I.smooth_blob_3d(milne=True, flow=0.3),
+    "blob3_cart": lambda: I.smooth_blob_3d(milne=False, flow=0.3, eos=I.CAUSAL_EOS),
+    "bjorken3": lambda: I.bjorken_lattice_3p1(),
+}
+
+
+def state_errors3(g, run):
+    st = g.read(("X", "U", "S", "BV", "PV"))
+    y = run.y
+    return {"x": relerr(st["X"], y[0:3]), "u": relerr(st["U"], y[3:6]), "S": relerr(st["S"], y[6]),
+            "Bv": relerr(st["BV"], y[7]), "Pv": relerr(st["PV"], y[8:13])}
+
+
+@pytest.mark.parametrize("case", list(CASES3))
+def test_3d_cells_neighbours_densities(Bd, case):
+    ev = CASES3[case]()
+    g = Bd.GpuEvent(ev, use_graph=False)
+    f = g.read(("CELL", "NNB", "SIGMA_STAR", "S_DENS", "T", "P"))
+    cc, _ = O.cell_coords(ev.x, ev.h)
+    assert np.array_equal(f["CELL"], cc)
+    pa, pb = g.neighbors()
+    oa, ob = O.neighbors(ev.x, ev.h, "cells")
+    assert np.array_equal(pa, oa) and np.array_equal(pb, ob)
+    assert np.array_equal(f["NNB"], np.bincount(oa, minlength=ev.n))
+    run = O.OracleRun.start(ev)
+    aux, st = run.observe()
+    assert relerr(f["SIGMA_STAR"], aux[O.AUX["sigstar"]]) < 1e-13
+    assert relerr(f["S_DENS"], aux[O.AUX["s"]]) < 1e-13
+    assert relerr(f["T"], aux[O.AUX["T"]]) < 1e-12 and relerr(f["P"], aux[O.AUX["p"]]) < 1e-12
+    g.free()
+
+
+@pytest.mark.parametrize("case", list(CASES3))
+def test_3d_rates(Bd, case):
+    ev = CASES3[case]()
+    g = Bd.GpuEvent(ev, use_graph=False)
+    r, grad = g.rates()
+    run = O.OracleRun.start(ev)
+    dydt, aux, ograd, st, wr = run.stage()
+    for k in range(13):
+        if not np.any(dydt[k]) and not np.any(r[k]):
+            continue
+        assert relerr(r[k], dydt[k]) < TOL_STEP, (k, relerr(r[k], dydt[k]))
+    assert relerr(grad[0:9], ograd[0:9]) < TOL_STEP and relerr(grad[9:12], ograd[9:12]) < TOL_STEP
+    g.free()
+
+
+@pytest.mark.parametrize("case", list(CASES3))
+def test_3d_step_and_evolution(Bd, case):
+    ev = CASES3[case]()
+    g = Bd.GpuEvent(ev, use_graph=True)
+    g.step(1, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(1)
+    errs = state_errors3(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    g.step(9, sync=True)
+    run.step(9)
+    errs = state_errors3(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    t, ot = g.totals(), run.totals()
+    assert abs(t["E"] / ot["E"] - 1) < TOL_EVOL
+    g.free()
+
+
+def test_3d_full_size_milne_event_one_step(Bd):
+    """The 3+1D hyperbolic viscous BSQ event (about 10^6 particles), one Heun step."""
+    ev = I.viscous_bsq_3p1()
+    assert ev.n > 900000
+    g = Bd.GpuEvent(ev, use_graph=True)
+    g.step(1, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(1)
+    errs = state_errors3(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    g.free()
 
 
 @pytest.mark.parametrize("case", list(CASES))

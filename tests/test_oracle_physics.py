@@ -144,3 +144,36 @@ def test_shear_reconstruction_properties():
             assert np.allclose(ul @ pi, 0, atol=1e-12 * np.abs(pi).max())
             assert abs(np.sum(g * np.diag(pi))) < 1e-12 * np.abs(pi).max()
             assert np.allclose(pi, pi.T)
+
+
+def test_bjorken_3p1_milne_against_ode():
+    """3+1D Milne (x, y, eta) lattice at rest: the centre follows the same Bjorken ODEs (the
+    longitudinal Christoffel terms, theta = 1/tau, sigma^{eta eta}, the traceless pi^{eta eta})."""
+    ev = I.bjorken_lattice_3p1(half_widths=(1.04, 1.04, 1.04), spacings=(0.08, 0.08, 0.08), h=0.2, nsteps=20)
+    tr = ev.transport
+    thermo = _eos_fns(ev.eos)
+
+    def rhs(tau, Y):
+        T, Pi, Phi = Y
+        p, s, dsdT = thermo(T)
+        e = T * s - p
+        eta = tr.eta_over_s * s
+        zeta = tr.zeta_peak * np.exp(-(T * I.HBARC - tr.zeta_T_GeV) ** 2 / (2 * tr.zeta_w_GeV ** 2)) * s
+        taupi = tr.tau_pi_coef * eta / (e + p)
+        return [-(e + p + Pi - Phi) / tau / (T * dsdT), -(Pi + zeta / tau) / (tr.tau_Pi_ratio * taupi) - Pi / tau,
+                (-Phi + 4 * eta / (3 * tau)) / taupi - 4 * Phi / (3 * tau)]
+
+    run = O.OracleRun.start(ev)
+    c = int(np.argmin(ev.x[0] ** 2 + ev.x[1] ** 2 + ev.x[2] ** 2))
+    aux0, _ = run.observe()
+    run.step(ev.nsteps)
+    aux, _ = run.observe()
+    sol = solve_ivp(rhs, (ev.tau0, run.tau), [aux0[O.AUX["T"]][c], 0.0, 0.0], rtol=1e-12, atol=1e-14)
+    Tode, Piode, Phiode = sol.y[:, -1]
+    sigma = aux[O.AUX["sigma"]][c]
+    assert abs(aux[O.AUX["T"]][c] / Tode - 1) < 1e-6
+    assert abs(aux[O.AUX["Pi"]][c] - Piode) < 2e-3 * abs(Piode)
+    # stored (11, 12, 13, 22, 23): pi^{xx} = pi^{yy} = Phi/2, off-diagonals vanish
+    assert abs(sigma * run.y[8][c] - Phiode / 2) < 1e-3 * abs(Phiode)
+    assert abs(sigma * run.y[11][c] - Phiode / 2) < 1e-3 * abs(Phiode)
+    assert max(abs(run.y[9][c]), abs(run.y[10][c]), abs(run.y[12][c])) < 1e-9 * abs(run.y[8][c])
