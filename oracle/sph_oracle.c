@@ -549,6 +549,9 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
             if (rnn < rn) break;
             lam *= 0.5;
         }
+        /* no decrease along the Newton direction (e.g. the root lies beyond a clamped table
+           edge): the iteration has stalled and ends unconverged */
+        if (!(rnn < rn)) return -1;
         memcpy(x, xn, sizeof(xn));
         memcpy(r, rr, sizeof(rr));
         memcpy(J, Jn, sizeof(Jn));
@@ -559,7 +562,8 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
 
 /* out[0..10]: T, muB, muS, muQ, p, e, p_s, p_nB, p_nS, p_nQ, cs2 (after the cap).
    guess: the previous stage's table solution (T, muB, muS, muQ) of this particle, T <= 0
-   for none (may be NULL).  Order of attempts (SURVEY reading A16):
+   for none (may be NULL).  The EoS-inversion passage does not fix the root finder's starting
+   point; this reading starts from the particle's previous solution.  Order of attempts:
      1. table Newton warm-started from the guess, if the guess lies in the table;
      2. otherwise (or if 1. does not converge) the closed-form solution, then table Newton
         started there if it lies in the table; else the closed form (flagged).

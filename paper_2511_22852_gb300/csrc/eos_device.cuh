@@ -274,6 +274,9 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
             if (rnn < rn) break;
             lam *= 0.5;
         }
+        // no decrease along the Newton direction (the root lies beyond a clamped table
+        // edge, or the interpolant is flat): the iteration has stalled and ends unconverged
+        if (!(rnn < rn)) return false;
 #pragma unroll
         for (int k = 0; k < 4; ++k) x[k] = xn[k];
         rn = rnn;

@@ -329,6 +329,38 @@ def test_warm_start_matches_oracle_over_steps(Bd):
     g.free()
 
 
+def test_eos_stall_at_table_edge_ends_fast(Bd):
+    """A warm start inside the table whose root lies below the table's lowest T: the clamped
+    Newton stalls at the edge, the failed line search ends it (at most 1 + 9 residual
+    evaluations), and the closed form takes over, flagged out-of-table -- as in the oracle."""
+    ev = CASES["bsq_small"]()
+    hot = Bd.GpuEvent(ev)
+    hot.step(1, sync=True)
+    gs = hot.read(("GUESS",))["GUESS"]
+    hot.free()
+    assert np.all(gs[0] > 0)
+    ev2 = CASES["bsq_small"]()
+    # s -> 1e-5 s puts every particle below T = 0.05 GeV (s ~ f(T) T^3, f from 2.8 down to 0.3)
+    ev2.S = ev2.S * 1e-5
+    ev2.Nq = ev2.Nq * 1e-5
+    g = Bd.GpuEvent(ev2)
+    g.write_state(guess=gs)
+    t0 = g.totals()
+    g.step(1, sync=True)
+    t1 = g.totals()
+    assert t1["eos_work"][0] - t0["eos_work"][0] <= 10 * ev2.n
+    run = O.OracleRun.start(ev2)
+    run.guess[:] = gs
+    run.step(1)
+    aux, st = run.observe()
+    f = g.read(("X", "U", "S", "T", "STATUS"))
+    assert np.array_equal(f["STATUS"] & Bd.PST_OUT_OF_TABLE, st.astype(np.uint32) & Bd.PST_OUT_OF_TABLE)
+    assert np.all(f["STATUS"] & Bd.PST_OUT_OF_TABLE)
+    assert relerr(f["X"], run.y[:2]) < TOL_STEP and relerr(f["U"], run.y[2:4]) < TOL_STEP
+    assert relerr(f["T"], aux[O.AUX["T"]]) < TOL_STEP
+    g.free()
+
+
 def test_edge_cases_and_errors(Bd):
     # empty event: every call succeeds
     ev = I.bjorken_lattice_2p1(n_side=3, viscous=False)
@@ -387,4 +419,44 @@ def test_infeasible_charges_are_flagged(Bd):
     with pytest.raises(Bd.SphError) as e:
         g.step(1, sync=True)
     assert e.value.code == Bd.SPH_ERR_EOS_NOCONV
+    g.free()
+
+
+TOL_MIXED = 1e-5  # the mixed-precision form against the FP64 oracle (T, mu, densities)
+
+
+@pytest.mark.parametrize("case,nsteps", [("bsq_small", 50), ("gubser", 60), ("blob_causal", 40)])
+def test_mixed_precision_against_fp64_oracle(Bd, case, nsteps):
+    """SPH_MIXED: FP32 neighbour passes, FP64 EoS/EoM -- within 1e-5 of the FP64 oracle on T, mu
+    and the densities after many steps; neighbour counts exactly those of the FP64 test."""
+    ev = CASES[case]()
+    g = Bd.GpuEvent(ev, precision=Bd.SPH_MIXED)
+    run = O.OracleRun.start(ev)
+    aux0, _ = run.observe()
+    assert np.array_equal(g.read(("NNB",))["NNB"], aux0[O.AUX["nnb"]].astype(np.int32))
+    g.step(nsteps, sync=True)
+    run.step(nsteps)
+    f = g.read(("T", "MU", "S_DENS", "N_DENS", "NNB"))
+    aux, _ = run.observe()
+    A = O.AUX
+    assert np.array_equal(f["NNB"], aux[A["nnb"]].astype(np.int32))
+    assert relerr(f["T"], aux[A["T"]]) < TOL_MIXED
+    assert relerr(f["S_DENS"], aux[A["s"]]) < TOL_MIXED
+    if np.any(aux[A["nB"]]):
+        assert relerr(f["N_DENS"], aux[A["nB"]:A["nQ"] + 1]) < TOL_MIXED
+        assert relerr(f["MU"], aux[A["muB"]:A["muQ"] + 1]) < TOL_MIXED
+    g.free()
+
+
+def test_mixed_precision_full_size_event(Bd):
+    ev = I.viscous_bsq_2p1()
+    g = Bd.GpuEvent(ev, precision=Bd.SPH_MIXED)
+    g.step(10, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(10)
+    f = g.read(("T", "MU", "S_DENS"))
+    aux, _ = run.observe()
+    A = O.AUX
+    assert relerr(f["T"], aux[A["T"]]) < TOL_MIXED and relerr(f["S_DENS"], aux[A["s"]]) < TOL_MIXED
+    assert relerr(f["MU"], aux[A["muB"]:A["muQ"] + 1]) < TOL_MIXED
     g.free()

@@ -173,7 +173,7 @@ def test_acausal_band_is_capped(bsq):
 
 
 def test_warm_started_inversion_reaches_the_same_root(bsq):
-    """Newton from the previous stage's solution converges to the root the cold
+    """Newton from the previous stage's solution (the warm-start reading) converges to the root the cold
     start (closed form, then table) finds; a guess outside the table falls back to the cold path."""
     import ctypes as C
     ev, P, _ = bsq
