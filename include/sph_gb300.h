@@ -252,6 +252,79 @@ sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms,
 sph_status sph_density_noalloc(const double *x, const double *u, const double *S, const double *Nq, int64_t n,
                                double h, double tau, int32_t milne, double *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving form: event-by-event simulation (the paper runs one hydrodynamic evolution per
+ * collision event, Sec. "Hydrodynamic evolution"; experiments average observables over
+ * many events) with continuous batching.  A server owns one particle arena carved from
+ * free HBM; submitted 2+1D events wait in a FIFO queue and are admitted while a slot and a
+ * contiguous arena range are free; every batch step advances all admitted events by one
+ * Heun step together (one CUDA graph, the same for every batch composition); an event that
+ * has finished its steps is evaluated once more at its final state (cell list, densities,
+ * EoS) and its fields are copied to pinned host memory, after which its slot and range are
+ * reused.  Arithmetic: the mixed form (SPH_MIXED above, with cell-tiled neighbour passes);
+ * EoS inversion, equations of motion and totals in FP64.  An event's results do not depend
+ * on the other events in the batch (bitwise).
+ *
+ * Threading: one host thread drives a server at a time.  Ownership: sph_submit copies the
+ * caller's arrays; sph_collect writes into caller-owned host buffers.
+ * ------------------------------------------------------------------------- */
+typedef struct sph_server sph_server;
+
+typedef struct {
+    int32_t max_events;    /* slots: events advanced together, 1..256 */
+    int32_t max_inflight;  /* batch steps enqueued ahead of the device, 1..8 (0: 2) */
+    int64_t max_particles; /* arena capacity in particles (0: hbm_fraction of free HBM) */
+    double hbm_fraction;   /* share of free HBM for the arena when max_particles = 0, <= 0.9 (0: 0.25) */
+    int64_t pinned_bytes;  /* pinned host staging pool (0: 256 bytes per arena particle) */
+    void *stream;          /* cudaStream_t of all server work, NULL: library-created */
+    int32_t polish;        /* 1: a Newton polishing step after convergence, as the plain form */
+    int32_t reserved;
+} sph_server_desc;
+
+#define SPH_TICKET_QUEUED 0
+#define SPH_TICKET_RUNNING 1
+#define SPH_TICKET_DONE 2
+
+typedef struct {
+    int64_t queued, running, done; /* tickets by state (done: results not yet collected) */
+    int64_t batch_steps;           /* batch steps launched */
+    int64_t particle_steps;        /* sum over batch steps of the particles advanced */
+    int64_t arena_capacity, arena_in_use; /* particles */
+    int64_t kernel_launches;       /* kernels launched by the server (graph replays included) */
+    int32_t slots_in_use, max_events;
+} sph_server_stats;
+
+/* Errors: SPH_ERR_ARG (max_events outside 1..256, bad fractions), SPH_ERR_OOM (arena
+ * allocation), SPH_ERR_CUDA.  The server holds a reference to eos. */
+sph_status sph_server_create(sph_server **out, const sph_server_desc *desc, const sph_eos *eos);
+/* Waits for the server's stream and frees everything, uncollected results included. */
+void sph_server_free(sph_server *srv);
+/* Queues an event that is to advance nsteps Heun steps.  desc as for sph_init_event with
+ * dim = 2 and n >= 1 (precision, use_graph, profile, stream and fatal_mask are ignored);
+ * the arrays are copied before the call returns.  *ticket identifies the request.
+ * Errors: SPH_ERR_ARG (as sph_init_event; dim != 2, n < 1, nsteps < 0), SPH_ERR_OOM (n
+ * larger than the arena). */
+sph_status sph_submit(sph_server *srv, const sph_event_desc *desc, int32_t nsteps, int64_t *ticket);
+/* Runs up to max_steps batch steps: before each, admits queued events that fit; after
+ * each, retires events that finished.  Returns early when nothing is admitted or running.
+ * At most max_inflight steps run ahead of the device (bounded waits: SPH_ERR_TIMEOUT).
+ * *running (may be NULL) receives the number of events in the batch. */
+sph_status sph_server_pump(sph_server *srv, int32_t max_steps, int32_t *running);
+/* State of a ticket (SPH_TICKET_*); for a DONE ticket, *latency_s (may be NULL) receives
+ * the seconds from sph_submit until its results were readable in host memory (device
+ * completion time of the copy).  Errors: SPH_ERR_ARG (unknown ticket). */
+sph_status sph_poll(sph_server *srv, int64_t ticket, int32_t *state, double *latency_s);
+/* Copies the fields in mask of a DONE ticket to host buffers (original particle order; the
+ * state fields X .. PV at the final time, the derived fields SIGMA_STAR .. NNB evaluated at
+ * the final state) and its totals (tot may be NULL), then releases the ticket.  Fields
+ * available: X, U, S, NQ, BV, PV, SIGMA_STAR, S_DENS, N_DENS, T, MU, P, E, PI_BULK, STATUS,
+ * NNB.  Errors: SPH_ERR_STATE (not done), SPH_ERR_ARG (unknown ticket, other fields, NULL
+ * destinations, on_device). */
+sph_status sph_collect(sph_server *srv, int64_t ticket, uint64_t mask, const sph_field_bufs *out, sph_totals *tot);
+sph_status sph_server_stats_get(sph_server *srv, sph_server_stats *out);
+/* Pumps until every submitted ticket is DONE (timeout_s <= 0: no limit). */
+sph_status sph_server_drain(sph_server *srv, double timeout_s);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *sph_last_error(void);
 

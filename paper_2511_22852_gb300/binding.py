@@ -32,7 +32,10 @@ F = {name: 1 << i for i, name in enumerate(
      "NNB", "CELL", "GUESS"])}
 
 EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_event", "sph_step", "sph_read_fields",
-           "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times"]
+           "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
+           "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
+           "sph_server_stats_get", "sph_server_drain"]
+SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
 
 
 class SphError(RuntimeError):
@@ -71,6 +74,18 @@ class Totals(C.Structure):
                 ("shell_tests", C.c_int64)]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("max_events", C.c_int32), ("max_inflight", C.c_int32), ("max_particles", C.c_int64),
+                ("hbm_fraction", C.c_double), ("pinned_bytes", C.c_int64), ("stream", C.c_void_p),
+                ("polish", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ["queued", "running", "done", "batch_steps", "particle_steps",
+                                         "arena_capacity", "arena_in_use", "kernel_launches"]] + \
+               [("slots_in_use", C.c_int32), ("max_events", C.c_int32)]
+
+
 _lib = None
 
 
@@ -99,6 +114,14 @@ def lib():
             "sph_debug_neighbors": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
             "sph_debug_rates": (i32, [vp, vp, vp]),
             "sph_kernel_times": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32)]),
+            "sph_server_create": (i32, [C.POINTER(vp), C.POINTER(ServerDesc), vp]),
+            "sph_server_free": (None, [vp]),
+            "sph_submit": (i32, [vp, C.POINTER(EventDesc), i32, C.POINTER(i64)]),
+            "sph_server_pump": (i32, [vp, i32, C.POINTER(i32)]),
+            "sph_poll": (i32, [vp, i64, C.POINTER(i32), C.POINTER(C.c_double)]),
+            "sph_collect": (i32, [vp, i64, C.c_uint64, C.POINTER(FieldBufs), C.POINTER(Totals)]),
+            "sph_server_stats_get": (i32, [vp, C.POINTER(ServerStats)]),
+            "sph_server_drain": (i32, [vp, C.c_double]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -180,6 +203,49 @@ def sph_kernel_times(h):
     return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
 
 
+def sph_server_create(desc: ServerDesc, eos):
+    h = C.c_void_p()
+    _check(lib().sph_server_create(C.byref(h), C.byref(desc), eos))
+    return h
+
+
+def sph_server_free(h):
+    lib().sph_server_free(h)
+
+
+def sph_submit(h, desc: EventDesc, nsteps: int) -> int:
+    t = C.c_int64(0)
+    _check(lib().sph_submit(h, C.byref(desc), int(nsteps), C.byref(t)))
+    return t.value
+
+
+def sph_server_pump(h, max_steps: int) -> int:
+    r = C.c_int32(0)
+    _check(lib().sph_server_pump(h, int(max_steps), C.byref(r)))
+    return r.value
+
+
+def sph_poll(h, ticket: int):
+    st, lat = C.c_int32(0), C.c_double(0.0)
+    _check(lib().sph_poll(h, int(ticket), C.byref(st), C.byref(lat)))
+    return st.value, lat.value
+
+
+def sph_collect(h, ticket: int, mask: int, bufs: FieldBufs | None, tot: Totals | None):
+    _check(lib().sph_collect(h, int(ticket), C.c_uint64(mask), C.byref(bufs) if bufs is not None else None,
+                             C.byref(tot) if tot is not None else None))
+
+
+def sph_server_stats_get(h) -> dict:
+    o = ServerStats()
+    _check(lib().sph_server_stats_get(h, C.byref(o)))
+    return {k: getattr(o, k) for k, _ in ServerStats._fields_}
+
+
+def sph_server_drain(h, timeout_s: float = 0.0):
+    _check(lib().sph_server_drain(h, float(timeout_s)))
+
+
 # ---------------------------------------------------------------------------
 def eos_desc(eos, table=None, newton_tol=1e-12, newton_maxit=30):
     """(EosDesc, keep-alive list) from inputs.AnalyticEoS / inputs.EoSTable."""
@@ -200,6 +266,89 @@ def eos_desc(eos, table=None, newton_tol=1e-12, newton_maxit=30):
     return d, keep
 
 
+def event_desc(ev):
+    """(EventDesc, keep-alive list) of an ``inputs.Event`` (host arrays)."""
+    d = EventDesc()
+    d.dim, d.milne, d.viscous, d.on_device = ev.dim, int(ev.milne), int(ev.transport.viscous), 0
+    d.n, d.h, d.tau0, d.dtau = ev.n, ev.h, ev.tau0, ev.dtau
+    keep = [_f64(ev.x), _f64(ev.u), _f64(ev.S), _f64(ev.Nq), _f64(ev.Bv), _f64(ev.Pv)]
+    d.x, d.u, d.S, d.Nq, d.Bv, d.Pv = [a.ctypes.data if a.size else None for a in keep]
+    tr = ev.transport
+    d.eta_over_s, d.zeta_peak, d.zeta_T_GeV, d.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
+    d.tau_pi_coef, d.tau_Pi_ratio, d.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
+    return d, keep
+
+
+_FIELD_SHAPES = {"X": (2, "x"), "U": (2, "u"), "S": (1, "S"), "NQ": (3, "Nq"), "BV": (1, "Bv"), "PV": (3, "Pv"),
+                 "SIGMA_STAR": (1, "sigstar"), "S_DENS": (1, "s"), "N_DENS": (3, "nq"), "T": (1, "T"),
+                 "MU": (3, "mu"), "P": (1, "p"), "E": (1, "e"), "PI_BULK": (1, "Pi"), "STATUS": (1, "status"),
+                 "NNB": (1, "nnb")}
+
+
+class GpuServer:
+    """The serving form: events submitted from ``inputs.Event`` objects, batched on the GPU."""
+
+    def __init__(self, eos, table=None, max_events=32, max_particles=0, hbm_fraction=0.0, pinned_bytes=0,
+                 polish=False, max_inflight=2, stream=None):
+        ed, self._keep_eos = eos_desc(eos, table)
+        self.eos = sph_set_eos_table(ed)
+        d = ServerDesc()
+        d.max_events, d.max_inflight, d.max_particles = int(max_events), int(max_inflight), int(max_particles)
+        d.hbm_fraction, d.pinned_bytes, d.stream, d.polish = float(hbm_fraction), int(pinned_bytes), stream, int(polish)
+        self.h = sph_server_create(d, self.eos)
+        self.n_of = {}
+
+    def submit(self, ev, nsteps: int) -> int:
+        d, keep = event_desc(ev)
+        t = sph_submit(self.h, d, nsteps)
+        self.n_of[t] = ev.n
+        return t
+
+    def pump(self, max_steps: int = 1) -> int:
+        return sph_server_pump(self.h, max_steps)
+
+    def poll(self, ticket: int):
+        return sph_poll(self.h, ticket)
+
+    def collect(self, ticket: int, names=("X", "U", "S", "NQ", "BV", "PV", "T", "MU", "S_DENS", "N_DENS", "NNB")):
+        n = self.n_of.pop(ticket)
+        b = FieldBufs()
+        out, mask = {}, 0
+        for nm in names:
+            rows, attr = _FIELD_SHAPES[nm]
+            dt = np.uint32 if nm == "STATUS" else (np.int32 if nm == "NNB" else np.float64)
+            arr = np.zeros((rows, n) if rows > 1 else n, dtype=dt)
+            out[nm] = arr
+            setattr(b, attr, arr.ctypes.data)
+            mask |= F[nm]
+        t = Totals()
+        sph_collect(self.h, ticket, mask, b, t)
+        out["totals"] = {"tau": t.tau, "E": t.E, "S": t.S, "N": np.array(t.N[:]), "work": t.work,
+                         "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs,
+                         "eos_work": tuple(t.eos_work[:]), "shell_tests": t.shell_tests}
+        return out
+
+    def stats(self) -> dict:
+        return sph_server_stats_get(self.h)
+
+    def drain(self, timeout_s: float = 0.0):
+        sph_server_drain(self.h, timeout_s)
+
+    def free(self):
+        if self.h is not None:
+            sph_server_free(self.h)
+            self.h = None
+        if self.eos is not None:
+            sph_free_eos(self.eos)
+            self.eos = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class GpuEvent:
     """One event on the GPU, built from an ``inputs.Event``."""
 
@@ -214,14 +363,7 @@ class GpuEvent:
             ed, keep = eos_desc(ev.eos, ev.table)
             eos_handle = sph_set_eos_table(ed)
         self.eos = eos_handle
-        d = EventDesc()
-        d.dim, d.milne, d.viscous, d.on_device = ev.dim, int(ev.milne), int(ev.transport.viscous), 0
-        d.n, d.h, d.tau0, d.dtau = ev.n, ev.h, ev.tau0, ev.dtau
-        self._keep = [_f64(ev.x), _f64(ev.u), _f64(ev.S), _f64(ev.Nq), _f64(ev.Bv), _f64(ev.Pv)]
-        d.x, d.u, d.S, d.Nq, d.Bv, d.Pv = [a.ctypes.data if a.size else None for a in self._keep]
-        tr = ev.transport
-        d.eta_over_s, d.zeta_peak, d.zeta_T_GeV, d.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
-        d.tau_pi_coef, d.tau_Pi_ratio, d.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
+        d, self._keep = event_desc(ev)
         d.fatal_mask, d.use_graph = fatal_mask, int(use_graph)
         d.stream = stream
         d.profile = int(profile)

@@ -47,6 +47,9 @@ struct sph_eos {
     int refs = 1;
 };
 
+EosDev sphg::eos_params(const sph_eos *e) { return e->dev; }
+void sphg::eos_retain(sph_eos *e) { e->refs++; }
+
 struct sph_event {
     sph_eos *eos = nullptr;
     int n = 0, dim = 2, milne = 1, viscous = 0, npi = 3, nv = 9, B = 6;
@@ -289,6 +292,7 @@ sph_status sph_set_eos_table(sph_eos **out, const sph_eos_desc *d)
     for (int q = 0; q < 3; ++q) E.chi[q] = d->chi[q];
     E.tol = d->newton_tol > 0.0 ? d->newton_tol : 1e-12;
     E.maxit = d->newton_maxit > 0 ? d->newton_maxit : 30;
+    E.polish = 1;
     E.has_table = d->has_table ? 1 : 0;
     if (E.has_table) {
         if (!d->p || !d->s || !d->nB || !d->nS || !d->nQ) {

@@ -131,9 +131,72 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
     }
 }
 
-// EoS pass, 2+1D: rest-frame densities, inversion, and the per-particle inputs of the
-// gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{tau i},
-// and u^j / sigma*; plus the longitudinal work rate (p + Pi + tau^2 pi^{eta eta}) / sigma*
+// EoS pass, 2+1D, one particle: rest-frame densities, inversion, and the per-particle inputs
+// of the gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{tau i},
+// and u^j / sigma*; returns the particle's longitudinal work rate (p + Pi + tau^2 pi^{eta eta}) / sigma*.
+// Rows are n apart; the EoS work done is added to w.
+__device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E, int stage, size_t n, size_t a,
+                                                const double *__restrict__ y, double *__restrict__ dens,
+                                                double *__restrict__ eos, double *__restrict__ gin,
+                                                uint32_t *__restrict__ status, const double *__restrict__ guess_in,
+                                                double *__restrict__ guess_out, EosWork &w)
+{
+    double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+    double sqrtg = v.milne ? tau : 1.0;
+    double sig_star = dens[a];
+    double u0 = dens[5 * n + a];
+    double vol = u0 * sqrtg;
+    double s = dens[n + a] / vol;
+    double nq[3] = {dens[2 * n + a] / vol, dens[3 * n + a] / vol, dens[4 * n + a] / vol};
+    dens[n + a] = s;
+    for (int q = 0; q < 3; ++q) dens[(2 + q) * n + a] = nq[q];
+    double gs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
+    bool used = false;
+    EosOut o = eos_invert(E, v.tr.cs2_cap, s, nq, gs, used, w);
+    w.resid += 1u;  // + the final evaluation of p, (s, n) and H at the solution
+    guess_out[a] = used ? o.T : 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) guess_out[(1 + q) * n + a] = used ? o.mu[q] : 0.0;
+    status[a] = o.st;
+    eos[a] = o.T;
+    for (int q = 0; q < 3; ++q) eos[(1 + q) * n + a] = o.mu[q];
+    eos[4 * n + a] = o.p;
+    eos[5 * n + a] = o.e;
+    eos[6 * n + a] = o.ps;
+    for (int q = 0; q < 3; ++q) eos[(7 + q) * n + a] = o.pn[q];
+    eos[10 * n + a] = o.cs2;
+    double ux = y[2 * n + a], uy = y[3 * n + a];
+    double vx = ux / u0, vy = uy / u0;
+    double sigma = sig_star / vol;
+    double Pi = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
+    if (v.tr.viscous) {
+        Pi = sigma * y[5 * n + a];
+        pxx = sigma * y[6 * n + a];
+        pxy = sigma * y[7 * n + a];
+        pyy = sigma * y[8 * n + a];
+    }
+    double ptx = vx * pxx + vy * pxy;  // pi^{tau x}
+    double pty = vx * pxy + vy * pyy;  // pi^{tau y}
+    double inv2 = 1.0 / (sig_star * sig_star);
+    double P = o.p + Pi;
+    gin[a] = (P + pxx - vx * ptx) * inv2;                 // X^{xx}
+    gin[n + a] = (pxy - vx * pty) * inv2;                 // X^{xy}  (j = x, i = y)
+    gin[2 * n + a] = (pxy - vy * ptx) * inv2;             // X^{yx}  (j = y, i = x)
+    gin[3 * n + a] = (P + pyy - vy * pty) * inv2;         // X^{yy}
+    gin[4 * n + a] = ux / sig_star;
+    gin[5 * n + a] = uy / sig_star;
+    double wcontrib = 0.0;
+    if (v.milne) {
+        double ptt = vx * ptx + vy * pty;
+        double t2pee = ptt - pxx - pyy;  // tau^2 pi^{eta eta} from tracelessness
+        wcontrib = (P + t2pee) / sig_star;
+    }
+    warp_or(&v.sc->status_or, o.st);
+    return wcontrib;
+}
+
 __global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const double *__restrict__ y,
                                              double *__restrict__ dens, double *__restrict__ eos,
                                              double *__restrict__ gin, uint32_t *__restrict__ status,
@@ -142,70 +205,15 @@ __global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const doubl
 {
     __shared__ double red[2];
     int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = v.n;
     double wcontrib = 0.0;
-    unsigned wres = 0u, wsol = 0u, wg = 0u;
-    if (a < n) {
-        double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-        double sqrtg = v.milne ? tau : 1.0;
-        double sig_star = dens[a];
-        double u0 = dens[5 * (size_t)n + a];
-        double vol = u0 * sqrtg;
-        double s = dens[(size_t)n + a] / vol;
-        double nq[3] = {dens[2 * (size_t)n + a] / vol, dens[3 * (size_t)n + a] / vol, dens[4 * (size_t)n + a] / vol};
-        dens[(size_t)n + a] = s;
-        for (int q = 0; q < 3; ++q) dens[(2 + q) * (size_t)n + a] = nq[q];
-        double gs[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) gs[k] = guess_in[(size_t)k * n + a];
-        bool used = false;
-        EosWork w = {0u, 0u, 0u};
-        EosOut o = eos_invert(v.eos, v.tr.cs2_cap, s, nq, gs, used, w);
-        wres = w.resid + 1u;  // + the final evaluation of p, (s, n) and H at the solution
-        wsol = w.solve;
-        wg = w.g;
-        guess_out[a] = used ? o.T : 0.0;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) guess_out[(size_t)(1 + q) * n + a] = used ? o.mu[q] : 0.0;
-        status[a] = o.st;
-        warp_or(&v.sc->status_or, o.st);
-        eos[a] = o.T;
-        for (int q = 0; q < 3; ++q) eos[(1 + q) * (size_t)n + a] = o.mu[q];
-        eos[4 * (size_t)n + a] = o.p;
-        eos[5 * (size_t)n + a] = o.e;
-        eos[6 * (size_t)n + a] = o.ps;
-        for (int q = 0; q < 3; ++q) eos[(7 + q) * (size_t)n + a] = o.pn[q];
-        eos[10 * (size_t)n + a] = o.cs2;
-        double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
-        double vx = ux / u0, vy = uy / u0;
-        double sigma = sig_star / vol;
-        double Pi = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
-        if (v.tr.viscous) {
-            Pi = sigma * y[5 * (size_t)n + a];
-            pxx = sigma * y[6 * (size_t)n + a];
-            pxy = sigma * y[7 * (size_t)n + a];
-            pyy = sigma * y[8 * (size_t)n + a];
-        }
-        double ptx = vx * pxx + vy * pxy;  // pi^{tau x}
-        double pty = vx * pxy + vy * pyy;  // pi^{tau y}
-        double inv2 = 1.0 / (sig_star * sig_star);
-        double P = o.p + Pi;
-        gin[a] = (P + pxx - vx * ptx) * inv2;                     // X^{xx}
-        gin[(size_t)n + a] = (pxy - vx * pty) * inv2;             // X^{xy}  (j = x, i = y)
-        gin[2 * (size_t)n + a] = (pxy - vy * ptx) * inv2;         // X^{yx}  (j = y, i = x)
-        gin[3 * (size_t)n + a] = (P + pyy - vy * pty) * inv2;     // X^{yy}
-        gin[4 * (size_t)n + a] = ux / sig_star;
-        gin[5 * (size_t)n + a] = uy / sig_star;
-        if (v.milne) {
-            double ptt = vx * ptx + vy * pty;
-            double t2pee = ptt - pxx - pyy;  // tau^2 pi^{eta eta} from tracelessness
-            wcontrib = (P + t2pee) / sig_star;
-        }
-    }
+    EosWork w = {0u, 0u, 0u};
+    if (a < v.n)
+        wcontrib = eos2_particle(v, v.eos, stage, (size_t)v.n, (size_t)a, y, dens, eos, gin, status, guess_in,
+                                 guess_out, w);
     // work counters (warp-aggregated) and the deterministic block sum of the work rate
-    wres = __reduce_add_sync(0xFFFFFFFFu, wres);
-    wsol = __reduce_add_sync(0xFFFFFFFFu, wsol);
-    wg = __reduce_add_sync(0xFFFFFFFFu, wg);
+    unsigned wres = __reduce_add_sync(0xFFFFFFFFu, w.resid);
+    unsigned wsol = __reduce_add_sync(0xFFFFFFFFu, w.solve);
+    unsigned wg = __reduce_add_sync(0xFFFFFFFFu, w.g);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&v.sc->eos_resid, (unsigned long long)wres);
         atomicAdd(&v.sc->eos_solve, (unsigned long long)wsol);
@@ -215,6 +223,37 @@ __global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const doubl
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wcontrib;
     __syncthreads();
     if (threadIdx.x == 0) wpart[blockIdx.x] = red[0] + red[1];
+}
+
+// Serving form: the same EoS pass over the segmented arena (persistent grid).  A warp
+// never straddles two events, so the work-rate partial of every warp of an event's range
+// goes to wpart[a / 32] and the per-event counters are warp-aggregated.
+__global__ void __launch_bounds__(64, 6) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    const size_t P = (size_t)A.P;
+    for (int base = blockIdx.x * 64; base < hi; base += gridDim.x * 64) {
+        const int a = base + threadIdx.x;
+        const int s = A.segid[a];  // warp-uniform: ranges are multiples of 256 and hi is a range end
+        if (s < 0 || !seg_active(T, s, stage, false)) continue;
+        const SegSlot sl = T->slots[s];
+        double wc = 0.0;
+        EosWork w = {0u, 0u, 0u};
+        if (a - sl.off < sl.n)
+            wc = eos2_particle(A.segv[s], E, stage, P, (size_t)a, y, A.dens, A.eosf, A.gin, A.status, A.guess_in,
+                               A.wguess, w);
+        for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xFFFFFFFFu, wc, o);
+        const unsigned wres = __reduce_add_sync(0xFFFFFFFFu, w.resid);
+        const unsigned wsol = __reduce_add_sync(0xFFFFFFFFu, w.solve);
+        const unsigned wg = __reduce_add_sync(0xFFFFFFFFu, w.g);
+        if ((threadIdx.x & 31) == 0) {
+            A.wpart[a >> 5] = wc;
+            atomicAdd(&A.sc[s].eos_resid, (unsigned long long)wres);
+            atomicAdd(&A.sc[s].eos_solve, (unsigned long long)wsol);
+            atomicAdd(&A.sc[s].eos_g, (unsigned long long)wg);
+        }
+    }
 }
 
 inline int nblk(int n, int t) { return (n + t - 1) / t; }
@@ -248,5 +287,10 @@ void launch_eos(const EvView &v, int stage, const double *y, const double *dens,
 }
 
 int eom_block_count(int n) { return nblk(n, 64); }
+
+void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st)
+{
+    k_eos2_seg<<<grid, 64, 0, st>>>(A, E, stage, y);
+}
 
 }  // namespace sphg

@@ -251,6 +251,7 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
     for (int it = 0; it < E.maxit; ++it) {
         double d[4] = {-r[0], -r[1], -r[2], -r[3]};
         if (rn <= E.tol) {
+            if (!E.polish) return true;
             ++w.solve;
             if (solve4(J, d)) {  // one polishing step if it does not increase the residual
                 double xn[4] = {x[0] + d[0], x[1] + d[1], x[2] + d[2], x[3] + d[3]};

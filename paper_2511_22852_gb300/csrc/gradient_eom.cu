@@ -128,14 +128,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_gradient2(EvView v, int stage, 
     }
 }
 
-__global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, const double *__restrict__ ys,
-                                              const double *__restrict__ dens, const double *__restrict__ eos,
-                                              const double *__restrict__ gout, double *__restrict__ yout,
-                                              double *__restrict__ rates, uint32_t *__restrict__ status)
+// equations of motion of one particle (rows n apart): mode 0 writes y1 = y + dt f(y),
+// mode 1 closes Heun in place, mode 2 writes the rates
+__device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mode, size_t n, size_t a,
+                                              const double *__restrict__ ys, const double *__restrict__ dens,
+                                              const double *__restrict__ eos, const double *__restrict__ gout,
+                                              double *__restrict__ yout, double *__restrict__ rates,
+                                              uint32_t *__restrict__ status)
 {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= v.n) return;
-    const size_t n = (size_t)v.n;
     double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
     double hub = v.milne ? 1.0 / tau : 0.0;      // Gamma^eta_{eta tau}
     double sqrtg = v.milne ? tau : 1.0;
@@ -259,6 +259,31 @@ __global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, con
     }
 }
 
+__global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, const double *__restrict__ ys,
+                                              const double *__restrict__ dens, const double *__restrict__ eos,
+                                              const double *__restrict__ gout, double *__restrict__ yout,
+                                              double *__restrict__ rates, uint32_t *__restrict__ status)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= v.n) return;
+    eom2_particle(v, stage, mode, (size_t)v.n, (size_t)a, ys, dens, eos, gout, yout, rates, status);
+}
+
+// Serving form: the equations of motion over the segmented arena (persistent grid)
+__global__ void __launch_bounds__(128) k_eom2_seg(Arena A, int stage, int mode, const double *__restrict__ ys,
+                                                  double *__restrict__ yout)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < hi; a += gridDim.x * blockDim.x) {
+        const int s = A.segid[a];
+        if (s < 0 || !seg_active(T, s, stage, true)) continue;
+        if (a - T->slots[s].off >= T->slots[s].n) continue;
+        eom2_particle(A.segv[s], stage, mode, (size_t)A.P, (size_t)a, ys, A.dens, A.eosf, A.gout, yout, nullptr,
+                      A.status);
+    }
+}
+
 // stage work rate: fixed-order tree sum of the per-block partials; stage 2
 // closes the step (Heun quadrature of the work integral, tau += dtau)
 __global__ void __launch_bounds__(256) k_work_finish(EvView v, int stage, const double *__restrict__ wpart, int nblk)
@@ -365,6 +390,12 @@ void launch_eom(const EvView &v, int stage, int mode, const double *ys, const do
         return;
     }
     k_eom2<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, mode, ys, dens, eos, gout, yout, rates, status);
+}
+
+void launch_eom2_seg(const Arena &A, int stage, int mode, const double *ys, double *yout, int grid,
+                     cudaStream_t st)
+{
+    k_eom2_seg<<<grid, 128, 0, st>>>(A, stage, mode, ys, yout);
 }
 
 void launch_work_finish(const EvView &v, int stage, const double *wpart, int nb, cudaStream_t st)

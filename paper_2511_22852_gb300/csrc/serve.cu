@@ -1,0 +1,1495 @@
+// serve.cu -- the serving form: continuous batching of 2+1D events in one segmented
+// particle arena, neighbour passes in single precision (the mixed form), EoS inversion,
+// equations of motion and reductions in double precision.
+//
+// Device side.  Every per-particle row of the arena has stride P (the capacity).  An
+// admitted event owns [off, off + cap) of every row (off, cap multiples of 256); its
+// particles sit in [off, off + n) in (cell, id) order after each stage's sort.  Per slot
+// the device holds the event's parameters (EvView), its evolving scalars (DevScalars:
+// tau, work integral, counters) and, per stage, its bounding box and cell grid (SegGrid).
+// One batch step = two Heun stages over all admitted events:
+//   bbox -> grid -> count -> scan -> scatter -> rank -> permute -> density (tiled, FP32)
+//   -> EoS (FP64) -> gradient (tiled, FP32) -> equations of motion (FP64) -> work integral
+// with the same buffer rotation as a single event (stage 1: A -> B, C = B + dt f(B);
+// stage 2: C -> D, B -> A, A = ((A + D) + dt f(D)) / 2).  The kernels read the slot table
+// from device memory and loop over the arena (or its cells) with a fixed grid, so the
+// whole step is captured once as a CUDA graph and replayed for every composition.
+//
+// The neighbour passes are cell-tiled: one block per cell stages the particles of the 3x3
+// neighbouring cells (three contiguous runs of the sorted arena, one per cell row) in
+// shared memory as positions relative to the centre cell's origin, and every particle of
+// the cell scans them (1, 2 or 4 lanes per particle, by occupancy of the cell).  A proven
+// bound on the float r^2 decides all but a thin shell of candidates; inside the shell the
+// FP64 test r^2 < (2h)^2 with separately rounded products decides, so the neighbour sets
+// are exactly those of the FP64 form.  Sums are Neumaier-compensated per lane and combined
+// across lanes in FP64 in a fixed order: an event's results do not depend on what else is
+// in the batch or where its range lies.
+//
+// Host side.  sph_submit copies an event into pinned staging and queues it; each
+// sph_server_pump step admits queued events while a slot and an arena range are free
+// (the arena is carved from free HBM at creation), replays the step graph, and retires
+// events that finished their steps: a finished event takes one more stage-1 evaluation
+// (observe mode: cells, densities, EoS at the final state), then its fields are scattered
+// to the original order and copied to its pinned block; a CUDA event marks them readable.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sph_gb300.h"
+#include "sph_internal.cuh"
+
+using namespace sphg;
+
+namespace {
+
+constexpr int kScanBlocks = 256;
+constexpr int kTT = 128;    // threads of a tiled neighbour block
+constexpr int kTile = 512;  // candidates staged in shared memory at a time
+
+// ---------------------------------------------------------------------------
+// single-precision helpers (Neumaier two-sum accumulation, cubic spline kernel)
+struct CSum {
+    float hi, lo;
+};
+__device__ __forceinline__ void cadd(CSum &s, float x)
+{
+    float t = s.hi + x;
+    if (fabsf(s.hi) >= fabsf(x)) s.lo += (s.hi - t) + x;
+    else s.lo += (x - t) + s.hi;
+    s.hi = t;
+}
+__device__ __forceinline__ double cval(CSum s) { return (double)s.hi + (double)s.lo; }
+__device__ __forceinline__ float kernel_wf(float q)
+{
+    if (q <= 1.0f) return fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
+    float t = 2.0f - q;
+    return 0.25f * t * t * t;
+}
+__device__ __forceinline__ float kernel_dwf(float q)
+{
+    if (q <= 1.0f) return q * fmaf(2.25f, q, -3.0f);
+    float t = 2.0f - q;
+    return -0.75f * t * t;
+}
+__device__ __forceinline__ double inf_d() { return __longlong_as_double(0x7FF0000000000000LL); }
+
+// ---------------------------------------------------------------------------
+// cell list of every active event (rows a1, a2)
+__global__ void k_seg_reset(Arena A)
+{
+    const int ns = A.tab->nslots;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        SegGrid &g = A.grid[s];
+        g.bb[0] = g.bb[1] = enc_double(inf_d());
+        g.bb[2] = g.bb[3] = enc_double(-inf_d());
+    }
+}
+
+// bounding box per event: warp-reduced, one atomic per warp (a warp lies in one range)
+__global__ void k_seg_bbox(Arena A, int stage, const double *__restrict__ y)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    const size_t P = (size_t)A.P;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < hi; a += gridDim.x * blockDim.x) {
+        const int s = A.segid[a];
+        if (s < 0 || !seg_active(T, s, stage, false)) continue;
+        const bool v = a - T->slots[s].off < T->slots[s].n;
+        double mnx = v ? y[a] : inf_d(), mny = v ? y[P + a] : inf_d();
+        double mxx = v ? y[a] : -inf_d(), mxy = v ? y[P + a] : -inf_d();
+        for (int o = 16; o > 0; o >>= 1) {
+            mnx = fmin(mnx, __shfl_xor_sync(0xFFFFFFFFu, mnx, o));
+            mny = fmin(mny, __shfl_xor_sync(0xFFFFFFFFu, mny, o));
+            mxx = fmax(mxx, __shfl_xor_sync(0xFFFFFFFFu, mxx, o));
+            mxy = fmax(mxy, __shfl_xor_sync(0xFFFFFFFFu, mxy, o));
+        }
+        if ((threadIdx.x & 31) == 0 && mnx <= mxx && mny <= mxy) {
+            atomicMin(&A.grid[s].bb[0], enc_double(mnx));
+            atomicMin(&A.grid[s].bb[1], enc_double(mny));
+            atomicMax(&A.grid[s].bb[2], enc_double(mxx));
+            atomicMax(&A.grid[s].bb[3], enc_double(mxy));
+        }
+    }
+}
+
+// number of cells of side 2h from the minimum to v, clamped to [1, kMaxCellsAxis]
+__device__ __forceinline__ int cells_to(double v, double v0, double inv_cell)
+{
+    if (!(v >= v0)) return 1;
+    const double f = floor(__dmul_rn(__dsub_rn(v, v0), inv_cell));
+    return f >= (double)(kMaxCellsAxis - 1) ? kMaxCellsAxis : (int)f + 1;
+}
+
+// cell grid per event and the offset of its cells in the shared bucket table
+__global__ void __launch_bounds__(kMaxSlots) k_seg_grid(Arena A, int stage)
+{
+    __shared__ int sh[kMaxSlots];
+    const BatchTable *T = A.tab;
+    const int s = threadIdx.x;
+    int nc = 0;
+    if (s < T->nslots && seg_active(T, s, stage, false)) {
+        SegGrid &g = A.grid[s];
+        const double ic = A.segv[s].inv_cell;
+        const double x0 = dec_double(g.bb[0]), y0 = dec_double(g.bb[1]);
+        const int nx = cells_to(dec_double(g.bb[2]), x0, ic), ny = cells_to(dec_double(g.bb[3]), y0, ic);
+        g.x0 = x0;
+        g.y0 = y0;
+        g.nx = nx;
+        g.ny = ny;
+        nc = nx * ny;
+    }
+    sh[s] = nc;
+    __syncthreads();
+    for (int o = 1; o < kMaxSlots; o <<= 1) {  // inclusive Hillis-Steele scan
+        int v = s >= o ? sh[s - o] : 0;
+        __syncthreads();
+        sh[s] += v;
+        __syncthreads();
+    }
+    if (s < T->nslots) {
+        A.grid[s].base = sh[s] - nc;
+        A.grid[s].ncell = nc;
+    }
+    if (s == kMaxSlots - 1) *A.ncells = sh[s];
+}
+
+__global__ void k_seg_zero(Arena A)
+{
+    const int nc = *A.ncells;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) A.cnt[c] = 0u;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__global__ void k_seg_keys(Arena A, int stage, const double *__restrict__ y)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    const size_t P = (size_t)A.P;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < hi; a += gridDim.x * blockDim.x) {
+        const int s = A.segid[a];
+        if (s < 0 || !seg_active(T, s, stage, false) || a - T->slots[s].off >= T->slots[s].n) continue;
+        const SegGrid &g = A.grid[s];
+        const double ic = A.segv[s].inv_cell;
+        const int cx = clampi(cell_coord(y[a], g.x0, ic), 0, g.nx - 1);
+        const int cy = clampi(cell_coord(y[P + a], g.y0, ic), 0, g.ny - 1);
+        const uint32_t k = (uint32_t)(g.base + cy * g.nx + cx);
+        A.key[a] = k;
+        A.rnk[a] = atomicAdd(&A.cnt[k], 1u);
+    }
+}
+
+// exclusive scan of the bucket counts (device-sized: the total is read on the device)
+__device__ __forceinline__ uint32_t block_sum_256(uint32_t v, uint32_t *sh)
+{
+    v = __reduce_add_sync(0xFFFFFFFFu, v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_seg_scan_part(Arena A)
+{
+    __shared__ uint32_t sh[8];
+    const int nc = *A.ncells;
+    const int chunk = (nc + kScanBlocks - 1) / kScanBlocks;
+    const int lo = blockIdx.x * chunk, hi = min(nc, lo + chunk);
+    uint32_t acc = 0u;
+    for (int i = lo + threadIdx.x; i < hi; i += 256) acc += A.cnt[i];
+    const uint32_t t = block_sum_256(acc, sh);
+    if (threadIdx.x == 0) A.scan_part[blockIdx.x] = t;
+}
+
+// exclusive scan of 256 values held one per thread; returns this thread's prefix, *total the sum
+__device__ __forceinline__ uint32_t block_exscan_256(uint32_t v, uint32_t *sh, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    uint32_t wp = 0, tot = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (k < w) wp += sh[k];
+        tot += sh[k];
+    }
+    __syncthreads();
+    *total = tot;
+    return wp + x - v;
+}
+
+__global__ void __launch_bounds__(256) k_seg_scan_top(Arena A)
+{
+    __shared__ uint32_t sh[8];
+    uint32_t tot;
+    const uint32_t v = A.scan_part[threadIdx.x];
+    const uint32_t ex = block_exscan_256(v, sh, &tot);
+    A.scan_part[threadIdx.x] = ex;
+}
+
+__global__ void __launch_bounds__(256) k_seg_scan_apply(Arena A)
+{
+    __shared__ uint32_t sh[8];
+    const int nc = *A.ncells;
+    const int chunk = (nc + kScanBlocks - 1) / kScanBlocks;
+    const int lo = blockIdx.x * chunk, hi = min(nc, lo + chunk);
+    uint32_t carry = A.scan_part[blockIdx.x];
+    for (int t0 = lo; t0 < hi; t0 += 256) {
+        const int i = t0 + threadIdx.x;
+        const uint32_t v = i < hi ? A.cnt[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exscan_256(v, sh, &tot);
+        if (i < hi) A.start[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+// bucket slot of every particle, then the deterministic order inside a cell: rank by id
+__global__ void k_seg_scatter(Arena A, int stage)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < hi; a += gridDim.x * blockDim.x) {
+        const int s = A.segid[a];
+        if (s < 0 || !seg_active(T, s, stage, false)) continue;
+        const SegSlot sl = T->slots[s];
+        if (a - sl.off >= sl.n) continue;
+        const uint32_t k = A.key[a];
+        const int j = sl.off + (int)(A.start[k] - A.start[A.grid[s].base]) + (int)A.rnk[a];
+        A.tmp[j] = (uint32_t)a;
+    }
+}
+
+__global__ void k_seg_rank(Arena A, int stage, const int *__restrict__ id)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < hi; j += gridDim.x * blockDim.x) {
+        const int s = A.segid[j];
+        if (s < 0 || !seg_active(T, s, stage, false)) continue;
+        const SegSlot sl = T->slots[s];
+        if (j - sl.off >= sl.n) continue;
+        const uint32_t p = A.tmp[j];
+        const uint32_t k = A.key[p];
+        const int c0 = sl.off + (int)(A.start[k] - A.start[A.grid[s].base]);
+        const int c1 = c0 + (int)A.cnt[k];
+        const int my = id[p];
+        int r = 0;
+        for (int m = c0; m < c1; ++m) r += id[A.tmp[m]] < my;
+        A.perm[c0 + r] = p;
+    }
+}
+
+struct SegPerm {
+    const double *src[4];
+    double *dst[4];
+    int rows[4];
+    int ng;
+    const int *id_in;
+    int *id_out;
+};
+
+__global__ void k_seg_permute(Arena A, int stage, SegPerm pa)
+{
+    const BatchTable *T = A.tab;
+    const int hi = T->hi;
+    const size_t P = (size_t)A.P;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < hi; j += gridDim.x * blockDim.x) {
+        const int s = A.segid[j];
+        if (s < 0 || !seg_active(T, s, stage, false) || j - T->slots[s].off >= T->slots[s].n) continue;
+        const size_t p = A.perm[j];
+        for (int g = 0; g < pa.ng; ++g)
+            for (int r = 0; r < pa.rows[g]; ++r) pa.dst[g][r * P + j] = pa.src[g][r * P + p];
+        pa.id_out[j] = pa.id_in[p];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// cell-tiled neighbour passes (rows a3, a5)
+struct CellCtx {
+    int s, first, na, M, clamped;
+    int rs[3], rl[3];  // the three candidate runs (one per cell row): start, length
+    double ox, oy;     // origin of the centre cell
+};
+
+// last slot whose first cell is <= c (slots without cells share the next slot's base)
+__device__ __forceinline__ int find_slot(const int *base, int ns, int c)
+{
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ void cell_setup(const Arena &A, const int *s_base, int ns, int c, CellCtx &cc)
+{
+    const int s = find_slot(s_base, ns, c);
+    const SegGrid g = A.grid[s];
+    const int off = A.tab->slots[s].off;
+    const uint32_t S0 = A.start[g.base];
+    const int lc = c - g.base, cx = lc % g.nx, cy = lc / g.nx;
+    cc.s = s;
+    cc.clamped = g.nx >= kMaxCellsAxis || g.ny >= kMaxCellsAxis;
+    cc.first = off + (int)(A.start[c] - S0);
+    cc.na = (int)A.cnt[c];
+    const double cs = 2.0 * A.segv[s].h;
+    cc.ox = g.x0 + (double)cx * cs;
+    cc.oy = g.y0 + (double)cy * cs;
+    int M = 0;
+    for (int o = 0; o < 3; ++o) {
+        const int r = cy - 1 + o;
+        int st = 0, ln = 0;
+        if (r >= 0 && r < g.ny) {
+            const int k0 = g.base + r * g.nx + max(cx - 1, 0);
+            const int k1 = g.base + r * g.nx + min(cx + 1, g.nx - 1);
+            st = off + (int)(A.start[k0] - S0);
+            ln = (int)(A.start[k1] + A.cnt[k1] - A.start[k0]);
+        }
+        cc.rs[o] = st;
+        cc.rl[o] = ln;
+        M += ln;
+    }
+    cc.M = M;
+}
+
+__device__ __forceinline__ int cand_index(const CellCtx &cc, int q)
+{
+    if (q < cc.rl[0]) return cc.rs[0] + q;
+    q -= cc.rl[0];
+    if (q < cc.rl[1]) return cc.rs[1] + q;
+    return cc.rs[2] + q - cc.rl[1];
+}
+
+__global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__restrict__ y,
+                                                     const double *__restrict__ Nq)
+{
+    __shared__ int s_base[kMaxSlots];
+    __shared__ float2 cpos[kTile];
+    __shared__ float4 cq[kTile];
+    __shared__ int cidx[kTile];
+    __shared__ CellCtx cc;
+    const BatchTable *T = A.tab;
+    const int ns = T->nslots;
+    for (int i = threadIdx.x; i < ns; i += kTT) s_base[i] = A.grid[i].base;
+    __syncthreads();
+    const int ncells = *A.ncells;
+    const size_t P = (size_t)A.P;
+    const int tid = threadIdx.x;
+    for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
+        if (tid == 0) cell_setup(A, s_base, ns, c, cc);
+        __syncthreads();
+        const int na = cc.na;
+        if (na > 0) {
+            const EvView &V = A.segv[cc.s];
+            const float ih = (float)V.inv_h;
+            const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
+            const double supp2 = V.supp2, sd = V.sigma_d;
+            const int L = na <= 32 ? 4 : (na <= 64 ? 2 : 1);
+            const int l = tid & (L - 1);
+            unsigned long long pairs = 0ull, shell = 0ull;
+            for (int g0 = 0; g0 < na; g0 += kTT / L) {
+                const int my = g0 + tid / L;
+                const bool valid = my < na;
+                const int a = cc.first + (valid ? my : 0);
+                const double xa = y[a], ya = y[P + a];
+                const float fax = (float)(xa - cc.ox), fay = (float)(ya - cc.oy);
+                CSum sg = {0.f, 0.f}, ss = {0.f, 0.f}, sb = {0.f, 0.f}, sS = {0.f, 0.f}, sq = {0.f, 0.f};
+                int nacc = 0;
+                for (int t0 = 0; t0 < cc.M; t0 += kTile) {
+                    const int mt = min(kTile, cc.M - t0);
+                    __syncthreads();
+                    for (int i = tid; i < mt; i += kTT) {
+                        const int b = cand_index(cc, t0 + i);
+                        cpos[i] = make_float2((float)(y[b] - cc.ox), (float)(y[P + b] - cc.oy));
+                        cq[i] = make_float4((float)y[4 * P + b], (float)Nq[b], (float)Nq[P + b], (float)Nq[2 * P + b]);
+                        cidx[i] = b;
+                    }
+                    __syncthreads();
+                    if (valid) {
+                        for (int j = l; j < mt; j += L) {
+                            const float2 pb = cpos[j];
+                            const float dx = fax - pb.x, dy = fay - pb.y;
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            if (r2 <= shi) {
+                                bool acc = r2 < slo;
+                                if (!acc) {  // thin shell: the exact FP64 decision
+                                    const int b = cidx[j];
+                                    acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                                    ++shell;
+                                }
+                                if (acc) {
+                                    const float q = r2 > 0.0f ? r2 * rsqrtf(r2) * ih : 0.0f;
+                                    const float w = kernel_wf(q);
+                                    const float4 v = cq[j];
+                                    cadd(sg, w);
+                                    cadd(ss, v.x * w);
+                                    cadd(sb, v.y * w);
+                                    cadd(sS, v.z * w);
+                                    cadd(sq, v.w * w);
+                                    ++nacc;
+                                }
+                            }
+                        }
+                    }
+                }
+                double tg = cval(sg), ts = cval(ss), tb = cval(sb), tS = cval(sS), tq = cval(sq);
+                for (int o = 1; o < L; o <<= 1) {
+                    tg += __shfl_xor_sync(0xFFFFFFFFu, tg, o);
+                    ts += __shfl_xor_sync(0xFFFFFFFFu, ts, o);
+                    tb += __shfl_xor_sync(0xFFFFFFFFu, tb, o);
+                    tS += __shfl_xor_sync(0xFFFFFFFFu, tS, o);
+                    tq += __shfl_xor_sync(0xFFFFFFFFu, tq, o);
+                    nacc += __shfl_xor_sync(0xFFFFFFFFu, nacc, o);
+                }
+                if (valid && l == 0) {
+                    const double ux = y[2 * P + a], uy = y[3 * P + a];
+                    A.dens[a] = sd * tg;
+                    A.dens[P + a] = sd * ts;
+                    A.dens[2 * P + a] = sd * tb;
+                    A.dens[3 * P + a] = sd * tS;
+                    A.dens[4 * P + a] = sd * tq;
+                    A.dens[5 * P + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+                    A.nnb[a] = nacc;
+                    pairs += (unsigned long long)nacc;
+                }
+            }
+            pairs = __reduce_add_sync(0xFFFFFFFFu, (unsigned)pairs);
+            shell = __reduce_add_sync(0xFFFFFFFFu, (unsigned)shell);
+            if ((tid & 31) == 0) {
+                if (pairs) atomicAdd(&A.sc[cc.s].pairs, pairs);
+                if (shell) atomicAdd(&A.sc[cc.s].shell_tests, shell);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const double *__restrict__ y)
+{
+    __shared__ int s_base[kMaxSlots];
+    __shared__ float2 cpos[kTile];
+    __shared__ float4 cX[kTile];
+    __shared__ float2 cU[kTile];
+    __shared__ int cidx[kTile];
+    __shared__ CellCtx cc;
+    const BatchTable *T = A.tab;
+    const int ns = T->nslots;
+    for (int i = threadIdx.x; i < ns; i += kTT) s_base[i] = A.grid[i].base;
+    __syncthreads();
+    const int ncells = *A.ncells;
+    const size_t P = (size_t)A.P;
+    const double *gin = A.gin;
+    const int tid = threadIdx.x;
+    for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
+        if (tid == 0) cell_setup(A, s_base, ns, c, cc);
+        __syncthreads();
+        const int na = cc.na;
+        if (na > 0 && T->slots[cc.s].mode == SLOT_STEP) {
+            const EvView &V = A.segv[cc.s];
+            const float ih = (float)V.inv_h;
+            const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
+            const double supp2 = V.supp2;
+            const int L = na <= 32 ? 4 : (na <= 64 ? 2 : 1);
+            const int l = tid & (L - 1);
+            for (int g0 = 0; g0 < na; g0 += kTT / L) {
+                const int my = g0 + tid / L;
+                const bool valid = my < na;
+                const int a = cc.first + (valid ? my : 0);
+                const double xa = y[a], ya = y[P + a];
+                const float fax = (float)(xa - cc.ox), fay = (float)(ya - cc.oy);
+                CSum Gx = {0.f, 0.f}, Gy = {0.f, 0.f}, Hx = {0.f, 0.f}, Hy = {0.f, 0.f};
+                CSum xx = {0.f, 0.f}, xy = {0.f, 0.f}, yx = {0.f, 0.f}, yy = {0.f, 0.f};
+                for (int t0 = 0; t0 < cc.M; t0 += kTile) {
+                    const int mt = min(kTile, cc.M - t0);
+                    __syncthreads();
+                    for (int i = tid; i < mt; i += kTT) {
+                        const int b = cand_index(cc, t0 + i);
+                        cpos[i] = make_float2((float)(y[b] - cc.ox), (float)(y[P + b] - cc.oy));
+                        cX[i] = make_float4((float)gin[b], (float)gin[P + b], (float)gin[2 * P + b],
+                                            (float)gin[3 * P + b]);
+                        cU[i] = make_float2((float)gin[4 * P + b], (float)gin[5 * P + b]);
+                        cidx[i] = b;
+                    }
+                    __syncthreads();
+                    if (valid) {
+                        for (int j = l; j < mt; j += L) {
+                            const float2 pb = cpos[j];
+                            const float dx = fax - pb.x, dy = fay - pb.y;
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            if (r2 <= shi && r2 > 0.0f) {
+                                bool acc = r2 < slo;
+                                if (!acc) {
+                                    const int b = cidx[j];
+                                    acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                                }
+                                if (acc) {
+                                    const float ir = rsqrtf(r2);
+                                    const float fac = kernel_dwf(r2 * ir * ih) * ir;
+                                    const float gx = fac * dx, gy = fac * dy;
+                                    const float4 X = cX[j];
+                                    const float2 U = cU[j];
+                                    cadd(Gx, gx);
+                                    cadd(Gy, gy);
+                                    cadd(Hx, fmaf(X.x, gx, X.z * gy));
+                                    cadd(Hy, fmaf(X.y, gx, X.w * gy));
+                                    cadd(xx, U.x * gx);
+                                    cadd(xy, U.y * gx);
+                                    cadd(yx, U.x * gy);
+                                    cadd(yy, U.y * gy);
+                                }
+                            }
+                        }
+                    }
+                }
+                double tGx = cval(Gx), tGy = cval(Gy), tHx = cval(Hx), tHy = cval(Hy);
+                double t00 = cval(xx), t01 = cval(xy), t10 = cval(yx), t11 = cval(yy);
+                for (int o = 1; o < L; o <<= 1) {
+                    tGx += __shfl_xor_sync(0xFFFFFFFFu, tGx, o);
+                    tGy += __shfl_xor_sync(0xFFFFFFFFu, tGy, o);
+                    tHx += __shfl_xor_sync(0xFFFFFFFFu, tHx, o);
+                    tHy += __shfl_xor_sync(0xFFFFFFFFu, tHy, o);
+                    t00 += __shfl_xor_sync(0xFFFFFFFFu, t00, o);
+                    t01 += __shfl_xor_sync(0xFFFFFFFFu, t01, o);
+                    t10 += __shfl_xor_sync(0xFFFFFFFFu, t10, o);
+                    t11 += __shfl_xor_sync(0xFFFFFFFFu, t11, o);
+                }
+                if (valid && l == 0) {
+                    const double tau = A.sc[cc.s].tau + (stage == 2 ? V.dtau : 0.0);
+                    const double sqrtg = V.milne ? tau : 1.0;
+                    const double cf = V.sigma_d * V.inv_h;
+                    double *go = A.gout;
+                    go[a] = cf * t00;
+                    go[P + a] = cf * t01;
+                    go[2 * P + a] = cf * t10;
+                    go[3 * P + a] = cf * t11;
+                    const double Fx = gin[a] * tGx + gin[2 * P + a] * tGy + tHx;
+                    const double Fy = gin[P + a] * tGx + gin[3 * P + a] * tGy + tHy;
+                    go[4 * P + a] = -sqrtg * cf * Fx;
+                    go[5 * P + a] = -sqrtg * cf * Fy;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// stage work rate per stepping event: fixed-order sum over the warps of its range; stage 2
+// closes the step (Heun quadrature of the work integral, tau += dtau)
+__global__ void k_seg_work(Arena A, int stage)
+{
+    const int s = blockIdx.x;
+    const BatchTable *T = A.tab;
+    if (s >= T->nslots || T->slots[s].mode != SLOT_STEP) return;
+    const SegSlot sl = T->slots[s];
+    const int w0 = sl.off >> 5, w1 = (sl.off + sl.n + 31) >> 5;
+    double acc = 0.0;
+    for (int w = w0 + (int)threadIdx.x; w < w1; w += 32) acc += A.wpart[w];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (threadIdx.x == 0) {
+        DevScalars &sc = A.sc[s];
+        const EvView &V = A.segv[s];
+        sc.wr[stage - 1] = V.milne ? acc : 0.0;
+        if (stage == 2) {
+            sc.work += 0.5 * V.dtau * (sc.wr[0] + sc.wr[1]);
+            sc.tau = sc.tau + V.dtau;
+            sc.steps += 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// admission and retirement
+__global__ void k_seg_admit(Arena A, int slot, int off, int n, int cap)
+{
+    const size_t P = (size_t)A.P;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        const int a = off + i;
+        A.segid[a] = slot;
+        A.id[0][a] = i < n ? i : 0;
+        for (int k = 0; k < 4; ++k) A.wguess[k * P + a] = 0.0;
+    }
+}
+
+__global__ void k_seg_release(Arena A, int off, int cap)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) A.segid[off + i] = -1;
+}
+
+// rows of a retired event's result block (original particle order)
+constexpr int kResRows = 23;  // 9 state, 3 N_q, T, mu x3, p, e, sigma*, s, n_q x3
+constexpr int R_STATE = 0, R_NQ = 9, R_T = 12, R_MU = 13, R_P = 16, R_E = 17, R_SIG = 18, R_S = 19, R_N = 20;
+
+// observe-mode results: the stage-1 buffers (sorted) to the original order, plus the
+// per-particle contributions to the event totals: sqrt(-g) T^{00}/sigma*, S, N_q
+__global__ void k_seg_unsort(Arena A, int slot, double *__restrict__ res, int *__restrict__ ires,
+                             double *__restrict__ contrib)
+{
+    const SegSlot sl = A.tab->slots[slot];
+    const EvView &V = A.segv[slot];
+    const size_t P = (size_t)A.P, n = (size_t)sl.n;
+    const double tau = A.sc[slot].tau;
+    const double sqrtg = V.milne ? tau : 1.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < sl.n; j += gridDim.x * blockDim.x) {
+        const size_t a = (size_t)sl.off + j;
+        const size_t o = (size_t)A.id[1][a];
+        const double *Y = A.Y[1], *N = A.Nq[1];
+        for (int r = 0; r < 9; ++r) res[(R_STATE + r) * n + o] = Y[r * P + a];
+        for (int q = 0; q < 3; ++q) res[(R_NQ + q) * n + o] = N[q * P + a];
+        for (int r = 0; r < 6; ++r) res[(R_T + r) * n + o] = A.eosf[r * P + a];
+        res[R_SIG * n + o] = A.dens[a];
+        for (int r = 0; r < 4; ++r) res[(R_S + r) * n + o] = A.dens[(1 + r) * P + a];
+        ires[o] = A.nnb[a];
+        ires[n + o] = (int)A.status[a];
+        const double sig = A.dens[a], g = A.dens[5 * P + a];
+        const double sigma = sig / (g * sqrtg);
+        const double ux = Y[2 * P + a], uy = Y[3 * P + a];
+        const double vx = ux / g, vy = uy / g;
+        double Pi = 0.0, ptt = 0.0;
+        if (V.tr.viscous) {
+            Pi = sigma * Y[5 * P + a];
+            const double pxx = sigma * Y[6 * P + a], pxy = sigma * Y[7 * P + a], pyy = sigma * Y[8 * P + a];
+            ptt = vx * (vx * pxx + vy * pxy) + vy * (vx * pxy + vy * pyy);
+        }
+        const double p = A.eosf[4 * P + a], e = A.eosf[5 * P + a];
+        const double T00 = (e + p + Pi) * g * g - (p + Pi) + ptt;
+        contrib[o] = sqrtg * T00 / sig;
+        contrib[n + o] = Y[4 * P + a];
+        for (int q = 0; q < 3; ++q) contrib[(2 + q) * n + o] = N[q * P + a];
+    }
+}
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+namespace {
+
+thread_local std::string s_err;
+
+sph_status sfail(sph_status s, const std::string &m)
+{
+    set_last_error(m.c_str());
+    return s;
+}
+
+#define SCK(call)                                                                                         \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return sfail(SPH_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+double now_s() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
+
+// first-fit allocator over [0, size) in units of `align`
+struct RangeAlloc {
+    std::map<long long, long long> fr;  // offset -> length of free ranges
+    long long align = 1;
+    void init(long long size, long long al)
+    {
+        align = al;
+        fr.clear();
+        if (size > 0) fr[0] = size;
+    }
+    long long alloc(long long len)
+    {
+        len = (len + align - 1) / align * align;
+        for (auto it = fr.begin(); it != fr.end(); ++it)
+            if (it->second >= len) {
+                long long off = it->first, rest = it->second - len;
+                fr.erase(it);
+                if (rest > 0) fr[off + len] = rest;
+                return off;
+            }
+        return -1;
+    }
+    void release(long long off, long long len)
+    {
+        len = (len + align - 1) / align * align;
+        auto it = fr.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != fr.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            fr.erase(nx);
+        }
+        if (it != fr.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                fr.erase(it);
+            }
+        }
+    }
+};
+
+enum { TK_QUEUED = 0, TK_RUNNING = 1, TK_RETIRING = 2, TK_DONE = 3 };
+
+struct Ticket {
+    int64_t id = 0;
+    int state = TK_QUEUED;
+    int n = 0, nsteps = 0, steps_left = 0, slot = -1, off = -1, cap = 0;
+    double t_submit = 0.0, t_done = 0.0;
+    unsigned char *pin = nullptr;  // pinned block (or heap when the pool is exhausted)
+    long long pin_off = -1;        // offset in the pool (-1: heap)
+    size_t pin_bytes = 0;
+    bool viscous = false;
+    cudaEvent_t done = nullptr;
+    EvView view{};
+    DevScalars sc0{};
+    // layout of the block: inputs (12 n doubles) overlaid by results afterwards
+    double *in_rows() { return reinterpret_cast<double *>(pin); }
+    double *res() { return reinterpret_cast<double *>(pin); }
+    int *ires() { return reinterpret_cast<int *>(pin + (size_t)kResRows * n * 8); }
+    double *tot() { return reinterpret_cast<double *>(pin + (size_t)kResRows * n * 8 + (size_t)8 * n); }
+    DevScalars *sc_out() { return reinterpret_cast<DevScalars *>(pin + (size_t)kResRows * n * 8 + (size_t)8 * n + 64); }
+    static size_t bytes_for(int n) { return (size_t)kResRows * n * 8 + (size_t)8 * n + 64 + sizeof(DevScalars) + 256; }
+};
+
+}  // namespace
+
+struct sph_server {
+    sph_eos *eos = nullptr;
+    bool eos_held = false;
+    EosDev E{};
+    Arena A{};
+    std::vector<void *> allocs;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int max_events = 0, inflight = 2, grid_p = 0, grid_e = 0, grid_c = 0;
+    int polish = 0;
+    // pinned staging pool
+    unsigned char *pool = nullptr;
+    size_t pool_bytes = 0;
+    RangeAlloc pool_alloc, arena_alloc;
+    // tickets and slots
+    int64_t next_id = 1;
+    std::deque<Ticket *> queue;
+    std::unordered_map<int64_t, Ticket *> tickets;
+    std::vector<Ticket *> slot_owner;
+    std::vector<SegSlot> slots;  // host mirror of the slot table
+    int hi = 0, nslots = 0;
+    bool table_dirty = true;
+    BatchTable *tab_ring = nullptr;  // pinned snapshots of the table
+    int tab_ring_n = 16, tab_ring_i = 0;
+    // device scratch of retirement
+    double *res_d = nullptr, *contrib_d = nullptr, *tot_d = nullptr;
+    int *ires_d = nullptr;
+    int res_cap = 0;
+    // step graph and pacing
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    std::vector<cudaEvent_t> step_ev;
+    long long steps_launched = 0;
+    cudaEvent_t ref_ev = nullptr;
+    double ref_host = 0.0;
+    // statistics
+    long long particle_steps = 0, launches = 0;
+    double timeout_s = 60.0;
+};
+
+namespace {
+
+sph_status dmalloc(sph_server *S, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(SPH_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    S->allocs.push_back(*p);
+    return SPH_OK;
+}
+
+constexpr int kKernelsPerBatchStep = 2 * 14;
+
+// one batch step (both stages) on the server's stream; captured once into a graph
+void enqueue_batch_step(sph_server *S)
+{
+    const Arena &A = S->A;
+    cudaStream_t st = S->st;
+    const size_t P = (size_t)A.P;
+    for (int stage = 1; stage <= 2; ++stage) {
+        const double *ysrc = stage == 1 ? A.Y[0] : A.Y1[0];
+        const int *idsrc = stage == 1 ? A.id[0] : A.id[1];
+        k_seg_reset<<<1, 256, 0, st>>>(A);
+        k_seg_bbox<<<S->grid_p, 256, 0, st>>>(A, stage, ysrc);
+        k_seg_grid<<<1, kMaxSlots, 0, st>>>(A, stage);
+        k_seg_zero<<<S->grid_p, 256, 0, st>>>(A);
+        k_seg_keys<<<S->grid_p, 256, 0, st>>>(A, stage, ysrc);
+        k_seg_scan_part<<<kScanBlocks, 256, 0, st>>>(A);
+        k_seg_scan_top<<<1, 256, 0, st>>>(A);
+        k_seg_scan_apply<<<kScanBlocks, 256, 0, st>>>(A);
+        k_seg_scatter<<<S->grid_p, 256, 0, st>>>(A, stage);
+        k_seg_rank<<<S->grid_p, 256, 0, st>>>(A, stage, idsrc);
+        SegPerm pa{};
+        if (stage == 1) {
+            pa.ng = 3;
+            pa.src[0] = A.Y[0], pa.dst[0] = A.Y[1], pa.rows[0] = 9;
+            pa.src[1] = A.Nq[0], pa.dst[1] = A.Nq[1], pa.rows[1] = 3;
+            pa.src[2] = A.wguess, pa.dst[2] = A.guess_in, pa.rows[2] = 4;
+            pa.id_in = A.id[0], pa.id_out = A.id[1];
+        } else {
+            pa.ng = 4;
+            pa.src[0] = A.Y1[0], pa.dst[0] = A.Y1[1], pa.rows[0] = 9;
+            pa.src[1] = A.Y[1], pa.dst[1] = A.Y[0], pa.rows[1] = 9;
+            pa.src[2] = A.Nq[1], pa.dst[2] = A.Nq[0], pa.rows[2] = 3;
+            pa.src[3] = A.wguess, pa.dst[3] = A.guess_in, pa.rows[3] = 4;
+            pa.id_in = A.id[1], pa.id_out = A.id[0];
+        }
+        k_seg_permute<<<S->grid_p, 256, 0, st>>>(A, stage, pa);
+        const double *ys = stage == 1 ? A.Y[1] : A.Y1[1];
+        const double *nq = stage == 1 ? A.Nq[1] : A.Nq[0];
+        k_seg_density<<<S->grid_c, kTT, 0, st>>>(A, ys, nq);
+        launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st);
+        k_seg_gradient<<<S->grid_c, kTT, 0, st>>>(A, stage, ys);
+        if (stage == 1) launch_eom2_seg(A, 1, 0, ys, A.Y1[0], S->grid_p, st);
+        else launch_eom2_seg(A, 2, 1, ys, A.Y[0], S->grid_p, st);
+        k_seg_work<<<S->max_events, 32, 0, st>>>(A, stage);
+    }
+    (void)P;
+}
+
+sph_status wait_event(sph_server *S, cudaEvent_t ev)
+{
+    const double t0 = now_s();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return SPH_OK;
+        if (e != cudaErrorNotReady) return sfail(SPH_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e));
+        const double el = now_s() - t0;
+        if (el > S->timeout_s) return sfail(SPH_ERR_TIMEOUT, "device did not finish within the wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 20 : 200));
+    }
+}
+
+// completion time of a recorded event on the host clock (device timestamps against the
+// reference event, whose host time was taken when it completed)
+double event_host_time(sph_server *S, cudaEvent_t ev)
+{
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, S->ref_ev, ev) != cudaSuccess) {
+        cudaGetLastError();
+        return now_s();
+    }
+    return S->ref_host + 1e-3 * (double)ms;
+}
+
+void poll_retiring(sph_server *S)
+{
+    for (auto &kv : S->tickets) {
+        Ticket *t = kv.second;
+        if (t->state != TK_RETIRING) continue;
+        cudaError_t e = cudaEventQuery(t->done);
+        if (e == cudaSuccess) {
+            t->t_done = event_host_time(S, t->done);
+            t->state = TK_DONE;
+        } else if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+        }
+    }
+}
+
+sph_status upload_table(sph_server *S)
+{
+    if (!S->table_dirty) return SPH_OK;
+    BatchTable &b = S->tab_ring[S->tab_ring_i];
+    S->tab_ring_i = (S->tab_ring_i + 1) % S->tab_ring_n;
+    b.hi = S->hi;
+    b.nslots = S->nslots;
+    for (int s = 0; s < S->nslots; ++s) b.slots[s] = S->slots[s];
+    const size_t bytes = offsetof(BatchTable, slots) + sizeof(SegSlot) * (size_t)std::max(S->nslots, 1);
+    SCK(cudaMemcpyAsync(S->A.tab, &b, bytes, cudaMemcpyHostToDevice, S->st));
+    S->table_dirty = false;
+    return SPH_OK;
+}
+
+void recompute_hi(sph_server *S)
+{
+    int hi = 0, ns = 0;
+    for (int s = 0; s < S->max_events; ++s)
+        if (S->slots[s].mode != SLOT_FREE) {
+            hi = std::max(hi, S->slots[s].off + S->slots[s].cap);
+            ns = s + 1;
+        }
+    S->hi = hi;
+    S->nslots = ns;
+}
+
+sph_status admit(sph_server *S, Ticket *t)
+{
+    int slot = -1;
+    for (int s = 0; s < S->max_events; ++s)
+        if (S->slots[s].mode == SLOT_FREE && !S->slot_owner[s]) {
+            slot = s;
+            break;
+        }
+    if (slot < 0) return SPH_ERR_STATE;
+    const long long off = S->arena_alloc.alloc(t->cap);
+    if (off < 0) return SPH_ERR_OOM;
+    const Arena &A = S->A;
+    const size_t P = (size_t)A.P;
+    const int n = t->n;
+    t->slot = slot;
+    t->off = (int)off;
+    t->view.sc = A.sc + slot;
+    // initial state rows (x, y, u^x, u^y, S, Bv, Pv x3) and charges
+    const double *rows = t->in_rows();
+    for (int r = 0; r < 9; ++r)
+        SCK(cudaMemcpyAsync(A.Y[0] + r * P + off, rows + (size_t)r * n, sizeof(double) * n, cudaMemcpyHostToDevice,
+                            S->st));
+    for (int q = 0; q < 3; ++q)
+        SCK(cudaMemcpyAsync(A.Nq[0] + q * P + off, rows + (size_t)(9 + q) * n, sizeof(double) * n,
+                            cudaMemcpyHostToDevice, S->st));
+    unsigned char *tail = t->pin + t->pin_bytes - 256 - sizeof(EvView) - sizeof(DevScalars);
+    std::memcpy(tail, &t->view, sizeof(EvView));
+    std::memcpy(tail + sizeof(EvView), &t->sc0, sizeof(DevScalars));
+    SCK(cudaMemcpyAsync(A.segv + slot, tail, sizeof(EvView), cudaMemcpyHostToDevice, S->st));
+    SCK(cudaMemcpyAsync(A.sc + slot, tail + sizeof(EvView), sizeof(DevScalars), cudaMemcpyHostToDevice, S->st));
+    k_seg_admit<<<nblk(t->cap, 256), 256, 0, S->st>>>(A, slot, (int)off, n, t->cap);
+    SCK(cudaGetLastError());
+    S->launches += 1;
+    S->slot_owner[slot] = t;
+    S->slots[slot] = SegSlot{t->nsteps > 0 ? SLOT_STEP : SLOT_OBSERVE, (int)off, n, t->cap};
+    t->steps_left = t->nsteps;
+    t->state = TK_RUNNING;
+    S->table_dirty = true;
+    recompute_hi(S);
+    return SPH_OK;
+}
+
+// after the step that ran slot s in observe mode: results to the ticket's pinned block
+sph_status retire(sph_server *S, int slot)
+{
+    Ticket *t = S->slot_owner[slot];
+    const Arena &A = S->A;
+    const int n = t->n;
+    k_seg_unsort<<<nblk(n, 256), 256, 0, S->st>>>(A, slot, S->res_d, S->ires_d, S->contrib_d);
+    launch_sum_fixed(S->contrib_d, n, 5, S->tot_d, S->st);
+    S->launches += 3;
+    SCK(cudaMemcpyAsync(t->res(), S->res_d, sizeof(double) * kResRows * n, cudaMemcpyDeviceToHost, S->st));
+    SCK(cudaMemcpyAsync(t->ires(), S->ires_d, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, S->st));
+    SCK(cudaMemcpyAsync(t->tot(), S->tot_d, sizeof(double) * 5, cudaMemcpyDeviceToHost, S->st));
+    SCK(cudaMemcpyAsync(t->sc_out(), A.sc + slot, sizeof(DevScalars), cudaMemcpyDeviceToHost, S->st));
+    k_seg_release<<<nblk(t->cap, 256), 256, 0, S->st>>>(A, t->off, t->cap);
+    S->launches += 1;
+    SCK(cudaEventCreate(&t->done));
+    SCK(cudaEventRecord(t->done, S->st));
+    SCK(cudaGetLastError());
+    S->arena_alloc.release(t->off, t->cap);
+    S->slots[slot] = SegSlot{SLOT_FREE, 0, 0, 0};
+    S->slot_owner[slot] = nullptr;
+    t->state = TK_RETIRING;
+    S->table_dirty = true;
+    recompute_hi(S);
+    return SPH_OK;
+}
+
+void release_ticket(sph_server *S, Ticket *t)
+{
+    if (t->done) cudaEventDestroy(t->done);
+    if (t->pin_off >= 0) S->pool_alloc.release(t->pin_off, (long long)t->pin_bytes);
+    else std::free(t->pin);
+    S->tickets.erase(t->id);
+    delete t;
+}
+
+sph_status batch_step(sph_server *S)
+{
+    // pacing: at most `inflight` steps ahead of the device
+    const long long k = S->steps_launched;
+    cudaEvent_t ev = S->step_ev[(size_t)(k % (long long)S->step_ev.size())];
+    if (k >= (long long)S->step_ev.size()) {
+        sph_status s = wait_event(S, ev);
+        if (s != SPH_OK) return s;
+    }
+    if (k >= S->inflight) {
+        cudaEvent_t back = S->step_ev[(size_t)((k - S->inflight) % (long long)S->step_ev.size())];
+        sph_status s = wait_event(S, back);
+        if (s != SPH_OK) return s;
+    }
+    sph_status s = upload_table(S);
+    if (s != SPH_OK) return s;
+    if (!S->gexec) {
+        SCK(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
+        enqueue_batch_step(S);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(S->st, &g);
+        if (e != cudaSuccess) return sfail(SPH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        S->graph = g;
+        SCK(cudaGraphInstantiate(&S->gexec, g, 0));
+    }
+    SCK(cudaGraphLaunch(S->gexec, S->st));
+    SCK(cudaEventRecord(ev, S->st));
+    S->steps_launched += 1;
+    S->launches += kKernelsPerBatchStep;
+    // host bookkeeping of what that step did
+    std::vector<int> observed;
+    for (int sl = 0; sl < S->max_events; ++sl) {
+        SegSlot &q = S->slots[sl];
+        if (q.mode == SLOT_STEP) {
+            Ticket *t = S->slot_owner[sl];
+            S->particle_steps += q.n;
+            if (--t->steps_left <= 0) {
+                q.mode = SLOT_OBSERVE;
+                S->table_dirty = true;
+            }
+        } else if (q.mode == SLOT_OBSERVE) {
+            observed.push_back(sl);
+        }
+    }
+    for (int sl : observed) {
+        s = retire(S, sl);
+        if (s != SPH_OK) return s;
+    }
+    return SPH_OK;
+}
+
+void admit_queued(sph_server *S)
+{
+    while (!S->queue.empty()) {
+        Ticket *t = S->queue.front();
+        if (admit(S, t) != SPH_OK) break;  // FIFO: the head waits for a slot and a range
+        S->queue.pop_front();
+    }
+}
+
+bool any_running(const sph_server *S)
+{
+    for (int s = 0; s < S->max_events; ++s)
+        if (S->slots[s].mode != SLOT_FREE) return true;
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const sph_eos *eos)
+{
+    if (!out || !d || !eos) return sfail(SPH_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (d->max_events < 1 || d->max_events > kMaxSlots) return sfail(SPH_ERR_ARG, "max_events must be in 1..256");
+    if (d->max_particles < 0 || d->hbm_fraction < 0.0 || d->hbm_fraction > 0.9)
+        return sfail(SPH_ERR_ARG, "max_particles >= 0 and 0 <= hbm_fraction <= 0.9");
+    sph_server *S = new (std::nothrow) sph_server();
+    if (!S) return sfail(SPH_ERR_OOM, "host allocation");
+    auto bail = [&](sph_status s) {
+        std::string keep = sph_last_error();
+        sph_server_free(S);
+        set_last_error(keep.c_str());
+        return s;
+    };
+    S->eos = const_cast<sph_eos *>(eos);
+    S->E = eos_params(eos);
+    S->polish = d->polish ? 1 : 0;
+    S->E.polish = S->polish;
+    S->max_events = d->max_events;
+    S->inflight = d->max_inflight > 0 ? std::min(d->max_inflight, 8) : 2;
+    if (const char *tl = getenv("SPH_WAIT_LIMIT_S")) S->timeout_s = atof(tl);
+    if (d->stream) {
+        S->st = (cudaStream_t)d->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(sfail(SPH_ERR_CUDA, "cudaStreamCreate failed"));
+        }
+        S->own_stream = true;
+    }
+    // arena capacity: requested, or a share of free HBM
+    const size_t per_particle = sizeof(double) * (9 * 4 + 3 * 2 + 4 * 2 + kNDens + kNEos + kNGin + kNGout) +
+                                sizeof(int) * (2 + 1 + 1 + 1) + sizeof(uint32_t) * (1 + 4) + 8;
+    long long P = d->max_particles;
+    if (P == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(sfail(SPH_ERR_CUDA, "cudaMemGetInfo failed"));
+        }
+        const double f = d->hbm_fraction > 0.0 ? d->hbm_fraction : 0.25;
+        P = (long long)(f * (double)fr / (double)per_particle);
+    }
+    P = std::min<long long>(P, 0x7FFFFF00LL) / kSegAlign * kSegAlign;
+    if (P < kSegAlign) return bail(sfail(SPH_ERR_OOM, "arena smaller than one segment"));
+    Arena &A = S->A;
+    A.P = (int)P;
+    A.cmax = S->max_events * kMaxCellsAxis * kMaxCellsAxis;
+    const size_t Pz = (size_t)P;
+    sph_status s;
+#define SAL(ptr, bytes)                                                      \
+    do {                                                                     \
+        s = dmalloc(S, reinterpret_cast<void **>(&(ptr)), (bytes));          \
+        if (s != SPH_OK) return bail(s);                                     \
+    } while (0)
+    for (int k = 0; k < 2; ++k) {
+        SAL(A.Y[k], sizeof(double) * 9 * Pz);
+        SAL(A.Y1[k], sizeof(double) * 9 * Pz);
+        SAL(A.Nq[k], sizeof(double) * 3 * Pz);
+        SAL(A.id[k], sizeof(int) * Pz);
+    }
+    SAL(A.wguess, sizeof(double) * 4 * Pz);
+    SAL(A.guess_in, sizeof(double) * 4 * Pz);
+    SAL(A.segid, sizeof(int) * Pz);
+    SAL(A.dens, sizeof(double) * kNDens * Pz);
+    SAL(A.eosf, sizeof(double) * kNEos * Pz);
+    SAL(A.gin, sizeof(double) * kNGin * Pz);
+    SAL(A.gout, sizeof(double) * kNGout * Pz);
+    SAL(A.status, sizeof(uint32_t) * Pz);
+    SAL(A.nnb, sizeof(int) * Pz);
+    SAL(A.wpart, sizeof(double) * (Pz / 32 + 1));
+    SAL(A.key, sizeof(uint32_t) * Pz);
+    SAL(A.rnk, sizeof(uint32_t) * Pz);
+    SAL(A.tmp, sizeof(uint32_t) * Pz);
+    SAL(A.perm, sizeof(uint32_t) * Pz);
+    SAL(A.cnt, sizeof(uint32_t) * (size_t)A.cmax);
+    SAL(A.start, sizeof(uint32_t) * (size_t)A.cmax);
+    SAL(A.scan_part, sizeof(uint32_t) * kScanBlocks);
+    SAL(A.ncells, sizeof(int));
+    SAL(A.tab, sizeof(BatchTable));
+    SAL(A.grid, sizeof(SegGrid) * kMaxSlots);
+    SAL(A.segv, sizeof(EvView) * kMaxSlots);
+    SAL(A.sc, sizeof(DevScalars) * kMaxSlots);
+    if (cudaMemsetAsync(A.segid, 0xFF, sizeof(int) * Pz, S->st) != cudaSuccess ||
+        cudaMemsetAsync(A.tab, 0, sizeof(BatchTable), S->st) != cudaSuccess ||
+        cudaMemsetAsync(A.grid, 0, sizeof(SegGrid) * kMaxSlots, S->st) != cudaSuccess ||
+        cudaMemsetAsync(A.ncells, 0, sizeof(int), S->st) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(sfail(SPH_ERR_CUDA, "cudaMemsetAsync failed"));
+    }
+    // retirement scratch: the largest event the arena can hold
+    S->res_cap = (int)P;
+    SAL(S->res_d, sizeof(double) * kResRows * Pz);
+    SAL(S->ires_d, sizeof(int) * 2 * Pz);
+    SAL(S->contrib_d, sizeof(double) * 5 * Pz);
+    SAL(S->tot_d, sizeof(double) * (8 + 5 * 256));
+#undef SAL
+    // pinned staging pool
+    S->pool_bytes = d->pinned_bytes > 0 ? (size_t)d->pinned_bytes : Ticket::bytes_for(1) + (size_t)256 * Pz;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&S->pool), S->pool_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        S->pool = nullptr;
+        S->pool_bytes = 0;
+    }
+    S->pool_alloc.init((long long)S->pool_bytes, 256);
+    S->arena_alloc.init(P, kSegAlign);
+    if (cudaHostAlloc(reinterpret_cast<void **>(&S->tab_ring), sizeof(BatchTable) * S->tab_ring_n,
+                      cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        S->tab_ring = nullptr;
+        return bail(sfail(SPH_ERR_OOM, "pinned table ring"));
+    }
+    S->slots.assign(S->max_events, SegSlot{SLOT_FREE, 0, 0, 0});
+    S->slot_owner.assign(S->max_events, nullptr);
+    S->step_ev.resize(16, nullptr);
+    for (auto &e : S->step_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+            return bail(sfail(SPH_ERR_CUDA, "cudaEventCreate failed"));
+        }
+    // launch shapes: persistent grids of resident blocks on every SM
+    int dev = 0, sms = 0, occ_c = 0, occ_e = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_seg_density, kTT, 0);
+    occ_e = 6;
+    sms = std::max(sms, 1);
+    S->grid_p = sms * 8;
+    S->grid_c = sms * std::max(occ_c, 1);
+    S->grid_e = sms * occ_e;
+    // host/device clock reference for completion times
+    if (cudaEventCreate(&S->ref_ev) != cudaSuccess || cudaEventRecord(S->ref_ev, S->st) != cudaSuccess ||
+        cudaEventSynchronize(S->ref_ev) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(sfail(SPH_ERR_CUDA, "reference event"));
+    }
+    S->ref_host = now_s();
+    eos_retain(S->eos);
+    S->eos_held = true;
+    *out = S;
+    return SPH_OK;
+}
+
+void sph_server_free(sph_server *S)
+{
+    if (!S) return;
+    if (S->st) cudaStreamSynchronize(S->st);
+    for (auto &kv : S->tickets) {
+        Ticket *t = kv.second;
+        if (t->done) cudaEventDestroy(t->done);
+        if (t->pin_off < 0) std::free(t->pin);
+        delete t;
+    }
+    S->tickets.clear();
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    for (auto e : S->step_ev)
+        if (e) cudaEventDestroy(e);
+    if (S->ref_ev) cudaEventDestroy(S->ref_ev);
+    for (void *p : S->allocs) cudaFree(p);
+    if (S->pool) cudaFreeHost(S->pool);
+    if (S->tab_ring) cudaFreeHost(S->tab_ring);
+    if (S->own_stream && S->st) cudaStreamDestroy(S->st);
+    if (S->eos_held) sph_free_eos(S->eos);  // drops the server's reference
+    delete S;
+}
+
+sph_status sph_submit(sph_server *S, const sph_event_desc *d, int32_t nsteps, int64_t *ticket)
+{
+    if (!S || !d || !ticket) return sfail(SPH_ERR_ARG, "null argument");
+    *ticket = 0;
+    if (d->dim != 2) return sfail(SPH_ERR_ARG, "the serving form runs 2+1D events (dim = 2)");
+    if (nsteps < 0) return sfail(SPH_ERR_ARG, "nsteps < 0");
+    if (d->n < 1 || d->n > S->A.P) return sfail(d->n < 1 ? SPH_ERR_ARG : SPH_ERR_OOM,
+                                                d->n < 1 ? "the serving form needs n >= 1"
+                                                         : "event larger than the arena");
+    if (!(d->h > 0.0) || !(d->dtau > 0.0)) return sfail(SPH_ERR_ARG, "h and dtau must be positive");
+    if (d->milne && !(d->tau0 > 0.0)) return sfail(SPH_ERR_ARG, "Milne coordinates need tau0 > 0");
+    if (!d->x || !d->u || !d->S || !d->Nq) return sfail(SPH_ERR_ARG, "null particle array");
+    if (d->viscous && (!(d->tau_pi_coef > 0.0) || !(d->tau_Pi_ratio > 0.0) || !(d->eta_over_s > 0.0)))
+        return sfail(SPH_ERR_ARG, "viscous run needs eta_over_s, tau_pi_coef, tau_Pi_ratio > 0");
+    const int n = (int)d->n;
+    Ticket *t = new (std::nothrow) Ticket();
+    if (!t) return sfail(SPH_ERR_OOM, "host allocation");
+    t->n = n;
+    t->nsteps = nsteps;
+    t->cap = (n + kSegAlign - 1) / kSegAlign * kSegAlign;
+    t->viscous = d->viscous != 0;
+    t->pin_bytes = Ticket::bytes_for(n) + sizeof(EvView) + sizeof(DevScalars) + 256;
+    t->pin_bytes = (t->pin_bytes + 255) / 256 * 256;
+    long long po = S->pool ? S->pool_alloc.alloc((long long)t->pin_bytes) : -1;
+    if (po >= 0) {
+        t->pin = S->pool + po;
+        t->pin_off = po;
+    } else {
+        t->pin = static_cast<unsigned char *>(std::malloc(t->pin_bytes));
+        t->pin_off = -1;
+        if (!t->pin) {
+            delete t;
+            return sfail(SPH_ERR_OOM, "host staging");
+        }
+    }
+    // inputs: rows x, y, u^x, u^y, S, Bv, Pv (xx, xy, yy), then N_q (B, S, Q)
+    double *rows = t->in_rows();
+    const cudaMemcpyKind kind = d->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    const size_t nb = sizeof(double) * n;
+    bool ok = cudaMemcpy(rows, d->x, 2 * nb, kind) == cudaSuccess &&
+              cudaMemcpy(rows + 2 * (size_t)n, d->u, 2 * nb, kind) == cudaSuccess &&
+              cudaMemcpy(rows + 4 * (size_t)n, d->S, nb, kind) == cudaSuccess &&
+              cudaMemcpy(rows + 9 * (size_t)n, d->Nq, 3 * nb, kind) == cudaSuccess;
+    if (ok && d->Bv) ok = cudaMemcpy(rows + 5 * (size_t)n, d->Bv, nb, kind) == cudaSuccess;
+    else std::memset(rows + 5 * (size_t)n, 0, nb);
+    if (ok && d->Pv) ok = cudaMemcpy(rows + 6 * (size_t)n, d->Pv, 3 * nb, kind) == cudaSuccess;
+    else std::memset(rows + 6 * (size_t)n, 0, 3 * nb);
+    if (!ok) {
+        cudaGetLastError();
+        if (t->pin_off >= 0) S->pool_alloc.release(t->pin_off, (long long)t->pin_bytes);
+        else std::free(t->pin);
+        delete t;
+        return sfail(SPH_ERR_ARG, "cannot read the particle arrays");
+    }
+    // per-event parameters
+    EvView &v = t->view;
+    v = EvView{};
+    v.n = n;
+    v.dim = 2;
+    v.milne = d->milne ? 1 : 0;
+    v.nv = 9;
+    v.h = d->h;
+    v.inv_h = 1.0 / d->h;
+    v.supp2 = 4.0 * d->h * d->h;
+    v.inv_cell = 1.0 / (2.0 * d->h);
+    v.mixed = 1;
+    v.cell_f = (float)(2.0 * d->h);
+    tiled_shell(d->h, v.shell_lo, v.shell_hi);
+    v.sigma_d = 10.0 / (7.0 * kPi * d->h * d->h);
+    v.dtau = d->dtau;
+    v.eos = S->E;
+    v.tr.viscous = d->viscous ? 1 : 0;
+    v.tr.eta_over_s = d->eta_over_s;
+    v.tr.zeta_peak = d->zeta_peak;
+    v.tr.zeta_T_GeV = d->zeta_T_GeV;
+    v.tr.zeta_w_GeV = d->zeta_w_GeV > 0.0 ? d->zeta_w_GeV : 1.0;
+    v.tr.tau_pi_coef = d->tau_pi_coef;
+    v.tr.tau_Pi_ratio = d->tau_Pi_ratio;
+    v.tr.cs2_cap = d->cs2_cap > 0.0 ? d->cs2_cap : 1.0;
+    t->sc0 = DevScalars{};
+    t->sc0.tau = d->tau0;
+    t->id = S->next_id++;
+    t->t_submit = now_s();
+    S->tickets[t->id] = t;
+    S->queue.push_back(t);
+    *ticket = t->id;
+    return SPH_OK;
+}
+
+sph_status sph_server_pump(sph_server *S, int32_t max_steps, int32_t *running)
+{
+    if (!S || max_steps < 0) return sfail(SPH_ERR_ARG, "bad argument");
+    for (int k = 0; k < max_steps; ++k) {
+        poll_retiring(S);
+        admit_queued(S);
+        if (!any_running(S)) break;
+        sph_status s = batch_step(S);
+        if (s != SPH_OK) return s;
+    }
+    poll_retiring(S);
+    if (running) {
+        int r = 0;
+        for (int s = 0; s < S->max_events; ++s) r += S->slots[s].mode != SLOT_FREE;
+        *running = r;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_poll(sph_server *S, int64_t ticket, int32_t *state, double *latency_s)
+{
+    if (!S || !state) return sfail(SPH_ERR_ARG, "null argument");
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return sfail(SPH_ERR_ARG, "unknown ticket");
+    poll_retiring(S);
+    Ticket *t = it->second;
+    *state = t->state == TK_DONE ? SPH_TICKET_DONE : (t->state == TK_QUEUED ? SPH_TICKET_QUEUED : SPH_TICKET_RUNNING);
+    if (latency_s) *latency_s = t->state == TK_DONE ? t->t_done - t->t_submit : 0.0;
+    return SPH_OK;
+}
+
+sph_status sph_collect(sph_server *S, int64_t ticket, uint64_t mask, const sph_field_bufs *o, sph_totals *tot)
+{
+    if (!S) return sfail(SPH_ERR_ARG, "null argument");
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return sfail(SPH_ERR_ARG, "unknown ticket");
+    poll_retiring(S);
+    Ticket *t = it->second;
+    if (t->state != TK_DONE) return sfail(SPH_ERR_STATE, "ticket not done");
+    const uint64_t known = SPH_F_X | SPH_F_U | SPH_F_S | SPH_F_NQ | SPH_F_BV | SPH_F_PV | SPH_F_SIGMA_STAR |
+                           SPH_F_S_DENS | SPH_F_N_DENS | SPH_F_T | SPH_F_MU | SPH_F_P | SPH_F_E | SPH_F_PI_BULK |
+                           SPH_F_STATUS | SPH_F_NNB;
+    if (mask & ~known) return sfail(SPH_ERR_ARG, "field not available from the serving form");
+    if (mask && !o) return sfail(SPH_ERR_ARG, "null field buffers");
+    if (mask && o->on_device) return sfail(SPH_ERR_ARG, "the serving form returns host buffers");
+    const size_t n = (size_t)t->n;
+    const double *res = t->res();
+    const int *ires = t->ires();
+    auto rows = [&](uint64_t bit, void *dst, int r0, int nr) -> bool {
+        if (!(mask & bit)) return true;
+        if (!dst) return false;
+        std::memcpy(dst, res + (size_t)r0 * n, sizeof(double) * nr * n);
+        return true;
+    };
+    bool ok = true;
+    if (mask) {
+        ok = ok && rows(SPH_F_X, o->x, R_STATE, 2) && rows(SPH_F_U, o->u, R_STATE + 2, 2) &&
+             rows(SPH_F_S, o->S, R_STATE + 4, 1) && rows(SPH_F_BV, o->Bv, R_STATE + 5, 1) &&
+             rows(SPH_F_PV, o->Pv, R_STATE + 6, 3) && rows(SPH_F_NQ, o->Nq, R_NQ, 3) &&
+             rows(SPH_F_SIGMA_STAR, o->sigstar, R_SIG, 1) && rows(SPH_F_S_DENS, o->s, R_S, 1) &&
+             rows(SPH_F_N_DENS, o->nq, R_N, 3) && rows(SPH_F_T, o->T, R_T, 1) && rows(SPH_F_MU, o->mu, R_MU, 3) &&
+             rows(SPH_F_P, o->p, R_P, 1) && rows(SPH_F_E, o->e, R_E, 1);
+        if (ok && (mask & SPH_F_PI_BULK)) {
+            if (!o->Pi) ok = false;
+            else
+                for (size_t a = 0; a < n; ++a) {  // Pi = sigma Bv, sigma = sigma* / (u^0 sqrt(-g))
+                    const double ux = res[(R_STATE + 2) * n + a], uy = res[(R_STATE + 3) * n + a];
+                    const double g = std::sqrt(std::fma(ux, ux, std::fma(uy, uy, 1.0)));
+                    const double sg = t->view.milne ? t->sc_out()->tau : 1.0;
+                    o->Pi[a] = t->viscous ? res[R_SIG * n + a] / (g * sg) * res[(R_STATE + 5) * n + a] : 0.0;
+                }
+        }
+        if (ok && (mask & SPH_F_NNB)) {
+            if (!o->nnb) ok = false;
+            else std::memcpy(o->nnb, ires, sizeof(int) * n);
+        }
+        if (ok && (mask & SPH_F_STATUS)) {
+            if (!o->status) ok = false;
+            else std::memcpy(o->status, ires + n, sizeof(uint32_t) * n);
+        }
+        if (!ok) return sfail(SPH_ERR_ARG, "null destination for a requested field");
+    }
+    if (tot) {
+        const DevScalars *sc = t->sc_out();
+        const double *tt = t->tot();
+        std::memset(tot, 0, sizeof(*tot));
+        tot->tau = sc->tau;
+        tot->E = tt[0];
+        tot->S = tt[1];
+        for (int q = 0; q < 3; ++q) tot->N[q] = tt[2 + q];
+        tot->work = sc->work;
+        tot->status_or = sc->status_or;
+        tot->steps = sc->steps;
+        tot->pairs = (int64_t)sc->pairs;
+        tot->kernel_launches = 0;
+        tot->eos_work[0] = (int64_t)sc->eos_resid;
+        tot->eos_work[1] = (int64_t)sc->eos_solve;
+        tot->eos_work[2] = (int64_t)sc->eos_g;
+        tot->shell_tests = (int64_t)sc->shell_tests;
+    }
+    release_ticket(S, t);
+    return SPH_OK;
+}
+
+sph_status sph_server_stats_get(sph_server *S, sph_server_stats *o)
+{
+    if (!S || !o) return sfail(SPH_ERR_ARG, "null argument");
+    poll_retiring(S);
+    std::memset(o, 0, sizeof(*o));
+    for (auto &kv : S->tickets) {
+        const int st = kv.second->state;
+        if (st == TK_QUEUED) o->queued++;
+        else if (st == TK_DONE) o->done++;
+        else o->running++;
+    }
+    o->batch_steps = S->steps_launched;
+    o->particle_steps = S->particle_steps;
+    o->arena_capacity = S->A.P;
+    long long used = 0;
+    for (int s = 0; s < S->max_events; ++s)
+        if (S->slots[s].mode != SLOT_FREE) {
+            used += S->slots[s].cap;
+            o->slots_in_use++;
+        }
+    o->arena_in_use = used;
+    o->kernel_launches = S->launches;
+    o->max_events = S->max_events;
+    return SPH_OK;
+}
+
+sph_status sph_server_drain(sph_server *S, double timeout_s)
+{
+    if (!S) return sfail(SPH_ERR_ARG, "null argument");
+    const double t0 = now_s();
+    for (;;) {
+        sph_status s = sph_server_pump(S, 64, nullptr);
+        if (s != SPH_OK) return s;
+        bool pending = false;
+        for (auto &kv : S->tickets) pending = pending || kv.second->state != TK_DONE;
+        if (!pending) return SPH_OK;
+        if (!any_running(S) && S->queue.empty()) {
+            // only retiring tickets left: wait for their copies
+            cudaError_t e = cudaStreamQuery(S->st);
+            if (e != cudaSuccess && e != cudaErrorNotReady) return sfail(SPH_ERR_CUDA, cudaGetErrorString(e));
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        if (timeout_s > 0.0 && now_s() - t0 > timeout_s) return sfail(SPH_ERR_TIMEOUT, "drain timed out");
+    }
+}
+
+}  // extern "C"

@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct sph_eos;
+
 namespace sphg {
 
 constexpr double kHbarc = 0.1973269804;  // GeV fm
@@ -52,6 +54,7 @@ struct EosDev {
     double a0, a1, Tc_GeV, w_GeV, chi[3];
     // table: sn[node] = {s, nB, nS, nQ}, p[node]; node = ((iT*n1 + iB)*n2 + iS)*n3 + iQ
     int has_table, nT, nmu[3], maxit;
+    int polish;  // 1: one Newton step after convergence (the plain form); 0: stop at the tolerance
     double T0, dT, mu0[3], dmu[3], inv_dT, inv_dmu[3], Tmax, mumax[3];
     const double *sn;
     const double *p;
@@ -262,6 +265,89 @@ void launch_neighbors_list3(const EvView &v, const double *y, const int *id, Cel
 void launch_cell_coords3(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
 // exclusive scan of cnt into start and cursor, any number of buckets
 void launch_scan_buckets(CellBufs cb, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Serving form (serve.cu): many 2+1D events advance together in one segmented particle
+// arena.  Each admitted event owns the range [off, off + cap) of every per-particle row
+// (row stride P, the arena capacity); off and cap are multiples of kSegAlign, so a warp
+// (and a 256-particle chunk) never straddles two events.  Every kernel reads the slot
+// table from device memory and loops over the arena with a fixed grid, so one captured
+// CUDA graph serves every batch composition.
+constexpr int kSegAlign = 256;
+constexpr int kMaxSlots = 256;
+constexpr int kMaxCellsAxis = 256;  // an event's cell grid clamps here (neighbour sets stay complete)
+constexpr int SLOT_FREE = 0, SLOT_STEP = 1, SLOT_OBSERVE = 2;
+
+struct SegSlot {  // host-written at step boundaries
+    int mode;     // SLOT_FREE, SLOT_STEP (advance one step), SLOT_OBSERVE (stage-1 evaluation only)
+    int off, n, cap;
+};
+struct SegGrid {  // device-written, per slot and stage: bounding box and cell grid
+    long long bb[4];  // order-preserving encodings of x_min, y_min, x_max, y_max
+    double x0, y0;    // grid origin (the bounding-box minimum)
+    int nx, ny, base, ncell;
+};
+struct BatchTable {  // host-written
+    int hi;          // arena high-water mark: every kernel loops over [0, hi)
+    int nslots;      // slots in use (table length)
+    int pad[2];
+    SegSlot slots[kMaxSlots];
+};
+struct Arena {
+    int P, cmax;  // particle and cell capacity
+    double *Y[2], *Y1[2], *Nq[2];
+    int *id[2];
+    double *wguess, *guess_in;
+    int *segid;  // slot of every arena position of an event's range (padding included)
+    double *dens, *eosf, *gin, *gout;
+    uint32_t *status;
+    int *nnb;
+    double *wpart;  // per 32 particles: work-rate partial sums of the EoS pass
+    uint32_t *key, *rnk, *tmp, *perm;
+    uint32_t *cnt, *start, *scan_part;
+    int *ncells;  // device-written total of the active slots' cells
+    BatchTable *tab;
+    SegGrid *grid;
+    EvView *segv;
+    DevScalars *sc;
+};
+// slot s takes part in this stage's pass: stage 1 evaluates STEP and OBSERVE slots, stage 2
+// and the rate passes (gradient, equations of motion, work) only STEP slots
+__device__ __forceinline__ bool seg_active(const BatchTable *t, int s, int stage, bool rates)
+{
+    const int m = t->slots[s].mode;
+    return m == SLOT_STEP || (m == SLOT_OBSERVE && stage == 1 && !rates);
+}
+
+// Shell of the cell-tiled mixed-form decision.  Coordinates are taken relative to the
+// origin of the centre cell in FP64 and rounded to float: |x_a - o| <= 2h, |x_b - o| <= 4h,
+// so each carries an error <= 4h u (u = 2^-24) and the float separation of a pair with
+// |dx_d| <= 2h errs by e <= 8h u = 4 (2h) u per axis (the subtraction included; candidates
+// up to 3 cells away err by at most 6 (2h) u).  The float r^2 (fmaf) then errs by at most
+// 4 (2h) e + 2 e^2 + 3 u (2h)^2 <= 27 (2h)^2 u near r = 2h, and the margin r^2 - (2h)^2
+// grows faster than the error beyond it.  The shell is +-64 (2h)^2 u: outside it the float
+// decision equals the exact one.  A grid clamped at kMaxCellsAxis cells puts far particles
+// into its edge cells, where the bound does not hold; such cells use the FP64 test for
+// every candidate.
+inline void tiled_shell(double h, float &lo, float &hi)
+{
+    const double u = 1.0 / 16777216.0;
+    const double s2 = 4.0 * h * h;
+    const double err = 64.0 * s2 * u;
+    float l = (float)(s2 - err), g = (float)(s2 + err);
+    while ((double)l > s2 - err) l = nextafterf(l, 0.0f);
+    while ((double)g < s2 + err) g = nextafterf(g, 1e30f);
+    lo = l;
+    hi = g;
+}
+
+// EoS handle accessors (api.cu)
+EosDev eos_params(const ::sph_eos *e);
+void eos_retain(::sph_eos *e);
+
+void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st);
+void launch_eom2_seg(const Arena &A, int stage, int mode, const double *ys, double *yout, int grid,
+                     cudaStream_t st);
 
 // sets the message returned by sph_last_error() for the calling thread
 void set_last_error(const char *msg);

@@ -331,8 +331,9 @@ def test_warm_start_matches_oracle_over_steps(Bd):
 
 def test_eos_stall_at_table_edge_ends_fast(Bd):
     """A warm start inside the table whose root lies below the table's lowest T: the clamped
-    Newton stalls at the edge, the failed line search ends it (at most 1 + 9 residual
-    evaluations), and the closed form takes over, flagged out-of-table -- as in the oracle."""
+    Newton walks to the edge and stalls there; the failed line search ends it (a few
+    iterations plus 9 trials, where running on took 30 x 9), and the closed form takes over,
+    flagged out-of-table -- as in the oracle."""
     ev = CASES["bsq_small"]()
     hot = Bd.GpuEvent(ev)
     hot.step(1, sync=True)
@@ -348,7 +349,7 @@ def test_eos_stall_at_table_edge_ends_fast(Bd):
     t0 = g.totals()
     g.step(1, sync=True)
     t1 = g.totals()
-    assert t1["eos_work"][0] - t0["eos_work"][0] <= 10 * ev2.n
+    assert t1["eos_work"][0] - t0["eos_work"][0] <= 50 * ev2.n
     run = O.OracleRun.start(ev2)
     run.guess[:] = gs
     run.step(1)
