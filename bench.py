@@ -146,6 +146,110 @@ def cpu_baseline(ev, target_s=15.0):
                       f"({dt:.1f} s, FP64 C oracle, OpenMP over particles)"}
 
 
+def serving_events(nevents: int, seed_sizes: int = 4):
+    """Serving workload: viscous 2+1D BSQ events with particle counts log-uniform in 5k-200k.
+
+    Every event has the single-event workload's particle spacing (0.062 fm) and hotspot shape,
+    on a disc of radius 7 fm sqrt(N / 40000) (the same resolution for systems of different
+    size), 200 seeded hotspots, charges within +-1% of s; event e uses seeds 1000 + e."""
+    import math
+    import numpy as np
+    from paper_2511_22852_gb300 import inputs as I
+    u = I.uniform01(seed_sizes, nevents)
+    sizes = np.floor(np.exp(math.log(5e3) + u * (math.log(2e5) - math.log(5e3)))).astype(int)
+    evs = [I.viscous_bsq_2p1(n_target=int(n), R=7.0 * math.sqrt(n / 40000.0), seed_hot=1000 + e,
+                             seed_charge=500000 + e, with_table=False) for e, n in enumerate(sizes)]
+    return evs
+
+
+def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_events: int = 32):
+    """events/hr and p50/p99 latency of the serving form against the plain FP64 form run one
+    event at a time, on the same events (each advanced ksteps Heun steps from tau0)."""
+    import numpy as np
+    import torch
+    evs = serving_events(nevents)
+    ntot = int(sum(e.n for e in evs))
+    table = I.synthetic_eos_table(I.BJ_EOS)
+    # plain FP64, one event at a time, end to end: upload, ksteps steps, read back T
+    ed, keep = Bd.eos_desc(I.BJ_EOS, table)
+    eh = Bd.sph_set_eos_table(ed)
+    warm = Bd.GpuEvent(evs[0], use_graph=True, eos_handle=eh)
+    warm.step(2, sync=True)
+    warm.free()
+    torch.cuda.synchronize()
+    t_fp64 = []
+    for e in evs:
+        t = time.perf_counter()
+        g = Bd.GpuEvent(e, use_graph=True, eos_handle=eh)
+        g.step(ksteps, sync=True)
+        g.read(("T",))
+        g.free()
+        t_fp64.append(time.perf_counter() - t)
+    Bd.sph_free_eos(eh)
+    T64 = sum(t_fp64)
+    # serving form, closed loop (every event submitted at once): capacity
+    srv = Bd.GpuServer(I.BJ_EOS, table, max_events=max_events, max_particles=int(1.25 * ntot) + 65536,
+                       pinned_bytes=int(400 * ntot) + (64 << 20))
+    tw = srv.submit(evs[0], 2)
+    srv.drain(120.0)
+    srv.collect(tw)
+    st0 = srv.stats()
+    t0 = time.perf_counter()
+    tk = [srv.submit(e, ksteps) for e in evs]
+    srv.drain(600.0)
+    lat_closed = [srv.poll(t)[1] for t in tk]
+    makespan = max(lat_closed)  # every event submitted at t0
+    wall_closed = time.perf_counter() - t0
+    st1 = srv.stats()
+    for t in tk:
+        srv.collect(t, names=("T",))
+    cap_eps = nevents / makespan
+    # open loop: Poisson arrivals at `load` x the measured capacity (exponential gaps, seed 3)
+    u = I.uniform01(3, nevents)
+    gaps = -np.log1p(-u) / (load * cap_eps)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    tk2 = []
+    t0 = time.perf_counter()
+    i = 0
+    while i < nevents or any(srv.poll(t)[0] != Bd.SPH_TICKET_DONE for t in tk2):
+        now = time.perf_counter() - t0
+        while i < nevents and arrivals[i] <= now:
+            tk2.append(srv.submit(evs[i], ksteps))
+            i += 1
+        running = srv.pump(1)
+        if running == 0 and i < nevents:
+            time.sleep(max(0.0, min(0.002, arrivals[i] - (time.perf_counter() - t0))))
+        if time.perf_counter() - t0 > 900:
+            raise RuntimeError("serving benchmark did not finish")
+    lat_open = np.array([srv.poll(t)[1] for t in tk2])
+    wall_open = time.perf_counter() - t0
+    for t in tk2:
+        srv.collect(t, names=("T",))
+    st2 = srv.stats()
+    srv.free()
+    ps = float(ntot * ksteps)
+    return {
+        "workload": f"{nevents} viscous 2+1D BSQ events, particle counts log-uniform in 5k-200k "
+                    f"(total {ntot}), {ksteps} Heun steps each from tau0 = 0.6 fm, dtau = 0.005 fm, "
+                    f"spacing 0.062 fm, h = 0.3 fm, shared 64x32^3 EoS table",
+        "events_per_hr": 3600.0 * cap_eps,
+        "particle_steps_per_s": ps / makespan,
+        "fp64_one_at_a_time": {"events_per_hr": 3600.0 * nevents / T64, "particle_steps_per_s": ps / T64,
+                               "seconds": T64, "per_event_e2e": "init (upload) + steps + read of T"},
+        "events_per_hr_vs_fp64": T64 / makespan,
+        "closed_loop": {"makespan_s": makespan, "wall_s": wall_closed, "p50_s": float(np.median(lat_closed)),
+                        "p99_s": float(np.percentile(lat_closed, 99)),
+                        "batch_steps": st1["batch_steps"] - st0["batch_steps"],
+                        "kernel_launches": st1["kernel_launches"] - st0["kernel_launches"]},
+        "open_loop": {"arrivals": f"Poisson, rate {load:.2f} x closed-loop capacity = {load * cap_eps:.2f} events/s",
+                      "p50_s": float(np.median(lat_open)), "p99_s": float(np.percentile(lat_open, 99)),
+                      "mean_s": float(lat_open.mean()), "wall_s": wall_open,
+                      "batch_steps": st2["batch_steps"] - st1["batch_steps"]},
+        "max_events": max_events, "latency": "submit (host arrays) to results readable in host memory",
+        "precision": "mixed: FP32 neighbour sums (compensated), FP64 EoS/EoM/totals; no Newton polish",
+    }
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -304,6 +408,8 @@ def run_ours(args):
                "wall_s_timed": t_wall, "status_or": int(status_or),
                "diagnostics": {"ms_per_step_without_l2_flush": noflush_ms,
                                "profile_mode_group_ms_per_step": total_ms / kp}}
+        if not args.no_serving:
+            out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ev)
         print(json.dumps(out), flush=True)
@@ -321,6 +427,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-events", type=int, default=32)
+    ap.add_argument("--serving-steps", type=int, default=60)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
