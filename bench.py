@@ -430,9 +430,18 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-events", type=int, default=32)
     ap.add_argument("--serving-steps", type=int, default=60)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving comparison (profiling helper; prints its own JSON line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.serving_only:
+        from paper_2511_22852_gb300 import binding as Bd
+        from paper_2511_22852_gb300 import build_lib
+        from paper_2511_22852_gb300 import inputs as I
+        build_lib.build()
+        print(json.dumps({"serving": serving_bench(Bd, I, args.serving_events, args.serving_steps)}), flush=True)
+        return 0
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -155,7 +155,6 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
     bool used = false;
     EosOut o = eos_invert(E, v.tr.cs2_cap, s, nq, gs, used, w);
-    w.resid += 1u;  // + the final evaluation of p, (s, n) and H at the solution
     guess_out[a] = used ? o.T : 0.0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) guess_out[(1 + q) * n + a] = used ? o.mu[q] : 0.0;
@@ -240,9 +239,15 @@ __global__ void __launch_bounds__(64, 6) k_eos2_seg(Arena A, EosDev E, int stage
         const SegSlot sl = T->slots[s];
         double wc = 0.0;
         EosWork w = {0u, 0u, 0u};
-        if (a - sl.off < sl.n)
+        if (a - sl.off < sl.n) {
             wc = eos2_particle(A.segv[s], E, stage, P, (size_t)a, y, A.dens, A.eosf, A.gin, A.status, A.guess_in,
                                A.wguess, w);
+            if (T->slots[s].mode == SLOT_STEP) {  // float copies of the gradient-pass inputs
+                const double *g = A.gin;
+                A.fX[a] = make_float4((float)g[a], (float)g[P + a], (float)g[2 * P + a], (float)g[3 * P + a]);
+                A.fU[a] = make_float2((float)g[4 * P + a], (float)g[5 * P + a]);
+            }
+        }
         for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xFFFFFFFFu, wc, o);
         const unsigned wres = __reduce_add_sync(0xFFFFFFFFu, w.resid);
         const unsigned wsol = __reduce_add_sync(0xFFFFFFFFu, w.solve);

@@ -169,9 +169,12 @@ __device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double 
 
 // 4x4 Gaussian elimination with partial pivoting, fully unrolled so every index is a
 // compile-time constant and the system stays in registers.  Row swaps are conditional
-// moves.  Returns false on a zero or non-finite pivot.
+// moves; each pivot is inverted once (FP64 division is a multi-instruction sequence on
+// the 1:64 FP64 pipe) and the back substitution multiplies by it.  Returns false on a
+// zero or non-finite pivot.
 __device__ __forceinline__ bool solve4(double A[4][4], double b[4])
 {
+    double ipv[4];  // reciprocal pivots, reused by the back substitution
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int piv = c;
@@ -200,6 +203,7 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4])
             }
         }
         double inv = 1.0 / A[c][c];
+        ipv[c] = inv;
 #pragma unroll
         for (int r = c + 1; r < 4; ++r) {
             double f = A[r][c] * inv;
@@ -213,7 +217,7 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4])
         double acc = b[r];
 #pragma unroll
         for (int k = r + 1; k < 4; ++k) acc = fma(-A[r][k], b[k], acc);
-        b[r] = acc / A[r][r];
+        b[r] = acc * ipv[r];
     }
     return true;
 }
@@ -243,23 +247,32 @@ __device__ double resid(const EosDev &E, const double *x, double s, const double
 // not needed after the step); each line-search trial overwrites r and J with their values
 // at the trial point, so the accepted point's residual and Jacobian are ready for the
 // next iteration (the same sequence as a copy-on-accept scheme, with fewer registers).
-__device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x, EosWork &w)
+// On convergence J holds d(s, n)/d(T, mu) / s at the returned x when *jx is set (the
+// caller then needs only p there); otherwise it is stale.
+__device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x, EosWork &w, double J[4][4],
+                           bool *jx)
 {
-    double r[4], J[4][4];
+    double r[4];
+    *jx = false;
     double rn = resid(E, x, s, n, r, J);
     ++w.resid;
     for (int it = 0; it < E.maxit; ++it) {
         double d[4] = {-r[0], -r[1], -r[2], -r[3]};
         if (rn <= E.tol) {
-            if (!E.polish) return true;
+            if (!E.polish) {
+                *jx = true;
+                return true;
+            }
             ++w.solve;
             if (solve4(J, d)) {  // one polishing step if it does not increase the residual
                 double xn[4] = {x[0] + d[0], x[1] + d[1], x[2] + d[2], x[3] + d[3]};
                 clamp4(E, xn);
                 ++w.resid;
-                if (resid(E, xn, s, n, r, J) <= rn)
+                if (resid(E, xn, s, n, r, J) <= rn) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) x[k] = xn[k];
+                    *jx = true;
+                }
             }
             return true;
         }
@@ -283,6 +296,29 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
         rn = rnn;
     }
     return rn <= E.tol;
+}
+
+// quadrilinear interpolant of p alone
+__device__ double tab_p(const EosDev &E, const double *x)
+{
+    int iT, iB, iS, iQ;
+    double tT, tB, tS, tQ;
+    locate(x[0], E.T0, E.inv_dT, E.nT, iT, tT);
+    locate(x[1], E.mu0[0], E.inv_dmu[0], E.nmu[0], iB, tB);
+    locate(x[2], E.mu0[1], E.inv_dmu[1], E.nmu[1], iS, tS);
+    locate(x[3], E.mu0[2], E.inv_dmu[2], E.nmu[2], iQ, tQ);
+    const int n3 = E.nmu[2], n23 = E.nmu[1] * E.nmu[2], n123 = E.nmu[0] * n23;
+    double pv = 0.0;
+    for (int bT = 0; bT < 2; ++bT)
+        for (int bB = 0; bB < 2; ++bB) {
+            double wT = bT ? tT : 1.0 - tT, wB = bB ? tB : 1.0 - tB;
+            size_t base = (size_t)(iT + bT) * n123 + (size_t)(iB + bB) * n23 + (size_t)iS * n3 + iQ;
+            double p00 = __ldg(E.p + base), p01 = __ldg(E.p + base + 1), p10 = __ldg(E.p + base + n3),
+                   p11 = __ldg(E.p + base + n3 + 1);
+            double a0 = p00 + tQ * (p01 - p00), a1 = p10 + tQ * (p11 - p10);
+            pv = fma(wT * wB, a0 + tS * (a1 - a0), pv);
+        }
+    return pv;
 }
 
 struct EosOut {
@@ -315,10 +351,11 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
         return o;
     }
     double x[4];
-    bool use_table = false;
+    double H[4][4];
+    bool use_table = false, hx = false;
     if (E.has_table && guess[0] > 0.0 && inside_table(E, guess)) {
         double xt[4] = {guess[0], guess[1], guess[2], guess[3]};
-        if (tab_newton(E, s, n, xt, w)) {
+        if (tab_newton(E, s, n, xt, w, H, &hx)) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) x[k] = xt[k];
             use_table = true;
@@ -330,7 +367,7 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
         if (E.has_table) {
             if (inside_table(E, x)) {
                 double xt[4] = {x[0], x[1], x[2], x[3]};
-                if (tab_newton(E, s, n, xt, w)) {
+                if (tab_newton(E, s, n, xt, w, H, &hx)) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) x[k] = xt[k];
                     use_table = true;
@@ -343,9 +380,19 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
         }
     }
     used_table = use_table;
-    double p, H[4][4], sn[4];
-    if (use_table) tab_eval(E, x, sn, H, &p);
-    else an_eval(E, x[0], x + 1, p, sn, H);
+    double p, sn[4];
+    if (use_table && hx) {  // the Newton's last Jacobian is the one at the solution
+        p = tab_p(E, x);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) H[i][j] *= s;
+    } else if (use_table) {
+        tab_eval(E, x, sn, H, &p);
+        ++w.resid;
+    } else {
+        an_eval(E, x[0], x + 1, p, sn, H);
+    }
     double e = x[0] * s + x[1] * n[0] + x[2] * n[1] + x[3] * n[2] - p;
     // (p_s, p_n) = H^-T (s, n) over the directions the EoS couples to; an uncoupled charge
     // direction (no table, chi_q = 0) becomes an identity row with zero right-hand side

@@ -302,8 +302,12 @@ struct SegPerm {
     int ng;
     const int *id_in;
     int *id_out;
+    const double *nq;  // the charges' source rows (group 0 holds the positions and S)
 };
 
+// Gathers the state into sorted order and writes the single-precision copies of the
+// neighbour passes: position relative to the origin of the particle's cell (the same FP64
+// expression as the centre-cell origin of the tiled passes) and (S, N_B, N_S, N_Q).
 __global__ void k_seg_permute(Arena A, int stage, SegPerm pa)
 {
     const BatchTable *T = A.tab;
@@ -316,6 +320,13 @@ __global__ void k_seg_permute(Arena A, int stage, SegPerm pa)
         for (int g = 0; g < pa.ng; ++g)
             for (int r = 0; r < pa.rows[g]; ++r) pa.dst[g][r * P + j] = pa.src[g][r * P + p];
         pa.id_out[j] = pa.id_in[p];
+        const SegGrid &g = A.grid[s];
+        const int lc = (int)A.key[p] - g.base;
+        const int cx = lc % g.nx, cy = lc / g.nx;
+        const double cs = 2.0 * A.segv[s].h;
+        const double *X = pa.src[0];
+        A.fpos[j] = make_float2((float)(X[p] - (g.x0 + (double)cx * cs)), (float)(X[P + p] - (g.y0 + (double)cy * cs)));
+        A.fq[j] = make_float4((float)X[4 * P + p], (float)pa.nq[p], (float)pa.nq[P + p], (float)pa.nq[2 * P + p]);
     }
 }
 
@@ -324,7 +335,8 @@ __global__ void k_seg_permute(Arena A, int stage, SegPerm pa)
 struct CellCtx {
     int s, first, na, M, clamped;
     int rs[3], rl[3];  // the three candidate runs (one per cell row): start, length
-    double ox, oy;     // origin of the centre cell
+    int rm0[3], rm1[3];  // positions where the centre column of each row starts and ends
+    float cs;            // cell side 2h in single precision
 };
 
 // last slot whose first cell is <= c (slots without cells share the next slot's base)
@@ -350,32 +362,48 @@ __device__ void cell_setup(const Arena &A, const int *s_base, int ns, int c, Cel
     cc.clamped = g.nx >= kMaxCellsAxis || g.ny >= kMaxCellsAxis;
     cc.first = off + (int)(A.start[c] - S0);
     cc.na = (int)A.cnt[c];
-    const double cs = 2.0 * A.segv[s].h;
-    cc.ox = g.x0 + (double)cx * cs;
-    cc.oy = g.y0 + (double)cy * cs;
+    cc.cs = (float)(2.0 * A.segv[s].h);
     int M = 0;
     for (int o = 0; o < 3; ++o) {
         const int r = cy - 1 + o;
-        int st = 0, ln = 0;
+        int st = 0, ln = 0, m0 = 0, m1 = 0;
         if (r >= 0 && r < g.ny) {
+            const int kc = g.base + r * g.nx + cx;
             const int k0 = g.base + r * g.nx + max(cx - 1, 0);
             const int k1 = g.base + r * g.nx + min(cx + 1, g.nx - 1);
             st = off + (int)(A.start[k0] - S0);
             ln = (int)(A.start[k1] + A.cnt[k1] - A.start[k0]);
+            m0 = off + (int)(A.start[kc] - S0);
+            m1 = m0 + (int)A.cnt[kc];
         }
         cc.rs[o] = st;
         cc.rl[o] = ln;
+        cc.rm0[o] = m0;
+        cc.rm1[o] = m1;
         M += ln;
     }
     cc.M = M;
 }
 
-__device__ __forceinline__ int cand_index(const CellCtx &cc, int q)
+// candidate q of the 3x3 block: its arena position and its position relative to the
+// centre cell's origin (own-cell-relative float position + the cell offset)
+__device__ __forceinline__ int cand_index(const CellCtx &cc, int q, const float2 *__restrict__ fpos, float2 &rel)
 {
-    if (q < cc.rl[0]) return cc.rs[0] + q;
-    q -= cc.rl[0];
-    if (q < cc.rl[1]) return cc.rs[1] + q;
-    return cc.rs[2] + q - cc.rl[1];
+    int o = 0;
+    if (q >= cc.rl[0]) {
+        q -= cc.rl[0];
+        o = 1;
+        if (q >= cc.rl[1]) {
+            q -= cc.rl[1];
+            o = 2;
+        }
+    }
+    const int b = cc.rs[o] + q;
+    const float ox = b < cc.rm0[o] ? -cc.cs : (b < cc.rm1[o] ? 0.0f : cc.cs);
+    const float oy = (float)(o - 1) * cc.cs;
+    const float2 f = fpos[b];
+    rel = make_float2(f.x + ox, f.y + oy);
+    return b;
 }
 
 __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__restrict__ y,
@@ -410,16 +438,18 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
                 const bool valid = my < na;
                 const int a = cc.first + (valid ? my : 0);
                 const double xa = y[a], ya = y[P + a];
-                const float fax = (float)(xa - cc.ox), fay = (float)(ya - cc.oy);
+                const float2 fa = A.fpos[a];
+                const float fax = fa.x, fay = fa.y;
                 CSum sg = {0.f, 0.f}, ss = {0.f, 0.f}, sb = {0.f, 0.f}, sS = {0.f, 0.f}, sq = {0.f, 0.f};
                 int nacc = 0;
                 for (int t0 = 0; t0 < cc.M; t0 += kTile) {
                     const int mt = min(kTile, cc.M - t0);
                     __syncthreads();
                     for (int i = tid; i < mt; i += kTT) {
-                        const int b = cand_index(cc, t0 + i);
-                        cpos[i] = make_float2((float)(y[b] - cc.ox), (float)(y[P + b] - cc.oy));
-                        cq[i] = make_float4((float)y[4 * P + b], (float)Nq[b], (float)Nq[P + b], (float)Nq[2 * P + b]);
+                        float2 rel;
+                        const int b = cand_index(cc, t0 + i, A.fpos, rel);
+                        cpos[i] = rel;
+                        cq[i] = A.fq[b];
                         cidx[i] = b;
                     }
                     __syncthreads();
@@ -514,18 +544,19 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
                 const bool valid = my < na;
                 const int a = cc.first + (valid ? my : 0);
                 const double xa = y[a], ya = y[P + a];
-                const float fax = (float)(xa - cc.ox), fay = (float)(ya - cc.oy);
+                const float2 fa = A.fpos[a];
+                const float fax = fa.x, fay = fa.y;
                 CSum Gx = {0.f, 0.f}, Gy = {0.f, 0.f}, Hx = {0.f, 0.f}, Hy = {0.f, 0.f};
                 CSum xx = {0.f, 0.f}, xy = {0.f, 0.f}, yx = {0.f, 0.f}, yy = {0.f, 0.f};
                 for (int t0 = 0; t0 < cc.M; t0 += kTile) {
                     const int mt = min(kTile, cc.M - t0);
                     __syncthreads();
                     for (int i = tid; i < mt; i += kTT) {
-                        const int b = cand_index(cc, t0 + i);
-                        cpos[i] = make_float2((float)(y[b] - cc.ox), (float)(y[P + b] - cc.oy));
-                        cX[i] = make_float4((float)gin[b], (float)gin[P + b], (float)gin[2 * P + b],
-                                            (float)gin[3 * P + b]);
-                        cU[i] = make_float2((float)gin[4 * P + b], (float)gin[5 * P + b]);
+                        float2 rel;
+                        const int b = cand_index(cc, t0 + i, A.fpos, rel);
+                        cpos[i] = rel;
+                        cX[i] = A.fX[b];
+                        cU[i] = A.fU[b];
                         cidx[i] = b;
                     }
                     __syncthreads();
@@ -848,6 +879,7 @@ void enqueue_batch_step(sph_server *S)
             pa.src[1] = A.Nq[0], pa.dst[1] = A.Nq[1], pa.rows[1] = 3;
             pa.src[2] = A.wguess, pa.dst[2] = A.guess_in, pa.rows[2] = 4;
             pa.id_in = A.id[0], pa.id_out = A.id[1];
+            pa.nq = A.Nq[0];
         } else {
             pa.ng = 4;
             pa.src[0] = A.Y1[0], pa.dst[0] = A.Y1[1], pa.rows[0] = 9;
@@ -855,6 +887,7 @@ void enqueue_batch_step(sph_server *S)
             pa.src[2] = A.Nq[1], pa.dst[2] = A.Nq[0], pa.rows[2] = 3;
             pa.src[3] = A.wguess, pa.dst[3] = A.guess_in, pa.rows[3] = 4;
             pa.id_in = A.id[1], pa.id_out = A.id[0];
+            pa.nq = A.Nq[1];
         }
         k_seg_permute<<<S->grid_p, 256, 0, st>>>(A, stage, pa);
         const double *ys = stage == 1 ? A.Y[1] : A.Y1[1];
@@ -1117,7 +1150,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     }
     // arena capacity: requested, or a share of free HBM
     const size_t per_particle = sizeof(double) * (9 * 4 + 3 * 2 + 4 * 2 + kNDens + kNEos + kNGin + kNGout) +
-                                sizeof(int) * (2 + 1 + 1 + 1) + sizeof(uint32_t) * (1 + 4) + 8;
+                                sizeof(int) * (2 + 1 + 1 + 1) + sizeof(uint32_t) * (1 + 4) + 8 + 48;
     long long P = d->max_particles;
     if (P == 0) {
         size_t fr = 0, tot = 0;
@@ -1160,6 +1193,10 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     SAL(A.rnk, sizeof(uint32_t) * Pz);
     SAL(A.tmp, sizeof(uint32_t) * Pz);
     SAL(A.perm, sizeof(uint32_t) * Pz);
+    SAL(A.fpos, sizeof(float2) * Pz);
+    SAL(A.fq, sizeof(float4) * Pz);
+    SAL(A.fX, sizeof(float4) * Pz);
+    SAL(A.fU, sizeof(float2) * Pz);
     SAL(A.cnt, sizeof(uint32_t) * (size_t)A.cmax);
     SAL(A.start, sizeof(uint32_t) * (size_t)A.cmax);
     SAL(A.scan_part, sizeof(uint32_t) * kScanBlocks);

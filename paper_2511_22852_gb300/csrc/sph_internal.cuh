@@ -305,6 +305,12 @@ struct Arena {
     double *wpart;  // per 32 particles: work-rate partial sums of the EoS pass
     uint32_t *key, *rnk, *tmp, *perm;
     uint32_t *cnt, *start, *scan_part;
+    // single-precision copies for the neighbour passes, written once per particle and stage:
+    // position relative to the origin of the particle's cell, (S, N_B, N_S, N_Q), and the
+    // gradient-pass inputs X^{xx}, X^{xy}, X^{yx}, X^{yy} and u^x/sigma*, u^y/sigma*
+    float2 *fpos;
+    float4 *fq, *fX;
+    float2 *fU;
     int *ncells;  // device-written total of the active slots' cells
     BatchTable *tab;
     SegGrid *grid;

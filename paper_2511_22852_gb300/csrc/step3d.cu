@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(64, 6) k_eos3(EvView v, int stage, const doubl
         bool used = false;
         EosWork w = {0u, 0u, 0u};
         EosOut o = eos_invert(v.eos, v.tr.cs2_cap, s, nq, gs, used, w);
-        wres = w.resid + 1u;
+        wres = w.resid;
         wsol = w.solve;
         wg = w.g;
         guess_out[a] = used ? o.T : 0.0;
