@@ -201,8 +201,11 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
     makespan = max(lat_closed)  # every event submitted at t0
     wall_closed = time.perf_counter() - t0
     st1 = srv.stats()
+    ew = np.zeros(3)
     for t in tk:
-        srv.collect(t, names=("T",))
+        ew += np.array(srv.collect(t, names=("T",))["totals"]["eos_work"], dtype=float)
+    # EoS work per particle and stage (the observe pass of each event counted as one stage)
+    eos_per_pstage = (ew / (ntot * (2 * ksteps + 1))).tolist()
     cap_eps = nevents / makespan
     # open loop: Poisson arrivals at `load` x the measured capacity (exponential gaps, seed 3)
     u = I.uniform01(3, nevents)
@@ -245,6 +248,8 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
                       "p50_s": float(np.median(lat_open)), "p99_s": float(np.percentile(lat_open, 99)),
                       "mean_s": float(lat_open.mean()), "wall_s": wall_open,
                       "batch_steps": st2["batch_steps"] - st1["batch_steps"]},
+        "eos_work_per_particle_stage": {"table_evals": eos_per_pstage[0], "solves": eos_per_pstage[1],
+                                        "closed_form_evals": eos_per_pstage[2]},
         "max_events": max_events, "latency": "submit (host arrays) to results readable in host memory",
         "precision": "mixed: FP32 neighbour sums (compensated), FP64 EoS/EoM/totals; no Newton polish",
     }

@@ -224,15 +224,22 @@ __global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const doubl
     if (threadIdx.x == 0) wpart[blockIdx.x] = red[0] + red[1];
 }
 
-// Serving form: the same EoS pass over the segmented arena (persistent grid).  A warp
-// never straddles two events, so the work-rate partial of every warp of an event's range
-// goes to wpart[a / 32] and the per-event counters are warp-aggregated.
+// Serving form: the same EoS pass over the segmented arena.  Persistent blocks claim chunks
+// of 64 particles from a counter (the Newton work per particle varies, so a static split
+// leaves a tail).  A warp never straddles two events, so the work-rate partial of every warp
+// of an event's range goes to wpart[a / 32] and the per-event counters are warp-aggregated.
 __global__ void __launch_bounds__(64, 6) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
 {
+    __shared__ int s_chunk;
     const BatchTable *T = A.tab;
     const int hi = T->hi;
     const size_t P = (size_t)A.P;
-    for (int base = blockIdx.x * 64; base < hi; base += gridDim.x * 64) {
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = (int)atomicAdd(&A.claim[CLAIM_EOS], 1u);
+        __syncthreads();
+        const int base = s_chunk * 64;
+        __syncthreads();
+        if (base >= hi) break;
         const int a = base + threadIdx.x;
         const int s = A.segid[a];  // warp-uniform: ranges are multiples of 256 and hi is a range end
         if (s < 0 || !seg_active(T, s, stage, false)) continue;

@@ -54,6 +54,10 @@ namespace {
 constexpr int kScanBlocks = 256;
 constexpr int kTT = 128;    // threads of a tiled neighbour block
 constexpr int kTile = 512;  // candidates staged in shared memory at a time
+// Accumulation: each lane sums runs of kRun candidates in plain FP32 (at most kRun terms, so a
+// run's sum errs by <= kRun u times the sum of its terms' magnitudes, u = 2^-24) and folds
+// every run into Neumaier-compensated FP32 sums; the lanes of a particle are combined in FP64.
+constexpr int kRun = 16;
 
 // ---------------------------------------------------------------------------
 // single-precision helpers (Neumaier two-sum accumulation, cubic spline kernel)
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(kMaxSlots) k_seg_grid(Arena A, int stage)
         A.grid[s].ncell = nc;
     }
     if (s == kMaxSlots - 1) *A.ncells = sh[s];
+    if (s < kClaims) A.claim[s] = 0u;
 }
 
 __global__ void k_seg_zero(Arena A)
@@ -421,9 +426,14 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
     const int ncells = *A.ncells;
     const size_t P = (size_t)A.P;
     const int tid = threadIdx.x;
-    for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
-        if (tid == 0) cell_setup(A, s_base, ns, c, cc);
+    __shared__ int s_cell;
+    for (;;) {
+        if (tid == 0) {
+            s_cell = (int)atomicAdd(&A.claim[CLAIM_DENSITY], 1u);
+            if (s_cell < ncells) cell_setup(A, s_base, ns, s_cell, cc);
+        }
         __syncthreads();
+        if (s_cell >= ncells) break;
         const int na = cc.na;
         if (na > 0) {
             const EvView &V = A.segv[cc.s];
@@ -454,29 +464,40 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
                     }
                     __syncthreads();
                     if (valid) {
-                        for (int j = l; j < mt; j += L) {
-                            const float2 pb = cpos[j];
-                            const float dx = fax - pb.x, dy = fay - pb.y;
-                            const float r2 = fmaf(dx, dx, dy * dy);
-                            if (r2 <= shi) {
-                                bool acc = r2 < slo;
-                                if (!acc) {  // thin shell: the exact FP64 decision
-                                    const int b = cidx[j];
-                                    acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
-                                    ++shell;
-                                }
-                                if (acc) {
-                                    const float q = r2 > 0.0f ? r2 * rsqrtf(r2) * ih : 0.0f;
-                                    const float w = kernel_wf(q);
-                                    const float4 v = cq[j];
-                                    cadd(sg, w);
-                                    cadd(ss, v.x * w);
-                                    cadd(sb, v.y * w);
-                                    cadd(sS, v.z * w);
-                                    cadd(sq, v.w * w);
-                                    ++nacc;
+                        // runs of kRun candidates summed in plain FP32, each run folded into the
+                        // compensated sums
+                        for (int jb = l; jb < mt; jb += kRun * L) {
+                            const int je = min(mt, jb + kRun * L);
+                            float pg = 0.f, ps = 0.f, pB = 0.f, pS = 0.f, pQ = 0.f;
+                            for (int j = jb; j < je; j += L) {
+                                const float2 pb = cpos[j];
+                                const float dx = fax - pb.x, dy = fay - pb.y;
+                                const float r2 = fmaf(dx, dx, dy * dy);
+                                if (r2 <= shi) {
+                                    bool acc = r2 < slo;
+                                    if (!acc) {  // thin shell: the exact FP64 decision
+                                        const int b = cidx[j];
+                                        acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                                        ++shell;
+                                    }
+                                    if (acc) {
+                                        const float q = r2 > 0.0f ? r2 * rsqrtf(r2) * ih : 0.0f;
+                                        const float w = kernel_wf(q);
+                                        const float4 v = cq[j];
+                                        pg += w;
+                                        ps = fmaf(v.x, w, ps);
+                                        pB = fmaf(v.y, w, pB);
+                                        pS = fmaf(v.z, w, pS);
+                                        pQ = fmaf(v.w, w, pQ);
+                                        ++nacc;
+                                    }
                                 }
                             }
+                            cadd(sg, pg);
+                            cadd(ss, ps);
+                            cadd(sb, pB);
+                            cadd(sS, pS);
+                            cadd(sq, pQ);
                         }
                     }
                 }
@@ -528,9 +549,14 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
     const size_t P = (size_t)A.P;
     const double *gin = A.gin;
     const int tid = threadIdx.x;
-    for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
-        if (tid == 0) cell_setup(A, s_base, ns, c, cc);
+    __shared__ int s_cell;
+    for (;;) {
+        if (tid == 0) {
+            s_cell = (int)atomicAdd(&A.claim[CLAIM_GRADIENT], 1u);
+            if (s_cell < ncells) cell_setup(A, s_base, ns, s_cell, cc);
+        }
         __syncthreads();
+        if (s_cell >= ncells) break;
         const int na = cc.na;
         if (na > 0 && T->slots[cc.s].mode == SLOT_STEP) {
             const EvView &V = A.segv[cc.s];
@@ -561,32 +587,45 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
                     }
                     __syncthreads();
                     if (valid) {
-                        for (int j = l; j < mt; j += L) {
-                            const float2 pb = cpos[j];
-                            const float dx = fax - pb.x, dy = fay - pb.y;
-                            const float r2 = fmaf(dx, dx, dy * dy);
-                            if (r2 <= shi && r2 > 0.0f) {
-                                bool acc = r2 < slo;
-                                if (!acc) {
-                                    const int b = cidx[j];
-                                    acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
-                                }
-                                if (acc) {
-                                    const float ir = rsqrtf(r2);
-                                    const float fac = kernel_dwf(r2 * ir * ih) * ir;
-                                    const float gx = fac * dx, gy = fac * dy;
-                                    const float4 X = cX[j];
-                                    const float2 U = cU[j];
-                                    cadd(Gx, gx);
-                                    cadd(Gy, gy);
-                                    cadd(Hx, fmaf(X.x, gx, X.z * gy));
-                                    cadd(Hy, fmaf(X.y, gx, X.w * gy));
-                                    cadd(xx, U.x * gx);
-                                    cadd(xy, U.y * gx);
-                                    cadd(yx, U.x * gy);
-                                    cadd(yy, U.y * gy);
+                        for (int jb = l; jb < mt; jb += kRun * L) {
+                            const int je = min(mt, jb + kRun * L);
+                            float pGx = 0.f, pGy = 0.f, pHx = 0.f, pHy = 0.f;
+                            float pxx = 0.f, pxy = 0.f, pyx = 0.f, pyy = 0.f;
+                            for (int j = jb; j < je; j += L) {
+                                const float2 pb = cpos[j];
+                                const float dx = fax - pb.x, dy = fay - pb.y;
+                                const float r2 = fmaf(dx, dx, dy * dy);
+                                if (r2 <= shi && r2 > 0.0f) {
+                                    bool acc = r2 < slo;
+                                    if (!acc) {
+                                        const int b = cidx[j];
+                                        acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                                    }
+                                    if (acc) {
+                                        const float ir = rsqrtf(r2);
+                                        const float fac = kernel_dwf(r2 * ir * ih) * ir;
+                                        const float gx = fac * dx, gy = fac * dy;
+                                        const float4 X = cX[j];
+                                        const float2 U = cU[j];
+                                        pGx += gx;
+                                        pGy += gy;
+                                        pHx = fmaf(X.x, gx, fmaf(X.z, gy, pHx));
+                                        pHy = fmaf(X.y, gx, fmaf(X.w, gy, pHy));
+                                        pxx = fmaf(U.x, gx, pxx);
+                                        pxy = fmaf(U.y, gx, pxy);
+                                        pyx = fmaf(U.x, gy, pyx);
+                                        pyy = fmaf(U.y, gy, pyy);
+                                    }
                                 }
                             }
+                            cadd(Gx, pGx);
+                            cadd(Gy, pGy);
+                            cadd(Hx, pHx);
+                            cadd(Hy, pHy);
+                            cadd(xx, pxx);
+                            cadd(xy, pxy);
+                            cadd(yx, pyx);
+                            cadd(yy, pyy);
                         }
                     }
                 }
@@ -1201,6 +1240,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     SAL(A.start, sizeof(uint32_t) * (size_t)A.cmax);
     SAL(A.scan_part, sizeof(uint32_t) * kScanBlocks);
     SAL(A.ncells, sizeof(int));
+    SAL(A.claim, sizeof(unsigned int) * kClaims);
     SAL(A.tab, sizeof(BatchTable));
     SAL(A.grid, sizeof(SegGrid) * kMaxSlots);
     SAL(A.segv, sizeof(EvView) * kMaxSlots);
@@ -1208,7 +1248,8 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     if (cudaMemsetAsync(A.segid, 0xFF, sizeof(int) * Pz, S->st) != cudaSuccess ||
         cudaMemsetAsync(A.tab, 0, sizeof(BatchTable), S->st) != cudaSuccess ||
         cudaMemsetAsync(A.grid, 0, sizeof(SegGrid) * kMaxSlots, S->st) != cudaSuccess ||
-        cudaMemsetAsync(A.ncells, 0, sizeof(int), S->st) != cudaSuccess) {
+        cudaMemsetAsync(A.ncells, 0, sizeof(int), S->st) != cudaSuccess ||
+        cudaMemsetAsync(A.claim, 0, sizeof(unsigned int) * kClaims, S->st) != cudaSuccess) {
         cudaGetLastError();
         return bail(sfail(SPH_ERR_CUDA, "cudaMemsetAsync failed"));
     }

@@ -312,11 +312,13 @@ struct Arena {
     float4 *fq, *fX;
     float2 *fU;
     int *ncells;  // device-written total of the active slots' cells
+    unsigned int *claim;  // work counters of the dynamically scheduled passes (reset per stage)
     BatchTable *tab;
     SegGrid *grid;
     EvView *segv;
     DevScalars *sc;
 };
+constexpr int CLAIM_EOS = 0, CLAIM_DENSITY = 1, CLAIM_GRADIENT = 2, kClaims = 4;
 // slot s takes part in this stage's pass: stage 1 evaluates STEP and OBSERVE slots, stage 2
 // and the rate passes (gradient, equations of motion, work) only STEP slots
 __device__ __forceinline__ bool seg_active(const BatchTable *t, int s, int stage, bool rates)
