@@ -120,7 +120,7 @@ static EvView make_view(const sph_event *ev)
     double two_h = 2.0 * ev->h;
     v.supp2 = two_h * two_h;
     v.inv_cell = 1.0 / (2.0 * ev->h);
-    v.supp2_hi = prefilter_bound(ev->h, ev->B, ev->dim);
+    prefilter_bounds(ev->h, ev->B, ev->dim, v.supp2_lo, v.supp2_hi);
     v.mixed = ev->mixed;
     v.cell_f = (float)(2.0 * ev->h);
     mixed_shell(ev->h, v.shell_lo, v.shell_hi);

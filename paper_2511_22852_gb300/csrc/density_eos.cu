@@ -65,10 +65,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
     const unsigned lt = (1u << lane) - 1u;
     double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
     int c = 0, qn = 0;
-    auto pair = [&](int b) {
-        double r2 = dist2_2d(xa - X[b], ya - Y[b]);
-        if (r2 < v.supp2) {
-            double q = r2 > 0.0 ? r2 * rsqrt_nr(r2) * v.inv_h : 0.0;
+    // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
+    auto pair = [&](int qb) {
+        const int b = qb & 0x7FFFFFFF;
+        const double dx = xa - X[b], dy = ya - Y[b];
+        if (qb < 0 && !(dist2_2d(dx, dy) < v.supp2)) return;
+        {
+            const double r2 = fma(dx, dx, dy * dy);
+            double q = r2 > 0.0 ? r2 * inv_sqrt(r2) * v.inv_h : 0.0;
             double w = kernel_w(q);
             sg += w;
             ss = fma(S[b], w, ss);
@@ -88,14 +92,16 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
             const uint32_t b0 = start[k], b1 = b0 + cnt[k];
             for (uint32_t base = b0; base < b1; base += 32) {
                 const uint32_t b = base + lane;
-                bool cand = false;
+                bool cand = false, sure = false;
                 if (b < b1) {
                     const float2 fb = fpos[b];
                     const float dx = fa.x - fb.x, dy = fa.y - fb.y;
-                    cand = fmaf(dx, dx, dy * dy) <= v.supp2_hi;
+                    const float r2f = fmaf(dx, dx, dy * dy);
+                    cand = r2f <= v.supp2_hi;
+                    sure = r2f < v.supp2_lo;
                 }
                 const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-                if (cand) q[qn + __popc(m & lt)] = (int)b;
+                if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
                 qn += __popc(m);
                 __syncwarp();
                 if (qn >= 32) {

@@ -54,11 +54,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_gradient2(EvView v, int stage, 
     double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
     double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
     int qn = 0;
-    auto pair = [&](int b) {
+    // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
+    auto pair = [&](int qb) {
+        const int b = qb & 0x7FFFFFFF;
         const double dx = xa - X[b], dy = ya - Y[b];
-        const double r2 = dist2_2d(dx, dy);
-        if (r2 < v.supp2 && r2 > 0.0) {
-            const double ir = rsqrt_nr(r2);
+        if (qb < 0 && !(dist2_2d(dx, dy) < v.supp2)) return;
+        const double r2 = fma(dx, dx, dy * dy);
+        if (r2 > 0.0) {
+            const double ir = inv_sqrt(r2);
             const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;  // (dW/dr)/r without sigma_d/h
             const double gx = fac * dx, gy = fac * dy;
             Gx += gx;
@@ -82,14 +85,16 @@ __global__ void __launch_bounds__(32 * kWarps) k_gradient2(EvView v, int stage, 
             const uint32_t b0 = start[k], b1 = b0 + cnt[k];
             for (uint32_t base = b0; base < b1; base += 32) {
                 const uint32_t b = base + lane;
-                bool cand = false;
+                bool cand = false, sure = false;
                 if (b < b1) {
                     const float2 fb = fpos[b];
                     const float dx = fa.x - fb.x, dy = fa.y - fb.y;
-                    cand = fmaf(dx, dx, dy * dy) <= v.supp2_hi;
+                    const float r2f = fmaf(dx, dx, dy * dy);
+                    cand = r2f <= v.supp2_hi;
+                    sure = r2f < v.supp2_lo;
                 }
                 const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-                if (cand) q[qn + __popc(m & lt)] = (int)b;
+                if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
                 qn += __popc(m);
                 __syncwarp();
                 if (qn >= 32) {

@@ -140,7 +140,7 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     double two_h = 2.0 * h;
     v.supp2 = two_h * two_h;
     v.inv_cell = 1.0 / (2.0 * h);
-    v.supp2_hi = prefilter_bound(h, kMaxBits);
+    prefilter_bounds(h, kMaxBits, 2, v.supp2_lo, v.supp2_hi);
     v.sigma_d = 10.0 / (7.0 * kPi * h * h);
     v.sc = sc;
 

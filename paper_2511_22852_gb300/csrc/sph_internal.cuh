@@ -73,6 +73,7 @@ struct EvView {
     const uint32_t *spread;   // 3D: spread[d * 1024 + c] = key bits of cell coordinate c on axis d
     double h, inv_h, supp2, inv_cell, sigma_d, dtau;
     float supp2_hi;  // single-precision prefilter bound, >= (2h)^2 plus the worst rounding error
+    float supp2_lo;  // below it the float r^2 proves r < 2h: the exact FP64 test is skipped
     int mixed;                 // 1: neighbour passes in FP32 with compensated sums (2D)
     float cell_f;              // mixed: cell side 2h in single precision
     float shell_lo, shell_hi;  // mixed: float r^2 below lo is inside, above hi outside, else FP64 test
@@ -123,17 +124,8 @@ __device__ __forceinline__ int cell_coord(double x, double xmin, double inv_cell
 // neighbour decision r^2 < (2h)^2 is bit-for-bit reproducible
 __device__ __forceinline__ double dist2_2d(double dx, double dy) { return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)); }
 
-// 1/sqrt(x) for x > 0: single-precision seed, then two Newton-Raphson steps
-// y <- y (3 - x y^2) / 2 in double precision (quadratic convergence: ~1e-7 ->
-// ~1e-14 -> below one ulp of rounding noise)
-__device__ __forceinline__ double rsqrt_nr(double x)
-{
-    double y = (double)rsqrtf((float)x);
-    double xh = 0.5 * x;
-    y = y * fma(-xh * y, y, 1.5);
-    y = y * fma(-xh * y, y, 1.5);
-    return y;
-}
+// 1/sqrt(x) for x > 0 in double precision: CUDA's rsqrt (at most 1 ulp of error)
+__device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
 
 // cubic spline kernel (Sec. "Kernel function") as functions of q = r/h:
 // W = sigma_d w(q), dW/dr = sigma_d/h w'(q)
@@ -187,17 +179,29 @@ struct CellBufs {
 // axes then errs by at most 4 (2h) e + 2 e^2 + 4 u (2h)^2 with e the difference error.
 // Twice that margin is added, so the prefilter never rejects a pair the exact
 // double-precision test r^2 < (2h)^2 accepts; the exact test decides every pair.
-inline float prefilter_bound(double h, int B, int dim = 2)
+// The same margin below (2h)^2 gives the lower bound: a float r^2 under it proves r < 2h (for
+// |dx_d| near 2h the error is at most err; farther candidates have r^2 - (2h)^2 much larger
+// than their error), so those pairs skip the exact test and the neighbour set is unchanged.
+inline void prefilter_bounds(double h, int B, int dim, float &lo_out, float &hi_out)
 {
     const double u = 1.0 / 16777216.0;
     const double two_h = 2.0 * h;
     const double L = (double)(1 << B) * two_h;
     const double e = 2.0 * L * u + 2.0 * two_h * u + L * u;
     const double err = 2.0 * dim * two_h * e + dim * e * e + (dim + 2) * u * two_h * two_h;
-    const double hi = two_h * two_h + 2.0 * err;
+    const double hi = two_h * two_h + 2.0 * err, lo = two_h * two_h - 2.0 * err;
     float f = (float)hi;
     while ((double)f < hi) f = nextafterf(f, 1e30f);
-    return f;
+    float g = (float)lo;
+    while ((double)g > lo) g = nextafterf(g, 0.0f);
+    hi_out = f;
+    lo_out = g;
+}
+inline float prefilter_bound(double h, int B, int dim = 2)
+{
+    float lo, hi;
+    prefilter_bounds(h, B, dim, lo, hi);
+    return hi;
 }
 
 void launch_bbox(const EvView &v, const double *y, cudaStream_t st);

@@ -92,14 +92,17 @@ __device__ __forceinline__ void walk27(const EvView &v, const uint32_t *__restri
                 const uint32_t b0 = start[k], b1 = b0 + cnt[k];
                 for (uint32_t base = b0; base < b1; base += 32) {
                     const uint32_t b = base + lane;
-                    bool cand = false;
+                    bool cand = false, sure = false;
                     if (b < b1) {
                         const float4 fb = fpos[b];
                         const float dx = fa.x - fb.x, dy = fa.y - fb.y, dz = fa.z - fb.z;
-                        cand = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= v.supp2_hi;
+                        const float r2f = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        cand = r2f <= v.supp2_hi;
+                        sure = r2f < v.supp2_lo;
                     }
                     const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-                    if (cand) q[qn + __popc(m & lt)] = (int)b;
+                    // bit 31 set: the float test left the pair undecided (exact test needed)
+                    if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
                     qn += __popc(m);
                     __syncwarp();
                     if (qn >= 32) {
@@ -140,10 +143,13 @@ __global__ void __launch_bounds__(32 * kWarps3) k_density3(EvView v, const doubl
     const double xa[3] = {X[a], Y[a], Z[a]};
     double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
     int c = 0;
-    auto pair = [&](int b) {
-        double r2 = dist2_3d(xa[0] - X[b], xa[1] - Y[b], xa[2] - Z[b]);
-        if (r2 < v.supp2) {
-            double q = r2 > 0.0 ? r2 * rsqrt_nr(r2) * v.inv_h : 0.0;
+    auto pair = [&](int qb) {
+        const int b = qb & 0x7FFFFFFF;
+        const double dx = xa[0] - X[b], dy = xa[1] - Y[b], dz = xa[2] - Z[b];
+        if (qb < 0 && !(dist2_3d(dx, dy, dz) < v.supp2)) return;
+        {
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            double q = r2 > 0.0 ? r2 * inv_sqrt(r2) * v.inv_h : 0.0;
             double w = kernel_w(q);
             sg += w;
             ss = fma(S[b], w, ss);
@@ -325,11 +331,13 @@ __global__ void __launch_bounds__(32 * kWarps3) k_gradient3(EvView v, int stage,
     const double *X = y, *Y = y + n, *Z = y + 2 * n;
     const double xa[3] = {X[a], Y[a], Z[a]};
     double G[3] = {0, 0, 0}, H[3] = {0, 0, 0}, du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    auto pair = [&](int b) {
+    auto pair = [&](int qb) {
+        const int b = qb & 0x7FFFFFFF;
         const double d[3] = {xa[0] - X[b], xa[1] - Y[b], xa[2] - Z[b]};
-        const double r2 = dist2_3d(d[0], d[1], d[2]);
-        if (r2 < v.supp2 && r2 > 0.0) {
-            const double ir = rsqrt_nr(r2);
+        if (qb < 0 && !(dist2_3d(d[0], d[1], d[2]) < v.supp2)) return;
+        const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+        if (r2 > 0.0) {
+            const double ir = inv_sqrt(r2);
             const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;
             double gw[3];
 #pragma unroll

@@ -48,3 +48,41 @@ def test_prefilter_keeps_every_true_neighbour(h, B):
     assert np.all(r2f[inside] <= bound)
     # and the margin stays small: the prefilter passes under 1 % more area than the exact test
     assert float(bound) / (two_h * two_h) - 1 < 1e-2
+
+
+def prefilter_bounds(h, B):
+    """(lo, hi): the same margin below and above (2h)^2 (float32, rounded outward)."""
+    hi = prefilter_bound(h, B)
+    two_h = 2.0 * h
+    lo = two_h * two_h - (float(hi) - two_h * two_h)
+    g = np.float32(lo)
+    while float(g) > lo:
+        g = np.nextafter(g, np.float32(0.0))
+    return g, hi
+
+
+@pytest.mark.parametrize("h,B", [(0.3, 7), (0.3, 10), (0.5, 6), (0.05, 12)])
+def test_lower_bound_proves_neighbours(h, B):
+    """A float r^2 below the lower bound proves r < 2h: pairs just outside the support never
+    fall under it, so skipping the exact test for them keeps the neighbour set exact."""
+    rng = np.random.default_rng(100 + B)
+    lo, hi = prefilter_bounds(h, B)
+    two_h = 2 * h
+    L = (1 << B) * two_h
+    m = 200000
+    xa = rng.uniform(0.0, L, (m, 2))
+    ang = rng.uniform(0, 2 * np.pi, m)
+    r = two_h * (1.0 + rng.uniform(0, 1e-9, m))  # just outside (or on) the support
+    xb = xa + np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1)
+    ok = np.all((xb >= 0) & (xb <= L), axis=1)
+    xa, xb = xa[ok], xb[ok]
+    d = xa - xb
+    r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+    outside = r2 >= two_h * two_h
+    fa, fb = xa.astype(np.float32), xb.astype(np.float32)
+    dx = (fa[:, 0] - fb[:, 0]).astype(np.float32)
+    dy = (fa[:, 1] - fb[:, 1]).astype(np.float32)
+    p = (dy * dy).astype(np.float32)
+    r2f = (dx.astype(np.float64) * dx.astype(np.float64) + p.astype(np.float64)).astype(np.float32)
+    assert np.all(r2f[outside] >= lo)
+    assert lo < two_h * two_h < hi
