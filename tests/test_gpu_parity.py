@@ -7,6 +7,7 @@ step and for the right-hand side; 1e-8 over a full evolution.
 import numpy as np
 import pytest
 
+import gubser_viscous as VG
 from oracle import oracle as O
 from paper_2511_22852_gb300 import inputs as I
 
@@ -46,6 +47,7 @@ CASES = {
     "bsq_small": lambda: I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20),
     "blob_causal": lambda: I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS),
     "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
+    "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2)),
 }
 CASES3 = {
     "blob3_milne": lambda: I.smooth_blob_3d(milne=True, flow=0.3),

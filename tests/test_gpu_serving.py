@@ -10,6 +10,7 @@
 import numpy as np
 import pytest
 
+import gubser_viscous as VG
 from oracle import oracle as O
 from paper_2511_22852_gb300 import inputs as I
 
@@ -68,11 +69,13 @@ def check_against_oracle(out, ev, nsteps):
     return run
 
 
-@pytest.mark.parametrize("case,nsteps", [("bsq", 20), ("gubser", 30), ("blob_causal", 20), ("bjorken", 10)])
+@pytest.mark.parametrize("case,nsteps", [("bsq", 20), ("gubser", 30), ("blob_causal", 20), ("bjorken", 10),
+                                        ("gubser_viscous", 30)])
 def test_server_event_matches_fp64_oracle(Bd, case, nsteps):
     ev = {"bsq": lambda: bsq(3000), "gubser": lambda: I.gubser_ideal_2p1(),
           "blob_causal": lambda: I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS),
-          "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21)}[case]()
+          "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
+          "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2))}[case]()
     out = serve_alone(Bd, ev, nsteps, max_events=4, max_particles=1 << 16)
     run = check_against_oracle(out, ev, nsteps)
     tt = out["totals"]

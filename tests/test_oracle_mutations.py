@@ -44,12 +44,8 @@ MUTATIONS = [
      "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
     ("entropy_drop_bulk", "R->dS = (-q->Pi * theta + pisig)", "R->dS = (pisig)",
      "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
-    pytest.param("shear_drop_accel_coupling", "double dpi = (rhs - chr - coup) / u0;", "double dpi = (rhs - chr) / u0;",
-                 "test_oracle_physics.py::test_viscous_second_law_and_energy_balance",
-                 marks=pytest.mark.xfail(strict=True, reason="parity unpinned: the projection coupling "
-                                         "u^i pi^{j alpha} a_alpha of the shear equation is second order and "
-                                         "no current pin resolves it (a viscous Gubser pin would)"),
-                 id="shear_drop_accel_coupling"),
+    ("shear_drop_accel_coupling", "double dpi = (rhs - chr - coup) / u0;", "double dpi = (rhs - chr) / u0;",
+     "test_oracle_physics.py::test_viscous_gubser_against_ode"),
     ("momentum_drop_pi0i", "R->dP[i] = (u[i] / q->sigma) * dw + (w / q->sigma) * a[i] - (w * u[i] / (q->sigma * q->sigma)) * dsig + dpi0;",
      "R->dP[i] = (u[i] / q->sigma) * dw + (w / q->sigma) * a[i] - (w * u[i] / (q->sigma * q->sigma)) * dsig;",
      "test_oracle_physics.py::test_viscous_second_law_and_energy_balance"),

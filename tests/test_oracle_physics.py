@@ -10,11 +10,16 @@
   conservation"), second law for viscous flow, and the energy balance of Milne
   coordinates (E(tau) + longitudinal work = E(tau0)).
 * Transversality and tracelessness of the reconstructed shear tensor.
+* Shear-viscous Gubser flow (conformal EoS) against the semi-analytic ODE solution for T and
+  pibar = tau^2 pi^{eta eta}/(e + p) (Sec. "Code validation", EoS2 without charges), with
+  second-order convergence: pins the shear equation's coupling to the acceleration and the
+  transverse pi^{ij} that Bjorken flow leaves untested.
 """
 import numpy as np
 import pytest
 from scipy.integrate import solve_ivp
 
+import gubser_viscous as VG
 from oracle import oracle as O
 from paper_2511_22852_gb300 import inputs as I
 
@@ -177,3 +182,37 @@ def test_bjorken_3p1_milne_against_ode():
     assert abs(sigma * run.y[8][c] - Phiode / 2) < 1e-3 * abs(Phiode)
     assert abs(sigma * run.y[11][c] - Phiode / 2) < 1e-3 * abs(Phiode)
     assert max(abs(run.y[9][c]), abs(run.y[10][c]), abs(run.y[12][c])) < 1e-9 * abs(run.y[8][c])
+
+
+def _viscous_gubser_errors(ode, n_side, h, dtau, nsteps, rmax=2.5):
+    """Max |T/T_ode - 1| and max |pibar - pibar_ode| over the particles within rmax at the end."""
+    ev = VG.gubser_viscous_2p1(ode, n_side=n_side, h=h, dtau=dtau, nsteps=nsteps)
+    run = O.OracleRun.start(ev)
+    run.step(nsteps)
+    aux, _ = run.observe()
+    A = O.AUX
+    x, y = run.y[0], run.y[1]
+    r = np.sqrt(x * x + y * y)
+    m = r <= rmax
+    rho = VG.rho_of(run.tau, r)
+    ux, uy = run.y[2], run.y[3]
+    g = np.sqrt(1.0 + ux * ux + uy * uy)
+    vx, vy = ux / g, uy / g
+    sig = aux[A["sigma"]]
+    pxx, pxy, pyy = sig * run.y[6], sig * run.y[7], sig * run.y[8]
+    t2pee = vx * (vx * pxx + vy * pxy) + vy * (vx * pxy + vy * pyy) - pxx - pyy  # tracelessness
+    pibar = t2pee / (aux[A["e"]] + aux[A["p"]])
+    eT = np.abs(aux[A["T"]][m] / (ode.T(rho[m]) / run.tau) - 1.0).max()
+    ep = np.abs(pibar[m] - ode.pibar(rho[m])).max()
+    assert run.status_or == 0 and abs(run.tau - 1.6) < 1e-9
+    return eT, ep, np.abs(ode.pibar(rho[m])).max()
+
+
+def test_viscous_gubser_against_ode():
+    ode = VG.GubserODE(eta_over_s=0.2)
+    eT1, ep1, pmax = _viscous_gubser_errors(ode, 51, 0.5, 0.01, 60)
+    assert pmax > 0.1  # the shear stress is well resolved in the compared region
+    assert eT1 < 0.035 and ep1 < 0.02
+    eT2, ep2, _ = _viscous_gubser_errors(ode, 101, 0.25, 0.005, 120)
+    assert eT2 < 0.3 * eT1 and ep2 < 0.4 * ep1
+    assert eT2 < 0.008 and ep2 < 0.006
