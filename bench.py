@@ -255,6 +255,33 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
     }
 
 
+def bench_3p1d(Bd, I, steps: int = 3):
+    """The 3+1D hyperbolic viscous BSQ event (about 10^6 particles): device ms per Heun step of
+    the plain FP64 form next to the mixed form (FP32 neighbour sums, FP64 EoS and equations of
+    motion), CUDA events on the event's stream after one untimed step."""
+    import torch
+    ev = I.viscous_bsq_3p1()
+    out = {"workload": f"3+1D Milne viscous BSQ event, {ev.n} particles, dx = dy = 0.124 fm, d_eta = 0.1, "
+                       f"h = 0.3 fm, dtau = 0.005 fm, 64x32^3 EoS table", "steps": steps}
+    for name, prec in (("fp64", Bd.SPH_FP64), ("mixed", Bd.SPH_MIXED)):
+        st = torch.cuda.Stream()
+        g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream, precision=prec)
+        g.step(1, sync=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            g.step(steps)
+            e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": ev.n / (ms / 1e3)}
+        if prec == Bd.SPH_MIXED:
+            out[name]["shell_tests"] = g.totals()["shell_tests"]
+        g.free()
+    out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -415,6 +442,8 @@ def run_ours(args):
                                "profile_mode_group_ms_per_step": total_ms / kp}}
         if not args.no_serving:
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
+        if not args.no_3d:
+            out["config_3p1d"] = bench_3p1d(Bd, I)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ev)
         print(json.dumps(out), flush=True)
@@ -433,6 +462,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--serving-events", type=int, default=32)
     ap.add_argument("--serving-steps", type=int, default=60)
     ap.add_argument("--serving-only", action="store_true",

@@ -139,7 +139,7 @@ typedef struct {
     int32_t precision; /* SPH_FP64 or SPH_MIXED (see below) */
 } sph_event_desc;
 
-/* Precision of the step.  SPH_FP64: every operation in double precision.  SPH_MIXED (dim = 2):
+/* Precision of the step.  SPH_FP64: every operation in double precision.  SPH_MIXED (dim 2 or 3):
  * the neighbour passes (kernel sums and gradients) run in single precision with positions
  * relative to their cell's origin and compensated (two-sum) accumulation, combined in double
  * precision per particle; the neighbour set stays exactly that of the FP64 test (a proven float

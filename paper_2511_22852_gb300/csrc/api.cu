@@ -123,7 +123,8 @@ static EvView make_view(const sph_event *ev)
     prefilter_bounds(ev->h, ev->B, ev->dim, v.supp2_lo, v.supp2_hi);
     v.mixed = ev->mixed;
     v.cell_f = (float)(2.0 * ev->h);
-    mixed_shell(ev->h, v.shell_lo, v.shell_hi);
+    if (ev->dim == 3) mixed_shell3(ev->h, v.shell_lo, v.shell_hi);
+    else mixed_shell(ev->h, v.shell_lo, v.shell_hi);
     v.sigma_d = ev->dim == 2 ? 10.0 / (7.0 * kPi * ev->h * ev->h) : 1.0 / (kPi * ev->h * ev->h * ev->h);
     v.dtau = ev->dtau;
     v.sc = ev->sc;
@@ -400,10 +401,6 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     if (d->precision != SPH_FP64 && d->precision != SPH_MIXED) {
         sph_free_event(ev);
         return fail(SPH_ERR_ARG, "precision must be SPH_FP64 or SPH_MIXED");
-    }
-    if (d->precision == SPH_MIXED && d->dim != 2) {
-        sph_free_event(ev);
-        return fail(SPH_ERR_ARG, "the mixed-precision form is implemented for dim = 2");
     }
     ev->mixed = d->precision == SPH_MIXED ? 1 : 0;
     ev->profile = d->profile != 0;

@@ -252,6 +252,25 @@ inline void mixed_shell(double h, float &lo, float &hi)
     hi = g;
 }
 
+// The same for 3+1D: three axes, so the float r^2 (nested fmaf) errs by at most
+// 2 dim (2h) e + dim e^2 + 6 u (2h)^2 <= 42 (2h)^2 u with e <= 6 (2h) u; the shell is
+// +-96 (2h)^2 u.
+inline void mixed_shell3(double h, float &lo, float &hi)
+{
+    const double u = 1.0 / 16777216.0;
+    const double s2 = 4.0 * h * h;
+    const double err = 96.0 * s2 * u;
+    float l = (float)(s2 - err), g = (float)(s2 + err);
+    while ((double)l > s2 - err) l = nextafterf(l, 0.0f);
+    while ((double)g < s2 + err) g = nextafterf(g, 1e30f);
+    lo = l;
+    hi = g;
+}
+void launch_density3m(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                      cudaStream_t st);
+void launch_gradient3m(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
+                       cudaStream_t st);
+
 // 3D versions (step3d.cu); the launchers above dispatch to them when v.dim == 3
 void launch_cells3(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st);
 void launch_density3(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,

@@ -718,6 +718,10 @@ void launch_cells3(const EvView &v, const double *y, const int *id, CellBufs cb,
 void launch_density3(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                      cudaStream_t st)
 {
+    if (v.mixed) {
+        launch_density3m(v, y, Nq, cb, dens, nnb, st);
+        return;
+    }
     k_fpos3<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos3);
     k_density3<<<nblk(v.n, kWarps3), 32 * kWarps3, 0, st>>>(v, y, cb.fpos3, Nq, cb.start, cb.cnt, dens, nnb);
 }
@@ -732,6 +736,10 @@ void launch_eos3(const EvView &v, int stage, const double *y, const double *dens
 void launch_gradient3(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
                       cudaStream_t st)
 {
+    if (v.mixed) {
+        launch_gradient3m(v, stage, y, gin, cb, gout, st);
+        return;
+    }
     k_gradient3<<<nblk(v.n, kWarps3), 32 * kWarps3, 0, st>>>(v, stage, y, cb.fpos3, gin, cb.start, cb.cnt, gout);
 }
 

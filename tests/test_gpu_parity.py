@@ -463,3 +463,42 @@ def test_mixed_precision_full_size_event(Bd):
     assert relerr(f["T"], aux[A["T"]]) < TOL_MIXED and relerr(f["S_DENS"], aux[A["s"]]) < TOL_MIXED
     assert relerr(f["MU"], aux[A["muB"]:A["muQ"] + 1]) < TOL_MIXED
     g.free()
+
+
+@pytest.mark.parametrize("case", list(CASES3))
+def test_mixed_precision_3d_against_fp64_oracle(Bd, case):
+    """SPH_MIXED in 3+1D: FP32 27-cell neighbour passes, FP64 EoS/EoM -- within 1e-5 of the FP64
+    oracle after 10 steps, neighbour counts exact."""
+    ev = CASES3[case]()
+    g = Bd.GpuEvent(ev, precision=Bd.SPH_MIXED)
+    run = O.OracleRun.start(ev)
+    g.step(10, sync=True)
+    run.step(10)
+    f = g.read(("X", "U", "T", "MU", "S_DENS", "N_DENS", "NNB"))
+    aux, _ = run.observe()
+    A = O.AUX
+    assert np.array_equal(f["NNB"], aux[A["nnb"]].astype(np.int32))
+    assert relerr(f["X"], run.y[0:3]) < TOL_MIXED and relerr(f["U"], run.y[3:6]) < TOL_MIXED
+    assert relerr(f["T"], aux[A["T"]]) < TOL_MIXED
+    assert relerr(f["S_DENS"], aux[A["s"]]) < TOL_MIXED
+    if np.any(aux[A["nB"]]):
+        assert relerr(f["N_DENS"], aux[A["nB"]:A["nQ"] + 1]) < TOL_MIXED
+        assert relerr(f["MU"], aux[A["muB"]:A["muQ"] + 1]) < TOL_MIXED
+    g.free()
+
+
+def test_mixed_precision_3d_full_size_event(Bd):
+    """The 3+1D hyperbolic viscous BSQ event (about 10^6 particles) in the mixed form, one step."""
+    ev = I.viscous_bsq_3p1()
+    g = Bd.GpuEvent(ev, precision=Bd.SPH_MIXED)
+    g.step(1, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(1)
+    f = g.read(("X", "U", "T", "S_DENS", "NNB"))
+    aux, _ = run.observe()
+    A = O.AUX
+    assert np.array_equal(f["NNB"], aux[A["nnb"]].astype(np.int32))
+    assert relerr(f["U"], run.y[3:6]) < TOL_MIXED and relerr(f["T"], aux[A["T"]]) < TOL_MIXED
+    assert relerr(f["S_DENS"], aux[A["s"]]) < TOL_MIXED
+    assert g.totals()["shell_tests"] >= 0
+    g.free()
