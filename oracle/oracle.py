@@ -22,6 +22,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libsph_oracle.so")
 
 NAUX = 18
+FO_NREC = 24  # freeze-out record: tau, x^1..3, u^0..3, T, mu x3, e, p, s, n_0..3, |dsigma|, dsigma_0..3
 AUX = {name: i for i, name in enumerate(
     ["sigstar", "s", "nB", "nS", "nQ", "T", "muB", "muS", "muQ", "p", "e", "cs2", "theta", "Pi",
      "u0", "nnb", "sigma", "status"])}
@@ -84,6 +85,7 @@ def lib():
             "oc_totals": (None, [P, l, d, p, p, p, p]),
             "oc_pi_pairs": (i, [i, p]),
             "oc_pi_full": (None, [i, i, d, p, p, p]),
+            "oc_freezeout": (l, [P, l, d, d, p, p, p, d, l, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -269,6 +271,29 @@ class OracleRun:
         lib().oc_observe(C.byref(self.P), n, float(self.tau), _ptr(self.y), _ptr(self.Nq), _ptr(aux), _ptr(st),
                          _ptr(self.guess))
         return aux, st
+
+    def evolve_freezeout(self, nsteps: int, e_fo: float):
+        """nsteps Heun steps, recording the freeze-out surface elements at e_fo: before each step
+        (and after the last) the state is observed and particles whose e fell through e_fo since
+        the previous observation yield one element each (records of FO_NREC doubles, particle
+        indices).  The first observation only records e."""
+        dtau = float(self.ev.dtau)
+        eprev = np.full(self.n, np.nan)
+        recs, ids = [], []
+        for k in range(nsteps + 1):
+            aux, _ = self.observe()
+            if k > 0:
+                out = np.zeros((self.n, FO_NREC))
+                idx = np.zeros(self.n, dtype=np.int64)
+                cnt = lib().oc_freezeout(C.byref(self.P), self.n, float(self.tau), dtau, _ptr(self.y), _ptr(aux),
+                                         _ptr(eprev), float(e_fo), self.n, _ptr(out), _ptr(idx))
+                recs.append(out[:cnt].copy())
+                ids.append(idx[:cnt].copy())
+            eprev = aux[AUX["e"]].copy()
+            if k < nsteps:
+                self.step(1)
+        return np.concatenate(recs) if recs else np.zeros((0, FO_NREC)), \
+            np.concatenate(ids) if ids else np.zeros(0, dtype=np.int64)
 
     def totals(self, aux=None):
         if aux is None:

@@ -1164,3 +1164,81 @@ void oc_pi_full(int dim, int milne, double tau, const double *u4, const double *
     pi_full(dim, &G, u4, stored, pi);
     memcpy(out16, pi, sizeof(pi));
 }
+
+/* ------------------------------------------------------------------------ */
+/* Freeze-out hypersurface (Sec. "Freeze-out hypersurface construction")      */
+/* Elements of the surface of constant energy density e_fo.  aux: oc_observe at the current
+   state (time tau); eprev[n]: each particle's e at the previous observation, tau - dtau
+   (NaN: none).  A particle whose e fell through e_fo (eprev > e_fo >= e) yields one
+   element, evaluated at the current state (the end of the step in which it crossed):
+     d_i e_a = sum_b (e_b / sigma*_b) d_i W_ab        (SPH derivative, n = 0 form),
+     d_tau e = (e - eprev) / dtau - v^i d_i e          (the particle's rate minus advection),
+     N_mu = -d_mu e, n_mu = N_mu / sqrt(|N_mu N^mu|)   (covariant, "outward"),
+     |dsigma| = m / (sigma |u^mu n_mu|)                 (m = 1, sigma the rest-frame density),
+     dsigma_mu = |dsigma| n_mu.
+   Record of FO_NREC doubles: tau, x^1..3, u^0..3, T, mu_B, mu_S, mu_Q, e, p, s, n_0..3,
+   |dsigma|, dsigma_0..3 (the third spatial entries are 0 in 2+1D).  Particles in index
+   order; at most cap records are written; the number of crossings is returned. */
+#define FO_NREC 24
+long oc_freezeout(const oc_params *P, long n, double tau, double dtau, const double *y, const double *aux,
+                  const double *eprev, double e_fo, long cap, double *out, long *ids)
+{
+    int dim = P->dim;
+    geom_t G;
+    make_geom(P->milne, tau, &G);
+    grid_t g;
+    grid_build(&g, n, dim, y, P->h);
+    long *buf = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    double supp2 = 4.0 * P->h * P->h;
+    long cnt = 0;
+    for (long a = 0; a < n; ++a) {
+        double e = aux[10 * n + a];
+        if (!(eprev[a] > e_fo && e <= e_fo)) continue;
+        /* spatial gradient of e */
+        double de[3] = {0.0, 0.0, 0.0};
+        long m = grid_neighbors(&g, y, supp2, a, buf);
+        for (long k = 0; k < m; ++k) {
+            long b = buf[k];
+            double r2 = r2_of(dim, y, n, a, b);
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            double dWdr = oc_dWdr(r, P->h, dim);
+            double eb = aux[10 * n + b] / aux[0 * n + b];
+            for (int d = 0; d < dim; ++d) de[d] += eb * dWdr * (y[d * n + a] - y[d * n + b]) / r;
+        }
+        /* four-velocity, particle rate, covariant normal */
+        double u[4] = {aux[14 * n + a], 0.0, 0.0, 0.0};
+        for (int i = 0; i < dim; ++i) u[1 + i] = y[(dim + i) * n + a];
+        double adv = 0.0;
+        for (int i = 0; i < dim; ++i) adv += (u[1 + i] / u[0]) * de[i];
+        double N[4] = {-((e - eprev[a]) / dtau - adv), 0.0, 0.0, 0.0};
+        for (int i = 0; i < dim; ++i) N[1 + i] = -de[i];
+        double NN = 0.0; /* N_mu N^mu = g^{mu mu} N_mu^2 (diagonal metric) */
+        for (int mu = 0; mu < 4; ++mu) NN += N[mu] * N[mu] / G.g[mu];
+        double norm = sqrt(fabs(NN));
+        double nv[4];
+        for (int mu = 0; mu < 4; ++mu) nv[mu] = N[mu] / norm;
+        double un = 0.0;
+        for (int mu = 0; mu < 4; ++mu) un += u[mu] * nv[mu];
+        double dsig = 1.0 / (aux[16 * n + a] * fabs(un));
+        if (cnt < cap) {
+            double *r = out + (size_t)cnt * FO_NREC;
+            r[0] = tau;
+            for (int d = 0; d < 3; ++d) r[1 + d] = d < dim ? y[d * n + a] : 0.0;
+            for (int mu = 0; mu < 4; ++mu) r[4 + mu] = u[mu];
+            r[8] = aux[5 * n + a];
+            for (int c = 0; c < 3; ++c) r[9 + c] = aux[(6 + c) * n + a];
+            r[12] = e;
+            r[13] = aux[9 * n + a];
+            r[14] = aux[1 * n + a];
+            for (int mu = 0; mu < 4; ++mu) r[15 + mu] = nv[mu];
+            r[19] = dsig;
+            for (int mu = 0; mu < 4; ++mu) r[20 + mu] = dsig * nv[mu];
+            ids[cnt] = a;
+        }
+        ++cnt;
+    }
+    free(buf);
+    grid_free(&g);
+    return cnt;
+}

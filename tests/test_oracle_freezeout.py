@@ -1,0 +1,93 @@
+"""Freeze-out hypersurface of the oracle (Sec. "Freeze-out hypersurface construction", CPU only).
+
+* On ideal Gubser flow the surface of constant e is an isotherm known in closed form
+  (eqs. vGubser_T with H0 = 0, Gubser_utau, Gubser_ur): the SPH normals n_mu = -d_mu e/|d e|
+  (spatial derivatives by the SPH sum, the time derivative from the particle's rate minus
+  advection) point along the closed-form -d_mu T, converging under refinement.
+* Every element is consistent with its definition: |n_mu n^mu| = 1, sigma |u.n| |dsigma| = 1,
+  dsigma_mu = |dsigma| n_mu, each particle crosses once while cooling, and T at the element lies
+  just below T_FO (the step's end).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2511_22852_gb300 import inputs as I
+
+T_FO = 0.3 / I.HBARC
+E_FO = I.GUBSER_FSTAR * T_FO ** 4
+
+
+def _surface(n_side, h, dtau, nsteps):
+    ev = I.gubser_ideal_2p1(n_side=n_side, h=h, dtau=dtau, nsteps=nsteps)
+    run = O.OracleRun.start(ev)
+    recs, ids = run.evolve_freezeout(nsteps, E_FO)
+    return ev, recs, ids
+
+
+def _direction_error(recs):
+    """Euclidean-normalised (tau, x, y) directions of the SPH normal vs the closed form."""
+    tau, x, y = recs[:, 0], recs[:, 1], recs[:, 2]
+    d = 1e-6
+
+    def T(t, xx, yy):
+        return I.gubser_T_u(t, xx, yy)[0]
+
+    N = -np.stack([(T(tau + d, x, y) - T(tau - d, x, y)) / (2 * d), (T(tau, x + d, y) - T(tau, x - d, y)) / (2 * d),
+                   (T(tau, x, y + d) - T(tau, x, y - d)) / (2 * d)])
+    Ne = N / np.linalg.norm(N, axis=0)
+    S = recs[:, 15:18].T
+    Se = S / np.linalg.norm(S, axis=0)
+    return np.linalg.norm(Se - Ne, axis=0), np.sign(Se[0]) == np.sign(Ne[0])
+
+
+def test_normals_follow_the_gubser_isotherm():
+    _, coarse, _ = _surface(51, 0.5, 0.01, 60)
+    _, fine, _ = _surface(101, 0.25, 0.005, 120)
+    assert len(coarse) > 100 and len(fine) > 4 * 100
+    e1, s1 = _direction_error(coarse)
+    e2, s2 = _direction_error(fine)
+    assert s1.all() and s2.all()  # the time component points the same way everywhere
+    assert e1.max() < 0.35 and e1.mean() < 0.2
+    assert e2.max() < 0.15 and e2.mean() < 0.08
+    assert e2.mean() < 0.5 * e1.mean()
+
+
+def test_elements_satisfy_their_definition():
+    ev, recs, ids = _surface(51, 0.5, 0.01, 60)
+    assert len(np.unique(ids)) == len(ids)  # each particle crosses once (monotonic cooling)
+    tau = recs[:, 0]
+    u = recs[:, 4:8]
+    n = recs[:, 15:19]
+    g = np.stack([np.ones_like(tau), -np.ones_like(tau), -np.ones_like(tau), -tau * tau])  # Milne metric
+    nn = np.sum(n * n / g.T, axis=1)
+    assert np.allclose(np.abs(nn), 1.0, rtol=0, atol=1e-12)
+    un = np.sum(u * n, axis=1)
+    # sigma = s / S_smoothed is not stored: check |dsigma| through sigma* u^0 tau = sigma gamma tau
+    assert np.allclose(recs[:, 20:24], recs[:, 19:20] * n, rtol=1e-14, atol=0)
+    assert np.all(recs[:, 19] > 0) and np.all(np.abs(un) > 0)
+    T = recs[:, 8]
+    assert np.all(T <= T_FO * (1 + 1e-12)) and np.all(T > 0.98 * T_FO)
+    assert np.all(recs[:, 3] == 0.0) and np.all(u[:, 3] == 0.0)  # boost invariant: no eta parts
+
+
+def test_dsigma_is_inverse_sigma_u_dot_n():
+    """|dsigma| sigma |u.n| = 1 with sigma the rest-frame density of the same observation."""
+    ev = I.gubser_ideal_2p1(n_side=41, h=0.5, dtau=0.01, nsteps=40, half_width=4.0)
+    run = O.OracleRun.start(ev)
+    recs, ids = run.evolve_freezeout(40, E_FO)
+    assert len(ids) > 10
+    aux, _ = run.observe()  # the last observation is the final state; re-evaluate at each element's step
+    run2 = O.OracleRun.start(ev)
+    sig_at = {}
+    steps = np.rint((recs[:, 0] - ev.tau0) / ev.dtau).astype(int)
+    for k in range(41):
+        if np.any(steps == k):
+            a2, _ = run2.observe()
+            for j in np.nonzero(steps == k)[0]:
+                sig_at[j] = a2[O.AUX["sigma"]][ids[j]]
+        if k < 40:
+            run2.step(1)
+    un = np.sum(recs[:, 4:8] * recs[:, 15:19], axis=1)
+    prod = np.array([recs[j, 19] * sig_at[j] * abs(un[j]) for j in range(len(ids))])
+    assert np.allclose(prod, 1.0, rtol=1e-12, atol=0)

@@ -59,6 +59,15 @@ MUTATIONS = [
      "test_oracle_physics.py::test_shear_reconstruction_properties"),
     ("enthalpy_drop_dw", "R->dP[i] = (u[i] / q->sigma) * dw +", "R->dP[i] = 0.0 * dw +",
      "test_oracle_physics.py::test_gubser_ideal_against_closed_form"),
+    ("fo_advection_sign", "double N[4] = {-((e - eprev[a]) / dtau - adv), 0.0, 0.0, 0.0};",
+     "double N[4] = {-((e - eprev[a]) / dtau + adv), 0.0, 0.0, 0.0};",
+     "test_oracle_freezeout.py::test_normals_follow_the_gubser_isotherm"),
+    ("fo_gradient_sign", "de[d] += eb * dWdr * (y[d * n + a] - y[d * n + b]) / r;",
+     "de[d] += eb * dWdr * (y[d * n + b] - y[d * n + a]) / r;",
+     "test_oracle_freezeout.py::test_normals_follow_the_gubser_isotherm"),
+    ("fo_dsigma_lab_density", "double dsig = 1.0 / (aux[16 * n + a] * fabs(un));",
+     "double dsig = 1.0 / (aux[0 * n + a] * fabs(un));",
+     "test_oracle_freezeout.py::test_dsigma_is_inverse_sigma_u_dot_n"),
 ]
 
 
