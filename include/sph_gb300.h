@@ -233,6 +233,29 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
 sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count);
 
 /* ---------------------------------------------------------------------------
+ * Freeze-out hypersurface (Sec. "Freeze-out hypersurface construction"), dim = 2.
+ * After sph_freezeout_setup, the first stage of every step finds the particles whose energy
+ * density fell through e_fo since the previous step's first stage and records one surface
+ * element each, evaluated at the current state (the end of the step in which it crossed):
+ *   n_mu = N_mu / sqrt(|N_mu N^mu|), N_mu = -d_mu e (covariant, pointing outwards), with the
+ *   spatial derivatives by the SPH sum d_i e_a = sum_b (e_b/sigma*_b) d_i W_ab and
+ *   d_tau e = (e - e_prev)/dtau - v^i d_i e (the particle's rate minus advection);
+ *   |dsigma| = m/(sigma |u^mu n_mu|) with unit SPH mass and the rest-frame density sigma;
+ *   dsigma_mu = |dsigma| n_mu.
+ * A record holds SPH_FO_NREC doubles: tau, x^1..3, u^0..3, T, mu_B, mu_S, mu_Q, e, p, s,
+ * n_0..3, |dsigma|, dsigma_0..3 (entries of the third spatial axis are 0 in 2+1D).  The
+ * crossings of the step that ends at tau are found by the next step's first stage.
+ * Setup (again) clears the recorded elements; the first step after it only records e.
+ * Errors: SPH_ERR_ARG (dim != 2, e_fo <= 0, capacity < 1), SPH_ERR_OOM. */
+#define SPH_FO_NREC 24
+sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity);
+/* Elements recorded so far, sorted by (tau, particle id): min(count, capacity, cap) records to
+ * elems[SPH_FO_NREC * cap] and their original particle indices to ids[cap] (host buffers);
+ * *count receives the number of crossings found.  SPH_ERR_STATE if recording is off or more
+ * crossings than the capacity occurred (the surplus was dropped). */
+sph_status sph_read_freezeout(sph_event *ev, int64_t cap, double *elems, int64_t *ids, int64_t *count);
+
+/* ---------------------------------------------------------------------------
  * Densities without device allocation.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory -- a serving loop that has
  * handed all free HBM to its own pool, or code running while another thread captures a

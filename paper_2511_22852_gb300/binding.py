@@ -34,7 +34,8 @@ F = {name: 1 << i for i, name in enumerate(
 EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_event", "sph_step", "sph_read_fields",
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
-           "sph_server_stats_get", "sph_server_drain"]
+           "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout"]
+SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
 
 
@@ -122,6 +123,8 @@ def lib():
             "sph_collect": (i32, [vp, i64, C.c_uint64, C.POINTER(FieldBufs), C.POINTER(Totals)]),
             "sph_server_stats_get": (i32, [vp, C.POINTER(ServerStats)]),
             "sph_server_drain": (i32, [vp, C.c_double]),
+            "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
+            "sph_read_freezeout": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -201,6 +204,16 @@ def sph_kernel_times(h):
     _check(lib().sph_kernel_times(h, 16, names, ms.ctypes.data, nl.ctypes.data, C.byref(cnt)))
     raw = names.raw
     return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
+
+
+def sph_freezeout_setup(h, e_fo: float, capacity: int):
+    _check(lib().sph_freezeout_setup(h, float(e_fo), int(capacity)))
+
+
+def sph_read_freezeout(h, cap: int, elems, ids) -> int:
+    cnt = C.c_int64(0)
+    _check(lib().sph_read_freezeout(h, int(cap), _ptr(elems), _ptr(ids), C.byref(cnt)))
+    return cnt.value
 
 
 def sph_server_create(desc: ServerDesc, eos):
@@ -425,6 +438,18 @@ class GpuEvent:
                 setattr(b, attr, a.ctypes.data)
                 mask |= F[nm]
         sph_write_state(self.h, mask, b)
+
+    def freezeout_setup(self, e_fo: float, capacity: int):
+        sph_freezeout_setup(self.h, e_fo, capacity)
+        self._fo_cap = int(capacity)
+
+    def read_freezeout(self):
+        """(records [count][SPH_FO_NREC], original particle ids [count]) sorted by (tau, id)."""
+        cap = self._fo_cap
+        rec = np.zeros((cap, SPH_FO_NREC))
+        ids = np.zeros(cap, dtype=np.int64)
+        cnt = sph_read_freezeout(self.h, cap, rec, ids)
+        return rec[:cnt].copy(), ids[:cnt].copy()
 
     def free(self):
         if self.h is not None:

@@ -69,6 +69,12 @@ struct sph_event {
     // EoS warm start: wguess (state order, carried across stages), guess_in (this stage's
     // sorted order), wguess_obs (written by read-out evaluations, which leave wguess alone)
     double *wguess = nullptr, *guess_in = nullptr, *wguess_obs = nullptr;
+    // freeze-out surface (off until sph_freezeout_setup): e at the previous step's first stage
+    // (ping-pong, permuted with the particles) and the element buffer
+    bool fo_on = false;
+    double e_fo = 0.0;
+    double *eprev[2] = {nullptr, nullptr};
+    FoBuf fo{};
     uint32_t *status = nullptr;
     int *nnb = nullptr;
     double *wpart = nullptr;
@@ -163,10 +169,10 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_CELLS, 1, 1);
     mark(ev, G_PERMUTE, 1, 0);
     {
-        const double *src[3] = {ev->Y[0], ev->Nq[0], ev->wguess};
-        double *dst[3] = {ev->Y[1], ev->Nq[1], ev->guess_in};
-        int rows[3] = {ev->nv, 3, 4};
-        launch_permute(v, ev->cb.perm, src, dst, rows, 3, ev->id[0], ev->id[1], st);
+        const double *src[4] = {ev->Y[0], ev->Nq[0], ev->wguess, ev->eprev[0]};
+        double *dst[4] = {ev->Y[1], ev->Nq[1], ev->guess_in, ev->eprev[1]};
+        int rows[4] = {ev->nv, 3, 4, 1};
+        launch_permute(v, ev->cb.perm, src, dst, rows, ev->fo_on ? 4 : 3, ev->id[0], ev->id[1], st);
     }
     mark(ev, G_PERMUTE, 1, 1);
     mark(ev, G_DENSITY, 1, 0);
@@ -174,6 +180,8 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_DENSITY, 1, 1);
     mark(ev, G_EOS, 1, 0);
     launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
+    if (ev->fo_on)
+        launch_freezeout2(v, ev->e_fo, ev->Y[1], ev->id[1], ev->dens, ev->eosf, ev->eprev[1], ev->cb, ev->fo, st);
     mark(ev, G_EOS, 1, 1);
     mark(ev, G_GRADIENT, 1, 0);
     launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
@@ -190,10 +198,10 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_CELLS, 2, 1);
     mark(ev, G_PERMUTE, 2, 0);
     {
-        const double *src[4] = {ev->Y1[0], ev->Y[1], ev->Nq[1], ev->wguess};
-        double *dst[4] = {ev->Y1[1], ev->Y[0], ev->Nq[0], ev->guess_in};
-        int rows[4] = {ev->nv, ev->nv, 3, 4};
-        launch_permute(v, ev->cb.perm, src, dst, rows, 4, ev->id[1], ev->id[0], st);
+        const double *src[5] = {ev->Y1[0], ev->Y[1], ev->Nq[1], ev->wguess, ev->eprev[1]};
+        double *dst[5] = {ev->Y1[1], ev->Y[0], ev->Nq[0], ev->guess_in, ev->eprev[0]};
+        int rows[5] = {ev->nv, ev->nv, 3, 4, 1};
+        launch_permute(v, ev->cb.perm, src, dst, rows, ev->fo_on ? 5 : 4, ev->id[1], ev->id[0], st);
     }
     mark(ev, G_PERMUTE, 2, 1);
     mark(ev, G_DENSITY, 2, 0);
@@ -598,7 +606,7 @@ sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags)
     }
     CK(cudaGetLastError());
     ev->host_steps += nsteps;
-    ev->launches += (long long)nsteps * 2 * kKernelsPerStage;
+    ev->launches += (long long)nsteps * (2 * kKernelsPerStage + (ev->fo_on ? 1 : 0));
     ev->observed = false;
     if (flags & SPH_SYNC) {
         DevScalars hs;
@@ -735,6 +743,80 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         tot->kernel_launches = ev->launches;
     }
     return wait_stream(ev);
+}
+
+sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (ev->dim != 2) return fail(SPH_ERR_ARG, "the freeze-out surface is implemented for dim = 2");
+    if (!(e_fo > 0.0) || capacity < 1) return fail(SPH_ERR_ARG, "e_fo > 0 and capacity >= 1 required");
+    CK(cudaStreamSynchronize(ev->stream));
+    const size_t N = (size_t)(ev->n > 0 ? ev->n : 1);
+    sph_status s;
+    if (!ev->eprev[0]) {
+        for (int k = 0; k < 2; ++k) {
+            s = dalloc(ev, reinterpret_cast<void **>(&ev->eprev[k]), sizeof(double) * N);
+            if (s != SPH_OK) return s;
+        }
+        s = dalloc(ev, reinterpret_cast<void **>(&ev->fo.count), sizeof(unsigned long long));
+        if (s != SPH_OK) return s;
+    }
+    if ((unsigned long long)capacity > ev->fo.cap) {
+        s = dalloc(ev, reinterpret_cast<void **>(&ev->fo.rec), sizeof(double) * kFoRec * (size_t)capacity);
+        if (s != SPH_OK) return s;
+        s = dalloc(ev, reinterpret_cast<void **>(&ev->fo.ids), sizeof(long long) * (size_t)capacity);
+        if (s != SPH_OK) return s;
+    }
+    ev->fo.cap = (unsigned long long)capacity;
+    // NaN: no previous value, so the first step after setup only records e
+    CK(cudaMemsetAsync(ev->eprev[0], 0xFF, sizeof(double) * N, ev->stream));
+    CK(cudaMemsetAsync(ev->fo.count, 0, sizeof(unsigned long long), ev->stream));
+    CK(cudaStreamSynchronize(ev->stream));
+    ev->e_fo = e_fo;
+    ev->fo_on = true;
+    if (ev->gexec) {  // the step graph changes: capture it again
+        cudaGraphExecDestroy(ev->gexec);
+        ev->gexec = nullptr;
+    }
+    if (ev->graph) {
+        cudaGraphDestroy(ev->graph);
+        ev->graph = nullptr;
+    }
+    ev->graph_ready = false;
+    return SPH_OK;
+}
+
+sph_status sph_read_freezeout(sph_event *ev, int64_t cap, double *elems, int64_t *ids, int64_t *count)
+{
+    if (!ev || !count) return fail(SPH_ERR_ARG, "null argument");
+    *count = 0;
+    if (!ev->fo_on) return fail(SPH_ERR_STATE, "freeze-out recording is off (sph_freezeout_setup)");
+    if (cap > 0 && (!elems || !ids)) return fail(SPH_ERR_ARG, "null destination");
+    unsigned long long total = 0;
+    CK(cudaMemcpyAsync(&total, ev->fo.count, sizeof(total), cudaMemcpyDeviceToHost, ev->stream));
+    sph_status s = wait_stream(ev);
+    if (s != SPH_OK) return s;
+    *count = (int64_t)total;
+    const size_t m = (size_t)std::min<unsigned long long>(total, ev->fo.cap);
+    if (cap <= 0 || m == 0) return total > ev->fo.cap ? fail(SPH_ERR_STATE, "freeze-out buffer overflowed") : SPH_OK;
+    std::vector<double> rec(m * kFoRec);
+    std::vector<long long> idv(m);
+    CK(cudaMemcpyAsync(rec.data(), ev->fo.rec, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, ev->stream));
+    CK(cudaMemcpyAsync(idv.data(), ev->fo.ids, sizeof(long long) * m, cudaMemcpyDeviceToHost, ev->stream));
+    s = wait_stream(ev);
+    if (s != SPH_OK) return s;
+    std::vector<size_t> ord(m);
+    for (size_t k = 0; k < m; ++k) ord[k] = k;
+    std::sort(ord.begin(), ord.end(), [&](size_t p, size_t q) {
+        const double tp = rec[p * kFoRec], tq = rec[q * kFoRec];
+        return tp != tq ? tp < tq : idv[p] < idv[q];
+    });
+    const size_t w = std::min<size_t>(m, (size_t)cap);
+    for (size_t k = 0; k < w; ++k) {
+        std::memcpy(elems + k * kFoRec, rec.data() + ord[k] * kFoRec, sizeof(double) * kFoRec);
+        ids[k] = (int64_t)idv[ord[k]];
+    }
+    return total > ev->fo.cap ? fail(SPH_ERR_STATE, "freeze-out buffer overflowed") : SPH_OK;
 }
 
 sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count)

@@ -380,6 +380,18 @@ void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y
 void launch_eom2_seg(const Arena &A, int stage, int mode, const double *ys, double *yout, int grid,
                      cudaStream_t st);
 
+// freeze-out surface elements (freezeout.cu): records of kFoRec doubles
+// (tau, x^1..3, u^0..3, T, mu_B, mu_S, mu_Q, e, p, s, n_0..3, |dsigma|, dsigma_0..3)
+constexpr int kFoRec = 24;
+struct FoBuf {
+    double *rec;
+    long long *ids;
+    unsigned long long *count;
+    unsigned long long cap;
+};
+void launch_freezeout2(const EvView &v, double e_fo, const double *y, const int *id, const double *dens,
+                       const double *eosf, double *eprev, CellBufs cb, FoBuf fo, cudaStream_t st);
+
 // sets the message returned by sph_last_error() for the calling thread
 void set_last_error(const char *msg);
 

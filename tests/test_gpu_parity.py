@@ -502,3 +502,45 @@ def test_mixed_precision_3d_full_size_event(Bd):
     assert relerr(f["S_DENS"], aux[A["s"]]) < TOL_MIXED
     assert g.totals()["shell_tests"] >= 0
     g.free()
+
+
+def _fo_compare(recs, ids, orecs, oids):
+    assert np.array_equal(ids, oids)
+    # ordering in both: (tau, id); state and thermodynamics columns to the step tolerance
+    for c in list(range(0, 15)):
+        assert relerr(recs[:, c], orecs[:, c]) < TOL_STEP, c
+    # the normal and the element: well conditioned away from light-like normals
+    nn = np.abs(orecs[:, 15] ** 2 - orecs[:, 16] ** 2 - orecs[:, 17] ** 2)
+    ok = np.abs(orecs[:, 15]) > 0  # every element
+    N = recs[:, 15:18] / np.linalg.norm(recs[:, 15:18], axis=1)[:, None]
+    ON = orecs[:, 15:18] / np.linalg.norm(orecs[:, 15:18], axis=1)[:, None]
+    assert np.max(np.abs(N - ON)[ok]) < 1e-9
+    good = nn > 1e-3
+    assert relerr(recs[good, 19], orecs[good, 19]) < 1e-8
+
+
+@pytest.mark.parametrize("case", ["gubser", "gubser_viscous", "blob_causal"])
+def test_freezeout_surface_matches_oracle(Bd, case):
+    """Freeze-out surface elements at constant e: the same particles cross in the same steps,
+    with the oracle's normals and element sizes."""
+    ev = CASES[case]()
+    run = O.OracleRun.start(ev)
+    aux0, _ = run.observe()
+    e0 = aux0[O.AUX["e"]]
+    # a surface that sweeps through the fluid as it cools, in the middle of a clear gap between
+    # particles' values (mirror particles of a symmetric lattice differ by rounding only, and a
+    # particle within rounding of e_fo would cross or not by rounding)
+    se = np.sort(e0)
+    k = int(0.6 * len(se))
+    while se[k + 1] - se[k] < 1e-6 * se[k]:
+        k += 1
+    e_fo = 0.5 * float(se[k] + se[k + 1])
+    nsteps = 40
+    orecs, oids = run.evolve_freezeout(nsteps, e_fo)
+    assert len(oids) > 20
+    g = Bd.GpuEvent(ev)
+    g.freezeout_setup(e_fo, 100000)
+    g.step(nsteps + 1, sync=True)  # crossings of step k are found by step k + 1's first stage
+    recs, ids = g.read_freezeout()
+    _fo_compare(recs, ids, orecs, oids)
+    g.free()
