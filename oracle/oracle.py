@@ -52,6 +52,7 @@ class Params(C.Structure):
         ("zeta_w_GeV", C.c_double), ("tau_pi_coef", C.c_double), ("tau_Pi_ratio", C.c_double),
         ("cs2_cap", C.c_double),
         ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("pad", C.c_int),
+        ("ntrack", C.c_int), ("pad2", C.c_int), ("tracks", C.c_void_p), ("track_sigma", C.c_double),
     ]
 
 
@@ -129,6 +130,13 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
     P.eta_over_s, P.zeta_peak, P.zeta_T_GeV, P.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
     P.tau_pi_coef, P.tau_Pi_ratio, P.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
     P.newton_tol, P.newton_maxit = newton_tol, newton_maxit
+    jets = getattr(ev, "jets", None)
+    if jets is not None and len(jets.tracks):
+        if ev.milne:
+            raise ValueError("jet sources are defined in Cartesian coordinates")
+        tr = _f64(jets.tracks).reshape(-1, 8)
+        keep.append(tr)
+        P.ntrack, P.tracks, P.track_sigma = tr.shape[0], tr.ctypes.data, float(jets.sigma)
     return P, keep
 
 

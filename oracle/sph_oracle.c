@@ -69,6 +69,12 @@ typedef struct {
     double newton_tol;
     int newton_maxit;
     int pad;
+    /* energy-momentum source I^nu of straight jet tracks (Cartesian coordinates only):
+       tracks[8 k ..]: x0, y0, z0, direction n (unit), start time t0, dE/dx (fm^-2) */
+    int ntrack;
+    int pad2;
+    const double *tracks;
+    double track_sigma;
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -710,6 +716,35 @@ static void pi_full(int dim, const geom_t *G, const double *u, const double *sto
 }
 
 /* ------------------------------------------------------------------------ */
+/* source term I^nu of jet tracks (eq. conservation_source with I^nu != 0)   */
+/* ------------------------------------------------------------------------ */
+/* Each track moves at the speed of light from x0 along n from time t0 and deposits energy
+   dE/dx per unit path length, spread over a normalised 3D Gaussian of width sigma around its
+   current position, with the momentum of light moving along n:
+     I^nu(t, x) = sum_k dEdx_k G_sigma(x - x0_k - n_k (t - t0_k)) (1, n_k)   for t >= t0_k.
+   x has dim components (z = 0 in 2D); Cartesian coordinates, I^nu contravariant. */
+static void jet_source(const oc_params *P, int dim, double t, const double *x, double *I)
+{
+    for (int mu = 0; mu < 4; ++mu) I[mu] = 0.0;
+    const double sg = P->track_sigma;
+    const double norm = 1.0 / (pow(2.0 * M_PI, 1.5) * sg * sg * sg);
+    for (int k = 0; k < P->ntrack; ++k) {
+        const double *tr = P->tracks + 8 * k;
+        double dt = t - tr[6];
+        if (dt < 0.0) continue;
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double xd = d < dim ? x[d] : 0.0;
+            double c = xd - (tr[d] + tr[3 + d] * dt);
+            r2 += c * c;
+        }
+        double dep = tr[7] * norm * exp(-r2 / (2.0 * sg * sg));
+        I[0] += dep;
+        for (int d = 0; d < 3; ++d) I[1 + d] += dep * tr[3 + d];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* equations of motion at one particle                                       */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -720,6 +755,7 @@ typedef struct {
     double Pi, Bv;
     double pi[4][4], Pv[4][4]; /* pi^{mu nu} and pi^{mu nu}/sigma */
     double eta, zeta, taupi, tauPi;
+    double uI; /* u_nu I^nu: energy deposited in the local rest frame per unit time and volume */
 } ppart;
 
 typedef struct {
@@ -785,7 +821,7 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
         double pisig = 0.0;
         for (int m = 0; m < 4; ++m)
             for (int nu = 0; nu < 4; ++nu) pisig += q->pi[m][nu] * G->g[m] * G->g[nu] * sig[m][nu];
-        R->dS = (-q->Pi * theta + pisig) / (u0 * q->sigma * q->T);
+        R->dS = (-q->Pi * theta + pisig + q->uI) / (u0 * q->sigma * q->T);
         R->dBv = -(q->Pi + q->zeta * theta) / (q->tauPi * u0 * q->sigma);
         double alow[4];
         for (int al = 0; al < 4; ++al) alow[al] = G->g[al] * Du[al];
@@ -805,7 +841,7 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
                 R->dPv[i][j] = dpi / q->sigma - q->pi[i][j] * dsig / (q->sigma * q->sigma);
             }
     } else {
-        R->dS = 0.0;
+        R->dS = q->uI / (u0 * q->sigma * q->T);
         R->dBv = 0.0;
     }
     double ds = q->sigma * R->dS + (q->s / q->sigma) * dsig;
@@ -1024,6 +1060,14 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
             for (int m = 0; m < 4; ++m)
                 for (int l = 0; l < 4; ++l) src += G.G[1 + i][m][l] * Tfull[16 * a + 4 * m + l];
             F[1 + i] = grad[(dim * dim + i) * n + a] - G.sqrtg * src / aux[0 * n + a];
+        }
+        /* jet source: dP^i/dx0 gains sqrt(-g) I^i / sigma*, dS/dx0 gains u_nu I^nu / (u^0 sigma T) */
+        if (P->ntrack > 0) {
+            double xa[3] = {0, 0, 0}, I[4];
+            for (int d = 0; d < dim; ++d) xa[d] = y[d * n + a];
+            jet_source(P, dim, tau, xa, I);
+            for (int i = 0; i < dim; ++i) F[1 + i] += G.sqrtg * I[1 + i] / aux[0 * n + a];
+            for (int mu = 0; mu < 4; ++mu) q.uI += G.g[mu] * q.u[mu] * I[mu];
         }
         /* M_ij = dP^i(e_j) - dP^i(0), c^i = dP^i(0); solve M a = F - c */
         double zero[4] = {0, 0, 0, 0};

@@ -99,6 +99,15 @@ class Transport:
 
 
 @dataclass
+class JetTracks:
+    """Straight jet tracks moving at the speed of light, each depositing energy dE/dx per unit
+    path length (spread over a Gaussian of width sigma) into the fluid: rows
+    (x0, y0, z0, n_x, n_y, n_z, t0, dE/dx [fm^-2]) in Cartesian coordinates."""
+    tracks: np.ndarray
+    sigma: float
+
+
+@dataclass
 class Event:
     """One event: SoA particle arrays plus run parameters."""
     name: str
@@ -118,6 +127,7 @@ class Event:
     table: EoSTable | None
     transport: Transport
     meta: dict = field(default_factory=dict)
+    jets: JetTracks | None = None
 
     @property
     def n(self) -> int:
@@ -388,3 +398,31 @@ def viscous_bsq_3p1(dx=0.124, deta=0.1, R=7.0, n_hot=200, sigma_hot=0.4, eta_sig
                  transport=Transport(viscous=True, eta_over_s=0.08, zeta_peak=0.05, zeta_T_GeV=0.155,
                                      zeta_w_GeV=0.02),
                  meta={"dx": dx, "deta": deta})
+
+
+def jet_tracks(n_tracks=10, R=7.0, dEdx_GeV_per_fm=5.0, sigma=0.3, t0=0.0, z_half=0.0, seed=5) -> JetTracks:
+    """Seeded straight tracks: origins uniform in the disc of radius R (z uniform in +-z_half),
+    isotropic directions, all starting at t0, depositing dEdx (GeV/fm, stored in fm^-2)."""
+    u = uniform01(seed, 5 * n_tracks).reshape(5, n_tracks)
+    rr = R * np.sqrt(u[0])
+    ph = 2.0 * math.pi * u[1]
+    z0 = z_half * (2.0 * u[2] - 1.0)
+    cth = 2.0 * u[3] - 1.0
+    sth = np.sqrt(np.maximum(0.0, 1.0 - cth * cth))
+    ps = 2.0 * math.pi * u[4]
+    tr = np.stack([rr * np.cos(ph), rr * np.sin(ph), z0, sth * np.cos(ps), sth * np.sin(ps), cth,
+                   np.full(n_tracks, float(t0)), np.full(n_tracks, dEdx_GeV_per_fm / HBARC)], axis=1)
+    return JetTracks(tracks=np.ascontiguousarray(tr), sigma=float(sigma))
+
+
+def uniform_box_3d(T_GeV=0.3, half_widths=(1.2, 1.2, 1.2), spacing=0.12, h=0.3, t0=1.0, dtau=0.005,
+                   nsteps=10, viscous=False, jets: JetTracks | None = None) -> Event:
+    """A uniform fluid at rest in a Cartesian box (the test medium of the source terms)."""
+    x = lattice_3d(half_widths, (spacing, spacing, spacing))
+    n = x.shape[1]
+    _, s, _ = _analytic_p_s_n(CAUSAL_EOS, np.full(n, T_GeV / HBARC), np.zeros((3, n)))
+    return Event(name="uniform_box_3d", dim=3, milne=False, h=h, tau0=t0, dtau=dtau, nsteps=nsteps, x=x,
+                 u=np.zeros((3, n)), S=s * spacing ** 3, Nq=np.zeros((3, n)), Bv=np.zeros(n),
+                 Pv=np.zeros((5, n)), eos=CAUSAL_EOS, table=None,
+                 transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0),
+                 meta={"dx": spacing}, jets=jets)

@@ -42,7 +42,7 @@ MUTATIONS = [
      "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
     ("shear_drop_theta_term", " - 4.0 / 3.0 * q->taupi * q->pi[i][j] * theta) / q->taupi;", ") / q->taupi;",
      "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
-    ("entropy_drop_bulk", "R->dS = (-q->Pi * theta + pisig)", "R->dS = (pisig)",
+    ("entropy_drop_bulk", "R->dS = (-q->Pi * theta + pisig + q->uI)", "R->dS = (pisig + q->uI)",
      "test_oracle_physics.py::test_bjorken_viscous_against_ode"),
     ("shear_drop_accel_coupling", "double dpi = (rhs - chr - coup) / u0;", "double dpi = (rhs - chr) / u0;",
      "test_oracle_physics.py::test_viscous_gubser_against_ode"),
@@ -68,6 +68,12 @@ MUTATIONS = [
     ("fo_dsigma_lab_density", "double dsig = 1.0 / (aux[16 * n + a] * fabs(un));",
      "double dsig = 1.0 / (aux[0 * n + a] * fabs(un));",
      "test_oracle_freezeout.py::test_dsigma_is_inverse_sigma_u_dot_n"),
+    ("src_drop_momentum", "for (int i = 0; i < dim; ++i) F[1 + i] += G.sqrtg * I[1 + i] / aux[0 * n + a];", "",
+     "test_oracle_sources.py::test_track_deposits_its_energy_and_momentum"),
+    ("src_drop_heat", "for (int mu = 0; mu < 4; ++mu) q.uI += G.g[mu] * q.u[mu] * I[mu];", "",
+     "test_oracle_sources.py::test_track_deposits_its_energy_and_momentum"),
+    ("src_gaussian_norm", "pow(2.0 * M_PI, 1.5)", "pow(M_PI, 1.5)",
+     "test_oracle_sources.py::test_track_deposits_its_energy_and_momentum"),
 ]
 
 
