@@ -233,6 +233,18 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
 sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count);
 
 /* ---------------------------------------------------------------------------
+ * Energy-momentum source of jet tracks (eq. conservation_source with I^nu != 0, Sec.
+ * "Equations of motion"; Cartesian events).  Track k (tracks[8 k ..] = x0, y0, z0, n_x, n_y,
+ * n_z, t0, dE/dx, host memory, n a unit vector, dE/dx in fm^-2) moves at the speed of light
+ * from x0 along n from time t0 and deposits dE/dx per unit path length into a normalised
+ * Gaussian of width sigma (fm) around its current position, with the momentum of light moving
+ * along n: I^nu(t, x) = sum_k dE/dx_k G_sigma(x - x0_k - n_k (t - t0_k)) (1, n_k) for t >= t0_k
+ * (z = 0 for dim = 2).  In the equations of motion dP^i/dt gains I^i/sigma* and dS/dt gains
+ * u_nu I^nu / (u^0 sigma T).  ntrack = 0 removes the source.  Errors: SPH_ERR_ARG (Milne
+ * coordinates, ntrack outside 0..4096, sigma <= 0, non-finite parameters), SPH_ERR_OOM. */
+sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, double sigma);
+
+/* ---------------------------------------------------------------------------
  * Freeze-out hypersurface (Sec. "Freeze-out hypersurface construction"), dim = 2.
  * After sph_freezeout_setup, the first stage of every step finds the particles whose energy
  * density fell through e_fo since the previous step's first stage and records one surface

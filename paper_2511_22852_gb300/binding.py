@@ -34,7 +34,8 @@ F = {name: 1 << i for i, name in enumerate(
 EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_event", "sph_step", "sph_read_fields",
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
-           "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout"]
+           "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
+           "sph_set_jets"]
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
 
@@ -124,6 +125,7 @@ def lib():
             "sph_server_stats_get": (i32, [vp, C.POINTER(ServerStats)]),
             "sph_server_drain": (i32, [vp, C.c_double]),
             "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
+            "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
             "sph_read_freezeout": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
@@ -204,6 +206,11 @@ def sph_kernel_times(h):
     _check(lib().sph_kernel_times(h, 16, names, ms.ctypes.data, nl.ctypes.data, C.byref(cnt)))
     raw = names.raw
     return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
+
+
+def sph_set_jets(h, tracks, sigma: float):
+    tr = _f64(tracks).reshape(-1, 8) if tracks is not None else np.zeros((0, 8))
+    _check(lib().sph_set_jets(h, int(tr.shape[0]), _ptr(tr) if tr.size else None, float(sigma)))
 
 
 def sph_freezeout_setup(h, e_fo: float, capacity: int):
@@ -382,6 +389,9 @@ class GpuEvent:
         d.profile = int(profile)
         d.precision = int(precision)
         self.h = sph_init_event(d, self.eos)
+        jets = getattr(ev, "jets", None)
+        if jets is not None and len(jets.tracks):
+            sph_set_jets(self.h, jets.tracks, jets.sigma)
 
     def step(self, nsteps: int, sync: bool = False):
         sph_step(self.h, nsteps, SPH_SYNC if sync else 0)

@@ -58,6 +58,9 @@ struct sph_event {
     std::vector<uint32_t> spread_host;
     uint32_t *spread = nullptr;     // 3D: generalized Morton spread tables (3 x 1024)
     double h = 0.3, dtau = 0.01, tau0 = 0.0;
+    int ntrack = 0;                 // jet tracks (sph_set_jets): device copy and Gaussian constants
+    double *d_tracks = nullptr;
+    double track_norm = 0.0, track_i2s2 = 0.0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     DevScalars *sc = nullptr;
@@ -136,6 +139,10 @@ static EvView make_view(const sph_event *ev)
     v.sc = ev->sc;
     v.eos = ev->eos->dev;
     v.tr = ev->tr;
+    v.ntrack = ev->ntrack;
+    v.tracks = ev->d_tracks;
+    v.track_norm = ev->track_norm;
+    v.track_i2s2 = ev->track_i2s2;
     return v;
 }
 
@@ -743,6 +750,36 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         tot->kernel_launches = ev->launches;
     }
     return wait_stream(ev);
+}
+
+sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, double sigma)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (ntrack < 0 || ntrack > 4096) return fail(SPH_ERR_ARG, "ntrack must be in 0..4096");
+    if (ntrack > 0 && (!tracks || !(sigma > 0.0))) return fail(SPH_ERR_ARG, "tracks and sigma > 0 required");
+    if (ntrack > 0 && ev->milne) return fail(SPH_ERR_ARG, "jet sources are defined in Cartesian coordinates");
+    for (int64_t k = 0; k < 8 * ntrack; ++k)
+        if (!std::isfinite(tracks[k])) return fail(SPH_ERR_ARG, "non-finite track parameter");
+    CK(cudaStreamSynchronize(ev->stream));
+    if (ntrack > ev->ntrack || !ev->d_tracks) {
+        sph_status s = dalloc(ev, reinterpret_cast<void **>(&ev->d_tracks), sizeof(double) * 8 * (size_t)(ntrack > 0 ? ntrack : 1));
+        if (s != SPH_OK) return s;
+    }
+    if (ntrack > 0) CK(cudaMemcpy(ev->d_tracks, tracks, sizeof(double) * 8 * (size_t)ntrack, cudaMemcpyHostToDevice));
+    ev->ntrack = (int)ntrack;
+    ev->track_norm = ntrack > 0 ? 1.0 / (std::pow(2.0 * kPi, 1.5) * sigma * sigma * sigma) : 0.0;
+    ev->track_i2s2 = ntrack > 0 ? 1.0 / (2.0 * sigma * sigma) : 0.0;
+    if (ev->gexec) {  // the parameters are part of the captured step: capture it again
+        cudaGraphExecDestroy(ev->gexec);
+        ev->gexec = nullptr;
+    }
+    if (ev->graph) {
+        cudaGraphDestroy(ev->graph);
+        ev->graph = nullptr;
+    }
+    ev->graph_ready = false;
+    ev->observed = false;
+    return SPH_OK;
 }
 
 sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity)

@@ -217,6 +217,14 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
         dPxy = isg * dpxy - (pxy * isg2) * dsg;
         dPyy = isg * dpyy - (pyy * isg2) * dsg;
     }
+    if (v.ntrack > 0) {  // jet tracks (Cartesian): dP^i/dt gains I^i/sigma*, dS/dt gains u.I/(u^0 sigma T)
+        double I[4];
+        jet_deposit(v, tau, ys[a], ys[n + a], 0.0, I);
+        Fx += I[1] / sig_star;
+        Fy += I[2] / sig_star;
+        const double uI = g * I[0] - ux * I[1] - uy * I[2];
+        dS = dS + aff((ig * isg / T) * uI);
+    }
     Aff ds = sigma * dS + (s * isg) * dsg;
     Aff dPi = sigma * dBv + Bv * dsg;
     Aff dw = (T + ps) * ds + (((mu0 + pn0) * nq0 + (mu1 + pn1) * nq1 + (mu2 + pn2) * nq2) * isg) * dsg + dPi;

@@ -80,7 +80,32 @@ struct EvView {
     DevScalars *sc;
     EosDev eos;
     TransportDev tr;
+    // energy-momentum source of jet tracks (Cartesian events; ntrack = 0: none): tracks[8 k ..]
+    // = x0, y0, z0, n_x, n_y, n_z, t0, dE/dx; the Gaussian's 1/((2 pi)^{3/2} sigma^3), 1/(2 sigma^2)
+    int ntrack;
+    const double *tracks;
+    double track_norm, track_i2s2;
 };
+
+// I^nu of the jet tracks at time t and position (x, y, z): every track moves at the speed of
+// light from x0 along n from t0 and deposits dE/dx per unit path length into a normalised
+// Gaussian around its current position, with the momentum of light moving along n
+// (eq. conservation_source with I^nu != 0)
+__device__ __forceinline__ void jet_deposit(const EvView &v, double t, double x, double y, double z, double I[4])
+{
+    I[0] = I[1] = I[2] = I[3] = 0.0;
+    for (int k = 0; k < v.ntrack; ++k) {
+        const double *tr = v.tracks + 8 * k;
+        const double dt = t - tr[6];
+        if (dt < 0.0) continue;
+        const double cx = x - (tr[0] + tr[3] * dt), cy = y - (tr[1] + tr[4] * dt), cz = z - (tr[2] + tr[5] * dt);
+        const double dep = tr[7] * v.track_norm * exp(-(cx * cx + cy * cy + cz * cz) * v.track_i2s2);
+        I[0] += dep;
+        I[1] += dep * tr[3];
+        I[2] += dep * tr[4];
+        I[3] += dep * tr[5];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // order-preserving map of doubles to signed 64-bit integers (for atomicMin)

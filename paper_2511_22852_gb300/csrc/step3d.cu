@@ -525,6 +525,12 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
                 dPv[j][i] = x;
             }
     }
+    double Isrc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (v.ntrack > 0) {  // jet tracks (Cartesian): dP^i/dt gains I^i/sigma*, dS/dt gains u.I/(u^0 sigma T)
+        jet_deposit(v, G.tau, ys[a], ys[n + a], ys[2 * n + a], Isrc);
+        const double uI = u[0] * Isrc[0] - u[1] * Isrc[1] - u[2] * Isrc[2] - u[3] * Isrc[3];
+        dS = dS + k3((ig * isg / T) * uI);
+    }
     const A3 ds = sigma * dS + (s * isg) * dsg;
     const A3 dPi = sigma * dBv + Bv * dsg;
     const A3 dw = (T + ps) * ds + (((mu[0] + pn[0]) * nq[0] + (mu[1] + pn[1]) * nq[1] + (mu[2] + pn[2]) * nq[2]) * isg) * dsg + dPi;
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
                     src += gml * (e * u[m] * u[l] - (p + Pi) * Delta + pi[m][l]);
                 }
             }
-        F[i - 1] = gout[(size_t)(9 + i - 1) * n + a] - G.sqrtg * src / sig_star;
+        F[i - 1] = gout[(size_t)(9 + i - 1) * n + a] - G.sqrtg * src / sig_star + G.sqrtg * Isrc[i] / sig_star;
         M[i - 1] = dP;
         cvec[i - 1] = dP.c;
     }

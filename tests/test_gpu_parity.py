@@ -49,10 +49,19 @@ CASES = {
     "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
     "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2)),
 }
+def _blob3_jets():
+    ev = I.smooth_blob_3d(milne=False, flow=0.3, eos=I.CAUSAL_EOS)
+    ev.jets = I.jet_tracks(n_tracks=3, R=1.0, t0=ev.tau0, z_half=0.5, seed=7)
+    return ev
+
+
 CASES3 = {
     "blob3_milne": lambda: I.smooth_blob_3d(milne=True, flow=0.3),
     "blob3_cart": lambda: I.smooth_blob_3d(milne=False, flow=0.3, eos=I.CAUSAL_EOS),
     "bjorken3": lambda: I.bjorken_lattice_3p1(),
+    "box_jet": lambda: I.uniform_box_3d(
+        jets=I.JetTracks(tracks=np.array([[-0.6, 0.1, -0.05, 1.0, 0.0, 0.0, 1.0, 5.0 / I.HBARC]]), sigma=0.3)),
+    "blob3_cart_jets": _blob3_jets,
 }
 
 
