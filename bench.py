@@ -282,6 +282,33 @@ def bench_3p1d(Bd, I, steps: int = 3):
     return out
 
 
+def bench_stress(Bd, I, steps: int = 3):
+    """The stress configuration: 3+1D Cartesian viscous BSQ event with 10 jet tracks, about
+    8 10^6 particles, 128 x 64^3 EoS table; device ms per Heun step of the FP64 form next to the
+    mixed form (CUDA events on the event's stream after one untimed step)."""
+    import torch
+    ev = I.stress_cartesian_3d()
+    out = {"workload": f"3+1D Cartesian viscous BSQ event with 10 jet tracks (5 GeV/fm, sigma 0.3 fm), "
+                       f"{ev.n} particles, spacing {ev.meta['dx']:.4f} fm, h = 0.15 fm, dt = 0.005 fm, "
+                       f"128x64^3 EoS table", "steps": steps}
+    for name, prec in (("fp64", Bd.SPH_FP64), ("mixed", Bd.SPH_MIXED)):
+        st = torch.cuda.Stream()
+        g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream, precision=prec)
+        g.step(1, sync=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            g.step(steps)
+            e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": ev.n / (ms / 1e3),
+                     "status_or": g.totals()["status_or"]}
+        g.free()
+    out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -444,6 +471,7 @@ def run_ours(args):
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
         if not args.no_3d:
             out["config_3p1d"] = bench_3p1d(Bd, I)
+            out["config_stress"] = bench_stress(Bd, I)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ev)
         print(json.dumps(out), flush=True)

@@ -426,3 +426,47 @@ def uniform_box_3d(T_GeV=0.3, half_widths=(1.2, 1.2, 1.2), spacing=0.12, h=0.3, 
                  Pv=np.zeros((5, n)), eos=CAUSAL_EOS, table=None,
                  transport=Transport(viscous=viscous, eta_over_s=0.08 if viscous else 0.0),
                  meta={"dx": spacing}, jets=jets)
+
+
+def stress_cartesian_3d(n_target=8_000_000, R=7.0, z_sigma=1.5, z_max=5.0, h=0.15, n_hot=200, sigma_hot=0.4,
+                        T_max_GeV=0.5, charge_frac=0.1, t0=0.6, dtau=0.005, n_tracks=10, seed_hot=1,
+                        seed_charge=2, seed_tracks=5, table_shape=(128, 64), with_table=True) -> Event:
+    """Config: 3+1D Cartesian (t, x, y, z) viscous BSQ event with jet tracks -- the transverse
+    hotspot profile of the 2+1D event times exp(-z^2/(2 z_sigma^2)) for |z| <= z_max on a cubic
+    lattice whose spacing gives about n_target particles (0.0577 fm for 8 10^6), h = 0.15 fm
+    (about 600 neighbours, as in the 3+1D Milne event), 10 seeded tracks (origins in the disc,
+    |z0| <= 1 fm, isotropic directions) depositing 5 GeV/fm into Gaussians of width 0.3 fm from
+    t0, and a 128 x 64^3 EoS table."""
+    dx = (math.pi * R * R * 2.0 * z_max / n_target) ** (1.0 / 3.0)
+    m = int(math.ceil(R / dx)) + 1
+    g = dx * np.arange(-m, m + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    keep = (X * X + Y * Y) <= R * R
+    xt, yt = X[keep], Y[keep]
+    kz = int(math.floor(z_max / dx))
+    zs = dx * np.arange(-kz, kz + 1)
+    u = uniform01(seed_hot, 2 * n_hot)
+    rc = R * np.sqrt(u[:n_hot])
+    ph = 2.0 * math.pi * u[n_hot:]
+    cx, cy = rc * np.cos(ph), rc * np.sin(ph)
+    s_t = np.zeros_like(xt)
+    for k in range(n_hot):
+        s_t += np.exp(-((xt - cx[k]) ** 2 + (yt - cy[k]) ** 2) / (2.0 * sigma_hot ** 2))
+    _, s_max, _ = _analytic_p_s_n(BJ_EOS, np.array(T_max_GeV / HBARC), np.zeros(3))
+    s_t *= float(s_max) / s_t.max()
+    nt, nz = xt.size, zs.size
+    x = np.tile(xt, nz)
+    y = np.tile(yt, nz)
+    z = np.repeat(zs, nt)
+    s = np.tile(s_t, nz) * np.exp(-z ** 2 / (2.0 * z_sigma ** 2))
+    n = x.size
+    eps = charge_frac * (2.0 * uniform01(seed_charge, 3 * n).reshape(3, n) - 1.0)
+    vol = dx ** 3
+    table = synthetic_eos_table(BJ_EOS, nT=table_shape[0], nmu=table_shape[1]) if with_table else None
+    return Event(name="stress_cartesian_3d", dim=3, milne=False, h=h, tau0=t0, dtau=dtau, nsteps=5,
+                 x=np.stack([x, y, z]), u=np.zeros((3, n)), S=s * vol, Nq=eps * (s * vol)[None, :],
+                 Bv=np.zeros(n), Pv=np.zeros((5, n)), eos=BJ_EOS, table=table,
+                 transport=Transport(viscous=True, eta_over_s=0.08, zeta_peak=0.05, zeta_T_GeV=0.155,
+                                     zeta_w_GeV=0.02),
+                 meta={"dx": dx},
+                 jets=jet_tracks(n_tracks=n_tracks, R=R, t0=t0, z_half=1.0, seed=seed_tracks))

@@ -553,3 +553,23 @@ def test_freezeout_surface_matches_oracle(Bd, case):
     recs, ids = g.read_freezeout()
     _fo_compare(recs, ids, orecs, oids)
     g.free()
+
+
+def test_stress_event_fp64_and_mixed(Bd):
+    """The stress configuration at full size (about 8 10^6 particles, Cartesian 3+1D, 10 jet
+    tracks, 128 x 64^3 table), one Heun step in each form: the same neighbour counts, T and u
+    within 1e-5 of each other, and no particle without an EoS solution."""
+    ev = I.stress_cartesian_3d()
+    assert ev.n > 7_000_000
+    out = {}
+    for prec in (Bd.SPH_FP64, Bd.SPH_MIXED):
+        g = Bd.GpuEvent(ev, precision=prec)
+        g.step(1, sync=True)
+        out[prec] = g.read(("U", "T", "NNB", "STATUS"))
+        g.free()
+    a, b = out[Bd.SPH_FP64], out[Bd.SPH_MIXED]
+    assert np.array_equal(a["NNB"], b["NNB"])
+    assert relerr(b["T"], a["T"]) < TOL_MIXED and relerr(b["U"], a["U"]) < TOL_MIXED
+    bad = Bd.PST_NOCONV | Bd.PST_NONFINITE
+    assert not np.any(a["STATUS"] & bad) and not np.any(b["STATUS"] & bad)
+    assert np.max(np.abs(a["U"])) > 0  # the jets and pressure gradients moved the fluid
