@@ -43,6 +43,9 @@ FLOPS_PER_PAIR = {"density": 22.0, "gradient": 32.0}
 FLOPS_EOS = (460.0, 64.0, 26.0)
 # FP64 vector peak of GB300 (nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock)
 FP64_PEAK_GFLOPS = 1250.0
+# DRAM bytes (read + write) per launch of the FP64 40k-event kernels, from one ncu capture of
+# the current kernels (profiles/ncu_fp64_kernels_viscous_bsq_40k.md); None once a kernel changes
+DRAM_BYTES_PER_LAUNCH = {"gradient": 2.922e6, "density": 2.917e6, "eos": 7.291e6, "eom": 13.04e6}
 
 
 def dist_env():
@@ -428,7 +431,8 @@ def run_ours(args):
             ms = times[k][0]
             achieved = flops[k] / (ms / 1e3) / 1e9
             rooflines[k] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": k,
+                            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(k),
+                            "kernel": k,
                             "peak_source": "nominal FP64 vector rate of GB300 (1.25 TFLOP/s at 2070 MHz)",
                             "avg_launch_ms": ms / times[k][1], "flops_per_launch": flops[k] / times[k][1]}
         rooflines["eos"]["work_per_launch"] = {"table_evals": ew[0] / times["eos"][1], "solves": ew[1] / times["eos"][1],
