@@ -314,6 +314,8 @@ typedef struct {
     void *stream;          /* cudaStream_t of all server work, NULL: library-created */
     int32_t polish;        /* 1: a Newton polishing step after convergence, as the plain form */
     int32_t reserved;
+    double newton_tol;     /* EoS Newton tolerance on max |residual|/s (<= 0: 1e-10; the plain form
+                              uses the EoS handle's, 1e-12 by default) */
 } sph_server_desc;
 
 #define SPH_TICKET_QUEUED 0

@@ -141,11 +141,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
 // of the gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{tau i},
 // and u^j / sigma*; returns the particle's longitudinal work rate (p + Pi + tau^2 pi^{eta eta}) / sigma*.
 // Rows are n apart; the EoS work done is added to w.
+// gprev (may be NULL): an earlier table solution, one step before guess_in; when both are table
+// solutions the guess is extrapolated linearly, 2 guess_in - gprev (kept if inside the table)
 __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E, int stage, size_t n, size_t a,
                                                 const double *__restrict__ y, double *__restrict__ dens,
                                                 double *__restrict__ eos, double *__restrict__ gin,
                                                 uint32_t *__restrict__ status, const double *__restrict__ guess_in,
-                                                double *__restrict__ guess_out, EosWork &w)
+                                                double *__restrict__ guess_out, EosWork &w,
+                                                const double *__restrict__ gprev = nullptr)
 {
     double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
     double sqrtg = v.milne ? tau : 1.0;
@@ -159,6 +162,14 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     double gs[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
+    if (gprev && gs[0] > 0.0 && gprev[a] > 0.0) {
+        double ge[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ge[k] = 2.0 * gs[k] - gprev[k * n + a];
+        if (inside_table(E, ge))
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gs[k] = ge[k];
+    }
     bool used = false;
     EosOut o = eos_invert(E, v.tr.cs2_cap, s, nq, gs, used, w);
     guess_out[a] = used ? o.T : 0.0;
@@ -253,8 +264,18 @@ __global__ void __launch_bounds__(64, 6) k_eos2_seg(Arena A, EosDev E, int stage
         double wc = 0.0;
         EosWork w = {0u, 0u, 0u};
         if (a - sl.off < sl.n) {
+            // stage 2 starts from the stage-1 solutions of this and the previous step,
+            // extrapolated to the later time; then keeps this step's for the next
+            const double *gp = stage == 2 ? A.xs1[0] : nullptr;
+            double keep[4];
+            if (stage == 2)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) keep[k] = A.guess_in[k * P + a];
             wc = eos2_particle(A.segv[s], E, stage, P, (size_t)a, y, A.dens, A.eosf, A.gin, A.status, A.guess_in,
-                               A.wguess, w);
+                               A.wguess, w, gp);
+            if (stage == 2)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) A.xs1[0][k * P + a] = keep[k];
             if (T->slots[s].mode == SLOT_STEP) {  // float copies of the gradient-pass inputs
                 const double *g = A.gin;
                 A.fX[a] = make_float4((float)g[a], (float)g[P + a], (float)g[2 * P + a], (float)g[3 * P + a]);

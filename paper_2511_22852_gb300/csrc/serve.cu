@@ -301,9 +301,9 @@ __global__ void k_seg_rank(Arena A, int stage, const int *__restrict__ id)
 }
 
 struct SegPerm {
-    const double *src[4];
-    double *dst[4];
-    int rows[4];
+    const double *src[6];
+    double *dst[6];
+    int rows[6];
     int ng;
     const int *id_in;
     int *id_out;
@@ -694,7 +694,7 @@ __global__ void k_seg_admit(Arena A, int slot, int off, int n, int cap)
         const int a = off + i;
         A.segid[a] = slot;
         A.id[0][a] = i < n ? i : 0;
-        for (int k = 0; k < 4; ++k) A.wguess[k * P + a] = 0.0;
+        for (int k = 0; k < 4; ++k) A.wguess[k * P + a] = A.xs1[0][k * P + a] = 0.0;
     }
 }
 
@@ -913,18 +913,20 @@ void enqueue_batch_step(sph_server *S)
         k_seg_rank<<<S->grid_p, 256, 0, st>>>(A, stage, idsrc);
         SegPerm pa{};
         if (stage == 1) {
-            pa.ng = 3;
+            pa.ng = 4;
             pa.src[0] = A.Y[0], pa.dst[0] = A.Y[1], pa.rows[0] = 9;
             pa.src[1] = A.Nq[0], pa.dst[1] = A.Nq[1], pa.rows[1] = 3;
             pa.src[2] = A.wguess, pa.dst[2] = A.guess_in, pa.rows[2] = 4;
+            pa.src[3] = A.xs1[0], pa.dst[3] = A.xs1[1], pa.rows[3] = 4;
             pa.id_in = A.id[0], pa.id_out = A.id[1];
             pa.nq = A.Nq[0];
         } else {
-            pa.ng = 4;
+            pa.ng = 5;
             pa.src[0] = A.Y1[0], pa.dst[0] = A.Y1[1], pa.rows[0] = 9;
             pa.src[1] = A.Y[1], pa.dst[1] = A.Y[0], pa.rows[1] = 9;
             pa.src[2] = A.Nq[1], pa.dst[2] = A.Nq[0], pa.rows[2] = 3;
             pa.src[3] = A.wguess, pa.dst[3] = A.guess_in, pa.rows[3] = 4;
+            pa.src[4] = A.xs1[1], pa.dst[4] = A.xs1[0], pa.rows[4] = 4;
             pa.id_in = A.id[1], pa.id_out = A.id[0];
             pa.nq = A.Nq[1];
         }
@@ -1175,6 +1177,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     S->E = eos_params(eos);
     S->polish = d->polish ? 1 : 0;
     S->E.polish = S->polish;
+    S->E.tol = d->newton_tol > 0.0 ? d->newton_tol : 1e-10;
     S->max_events = d->max_events;
     S->inflight = d->max_inflight > 0 ? std::min(d->max_inflight, 8) : 2;
     if (const char *tl = getenv("SPH_WAIT_LIMIT_S")) S->timeout_s = atof(tl);
@@ -1188,7 +1191,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
         S->own_stream = true;
     }
     // arena capacity: requested, or a share of free HBM
-    const size_t per_particle = sizeof(double) * (9 * 4 + 3 * 2 + 4 * 2 + kNDens + kNEos + kNGin + kNGout) +
+    const size_t per_particle = sizeof(double) * (9 * 4 + 3 * 2 + 4 * 4 + kNDens + kNEos + kNGin + kNGout) +
                                 sizeof(int) * (2 + 1 + 1 + 1) + sizeof(uint32_t) * (1 + 4) + 8 + 48;
     long long P = d->max_particles;
     if (P == 0) {
@@ -1219,6 +1222,8 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
         SAL(A.id[k], sizeof(int) * Pz);
     }
     SAL(A.wguess, sizeof(double) * 4 * Pz);
+    SAL(A.xs1[0], sizeof(double) * 4 * Pz);
+    SAL(A.xs1[1], sizeof(double) * 4 * Pz);
     SAL(A.guess_in, sizeof(double) * 4 * Pz);
     SAL(A.segid, sizeof(int) * Pz);
     SAL(A.dens, sizeof(double) * kNDens * Pz);

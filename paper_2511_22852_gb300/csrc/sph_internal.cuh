@@ -346,6 +346,7 @@ struct Arena {
     double *Y[2], *Y1[2], *Nq[2];
     int *id[2];
     double *wguess, *guess_in;
+    double *xs1[2];  // the previous step's stage-1 table solution (T = 0: none), ping-pong with the sorts
     int *segid;  // slot of every arena position of an event's range (padding included)
     double *dens, *eosf, *gin, *gout;
     uint32_t *status;
