@@ -193,9 +193,13 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
     # serving form, closed loop (every event submitted at once): capacity
     srv = Bd.GpuServer(I.BJ_EOS, table, max_events=max_events, max_particles=int(1.25 * ntot) + 65536,
                        pinned_bytes=int(400 * ntot) + (64 << 20))
-    tw = srv.submit(evs[0], 2)
+    # warm-up batch (8 events), on which the autotuner picks the tiled passes' launch shape
+    tw = [srv.submit(e, 4) for e in evs[:8]]
+    srv.pump(2)
+    tuned = srv.autotune(3)
     srv.drain(120.0)
-    srv.collect(tw)
+    for t in tw:
+        srv.collect(t, names=("T",))
     st0 = srv.stats()
     t0 = time.perf_counter()
     tk = [srv.submit(e, ksteps) for e in evs]
@@ -253,7 +257,8 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
                       "batch_steps": st2["batch_steps"] - st1["batch_steps"]},
         "eos_work_per_particle_stage": {"table_evals": eos_per_pstage[0], "solves": eos_per_pstage[1],
                                         "closed_form_evals": eos_per_pstage[2]},
-        "max_events": max_events, "latency": "submit (host arrays) to results readable in host memory",
+        "max_events": max_events, "tiled_block_threads": tuned,
+        "latency": "submit (host arrays) to results readable in host memory",
         "precision": "mixed: FP32 neighbour sums (compensated), FP64 EoS/EoM/totals; no Newton polish",
     }
 

@@ -361,6 +361,13 @@ sph_status sph_collect(sph_server *srv, int64_t ticket, uint64_t mask, const sph
 sph_status sph_server_stats_get(sph_server *srv, sph_server_stats *out);
 /* Pumps until every submitted ticket is DONE (timeout_s <= 0: no limit). */
 sph_status sph_server_drain(sph_server *srv, double timeout_s);
+/* Autotuner of the launch shape: times the tiled neighbour passes of the running batch (the
+ * state of its last step) with 64, 96, 128, 192 and 256 threads per block, trials runs each,
+ * and keeps the fastest for the following steps (*chosen, may be NULL).  The work per cell is
+ * split into lanes by the block size, so the choice changes the summation order of the kernel
+ * sums (results then differ at the rounding level; they stay bitwise independent of the batch
+ * composition for a fixed shape).  Errors: SPH_ERR_STATE (no batch has run a step). */
+sph_status sph_server_autotune(sph_server *srv, int32_t trials, int32_t *chosen);
 
 /* Message of the calling thread's last error ("" if none). */
 const char *sph_last_error(void);

@@ -35,7 +35,7 @@ EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_even
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
-           "sph_set_jets"]
+           "sph_set_jets", "sph_server_autotune"]
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
 
@@ -126,6 +126,7 @@ def lib():
             "sph_server_drain": (i32, [vp, C.c_double]),
             "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
             "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
+            "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
             "sph_read_freezeout": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
@@ -351,6 +352,11 @@ class GpuServer:
 
     def stats(self) -> dict:
         return sph_server_stats_get(self.h)
+
+    def autotune(self, trials: int = 3) -> int:
+        c = C.c_int32(0)
+        _check(lib().sph_server_autotune(self.h, int(trials), C.byref(c)))
+        return c.value
 
     def drain(self, timeout_s: float = 0.0):
         sph_server_drain(self.h, timeout_s)

@@ -52,7 +52,7 @@ using namespace sphg;
 namespace {
 
 constexpr int kScanBlocks = 256;
-constexpr int kTT = 128;    // threads of a tiled neighbour block
+constexpr int kTTDefault = 128;  // threads of a tiled neighbour block (the autotuner may pick another)
 constexpr int kTile = 512;  // candidates staged in shared memory at a time
 // Accumulation: each lane sums runs of kRun candidates in plain FP32 (at most kRun terms, so a
 // run's sum errs by <= kRun u times the sum of its terms' magnitudes, u = 2^-24) and folds
@@ -411,7 +411,8 @@ __device__ __forceinline__ int cand_index(const CellCtx &cc, int q, const float2
     return b;
 }
 
-__global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__restrict__ y,
+template <int TT>
+__global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__restrict__ y,
                                                      const double *__restrict__ Nq)
 {
     __shared__ int s_base[kMaxSlots];
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
     __shared__ CellCtx cc;
     const BatchTable *T = A.tab;
     const int ns = T->nslots;
-    for (int i = threadIdx.x; i < ns; i += kTT) s_base[i] = A.grid[i].base;
+    for (int i = threadIdx.x; i < ns; i += TT) s_base[i] = A.grid[i].base;
     __syncthreads();
     const int ncells = *A.ncells;
     const size_t P = (size_t)A.P;
@@ -440,10 +441,11 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
             const float ih = (float)V.inv_h;
             const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
             const double supp2 = V.supp2, sd = V.sigma_d;
-            const int L = na <= 32 ? 4 : (na <= 64 ? 2 : 1);
+            int L = 1;  // lanes per particle: as many as the block holds, up to 8
+            while (L < 8 && na * 2 * L <= TT) L *= 2;
             const int l = tid & (L - 1);
             unsigned long long pairs = 0ull, shell = 0ull;
-            for (int g0 = 0; g0 < na; g0 += kTT / L) {
+            for (int g0 = 0; g0 < na; g0 += TT / L) {
                 const int my = g0 + tid / L;
                 const bool valid = my < na;
                 const int a = cc.first + (valid ? my : 0);
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
                 for (int t0 = 0; t0 < cc.M; t0 += kTile) {
                     const int mt = min(kTile, cc.M - t0);
                     __syncthreads();
-                    for (int i = tid; i < mt; i += kTT) {
+                    for (int i = tid; i < mt; i += TT) {
                         float2 rel;
                         const int b = cand_index(cc, t0 + i, A.fpos, rel);
                         cpos[i] = rel;
@@ -533,7 +535,8 @@ __global__ void __launch_bounds__(kTT) k_seg_density(Arena A, const double *__re
     }
 }
 
-__global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const double *__restrict__ y)
+template <int TT>
+__global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const double *__restrict__ y)
 {
     __shared__ int s_base[kMaxSlots];
     __shared__ float2 cpos[kTile];
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
     __shared__ CellCtx cc;
     const BatchTable *T = A.tab;
     const int ns = T->nslots;
-    for (int i = threadIdx.x; i < ns; i += kTT) s_base[i] = A.grid[i].base;
+    for (int i = threadIdx.x; i < ns; i += TT) s_base[i] = A.grid[i].base;
     __syncthreads();
     const int ncells = *A.ncells;
     const size_t P = (size_t)A.P;
@@ -563,9 +566,10 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
             const float ih = (float)V.inv_h;
             const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
             const double supp2 = V.supp2;
-            const int L = na <= 32 ? 4 : (na <= 64 ? 2 : 1);
+            int L = 1;  // lanes per particle: as many as the block holds, up to 8
+            while (L < 8 && na * 2 * L <= TT) L *= 2;
             const int l = tid & (L - 1);
-            for (int g0 = 0; g0 < na; g0 += kTT / L) {
+            for (int g0 = 0; g0 < na; g0 += TT / L) {
                 const int my = g0 + tid / L;
                 const bool valid = my < na;
                 const int a = cc.first + (valid ? my : 0);
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
                 for (int t0 = 0; t0 < cc.M; t0 += kTile) {
                     const int mt = min(kTile, cc.M - t0);
                     __syncthreads();
-                    for (int i = tid; i < mt; i += kTT) {
+                    for (int i = tid; i < mt; i += TT) {
                         float2 rel;
                         const int b = cand_index(cc, t0 + i, A.fpos, rel);
                         cpos[i] = rel;
@@ -658,6 +662,51 @@ __global__ void __launch_bounds__(kTT) k_seg_gradient(Arena A, int stage, const 
             }
         }
         __syncthreads();
+    }
+}
+
+// launch shapes of the tiled passes the autotuner chooses among (threads per block)
+constexpr int kTTChoices[] = {64, 96, 128, 192, 256};
+
+template <int TT>
+int tiled_grid(int sms)
+{
+    int o1 = 0, o2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_seg_density<TT>, TT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_seg_gradient<TT>, TT, 0);
+    return sms * std::max(1, std::min(o1, o2));
+}
+
+int tiled_grid_for(int tt, int sms)
+{
+    switch (tt) {
+    case 64: return tiled_grid<64>(sms);
+    case 96: return tiled_grid<96>(sms);
+    case 192: return tiled_grid<192>(sms);
+    case 256: return tiled_grid<256>(sms);
+    default: return tiled_grid<128>(sms);
+    }
+}
+
+void tiled_density(int tt, int grid, cudaStream_t st, const Arena &A, const double *ys, const double *nq)
+{
+    switch (tt) {
+    case 64: k_seg_density<64><<<grid, 64, 0, st>>>(A, ys, nq); break;
+    case 96: k_seg_density<96><<<grid, 96, 0, st>>>(A, ys, nq); break;
+    case 192: k_seg_density<192><<<grid, 192, 0, st>>>(A, ys, nq); break;
+    case 256: k_seg_density<256><<<grid, 256, 0, st>>>(A, ys, nq); break;
+    default: k_seg_density<128><<<grid, 128, 0, st>>>(A, ys, nq); break;
+    }
+}
+
+void tiled_gradient(int tt, int grid, cudaStream_t st, const Arena &A, int stage, const double *ys)
+{
+    switch (tt) {
+    case 64: k_seg_gradient<64><<<grid, 64, 0, st>>>(A, stage, ys); break;
+    case 96: k_seg_gradient<96><<<grid, 96, 0, st>>>(A, stage, ys); break;
+    case 192: k_seg_gradient<192><<<grid, 192, 0, st>>>(A, stage, ys); break;
+    case 256: k_seg_gradient<256><<<grid, 256, 0, st>>>(A, stage, ys); break;
+    default: k_seg_gradient<128><<<grid, 128, 0, st>>>(A, stage, ys); break;
     }
 }
 
@@ -844,7 +893,8 @@ struct sph_server {
     std::vector<void *> allocs;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    int max_events = 0, inflight = 2, grid_p = 0, grid_e = 0, grid_c = 0;
+    int max_events = 0, inflight = 2, grid_p = 0, grid_e = 0, grid_c = 0, sms = 1;
+    int tt = kTTDefault;  // threads per block of the tiled passes
     int polish = 0;
     // pinned staging pool
     unsigned char *pool = nullptr;
@@ -933,9 +983,9 @@ void enqueue_batch_step(sph_server *S)
         k_seg_permute<<<S->grid_p, 256, 0, st>>>(A, stage, pa);
         const double *ys = stage == 1 ? A.Y[1] : A.Y1[1];
         const double *nq = stage == 1 ? A.Nq[1] : A.Nq[0];
-        k_seg_density<<<S->grid_c, kTT, 0, st>>>(A, ys, nq);
+        tiled_density(S->tt, S->grid_c, st, A, ys, nq);
         launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st);
-        k_seg_gradient<<<S->grid_c, kTT, 0, st>>>(A, stage, ys);
+        tiled_gradient(S->tt, S->grid_c, st, A, stage, ys);
         if (stage == 1) launch_eom2_seg(A, 1, 0, ys, A.Y1[0], S->grid_p, st);
         else launch_eom2_seg(A, 2, 1, ys, A.Y[0], S->grid_p, st);
         k_seg_work<<<S->max_events, 32, 0, st>>>(A, stage);
@@ -1290,14 +1340,13 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
             return bail(sfail(SPH_ERR_CUDA, "cudaEventCreate failed"));
         }
     // launch shapes: persistent grids of resident blocks on every SM
-    int dev = 0, sms = 0, occ_c = 0, occ_e = 0;
+    int dev = 0, sms = 0, occ_e = 6;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_seg_density, kTT, 0);
-    occ_e = 6;
     sms = std::max(sms, 1);
+    S->sms = sms;
     S->grid_p = sms * 8;
-    S->grid_c = sms * std::max(occ_c, 1);
+    S->grid_c = tiled_grid_for(S->tt, sms);
     S->grid_e = sms * occ_e;
     // host/device clock reference for completion times
     if (cudaEventCreate(&S->ref_ev) != cudaSuccess || cudaEventRecord(S->ref_ev, S->st) != cudaSuccess ||
@@ -1552,6 +1601,61 @@ sph_status sph_server_stats_get(sph_server *S, sph_server_stats *o)
     o->arena_in_use = used;
     o->kernel_launches = S->launches;
     o->max_events = S->max_events;
+    return SPH_OK;
+}
+
+sph_status sph_server_autotune(sph_server *S, int32_t trials, int32_t *chosen)
+{
+    if (!S) return sfail(SPH_ERR_ARG, "null argument");
+    if (trials < 1) trials = 3;
+    if (!any_running(S) || S->steps_launched == 0)
+        return sfail(SPH_ERR_STATE, "the autotuner times the running batch: pump a step first");
+    SCK(cudaStreamSynchronize(S->st));
+    // The last batch step's second stage left a consistent sorted state, cell list and
+    // gradient inputs.  Each candidate re-runs that stage's tiled passes; their outputs are
+    // recomputed by the next step, and the counters they add to are restored afterwards.
+    const int ns = std::max(S->nslots, 1);
+    std::vector<DevScalars> save((size_t)ns);
+    SCK(cudaMemcpy(save.data(), S->A.sc, sizeof(DevScalars) * (size_t)ns, cudaMemcpyDeviceToHost));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SCK(cudaEventCreate(&e0));
+    SCK(cudaEventCreate(&e1));
+    const Arena &A = S->A;
+    float best = 1e30f;
+    int best_tt = S->tt;
+    for (int tt : kTTChoices) {
+        const int grid = tiled_grid_for(tt, S->sms);
+        float tot = 0.0f;
+        for (int r = 0; r <= trials; ++r) {  // r = 0: warm-up
+            SCK(cudaMemsetAsync(A.claim, 0, sizeof(unsigned int) * kClaims, S->st));
+            SCK(cudaEventRecord(e0, S->st));
+            tiled_density(tt, grid, S->st, A, A.Y1[1], A.Nq[0]);
+            tiled_gradient(tt, grid, S->st, A, 2, A.Y1[1]);
+            SCK(cudaEventRecord(e1, S->st));
+            SCK(cudaGetLastError());
+            sph_status s = wait_event(S, e1);
+            if (s != SPH_OK) return s;
+            float ms = 0.0f;
+            SCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_tt = tt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SCK(cudaMemcpy(S->A.sc, save.data(), sizeof(DevScalars) * (size_t)ns, cudaMemcpyHostToDevice));
+    if (best_tt != S->tt) {  // the step graph holds the launch shape: capture it again
+        S->tt = best_tt;
+        S->grid_c = tiled_grid_for(best_tt, S->sms);
+        if (S->gexec) cudaGraphExecDestroy(S->gexec);
+        if (S->graph) cudaGraphDestroy(S->graph);
+        S->gexec = nullptr;
+        S->graph = nullptr;
+    }
+    if (chosen) *chosen = S->tt;
     return SPH_OK;
 }
 

@@ -174,3 +174,25 @@ def test_server_errors(Bd):
     s.free()
     with pytest.raises(Bd.SphError):
         Bd.GpuServer(ev.eos, ev.table, max_events=0)
+
+
+def test_autotuner_keeps_results_and_counters(Bd):
+    """The autotuner times the tiled passes on the running batch and picks a launch shape; the
+    events still match the oracle, and the counters its trial runs touched are restored (the
+    neighbour-pair count equals that of an untuned run)."""
+    evs = [bsq(3000, seed=61), bsq(5000, seed=62)]
+    s = Bd.GpuServer(evs[0].eos, evs[0].table, max_events=4, max_particles=1 << 16)
+    with pytest.raises(Bd.SphError) as e:
+        s.autotune(1)
+    assert e.value.code == Bd.SPH_ERR_STATE
+    tk = [s.submit(ev, 12) for ev in evs]
+    s.pump(2)
+    tt = s.autotune(2)
+    assert tt in (64, 96, 128, 192, 256)
+    s.drain(120.0)
+    out = [s.collect(t) for t in tk]
+    s.free()
+    check_against_oracle(out[0], evs[0], 12)
+    plain = serve_alone(Bd, evs[1], 12, max_events=4, max_particles=1 << 16)
+    assert out[1]["totals"]["pairs"] == plain["totals"]["pairs"]
+    assert np.array_equal(out[1]["NNB"], plain["NNB"])
