@@ -263,6 +263,45 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
     }
 
 
+def bench_freezeout(Bd, I, steps: int = 40):
+    """Cost of recording the freeze-out surface on the 40k-particle event: device ms per step
+    with and without recording (CUDA graphs, CUDA events), and the elements recorded, for a
+    surface at the 20 % quantile of the initial energy density (it sweeps through the cooling
+    edge during the window)."""
+    import numpy as np
+    import torch
+    ev = I.viscous_bsq_2p1()
+    g0 = Bd.GpuEvent(ev)
+    e0 = g0.read(("E",))["E"]
+    g0.free()
+    se = np.sort(e0)
+    k = int(0.2 * len(se))
+    while se[k + 1] - se[k] < 1e-6 * se[k]:
+        k += 1
+    e_fo = 0.5 * float(se[k] + se[k + 1])
+    out = {"workload": f"40k-particle viscous BSQ event, e_fo = {e_fo:.4g} fm^-4 (20 % quantile of the initial e), "
+                       f"{steps} steps", "e_fo": e_fo}
+    for name, on in (("without", False), ("with", True)):
+        st = torch.cuda.Stream()
+        g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream)
+        if on:
+            g.freezeout_setup(e_fo, 100000)
+        g.step(2, sync=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record(st)
+            g.step(steps)
+            b.record(st)
+        torch.cuda.synchronize()
+        out[name + "_ms_per_step"] = a.elapsed_time(b) / steps
+        if on:
+            rec, ids = g.read_freezeout()
+            out["elements"] = int(len(ids))
+        g.free()
+    out["overhead"] = out["with_ms_per_step"] / out["without_ms_per_step"] - 1.0
+    return out
+
+
 def bench_3p1d(Bd, I, steps: int = 3):
     """The 3+1D hyperbolic viscous BSQ event (about 10^6 particles): device ms per Heun step of
     the plain FP64 form next to the mixed form (FP32 neighbour sums, FP64 EoS and equations of
@@ -478,6 +517,7 @@ def run_ours(args):
                                "profile_mode_group_ms_per_step": total_ms / kp}}
         if not args.no_serving:
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
+        out["freezeout"] = bench_freezeout(Bd, I)
         if not args.no_3d:
             out["config_3p1d"] = bench_3p1d(Bd, I)
             out["config_stress"] = bench_stress(Bd, I)
