@@ -53,6 +53,8 @@ class Params(C.Structure):
         ("cs2_cap", C.c_double),
         ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("pad", C.c_int),
         ("ntrack", C.c_int), ("pad2", C.c_int), ("tracks", C.c_void_p), ("track_sigma", C.c_double),
+        ("inv", C.c_void_p), ("inv_p10", C.c_void_p), ("inv_K", C.c_int), ("inv_nd", C.c_int), ("inv_nx", C.c_int),
+        ("pad3", C.c_int), ("inv_xmax", C.c_double),
     ]
 
 
@@ -87,6 +89,8 @@ def lib():
             "oc_pi_pairs": (i, [i, p]),
             "oc_pi_full": (None, [i, i, d, p, p, p]),
             "oc_freezeout": (l, [P, l, d, d, p, p, p, d, l, p, p]),
+            "oc_inverse_lookup": (i, [P, d, p, p]),
+            "oc_inverse_build": (None, [P, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -130,6 +134,12 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
     P.eta_over_s, P.zeta_peak, P.zeta_T_GeV, P.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
     P.tau_pi_coef, P.tau_Pi_ratio, P.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
     P.newton_tol, P.newton_maxit = newton_tol, newton_maxit
+    inv = getattr(ev, "inverse", None)
+    if inv is not None:
+        table, p10 = inverse_table(P, inv)
+        keep += [table, p10]
+        P.inv, P.inv_p10 = table.ctypes.data, p10.ctypes.data
+        P.inv_K, P.inv_nd, P.inv_nx, P.inv_xmax = inv.per_decade, inv.decades, inv.nx, inv.xmax
     jets = getattr(ev, "jets", None)
     if jets is not None and len(jets.tracks):
         if ev.milne:
@@ -138,6 +148,27 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
         keep.append(tr)
         P.ntrack, P.tracks, P.track_sigma = tr.shape[0], tr.ctypes.data, float(jets.sigma)
     return P, keep
+
+
+_inverse_cache = {}
+
+
+def inverse_table(P: Params, grid):
+    """The oracle's inverted EoS table on grid (inputs.InverseGrid): (T, mu_B, mu_S, mu_Q) at every
+    node of the log-decade s axis times the charge-ratio axes, from the online root finder."""
+    key = (P.tp, P.has_table, grid.per_decade, grid.decade_lo, grid.decades, grid.nx, grid.xmax)
+    if key in _inverse_cache:
+        return _inverse_cache[key]
+    p10 = np.array([10.0 ** (grid.decade_lo + d) for d in range(grid.decades + 1)])
+    ns = grid.per_decade * grid.decades + 1
+    table = np.zeros((ns, grid.nx, grid.nx, grid.nx, 4))
+    Q = Params()
+    C.pointer(Q)[0] = P  # a copy without the inverse table: the build inverts online
+    Q.inv, Q.inv_p10 = None, p10.ctypes.data
+    Q.inv_K, Q.inv_nd, Q.inv_nx, Q.inv_xmax = grid.per_decade, grid.decades, grid.nx, grid.xmax
+    lib().oc_inverse_build(C.byref(Q), _ptr(table))
+    _inverse_cache[key] = (table, p10)
+    return table, p10
 
 
 def npi(dim: int) -> int:

@@ -75,6 +75,14 @@ typedef struct {
     int pad2;
     const double *tracks;
     double track_sigma;
+    /* offline inverter (NULL: online Newton): (T, mu_B, mu_S, mu_Q) on the grid of s (log
+       decades: node i at s_i = p10[i / K] (1 + 9 (i % K) / K), i <= K nd, p10[d] = 10^(d0 + d))
+       times the charge ratios x_q = n_q / s (inv_nx nodes uniform on [-xmax, xmax]);
+       node [i][jB][jS][jQ][4] */
+    const double *inv;
+    const double *inv_p10;
+    int inv_K, inv_nd, inv_nx, pad3;
+    double inv_xmax;
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -574,6 +582,89 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
      2. otherwise (or if 1. does not converge) the closed-form solution, then table Newton
         started there if it lies in the table; else the closed form (flagged).
    used_table (may be NULL) receives 1 when the table produced the result. */
+/* Offline inverter (Sec. "Equation of state", offline inversion onto a grid in (s, n)): the
+   quadrilinear interpolant of the inverted table at (s, n_q / s); -1 outside the grid or where a
+   corner holds no solution. */
+int oc_inverse_lookup(const oc_params *P, double s, const double *n, double *x)
+{
+    if (!(s > 0.0)) return -1;
+    const int K = P->inv_K, nd = P->inv_nd, nx = P->inv_nx;
+    int d = (int)floor(log10(s / P->inv_p10[0]));
+    if (d < 0 || d >= nd + 1) return -1;
+    double m = s / P->inv_p10[d];
+    if (m >= 10.0 && d < nd) {
+        m /= 10.0;
+        d += 1;
+    }
+    if (m < 1.0 && d > 0) {
+        m *= 10.0;
+        d -= 1;
+    }
+    double r = (m - 1.0) * K / 9.0;
+    int j = (int)floor(r);
+    if (j > K - 1) j = K - 1;
+    if (j < 0) j = 0;
+    long i = (long)d * K + j;
+    double t[4];
+    int ix[4];
+    if (i < 0 || i > (long)K * nd - 1) return -1;
+    ix[0] = (int)i;
+    t[0] = r - j;
+    if (t[0] < 0.0 || t[0] > 1.0) return -1;
+    const double dxr = 2.0 * P->inv_xmax / (nx - 1);
+    for (int q = 0; q < 3; ++q) {
+        double rr = (n[q] / s + P->inv_xmax) / dxr;
+        if (!(rr >= 0.0 && rr <= (double)(nx - 1))) return -1;
+        int k = (int)floor(rr);
+        if (k > nx - 2) k = nx - 2;
+        ix[1 + q] = k;
+        t[1 + q] = rr - k;
+    }
+    for (int c = 0; c < 4; ++c) x[c] = 0.0;
+    for (int corner = 0; corner < 16; ++corner) {
+        long node = 0;
+        double w = 1.0;
+        const long dims[4] = {(long)K * nd + 1, nx, nx, nx};
+        for (int a = 0; a < 4; ++a) {
+            int bit = (corner >> (3 - a)) & 1;
+            node = node * dims[a] + ix[a] + bit;
+            w *= bit ? t[a] : 1.0 - t[a];
+        }
+        const double *v = P->inv + 4 * node;
+        if (!isfinite(v[0])) return -1;
+        for (int c = 0; c < 4; ++c) x[c] += w * v[c];
+    }
+    return 0;
+}
+
+unsigned oc_eos_invert_ws(const oc_params *P, double s, const double *n, const double *guess, double *out,
+                          int *used_table);
+
+/* builds the inverted table: every node (s_i, x_j) inverted by the online root finder started
+   cold (closed form, then table Newton); NaN where no solution exists */
+void oc_inverse_build(const oc_params *P, double *inv)
+{
+    const int K = P->inv_K, nd = P->inv_nd, nx = P->inv_nx;
+    const long ns = (long)K * nd + 1;
+    const double dxr = 2.0 * P->inv_xmax / (nx - 1);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long node = 0; node < ns * nx * nx * nx; ++node) {
+        long r = node;
+        int jQ = (int)(r % nx);
+        r /= nx;
+        int jS = (int)(r % nx);
+        r /= nx;
+        int jB = (int)(r % nx);
+        long i = r / nx;
+        double s = P->inv_p10[i / K] * (1.0 + 9.0 * (double)(i % K) / K);
+        double nq[3] = {(-P->inv_xmax + jB * dxr) * s, (-P->inv_xmax + jS * dxr) * s, (-P->inv_xmax + jQ * dxr) * s};
+        double out[11];
+        int used = 0;
+        unsigned st = oc_eos_invert_ws(P, s, nq, NULL, out, &used);
+        for (int c = 0; c < 4; ++c) inv[4 * node + c] = (st & ST_NOCONV) ? NAN : out[c];
+    }
+}
+
 unsigned oc_eos_invert_ws(const oc_params *P, double s, const double *n, const double *guess, double *out,
                           int *used_table)
 {
@@ -584,7 +675,9 @@ unsigned oc_eos_invert_ws(const oc_params *P, double s, const double *n, const d
     double x[4];
     double p, H[16], sn[4];
     int use_table = 0;
-    if (P->has_table && guess && guess[0] > 0.0 && in_table(P, guess)) {
+    /* offline inverter: interpolate (T, mu) from the inverted table (no root finding) */
+    if (P->inv && P->has_table && oc_inverse_lookup(P, s, n, x) == 0 && in_table(P, x)) use_table = 1;
+    if (!use_table && P->has_table && guess && guess[0] > 0.0 && in_table(P, guess)) {
         double xt[4];
         memcpy(xt, guess, sizeof(xt));
         if (table_newton(P, s, n, xt) == 0) {

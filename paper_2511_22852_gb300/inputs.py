@@ -108,6 +108,18 @@ class JetTracks:
 
 
 @dataclass
+class InverseGrid:
+    """Grid of the offline-inverted EoS table: s on log decades 10^decade_lo .. 10^(decade_lo +
+    decades) with per_decade uniform nodes per decade (s = 10^d (1 + 9 j / per_decade)), and the
+    charge ratios n_q / s on nx uniform nodes in [-xmax, xmax]."""
+    per_decade: int = 90
+    decade_lo: int = -3
+    decades: int = 6
+    nx: int = 17
+    xmax: float = 0.04
+
+
+@dataclass
 class Event:
     """One event: SoA particle arrays plus run parameters."""
     name: str
@@ -128,6 +140,7 @@ class Event:
     transport: Transport
     meta: dict = field(default_factory=dict)
     jets: JetTracks | None = None
+    inverse: InverseGrid | None = None  # set: the EoS is inverted by the offline table
 
     @property
     def n(self) -> int:

@@ -74,6 +74,11 @@ MUTATIONS = [
      "test_oracle_sources.py::test_track_deposits_its_energy_and_momentum"),
     ("src_gaussian_norm", "pow(2.0 * M_PI, 1.5)", "pow(M_PI, 1.5)",
      "test_oracle_sources.py::test_track_deposits_its_energy_and_momentum"),
+    ("inv_weight_swap", "w *= bit ? t[a] : 1.0 - t[a];", "w *= bit ? 1.0 - t[a] : t[a];",
+     "test_oracle_offline_inverter.py::test_interpolant_converges_to_the_online_inversion"),
+    ("inv_node_spacing", "double s = P->inv_p10[i / K] * (1.0 + 9.0 * (double)(i % K) / K);",
+     "double s = P->inv_p10[i / K] * (1.0 + 9.5 * (double)(i % K) / K);",
+     "test_oracle_offline_inverter.py::test_nodes_reproduce_the_online_inversion"),
 ]
 
 
