@@ -302,6 +302,45 @@ def bench_freezeout(Bd, I, steps: int = 40):
     return out
 
 
+def bench_offline_eos(Bd, I, steps: int = 20):
+    """The offline EoS inverter (interpolation in an inverted (s, n/s) table) against the online
+    Newton inversion on the 40k-particle event: device ms per step and per EoS pass (profile
+    mode), table build time, and the accuracy of T and mu_B against the online inversion."""
+    import numpy as np
+    import torch
+    out = {}
+    grid = I.InverseGrid(per_decade=90, decade_lo=-3, decades=6, nx=17, xmax=0.04)
+    res = {}
+    for name in ("online", "offline"):
+        ev = I.viscous_bsq_2p1()
+        if name == "offline":
+            ev.inverse = grid
+        t0 = time.perf_counter()
+        g = Bd.GpuEvent(ev, use_graph=False, profile=True)
+        build_s = time.perf_counter() - t0
+        f = g.read(("T", "MU"))
+        g.step(2)
+        k0 = g.kernel_times()
+        g.step(steps)
+        k1 = g.kernel_times()
+        torch.cuda.synchronize()
+        eos_ms = (k1["eos"][0] - k0["eos"][0]) / (2 * steps)
+        tot_ms = sum(k1[k][0] - k0[k][0] for k in k1) / steps
+        res[name] = (f, eos_ms, tot_ms, build_s)
+        g.free()
+    fo, fn = res["offline"][0], res["online"][0]
+    out = {"workload": "40k-particle viscous BSQ event; inverted table: s on 10^-3..10^3 with 90 nodes per decade, "
+                       "n_q/s on 17 nodes in +-0.04 (2.66M nodes, 85 MB)",
+           "online_eos_ms_per_pass": res["online"][1], "offline_eos_ms_per_pass": res["offline"][1],
+           "online_ms_per_step": res["online"][2], "offline_ms_per_step": res["offline"][2],
+           "eos_speedup": res["online"][1] / res["offline"][1],
+           "table_build_s": res["offline"][3] - res["online"][3],
+           "T_max_rel_err": float(np.max(np.abs(fo["T"] / fn["T"] - 1))),
+           "T_mean_rel_err": float(np.mean(np.abs(fo["T"] / fn["T"] - 1))),
+           "muB_err_normwise": float(np.max(np.abs(fo["MU"][0] - fn["MU"][0])) / np.max(np.abs(fn["MU"][0])))}
+    return out
+
+
 def bench_3p1d(Bd, I, steps: int = 3):
     """The 3+1D hyperbolic viscous BSQ event (about 10^6 particles): device ms per Heun step of
     the plain FP64 form next to the mixed form (FP32 neighbour sums, FP64 EoS and equations of
@@ -518,6 +557,7 @@ def run_ours(args):
         if not args.no_serving:
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
         out["freezeout"] = bench_freezeout(Bd, I)
+        out["offline_eos"] = bench_offline_eos(Bd, I)
         if not args.no_3d:
             out["config_3p1d"] = bench_3p1d(Bd, I)
             out["config_stress"] = bench_stress(Bd, I)

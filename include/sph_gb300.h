@@ -233,6 +233,26 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
 sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms, int64_t *launches, int32_t *count);
 
 /* ---------------------------------------------------------------------------
+ * Offline EoS inverter (Sec. "Equation of state": the EoS converted once onto a grid in
+ * (s, n) with s on logarithmic decades, uniform within each decade; interpolation instead of
+ * root finding).  sph_eos_build_inverse inverts the handle's table at every node by the
+ * online root finder (closed form, then table Newton; NaN where no solution exists): s at
+ * 10^d (1 + 9 j / per_decade) for d = decade_lo .. decade_lo + decades - 1, j < per_decade,
+ * plus 10^(decade_lo + decades); the charge ratios n_q / s on nx uniform nodes in [-xmax, xmax]
+ * (4 doubles per node; at most 2^28 nodes).  An event in SPH_EOS_OFFLINE mode takes (T, mu)
+ * from the quadrilinear interpolant of that table, then p, e and the derivatives from the
+ * forward table there; points off the grid, or whose interpolated (T, mu) leave the forward
+ * table, use the online inversion.  Faster, less accurate (first order in the grid spacing
+ * for T: the inverse of the piecewise-multilinear forward table has kinks).
+ * Errors: SPH_ERR_ARG (no table, bad grid), SPH_ERR_OOM; sph_set_eos_mode: SPH_ERR_STATE when
+ * the handle has no inverted table. */
+#define SPH_EOS_ONLINE 0
+#define SPH_EOS_OFFLINE 1
+sph_status sph_eos_build_inverse(sph_eos *eos, int32_t per_decade, int32_t decade_lo, int32_t decades, int32_t nx,
+                                 double xmax);
+sph_status sph_set_eos_mode(sph_event *ev, int32_t mode);
+
+/* ---------------------------------------------------------------------------
  * Energy-momentum source of jet tracks (eq. conservation_source with I^nu != 0, Sec.
  * "Equations of motion"; Cartesian events).  Track k (tracks[8 k ..] = x0, y0, z0, n_x, n_y,
  * n_z, t0, dE/dx, host memory, n a unit vector, dE/dx in fm^-2) moves at the speed of light

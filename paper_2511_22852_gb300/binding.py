@@ -35,7 +35,8 @@ EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_even
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
-           "sph_set_jets", "sph_server_autotune"]
+           "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode"]
+SPH_EOS_ONLINE, SPH_EOS_OFFLINE = 0, 1
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
 
@@ -127,6 +128,8 @@ def lib():
             "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
             "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
             "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
+            "sph_eos_build_inverse": (i32, [vp, i32, i32, i32, i32, C.c_double]),
+            "sph_set_eos_mode": (i32, [vp, i32]),
             "sph_read_freezeout": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
@@ -207,6 +210,16 @@ def sph_kernel_times(h):
     _check(lib().sph_kernel_times(h, 16, names, ms.ctypes.data, nl.ctypes.data, C.byref(cnt)))
     raw = names.raw
     return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
+
+
+def sph_eos_build_inverse(eos, grid):
+    """Builds the offline inverter of an EoS handle on grid (inputs.InverseGrid)."""
+    _check(lib().sph_eos_build_inverse(eos, int(grid.per_decade), int(grid.decade_lo), int(grid.decades),
+                                       int(grid.nx), float(grid.xmax)))
+
+
+def sph_set_eos_mode(h, mode: int):
+    _check(lib().sph_set_eos_mode(h, int(mode)))
 
 
 def sph_set_jets(h, tracks, sigma: float):
@@ -396,6 +409,10 @@ class GpuEvent:
         d.profile = int(profile)
         d.precision = int(precision)
         self.h = sph_init_event(d, self.eos)
+        inv = getattr(ev, "inverse", None)
+        if inv is not None:
+            sph_eos_build_inverse(self.eos, inv)
+            sph_set_eos_mode(self.h, SPH_EOS_OFFLINE)
         jets = getattr(ev, "jets", None)
         if jets is not None and len(jets.tracks):
             sph_set_jets(self.h, jets.tracks, jets.sigma)

@@ -44,6 +44,7 @@ void sphg::set_last_error(const char *msg) { g_err = msg; }
 struct sph_eos {
     EosDev dev;
     double *d_sn = nullptr, *d_p = nullptr;
+    double *d_inv = nullptr, *d_p10 = nullptr;  // offline inverter (sph_eos_build_inverse)
     int refs = 1;
 };
 
@@ -58,6 +59,7 @@ struct sph_event {
     std::vector<uint32_t> spread_host;
     uint32_t *spread = nullptr;     // 3D: generalized Morton spread tables (3 x 1024)
     double h = 0.3, dtau = 0.01, tau0 = 0.0;
+    int eos_offline = 0;            // 1: invert through the EoS handle's offline table
     int ntrack = 0;                 // jet tracks (sph_set_jets): device copy and Gaussian constants
     double *d_tracks = nullptr;
     double track_norm = 0.0, track_i2s2 = 0.0;
@@ -138,6 +140,7 @@ static EvView make_view(const sph_event *ev)
     v.dtau = ev->dtau;
     v.sc = ev->sc;
     v.eos = ev->eos->dev;
+    v.eos.offline = ev->eos_offline && ev->eos->dev.inv ? 1 : 0;
     v.tr = ev->tr;
     v.ntrack = ev->ntrack;
     v.tracks = ev->d_tracks;
@@ -370,6 +373,8 @@ void sph_free_eos(sph_eos *e)
     if (--e->refs > 0) return;
     if (e->d_sn) cudaFree(e->d_sn);
     if (e->d_p) cudaFree(e->d_p);
+    if (e->d_inv) cudaFree(e->d_inv);
+    if (e->d_p10) cudaFree(e->d_p10);
     delete e;
 }
 
@@ -750,6 +755,66 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         tot->kernel_launches = ev->launches;
     }
     return wait_stream(ev);
+}
+
+sph_status sph_eos_build_inverse(sph_eos *e, int32_t per_decade, int32_t decade_lo, int32_t decades, int32_t nx,
+                                 double xmax)
+{
+    if (!e) return fail(SPH_ERR_ARG, "null EoS");
+    if (!e->dev.has_table) return fail(SPH_ERR_ARG, "the offline inverter inverts a tabulated EoS");
+    if (per_decade < 1 || decades < 1 || nx < 2 || !(xmax > 0.0) || decade_lo < -30 || decade_lo + decades > 30)
+        return fail(SPH_ERR_ARG, "per_decade >= 1, decades >= 1, nx >= 2, xmax > 0 required");
+    const long long ns = (long long)per_decade * decades + 1;
+    const long long nnodes = ns * nx * nx * nx;
+    if (nnodes > (1LL << 28)) return fail(SPH_ERR_ARG, "inverted table too large (more than 2^28 nodes)");
+    std::vector<double> p10((size_t)decades + 1);
+    for (int d = 0; d <= decades; ++d) p10[(size_t)d] = std::pow(10.0, (double)(decade_lo + d));
+    double *inv = nullptr, *dp = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&inv), sizeof(double) * 4 * (size_t)nnodes) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&dp), sizeof(double) * p10.size()) != cudaSuccess) {
+        cudaGetLastError();
+        if (inv) cudaFree(inv);
+        return fail(SPH_ERR_OOM, "cudaMalloc failed for the inverted table");
+    }
+    CK(cudaMemcpy(dp, p10.data(), sizeof(double) * p10.size(), cudaMemcpyHostToDevice));
+    EosDev E = e->dev;
+    E.inv = inv;
+    E.inv_p10 = dp;
+    E.inv_K = per_decade;
+    E.inv_nd = decades;
+    E.inv_nx = nx;
+    E.inv_xmax = xmax;
+    launch_inverse_build(E, inv, nnodes, 0);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    if (e->d_inv) cudaFree(e->d_inv);
+    if (e->d_p10) cudaFree(e->d_p10);
+    e->d_inv = inv;
+    e->d_p10 = dp;
+    E.offline = 0;
+    e->dev = E;
+    return SPH_OK;
+}
+
+sph_status sph_set_eos_mode(sph_event *ev, int32_t mode)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (mode != SPH_EOS_ONLINE && mode != SPH_EOS_OFFLINE) return fail(SPH_ERR_ARG, "unknown EoS mode");
+    if (mode == SPH_EOS_OFFLINE && !ev->eos->dev.inv)
+        return fail(SPH_ERR_STATE, "the EoS handle has no inverted table (sph_eos_build_inverse)");
+    CK(cudaStreamSynchronize(ev->stream));
+    ev->eos_offline = mode == SPH_EOS_OFFLINE ? 1 : 0;
+    if (ev->gexec) {  // the EoS parameters are part of the captured step: capture it again
+        cudaGraphExecDestroy(ev->gexec);
+        ev->gexec = nullptr;
+    }
+    if (ev->graph) {
+        cudaGraphDestroy(ev->graph);
+        ev->graph = nullptr;
+    }
+    ev->graph_ready = false;
+    ev->observed = false;
+    return SPH_OK;
 }
 
 sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, double sigma)

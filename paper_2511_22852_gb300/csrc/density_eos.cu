@@ -19,6 +19,8 @@
 //   3. p, e = T s + mu.n - p, and (dp/ds, dp/dn_q) = H^-T (s, n) with H the
 //      Jacobian d(s, n)/d(T, mu) of the EoS used; c_s^2 above the cap scales
 //      them down (flagged).
+#include <algorithm>
+
 #include "sph_internal.cuh"
 #include "eos_device.cuh"
 
@@ -326,6 +328,43 @@ void launch_eos(const EvView &v, int stage, const double *y, const double *dens,
 }
 
 int eom_block_count(int n) { return nblk(n, 64); }
+
+// Offline inverter: every node (s_i, x_j) of the inverted table solved by the online inversion
+// started cold (closed form, then table Newton), as the offline procedure uses the existing
+// root finder; NaN where no solution exists
+__global__ void k_inverse_build(EosDev E, double *__restrict__ inv, long long nnodes)
+{
+    const int K = E.inv_K, nx = E.inv_nx;
+    const double dxr = 2.0 * E.inv_xmax / (nx - 1);
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nnodes;
+         node += (long long)gridDim.x * blockDim.x) {
+        long long r = node;
+        const int jQ = (int)(r % nx);
+        r /= nx;
+        const int jS = (int)(r % nx);
+        r /= nx;
+        const int jB = (int)(r % nx);
+        const long long i = r / nx;
+        const double s = E.inv_p10[i / K] * (1.0 + 9.0 * (double)(i % K) / K);
+        const double n[3] = {(-E.inv_xmax + jB * dxr) * s, (-E.inv_xmax + jS * dxr) * s, (-E.inv_xmax + jQ * dxr) * s};
+        const double g[4] = {0.0, 0.0, 0.0, 0.0};
+        bool used = false;
+        EosWork w = {0u, 0u, 0u};
+        const EosOut o = eos_invert(E, 1.0, s, n, g, used, w);
+        const bool ok = !(o.st & PST_NOCONV);
+        const double nan = __longlong_as_double(0x7FF8000000000000LL);
+        inv[4 * node] = ok ? o.T : nan;
+        for (int q = 0; q < 3; ++q) inv[4 * node + 1 + q] = ok ? o.mu[q] : nan;
+    }
+}
+
+void launch_inverse_build(const EosDev &E, double *inv, long long nnodes, cudaStream_t st)
+{
+    EosDev online = E;
+    online.offline = 0;
+    const int grid = (int)std::min<long long>((nnodes + 127) / 128, 152LL * 16);
+    k_inverse_build<<<grid, 128, 0, st>>>(online, inv, nnodes);
+}
 
 void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st)
 {

@@ -321,6 +321,61 @@ __device__ double tab_p(const EosDev &E, const double *x)
     return pv;
 }
 
+// Offline inverter: the quadrilinear interpolant of the inverted table at (s, n_q / s); false
+// outside the grid or where a corner holds no solution
+__device__ bool inv_lookup(const EosDev &E, double s, const double *n, double *x)
+{
+    if (!(s > 0.0)) return false;
+    const int K = E.inv_K, nd = E.inv_nd, nx = E.inv_nx;
+    int d = (int)floor(log10(s / E.inv_p10[0]));
+    if (d < 0 || d > nd) return false;
+    double m = s / E.inv_p10[d];
+    if (m >= 10.0 && d < nd) {
+        m /= 10.0;
+        d += 1;
+    }
+    if (m < 1.0 && d > 0) {
+        m *= 10.0;
+        d -= 1;
+    }
+    const double r = (m - 1.0) * K / 9.0;
+    int j = (int)floor(r);
+    j = max(0, min(j, K - 1));
+    const long long i = (long long)d * K + j;
+    if (i < 0 || i > (long long)K * nd - 1) return false;
+    int ix[4];
+    double t[4];
+    ix[0] = (int)i;
+    t[0] = r - j;
+    if (!(t[0] >= 0.0 && t[0] <= 1.0)) return false;
+    const double dxr = 2.0 * E.inv_xmax / (nx - 1);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double rr = (n[q] / s + E.inv_xmax) / dxr;
+        if (!(rr >= 0.0 && rr <= (double)(nx - 1))) return false;
+        const int k = min((int)floor(rr), nx - 2);
+        ix[1 + q] = k;
+        t[1 + q] = rr - k;
+    }
+    x[0] = x[1] = x[2] = x[3] = 0.0;
+    const long long ns = (long long)K * nd + 1;
+    for (int corner = 0; corner < 16; ++corner) {
+        const int b0 = (corner >> 3) & 1, b1 = (corner >> 2) & 1, b2 = (corner >> 1) & 1, b3 = corner & 1;
+        const long long node = (((long long)(ix[0] + b0) * nx + ix[1] + b1) * nx + ix[2] + b2) * nx + ix[3] + b3;
+        const double w = (b0 ? t[0] : 1.0 - t[0]) * (b1 ? t[1] : 1.0 - t[1]) * (b2 ? t[2] : 1.0 - t[2]) *
+                         (b3 ? t[3] : 1.0 - t[3]);
+        const double2 *v = reinterpret_cast<const double2 *>(E.inv + 4 * node);
+        const double2 a = __ldg(v), b = __ldg(v + 1);
+        if (!isfinite(a.x)) return false;
+        x[0] = fma(w, a.x, x[0]);
+        x[1] = fma(w, a.y, x[1]);
+        x[2] = fma(w, b.x, x[2]);
+        x[3] = fma(w, b.y, x[3]);
+    }
+    (void)ns;
+    return true;
+}
+
 struct EosOut {
     double T, mu[3], p, e, ps, pn[3], cs2;
     uint32_t st;
@@ -353,7 +408,8 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
     double x[4];
     double H[4][4];
     bool use_table = false, hx = false;
-    if (E.has_table && guess[0] > 0.0 && inside_table(E, guess)) {
+    if (E.offline && E.has_table && inv_lookup(E, s, n, x) && inside_table(E, x)) use_table = true;
+    if (!use_table && E.has_table && guess[0] > 0.0 && inside_table(E, guess)) {
         double xt[4] = {guess[0], guess[1], guess[2], guess[3]};
         if (tab_newton(E, s, n, xt, w, H, &hx)) {
 #pragma unroll

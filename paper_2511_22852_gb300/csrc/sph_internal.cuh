@@ -59,6 +59,13 @@ struct EosDev {
     const double *sn;
     const double *p;
     double tol;
+    // offline inverter (Sec. "Equation of state"): (T, mu) on a grid in s (log decades,
+    // node i at s_i = inv_p10[i / inv_K] (1 + 9 (i % inv_K) / inv_K)) times the charge ratios
+    // n_q / s (inv_nx nodes on [-inv_xmax, inv_xmax]); used when offline = 1
+    const double *inv;
+    const double *inv_p10;
+    int inv_K, inv_nd, inv_nx, offline;
+    double inv_xmax;
 };
 
 struct TransportDev {
@@ -397,6 +404,9 @@ inline void tiled_shell(double h, float &lo, float &hi)
     lo = l;
     hi = g;
 }
+
+// offline inverter: fills the inverted table of E's grid (density_eos.cu)
+void launch_inverse_build(const EosDev &E, double *inv, long long nnodes, cudaStream_t st);
 
 // EoS handle accessors (api.cu)
 EosDev eos_params(const ::sph_eos *e);

@@ -573,3 +573,35 @@ def test_stress_event_fp64_and_mixed(Bd):
     bad = Bd.PST_NOCONV | Bd.PST_NONFINITE
     assert not np.any(a["STATUS"] & bad) and not np.any(b["STATUS"] & bad)
     assert np.max(np.abs(a["U"])) > 0  # the jets and pressure gradients moved the fluid
+
+
+def test_offline_inverter_matches_oracle(Bd):
+    """SPH_EOS_OFFLINE: the inverted table built on the device by the online root finder, then
+    interpolated -- the oracle's offline inverter on the same grid, to the step and evolution
+    tolerances; and the mode takes effect (the results differ from the online inversion)."""
+    ev = I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS)
+    ev.inverse = I.InverseGrid(per_decade=90, nx=17, xmax=0.12)
+    g = Bd.GpuEvent(ev)
+    run = O.OracleRun.start(ev)
+    aux, _ = run.observe()
+    f = g.read(("T", "MU", "P"))
+    A = O.AUX
+    assert relerr(f["T"], aux[A["T"]]) < TOL_STEP and relerr(f["P"], aux[A["p"]]) < TOL_STEP
+    assert relerr(f["MU"], aux[A["muB"]:A["muQ"] + 1]) < TOL_STEP
+    online = O.OracleRun.start(I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS)).observe()[0]
+    assert relerr(f["T"], online[A["T"]]) > 1e-6
+    g.step(1, sync=True)
+    run.step(1)
+    st = g.read(("X", "U", "S", "BV", "PV"))
+    assert relerr(st["U"], run.y[2:4]) < TOL_STEP and relerr(st["S"], run.y[4]) < TOL_STEP
+    g.step(9, sync=True)
+    run.step(9)
+    st = g.read(("X", "U", "S", "BV", "PV"))
+    assert relerr(st["U"], run.y[2:4]) < TOL_EVOL and relerr(st["PV"], run.y[6:9]) < TOL_EVOL
+    g.free()
+    ev2 = I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS)
+    g2 = Bd.GpuEvent(ev2)
+    with pytest.raises(Bd.SphError) as e:
+        Bd.sph_set_eos_mode(g2.h, Bd.SPH_EOS_OFFLINE)
+    assert e.value.code == Bd.SPH_ERR_STATE
+    g2.free()
