@@ -263,6 +263,42 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
     }
 
 
+def bench_mixed_single(Bd, I, steps: int = 50):
+    """The 40k-particle event in the mixed-precision forms: the per-event SPH_MIXED path (warp
+    per particle neighbour passes) and the serving form holding this one event (cell-tiled
+    passes, one CUDA graph per batch step); device or wall ms per step after warm-up."""
+    import torch
+    ev = I.viscous_bsq_2p1()
+    st = torch.cuda.Stream()
+    g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream, precision=Bd.SPH_MIXED)
+    g.step(3, sync=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        a.record(st)
+        g.step(steps)
+        b.record(st)
+    torch.cuda.synchronize()
+    per_event = a.elapsed_time(b) / steps
+    g.free()
+    srv = Bd.GpuServer(ev.eos, ev.table, max_events=2, max_particles=1 << 17)
+    t = srv.submit(ev, steps + 8)
+    srv.pump(4)
+    srv.autotune(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    srv.pump(steps)
+    torch.cuda.synchronize()
+    served = 1e3 * (time.perf_counter() - t0) / steps
+    srv.drain(60.0)
+    srv.collect(t, names=("T",))
+    srv.free()
+    return {"workload": "40k-particle viscous BSQ event, mixed precision", "per_event_ms_per_step": per_event,
+            "per_event_particle_steps_per_s": ev.n / (per_event / 1e3),
+            "serving_one_event_ms_per_step": served,
+            "serving_one_event_particle_steps_per_s": ev.n / (served / 1e3),
+            "note": "per-event: CUDA events; serving: wall clock over pumped batch steps (host pacing included)"}
+
+
 def bench_freezeout(Bd, I, steps: int = 40):
     """Cost of recording the freeze-out surface on the 40k-particle event: device ms per step
     with and without recording (CUDA graphs, CUDA events), and the elements recorded, for a
@@ -556,6 +592,7 @@ def run_ours(args):
                                "profile_mode_group_ms_per_step": total_ms / kp}}
         if not args.no_serving:
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
+        out["mixed_single_event"] = bench_mixed_single(Bd, I)
         out["freezeout"] = bench_freezeout(Bd, I)
         out["offline_eos"] = bench_offline_eos(Bd, I)
         if not args.no_3d:
