@@ -207,6 +207,7 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
     lat_closed = [srv.poll(t)[1] for t in tk]
     makespan = max(lat_closed)  # every event submitted at t0
     wall_closed = time.perf_counter() - t0
+    torch.cuda.synchronize()
     st1 = srv.stats()
     ew = np.zeros(3)
     for t in tk:
@@ -250,6 +251,8 @@ def serving_bench(Bd, I, nevents: int, ksteps: int, load: float = 0.7, max_event
         "closed_loop": {"makespan_s": makespan, "wall_s": wall_closed, "p50_s": float(np.median(lat_closed)),
                         "p99_s": float(np.percentile(lat_closed, 99)),
                         "batch_steps": st1["batch_steps"] - st0["batch_steps"],
+                        "device_s_of_batch_steps": 1e-3 * (st1["device_ms"] - st0["device_ms"]),
+                        "device_particle_steps_per_s": ps / max(1e-9, 1e-3 * (st1["device_ms"] - st0["device_ms"])),
                         "kernel_launches": st1["kernel_launches"] - st0["kernel_launches"]},
         "open_loop": {"arrivals": f"Poisson, rate {load:.2f} x closed-loop capacity = {load * cap_eps:.2f} events/s",
                       "p50_s": float(np.median(lat_open)), "p99_s": float(np.percentile(lat_open, 99)),

@@ -349,6 +349,9 @@ typedef struct {
     int64_t arena_capacity, arena_in_use; /* particles */
     int64_t kernel_launches;       /* kernels launched by the server (graph replays included) */
     int32_t slots_in_use, max_events;
+    double device_ms;              /* device time of the batch steps completed so far (CUDA events
+                                      around each step's graph launch) */
+    int64_t steps_timed;           /* batch steps included in device_ms */
 } sph_server_stats;
 
 /* Errors: SPH_ERR_ARG (max_events outside 1..256, bad fractions), SPH_ERR_OOM (arena

@@ -86,7 +86,8 @@ class ServerDesc(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ["queued", "running", "done", "batch_steps", "particle_steps",
                                          "arena_capacity", "arena_in_use", "kernel_launches"]] + \
-               [("slots_in_use", C.c_int32), ("max_events", C.c_int32)]
+               [("slots_in_use", C.c_int32), ("max_events", C.c_int32), ("device_ms", C.c_double),
+                ("steps_timed", C.c_int64)]
 
 
 _lib = None

@@ -273,10 +273,19 @@ static sph_status wait_stream(sph_event *ev)
     }
 }
 
+// device-to-host copy behind a bounded wait: a copy into pageable memory blocks the host until
+// the stream has drained, so the stream is waited on (with the event's limit) before the copy
+static sph_status fetch(sph_event *ev, void *dst, const void *src, size_t bytes)
+{
+    sph_status s = wait_stream(ev);
+    if (s != SPH_OK) return s;
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ev->stream));
+    return wait_stream(ev);
+}
+
 static sph_status check_device_flags(sph_event *ev, DevScalars *hs)
 {
-    CK(cudaMemcpyAsync(hs, ev->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ev->stream));
-    sph_status s = wait_stream(ev);
+    sph_status s = fetch(ev, hs, ev->sc, sizeof(DevScalars));
     if (s != SPH_OK) return s;
     if (hs->err_flags & ERR_CELL_OVERFLOW)
         return fail(SPH_ERR_STATE, "particles spread beyond the cell table fixed at sph_init_event");
@@ -629,7 +638,8 @@ sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags)
 
 static sph_status copy_out(sph_event *ev, void *dst, const void *src, size_t bytes, int on_device)
 {
-    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ev->stream));
+    if (!on_device) return fetch(ev, dst, src, bytes);
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ev->stream));
     return wait_stream(ev);
 }
 
@@ -693,7 +703,7 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
             launch_scatter_orig(dens + 5 * N, ev->scratch, ev->id[1], n, 1, st);
             if ((s = copy_out(ev, u0.data(), ev->scratch, dn, 0)) != SPH_OK) return s;
             DevScalars hs;
-            CK(cudaMemcpy(&hs, ev->sc, sizeof(hs), cudaMemcpyDeviceToHost));
+            if ((s = fetch(ev, &hs, ev->sc, sizeof(hs))) != SPH_OK) return s;
             double sqrtg = ev->milne ? hs.tau : 1.0;
             std::vector<double> Pi(n);
             for (int i = 0; i < n; ++i) Pi[i] = ev->viscous ? sg[i] / (u0[i] * sqrtg) * bv[i] : 0.0;
@@ -733,15 +743,17 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
             launch_totals(v, ev->Y[1], ev->Nq[1], ev->id[1], dens, eo, ev->scratch, st);
             launch_sum_fixed(ev->scratch, n, 2, ev->tot, st);
             double h2[2], hn[3];
-            CK(cudaMemcpyAsync(h2, ev->tot, sizeof(h2), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(hn, ev->ntot, sizeof(hn), cudaMemcpyDeviceToHost, st));
-            sph_status s = check_device_flags(ev, &hs);
+            sph_status s = fetch(ev, h2, ev->tot, sizeof(h2));
+            if (s != SPH_OK) return s;
+            if ((s = fetch(ev, hn, ev->ntot, sizeof(hn))) != SPH_OK) return s;
+            s = check_device_flags(ev, &hs);
             if (s != SPH_OK && s != SPH_ERR_EOS_RANGE && s != SPH_ERR_EOS_NOCONV && s != SPH_ERR_NONFINITE) return s;
             tot->E = h2[0];
             tot->S = h2[1];
             for (int q = 0; q < 3; ++q) tot->N[q] = hn[q];
         } else {
-            CK(cudaMemcpy(&hs, ev->sc, sizeof(hs), cudaMemcpyDeviceToHost));
+            sph_status s = fetch(ev, &hs, ev->sc, sizeof(hs));
+            if (s != SPH_OK) return s;
         }
         tot->tau = hs.tau;
         tot->work = hs.work;
@@ -895,18 +907,15 @@ sph_status sph_read_freezeout(sph_event *ev, int64_t cap, double *elems, int64_t
     if (!ev->fo_on) return fail(SPH_ERR_STATE, "freeze-out recording is off (sph_freezeout_setup)");
     if (cap > 0 && (!elems || !ids)) return fail(SPH_ERR_ARG, "null destination");
     unsigned long long total = 0;
-    CK(cudaMemcpyAsync(&total, ev->fo.count, sizeof(total), cudaMemcpyDeviceToHost, ev->stream));
-    sph_status s = wait_stream(ev);
+    sph_status s = fetch(ev, &total, ev->fo.count, sizeof(total));
     if (s != SPH_OK) return s;
     *count = (int64_t)total;
     const size_t m = (size_t)std::min<unsigned long long>(total, ev->fo.cap);
     if (cap <= 0 || m == 0) return total > ev->fo.cap ? fail(SPH_ERR_STATE, "freeze-out buffer overflowed") : SPH_OK;
     std::vector<double> rec(m * kFoRec);
     std::vector<long long> idv(m);
-    CK(cudaMemcpyAsync(rec.data(), ev->fo.rec, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, ev->stream));
-    CK(cudaMemcpyAsync(idv.data(), ev->fo.ids, sizeof(long long) * m, cudaMemcpyDeviceToHost, ev->stream));
-    s = wait_stream(ev);
-    if (s != SPH_OK) return s;
+    if ((s = fetch(ev, rec.data(), ev->fo.rec, sizeof(double) * rec.size())) != SPH_OK) return s;
+    if ((s = fetch(ev, idv.data(), ev->fo.ids, sizeof(long long) * m)) != SPH_OK) return s;
     std::vector<size_t> ord(m);
     for (size_t k = 0; k < m; ++k) ord[k] = k;
     std::sort(ord.begin(), ord.end(), [&](size_t p, size_t q) {
@@ -998,8 +1007,8 @@ sph_status sph_debug_neighbors(sph_event *ev, int64_t cap, int32_t *pa, int32_t 
     launch_neighbors_list(v, ev->Y[1], ev->id[1], ev->cb, nullptr, d_cnt, nullptr, st);
     launch_scan_counts(d_cnt, d_off, n, st);
     long long total = 0;
-    CK(cudaMemcpyAsync(&total, d_off + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    sph_status s = wait_stream(ev);
+    // on a timed-out wait the scratch stays allocated: freeing it would block until the device is idle
+    sph_status s = fetch(ev, &total, d_off + n, sizeof(long long));
     if (s != SPH_OK) return s;
     int *d_pa = nullptr, *d_pb = nullptr;
     CK(cudaMalloc(&d_pa, sizeof(int) * (total > 0 ? total : 1)));
@@ -1007,8 +1016,8 @@ sph_status sph_debug_neighbors(sph_event *ev, int64_t cap, int32_t *pa, int32_t 
     launch_neighbors_list(v, ev->Y[1], ev->id[1], ev->cb, d_off, d_pa, d_pb, st);
     std::vector<int> ha(total), hb(total);
     if (total > 0) {
-        CK(cudaMemcpyAsync(ha.data(), d_pa, sizeof(int) * total, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hb.data(), d_pb, sizeof(int) * total, cudaMemcpyDeviceToHost, st));
+        if ((s = fetch(ev, ha.data(), d_pa, sizeof(int) * total)) != SPH_OK) return s;
+        if ((s = fetch(ev, hb.data(), d_pb, sizeof(int) * total)) != SPH_OK) return s;
     }
     s = wait_stream(ev);
     cudaFree(d_cnt);

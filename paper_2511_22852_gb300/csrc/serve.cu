@@ -918,7 +918,9 @@ struct sph_server {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     std::vector<cudaEvent_t> step_ev;
-    long long steps_launched = 0;
+    std::vector<cudaEvent_t> step_t0;  // timing events at the start of each batch step (same ring)
+    long long steps_launched = 0, steps_timed = 0;
+    double device_ms = 0.0;            // device time of the completed batch steps
     cudaEvent_t ref_ev = nullptr;
     double ref_host = 0.0;
     // statistics
@@ -1137,15 +1139,34 @@ void release_ticket(sph_server *S, Ticket *t)
     delete t;
 }
 
+// adds the device time of completed batch steps (their start/end events) to device_ms
+void account_steps(sph_server *S)
+{
+    const long long R = (long long)S->step_ev.size();
+    while (S->steps_timed < S->steps_launched) {
+        const size_t i = (size_t)(S->steps_timed % R);
+        if (cudaEventQuery(S->step_ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, S->step_t0[i], S->step_ev[i]) == cudaSuccess) S->device_ms += ms;
+        else cudaGetLastError();
+        ++S->steps_timed;
+    }
+}
+
 sph_status batch_step(sph_server *S)
 {
     // pacing: at most `inflight` steps ahead of the device
     const long long k = S->steps_launched;
     cudaEvent_t ev = S->step_ev[(size_t)(k % (long long)S->step_ev.size())];
+    cudaEvent_t ev0 = S->step_t0[(size_t)(k % (long long)S->step_ev.size())];
     if (k >= (long long)S->step_ev.size()) {
         sph_status s = wait_event(S, ev);
         if (s != SPH_OK) return s;
     }
+    account_steps(S);
     if (k >= S->inflight) {
         cudaEvent_t back = S->step_ev[(size_t)((k - S->inflight) % (long long)S->step_ev.size())];
         sph_status s = wait_event(S, back);
@@ -1162,6 +1183,7 @@ sph_status batch_step(sph_server *S)
         S->graph = g;
         SCK(cudaGraphInstantiate(&S->gexec, g, 0));
     }
+    SCK(cudaEventRecord(ev0, S->st));
     SCK(cudaGraphLaunch(S->gexec, S->st));
     SCK(cudaEventRecord(ev, S->st));
     S->steps_launched += 1;
@@ -1333,12 +1355,14 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     S->slots.assign(S->max_events, SegSlot{SLOT_FREE, 0, 0, 0});
     S->slot_owner.assign(S->max_events, nullptr);
     S->step_ev.resize(16, nullptr);
-    for (auto &e : S->step_ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            e = nullptr;
-            return bail(sfail(SPH_ERR_CUDA, "cudaEventCreate failed"));
-        }
+    S->step_t0.resize(16, nullptr);
+    for (auto *ring : {&S->step_ev, &S->step_t0})
+        for (auto &e : *ring)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                e = nullptr;
+                return bail(sfail(SPH_ERR_CUDA, "cudaEventCreate failed"));
+            }
     // launch shapes: persistent grids of resident blocks on every SM
     int dev = 0, sms = 0, occ_e = 6;
     cudaGetDevice(&dev);
@@ -1375,6 +1399,8 @@ void sph_server_free(sph_server *S)
     if (S->gexec) cudaGraphExecDestroy(S->gexec);
     if (S->graph) cudaGraphDestroy(S->graph);
     for (auto e : S->step_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : S->step_t0)
         if (e) cudaEventDestroy(e);
     if (S->ref_ev) cudaEventDestroy(S->ref_ev);
     for (void *p : S->allocs) cudaFree(p);
@@ -1601,6 +1627,9 @@ sph_status sph_server_stats_get(sph_server *S, sph_server_stats *o)
     o->arena_in_use = used;
     o->kernel_launches = S->launches;
     o->max_events = S->max_events;
+    account_steps(S);
+    o->device_ms = S->device_ms;
+    o->steps_timed = S->steps_timed;
     return SPH_OK;
 }
 

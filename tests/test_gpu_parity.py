@@ -605,3 +605,21 @@ def test_offline_inverter_matches_oracle(Bd):
         Bd.sph_set_eos_mode(g2.h, Bd.SPH_EOS_OFFLINE)
     assert e.value.code == Bd.SPH_ERR_STATE
     g2.free()
+
+
+def test_wait_limit_reports_timeout(Bd, monkeypatch):
+    """Failure detection without a GPU fault: a host wait limit far below the step's duration
+    makes a synchronous step return SPH_ERR_TIMEOUT (the device finishes its work normally; the
+    handle stays usable and is freed after its stream drains)."""
+    monkeypatch.setenv("SPH_WAIT_LIMIT_S", "0.000001")
+    ev = I.viscous_bsq_2p1()
+    g = Bd.GpuEvent(ev)
+    with pytest.raises(Bd.SphError) as e:
+        g.step(20, sync=True)
+    assert e.value.code == Bd.SPH_ERR_TIMEOUT
+    g.free()
+    monkeypatch.delenv("SPH_WAIT_LIMIT_S")
+    g2 = Bd.GpuEvent(ev)  # the default limit: the same call completes
+    g2.step(2, sync=True)
+    assert g2.totals()["steps"] == 2
+    g2.free()

@@ -196,3 +196,17 @@ def test_autotuner_keeps_results_and_counters(Bd):
     plain = serve_alone(Bd, evs[1], 12, max_events=4, max_particles=1 << 16)
     assert out[1]["totals"]["pairs"] == plain["totals"]["pairs"]
     assert np.array_equal(out[1]["NNB"], plain["NNB"])
+
+
+def test_server_wait_limit_reports_timeout(Bd, monkeypatch):
+    """The server's bounded waits: a wait limit far below a batch step's duration makes the pump
+    return SPH_ERR_TIMEOUT instead of blocking; the server is then freed cleanly."""
+    monkeypatch.setenv("SPH_WAIT_LIMIT_S", "0.000001")
+    ev = bsq(40000)
+    s = Bd.GpuServer(ev.eos, ev.table, max_events=2, max_particles=1 << 17, max_inflight=1)
+    s.submit(ev, 20)
+    with pytest.raises(Bd.SphError) as e:
+        for _ in range(10):
+            s.pump(1)
+    assert e.value.code == Bd.SPH_ERR_TIMEOUT
+    s.free()
