@@ -228,6 +228,35 @@ def gubser_ideal_2p1(n_side=51, half_width=5.0, h=0.5, tau0=1.0, dtau=0.01, nste
                  transport=Transport(viscous=False), meta={"dx": dx})
 
 
+def gubser_shifted_T_u(tau, x, y, eta, t0=0.5, q=1.0, T0_GeV=0.4):
+    """Ideal Gubser flow shifted in Minkowski time, t -> t + t0 (Sec. "Code validation", eqs.
+    tau_prime, shifted_viscous_Gubser_T/_ur/_utau/_ueta with H0 = 0): T(tau', r) in fm^-1 and the
+    contravariant (u^tau, u^x, u^y, u^eta) in Milne coordinates (tau, x, y, eta)."""
+    ch, sh = np.cosh(eta), np.sinh(eta)
+    taup = np.sqrt(tau * tau + 2.0 * t0 * tau * ch + t0 * t0)
+    T, utp, ux, uy = gubser_T_u(taup, x, y, q=q, T0_GeV=T0_GeV)
+    utau = utp * (tau + t0 * ch) / taup
+    ueta = -utp * t0 * sh / (tau * taup)
+    return T, utau, ux, uy, ueta
+
+
+def gubser_shifted_3p1(half_widths=(2.4, 2.4, 1.5), spacings=(0.2, 0.2, 0.1), h=0.4, tau0=1.0, t0=0.5,
+                       dtau=0.01, nsteps=20) -> Event:
+    """Config: ideal conformal 3+1D Milne flow with rapidity dependence, the Gubser solution
+    shifted by t0 in Minkowski time (q = 1/fm; T = 0.4 GeV at tau' = 1 fm, r = 0), on a box
+    lattice in (x, y, eta)."""
+    x = lattice_3d(half_widths, spacings)
+    n = x.shape[1]
+    T, utau, ux, uy, ueta = gubser_shifted_T_u(tau0, x[0], x[1], x[2], t0=t0)
+    eos = AnalyticEoS(a0=GUBSER_FSTAR / 3.0)
+    _, s, _ = _analytic_p_s_n(eos, T, np.zeros((3, n)))
+    S = s * utau * tau0 * spacings[0] * spacings[1] * spacings[2]
+    return Event(name="gubser_shifted_3p1", dim=3, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                 x=x, u=np.stack([ux, uy, ueta]), S=S, Nq=np.zeros((3, n)), Bv=np.zeros(n),
+                 Pv=np.zeros((5, n)), eos=eos, table=None, transport=Transport(viscous=False),
+                 meta={"spacings": spacings, "t0": t0})
+
+
 def disc_lattice(R: float, n_target: int):
     """Square lattice with spacing sqrt(pi R^2 / n_target), points with x^2 + y^2 <= R^2."""
     dx = math.sqrt(math.pi * R * R / n_target)

@@ -62,6 +62,7 @@ CASES3 = {
     "box_jet": lambda: I.uniform_box_3d(
         jets=I.JetTracks(tracks=np.array([[-0.6, 0.1, -0.05, 1.0, 0.0, 0.0, 1.0, 5.0 / I.HBARC]]), sigma=0.3)),
     "blob3_cart_jets": _blob3_jets,
+    "gubser_shifted3": lambda: I.gubser_shifted_3p1(t0=2.0),
 }
 
 
