@@ -32,11 +32,12 @@ METRIC = "SPH particle-steps/s"
 UNIT = "particle-steps/s"
 WORKLOAD = "viscous 2+1D BSQ single event, FP64: 40k particles, 64x32^3 EoS table, h=0.3 fm, dtau=0.005 fm"
 
-# algorithmic FP64 flops per accepted neighbour pair (fused multiply-add = 2):
-#   density : distance 5, sqrt 1, q 1, kernel polynomial 5, five accumulations 10          = 22
-#   gradient: distance 5, sqrt 1, q 1, kernel-derivative polynomial 3, 1/r and factor 2,
-#             dW vector 2, sum of dW 2, stress divergence 8, velocity gradient 8          = 32
-FLOPS_PER_PAIR = {"density": 22.0, "gradient": 32.0}
+# algorithmic FP64 flops per accepted ordered neighbour pair (fused multiply-add = 2), with the
+# kernel of each unordered pair evaluated once (its two ordered pairs share it):
+#   density : [distance 5, sqrt 1, q 1, kernel polynomial 5, kernel-derivative polynomial 3,
+#             1/r and factor 2] / 2 shared, five accumulations 10                           = 18.5
+#   gradient: dW vector 2, sum of dW 2, stress divergence 8, velocity gradient 8          = 20
+FLOPS_PER_PAIR = {"density": 18.5, "gradient": 20.0}
 # EoS inversion, per unit of work actually done (counted on the device):
 #   table residual + Jacobian evaluation (quadrilinear, 4 fields x 4 patches with derivatives,
 #   scaling) 460; 4x4 Gaussian elimination with pivoting 64; closed-form g(T), g'(T) 26
@@ -45,7 +46,7 @@ FLOPS_EOS = (460.0, 64.0, 26.0)
 FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes (read + write) per launch of the FP64 40k-event kernels, from one ncu capture of
 # the current kernels (profiles/ncu_fp64_kernels_viscous_bsq_40k.md); None once a kernel changes
-DRAM_BYTES_PER_LAUNCH = {"gradient": 2.922e6, "density": 2.917e6, "eos": 7.291e6, "eom": 13.04e6}
+DRAM_BYTES_PER_LAUNCH = {"gradient": None, "density": None, "eos": 7.291e6, "eom": 13.04e6}
 
 
 def dist_env():

@@ -209,7 +209,9 @@ typedef struct {
     double N[3];   /* sum_a N_qa (fixed-order sums: bitwise constant) */
     double work;   /* int dtau sum_a sqrt(-g) Gamma^0_{mu nu} T^{mu nu} / sigma* (Milne) */
     uint32_t status_or;
-    int32_t pad;
+    int32_t pair_overflows; /* plain 2D: stages (and read-out evaluations) whose neighbour pair
+                               lists overflowed their capacity and ran the per-particle passes
+                               instead (the lists then grow before the next step) */
     int64_t steps;
     int64_t pairs;          /* accepted neighbour pairs (self pairs included) summed over all stages */
     int64_t kernel_launches; /* kernels launched by sph_step so far (graph replays included) */

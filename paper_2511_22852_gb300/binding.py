@@ -72,7 +72,7 @@ class FieldBufs(C.Structure):
 
 class Totals(C.Structure):
     _fields_ = [("tau", C.c_double), ("E", C.c_double), ("S", C.c_double), ("N", C.c_double * 3),
-                ("work", C.c_double), ("status_or", C.c_uint32), ("pad", C.c_int32), ("steps", C.c_int64),
+                ("work", C.c_double), ("status_or", C.c_uint32), ("pair_overflows", C.c_int32), ("steps", C.c_int64),
                 ("pairs", C.c_int64), ("kernel_launches", C.c_int64), ("eos_work", C.c_int64 * 3),
                 ("shell_tests", C.c_int64)]
 
@@ -361,7 +361,7 @@ class GpuServer:
         sph_collect(self.h, ticket, mask, b, t)
         out["totals"] = {"tau": t.tau, "E": t.E, "S": t.S, "N": np.array(t.N[:]), "work": t.work,
                          "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs,
-                         "eos_work": tuple(t.eos_work[:]), "shell_tests": t.shell_tests}
+                         "eos_work": tuple(t.eos_work[:]), "shell_tests": t.shell_tests, "pair_overflows": t.pair_overflows}
         return out
 
     def stats(self) -> dict:
@@ -444,7 +444,7 @@ class GpuEvent:
         sph_read_fields(self.h, 0, None, t)
         return {"tau": t.tau, "E": t.E, "S": t.S, "N": np.array(t.N[:]), "work": t.work,
                 "status_or": t.status_or, "steps": t.steps, "pairs": t.pairs, "kernel_launches": t.kernel_launches,
-                "eos_work": tuple(t.eos_work[:]), "shell_tests": t.shell_tests}
+                "eos_work": tuple(t.eos_work[:]), "shell_tests": t.shell_tests, "pair_overflows": t.pair_overflows}
 
     def kernel_times(self):
         return sph_kernel_times(self.h)

@@ -97,6 +97,12 @@ struct sph_event {
     long long launches = 0;
     double timeout_s = 600.0;
     std::vector<void *> allocs;
+    // half-pair lists of the plain 2D neighbour passes (cb.pl): sized on the first step from the
+    // neighbour counts, grown after a stage whose lists overflowed (pair_ovf rose)
+    int kernels_per_step = 0;  // kernel nodes of one captured step (0: not counted yet)
+    bool pairs_off = false, pairs_grow = false;
+    unsigned int pair_ovf_seen = 0;
+    void *pair_mem = nullptr;
     // profile mode: CUDA events around every kernel group of a step
     bool profile = false;
     std::vector<cudaEvent_t> pev;  // 2 per (group, stage)
@@ -107,8 +113,6 @@ struct sph_event {
 // kernel groups timed in profile mode
 enum { G_CELLS = 0, G_PERMUTE, G_DENSITY, G_EOS, G_GRADIENT, G_EOM, G_WORK, G_COUNT };
 static const char *kGroupNames[G_COUNT] = {"cells", "permute", "density", "eos", "gradient", "eom", "work"};
-// kernels per stage: bbox (2), cells/scan/scatter/rank (4), permute, density, eos, gradient, eom, work
-constexpr int kKernelsPerStage = 12;
 
 static inline void mark(sph_event *ev, int group, int stage, int end)
 {
@@ -287,6 +291,11 @@ static sph_status check_device_flags(sph_event *ev, DevScalars *hs)
 {
     sph_status s = fetch(ev, hs, ev->sc, sizeof(DevScalars));
     if (s != SPH_OK) return s;
+    if (hs->pair_ovf > ev->pair_ovf_seen) {  // a stage overflowed the pair lists: grow them
+        ev->pair_ovf_seen = hs->pair_ovf;
+        ev->pairs_grow = true;
+    }
+    if (hs->err_flags & ERR_PAIR_LIST) return fail(SPH_ERR_STATE, "inconsistent neighbour pair lists");
     if (hs->err_flags & ERR_CELL_OVERFLOW)
         return fail(SPH_ERR_STATE, "particles spread beyond the cell table fixed at sph_init_event");
     uint32_t bad = hs->status_or & ev->fatal_mask;
@@ -395,6 +404,7 @@ void sph_free_event(sph_event *ev)
     if (ev->graph) cudaGraphDestroy(ev->graph);
     for (cudaEvent_t e : ev->pev) cudaEventDestroy(e);
     for (void *p : ev->allocs) cudaFree(p);
+    if (ev->pair_mem) cudaFree(ev->pair_mem);
     if (ev->own_stream && ev->stream) cudaStreamDestroy(ev->stream);
     sph_free_eos(ev->eos);
     delete ev;
@@ -599,11 +609,132 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     return SPH_OK;
 }
 
+// Sizes (or grows) the half-pair lists of the plain 2D passes: capacity per particle = 1.25 x the
+// largest neighbour count of the current state + 32, a multiple of 32 (at least 1.5 x the old
+// capacity when growing).  The lists stay off (the per-particle passes run) for other forms, when
+// SPH_PAIR_LISTS=0, or when they would take more than a quarter of the free device memory.
+// SPH_PAIR_CAP=<c> fixes the capacity (tests of the overflow path).
+static sph_status size_pair_lists(sph_event *ev)
+{
+    if (ev->pairs_off || ev->dim != 2 || ev->mixed || ev->n == 0) return SPH_OK;
+    if (ev->cb.pl.cap > 0 && !ev->pairs_grow) return SPH_OK;
+    if (const char *t = getenv("SPH_PAIR_LISTS"))
+        if (atoi(t) == 0) {
+            ev->pairs_off = true;
+            return SPH_OK;
+        }
+    const int n = ev->n;
+    long long cap;
+    if (const char *t = getenv("SPH_PAIR_CAP")) {
+        cap = atoll(t);
+        if (ev->pairs_grow) cap = std::max<long long>(cap, (long long)ev->cb.pl.cap * 3 / 2);
+    } else {
+        // the neighbour counts of the current state (a read-out evaluation, which leaves the
+        // warm start and the step state alone)
+        if (!ev->observed) {
+            enqueue_observe(ev);
+            CK(cudaGetLastError());
+            ev->observed = true;
+        }
+        std::vector<int> h(n);
+        sph_status s = fetch(ev, h.data(), ev->nnb, sizeof(int) * (size_t)n);
+        if (s != SPH_OK) return s;
+        int mx = 1;
+        for (int i = 0; i < n; ++i) mx = std::max(mx, h[i]);
+        cap = ((long long)mx * 5 / 4 + 32 + 31) / 32 * 32;
+        if (ev->pairs_grow) cap = std::max<long long>(cap, ((long long)ev->cb.pl.cap * 3 / 2 + 31) / 32 * 32);
+    }
+    cap = std::max<long long>(cap, 1);
+    const size_t rows = (size_t)n * (size_t)cap;
+    const size_t bytes = rows * (3 * sizeof(int) + 2 * sizeof(double)) + 2 * sizeof(int) * (size_t)n + 1024;
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    if (cap > 0x7FFFFFFF || bytes > fr / 4) {
+        ev->pairs_off = true;
+        ev->pairs_grow = false;
+        return SPH_OK;
+    }
+    CK(cudaStreamSynchronize(ev->stream));  // the old lists may still be in use
+    if (ev->pair_mem) {
+        cudaFree(ev->pair_mem);
+        ev->pair_mem = nullptr;
+        ev->cb.pl = PairBufs{};
+    }
+    void *m = nullptr;
+    if (cudaMalloc(&m, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ev->pairs_off = true;
+        ev->pairs_grow = false;
+        return SPH_OK;
+    }
+    ev->pair_mem = m;
+    char *b = static_cast<char *>(m);
+    PairBufs pl{};
+    pl.cap = (int)cap;
+    pl.W = reinterpret_cast<double *>(b);
+    pl.FAC = pl.W + rows;
+    pl.F = reinterpret_cast<int *>(pl.FAC + rows);
+    pl.B = pl.F + rows;
+    pl.P = pl.B + rows;
+    pl.cntF = pl.P + rows;
+    pl.cntB = pl.cntF + n;
+    ev->cb.pl = pl;
+    ev->pairs_grow = false;
+    ev->kernels_per_step = 0;
+    // the captured step holds the old buffers
+    if (ev->gexec) cudaGraphExecDestroy(ev->gexec);
+    if (ev->graph) cudaGraphDestroy(ev->graph);
+    ev->gexec = nullptr;
+    ev->graph = nullptr;
+    ev->graph_ready = false;
+    ev->kernels_per_step = 0;
+    return SPH_OK;
+}
+
+static int kernel_nodes(cudaGraph_t g)
+{
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+// kernels launched by one step: counted on a capture of the step's launch sequence
+static sph_status count_step_kernels(sph_event *ev)
+{
+    if (ev->kernels_per_step > 0) return SPH_OK;
+    if (ev->graph) {
+        ev->kernels_per_step = kernel_nodes(ev->graph);
+        return SPH_OK;
+    }
+    CK(cudaStreamBeginCapture(ev->stream, cudaStreamCaptureModeThreadLocal));
+    const bool prof = ev->profile;
+    ev->profile = false;  // no event records in the counting capture
+    enqueue_step(ev);
+    ev->profile = prof;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ev->stream, &g);
+    if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    ev->kernels_per_step = kernel_nodes(g);
+    cudaGraphDestroy(g);
+    return SPH_OK;
+}
+
 sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags)
 {
     if (!ev) return fail(SPH_ERR_ARG, "null event");
     if (nsteps < 0) return fail(SPH_ERR_ARG, "nsteps < 0");
     if (ev->n == 0 || nsteps == 0) return SPH_OK;
+    {
+        sph_status s = size_pair_lists(ev);
+        if (s != SPH_OK) return s;
+    }
     if (ev->use_graph && !ev->graph_ready) {
         CK(cudaStreamBeginCapture(ev->stream, cudaStreamCaptureModeThreadLocal));
         enqueue_step(ev);
@@ -627,7 +758,11 @@ sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags)
     }
     CK(cudaGetLastError());
     ev->host_steps += nsteps;
-    ev->launches += (long long)nsteps * (2 * kKernelsPerStage + (ev->fo_on ? 1 : 0));
+    {
+        sph_status s = count_step_kernels(ev);
+        if (s != SPH_OK) return s;
+    }
+    ev->launches += (long long)nsteps * ev->kernels_per_step;
     ev->observed = false;
     if (flags & SPH_SYNC) {
         DevScalars hs;
@@ -758,6 +893,7 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         tot->tau = hs.tau;
         tot->work = hs.work;
         tot->status_or = hs.status_or;
+        tot->pair_overflows = (int32_t)hs.pair_ovf;
         tot->steps = hs.steps;
         tot->pairs = (int64_t)hs.pairs;
         tot->eos_work[0] = (int64_t)hs.eos_resid;
@@ -825,6 +961,7 @@ sph_status sph_set_eos_mode(sph_event *ev, int32_t mode)
         ev->graph = nullptr;
     }
     ev->graph_ready = false;
+    ev->kernels_per_step = 0;
     ev->observed = false;
     return SPH_OK;
 }
@@ -855,6 +992,7 @@ sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, dou
         ev->graph = nullptr;
     }
     ev->graph_ready = false;
+    ev->kernels_per_step = 0;
     ev->observed = false;
     return SPH_OK;
 }
@@ -897,6 +1035,7 @@ sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity)
         ev->graph = nullptr;
     }
     ev->graph_ready = false;
+    ev->kernels_per_step = 0;
     return SPH_OK;
 }
 

@@ -49,8 +49,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
                                                           const double *__restrict__ Nq,
                                                           const uint32_t *__restrict__ start,
                                                           const uint32_t *__restrict__ cnt,
-                                                          double *__restrict__ dens, int *__restrict__ nnb)
+                                                          double *__restrict__ dens, int *__restrict__ nnb,
+                                                          int fallback)
 {
+    // fallback = 1: the pair-list passes ran first; this pass only runs if one of their lists
+    // overflowed (and counts such stages)
+    if (fallback) {
+        if (!v.sc->pair_flag) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&v.sc->pair_ovf, 1u);
+    }
     __shared__ int queue[kWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int a = blockIdx.x * kWarps + wid;
@@ -313,7 +320,9 @@ void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs
         return;
     }
     k_fpos<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos);
-    k_density2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb);
+    const int lists = cb.pl.cap > 0;
+    if (lists) launch_pairs_density(v, y, Nq, cb, dens, nnb, st);
+    k_density2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb, lists);
 }
 
 void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,

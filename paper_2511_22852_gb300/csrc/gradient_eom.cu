@@ -34,8 +34,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_gradient2(EvView v, int stage, 
                                                            const float2 *__restrict__ fpos,
                                                            const double *__restrict__ gin,
                                                            const uint32_t *__restrict__ start,
-                                                           const uint32_t *__restrict__ cnt, double *__restrict__ gout)
+                                                           const uint32_t *__restrict__ cnt, double *__restrict__ gout,
+                                                           int fallback)
 {
+    if (fallback && !v.sc->pair_flag) return;  // the pair-list pass did the work
     __shared__ int queue[kWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int a = blockIdx.x * kWarps + wid;
@@ -392,7 +394,9 @@ void launch_gradient(const EvView &v, int stage, const double *y, const double *
         launch_gradient2m(v, stage, y, gin, cb, gout, st);
         return;
     }
-    k_gradient2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout);
+    const int lists = cb.pl.cap > 0;
+    if (lists) launch_pairs_gradient(v, stage, y, gin, cb, gout, st);
+    k_gradient2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout, lists);
 }
 
 void launch_eom(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,

@@ -112,7 +112,7 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     cudaStream_t st = (cudaStream_t)stream;
     const int nn = (int)n;
     DevScalars *sc = reinterpret_cast<DevScalars *>(b + kOffSc);
-    CellBufs cb;
+    CellBufs cb{};
     cb.key = reinterpret_cast<uint32_t *>(b + kOffKey);
     cb.tmp = reinterpret_cast<uint32_t *>(b + kOffTmp);
     cb.perm = reinterpret_cast<uint32_t *>(b + kOffPerm);

@@ -1,0 +1,338 @@
+// pairs2d.cu -- plain 2D neighbour passes over half-pair lists.
+//
+// The density sums (Sec. "SPH formalism": sigma*, s*, n*_q as kernel sums) and the gradient sums
+// (Sec. "SPH formalism", the n = 0 and n = -1 derivative forms) use W(r_ab) and dW/dr(r_ab) / r_ab
+// of every accepted pair; both depend on r_ab only, so they are the same for (a, b) and (b, a).
+// Each stage's forward density pass evaluates them once per unordered pair -- on the pairs
+// b > a of particle a (sorted index) -- and keeps them with the pair; the backward pass and the
+// gradient pass then add every pair's contribution to both of its particles without evaluating
+// the kernel again.  All sums run in a fixed order (a warp per particle, lanes over its list in
+// ascending neighbour index, then a fixed butterfly), so results are reproducible run to run; they
+// differ from the per-particle passes only in the order of the additions.
+//
+// Per pair the FP64 work of the two passes drops from about 126 operations (two kernel
+// evaluations with the sums of each side, in each of the two passes) to about 67.
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+namespace {
+
+constexpr int kWarps = 4;  // particles (warps) per block
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// cells of the 3x3 block around (cx, cy) inside the grid, in ascending Morton key, so that their
+// particles come in ascending sorted index
+__device__ __forceinline__ int block_cells_ascending(int cx, int cy, int lim, uint32_t keys[9])
+{
+    int nk = 0;
+    for (int oy = -1; oy <= 1; ++oy) {
+        const int ny = cy + oy;
+        if (ny < 0 || ny >= lim) continue;
+        for (int ox = -1; ox <= 1; ++ox) {
+            const int nx = cx + ox;
+            if (nx < 0 || nx >= lim) continue;
+            const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+            int j = nk++;
+            while (j > 0 && keys[j - 1] > k) {
+                keys[j] = keys[j - 1];
+                --j;
+            }
+            keys[j] = k;
+        }
+    }
+    return nk;
+}
+
+// Forward density pass, one warp per particle a.  Candidates of the 3x3 cells pass the
+// single-precision prefilter; a neighbour b < a is decided at once (exact FP64 test when the
+// float test left it undecided) and listed in B; a candidate b > a is queued, and 32 at a time
+// the exact test, W and dW/dr / r run on full warps, are listed in F/W/FAC and summed for a.
+// dpart receives a's unscaled partial sums (self pair and pairs b > a): sigma*, S, N_B, N_S, N_Q.
+__global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, const double *__restrict__ y,
+                                                                   const float2 *__restrict__ fpos,
+                                                                   const double *__restrict__ Nq,
+                                                                   const uint32_t *__restrict__ start,
+                                                                   const uint32_t *__restrict__ cnt, PairBufs pl,
+                                                                   double *__restrict__ dpart)
+{
+    __shared__ int queue[kWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarps + wid;
+    if (a >= v.n) return;  // warp-uniform
+    int *q = queue[wid];
+    const int n = v.n;
+    const double *X = y, *Y = y + n, *S = y + 4 * (size_t)n;
+    const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
+    const double xa = X[a], ya = Y[a];
+    const float2 fa = fpos[a];
+    const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+    const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+    uint32_t keys[9];
+    const int nk = block_cells_ascending(cx, cy, 1 << v.B, keys);
+    const unsigned lt = (1u << lane) - 1u;
+    const int cap = pl.cap;
+    const size_t row = (size_t)a * cap;
+    int *F = pl.F + row, *Bl = pl.B + row;
+    double *Wr = pl.W + row, *Fr = pl.FAC + row;
+    double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
+    if (lane == 0) {  // the self pair, W(0)
+        const double w0 = kernel_w(0.0);
+        sg = w0;
+        ss = S[a] * w0;
+        sb = NB[a] * w0;
+        sS = NS[a] * w0;
+        sq = NQ[a] * w0;
+    }
+    int nf = 0, nbk = 0, qn = 0;
+    // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
+    auto forward = [&](int qb, bool valid) {
+        const int b = qb & 0x7FFFFFFF;
+        double dx = 0.0, dy = 0.0;
+        bool acc = false;
+        if (valid) {
+            dx = xa - X[b];
+            dy = ya - Y[b];
+            acc = qb >= 0 || dist2_2d(dx, dy) < v.supp2;
+        }
+        const unsigned m = __ballot_sync(kFull, acc);
+        if (acc) {
+            const double r2 = fma(dx, dx, dy * dy);
+            double w = kernel_w(0.0), fac = 0.0;  // coincident particles: W(0), no gradient
+            if (r2 > 0.0) {
+                const double ir = inv_sqrt(r2);
+                const double qq = r2 * ir * v.inv_h;
+                w = kernel_w(qq);
+                fac = kernel_dw(qq) * ir;
+            }
+            const int slot = nf + __popc(m & lt);
+            if (slot < cap) {
+                F[slot] = b;
+                Wr[slot] = w;
+                Fr[slot] = fac;
+            }
+            sg += w;
+            ss = fma(S[b], w, ss);
+            sb = fma(NB[b], w, sb);
+            sS = fma(NS[b], w, sS);
+            sq = fma(NQ[b], w, sq);
+        }
+        nf += __popc(m);
+    };
+    for (int kc = 0; kc < nk; ++kc) {
+        const uint32_t k = keys[kc];
+        const uint32_t b0 = start[k], b1 = b0 + cnt[k];
+        for (uint32_t base = b0; base < b1; base += 32) {
+            const uint32_t b = base + lane;
+            bool cand = false, sure = false;
+            if (b < b1 && b != (uint32_t)a) {
+                const float2 fb = fpos[b];
+                const float dx = fa.x - fb.x, dy = fa.y - fb.y;
+                const float r2f = fmaf(dx, dx, dy * dy);
+                cand = r2f <= v.supp2_hi;
+                sure = r2f < v.supp2_lo;
+            }
+            // b < a: decided here and listed; its pair values come from b's own forward pass
+            bool accB = false;
+            if (cand && (int)b < a) accB = sure || dist2_2d(xa - X[b], ya - Y[b]) < v.supp2;
+            const unsigned mb = __ballot_sync(kFull, accB);
+            if (accB) {
+                const int slot = nbk + __popc(mb & lt);
+                if (slot < cap) Bl[slot] = (int)b;
+            }
+            nbk += __popc(mb);
+            // b > a: queued in arrival (ascending) order for the FP64 pair arithmetic
+            const bool fw = cand && (int)b > a;
+            const unsigned m = __ballot_sync(kFull, fw);
+            if (fw) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                forward(q[lane], true);
+                qn -= 32;
+                __syncwarp();
+                if (lane < qn) q[lane] = q[32 + lane];
+                __syncwarp();
+            }
+        }
+    }
+    if (qn > 0) forward(lane < qn ? q[lane] : 0, lane < qn);
+    for (int o = 16; o > 0; o >>= 1) {
+        sg += __shfl_xor_sync(kFull, sg, o);
+        ss += __shfl_xor_sync(kFull, ss, o);
+        sb += __shfl_xor_sync(kFull, sb, o);
+        sS += __shfl_xor_sync(kFull, sS, o);
+        sq += __shfl_xor_sync(kFull, sq, o);
+    }
+    if (lane == 0) {
+        dpart[a] = sg;
+        dpart[(size_t)n + a] = ss;
+        dpart[2 * (size_t)n + a] = sb;
+        dpart[3 * (size_t)n + a] = sS;
+        dpart[4 * (size_t)n + a] = sq;
+        pl.cntF[a] = nf;
+        pl.cntB[a] = nbk;
+        if (nf > cap || nbk > cap) atomicOr(&v.sc->pair_flag, 1u);
+    }
+}
+
+// Backward density pass, one warp per particle a: the pairs (b, a) with b < a, whose W the
+// forward pass of b stored; the slot is found by binary search of a in b's ascending list and
+// kept in P for the gradient pass.  Completes a's sums (forward partial + backward partial) and
+// writes the density rows as the per-particle pass does.
+__global__ void __launch_bounds__(32 * kWarps) k_pairs_density_bwd(EvView v, const double *__restrict__ y,
+                                                                   const double *__restrict__ Nq, PairBufs pl,
+                                                                   double *__restrict__ dens, int *__restrict__ nnb)
+{
+    if (v.sc->pair_flag) return;  // a list overflowed: the per-particle pass runs instead
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarps + wid;
+    if (a >= v.n) return;  // warp-uniform
+    const int n = v.n;
+    const double *S = y + 4 * (size_t)n;
+    const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
+    const int cap = pl.cap;
+    const size_t row = (size_t)a * cap;
+    const int nb = pl.cntB[a];
+    double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < nb) {
+            const int b = pl.B[row + j];
+            const int *Fb = pl.F + (size_t)b * cap;
+            const int nfb = pl.cntF[b];
+            int lo = 0, hi = nfb;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (Fb[mid] < a) lo = mid + 1;
+                else hi = mid;
+            }
+            // both sides take the same acceptance decision (the float and the exact test see
+            // exactly negated differences), so a is in b's list; checked all the same
+            if (lo >= nfb || Fb[lo] != a) {
+                atomicOr(&v.sc->err_flags, ERR_PAIR_LIST);
+                lo = 0;
+            }
+            pl.P[row + j] = lo;
+            const double w = nfb > 0 ? pl.W[(size_t)b * cap + lo] : 0.0;
+            sg += w;
+            ss = fma(S[b], w, ss);
+            sb = fma(NB[b], w, sb);
+            sS = fma(NS[b], w, sS);
+            sq = fma(NQ[b], w, sq);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sg += __shfl_xor_sync(kFull, sg, o);
+        ss += __shfl_xor_sync(kFull, ss, o);
+        sb += __shfl_xor_sync(kFull, sb, o);
+        sS += __shfl_xor_sync(kFull, sS, o);
+        sq += __shfl_xor_sync(kFull, sq, o);
+    }
+    if (lane == 0) {
+        const double sd = v.sigma_d;
+        const size_t N = (size_t)n;
+        const double ux = y[2 * N + a], uy = y[3 * N + a];
+        dens[a] = sd * (dens[a] + sg);  // the forward partials were left in the density rows
+        dens[N + a] = sd * (dens[N + a] + ss);  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
+        dens[2 * N + a] = sd * (dens[2 * N + a] + sb);
+        dens[3 * N + a] = sd * (dens[3 * N + a] + sS);
+        dens[4 * N + a] = sd * (dens[4 * N + a] + sq);
+        dens[5 * N + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+        const int c = 1 + pl.cntF[a] + nb;
+        nnb[a] = c;
+        atomicAdd(&v.sc->pairs, (unsigned long long)c);
+    }
+}
+
+// Gradient pass, one warp per particle a, over its pairs b > a (F, FAC in a's row) and then
+// b < a (B, with FAC at b's row, slot P): grad_a W_ab = FAC (x_a - x_b) sigma_d / h, then the
+// sums of the per-particle pass: sum grad W, sum X_b grad W, sum u_b grad W.
+__global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int stage, const double *__restrict__ y,
+                                                                const double *__restrict__ gin, PairBufs pl,
+                                                                double *__restrict__ gout)
+{
+    if (v.sc->pair_flag) return;  // a list overflowed: the per-particle pass runs instead
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarps + wid;
+    if (a >= v.n) return;  // warp-uniform
+    const int n = v.n;
+    const double *X = y, *Y = y + n;
+    const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
+    const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
+    const double xa = X[a], ya = Y[a];
+    const int cap = pl.cap;
+    const size_t row = (size_t)a * cap;
+    const int nf = pl.cntF[a], nt = nf + pl.cntB[a];
+    double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
+    double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
+    for (int j0 = 0; j0 < nt; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < nt) {
+            int b;
+            double fac;
+            if (j < nf) {
+                b = pl.F[row + j];
+                fac = pl.FAC[row + j];
+            } else {
+                b = pl.B[row + (j - nf)];
+                fac = pl.FAC[(size_t)b * cap + pl.P[row + (j - nf)]];
+            }
+            const double dx = xa - X[b], dy = ya - Y[b];
+            const double gx = fac * dx, gy = fac * dy;
+            Gx += gx;
+            Gy += gy;
+            Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));
+            Hy = fma(Xxy[b], gx, fma(Xyy[b], gy, Hy));
+            const double ubx = Ux[b], uby = Uy[b];
+            dxux = fma(ubx, gx, dxux);
+            dxuy = fma(uby, gx, dxuy);
+            dyux = fma(ubx, gy, dyux);
+            dyuy = fma(uby, gy, dyuy);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        Gx += __shfl_xor_sync(kFull, Gx, o);
+        Gy += __shfl_xor_sync(kFull, Gy, o);
+        Hx += __shfl_xor_sync(kFull, Hx, o);
+        Hy += __shfl_xor_sync(kFull, Hy, o);
+        dxux += __shfl_xor_sync(kFull, dxux, o);
+        dxuy += __shfl_xor_sync(kFull, dxuy, o);
+        dyux += __shfl_xor_sync(kFull, dyux, o);
+        dyuy += __shfl_xor_sync(kFull, dyuy, o);
+    }
+    if (lane == 0) {
+        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+        const double sqrtg = v.milne ? tau : 1.0;
+        const double c = v.sigma_d * v.inv_h;
+        gout[a] = c * dxux;
+        gout[(size_t)n + a] = c * dxuy;
+        gout[2 * (size_t)n + a] = c * dyux;
+        gout[3 * (size_t)n + a] = c * dyuy;
+        const double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
+        const double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
+        gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
+        gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+    }
+}
+
+inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+void launch_pairs_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                          cudaStream_t st)
+{
+    // the forward partials go to the density rows, which the backward pass completes in place
+    k_pairs_density_fwd<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, cb.pl,
+                                                                   dens);
+    k_pairs_density_bwd<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, Nq, cb.pl, dens, nnb);
+}
+
+void launch_pairs_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb,
+                           double *gout, cudaStream_t st)
+{
+    k_pairs_gradient<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, stage, y, gin, cb.pl, gout);
+}
+
+}  // namespace sphg

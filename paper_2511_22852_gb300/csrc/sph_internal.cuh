@@ -29,6 +29,7 @@ constexpr uint32_t PST_FALLBACK = 1u, PST_OUT_OF_TABLE = 2u, PST_NOCONV = 4u, PS
                    PST_CS2_CAPPED = 16u, PST_SOLVE_FAIL = 32u;
 // event-level device error bits
 constexpr uint32_t ERR_CELL_OVERFLOW = 1u;
+constexpr uint32_t ERR_PAIR_LIST = 2u;  // a backward pair missing from its partner's forward list
 
 constexpr int kNDens = 6, kNEos = 11, kNGin = 6, kNGout = 6;
 
@@ -47,6 +48,11 @@ struct DevScalars {
     // 4x4 solves, closed-form g(T) evaluations
     unsigned long long eos_resid, eos_solve, eos_g;
     unsigned long long shell_tests;  // mixed form: candidates that needed the exact FP64 test
+    // pair-list neighbour passes (plain 2D): set when a particle's neighbours exceeded the list
+    // capacity in this stage (reset with the bounding box; the stage then runs the per-particle
+    // passes), and the number of stages that did so
+    unsigned int pair_flag;
+    unsigned int pair_ovf;
 };
 
 struct EosDev {
@@ -196,12 +202,25 @@ __device__ __forceinline__ void warp_or(unsigned int *dst, unsigned int v)
 
 // ---------------------------------------------------------------------------
 // launchers (implemented in cells.cu, density_eos.cu, gradient_eom.cu)
+// Half-pair lists of the plain 2D neighbour passes, rebuilt in every stage's density pass.
+// Particle a (sorted index) owns rows [a cap, a cap + cap) of F, B, P, W, FAC:
+//   F: its accepted neighbours b > a, ascending; W, FAC: W(r)/sigma_d and (dW/dr)/r * h/sigma_d
+//      of each such pair (the kernel values are symmetric in a, b, so each is computed once);
+//   B: its accepted neighbours b < a, ascending; P: the index in F/W/FAC of the pair (b, a).
+// cap = 0: lists off (the per-particle passes run).
+struct PairBufs {
+    int cap;
+    int *F, *B, *P, *cntF, *cntB;
+    double *W, *FAC;
+};
+
 struct CellBufs {
     uint32_t *key, *cnt, *start, *cursor, *tmp, *perm;
     float2 *fpos;   // 2D: sorted positions relative to the bounding-box minimum, single precision
     float4 *fpos3;  // 3D: the same with three coordinates
     uint32_t *part; // scan partial sums (multi-block scan of large bucket tables)
     int nb;         // number of buckets: 1 << (2 B) in 2D, 1 << (B3[0] + B3[1] + B3[2]) in 3D
+    PairBufs pl;    // plain 2D: half-pair lists (pl.cap = 0: off)
 };
 
 // Bound for the single-precision candidate prefilter of the neighbour passes.  With
@@ -240,6 +259,11 @@ void launch_bbox(const EvView &v, const double *y, cudaStream_t st);
 void launch_cells(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st);
 void launch_permute(const EvView &v, const uint32_t *perm, const double *const *src, double *const *dst,
                     const int *nrows, int ngroups, const int *id_in, int *id_out, cudaStream_t st);
+// plain 2D neighbour passes over the half-pair lists (cb.pl.cap > 0)
+void launch_pairs_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                          cudaStream_t st);
+void launch_pairs_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb,
+                           double *gout, cudaStream_t st);
 void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                     cudaStream_t st);
 void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,

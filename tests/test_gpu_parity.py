@@ -624,3 +624,56 @@ def test_wait_limit_reports_timeout(Bd, monkeypatch):
     g2.step(2, sync=True)
     assert g2.totals()["steps"] == 2
     g2.free()
+
+
+def test_pair_lists_match_per_particle_passes(Bd, monkeypatch):
+    """Plain 2D: the neighbour passes over half-pair lists (the kernel of each pair evaluated once
+    and added to both particles) and the per-particle passes (SPH_PAIR_LISTS=0) form the same sums
+    in another order: states agree to rounding, pair counts exactly, and both follow the oracle."""
+    ev = CASES["bsq_small"]()
+    g = Bd.GpuEvent(ev)
+    g.step(5, sync=True)
+    monkeypatch.setenv("SPH_PAIR_LISTS", "0")
+    g0 = Bd.GpuEvent(ev)
+    g0.step(5, sync=True)
+    names = ("X", "U", "S", "BV", "PV", "T", "SIGMA_STAR")
+    a, b = g.read(names), g0.read(names)
+    for k in names:
+        assert relerr(a[k], b[k]) < 1e-13, (k, relerr(a[k], b[k]))
+    t, t0 = g.totals(), g0.totals()
+    assert t["pair_overflows"] == 0 and t0["pair_overflows"] == 0
+    assert t["kernel_launches"] == 5 * 32 and t0["kernel_launches"] == 5 * 26  # 16 and 13 per stage
+    # the lists were sized by one read-out evaluation (its pairs are counted): compare one step
+    g.step(1, sync=True)
+    g0.step(1, sync=True)
+    assert g.totals()["pairs"] - t["pairs"] == g0.totals()["pairs"] - t0["pairs"] > 0
+    run = O.OracleRun.start(ev)
+    run.step(6)
+    errs = state_errors(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    g.free()
+    g0.free()
+
+
+def test_pair_list_overflow_falls_back_then_grows(Bd, monkeypatch):
+    """Lists too small for the neighbour counts (capacity 64 against ~120 neighbours): the stage
+    runs the per-particle passes (the result still follows the oracle), the overflow is counted,
+    and the lists grow at the next step until they fit."""
+    monkeypatch.setenv("SPH_PAIR_CAP", "64")
+    ev = CASES["bsq_small"]()
+    g = Bd.GpuEvent(ev)
+    run = O.OracleRun.start(ev)
+    g.step(1, sync=True)
+    run.step(1)
+    assert g.totals()["pair_overflows"] >= 2  # both stages (and the read-out evaluation of totals)
+    errs = state_errors(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    seen = []
+    for _ in range(5):
+        g.step(1, sync=True)
+        seen.append(g.totals()["pair_overflows"])
+    run.step(5)
+    assert seen[-1] == seen[-2] == seen[-3], seen  # the grown lists fit
+    errs = state_errors(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    g.free()
