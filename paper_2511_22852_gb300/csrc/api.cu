@@ -568,7 +568,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     AL(ev->wguess_obs, dv * 4);
     AL(ev->status, sizeof(uint32_t) * N);
     AL(ev->nnb, sizeof(int) * N);
-    ev->nwblk = eom_block_count(n > 0 ? n : 1);
+    ev->nwblk = eos_block_count(n > 0 ? n : 1, ev->dim);
     AL(ev->wpart, sizeof(double) * (size_t)ev->nwblk);
     AL(ev->scratch, dv * std::max(std::max(ev->nv, kNEos), ev->ngout));
     AL(ev->ntot, sizeof(double) * (8 + 3 * 256));

@@ -28,13 +28,17 @@ namespace sphg {
 
 namespace {
 
-// single-precision positions relative to the bounding-box minimum (prefilter input)
-__global__ void k_fpos(EvView v, const double *__restrict__ y, float2 *__restrict__ fpos)
+// single-precision positions relative to the bounding-box minimum (prefilter input), and
+// u0 = sqrt(1 + u.u) (density row 5), one thread per particle
+__global__ void k_fpos(EvView v, const double *__restrict__ y, float2 *__restrict__ fpos, double *__restrict__ dens)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= v.n) return;
     double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
     fpos[j] = make_float2(__double2float_rn(__dsub_rn(y[j], xmin0)), __double2float_rn(__dsub_rn(y[v.n + j], xmin1)));
+    const size_t N = (size_t)v.n;
+    const double ux = y[2 * N + j], uy = y[3 * N + j];
+    dens[5 * N + j] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
 }
 
 constexpr int kWarps = 4;  // warps (particles in flight) per block of the neighbour passes
@@ -222,13 +226,14 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     return wcontrib;
 }
 
-__global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const double *__restrict__ y,
+// One warp per block: the pass holds 40k-particle events in a fraction of a wave, and with
+// blocks of one warp the blocks (and the varying Newton work) spread more evenly over the SMs.
+__global__ void __launch_bounds__(32, 12) k_eos2(EvView v, int stage, const double *__restrict__ y,
                                              double *__restrict__ dens, double *__restrict__ eos,
                                              double *__restrict__ gin, uint32_t *__restrict__ status,
                                              double *__restrict__ wpart, const double *__restrict__ guess_in,
                                              double *__restrict__ guess_out)
 {
-    __shared__ double red[2];
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     double wcontrib = 0.0;
     EosWork w = {0u, 0u, 0u};
@@ -245,9 +250,7 @@ __global__ void __launch_bounds__(64, 6) k_eos2(EvView v, int stage, const doubl
         atomicAdd(&v.sc->eos_g, (unsigned long long)wg);
     }
     for (int o = 16; o > 0; o >>= 1) wcontrib += __shfl_xor_sync(0xFFFFFFFFu, wcontrib, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wcontrib;
-    __syncthreads();
-    if (threadIdx.x == 0) wpart[blockIdx.x] = red[0] + red[1];
+    if (threadIdx.x == 0) wpart[blockIdx.x] = wcontrib;
 }
 
 // Serving form: the same EoS pass over the segmented arena.  Persistent blocks claim chunks
@@ -319,7 +322,7 @@ void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs
         launch_density2m(v, y, Nq, cb, dens, nnb, st);
         return;
     }
-    k_fpos<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos);
+    k_fpos<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos, dens);
     const int lists = cb.pl.cap > 0;
     if (lists) launch_pairs_density(v, y, Nq, cb, dens, nnb, st);
     k_density2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb, lists);
@@ -332,11 +335,11 @@ void launch_eos(const EvView &v, int stage, const double *y, const double *dens,
         launch_eos3(v, stage, y, dens, eos, gin, status, wpart, guess_in, guess_out, st);
         return;
     }
-    k_eos2<<<nblk(v.n, 64), 64, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart, guess_in,
+    k_eos2<<<nblk(v.n, 32), 32, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart, guess_in,
                                          guess_out);
 }
 
-int eom_block_count(int n) { return nblk(n, 64); }
+int eos_block_count(int n, int dim) { return nblk(n, dim == 2 ? 32 : 64); }
 
 // Offline inverter: every node (s_i, x_j) of the inverted table solved by the online inversion
 // started cold (closed form, then table Newton), as the offline procedure uses the existing

@@ -100,10 +100,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
             const double r2 = fma(dx, dx, dy * dy);
             double w = kernel_w(0.0), fac = 0.0;  // coincident particles: W(0), no gradient
             if (r2 > 0.0) {
+                // the cubic spline without a branch on q: w = (2-q)^3/4 - max(1-q, 0)^3,
+                // w' = -3/4 (2-q)^2 + 3 max(1-q, 0)^2 (the same polynomials on both pieces)
                 const double ir = inv_sqrt(r2);
                 const double qq = r2 * ir * v.inv_h;
-                w = kernel_w(qq);
-                fac = kernel_dw(qq) * ir;
+                const double t = 2.0 - qq, u = fmax(1.0 - qq, 0.0);
+                const double t2 = t * t, u2 = u * u;
+                w = fma(0.25 * t2, t, -(u2 * u));
+                fac = fma(-0.75, t2, 3.0 * u2) * ir;
             }
             const int slot = nf + __popc(m & lt);
             if (slot < cap) {
@@ -157,19 +161,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
         }
     }
     if (qn > 0) forward(lane < qn ? q[lane] : 0, lane < qn);
-    for (int o = 16; o > 0; o >>= 1) {
-        sg += __shfl_xor_sync(kFull, sg, o);
-        ss += __shfl_xor_sync(kFull, ss, o);
-        sb += __shfl_xor_sync(kFull, sb, o);
-        sS += __shfl_xor_sync(kFull, sS, o);
-        sq += __shfl_xor_sync(kFull, sq, o);
-    }
+    const double vals[8] = {sg, ss, sb, sS, sq, 0.0, 0.0, 0.0};
+    const double tot = warp_reduce_scatter8(vals, lane);
+    const int k = lane >> 2;
+    if ((lane & 3) == 0 && k < 5) dpart[(size_t)k * n + a] = tot;
     if (lane == 0) {
-        dpart[a] = sg;
-        dpart[(size_t)n + a] = ss;
-        dpart[2 * (size_t)n + a] = sb;
-        dpart[3 * (size_t)n + a] = sS;
-        dpart[4 * (size_t)n + a] = sq;
         pl.cntF[a] = nf;
         pl.cntB[a] = nbk;
         if (nf > cap || nbk > cap) atomicOr(&v.sc->pair_flag, 1u);
@@ -222,23 +218,16 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_bwd(EvView v, con
             sq = fma(NQ[b], w, sq);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        sg += __shfl_xor_sync(kFull, sg, o);
-        ss += __shfl_xor_sync(kFull, ss, o);
-        sb += __shfl_xor_sync(kFull, sb, o);
-        sS += __shfl_xor_sync(kFull, sS, o);
-        sq += __shfl_xor_sync(kFull, sq, o);
+    const double vals[8] = {sg, ss, sb, sS, sq, 0.0, 0.0, 0.0};
+    const double tot = warp_reduce_scatter8(vals, lane);
+    const int k = lane >> 2;
+    if ((lane & 3) == 0 && k < 5) {
+        // rows sigma*, lab-frame s* (divided by u0 sqrt(-g) in the EoS pass), n*_B, n*_S, n*_Q:
+        // the forward partials were left in the density rows; u0 (row 5) is written by k_fpos
+        double *d = dens + (size_t)k * n + a;
+        *d = v.sigma_d * (*d + tot);
     }
     if (lane == 0) {
-        const double sd = v.sigma_d;
-        const size_t N = (size_t)n;
-        const double ux = y[2 * N + a], uy = y[3 * N + a];
-        dens[a] = sd * (dens[a] + sg);  // the forward partials were left in the density rows
-        dens[N + a] = sd * (dens[N + a] + ss);  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
-        dens[2 * N + a] = sd * (dens[2 * N + a] + sb);
-        dens[3 * N + a] = sd * (dens[3 * N + a] + sS);
-        dens[4 * N + a] = sd * (dens[4 * N + a] + sq);
-        dens[5 * N + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
         const int c = 1 + pl.cntF[a] + nb;
         nnb[a] = c;
         atomicAdd(&v.sc->pairs, (unsigned long long)c);
@@ -291,28 +280,22 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int st
             dyuy = fma(uby, gy, dyuy);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        Gx += __shfl_xor_sync(kFull, Gx, o);
-        Gy += __shfl_xor_sync(kFull, Gy, o);
-        Hx += __shfl_xor_sync(kFull, Hx, o);
-        Hy += __shfl_xor_sync(kFull, Hy, o);
-        dxux += __shfl_xor_sync(kFull, dxux, o);
-        dxuy += __shfl_xor_sync(kFull, dxuy, o);
-        dyux += __shfl_xor_sync(kFull, dyux, o);
-        dyuy += __shfl_xor_sync(kFull, dyuy, o);
-    }
-    if (lane == 0) {
-        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-        const double sqrtg = v.milne ? tau : 1.0;
+    const double vals[8] = {Gx, Gy, Hx, Hy, dxux, dxuy, dyux, dyuy};
+    const double tot = warp_reduce_scatter8(vals, lane);
+    // totals: lanes 0, 4: sum grad W (x, y); 8, 12: sum X_b grad W (x, y); 16..28: sum u_b grad W
+    const double Sx = __shfl_sync(kFull, tot, 0), Sy = __shfl_sync(kFull, tot, 4);
+    const int k = lane >> 2;
+    if ((lane & 3) == 0 && k >= 2) {
         const double c = v.sigma_d * v.inv_h;
-        gout[a] = c * dxux;
-        gout[(size_t)n + a] = c * dxuy;
-        gout[2 * (size_t)n + a] = c * dyux;
-        gout[3 * (size_t)n + a] = c * dyuy;
-        const double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
-        const double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
-        gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
-        gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+        if (k >= 4) {
+            gout[(size_t)(k - 4) * n + a] = c * tot;  // d_x u^x, d_x u^y, d_y u^x, d_y u^y
+        } else {
+            // minus the stress divergence: X_a . sum grad W + sum X_b grad W, times sqrt(-g)
+            const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+            const double sqrtg = v.milne ? tau : 1.0;
+            const double X0 = k == 2 ? Xxx[a] : Xxy[a], X1 = k == 2 ? Xyx[a] : Xyy[a];
+            gout[(size_t)(k + 2) * n + a] = -sqrtg * c * (X0 * Sx + X1 * Sy + tot);
+        }
     }
 }
 

@@ -165,6 +165,33 @@ __device__ __forceinline__ double dist2_2d(double dx, double dy) { return __dadd
 // 1/sqrt(x) for x > 0 in double precision: CUDA's rsqrt (at most 1 ulp of error)
 __device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
 
+// Warp sum of up to 8 per-lane values by recursive halving (a reduce-scatter): at each of the
+// first three levels a lane keeps half of its values and adds its partner's copy of them, then
+// two butterfly levels finish one value.  9 additions per lane instead of 5 per value for a full
+// butterfly -- on the 1:64 FP64 pipe a warp-wide addition costs as much as 32 lanes of pair
+// work.  Returns, in lanes 4k .. 4k+3, the warp total of v[k]; the order of the additions is
+// fixed, so results are reproducible.
+__device__ __forceinline__ double warp_reduce_scatter8(const double (&v)[8], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    double h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double keep = b4 ? v[4 + i] : v[i], give = b4 ? v[i] : v[4 + i];
+        h[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, 16);
+    }
+    double g[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double keep = b3 ? h[2 + i] : h[i], give = b3 ? h[i] : h[2 + i];
+        g[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, 8);
+    }
+    double f = (b2 ? g[1] : g[0]) + __shfl_xor_sync(0xFFFFFFFFu, b2 ? g[0] : g[1], 4);
+    f += __shfl_xor_sync(0xFFFFFFFFu, f, 2);
+    f += __shfl_xor_sync(0xFFFFFFFFu, f, 1);
+    return f;
+}
+
 // cubic spline kernel (Sec. "Kernel function") as functions of q = r/h:
 // W = sigma_d w(q), dW/dr = sigma_d/h w'(q)
 __device__ __forceinline__ double kernel_w(double q)
@@ -283,7 +310,7 @@ void launch_sum_fixed(const double *vals, int n, int nfield, double *out, cudaSt
 void launch_scatter_orig(const double *src, double *dst, const int *id, int n, int nrows, cudaStream_t st);
 void launch_scatter_orig_u32(const uint32_t *src, uint32_t *dst, const int *id, int n, cudaStream_t st);
 void launch_cell_coords(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
-int eom_block_count(int n);
+int eos_block_count(int n, int dim);  // blocks of the EoS pass (entries of its work-rate partials)
 
 // mixed-precision 2D neighbour passes (mixed2d.cu); dispatched when v.mixed
 void launch_density2m(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
