@@ -103,8 +103,8 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
 }
 
 // ---------------------------------------------------------------------------
-// table: quadrilinear interpolation evaluated as four bilinear (mu_S, mu_Q)
-// patches combined over (T, mu_B), carrying all four partial derivatives
+// table: the quadrilinear interpolant reduced one axis at a time (mu_Q, mu_S inside each of the
+// four (T, mu_B) corner patches, then mu_B, then T), carrying the partial derivatives along
 __device__ __forceinline__ void locate(double x, double x0, double inv, int nx, int &i, double &t)
 {
     double r = (x - x0) * inv;
@@ -114,8 +114,9 @@ __device__ __forceinline__ void locate(double x, double x0, double inv, int nx, 
     t = r - (double)k;
 }
 
-// sn: interpolated (s, nB, nS, nQ); J[f][k] = d sn_f / d x_k; p optional
-__device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double J[4][4], double *p)
+// sn: interpolated (s, nB, nS, nQ); J[f][k] = d sn_f / d x_k per grid step of axis k (times
+// inv_dT, inv_dmu[k-1] for the derivative per unit of x_k); p optional
+__device__ void tab_eval_steps(const EosDev &E, const double *x, double sn[4], double J[4][4], double *p)
 {
     int iT, iB, iS, iQ;
     double tT, tB, tS, tQ;
@@ -124,47 +125,67 @@ __device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double 
     locate(x[2], E.mu0[1], E.inv_dmu[1], E.nmu[1], iS, tS);
     locate(x[3], E.mu0[2], E.inv_dmu[2], E.nmu[2], iQ, tQ);
     const int n3 = E.nmu[2], n23 = E.nmu[1] * E.nmu[2], n123 = E.nmu[0] * n23;
-    for (int f = 0; f < 4; ++f) {
-        sn[f] = 0.0;
-        for (int k = 0; k < 4; ++k) J[f][k] = 0.0;
-    }
-    double pv = 0.0;
-    for (int bT = 0; bT < 2; ++bT)
-        for (int bB = 0; bB < 2; ++bB) {
-            double wT = bT ? tT : 1.0 - tT, wB = bB ? tB : 1.0 - tB;
-            double dT = bT ? E.inv_dT : -E.inv_dT, dB = bB ? E.inv_dmu[0] : -E.inv_dmu[0];
-            size_t base = (size_t)(iT + bT) * n123 + (size_t)(iB + bB) * n23 + (size_t)iS * n3 + iQ;
-            const double2 *c00 = reinterpret_cast<const double2 *>(E.sn + 4 * base);
-            const double2 *c01 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + 1));
-            const double2 *c10 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + n3));
-            const double2 *c11 = reinterpret_cast<const double2 *>(E.sn + 4 * (base + n3 + 1));
-            double v00[4], v01[4], v10[4], v11[4];
-            double2 t;
-            t = __ldg(c00); v00[0] = t.x; v00[1] = t.y; t = __ldg(c00 + 1); v00[2] = t.x; v00[3] = t.y;
-            t = __ldg(c01); v01[0] = t.x; v01[1] = t.y; t = __ldg(c01 + 1); v01[2] = t.x; v01[3] = t.y;
-            t = __ldg(c10); v10[0] = t.x; v10[1] = t.y; t = __ldg(c10 + 1); v10[2] = t.x; v10[3] = t.y;
-            t = __ldg(c11); v11[0] = t.x; v11[1] = t.y; t = __ldg(c11 + 1); v11[2] = t.x; v11[3] = t.y;
-            double wTB = wT * wB;
-            for (int f = 0; f < 4; ++f) {
-                double a0 = v00[f] + tQ * (v01[f] - v00[f]);  // mu_S lower face
-                double a1 = v10[f] + tQ * (v11[f] - v10[f]);  // mu_S upper face
-                double val = a0 + tS * (a1 - a0);
-                double dS = (a1 - a0) * E.inv_dmu[1];
-                double dQ = ((v01[f] - v00[f]) + tS * ((v11[f] - v10[f]) - (v01[f] - v00[f]))) * E.inv_dmu[2];
-                sn[f] = fma(wTB, val, sn[f]);
-                J[f][0] = fma(dT * wB, val, J[f][0]);
-                J[f][1] = fma(wT * dB, val, J[f][1]);
-                J[f][2] = fma(wTB, dS, J[f][2]);
-                J[f][3] = fma(wTB, dQ, J[f][3]);
+    const size_t node0 = (size_t)iT * n123 + (size_t)iB * n23 + (size_t)iS * n3 + iQ;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {  // one field at a time: its 16 corner values
+        double lv[2], lb[2], ls[2], lq[2];  // [bT]: after the mu_B reduction
+#pragma unroll
+        for (int bT = 0; bT < 2; ++bT) {
+            double pv[2], ps[2], pq[2];  // [bB]: (mu_S, mu_Q) patch value, d/dS, d/dQ
+#pragma unroll
+            for (int bB = 0; bB < 2; ++bB) {
+                const size_t base = node0 + (size_t)bT * n123 + (size_t)bB * n23;
+                const double *c = E.sn + f;
+                const double c00 = __ldg(c + 4 * base), c01 = __ldg(c + 4 * (base + 1));
+                const double c10 = __ldg(c + 4 * (base + n3)), c11 = __ldg(c + 4 * (base + n3 + 1));
+                const double d0 = c01 - c00, d1 = c11 - c10;  // along mu_Q
+                const double a0 = fma(tQ, d0, c00), a1 = fma(tQ, d1, c10);
+                const double ds = a1 - a0;  // along mu_S
+                pv[bB] = fma(tS, ds, a0);
+                ps[bB] = ds;
+                pq[bB] = fma(tS, d1 - d0, d0);
             }
-            if (p) {
-                double p00 = __ldg(E.p + base), p01 = __ldg(E.p + base + 1), p10 = __ldg(E.p + base + n3),
-                       p11 = __ldg(E.p + base + n3 + 1);
-                double a0 = p00 + tQ * (p01 - p00), a1 = p10 + tQ * (p11 - p10);
-                pv = fma(wTB, a0 + tS * (a1 - a0), pv);
-            }
+            const double db = pv[1] - pv[0];  // along mu_B
+            lv[bT] = fma(tB, db, pv[0]);
+            lb[bT] = db;
+            ls[bT] = fma(tB, ps[1] - ps[0], ps[0]);
+            lq[bT] = fma(tB, pq[1] - pq[0], pq[0]);
         }
-    if (p) *p = pv;
+        const double dt = lv[1] - lv[0];  // along T
+        sn[f] = fma(tT, dt, lv[0]);
+        J[f][0] = dt;
+        J[f][1] = fma(tT, lb[1] - lb[0], lb[0]);
+        J[f][2] = fma(tT, ls[1] - ls[0], ls[0]);
+        J[f][3] = fma(tT, lq[1] - lq[0], lq[0]);
+    }
+    if (p) {
+        double lp[2];
+#pragma unroll
+        for (int bT = 0; bT < 2; ++bT) {
+            double pb[2];
+#pragma unroll
+            for (int bB = 0; bB < 2; ++bB) {
+                const size_t base = node0 + (size_t)bT * n123 + (size_t)bB * n23;
+                const double p00 = __ldg(E.p + base), p01 = __ldg(E.p + base + 1);
+                const double p10 = __ldg(E.p + base + n3), p11 = __ldg(E.p + base + n3 + 1);
+                const double a0 = fma(tQ, p01 - p00, p00), a1 = fma(tQ, p11 - p10, p10);
+                pb[bB] = fma(tS, a1 - a0, a0);
+            }
+            lp[bT] = fma(tB, pb[1] - pb[0], pb[0]);
+        }
+        *p = fma(tT, lp[1] - lp[0], lp[0]);
+    }
+}
+
+// the same with the derivatives per unit of (T, mu_B, mu_S, mu_Q)
+__device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double J[4][4], double *p)
+{
+    tab_eval_steps(E, x, sn, J, p);
+    const double sc[4] = {E.inv_dT, E.inv_dmu[0], E.inv_dmu[1], E.inv_dmu[2]};
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) J[f][k] *= sc[k];
 }
 
 // 4x4 Gaussian elimination with partial pivoting, fully unrolled so every index is a
@@ -231,14 +252,16 @@ __device__ __forceinline__ void clamp4(const EosDev &E, double *x)
 __device__ double resid(const EosDev &E, const double *x, double s, const double *n, double r[4], double J[4][4])
 {
     double sn[4];
-    tab_eval(E, x, sn, J, nullptr);
+    tab_eval_steps(E, x, sn, J, nullptr);
     double inv_s = 1.0 / s;
+    // J / s per unit of x: the grid-step scaling folded into the 1/s scaling
+    const double sc[4] = {E.inv_dT * inv_s, E.inv_dmu[0] * inv_s, E.inv_dmu[1] * inv_s, E.inv_dmu[2] * inv_s};
     double tgt[4] = {s, n[0], n[1], n[2]};
     double m = 0.0;
     for (int k = 0; k < 4; ++k) {
         r[k] = (sn[k] - tgt[k]) * inv_s;
         m = isfinite(r[k]) ? fmax(m, fabs(r[k])) : __longlong_as_double(0x7FF0000000000000LL);
-        for (int j = 0; j < 4; ++j) J[k][j] *= inv_s;
+        for (int j = 0; j < 4; ++j) J[k][j] *= sc[j];
     }
     return m;
 }
