@@ -593,6 +593,7 @@ def run_ours(args):
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                "wall_s_timed": t_wall, "status_or": int(status_or),
                "diagnostics": {"ms_per_step_without_l2_flush": noflush_ms,
+                               "pair_list_overflow_stages_timed": int(t_after["pair_overflows"] - t_before["pair_overflows"]),
                                "profile_mode_group_ms_per_step": total_ms / kp}}
         if not args.no_serving:
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)

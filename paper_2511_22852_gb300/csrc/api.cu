@@ -100,9 +100,13 @@ struct sph_event {
     // half-pair lists of the plain 2D neighbour passes (cb.pl): sized on the first step from the
     // neighbour counts, grown after a stage whose lists overflowed (pair_ovf rose)
     int kernels_per_step = 0;  // kernel nodes of one captured step (0: not counted yet)
-    bool pairs_off = false, pairs_grow = false;
+    bool pairs_off = false, pairs_grow = false, pairs_recount = false;
     unsigned int pair_ovf_seen = 0;
     void *pair_mem = nullptr;
+    int *pcnt[2] = {nullptr, nullptr};  // neighbour counts carried with the state (Y[0], Y1[0] order)
+    // pinned copy of the device's overflow counter, refreshed after every sph_step call and read
+    // (without a sync) at the next: the lists grow within a call of their first overflow
+    volatile unsigned int *pair_ovf_host = nullptr;
     // profile mode: CUDA events around every kernel group of a step
     bool profile = false;
     std::vector<cudaEvent_t> pev;  // 2 per (group, stage)
@@ -173,6 +177,16 @@ static void enqueue_sort(sph_event *ev, const EvView &v, const double *ysrc, con
     launch_cells(v, ysrc, idsrc, ev->cb, ev->stream);
 }
 
+// the cell buffers of a density pass: its pair-list rows are sized by the counts carried in
+// pcnt[src]; it records its own counts in pcnt[dst] (dst < 0: not recorded, read-outs)
+static CellBufs stage_cb(const sph_event *ev, int src, int dst)
+{
+    CellBufs cb = ev->cb;
+    cb.pl.cnt_src = ev->pcnt[src];
+    cb.pl.cnt_dst = dst >= 0 ? ev->pcnt[dst] : nullptr;
+    return cb;
+}
+
 static void enqueue_step(sph_event *ev)
 {
     EvView v = make_view(ev);
@@ -190,7 +204,7 @@ static void enqueue_step(sph_event *ev)
     }
     mark(ev, G_PERMUTE, 1, 1);
     mark(ev, G_DENSITY, 1, 0);
-    launch_density(v, ev->Y[1], ev->Nq[1], ev->cb, ev->dens, ev->nnb, st);
+    launch_density(v, ev->Y[1], ev->Nq[1], stage_cb(ev, 0, 1), ev->dens, ev->nnb, st);
     mark(ev, G_DENSITY, 1, 1);
     mark(ev, G_EOS, 1, 0);
     launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
@@ -219,7 +233,7 @@ static void enqueue_step(sph_event *ev)
     }
     mark(ev, G_PERMUTE, 2, 1);
     mark(ev, G_DENSITY, 2, 0);
-    launch_density(v, ev->Y1[1], ev->Nq[0], ev->cb, ev->dens, ev->nnb, st);
+    launch_density(v, ev->Y1[1], ev->Nq[0], stage_cb(ev, 1, 0), ev->dens, ev->nnb, st);
     mark(ev, G_DENSITY, 2, 1);
     mark(ev, G_EOS, 2, 0);
     launch_eos(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
@@ -260,7 +274,7 @@ static void enqueue_observe(sph_event *ev)
     double *dst[3] = {ev->Y[1], ev->Nq[1], ev->guess_in};
     int rows[3] = {ev->nv, 3, 4};
     launch_permute(v, ev->cb.perm, src, dst, rows, 3, ev->id[0], ev->id[1], st);
-    launch_density(v, ev->Y[1], ev->Nq[1], ev->cb, ev->dens, ev->nnb, st);
+    launch_density(v, ev->Y[1], ev->Nq[1], stage_cb(ev, 0, -1), ev->dens, ev->nnb, st);
     launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess_obs, st);
 }
 
@@ -405,6 +419,7 @@ void sph_free_event(sph_event *ev)
     for (cudaEvent_t e : ev->pev) cudaEventDestroy(e);
     for (void *p : ev->allocs) cudaFree(p);
     if (ev->pair_mem) cudaFree(ev->pair_mem);
+    if (ev->pair_ovf_host) cudaFreeHost((void *)ev->pair_ovf_host);
     if (ev->own_stream && ev->stream) cudaStreamDestroy(ev->stream);
     sph_free_eos(ev->eos);
     delete ev;
@@ -609,52 +624,65 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     return SPH_OK;
 }
 
-// Sizes (or grows) the half-pair lists of the plain 2D passes: capacity per particle = 1.25 x the
-// largest neighbour count of the current state + 32, a multiple of 32 (at least 1.5 x the old
-// capacity when growing).  The lists stay off (the per-particle passes run) for other forms, when
-// SPH_PAIR_LISTS=0, or when they would take more than a quarter of the free device memory.
-// SPH_PAIR_CAP=<c> fixes the capacity (tests of the overflow path).
+// Sizes (or grows) the half-pair lists of the plain 2D passes.  Each stage gives particle a a row
+// of (its previous neighbour count - 1 + margin) entries; the allocation holds 1.5 x those rows
+// for the current state (at least 1.5 x the old allocation when growing), margin = 32.  Counts
+// are carried from stage to stage in the state order (pcnt[0] with Y[0], pcnt[1] with Y1[0]);
+// here they are taken from a read-out evaluation of the current state.  The lists stay off (the
+// per-particle passes run) for other forms, when SPH_PAIR_LISTS=0, or when they would take more
+// than a quarter of the free device memory.  SPH_PAIR_MARGIN and SPH_PAIR_TOTAL override the
+// margin and the first allocation (tests of the overflow paths).
 static sph_status size_pair_lists(sph_event *ev)
 {
     if (ev->pairs_off || ev->dim != 2 || ev->mixed || ev->n == 0) return SPH_OK;
-    if (ev->cb.pl.cap > 0 && !ev->pairs_grow) return SPH_OK;
+    if (ev->cb.pl.total > 0 && ev->pair_ovf_host && *ev->pair_ovf_host > ev->pair_ovf_seen) {
+        ev->pair_ovf_seen = *ev->pair_ovf_host;
+        ev->pairs_grow = true;
+    }
+    if (ev->cb.pl.total > 0 && !ev->pairs_grow && !ev->pairs_recount) return SPH_OK;
     if (const char *t = getenv("SPH_PAIR_LISTS"))
         if (atoi(t) == 0) {
             ev->pairs_off = true;
             return SPH_OK;
         }
     const int n = ev->n;
-    long long cap;
-    if (const char *t = getenv("SPH_PAIR_CAP")) {
-        cap = atoll(t);
-        if (ev->pairs_grow) cap = std::max<long long>(cap, (long long)ev->cb.pl.cap * 3 / 2);
-    } else {
-        // the neighbour counts of the current state (a read-out evaluation, which leaves the
-        // warm start and the step state alone)
-        if (!ev->observed) {
-            enqueue_observe(ev);
-            CK(cudaGetLastError());
-            ev->observed = true;
-        }
-        std::vector<int> h(n);
-        sph_status s = fetch(ev, h.data(), ev->nnb, sizeof(int) * (size_t)n);
-        if (s != SPH_OK) return s;
-        int mx = 1;
-        for (int i = 0; i < n; ++i) mx = std::max(mx, h[i]);
-        cap = ((long long)mx * 5 / 4 + 32 + 31) / 32 * 32;
-        if (ev->pairs_grow) cap = std::max<long long>(cap, ((long long)ev->cb.pl.cap * 3 / 2 + 31) / 32 * 32);
+    int margin = 32;
+    if (const char *t = getenv("SPH_PAIR_MARGIN")) margin = std::max(0, atoi(t));
+    // neighbour counts of the current state, moved from the evaluation's sorted order to the state
+    // order (the sort's gather map: sorted j <- state perm[j])
+    enqueue_observe(ev);
+    CK(cudaGetLastError());
+    ev->observed = true;
+    std::vector<int> cnt(n), perm(n), state(n);
+    sph_status s = fetch(ev, cnt.data(), ev->nnb, sizeof(int) * (size_t)n);
+    if (s != SPH_OK) return s;
+    if ((s = fetch(ev, perm.data(), ev->cb.perm, sizeof(int) * (size_t)n)) != SPH_OK) return s;
+    long long rows = 0;
+    for (int j = 0; j < n; ++j) {
+        state[perm[j]] = cnt[j];
+        rows += std::max(cnt[j] - 1, 0) + margin;
     }
-    cap = std::max<long long>(cap, 1);
-    const size_t rows = (size_t)n * (size_t)cap;
-    const size_t bytes = rows * (3 * sizeof(int) + 2 * sizeof(double)) + 2 * sizeof(int) * (size_t)n + 1024;
+    if (ev->cb.pl.total > 0 && !ev->pairs_grow && rows <= ev->cb.pl.total) {
+        // recount only: the same allocation, counts of the new state
+        CK(cudaMemcpyAsync(ev->pcnt[0], state.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, ev->stream));
+        ev->pairs_recount = false;
+        return wait_stream(ev);
+    }
+    ev->pairs_recount = false;
+    long long total = rows * 3 / 2 + 1024;
+    if (ev->pairs_grow) total = std::max<long long>(total, ev->cb.pl.total * 3 / 2);
+    else if (const char *t = getenv("SPH_PAIR_TOTAL")) total = std::max<long long>(1, atoll(t));
+    const int nparts = (n + 2047) / 2048;
+    const size_t bytes = (size_t)total * (2 * sizeof(double) + 2 * sizeof(int)) + (size_t)(n + 1) * sizeof(long long) +
+                         (size_t)nparts * sizeof(unsigned long long) + 4 * sizeof(int) * (size_t)n + 1024;
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
-    if (cap > 0x7FFFFFFF || bytes > fr / 4) {
+    if (bytes > fr / 4) {
         ev->pairs_off = true;
         ev->pairs_grow = false;
         return SPH_OK;
     }
-    CK(cudaStreamSynchronize(ev->stream));  // the old lists may still be in use
+    if ((s = wait_stream(ev)) != SPH_OK) return s;  // the old lists may still be in use
     if (ev->pair_mem) {
         cudaFree(ev->pair_mem);
         ev->pair_mem = nullptr;
@@ -668,26 +696,40 @@ static sph_status size_pair_lists(sph_event *ev)
         return SPH_OK;
     }
     ev->pair_mem = m;
-    char *b = static_cast<char *>(m);
     PairBufs pl{};
-    pl.cap = (int)cap;
-    pl.W = reinterpret_cast<double *>(b);
-    pl.FAC = pl.W + rows;
-    pl.F = reinterpret_cast<int *>(pl.FAC + rows);
-    pl.B = pl.F + rows;
-    pl.P = pl.B + rows;
-    pl.cntF = pl.P + rows;
+    pl.total = total;
+    pl.margin = margin;
+    pl.W = static_cast<double *>(m);
+    pl.FAC = pl.W + total;
+    pl.off = reinterpret_cast<long long *>(pl.FAC + total);
+    pl.part = reinterpret_cast<unsigned long long *>(pl.off + (n + 1));
+    pl.L = reinterpret_cast<int *>(pl.part + nparts);
+    pl.P = pl.L + total;
+    pl.cntF = pl.P + total;
     pl.cntB = pl.cntF + n;
+    ev->pcnt[0] = pl.cntB + n;
+    ev->pcnt[1] = ev->pcnt[0] + n;
+    CK(cudaMemcpyAsync(ev->pcnt[0], state.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, ev->stream));
+    if ((s = wait_stream(ev)) != SPH_OK) return s;
+    pl.cnt_src = ev->pcnt[0];
     ev->cb.pl = pl;
     ev->pairs_grow = false;
     ev->kernels_per_step = 0;
+    if (!ev->pair_ovf_host) {
+        void *hp = nullptr;
+        if (cudaHostAlloc(&hp, sizeof(unsigned int), cudaHostAllocDefault) == cudaSuccess) {
+            ev->pair_ovf_host = static_cast<volatile unsigned int *>(hp);
+            *ev->pair_ovf_host = ev->pair_ovf_seen;
+        } else {
+            cudaGetLastError();
+        }
+    }
     // the captured step holds the old buffers
     if (ev->gexec) cudaGraphExecDestroy(ev->gexec);
     if (ev->graph) cudaGraphDestroy(ev->graph);
     ev->gexec = nullptr;
     ev->graph = nullptr;
     ev->graph_ready = false;
-    ev->kernels_per_step = 0;
     return SPH_OK;
 }
 
@@ -757,6 +799,9 @@ sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags)
         }
     }
     CK(cudaGetLastError());
+    if (ev->cb.pl.total > 0 && ev->pair_ovf_host)  // picked up by the next call
+        CK(cudaMemcpyAsync((void *)ev->pair_ovf_host, &ev->sc->pair_ovf, sizeof(unsigned int),
+                           cudaMemcpyDeviceToHost, ev->stream));
     ev->host_steps += nsteps;
     {
         sph_status s = count_step_kernels(ev);
@@ -1125,6 +1170,7 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
         if (!in->guess) return fail(SPH_ERR_ARG, "masked field has a null source");
         CK(cudaMemcpyAsync(ev->wguess, in->guess, sizeof(double) * 4 * N, k, st));
     }
+    ev->pairs_recount = true;  // the carried neighbour counts no longer follow the state order
     ev->observed = false;
     return wait_stream(ev);
 }

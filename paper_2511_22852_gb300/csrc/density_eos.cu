@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
                                                           const uint32_t *__restrict__ start,
                                                           const uint32_t *__restrict__ cnt,
                                                           double *__restrict__ dens, int *__restrict__ nnb,
-                                                          int fallback)
+                                                          int fallback, int *__restrict__ cnt_dst)
 {
     // fallback = 1: the pair-list passes ran first; this pass only runs if one of their lists
     // overflowed (and counts such stages)
@@ -64,89 +64,92 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
     }
     __shared__ int queue[kWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarps + wid;
-    if (a >= v.n) return;  // warp-uniform
-    int *q = queue[wid];
-    const int n = v.n;
-    const double *X = y, *Y = y + n, *S = y + 4 * (size_t)n;
-    const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
-    const double xa = X[a], ya = Y[a];
-    const float2 fa = fpos[a];
-    const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
-    const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
-    const int lim = 1 << v.B;
-    const unsigned lt = (1u << lane) - 1u;
-    double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
-    int c = 0, qn = 0;
-    // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
-    auto pair = [&](int qb) {
-        const int b = qb & 0x7FFFFFFF;
-        const double dx = xa - X[b], dy = ya - Y[b];
-        if (qb < 0 && !(dist2_2d(dx, dy) < v.supp2)) return;
-        {
-            const double r2 = fma(dx, dx, dy * dy);
-            double q = r2 > 0.0 ? r2 * inv_sqrt(r2) * v.inv_h : 0.0;
-            double w = kernel_w(q);
-            sg += w;
-            ss = fma(S[b], w, ss);
-            sb = fma(NB[b], w, sb);
-            sS = fma(NS[b], w, sS);
-            sq = fma(NQ[b], w, sq);
-            ++c;
-        }
-    };
-    for (int oy = -1; oy <= 1; ++oy) {
-        const int ny = cy + oy;
-        if (ny < 0 || ny >= lim) continue;
-        for (int ox = -1; ox <= 1; ++ox) {
-            const int nx = cx + ox;
-            if (nx < 0 || nx >= lim) continue;
-            const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
-            const uint32_t b0 = start[k], b1 = b0 + cnt[k];
-            for (uint32_t base = b0; base < b1; base += 32) {
-                const uint32_t b = base + lane;
-                bool cand = false, sure = false;
-                if (b < b1) {
-                    const float2 fb = fpos[b];
-                    const float dx = fa.x - fb.x, dy = fa.y - fb.y;
-                    const float r2f = fmaf(dx, dx, dy * dy);
-                    cand = r2f <= v.supp2_hi;
-                    sure = r2f < v.supp2_lo;
-                }
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-                if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
-                qn += __popc(m);
-                __syncwarp();
-                if (qn >= 32) {
-                    pair(q[lane]);
-                    qn -= 32;
+    // grid-stride over particles (one warp each): launched at a few blocks per SM when it is
+    // only the fallback of the pair-list passes
+    for (int a = blockIdx.x * kWarps + wid; a < v.n; a += gridDim.x * kWarps) {  // warp-uniform
+        int *q = queue[wid];
+        const int n = v.n;
+        const double *X = y, *Y = y + n, *S = y + 4 * (size_t)n;
+        const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
+        const double xa = X[a], ya = Y[a];
+        const float2 fa = fpos[a];
+        const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+        const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+        const int lim = 1 << v.B;
+        const unsigned lt = (1u << lane) - 1u;
+        double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
+        int c = 0, qn = 0;
+        // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
+        auto pair = [&](int qb) {
+            const int b = qb & 0x7FFFFFFF;
+            const double dx = xa - X[b], dy = ya - Y[b];
+            if (qb < 0 && !(dist2_2d(dx, dy) < v.supp2)) return;
+            {
+                const double r2 = fma(dx, dx, dy * dy);
+                double q = r2 > 0.0 ? r2 * inv_sqrt(r2) * v.inv_h : 0.0;
+                double w = kernel_w(q);
+                sg += w;
+                ss = fma(S[b], w, ss);
+                sb = fma(NB[b], w, sb);
+                sS = fma(NS[b], w, sS);
+                sq = fma(NQ[b], w, sq);
+                ++c;
+            }
+        };
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int ny = cy + oy;
+            if (ny < 0 || ny >= lim) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int nx = cx + ox;
+                if (nx < 0 || nx >= lim) continue;
+                const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+                const uint32_t b0 = start[k], b1 = b0 + cnt[k];
+                for (uint32_t base = b0; base < b1; base += 32) {
+                    const uint32_t b = base + lane;
+                    bool cand = false, sure = false;
+                    if (b < b1) {
+                        const float2 fb = fpos[b];
+                        const float dx = fa.x - fb.x, dy = fa.y - fb.y;
+                        const float r2f = fmaf(dx, dx, dy * dy);
+                        cand = r2f <= v.supp2_hi;
+                        sure = r2f < v.supp2_lo;
+                    }
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+                    if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
+                    qn += __popc(m);
                     __syncwarp();
-                    if (lane < qn) q[lane] = q[32 + lane];
-                    __syncwarp();
+                    if (qn >= 32) {
+                        pair(q[lane]);
+                        qn -= 32;
+                        __syncwarp();
+                        if (lane < qn) q[lane] = q[32 + lane];
+                        __syncwarp();
+                    }
                 }
             }
         }
-    }
-    if (lane < qn) pair(q[lane]);
-    for (int o = 16; o > 0; o >>= 1) {
-        sg += __shfl_xor_sync(0xFFFFFFFFu, sg, o);
-        ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
-        sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
-        sS += __shfl_xor_sync(0xFFFFFFFFu, sS, o);
-        sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
-        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-    }
-    if (lane == 0) {
-        const double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
-        const double sd = v.sigma_d;
-        dens[a] = sd * sg;
-        dens[(size_t)n + a] = sd * ss;  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
-        dens[2 * (size_t)n + a] = sd * sb;
-        dens[3 * (size_t)n + a] = sd * sS;
-        dens[4 * (size_t)n + a] = sd * sq;
-        dens[5 * (size_t)n + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
-        nnb[a] = c;
-        atomicAdd(&v.sc->pairs, (unsigned long long)c);
+        if (lane < qn) pair(q[lane]);
+        for (int o = 16; o > 0; o >>= 1) {
+            sg += __shfl_xor_sync(0xFFFFFFFFu, sg, o);
+            ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+            sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+            sS += __shfl_xor_sync(0xFFFFFFFFu, sS, o);
+            sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+            c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        }
+        if (lane == 0) {
+            const double ux = y[2 * (size_t)n + a], uy = y[3 * (size_t)n + a];
+            const double sd = v.sigma_d;
+            dens[a] = sd * sg;
+            dens[(size_t)n + a] = sd * ss;  // lab-frame s*, divided by u0 sqrt(-g) in the EoS pass
+            dens[2 * (size_t)n + a] = sd * sb;
+            dens[3 * (size_t)n + a] = sd * sS;
+            dens[4 * (size_t)n + a] = sd * sq;
+            dens[5 * (size_t)n + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+            nnb[a] = c;
+            if (cnt_dst) cnt_dst[a] = c;  // sizes the pair-list rows of the next stage
+            atomicAdd(&v.sc->pairs, (unsigned long long)c);
+        }
     }
 }
 
@@ -168,8 +171,10 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     double sig_star = dens[a];
     double u0 = dens[5 * n + a];
     double vol = u0 * sqrtg;
-    double s = dens[n + a] / vol;
-    double nq[3] = {dens[2 * n + a] / vol, dens[3 * n + a] / vol, dens[4 * n + a] / vol};
+    // one reciprocal per shared denominator (an FP64 division is a multi-instruction sequence)
+    const double ivol = 1.0 / vol, isig = 1.0 / sig_star;
+    double s = dens[n + a] * ivol;
+    double nq[3] = {dens[2 * n + a] * ivol, dens[3 * n + a] * ivol, dens[4 * n + a] * ivol};
     dens[n + a] = s;
     for (int q = 0; q < 3; ++q) dens[(2 + q) * n + a] = nq[q];
     double gs[4];
@@ -197,8 +202,9 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     for (int q = 0; q < 3; ++q) eos[(7 + q) * n + a] = o.pn[q];
     eos[10 * n + a] = o.cs2;
     double ux = y[2 * n + a], uy = y[3 * n + a];
-    double vx = ux / u0, vy = uy / u0;
-    double sigma = sig_star / vol;
+    const double iu0 = ivol * sqrtg;
+    double vx = ux * iu0, vy = uy * iu0;
+    double sigma = sig_star * ivol;
     double Pi = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
     if (v.tr.viscous) {
         Pi = sigma * y[5 * n + a];
@@ -208,19 +214,19 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     }
     double ptx = vx * pxx + vy * pxy;  // pi^{tau x}
     double pty = vx * pxy + vy * pyy;  // pi^{tau y}
-    double inv2 = 1.0 / (sig_star * sig_star);
+    double inv2 = isig * isig;
     double P = o.p + Pi;
     gin[a] = (P + pxx - vx * ptx) * inv2;                 // X^{xx}
     gin[n + a] = (pxy - vx * pty) * inv2;                 // X^{xy}  (j = x, i = y)
     gin[2 * n + a] = (pxy - vy * ptx) * inv2;             // X^{yx}  (j = y, i = x)
     gin[3 * n + a] = (P + pyy - vy * pty) * inv2;         // X^{yy}
-    gin[4 * n + a] = ux / sig_star;
-    gin[5 * n + a] = uy / sig_star;
+    gin[4 * n + a] = ux * isig;
+    gin[5 * n + a] = uy * isig;
     double wcontrib = 0.0;
     if (v.milne) {
         double ptt = vx * ptx + vy * pty;
         double t2pee = ptt - pxx - pyy;  // tau^2 pi^{eta eta} from tracelessness
-        wcontrib = (P + t2pee) / sig_star;
+        wcontrib = (P + t2pee) * isig;
     }
     warp_or(&v.sc->status_or, o.st);
     return wcontrib;
@@ -323,9 +329,12 @@ void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs
         return;
     }
     k_fpos<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos, dens);
-    const int lists = cb.pl.cap > 0;
+    const int lists = cb.pl.total > 0;
     if (lists) launch_pairs_density(v, y, Nq, cb, dens, nnb, st);
-    k_density2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb, lists);
+    // as the fallback of the pair-list passes it usually exits at once: a few blocks per SM
+    const int grid = lists ? std::min(nblk(v.n, kWarps), 8 * device_sm_count()) : nblk(v.n, kWarps);
+    k_density2<<<grid, 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb, lists,
+                                             lists ? cb.pl.cnt_dst : nullptr);
 }
 
 void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
@@ -340,6 +349,20 @@ void launch_eos(const EvView &v, int stage, const double *y, const double *dens,
 }
 
 int eos_block_count(int n, int dim) { return nblk(n, dim == 2 ? 32 : 64); }
+
+int device_sm_count()
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            sms = 152;
+        }
+    }
+    return sms;
+}
 
 // Offline inverter: every node (s_i, x_j) of the inverted table solved by the online inversion
 // started cold (closed form, then table Newton), as the offline procedure uses the existing

@@ -249,11 +249,11 @@ __device__ __forceinline__ void clamp4(const EosDev &E, double *x)
     for (int q = 0; q < 3; ++q) x[1 + q] = fmin(fmax(x[1 + q], E.mu0[q]), E.mumax[q]);
 }
 
-__device__ double resid(const EosDev &E, const double *x, double s, const double *n, double r[4], double J[4][4])
+__device__ double resid(const EosDev &E, const double *x, double s, double inv_s, const double *n, double r[4],
+                        double J[4][4])
 {
     double sn[4];
     tab_eval_steps(E, x, sn, J, nullptr);
-    double inv_s = 1.0 / s;
     // J / s per unit of x: the grid-step scaling folded into the 1/s scaling
     const double sc[4] = {E.inv_dT * inv_s, E.inv_dmu[0] * inv_s, E.inv_dmu[1] * inv_s, E.inv_dmu[2] * inv_s};
     double tgt[4] = {s, n[0], n[1], n[2]};
@@ -277,7 +277,8 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
 {
     double r[4];
     *jx = false;
-    double rn = resid(E, x, s, n, r, J);
+    const double inv_s = 1.0 / s;
+    double rn = resid(E, x, s, inv_s, n, r, J);
     ++w.resid;
     for (int it = 0; it < E.maxit; ++it) {
         double d[4] = {-r[0], -r[1], -r[2], -r[3]};
@@ -291,7 +292,7 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
                 double xn[4] = {x[0] + d[0], x[1] + d[1], x[2] + d[2], x[3] + d[3]};
                 clamp4(E, xn);
                 ++w.resid;
-                if (resid(E, xn, s, n, r, J) <= rn) {
+                if (resid(E, xn, s, inv_s, n, r, J) <= rn) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) x[k] = xn[k];
                     *jx = true;
@@ -306,7 +307,7 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
 #pragma unroll
             for (int k = 0; k < 4; ++k) xn[k] = fma(lam, d[k], x[k]);
             clamp4(E, xn);
-            rnn = resid(E, xn, s, n, r, J);
+            rnn = resid(E, xn, s, inv_s, n, r, J);
             ++w.resid;
             if (rnn < rn) break;
             lam *= 0.5;

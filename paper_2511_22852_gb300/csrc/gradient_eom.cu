@@ -18,6 +18,8 @@
 // D sigma = -sigma theta), so dP^i/dx^0 = M^i_j a^j + c^i is assembled with
 // affine arithmetic (exact coefficients, no differencing) and M a = F - c is
 // solved per particle by Cramer's rule -- the D x D system of eq. unugeneral.
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace sphg {
@@ -40,98 +42,100 @@ __global__ void __launch_bounds__(32 * kWarps) k_gradient2(EvView v, int stage, 
     if (fallback && !v.sc->pair_flag) return;  // the pair-list pass did the work
     __shared__ int queue[kWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarps + wid;
-    if (a >= v.n) return;  // warp-uniform
-    int *q = queue[wid];
-    const int n = v.n;
-    const double *X = y, *Y = y + n;
-    const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
-    const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
-    const double xa = X[a], ya = Y[a];
-    const float2 fa = fpos[a];
-    const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
-    const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
-    const int lim = 1 << v.B;
-    const unsigned lt = (1u << lane) - 1u;
-    double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
-    double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
-    int qn = 0;
-    // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
-    auto pair = [&](int qb) {
-        const int b = qb & 0x7FFFFFFF;
-        const double dx = xa - X[b], dy = ya - Y[b];
-        if (qb < 0 && !(dist2_2d(dx, dy) < v.supp2)) return;
-        const double r2 = fma(dx, dx, dy * dy);
-        if (r2 > 0.0) {
-            const double ir = inv_sqrt(r2);
-            const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;  // (dW/dr)/r without sigma_d/h
-            const double gx = fac * dx, gy = fac * dy;
-            Gx += gx;
-            Gy += gy;
-            Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));
-            Hy = fma(Xxy[b], gx, fma(Xyy[b], gy, Hy));
-            const double ubx = Ux[b], uby = Uy[b];
-            dxux = fma(ubx, gx, dxux);
-            dxuy = fma(uby, gx, dxuy);
-            dyux = fma(ubx, gy, dyux);
-            dyuy = fma(uby, gy, dyuy);
-        }
-    };
-    for (int oy = -1; oy <= 1; ++oy) {
-        const int ny = cy + oy;
-        if (ny < 0 || ny >= lim) continue;
-        for (int ox = -1; ox <= 1; ++ox) {
-            const int nx = cx + ox;
-            if (nx < 0 || nx >= lim) continue;
-            const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
-            const uint32_t b0 = start[k], b1 = b0 + cnt[k];
-            for (uint32_t base = b0; base < b1; base += 32) {
-                const uint32_t b = base + lane;
-                bool cand = false, sure = false;
-                if (b < b1) {
-                    const float2 fb = fpos[b];
-                    const float dx = fa.x - fb.x, dy = fa.y - fb.y;
-                    const float r2f = fmaf(dx, dx, dy * dy);
-                    cand = r2f <= v.supp2_hi;
-                    sure = r2f < v.supp2_lo;
-                }
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
-                if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
-                qn += __popc(m);
-                __syncwarp();
-                if (qn >= 32) {
-                    pair(q[lane]);
-                    qn -= 32;
+    // grid-stride over particles (one warp each): launched at a few blocks per SM when it is
+    // only the fallback of the pair-list passes
+    for (int a = blockIdx.x * kWarps + wid; a < v.n; a += gridDim.x * kWarps) {  // warp-uniform
+        int *q = queue[wid];
+        const int n = v.n;
+        const double *X = y, *Y = y + n;
+        const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
+        const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
+        const double xa = X[a], ya = Y[a];
+        const float2 fa = fpos[a];
+        const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
+        const int cx = cell_coord(xa, xmin0, v.inv_cell), cy = cell_coord(ya, xmin1, v.inv_cell);
+        const int lim = 1 << v.B;
+        const unsigned lt = (1u << lane) - 1u;
+        double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
+        double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
+        int qn = 0;
+        // queued index with bit 31 set: the float test left the pair undecided (exact test needed)
+        auto pair = [&](int qb) {
+            const int b = qb & 0x7FFFFFFF;
+            const double dx = xa - X[b], dy = ya - Y[b];
+            if (qb < 0 && !(dist2_2d(dx, dy) < v.supp2)) return;
+            const double r2 = fma(dx, dx, dy * dy);
+            if (r2 > 0.0) {
+                const double ir = inv_sqrt(r2);
+                const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;  // (dW/dr)/r without sigma_d/h
+                const double gx = fac * dx, gy = fac * dy;
+                Gx += gx;
+                Gy += gy;
+                Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));
+                Hy = fma(Xxy[b], gx, fma(Xyy[b], gy, Hy));
+                const double ubx = Ux[b], uby = Uy[b];
+                dxux = fma(ubx, gx, dxux);
+                dxuy = fma(uby, gx, dxuy);
+                dyux = fma(ubx, gy, dyux);
+                dyuy = fma(uby, gy, dyuy);
+            }
+        };
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int ny = cy + oy;
+            if (ny < 0 || ny >= lim) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int nx = cx + ox;
+                if (nx < 0 || nx >= lim) continue;
+                const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
+                const uint32_t b0 = start[k], b1 = b0 + cnt[k];
+                for (uint32_t base = b0; base < b1; base += 32) {
+                    const uint32_t b = base + lane;
+                    bool cand = false, sure = false;
+                    if (b < b1) {
+                        const float2 fb = fpos[b];
+                        const float dx = fa.x - fb.x, dy = fa.y - fb.y;
+                        const float r2f = fmaf(dx, dx, dy * dy);
+                        cand = r2f <= v.supp2_hi;
+                        sure = r2f < v.supp2_lo;
+                    }
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+                    if (cand) q[qn + __popc(m & lt)] = sure ? (int)b : (int)(b | 0x80000000u);
+                    qn += __popc(m);
                     __syncwarp();
-                    if (lane < qn) q[lane] = q[32 + lane];
-                    __syncwarp();
+                    if (qn >= 32) {
+                        pair(q[lane]);
+                        qn -= 32;
+                        __syncwarp();
+                        if (lane < qn) q[lane] = q[32 + lane];
+                        __syncwarp();
+                    }
                 }
             }
         }
-    }
-    if (lane < qn) pair(q[lane]);
-    for (int o = 16; o > 0; o >>= 1) {
-        Gx += __shfl_xor_sync(0xFFFFFFFFu, Gx, o);
-        Gy += __shfl_xor_sync(0xFFFFFFFFu, Gy, o);
-        Hx += __shfl_xor_sync(0xFFFFFFFFu, Hx, o);
-        Hy += __shfl_xor_sync(0xFFFFFFFFu, Hy, o);
-        dxux += __shfl_xor_sync(0xFFFFFFFFu, dxux, o);
-        dxuy += __shfl_xor_sync(0xFFFFFFFFu, dxuy, o);
-        dyux += __shfl_xor_sync(0xFFFFFFFFu, dyux, o);
-        dyuy += __shfl_xor_sync(0xFFFFFFFFu, dyuy, o);
-    }
-    if (lane == 0) {
-        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-        const double sqrtg = v.milne ? tau : 1.0;
-        const double c = v.sigma_d * v.inv_h;
-        gout[a] = c * dxux;
-        gout[(size_t)n + a] = c * dxuy;
-        gout[2 * (size_t)n + a] = c * dyux;
-        gout[3 * (size_t)n + a] = c * dyuy;
-        const double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
-        const double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
-        gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
-        gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+        if (lane < qn) pair(q[lane]);
+        for (int o = 16; o > 0; o >>= 1) {
+            Gx += __shfl_xor_sync(0xFFFFFFFFu, Gx, o);
+            Gy += __shfl_xor_sync(0xFFFFFFFFu, Gy, o);
+            Hx += __shfl_xor_sync(0xFFFFFFFFu, Hx, o);
+            Hy += __shfl_xor_sync(0xFFFFFFFFu, Hy, o);
+            dxux += __shfl_xor_sync(0xFFFFFFFFu, dxux, o);
+            dxuy += __shfl_xor_sync(0xFFFFFFFFu, dxuy, o);
+            dyux += __shfl_xor_sync(0xFFFFFFFFu, dyux, o);
+            dyuy += __shfl_xor_sync(0xFFFFFFFFu, dyuy, o);
+        }
+        if (lane == 0) {
+            const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+            const double sqrtg = v.milne ? tau : 1.0;
+            const double c = v.sigma_d * v.inv_h;
+            gout[a] = c * dxux;
+            gout[(size_t)n + a] = c * dxuy;
+            gout[2 * (size_t)n + a] = c * dyux;
+            gout[3 * (size_t)n + a] = c * dyuy;
+            const double Fx = Xxx[a] * Gx + Xyx[a] * Gy + Hx;
+            const double Fy = Xxy[a] * Gx + Xyy[a] * Gy + Hy;
+            gout[4 * (size_t)n + a] = -sqrtg * c * Fx;
+            gout[5 * (size_t)n + a] = -sqrtg * c * Fy;
+        }
     }
 }
 
@@ -154,8 +158,11 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
     double pn0 = eos[7 * n + a], pn1 = eos[8 * n + a], pn2 = eos[9 * n + a];
     double dxux = gout[a], dxuy = gout[n + a], dyux = gout[2 * n + a], dyuy = gout[3 * n + a];
     double Fx = gout[4 * n + a], Fy = gout[5 * n + a];
-    double sigma = sig_star / (g * sqrtg);
-    double ig = 1.0 / g, isg = 1.0 / sigma;
+    // one reciprocal per denominator (an FP64 division is a multi-instruction sequence):
+    // sigma = sig_star / (u0 sqrt(-g)) and 1 / sigma from 1/u0 and 1/sig_star
+    double ig = 1.0 / g, isig = 1.0 / sig_star;
+    double sigma = sig_star * ig * (v.milne ? hub : 1.0);
+    double isg = g * sqrtg * isig;
     double vx = ux * ig, vy = uy * ig;
     const bool visc = v.tr.viscous != 0;
     double Bv = 0.0, Pvxx = 0.0, Pvxy = 0.0, Pvyy = 0.0;
@@ -203,17 +210,20 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
         double eta = v.tr.eta_over_s * s;
         double dTg = T * kHbarc - v.tr.zeta_T_GeV;
         double zeta = v.tr.zeta_peak * exp(-dTg * dTg / (2.0 * v.tr.zeta_w_GeV * v.tr.zeta_w_GeV)) * s;
-        double taupi = v.tr.tau_pi_coef * eta / (e + p);
-        double tauPi = v.tr.tau_Pi_ratio * taupi;
-        dS = (ig * isg / T) * (pisig - Pi * th);
-        dBv = (-ig * isg / tauPi) * (zeta * th + Pi);
+        // 1/tau_pi = (e + p) / (c eta), tau_pi = c eta / (e + p); tau_Pi = ratio tau_pi
+        double itp = (e + p) / (v.tr.tau_pi_coef * eta);
+        double itPi = itp / v.tr.tau_Pi_ratio;
+        double iT = 1.0 / T;
+        dS = (ig * isg * iT) * (pisig - Pi * th);
+        dBv = (-ig * isg * itPi) * (zeta * th + Pi);
         // pi^{j alpha} a_alpha with the lowered four-acceleration (u^0 du^0/dx^0, -u^0 a^i)
         Aff pax = g * (pvx * dg - (pxx * ax + pxy * ay));
         Aff pay = g * (pvy * dg - (pxy * ax + pyy * ay));
-        double itp = 1.0 / taupi, f43 = 4.0 / 3.0;
-        Aff dpxx = ig * (itp * (2.0 * eta * sxx - f43 * taupi * pxx * th + (-pxx)) - 2.0 * ux * pax);
-        Aff dpxy = ig * (itp * (2.0 * eta * sxy - f43 * taupi * pxy * th + (-pxy)) - (ux * pay + uy * pax));
-        Aff dpyy = ig * (itp * (2.0 * eta * syy - f43 * taupi * pyy * th + (-pyy)) - 2.0 * uy * pay);
+        // d pi^{ij}/d tau = [(2 eta sigma^{ij} - pi^{ij}) / tau_pi - 4/3 pi^{ij} theta - coupling] / u0
+        const double f43 = 4.0 / 3.0;
+        Aff dpxx = ig * (itp * (2.0 * eta * sxx + (-pxx)) - (f43 * pxx) * th - 2.0 * ux * pax);
+        Aff dpxy = ig * (itp * (2.0 * eta * sxy + (-pxy)) - (f43 * pxy) * th - (ux * pay + uy * pax));
+        Aff dpyy = ig * (itp * (2.0 * eta * syy + (-pyy)) - (f43 * pyy) * th - 2.0 * uy * pay);
         double isg2 = isg * isg;
         dPxx = isg * dpxx - (pxx * isg2) * dsg;
         dPxy = isg * dpxy - (pxy * isg2) * dsg;
@@ -222,8 +232,8 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
     if (v.ntrack > 0) {  // jet tracks (Cartesian): dP^i/dt gains I^i/sigma*, dS/dt gains u.I/(u^0 sigma T)
         double I[4];
         jet_deposit(v, tau, ys[a], ys[n + a], 0.0, I);
-        Fx += I[1] / sig_star;
-        Fy += I[2] / sig_star;
+        Fx += I[1] * isig;
+        Fy += I[2] * isig;
         const double uI = g * I[0] - ux * I[1] - uy * I[2];
         dS = dS + aff((ig * isg / T) * uI);
     }
@@ -394,9 +404,10 @@ void launch_gradient(const EvView &v, int stage, const double *y, const double *
         launch_gradient2m(v, stage, y, gin, cb, gout, st);
         return;
     }
-    const int lists = cb.pl.cap > 0;
+    const int lists = cb.pl.total > 0;
     if (lists) launch_pairs_gradient(v, stage, y, gin, cb, gout, st);
-    k_gradient2<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout, lists);
+    const int grid = lists ? std::min(nblk(v.n, kWarps), 8 * device_sm_count()) : nblk(v.n, kWarps);
+    k_gradient2<<<grid, 32 * kWarps, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout, lists);
 }
 
 void launch_eom(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,

@@ -12,6 +12,9 @@
 //
 // Per pair the FP64 work of the two passes drops from about 126 operations (two kernel
 // evaluations with the sums of each side, in each of the two passes) to about 67.
+//
+// Rows: a particle's row holds its previous neighbour count plus a margin (a prefix scan per
+// stage); forward entries fill it from the start, backward entries from the end.
 #include "sph_internal.cuh"
 
 namespace sphg {
@@ -44,6 +47,92 @@ __device__ __forceinline__ int block_cells_ascending(int cx, int cy, int lim, ui
     return nk;
 }
 
+// ---------------------------------------------------------------------------
+// Row offsets: row j (sorted order) holds cnt_src[perm[j]] - 1 + margin entries (the previous
+// neighbour count without the self pair); off = exclusive prefix sums, off[n] = entries needed.
+constexpr int kScanThreads = 256, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ long long row_size(const PairBufs &pl, const uint32_t *perm, int j)
+{
+    const int c = pl.cnt_src[perm[j]];
+    return (long long)(c > 1 ? c - 1 : 0) + pl.margin;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_rows_part(int n, const uint32_t *__restrict__ perm, PairBufs pl)
+{
+    __shared__ long long ws[kScanThreads / 32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    long long t = 0;
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < n) t += row_size(pl, perm, base + k);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long b = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) b += ws[w];
+        pl.part[blockIdx.x] = (unsigned long long)b;
+    }
+}
+
+// exclusive scan of the block sums (one block); off[n] = total; rows beyond the allocation flag
+// the stage (the per-particle passes run)
+__global__ void __launch_bounds__(1024) k_rows_top(int n, int nparts, PairBufs pl, DevScalars *sc)
+{
+    __shared__ unsigned long long tot[1024];
+    const int t = threadIdx.x, per = (nparts + 1023) / 1024;
+    const int b0 = min(t * per, nparts), b1 = min(b0 + per, nparts);
+    unsigned long long s = 0;
+    for (int i = b0; i < b1; ++i) s += pl.part[i];
+    tot[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long run = 0;
+        for (int k = 0; k < 1024; ++k) {
+            const unsigned long long x = tot[k];
+            tot[k] = run;
+            run += x;
+        }
+        pl.off[n] = (long long)run;
+        if ((long long)run > pl.total) atomicOr(&sc->pair_flag, 1u);
+    }
+    __syncthreads();
+    unsigned long long run = tot[t];
+    for (int i = b0; i < b1; ++i) {
+        const unsigned long long x = pl.part[i];
+        pl.part[i] = run;
+        run += x;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_rows_apply(int n, const uint32_t *__restrict__ perm, PairBufs pl)
+{
+    __shared__ long long ws[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    long long v[kScanPer], t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < n ? row_size(pl, perm, base + k) : 0;
+        t += v[k];
+    }
+    long long incl = t;  // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    long long wbase = 0;
+    for (int w = 0; w < wid; ++w) wbase += ws[w];
+    long long run = (long long)pl.part[blockIdx.x] + wbase + incl - t;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) pl.off[base + k] = run;
+        run += v[k];
+    }
+}
+
 // Forward density pass, one warp per particle a.  Candidates of the 3x3 cells pass the
 // single-precision prefilter; a neighbour b < a is decided at once (exact FP64 test when the
 // float test left it undecided) and listed in B; a candidate b > a is queued, and 32 at a time
@@ -71,10 +160,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
     uint32_t keys[9];
     const int nk = block_cells_ascending(cx, cy, 1 << v.B, keys);
     const unsigned lt = (1u << lane) - 1u;
-    const int cap = pl.cap;
-    const size_t row = (size_t)a * cap;
-    int *F = pl.F + row, *Bl = pl.B + row;
-    double *Wr = pl.W + row, *Fr = pl.FAC + row;
+    const long long r0 = pl.off[a], r1 = pl.off[a + 1];
+    // rows beyond the allocation write nothing (the scan has flagged the stage)
+    const int cap = r1 <= pl.total ? (int)(r1 - r0) : 0;
+    int *F = pl.L + r0, *Bl = pl.L + (r1 - 1);  // forward up from the start, backward down from the end
+    double *Wr = pl.W + r0, *Fr = pl.FAC + r0;
     double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
     if (lane == 0) {  // the self pair, W(0)
         const double w0 = kernel_w(0.0);
@@ -142,7 +232,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
             const unsigned mb = __ballot_sync(kFull, accB);
             if (accB) {
                 const int slot = nbk + __popc(mb & lt);
-                if (slot < cap) Bl[slot] = (int)b;
+                if (slot < cap) Bl[-slot] = (int)b;
             }
             nbk += __popc(mb);
             // b > a: queued in arrival (ascending) order for the FP64 pair arithmetic
@@ -168,7 +258,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
     if (lane == 0) {
         pl.cntF[a] = nf;
         pl.cntB[a] = nbk;
-        if (nf > cap || nbk > cap) atomicOr(&v.sc->pair_flag, 1u);
+        if (nf + nbk > cap) atomicOr(&v.sc->pair_flag, 1u);  // the two ends met: lists unusable
     }
 }
 
@@ -187,15 +277,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_bwd(EvView v, con
     const int n = v.n;
     const double *S = y + 4 * (size_t)n;
     const double *NB = Nq, *NS = Nq + n, *NQ = Nq + 2 * (size_t)n;
-    const int cap = pl.cap;
-    const size_t row = (size_t)a * cap;
+    const long long rend = pl.off[a + 1] - 1;  // backward entries: rend, rend - 1, ...
     const int nb = pl.cntB[a];
     double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
     for (int j0 = 0; j0 < nb; j0 += 32) {
         const int j = j0 + lane;
         if (j < nb) {
-            const int b = pl.B[row + j];
-            const int *Fb = pl.F + (size_t)b * cap;
+            const int b = pl.L[rend - j];
+            const long long rb = pl.off[b];
+            const int *Fb = pl.L + rb;
             const int nfb = pl.cntF[b];
             int lo = 0, hi = nfb;
             while (lo < hi) {
@@ -209,8 +299,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_bwd(EvView v, con
                 atomicOr(&v.sc->err_flags, ERR_PAIR_LIST);
                 lo = 0;
             }
-            pl.P[row + j] = lo;
-            const double w = nfb > 0 ? pl.W[(size_t)b * cap + lo] : 0.0;
+            pl.P[rend - j] = lo;
+            const double w = nfb > 0 ? pl.W[rb + lo] : 0.0;
             sg += w;
             ss = fma(S[b], w, ss);
             sb = fma(NB[b], w, sb);
@@ -230,6 +320,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_bwd(EvView v, con
     if (lane == 0) {
         const int c = 1 + pl.cntF[a] + nb;
         nnb[a] = c;
+        if (pl.cnt_dst) pl.cnt_dst[a] = c;  // sizes this particle's row in the next stage
         atomicAdd(&v.sc->pairs, (unsigned long long)c);
     }
 }
@@ -250,8 +341,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int st
     const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
     const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
     const double xa = X[a], ya = Y[a];
-    const int cap = pl.cap;
-    const size_t row = (size_t)a * cap;
+    const long long r0 = pl.off[a], rend = pl.off[a + 1] - 1;
     const int nf = pl.cntF[a], nt = nf + pl.cntB[a];
     double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
     double dxux = 0.0, dxuy = 0.0, dyux = 0.0, dyuy = 0.0;
@@ -261,11 +351,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int st
             int b;
             double fac;
             if (j < nf) {
-                b = pl.F[row + j];
-                fac = pl.FAC[row + j];
+                b = pl.L[r0 + j];
+                fac = pl.FAC[r0 + j];
             } else {
-                b = pl.B[row + (j - nf)];
-                fac = pl.FAC[(size_t)b * cap + pl.P[row + (j - nf)]];
+                b = pl.L[rend - (j - nf)];
+                fac = pl.FAC[pl.off[b] + pl.P[rend - (j - nf)]];
             }
             const double dx = xa - X[b], dy = ya - Y[b];
             const double gx = fac * dx, gy = fac * dy;
@@ -306,6 +396,10 @@ inline int nblk(int n, int t) { return (n + t - 1) / t; }
 void launch_pairs_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                           cudaStream_t st)
 {
+    const int nparts = (v.n + kScanTile - 1) / kScanTile;
+    k_rows_part<<<nparts, kScanThreads, 0, st>>>(v.n, cb.perm, cb.pl);
+    k_rows_top<<<1, 1024, 0, st>>>(v.n, nparts, cb.pl, v.sc);
+    k_rows_apply<<<nparts, kScanThreads, 0, st>>>(v.n, cb.perm, cb.pl);
     // the forward partials go to the density rows, which the backward pass completes in place
     k_pairs_density_fwd<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, cb.pl,
                                                                    dens);

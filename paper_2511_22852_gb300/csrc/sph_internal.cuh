@@ -230,14 +230,23 @@ __device__ __forceinline__ void warp_or(unsigned int *dst, unsigned int v)
 // ---------------------------------------------------------------------------
 // launchers (implemented in cells.cu, density_eos.cu, gradient_eom.cu)
 // Half-pair lists of the plain 2D neighbour passes, rebuilt in every stage's density pass.
-// Particle a (sorted index) owns rows [a cap, a cap + cap) of F, B, P, W, FAC:
-//   F: its accepted neighbours b > a, ascending; W, FAC: W(r)/sigma_d and (dW/dr)/r * h/sigma_d
-//      of each such pair (the kernel values are symmetric in a, b, so each is computed once);
-//   B: its accepted neighbours b < a, ascending; P: the index in F/W/FAC of the pair (b, a).
-// cap = 0: lists off (the per-particle passes run).
+// Particle a (sorted index) owns entries [off[a], off[a+1]) of L, P, W, FAC, sized by its
+// neighbour count of the previous stage plus a margin (a prefix scan per stage):
+//   from the row start: its accepted neighbours b > a, ascending (L), with W(r)/sigma_d and
+//      (dW/dr)/r * h/sigma_d of the pair (W, FAC: symmetric in a, b, so computed once);
+//   from the row end, downwards: its accepted neighbours b < a, ascending (L), with the slot of
+//      the pair (b, a) in b's row (P).
+// A particle whose neighbours exceed its row (or rows beyond the allocation) flags the stage,
+// which then runs the per-particle passes; the counts it records size the next stage's rows.
+// total = 0: lists off (the per-particle passes run).
 struct PairBufs {
-    int cap;
-    int *F, *B, *P, *cntF, *cntB;
+    long long total;              // entries allocated
+    int margin;                   // entries added to each particle's previous count
+    const int *cnt_src;           // previous counts (self included), state order (read through perm)
+    int *cnt_dst;                 // this stage's counts, sorted order (NULL: not recorded)
+    long long *off;               // [n + 1] row offsets of this stage
+    unsigned long long *part;     // scan partial sums
+    int *L, *P, *cntF, *cntB;
     double *W, *FAC;
 };
 
@@ -247,7 +256,7 @@ struct CellBufs {
     float4 *fpos3;  // 3D: the same with three coordinates
     uint32_t *part; // scan partial sums (multi-block scan of large bucket tables)
     int nb;         // number of buckets: 1 << (2 B) in 2D, 1 << (B3[0] + B3[1] + B3[2]) in 3D
-    PairBufs pl;    // plain 2D: half-pair lists (pl.cap = 0: off)
+    PairBufs pl;    // plain 2D: half-pair lists (pl.total = 0: off)
 };
 
 // Bound for the single-precision candidate prefilter of the neighbour passes.  With
@@ -286,7 +295,8 @@ void launch_bbox(const EvView &v, const double *y, cudaStream_t st);
 void launch_cells(const EvView &v, const double *y, const int *id, CellBufs cb, cudaStream_t st);
 void launch_permute(const EvView &v, const uint32_t *perm, const double *const *src, double *const *dst,
                     const int *nrows, int ngroups, const int *id_in, int *id_out, cudaStream_t st);
-// plain 2D neighbour passes over the half-pair lists (cb.pl.cap > 0)
+// plain 2D neighbour passes over the half-pair lists (cb.pl.total > 0): row offsets from the
+// previous counts, then the forward and backward density passes
 void launch_pairs_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                           cudaStream_t st);
 void launch_pairs_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb,
@@ -310,6 +320,7 @@ void launch_sum_fixed(const double *vals, int n, int nfield, double *out, cudaSt
 void launch_scatter_orig(const double *src, double *dst, const int *id, int n, int nrows, cudaStream_t st);
 void launch_scatter_orig_u32(const uint32_t *src, uint32_t *dst, const int *id, int n, cudaStream_t st);
 void launch_cell_coords(const EvView &v, const double *y, const int *id, int *cell_orig, cudaStream_t st);
+int device_sm_count();  // SMs of the current device (cached after the first call)
 int eos_block_count(int n, int dim);  // blocks of the EoS pass (entries of its work-rate partials)
 
 // mixed-precision 2D neighbour passes (mixed2d.cu); dispatched when v.mixed

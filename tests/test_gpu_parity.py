@@ -642,7 +642,7 @@ def test_pair_lists_match_per_particle_passes(Bd, monkeypatch):
         assert relerr(a[k], b[k]) < 1e-13, (k, relerr(a[k], b[k]))
     t, t0 = g.totals(), g0.totals()
     assert t["pair_overflows"] == 0 and t0["pair_overflows"] == 0
-    assert t["kernel_launches"] == 5 * 32 and t0["kernel_launches"] == 5 * 26  # 16 and 13 per stage
+    assert t["kernel_launches"] == 5 * 38 and t0["kernel_launches"] == 5 * 26  # 19 and 13 per stage
     # the lists were sized by one read-out evaluation (its pairs are counted): compare one step
     g.step(1, sync=True)
     g0.step(1, sync=True)
@@ -656,10 +656,10 @@ def test_pair_lists_match_per_particle_passes(Bd, monkeypatch):
 
 
 def test_pair_list_overflow_falls_back_then_grows(Bd, monkeypatch):
-    """Lists too small for the neighbour counts (capacity 64 against ~120 neighbours): the stage
-    runs the per-particle passes (the result still follows the oracle), the overflow is counted,
-    and the lists grow at the next step until they fit."""
-    monkeypatch.setenv("SPH_PAIR_CAP", "64")
+    """Lists allocated far too small (64 entries against ~330,000 needed): the stage runs the
+    per-particle passes (the result still follows the oracle), the overflow is counted, and the
+    allocation grows before the next step, after which the stages run on the lists."""
+    monkeypatch.setenv("SPH_PAIR_TOTAL", "64")
     ev = CASES["bsq_small"]()
     g = Bd.GpuEvent(ev)
     run = O.OracleRun.start(ev)
@@ -669,11 +669,28 @@ def test_pair_list_overflow_falls_back_then_grows(Bd, monkeypatch):
     errs = state_errors(g, run)
     assert all(v < TOL_STEP for v in errs.values()), errs
     seen = []
-    for _ in range(5):
+    for _ in range(4):
         g.step(1, sync=True)
         seen.append(g.totals()["pair_overflows"])
-    run.step(5)
+    run.step(4)
     assert seen[-1] == seen[-2] == seen[-3], seen  # the grown lists fit
     errs = state_errors(g, run)
     assert all(v < TOL_EVOL for v in errs.values()), errs
+    g.free()
+
+
+def test_pair_list_rows_resize_on_the_device(Bd, monkeypatch):
+    """Rows with no margin over the previous stage's neighbour counts: a particle whose count
+    grew overflows its row, the stage runs the per-particle passes and records the new counts,
+    which size the next stage's rows -- no host involvement; every stage follows the oracle."""
+    monkeypatch.setenv("SPH_PAIR_MARGIN", "0")
+    ev = CASES["bsq_small"]()
+    g = Bd.GpuEvent(ev)
+    g.step(10, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(10)
+    errs = state_errors(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    t = g.totals()
+    assert t["pair_overflows"] <= 21  # at most every stage and the read-out
     g.free()
