@@ -34,14 +34,15 @@ WORKLOAD = "viscous 2+1D BSQ single event, FP64: 40k particles, 64x32^3 EoS tabl
 
 # algorithmic FP64 flops per accepted ordered neighbour pair (fused multiply-add = 2), with the
 # kernel of each unordered pair evaluated once (its two ordered pairs share it):
-#   density : [distance 5, sqrt 1, q 1, kernel polynomial 5, kernel-derivative polynomial 3,
-#             1/r and factor 2] / 2 shared, five accumulations 10                           = 18.5
-#   gradient: dW vector 2, sum of dW 2, stress divergence 8, velocity gradient 8          = 20
-FLOPS_PER_PAIR = {"density": 18.5, "gradient": 20.0}
+#   density : [distance 5, sqrt 1, q 1, kernel and kernel-derivative polynomials with 1/r 12,
+#             dW vector 2] / 2 shared, five accumulations 10                                = 20.5
+#   gradient: sum of dW 2, stress divergence 8, velocity gradient 8                        = 18
+FLOPS_PER_PAIR = {"density": 20.5, "gradient": 18.0}
 # EoS inversion, per unit of work actually done (counted on the device):
-#   table residual + Jacobian evaluation (quadrilinear, 4 fields x 4 patches with derivatives,
-#   scaling) 460; 4x4 Gaussian elimination with pivoting 64; closed-form g(T), g'(T) 26
-FLOPS_EOS = (460.0, 64.0, 26.0)
+#   table residual + Jacobian evaluation (the quadrilinear interpolant reduced axis by axis with
+#   its four derivatives: 16 corner patches x 12, 8 x 9, 4 x 12; location 12; residual and
+#   scaling 28) 352; 4x4 Gaussian elimination with pivoting 64; closed-form g(T), g'(T) 26
+FLOPS_EOS = (352.0, 64.0, 26.0)
 # FP64 vector peak of GB300 (nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock)
 FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes (read + write) per launch of the FP64 40k-event kernels, from one ncu capture of

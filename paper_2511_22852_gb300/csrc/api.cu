@@ -100,7 +100,7 @@ struct sph_event {
     // half-pair lists of the plain 2D neighbour passes (cb.pl): sized on the first step from the
     // neighbour counts, grown after a stage whose lists overflowed (pair_ovf rose)
     int kernels_per_step = 0;  // kernel nodes of one captured step (0: not counted yet)
-    bool pairs_off = false, pairs_grow = false, pairs_recount = false;
+    bool pairs_off = false, pairs_grow = false;
     unsigned int pair_ovf_seen = 0;
     void *pair_mem = nullptr;
     int *pcnt[2] = {nullptr, nullptr};  // neighbour counts carried with the state (Y[0], Y1[0] order)
@@ -639,7 +639,7 @@ static sph_status size_pair_lists(sph_event *ev)
         ev->pair_ovf_seen = *ev->pair_ovf_host;
         ev->pairs_grow = true;
     }
-    if (ev->cb.pl.total > 0 && !ev->pairs_grow && !ev->pairs_recount) return SPH_OK;
+    if (ev->cb.pl.total > 0 && !ev->pairs_grow) return SPH_OK;
     if (const char *t = getenv("SPH_PAIR_LISTS"))
         if (atoi(t) == 0) {
             ev->pairs_off = true;
@@ -662,18 +662,11 @@ static sph_status size_pair_lists(sph_event *ev)
         state[perm[j]] = cnt[j];
         rows += std::max(cnt[j] - 1, 0) + margin;
     }
-    if (ev->cb.pl.total > 0 && !ev->pairs_grow && rows <= ev->cb.pl.total) {
-        // recount only: the same allocation, counts of the new state
-        CK(cudaMemcpyAsync(ev->pcnt[0], state.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, ev->stream));
-        ev->pairs_recount = false;
-        return wait_stream(ev);
-    }
-    ev->pairs_recount = false;
     long long total = rows * 3 / 2 + 1024;
     if (ev->pairs_grow) total = std::max<long long>(total, ev->cb.pl.total * 3 / 2);
     else if (const char *t = getenv("SPH_PAIR_TOTAL")) total = std::max<long long>(1, atoll(t));
     const int nparts = (n + 2047) / 2048;
-    const size_t bytes = (size_t)total * (2 * sizeof(double) + 2 * sizeof(int)) + (size_t)(n + 1) * sizeof(long long) +
+    const size_t bytes = (size_t)total * (3 * sizeof(double) + 2 * sizeof(int)) + (size_t)(n + 1) * sizeof(long long) +
                          (size_t)nparts * sizeof(unsigned long long) + 4 * sizeof(int) * (size_t)n + 1024;
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
@@ -699,9 +692,9 @@ static sph_status size_pair_lists(sph_event *ev)
     PairBufs pl{};
     pl.total = total;
     pl.margin = margin;
-    pl.W = static_cast<double *>(m);
-    pl.FAC = pl.W + total;
-    pl.off = reinterpret_cast<long long *>(pl.FAC + total);
+    pl.G = static_cast<double2 *>(m);
+    pl.W = reinterpret_cast<double *>(pl.G + total);
+    pl.off = reinterpret_cast<long long *>(pl.W + total);
     pl.part = reinterpret_cast<unsigned long long *>(pl.off + (n + 1));
     pl.L = reinterpret_cast<int *>(pl.part + nparts);
     pl.P = pl.L + total;
@@ -1145,6 +1138,10 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
     CK(cudaMemcpyAsync(ev->Nq[0], ev->scratch, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st));
     launch_scatter_orig(ev->wguess, ev->scratch, ev->id[0], n, 4, st);
     CK(cudaMemcpyAsync(ev->wguess, ev->scratch, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, st));
+    if (ev->cb.pl.total > 0) {  // the neighbour counts carried with the state follow it
+        launch_scatter_orig_u32((const uint32_t *)ev->pcnt[0], (uint32_t *)ev->pcnt[1], ev->id[0], n, st);
+        CK(cudaMemcpyAsync(ev->pcnt[0], ev->pcnt[1], sizeof(int) * N, cudaMemcpyDeviceToDevice, st));
+    }
     std::vector<int> iota(n);
     for (int i = 0; i < n; ++i) iota[i] = i;
     CK(cudaMemcpyAsync(ev->id[0], iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
@@ -1170,7 +1167,6 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
         if (!in->guess) return fail(SPH_ERR_ARG, "masked field has a null source");
         CK(cudaMemcpyAsync(ev->wguess, in->guess, sizeof(double) * 4 * N, k, st));
     }
-    ev->pairs_recount = true;  // the carried neighbour counts no longer follow the state order
     ev->observed = false;
     return wait_stream(ev);
 }

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kScanThreads) k_rows_apply(int n, const uint32
 // Forward density pass, one warp per particle a.  Candidates of the 3x3 cells pass the
 // single-precision prefilter; a neighbour b < a is decided at once (exact FP64 test when the
 // float test left it undecided) and listed in B; a candidate b > a is queued, and 32 at a time
-// the exact test, W and dW/dr / r run on full warps, are listed in F/W/FAC and summed for a.
+// the exact test, W and dW/dr / r run on full warps, are listed (L, W, G) and summed for a.
 // dpart receives a's unscaled partial sums (self pair and pairs b > a): sigma*, S, N_B, N_S, N_Q.
 __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, const double *__restrict__ y,
                                                                    const float2 *__restrict__ fpos,
@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
     // rows beyond the allocation write nothing (the scan has flagged the stage)
     const int cap = r1 <= pl.total ? (int)(r1 - r0) : 0;
     int *F = pl.L + r0, *Bl = pl.L + (r1 - 1);  // forward up from the start, backward down from the end
-    double *Wr = pl.W + r0, *Fr = pl.FAC + r0;
+    double *Wr = pl.W + r0;
+    double2 *Gr = pl.G + r0;
     double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
     if (lane == 0) {  // the self pair, W(0)
         const double w0 = kernel_w(0.0);
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
             if (slot < cap) {
                 F[slot] = b;
                 Wr[slot] = w;
-                Fr[slot] = fac;
+                Gr[slot] = make_double2(fac * dx, fac * dy);
             }
             sg += w;
             ss = fma(S[b], w, ss);
@@ -325,9 +326,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_bwd(EvView v, con
     }
 }
 
-// Gradient pass, one warp per particle a, over its pairs b > a (F, FAC in a's row) and then
-// b < a (B, with FAC at b's row, slot P): grad_a W_ab = FAC (x_a - x_b) sigma_d / h, then the
-// sums of the per-particle pass: sum grad W, sum X_b grad W, sum u_b grad W.
+// Gradient pass, one warp per particle a, over its pairs b > a (forward entries of a's row, with
+// G = grad_a W_ab h / sigma_d) and then b < a (backward entries: -G of the pair in b's row, slot
+// P), forming the sums of the per-particle pass: sum grad W, sum X_b grad W, sum u_b grad W.
 __global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int stage, const double *__restrict__ y,
                                                                 const double *__restrict__ gin, PairBufs pl,
                                                                 double *__restrict__ gout)
@@ -337,10 +338,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int st
     const int a = blockIdx.x * kWarps + wid;
     if (a >= v.n) return;  // warp-uniform
     const int n = v.n;
-    const double *X = y, *Y = y + n;
     const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * (size_t)n, *Xyy = gin + 3 * (size_t)n;
     const double *Ux = gin + 4 * (size_t)n, *Uy = gin + 5 * (size_t)n;
-    const double xa = X[a], ya = Y[a];
     const long long r0 = pl.off[a], rend = pl.off[a + 1] - 1;
     const int nf = pl.cntF[a], nt = nf + pl.cntB[a];
     double Gx = 0.0, Gy = 0.0, Hx = 0.0, Hy = 0.0;
@@ -349,16 +348,18 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_gradient(EvView v, int st
         const int j = j0 + lane;
         if (j < nt) {
             int b;
-            double fac;
+            double gx, gy;
             if (j < nf) {
                 b = pl.L[r0 + j];
-                fac = pl.FAC[r0 + j];
-            } else {
+                const double2 g = pl.G[r0 + j];
+                gx = g.x;
+                gy = g.y;
+            } else {  // grad_a W_ab = -grad_b W_ba, stored with b's forward pair
                 b = pl.L[rend - (j - nf)];
-                fac = pl.FAC[pl.off[b] + pl.P[rend - (j - nf)]];
+                const double2 g = pl.G[pl.off[b] + pl.P[rend - (j - nf)]];
+                gx = -g.x;
+                gy = -g.y;
             }
-            const double dx = xa - X[b], dy = ya - Y[b];
-            const double gx = fac * dx, gy = fac * dy;
             Gx += gx;
             Gy += gy;
             Hx = fma(Xxx[b], gx, fma(Xyx[b], gy, Hx));

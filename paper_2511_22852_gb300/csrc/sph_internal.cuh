@@ -232,8 +232,9 @@ __device__ __forceinline__ void warp_or(unsigned int *dst, unsigned int v)
 // Half-pair lists of the plain 2D neighbour passes, rebuilt in every stage's density pass.
 // Particle a (sorted index) owns entries [off[a], off[a+1]) of L, P, W, FAC, sized by its
 // neighbour count of the previous stage plus a margin (a prefix scan per stage):
-//   from the row start: its accepted neighbours b > a, ascending (L), with W(r)/sigma_d and
-//      (dW/dr)/r * h/sigma_d of the pair (W, FAC: symmetric in a, b, so computed once);
+//   from the row start: its accepted neighbours b > a, ascending (L), with W(r)/sigma_d of the
+//      pair (W) and grad_a W_ab h/sigma_d = (dW/dr)/r (x_a - x_b) h/sigma_d (G); both are
+//      computed once per pair (W is symmetric in a, b; grad_b W_ba = -grad_a W_ab);
 //   from the row end, downwards: its accepted neighbours b < a, ascending (L), with the slot of
 //      the pair (b, a) in b's row (P).
 // A particle whose neighbours exceed its row (or rows beyond the allocation) flags the stage,
@@ -247,7 +248,8 @@ struct PairBufs {
     long long *off;               // [n + 1] row offsets of this stage
     unsigned long long *part;     // scan partial sums
     int *L, *P, *cntF, *cntB;
-    double *W, *FAC;
+    double *W;
+    double2 *G;
 };
 
 struct CellBufs {
