@@ -55,6 +55,7 @@ class Params(C.Structure):
         ("ntrack", C.c_int), ("pad2", C.c_int), ("tracks", C.c_void_p), ("track_sigma", C.c_double),
         ("inv", C.c_void_p), ("inv_p10", C.c_void_p), ("inv_K", C.c_int), ("inv_nd", C.c_int), ("inv_nx", C.c_int),
         ("pad3", C.c_int), ("inv_xmax", C.c_double),
+        ("eom_model", C.c_int), ("pad4", C.c_int), ("dnmr", C.c_double * 6),
     ]
 
 
@@ -133,6 +134,11 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
     tr = ev.transport
     P.eta_over_s, P.zeta_peak, P.zeta_T_GeV, P.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
     P.tau_pi_coef, P.tau_Pi_ratio, P.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
+    dn = getattr(tr, "dnmr", None)
+    if dn is not None:
+        P.eom_model = 1
+        for k in range(6):
+            P.dnmr[k] = float(dn[k])
     P.newton_tol, P.newton_maxit = newton_tol, newton_maxit
     inv = getattr(ev, "inverse", None)
     if inv is not None:

@@ -83,6 +83,13 @@ typedef struct {
     const double *inv_p10;
     int inv_K, inv_nd, inv_nx, pad3;
     double inv_xmax;
+    /* viscous equations of motion: 0 minimal Israel-Stewart (eqs. min_bul_rel, min_she_rel);
+       1 DNMR without K terms and diffusion couplings (eq. dnmr, with the shear-bulk J terms and
+       the R term phi_7), coefficients as ratios: dnmr[0] = delta_PiPi / tau_Pi,
+       dnmr[1] = lambda_Pipi / (tau_Pi (1/3 - c_s^2)), dnmr[2] = delta_pipi / tau_pi,
+       dnmr[3] = tau_pipi / tau_pi, dnmr[4] = lambda_piPi / tau_pi, dnmr[5] = phi_7 p */
+    int eom_model, pad4;
+    double dnmr[6];
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -849,6 +856,9 @@ typedef struct {
     double pi[4][4], Pv[4][4]; /* pi^{mu nu} and pi^{mu nu}/sigma */
     double eta, zeta, taupi, tauPi;
     double uI; /* u_nu I^nu: energy deposited in the local rest frame per unit time and volume */
+    int model;      /* viscous equations of motion (oc_params.eom_model) */
+    double cs2;     /* speed of sound squared (DNMR lambda_Pipi) */
+    double dnmr[6]; /* DNMR coefficient ratios (oc_params.dnmr) */
 } ppart;
 
 typedef struct {
@@ -915,7 +925,55 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
         for (int m = 0; m < 4; ++m)
             for (int nu = 0; nu < 4; ++nu) pisig += q->pi[m][nu] * G->g[m] * G->g[nu] * sig[m][nu];
         R->dS = (-q->Pi * theta + pisig + q->uI) / (u0 * q->sigma * q->T);
-        R->dBv = -(q->Pi + q->zeta * theta) / (q->tauPi * u0 * q->sigma);
+        if (q->model == 1) {
+            /* DNMR bulk: tau_Pi D Pi + Pi = -zeta theta - delta_PiPi Pi theta + lambda_Pipi pi:sigma;
+               the stored Pi/sigma obeys u^0 d(Pi/sigma)/dx^0 = (D Pi + Pi theta)/sigma (D sigma = -sigma theta) */
+            double dPP = q->dnmr[0] * q->tauPi, lPp = q->dnmr[1] * q->tauPi * (1.0 / 3.0 - q->cs2);
+            double DPi = (-q->Pi - q->zeta * theta - dPP * q->Pi * theta + lPp * pisig) / q->tauPi;
+            R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);
+        } else {
+            R->dBv = -(q->Pi + q->zeta * theta) / (q->tauPi * u0 * q->sigma);
+        }
+        /* DNMR shear: the symmetric, traceless, transverse parts of pi^mu_lambda sigma^{nu lambda}
+           and pi^mu_lambda pi^{nu lambda}, with Delta^mu_alpha = delta^mu_alpha - u^mu u_alpha */
+        double Ppis[4][4], Ppipi[4][4];
+        memset(Ppis, 0, sizeof(Ppis));
+        memset(Ppipi, 0, sizeof(Ppipi));
+        if (q->model == 1) {
+            double ulow[4], Dm[4][4], A[4][4], Bm[4][4], trA = 0.0, trB = 0.0;
+            for (int al = 0; al < 4; ++al) ulow[al] = G->g[al] * u[al];
+            for (int m = 0; m < 4; ++m)
+                for (int al = 0; al < 4; ++al) Dm[m][al] = (m == al ? 1.0 : 0.0) - u[m] * ulow[al];
+            for (int al = 0; al < 4; ++al)
+                for (int be = 0; be < 4; ++be) {
+                    double sa = 0.0, sb = 0.0;
+                    for (int l = 0; l < 4; ++l) {
+                        sa += q->pi[al][l] * G->g[l] * sig[be][l];
+                        sb += q->pi[al][l] * G->g[l] * q->pi[be][l];
+                    }
+                    A[al][be] = sa;
+                    Bm[al][be] = sb;
+                }
+            for (int al = 0; al < 4; ++al)
+                for (int be = 0; be < 4; ++be) {
+                    double Dl = (al == be ? G->g[al] : 0.0) - ulow[al] * ulow[be]; /* Delta_{alpha beta} */
+                    trA += Dl * A[al][be];
+                    trB += Dl * Bm[al][be];
+                }
+            for (int m = 0; m < 4; ++m)
+                for (int nu = 0; nu < 4; ++nu) {
+                    double pa = 0.0, pb = 0.0;
+                    for (int al = 0; al < 4; ++al)
+                        for (int be = 0; be < 4; ++be) {
+                            double w2 = 0.5 * (Dm[m][al] * Dm[nu][be] + Dm[m][be] * Dm[nu][al]);
+                            pa += w2 * A[al][be];
+                            pb += w2 * Bm[al][be];
+                        }
+                    double Du_up = (m == nu ? G->gi[m] : 0.0) - u[m] * u[nu]; /* Delta^{mu nu} */
+                    Ppis[m][nu] = pa - Du_up * trA / 3.0;
+                    Ppipi[m][nu] = pb - Du_up * trB / 3.0;
+                }
+        }
         double alow[4];
         for (int al = 0; al < 4; ++al) alow[al] = G->g[al] * Du[al];
         for (int i = 1; i < 4; ++i)
@@ -929,7 +987,18 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
                     pia += q->pi[i][al] * alow[al];
                 }
                 double coup = u[i] * pja + u[j] * pia;
-                double rhs = (-q->pi[i][j] + 2.0 * q->eta * sig[i][j] - 4.0 / 3.0 * q->taupi * q->pi[i][j] * theta) / q->taupi;
+                double rhs;
+                if (q->model == 1) {
+                    /* tau_pi D pi + pi = 2 eta sigma - delta_pipi pi theta - tau_pipi <pi sigma>
+                       + phi_7 <pi pi> + lambda_piPi Pi sigma */
+                    double dpp = q->dnmr[2] * q->taupi, tpp = q->dnmr[3] * q->taupi;
+                    double lpP = q->dnmr[4] * q->taupi, ph7 = q->dnmr[5] / q->p;
+                    rhs = (-q->pi[i][j] + 2.0 * q->eta * sig[i][j] - dpp * q->pi[i][j] * theta - tpp * Ppis[i][j] +
+                           ph7 * Ppipi[i][j] + lpP * q->Pi * sig[i][j]) /
+                          q->taupi;
+                } else {
+                    rhs = (-q->pi[i][j] + 2.0 * q->eta * sig[i][j] - 4.0 / 3.0 * q->taupi * q->pi[i][j] * theta) / q->taupi;
+                }
                 double dpi = (rhs - chr - coup) / u0;
                 R->dPv[i][j] = dpi / q->sigma - q->pi[i][j] * dsig / (q->sigma * q->sigma);
             }
@@ -1020,7 +1089,7 @@ static void densities_eos(const oc_params *P, long n, double tau, const double *
 
 /* EoS derivative outputs are kept aside for the rates */
 typedef struct {
-    double ps, pn[3];
+    double ps, pn[3], cs2;
 } eosder_t;
 
 int oc_stage(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *dydt, double *aux,
@@ -1051,6 +1120,7 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
         oc_eos_invert_ws(P, aux[1 * n + a], nr, gs, out, NULL);
         ed[a].ps = out[6];
         for (int c = 0; c < 3; ++c) ed[a].pn[c] = out[7 + c];
+        ed[a].cs2 = out[10];
         double u[4] = {aux[14 * n + a], 0, 0, 0};
         for (int i = 0; i < dim; ++i) u[1 + i] = y[(dim + i) * n + a];
         double sigma = aux[16 * n + a];
@@ -1134,6 +1204,9 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
         q.e = aux[10 * n + a];
         q.ps = ed[a].ps;
         for (int c = 0; c < 3; ++c) q.pn[c] = ed[a].pn[c];
+        q.cs2 = ed[a].cs2;
+        q.model = P->eom_model;
+        for (int k = 0; k < 6; ++k) q.dnmr[k] = P->dnmr[k];
         q.Pi = aux[13 * n + a];
         q.Bv = P->viscous ? y[(2 * dim + 1) * n + a] : 0.0;
         memcpy(q.pi, &pif[16 * a], sizeof(q.pi));

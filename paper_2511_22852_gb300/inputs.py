@@ -96,6 +96,14 @@ class Transport:
     tau_pi_coef: float = 5.0      # tau_pi = coef * eta / (eps + p)
     tau_Pi_ratio: float = 1.0     # tau_Pi = ratio * tau_pi
     cs2_cap: float = 1.0          # causal cap on c_s^2 in the acceleration system
+    # None: minimal Israel-Stewart; else DNMR with the coefficient ratios (delta_PiPi / tau_Pi,
+    # lambda_Pipi / (tau_Pi (1/3 - c_s^2)), delta_pipi / tau_pi, tau_pipi / tau_pi,
+    # lambda_piPi / tau_pi, phi_7 p), e.g. DNMR_14_MOMENT
+    dnmr: tuple | None = None
+
+
+# DNMR coefficient ratios of the 14-moment approximation for a massless Boltzmann gas
+DNMR_14_MOMENT = (2.0 / 3.0, 8.0 / 5.0, 4.0 / 3.0, 10.0 / 7.0, 6.0 / 5.0, 9.0 / 70.0)
 
 
 @dataclass

@@ -87,6 +87,18 @@ MUTATIONS = [
      "acc += 2.0 * G->g[i] * u[i] * a[i];", "test_oracle_physics.py::test_shifted_gubser_3p1_against_closed_form"),
     ("milne_norm_flat_metric", "uu += -G.g[1 + i] * ui * ui;", "uu += ui * ui;",
      "test_oracle_physics.py::test_shifted_gubser_3p1_against_closed_form"),
+    ("dnmr_drop_tau_pipi", "dpp * q->pi[i][j] * theta - tpp * Ppis[i][j] +", "dpp * q->pi[i][j] * theta +",
+     "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("dnmr_phi7_sign", "ph7 * Ppipi[i][j] + lpP * q->Pi * sig[i][j])", "-ph7 * Ppipi[i][j] + lpP * q->Pi * sig[i][j])",
+     "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("dnmr_drop_lambda_piPi", "ph7 * Ppipi[i][j] + lpP * q->Pi * sig[i][j])", "ph7 * Ppipi[i][j])",
+     "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("dnmr_lambda_Pipi_sign", "dPP * q->Pi * theta + lPp * pisig) / q->tauPi;",
+     "dPP * q->Pi * theta - lPp * pisig) / q->tauPi;", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("dnmr_projector_trace", "Ppis[m][nu] = pa - Du_up * trA / 3.0;", "Ppis[m][nu] = pa - Du_up * trA / 2.0;",
+     "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("dnmr_bulk_drop_volume_rate", "R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);",
+     "R->dBv = DPi / (u0 * q->sigma);", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
 ]
 
 

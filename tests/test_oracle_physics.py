@@ -18,6 +18,8 @@
   validation", eqs. tau_prime to shifted_viscous_Gubser_ueta with H0 = 0) against its closed
   form, with second-order convergence: pins the longitudinal flow u^eta, the Christoffel
   coupling of u^eta to u^tau and the metric factor tau^2 in the normalisation of u.
+* DNMR equations of motion (eq. dnmr: shear and bulk J terms and phi_7, 14-moment
+  coefficients) on Bjorken lattices (2+1D and 3+1D) against ODEs reduced by hand.
 """
 import numpy as np
 import pytest
@@ -264,3 +266,81 @@ def test_shifted_gubser_3p1_convergence():
                                dtau=0.005, nsteps=40)
     for a, b in zip(c, f):
         assert b < 0.35 * a, (c, f)
+
+
+def _bjorken_dnmr_rhs(tr, thermo, c):
+    """Longitudinal Bjorken flow with the DNMR equations (shear and bulk J terms, phi_7), reduced by
+    hand: with pi^{xx} = pi^{yy} = Phi/2, tau^2 pi^{eta eta} = -Phi, theta = 1/tau,
+    sigma^{xx} = 1/(3 tau) and tau^2 sigma^{eta eta} = -2/(3 tau), the contractions are
+    pi:sigma = Phi/tau, <pi sigma>^{xx} = Phi/(6 tau), <pi pi>^{xx} = Phi^2/4, so
+      tau_Pi dPi/dtau + Pi = -zeta/tau - delta_PiPi Pi/tau + lambda_Pipi Phi/tau,
+      tau_pi dPhi/dtau + Phi = 4 eta/(3 tau) - delta_pipi Phi/tau - tau_pipi Phi/(3 tau)
+                               + phi_7 Phi^2/2 + 2 lambda_piPi Pi/(3 tau)."""
+    def rhs(tau, Y):
+        T, Pi, Phi = Y
+        p, s, dsdT = thermo(T)
+        e = T * s - p
+        cs2 = s / (T * dsdT)
+        eta = tr.eta_over_s * s
+        zeta = tr.zeta_peak * np.exp(-(T * I.HBARC - tr.zeta_T_GeV) ** 2 / (2 * tr.zeta_w_GeV ** 2)) * s
+        taupi = tr.tau_pi_coef * eta / (e + p)
+        tauPi = tr.tau_Pi_ratio * taupi
+        dPP, lPp = c[0] * tauPi, c[1] * tauPi * (1.0 / 3.0 - cs2)
+        dpp, tpp, lpP, ph7 = c[2] * taupi, c[3] * taupi, c[4] * taupi, c[5] / p
+        dT = -(e + p + Pi - Phi) / tau / (T * dsdT)
+        dPi = (-Pi - zeta / tau - dPP * Pi / tau + lPp * Phi / tau) / tauPi
+        dPhi = (-Phi + 4 * eta / (3 * tau) - dpp * Phi / tau - tpp * Phi / (3 * tau) + ph7 * Phi * Phi / 2
+                + 2 * lpP * Pi / (3 * tau)) / taupi
+        return [dT, dPi, dPhi]
+    return rhs
+
+
+@pytest.mark.parametrize("T0", [0.16, 0.3])
+def test_bjorken_dnmr_against_ode(T0):
+    """DNMR equations of motion (14-moment coefficients) on a 2+1D Bjorken lattice: the centre
+    particle follows the hand-reduced ODEs; the coefficients move Pi and Phi well beyond the
+    tolerances relative to minimal Israel-Stewart (checked below), so each term is exercised."""
+    ev = I.bjorken_lattice_2p1(T0_GeV=T0, n_side=41, nsteps=100)
+    ev.transport.dnmr = I.DNMR_14_MOMENT
+    tr = ev.transport
+    thermo = _eos_fns(ev.eos)
+    run = O.OracleRun.start(ev)
+    c = int(np.argmin(ev.x[0] ** 2 + ev.x[1] ** 2))
+    aux0, _ = run.observe()
+    run.step(ev.nsteps)
+    aux, _ = run.observe()
+    y0 = [aux0[O.AUX["T"]][c], 0.0, 0.0]
+    sol = solve_ivp(_bjorken_dnmr_rhs(tr, thermo, I.DNMR_14_MOMENT), (ev.tau0, run.tau), y0, rtol=1e-12, atol=1e-14)
+    Tode, Piode, Phiode = sol.y[:, -1]
+    sigma = aux[O.AUX["sigma"]][c]
+    assert abs(aux[O.AUX["T"]][c] / Tode - 1) < 1e-6
+    assert abs(aux[O.AUX["Pi"]][c] - Piode) < 2e-3 * abs(Piode)
+    pixx, pixy, piyy = sigma * run.y[6][c], sigma * run.y[7][c], sigma * run.y[8][c]
+    assert abs(pixx - Phiode / 2) < 1e-4 * abs(Phiode) and abs(piyy - Phiode / 2) < 1e-4 * abs(Phiode)
+    assert abs(pixy) < 1e-10 * abs(Phiode)
+    # minimal IS (delta_PiPi = tau_Pi, delta_pipi = 4/3 tau_pi, no other terms) lands elsewhere
+    mis = solve_ivp(_bjorken_dnmr_rhs(tr, thermo, (1.0, 0.0, 4.0 / 3.0, 0.0, 0.0, 0.0)), (ev.tau0, run.tau), y0,
+                    rtol=1e-12, atol=1e-14).y[:, -1]
+    assert abs(mis[2] - Phiode) > 20 * 1e-4 * abs(Phiode) and abs(mis[1] - Piode) > 5 * 2e-3 * abs(Piode)
+
+
+def test_bjorken_3p1_dnmr_against_ode():
+    """The same DNMR ODEs on the 3+1D Milne lattice (the longitudinal tensor components evolved
+    explicitly): pi^{xx} = pi^{yy} = Phi/2, off-diagonal components zero."""
+    ev = I.bjorken_lattice_3p1(half_widths=(1.04, 1.04, 1.04), spacings=(0.08, 0.08, 0.08), h=0.2, nsteps=20)
+    ev.transport.dnmr = I.DNMR_14_MOMENT
+    thermo = _eos_fns(ev.eos)
+    run = O.OracleRun.start(ev)
+    c = int(np.argmin(ev.x[0] ** 2 + ev.x[1] ** 2 + ev.x[2] ** 2))
+    aux0, _ = run.observe()
+    run.step(ev.nsteps)
+    aux, _ = run.observe()
+    sol = solve_ivp(_bjorken_dnmr_rhs(ev.transport, thermo, I.DNMR_14_MOMENT), (ev.tau0, run.tau),
+                    [aux0[O.AUX["T"]][c], 0.0, 0.0], rtol=1e-12, atol=1e-14)
+    Tode, Piode, Phiode = sol.y[:, -1]
+    sigma = aux[O.AUX["sigma"]][c]
+    assert abs(aux[O.AUX["T"]][c] / Tode - 1) < 1e-6
+    assert abs(aux[O.AUX["Pi"]][c] - Piode) < 2e-3 * abs(Piode)
+    assert abs(sigma * run.y[8][c] - Phiode / 2) < 1e-3 * abs(Phiode)
+    assert abs(sigma * run.y[11][c] - Phiode / 2) < 1e-3 * abs(Phiode)
+    assert max(abs(run.y[9][c]), abs(run.y[10][c]), abs(run.y[12][c])) < 1e-9 * abs(run.y[8][c])
