@@ -343,6 +343,35 @@ def bench_freezeout(Bd, I, steps: int = 40):
     return out
 
 
+def bench_dnmr(Bd, I, steps: int = 40):
+    """The DNMR equations of motion (14-moment coefficients) against minimal Israel-Stewart on
+    the 40k-particle event: device ms per step (CUDA graphs, CUDA events) and the EoM pass."""
+    import torch
+    out = {"workload": f"40k-particle viscous BSQ event, {steps} steps, DNMR (14-moment coefficients) vs minimal IS"}
+    for name, dn in (("min_is", None), ("dnmr", I.DNMR_14_MOMENT)):
+        ev = I.viscous_bsq_2p1()
+        ev.transport.dnmr = dn
+        st = torch.cuda.Stream()
+        g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream)
+        g.step(2, sync=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record(st)
+            g.step(steps)
+            b.record(st)
+        torch.cuda.synchronize()
+        out[name + "_ms_per_step"] = a.elapsed_time(b) / steps
+        g.free()
+        gp = Bd.GpuEvent(ev, use_graph=False, stream=st.cuda_stream, profile=True)
+        gp.step(4)
+        torch.cuda.synchronize()
+        kt = gp.kernel_times()
+        out[name + "_eom_ms_per_pass"] = kt["eom"][0] / max(1, kt["eom"][1])
+        gp.free()
+    out["overhead"] = out["dnmr_ms_per_step"] / out["min_is_ms_per_step"] - 1.0
+    return out
+
+
 def bench_offline_eos(Bd, I, steps: int = 20):
     """The offline EoS inverter (interpolation in an inverted (s, n/s) table) against the online
     Newton inversion on the 40k-particle event: device ms per step and per EoS pass (profile
@@ -600,6 +629,7 @@ def run_ours(args):
             out["serving"] = serving_bench(Bd, I, args.serving_events, args.serving_steps)
         out["mixed_single_event"] = bench_mixed_single(Bd, I)
         out["freezeout"] = bench_freezeout(Bd, I)
+        out["dnmr"] = bench_dnmr(Bd, I)
         out["offline_eos"] = bench_offline_eos(Bd, I)
         if not args.no_3d:
             out["config_3p1d"] = bench_3p1d(Bd, I)

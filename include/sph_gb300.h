@@ -255,6 +255,26 @@ sph_status sph_eos_build_inverse(sph_eos *eos, int32_t per_decade, int32_t decad
 sph_status sph_set_eos_mode(sph_event *ev, int32_t mode);
 
 /* ---------------------------------------------------------------------------
+ * Viscous equations of motion (Sec. "Equations of motion": eqs. min_bul_rel, min_she_rel and
+ * eq. dnmr).  SPH_EOM_MIN_IS (the default): minimal Israel-Stewart.  SPH_EOM_DNMR: DNMR without
+ * the K terms and the couplings to diffusion, with the shear-bulk J terms and the R term phi_7
+ * (phi_1 = phi_3 = phi_6 = 0):
+ *   tau_Pi D Pi + Pi = -zeta theta - delta_PiPi Pi theta + lambda_Pipi pi:sigma,
+ *   tau_pi D pi^<mu nu> + pi^{mu nu} = 2 eta sigma^{mu nu} - delta_pipi pi^{mu nu} theta
+ *       - tau_pipi pi_lambda^<mu sigma^nu>lambda + phi_7 pi_alpha^<mu pi^nu>alpha
+ *       + lambda_piPi Pi sigma^{mu nu};
+ * coeffs[6] (host, copied): delta_PiPi / tau_Pi, lambda_Pipi / (tau_Pi (1/3 - c_s^2)),
+ * delta_pipi / tau_pi, tau_pipi / tau_pi, lambda_piPi / tau_pi, phi_7 p (the 14-moment values
+ * for a massless gas are 2/3, 8/5, 4/3, 10/7, 6/5, 9/70).  coeffs is ignored for
+ * SPH_EOM_MIN_IS.  Applies to the plain and mixed single-event forms, 2D and 3D (the serving
+ * form runs minimal Israel-Stewart).  Errors: SPH_ERR_ARG for an unknown model, missing or
+ * non-finite coefficients; SPH_ERR_TIMEOUT if the event's stream does not drain.
+ * ------------------------------------------------------------------------- */
+#define SPH_EOM_MIN_IS 0
+#define SPH_EOM_DNMR 1
+sph_status sph_set_viscous_eom(sph_event *ev, int32_t model, const double *coeffs);
+
+/* ---------------------------------------------------------------------------
  * Energy-momentum source of jet tracks (eq. conservation_source with I^nu != 0, Sec.
  * "Equations of motion"; Cartesian events).  Track k (tracks[8 k ..] = x0, y0, z0, n_x, n_y,
  * n_z, t0, dE/dx, host memory, n a unit vector, dE/dx in fm^-2) moves at the speed of light

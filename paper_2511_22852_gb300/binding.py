@@ -35,7 +35,8 @@ EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_even
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
-           "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode"]
+           "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode",
+           "sph_set_viscous_eom"]
 SPH_EOS_ONLINE, SPH_EOS_OFFLINE = 0, 1
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
@@ -128,6 +129,7 @@ def lib():
             "sph_server_drain": (i32, [vp, C.c_double]),
             "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
             "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
+            "sph_set_viscous_eom": (i32, [vp, i32, vp]),
             "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
             "sph_eos_build_inverse": (i32, [vp, i32, i32, i32, i32, C.c_double]),
             "sph_set_eos_mode": (i32, [vp, i32]),
@@ -226,6 +228,14 @@ def sph_set_eos_mode(h, mode: int):
 def sph_set_jets(h, tracks, sigma: float):
     tr = _f64(tracks).reshape(-1, 8) if tracks is not None else np.zeros((0, 8))
     _check(lib().sph_set_jets(h, int(tr.shape[0]), _ptr(tr) if tr.size else None, float(sigma)))
+
+
+SPH_EOM_MIN_IS, SPH_EOM_DNMR = 0, 1
+
+
+def sph_set_viscous_eom(h, model: int, coeffs=None):
+    c = _f64(coeffs) if coeffs is not None else None
+    _check(lib().sph_set_viscous_eom(h, int(model), _ptr(c) if c is not None else None))
 
 
 def sph_freezeout_setup(h, e_fo: float, capacity: int):
@@ -417,6 +427,9 @@ class GpuEvent:
         jets = getattr(ev, "jets", None)
         if jets is not None and len(jets.tracks):
             sph_set_jets(self.h, jets.tracks, jets.sigma)
+        dnmr = getattr(ev.transport, "dnmr", None)
+        if dnmr is not None:
+            sph_set_viscous_eom(self.h, SPH_EOM_DNMR, dnmr)
 
     def step(self, nsteps: int, sync: bool = False):
         sph_step(self.h, nsteps, SPH_SYNC if sync else 0)

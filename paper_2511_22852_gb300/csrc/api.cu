@@ -1012,7 +1012,10 @@ sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, dou
     if (ntrack > 0 && ev->milne) return fail(SPH_ERR_ARG, "jet sources are defined in Cartesian coordinates");
     for (int64_t k = 0; k < 8 * ntrack; ++k)
         if (!std::isfinite(tracks[k])) return fail(SPH_ERR_ARG, "non-finite track parameter");
-    CK(cudaStreamSynchronize(ev->stream));
+    {
+        sph_status ws = wait_stream(ev);  // bounded: the buffers below may be in use
+        if (ws != SPH_OK) return ws;
+    }
     if (ntrack > ev->ntrack || !ev->d_tracks) {
         sph_status s = dalloc(ev, reinterpret_cast<void **>(&ev->d_tracks), sizeof(double) * 8 * (size_t)(ntrack > 0 ? ntrack : 1));
         if (s != SPH_OK) return s;
@@ -1035,12 +1038,44 @@ sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, dou
     return SPH_OK;
 }
 
+sph_status sph_set_viscous_eom(sph_event *ev, int32_t model, const double *coeffs)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (model != SPH_EOM_MIN_IS && model != SPH_EOM_DNMR) return fail(SPH_ERR_ARG, "unknown equations of motion");
+    if (model == SPH_EOM_DNMR) {
+        if (!coeffs) return fail(SPH_ERR_ARG, "DNMR needs its six coefficient ratios");
+        for (int k = 0; k < 6; ++k)
+            if (!std::isfinite(coeffs[k])) return fail(SPH_ERR_ARG, "non-finite DNMR coefficient");
+    }
+    {
+        sph_status ws = wait_stream(ev);
+        if (ws != SPH_OK) return ws;
+    }
+    ev->tr.model = model;
+    for (int k = 0; k < 6; ++k) ev->tr.dnmr[k] = model == SPH_EOM_DNMR ? coeffs[k] : 0.0;
+    if (ev->gexec) {  // the parameters are part of the captured step: capture it again
+        cudaGraphExecDestroy(ev->gexec);
+        ev->gexec = nullptr;
+    }
+    if (ev->graph) {
+        cudaGraphDestroy(ev->graph);
+        ev->graph = nullptr;
+    }
+    ev->graph_ready = false;
+    ev->kernels_per_step = 0;
+    ev->observed = false;
+    return SPH_OK;
+}
+
 sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity)
 {
     if (!ev) return fail(SPH_ERR_ARG, "null event");
     if (ev->dim != 2) return fail(SPH_ERR_ARG, "the freeze-out surface is implemented for dim = 2");
     if (!(e_fo > 0.0) || capacity < 1) return fail(SPH_ERR_ARG, "e_fo > 0 and capacity >= 1 required");
-    CK(cudaStreamSynchronize(ev->stream));
+    {
+        sph_status ws = wait_stream(ev);  // bounded: the buffers below may be in use
+        if (ws != SPH_OK) return ws;
+    }
     const size_t N = (size_t)(ev->n > 0 ? ev->n : 1);
     sph_status s;
     if (!ev->eprev[0]) {
@@ -1061,7 +1096,10 @@ sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity)
     // NaN: no previous value, so the first step after setup only records e
     CK(cudaMemsetAsync(ev->eprev[0], 0xFF, sizeof(double) * N, ev->stream));
     CK(cudaMemsetAsync(ev->fo.count, 0, sizeof(unsigned long long), ev->stream));
-    CK(cudaStreamSynchronize(ev->stream));
+    {
+        sph_status ws = wait_stream(ev);  // bounded: the buffers below may be in use
+        if (ws != SPH_OK) return ws;
+    }
     ev->e_fo = e_fo;
     ev->fo_on = true;
     if (ev->gexec) {  // the step graph changes: capture it again

@@ -214,16 +214,47 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
         double itp = (e + p) / (v.tr.tau_pi_coef * eta);
         double itPi = itp / v.tr.tau_Pi_ratio;
         double iT = 1.0 / T;
+        const bool dnmr = v.tr.model == 1;
         dS = (ig * isg * iT) * (pisig - Pi * th);
-        dBv = (-ig * isg * itPi) * (zeta * th + Pi);
+        if (dnmr) {
+            // tau_Pi D Pi + Pi = -zeta theta - delta_PiPi Pi theta + lambda_Pipi pi:sigma; the stored
+            // Pi/sigma obeys u0 d(Pi/sigma)/dtau = (D Pi + Pi theta)/sigma
+            const double cs2 = eos[10 * n + a];
+            dBv = (ig * isg) * ((-itPi) * (zeta * th + Pi) + ((1.0 - v.tr.dnmr[0]) * Pi) * th +
+                                (v.tr.dnmr[1] * (1.0 / 3.0 - cs2)) * pisig);
+        } else {
+            dBv = (-ig * isg * itPi) * (zeta * th + Pi);
+        }
         // pi^{j alpha} a_alpha with the lowered four-acceleration (u^0 du^0/dx^0, -u^0 a^i)
         Aff pax = g * (pvx * dg - (pxx * ax + pxy * ay));
         Aff pay = g * (pvy * dg - (pxy * ax + pyy * ay));
         // d pi^{ij}/d tau = [(2 eta sigma^{ij} - pi^{ij}) / tau_pi - 4/3 pi^{ij} theta - coupling] / u0
         const double f43 = 4.0 / 3.0;
-        Aff dpxx = ig * (itp * (2.0 * eta * sxx + (-pxx)) - (f43 * pxx) * th - 2.0 * ux * pax);
-        Aff dpxy = ig * (itp * (2.0 * eta * sxy + (-pxy)) - (f43 * pxy) * th - (ux * pay + uy * pax));
-        Aff dpyy = ig * (itp * (2.0 * eta * syy + (-pyy)) - (f43 * pyy) * th - 2.0 * uy * pay);
+        Aff dpxx, dpxy, dpyy;
+        if (dnmr) {
+            // DNMR: - delta_pipi pi theta - tau_pipi <pi sigma> + phi_7 <pi pi> + lambda_piPi Pi sigma,
+            // <A>^{ij} = (A^{ij} + A^{ji})/2 - Delta^{ij} tr A / 3 for transverse pi and sigma;
+            // A^{ij} = pi^{i0} sigma^{j0} - pi^{ix} sigma^{jx} - pi^{iy} sigma^{jy} (pi^{i eta} = 0)
+            const double c2 = v.tr.dnmr[2], c3 = v.tr.dnmr[3], c4 = v.tr.dnmr[4], f7 = itp * v.tr.dnmr[5] / p;
+            const Aff Axx = pvx * svx - pxx * sxx - pxy * sxy, Axy = pvx * svy - pxx * sxy - pxy * syy;
+            const Aff Ayx = pvy * svx - pxy * sxx - pyy * sxy, Ayy = pvy * svy - pxy * sxy - pyy * syy;
+            const double dxx = (1.0 + ux * ux) / 3.0, dxy = ux * uy / 3.0, dyy = (1.0 + uy * uy) / 3.0;  // -Delta^{ij}/3
+            const Aff PAxx = Axx + dxx * pisig, PAxy = 0.5 * (Axy + Ayx) + dxy * pisig, PAyy = Ayy + dyy * pisig;
+            const double trB = vpv * vpv - 2.0 * (pvx * pvx + pvy * pvy) + pxx * pxx + 2.0 * pxy * pxy + pyy * pyy + pee * pee;
+            const double PBxx = pvx * pvx - pxx * pxx - pxy * pxy + dxx * trB;
+            const double PBxy = pvx * pvy - pxx * pxy - pxy * pyy + dxy * trB;
+            const double PByy = pvy * pvy - pxy * pxy - pyy * pyy + dyy * trB;
+            dpxx = ig * (itp * (2.0 * eta * sxx + (-pxx)) + aff(f7 * PBxx) - (c2 * pxx) * th - c3 * PAxx + (c4 * Pi) * sxx -
+                         2.0 * ux * pax);
+            dpxy = ig * (itp * (2.0 * eta * sxy + (-pxy)) + aff(f7 * PBxy) - (c2 * pxy) * th - c3 * PAxy + (c4 * Pi) * sxy -
+                         (ux * pay + uy * pax));
+            dpyy = ig * (itp * (2.0 * eta * syy + (-pyy)) + aff(f7 * PByy) - (c2 * pyy) * th - c3 * PAyy + (c4 * Pi) * syy -
+                         2.0 * uy * pay);
+        } else {
+            dpxx = ig * (itp * (2.0 * eta * sxx + (-pxx)) - (f43 * pxx) * th - 2.0 * ux * pax);
+            dpxy = ig * (itp * (2.0 * eta * sxy + (-pxy)) - (f43 * pxy) * th - (ux * pay + uy * pax));
+            dpyy = ig * (itp * (2.0 * eta * syy + (-pyy)) - (f43 * pyy) * th - 2.0 * uy * pay);
+        }
         double isg2 = isg * isg;
         dPxx = isg * dpxx - (pxx * isg2) * dsg;
         dPxy = isg * dpxy - (pxy * isg2) * dsg;

@@ -77,6 +77,11 @@ struct EosDev {
 struct TransportDev {
     int viscous;
     double eta_over_s, zeta_peak, zeta_T_GeV, zeta_w_GeV, tau_pi_coef, tau_Pi_ratio, cs2_cap;
+    // viscous equations of motion: 0 minimal Israel-Stewart, 1 DNMR (shear and bulk J terms,
+    // phi_7) with the ratios delta_PiPi/tau_Pi, lambda_Pipi/(tau_Pi (1/3 - c_s^2)),
+    // delta_pipi/tau_pi, tau_pipi/tau_pi, lambda_piPi/tau_pi, phi_7 p
+    int model;
+    double dnmr[6];
 };
 
 // everything a kernel of one event needs, passed by value

@@ -504,7 +504,18 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
         const double taupi = v.tr.tau_pi_coef * eta / (e + p);
         const double tauPi = v.tr.tau_Pi_ratio * taupi;
         dS = (ig * isg / T) * (pisig - Pi * th);
-        dBv = (-ig * isg / tauPi) * (zeta * th + Pi);
+        const bool dnmr = v.tr.model == 1;
+        if (dnmr) {  // DNMR bulk (see the 2+1D equations of motion)
+            const double cs2 = eos[10 * n + a];
+            dBv = (ig * isg) * ((-1.0 / tauPi) * (zeta * th + Pi) + ((1.0 - v.tr.dnmr[0]) * Pi) * th +
+                                (v.tr.dnmr[1] * (1.0 / 3.0 - cs2)) * pisig);
+        } else {
+            dBv = (-ig * isg / tauPi) * (zeta * th + Pi);
+        }
+        double trB = 0.0;  // pi:pi
+        if (dnmr)
+            for (int m = 0; m < 4; ++m)
+                for (int l = 0; l < 4; ++l) trB += pi[m][l] * G.g[m] * G.g[l] * pi[m][l];
         A3 alow[4];
         for (int al = 0; al < 4; ++al) alow[al] = G.g[al] * Du[al];
         const double itp = 1.0 / taupi;
@@ -518,7 +529,25 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
                     pja = pja + pi[j][al] * alow[al];
                     pia = pia + pi[i][al] * alow[al];
                 }
-                A3 rhs = itp * (2.0 * eta * sg[i][j] - (4.0 / 3.0 * taupi * pi[i][j]) * th + (-pi[i][j]));
+                A3 rhs;
+                if (dnmr) {
+                    // - delta_pipi pi theta - tau_pipi <pi sigma> + phi_7 <pi pi> + lambda_piPi Pi sigma with
+                    // <A>^{ij} = (A^{ij} + A^{ji})/2 - Delta^{ij} tr A / 3 (pi, sigma transverse)
+                    A3 Aij = k3(0.0), Aji = k3(0.0);
+                    double Bij = 0.0;
+                    for (int l = 0; l < 4; ++l) {
+                        Aij = Aij + (pi[i][l] * G.g[l]) * sg[j][l];
+                        Aji = Aji + (pi[j][l] * G.g[l]) * sg[i][l];
+                        Bij += pi[i][l] * G.g[l] * pi[j][l];
+                    }
+                    const double Dij = (i == j ? G.gi[i] : 0.0) - u[i] * u[j];
+                    const A3 PA = 0.5 * (Aij + Aji) - (Dij / 3.0) * pisig;
+                    const double PB = Bij - Dij * trB / 3.0;
+                    rhs = itp * (2.0 * eta * sg[i][j] + (-pi[i][j]) + k3(v.tr.dnmr[5] / p * PB)) -
+                          (v.tr.dnmr[2] * pi[i][j]) * th - v.tr.dnmr[3] * PA + (v.tr.dnmr[4] * Pi) * sg[i][j];
+                } else {
+                    rhs = itp * (2.0 * eta * sg[i][j] - (4.0 / 3.0 * taupi * pi[i][j]) * th + (-pi[i][j]));
+                }
                 A3 dpi = ig * (rhs + (-chr) - (u[i] * pja + u[j] * pia));
                 A3 x = isg * dpi - (pi[i][j] * isg * isg) * dsg;
                 dPv[i][j] = x;

@@ -42,12 +42,19 @@ def state_errors(g, run):
             "Bv": relerr(st["BV"], y[5]), "Pv": relerr(st["PV"], y[6:9])}
 
 
+def _with_dnmr(ev):
+    """The event with the DNMR equations of motion (14-moment coefficients)."""
+    ev.transport.dnmr = I.DNMR_14_MOMENT
+    return ev
+
+
 CASES = {
     "gubser": lambda: I.gubser_ideal_2p1(),
     "bsq_small": lambda: I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20),
     "blob_causal": lambda: I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS),
     "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
     "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2)),
+    "bsq_small_dnmr": lambda: _with_dnmr(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20)),
 }
 def _blob3_jets():
     ev = I.smooth_blob_3d(milne=False, flow=0.3, eos=I.CAUSAL_EOS)
@@ -63,6 +70,7 @@ CASES3 = {
         jets=I.JetTracks(tracks=np.array([[-0.6, 0.1, -0.05, 1.0, 0.0, 0.0, 1.0, 5.0 / I.HBARC]]), sigma=0.3)),
     "blob3_cart_jets": _blob3_jets,
     "gubser_shifted3": lambda: I.gubser_shifted_3p1(t0=2.0),
+    "blob3_milne_dnmr": lambda: _with_dnmr(I.smooth_blob_3d(milne=True, flow=0.3)),
 }
 
 
@@ -252,7 +260,8 @@ def test_graph_and_stream_launches_are_bitwise_identical(Bd):
     b.free()
 
 
-@pytest.mark.parametrize("case,nsteps", [("gubser", 60), ("bsq_small", 150), ("blob_causal", 100)])
+@pytest.mark.parametrize("case,nsteps", [("gubser", 60), ("bsq_small", 150), ("blob_causal", 100),
+                                        ("bsq_small_dnmr", 100)])
 def test_evolution(Bd, case, nsteps):
     ev = CASES[case]()
     g = Bd.GpuEvent(ev, use_graph=True)
