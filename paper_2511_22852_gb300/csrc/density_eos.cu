@@ -259,21 +259,20 @@ __global__ void __launch_bounds__(32, 12) k_eos2(EvView v, int stage, const doub
     if (threadIdx.x == 0) wpart[blockIdx.x] = wcontrib;
 }
 
-// Serving form: the same EoS pass over the segmented arena.  Persistent blocks claim chunks
-// of 64 particles from a counter (the Newton work per particle varies, so a static split
-// leaves a tail).  A warp never straddles two events, so the work-rate partial of every warp
-// of an event's range goes to wpart[a / 32] and the per-event counters are warp-aggregated.
-__global__ void __launch_bounds__(64, 6) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
+// Serving form: the same EoS pass over the segmented arena.  Persistent one-warp blocks claim
+// chunks of 32 particles from a counter (the Newton work per particle varies, so a static split,
+// or coarser chunks, leave a tail).  A warp never straddles two events, so the work-rate partial
+// of every warp of an event's range goes to wpart[a / 32] and the per-event counters are
+// warp-aggregated.
+__global__ void __launch_bounds__(32, 12) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
 {
-    __shared__ int s_chunk;
     const BatchTable *T = A.tab;
     const int hi = T->hi;
     const size_t P = (size_t)A.P;
     for (;;) {
-        if (threadIdx.x == 0) s_chunk = (int)atomicAdd(&A.claim[CLAIM_EOS], 1u);
-        __syncthreads();
-        const int base = s_chunk * 64;
-        __syncthreads();
+        int chunk = 0;
+        if (threadIdx.x == 0) chunk = (int)atomicAdd(&A.claim[CLAIM_EOS], 1u);
+        const int base = __shfl_sync(0xFFFFFFFFu, chunk, 0) * 32;
         if (base >= hi) break;
         const int a = base + threadIdx.x;
         const int s = A.segid[a];  // warp-uniform: ranges are multiples of 256 and hi is a range end
@@ -403,7 +402,7 @@ void launch_inverse_build(const EosDev &E, double *inv, long long nnodes, cudaSt
 
 void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st)
 {
-    k_eos2_seg<<<grid, 64, 0, st>>>(A, E, stage, y);
+    k_eos2_seg<<<grid, 32, 0, st>>>(A, E, stage, y);
 }
 
 }  // namespace sphg

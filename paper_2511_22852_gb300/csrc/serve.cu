@@ -1364,7 +1364,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
                 return bail(sfail(SPH_ERR_CUDA, "cudaEventCreate failed"));
             }
     // launch shapes: persistent grids of resident blocks on every SM
-    int dev = 0, sms = 0, occ_e = 6;
+    int dev = 0, sms = 0, occ_e = 12;  // EoS pass: one-warp blocks, 12 per SM (168 registers)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::max(sms, 1);
