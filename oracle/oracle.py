@@ -56,6 +56,8 @@ class Params(C.Structure):
         ("inv", C.c_void_p), ("inv_p10", C.c_void_p), ("inv_K", C.c_int), ("inv_nd", C.c_int), ("inv_nx", C.c_int),
         ("pad3", C.c_int), ("inv_xmax", C.c_double),
         ("eom_model", C.c_int), ("pad4", C.c_int), ("dnmr", C.c_double * 6),
+        ("nparton", C.c_int), ("pad5", C.c_int), ("partons", C.c_void_p),
+        ("parton_norm", C.c_double), ("parton_h", C.c_double), ("parton_dt", C.c_double),
     ]
 
 
@@ -153,6 +155,12 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
         tr = _f64(jets.tracks).reshape(-1, 8)
         keep.append(tr)
         P.ntrack, P.tracks, P.track_sigma = tr.shape[0], tr.ctypes.data, float(jets.sigma)
+    src = getattr(ev, "partons", None)
+    if src is not None and len(src.partons):
+        pt = _f64(src.partons).reshape(-1, 8)
+        keep.append(pt)
+        P.nparton, P.partons = pt.shape[0], pt.ctypes.data
+        P.parton_norm, P.parton_h, P.parton_dt = float(src.norm), float(src.h), float(ev.dtau)
     return P, keep
 
 

@@ -90,6 +90,13 @@ typedef struct {
        dnmr[3] = tau_pipi / tau_pi, dnmr[4] = lambda_piPi / tau_pi, dnmr[5] = phi_7 p */
     int eom_model, pad4;
     double dnmr[6];
+    /* dynamical-initialisation sources (Sec. "Dynamical initialization"): partons[8 k ..] =
+       formation time x^0_k, position (x, y, z|eta), four-momentum p^mu (contravariant, the
+       event's coordinates); a parton formed in (x^0 - dt, x^0] deposits
+       N p^mu W(r - r_k, h_src) / (sqrt(-g) dt) at the stage evaluated at x^0 */
+    int nparton, pad5;
+    const double *partons;
+    double parton_norm, parton_h, parton_dt;
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -844,6 +851,22 @@ static void jet_source(const oc_params *P, int dim, double t, const double *x, d
     }
 }
 
+/* I^mu of the partons formed in (t - dt, t], smeared with the SPH kernel of width h_src in the
+   event's dimensions (distances Euclidean in the event's spatial coordinates) */
+static void parton_source(const oc_params *P, int dim, int milne, double t, const double *x, double *I)
+{
+    for (int mu = 0; mu < 4; ++mu) I[mu] = 0.0;
+    const double sqrtg = milne ? t : 1.0;
+    for (int k = 0; k < P->nparton; ++k) {
+        const double *q = P->partons + 8 * k;
+        if (!(q[0] > t - P->parton_dt && q[0] <= t)) continue;
+        double r2 = 0.0;
+        for (int d = 0; d < dim; ++d) r2 += (x[d] - q[1 + d]) * (x[d] - q[1 + d]);
+        const double f = P->parton_norm * oc_W(sqrt(r2), P->parton_h, dim) / (sqrtg * P->parton_dt);
+        for (int mu = 0; mu < 4; ++mu) I[mu] += f * q[4 + mu];
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* equations of motion at one particle                                       */
 /* ------------------------------------------------------------------------ */
@@ -1227,11 +1250,19 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
                 for (int l = 0; l < 4; ++l) src += G.G[1 + i][m][l] * Tfull[16 * a + 4 * m + l];
             F[1 + i] = grad[(dim * dim + i) * n + a] - G.sqrtg * src / aux[0 * n + a];
         }
-        /* jet source: dP^i/dx0 gains sqrt(-g) I^i / sigma*, dS/dx0 gains u_nu I^nu / (u^0 sigma T) */
-        if (P->ntrack > 0) {
-            double xa[3] = {0, 0, 0}, I[4];
+        /* jet and parton sources: dP^i/dx0 gains sqrt(-g) I^i / sigma*, dS/dx0 gains
+           u_nu I^nu / (u^0 sigma T) */
+        if (P->ntrack > 0 || P->nparton > 0) {
+            double xa[3] = {0, 0, 0}, I[4] = {0, 0, 0, 0}, Ik[4];
             for (int d = 0; d < dim; ++d) xa[d] = y[d * n + a];
-            jet_source(P, dim, tau, xa, I);
+            if (P->ntrack > 0) {
+                jet_source(P, dim, tau, xa, Ik);
+                for (int mu = 0; mu < 4; ++mu) I[mu] += Ik[mu];
+            }
+            if (P->nparton > 0) {
+                parton_source(P, dim, P->milne, tau, xa, Ik);
+                for (int mu = 0; mu < 4; ++mu) I[mu] += Ik[mu];
+            }
             for (int i = 0; i < dim; ++i) F[1 + i] += G.sqrtg * I[1 + i] / aux[0 * n + a];
             for (int mu = 0; mu < 4; ++mu) q.uI += G.g[mu] * q.u[mu] * I[mu];
         }

@@ -116,6 +116,16 @@ class JetTracks:
 
 
 @dataclass
+class PartonSources:
+    """Dynamical-initialisation sources: partons [N][8] = formation time, position (x, y,
+    z or eta), four-momentum p^mu (contravariant, fm^-1, the event's coordinates); each is
+    smeared with the SPH kernel of width h over the step in which it forms, scaled by norm."""
+    partons: np.ndarray
+    norm: float = 1.0
+    h: float = 1.4
+
+
+@dataclass
 class InverseGrid:
     """Grid of the offline-inverted EoS table: s on log decades 10^decade_lo .. 10^(decade_lo +
     decades) with per_decade uniform nodes per decade (s = 10^d (1 + 9 j / per_decade)), and the
@@ -149,6 +159,7 @@ class Event:
     meta: dict = field(default_factory=dict)
     jets: JetTracks | None = None
     inverse: InverseGrid | None = None  # set: the EoS is inverted by the offline table
+    partons: PartonSources | None = None  # dynamical-initialisation sources
 
     @property
     def n(self) -> int:
@@ -520,3 +531,25 @@ def stress_cartesian_3d(n_target=8_000_000, R=7.0, z_sigma=1.5, z_max=5.0, h=0.1
                                      zeta_w_GeV=0.02),
                  meta={"dx": dx},
                  jets=jet_tracks(n_tracks=n_tracks, R=R, t0=t0, z_half=1.0, seed=seed_tracks))
+
+
+def parton_sources(n: int, t_range, half_extent, dim: int, E_GeV=(1.0, 3.0), norm=0.42, h=1.4, seed=6):
+    """n seeded partons with formation times uniform in t_range, positions uniform in a centred
+    cube of half-width half_extent (dim axes), massless four-momenta with energies uniform in
+    E_GeV and isotropic directions in the event's dimensions."""
+    u = uniform01(seed, 6 * n).reshape(6, n)
+    t = t_range[0] + (t_range[1] - t_range[0]) * u[0]
+    x = np.zeros((3, n))
+    for d in range(dim):
+        x[d] = half_extent * (2.0 * u[1 + d] - 1.0)
+    E = (E_GeV[0] + (E_GeV[1] - E_GeV[0]) * u[4]) / HBARC
+    phi = 2.0 * np.pi * u[5]
+    if dim == 3:
+        ct = 2.0 * u[3] - 1.0
+        st = np.sqrt(1.0 - ct * ct)
+        nvec = np.stack([st * np.cos(phi), st * np.sin(phi), ct])
+    else:
+        nvec = np.stack([np.cos(phi), np.sin(phi), np.zeros(n)])
+    p = np.concatenate([E[None, :], E[None, :] * nvec])
+    partons = np.concatenate([t[None, :], x, p]).T.copy()
+    return PartonSources(partons=partons, norm=norm, h=h)

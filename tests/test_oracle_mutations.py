@@ -97,6 +97,15 @@ MUTATIONS = [
      "dPP * q->Pi * theta - lPp * pisig) / q->tauPi;", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
     ("dnmr_projector_trace", "Ppis[m][nu] = pa - Du_up * trA / 3.0;", "Ppis[m][nu] = pa - Du_up * trA / 2.0;",
      "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("parton_drop_sqrtg", "const double f = P->parton_norm * oc_W(sqrt(r2), P->parton_h, dim) / (sqrtg * P->parton_dt);",
+     "const double f = P->parton_norm * oc_W(sqrt(r2), P->parton_h, dim) / P->parton_dt;",
+     "test_oracle_sources.py::test_partons_in_milne_coordinates"),
+    ("parton_kernel_dim", "const double f = P->parton_norm * oc_W(sqrt(r2), P->parton_h, dim) / (sqrtg * P->parton_dt);",
+     "const double f = P->parton_norm * oc_W(sqrt(r2), P->parton_h, 2) / (sqrtg * P->parton_dt);",
+     "test_oracle_sources.py::test_partons_deposit_their_four_momentum"),
+    ("parton_window_open_end", "if (!(q[0] > t - P->parton_dt && q[0] <= t)) continue;",
+     "if (!(q[0] > t - 2.0 * P->parton_dt && q[0] <= t)) continue;",
+     "test_oracle_sources.py::test_partons_deposit_their_four_momentum"),
     ("dnmr_bulk_drop_volume_rate", "R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);",
      "R->dBv = DPi / (u0 * q->sigma);", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
 ]
