@@ -372,6 +372,33 @@ def bench_dnmr(Bd, I, steps: int = 40):
     return out
 
 
+def bench_partons(Bd, I, steps: int = 40, per_step: int = 100):
+    """Cost of dynamical-initialisation sources on the 40k-particle event: partons forming at
+    per_step per step over the window (h_src = 1.4 fm, the paper's smearing width), device ms
+    per step with and without them (CUDA graphs, CUDA events)."""
+    import torch
+    ev = I.viscous_bsq_2p1()
+    npart = per_step * steps
+    src = I.parton_sources(npart, (ev.tau0, ev.tau0 + steps * ev.dtau), 4.0, 2, E_GeV=(0.1, 0.3), norm=0.42, h=1.4)
+    out = {"workload": f"40k-particle viscous BSQ event, {npart} partons forming over {steps} steps "
+                       f"({per_step} per step, h_src = 1.4 fm, |x|, |y| <= 4 fm)"}
+    for name, on in (("without", False), ("with", True)):
+        ev.partons = src if on else None
+        st = torch.cuda.Stream()
+        g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream)
+        g.step(1, sync=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record(st)
+            g.step(steps)
+            b.record(st)
+        torch.cuda.synchronize()
+        out[name + "_ms_per_step"] = a.elapsed_time(b) / steps
+        g.free()
+    out["overhead"] = out["with_ms_per_step"] / out["without_ms_per_step"] - 1.0
+    return out
+
+
 def bench_offline_eos(Bd, I, steps: int = 20):
     """The offline EoS inverter (interpolation in an inverted (s, n/s) table) against the online
     Newton inversion on the 40k-particle event: device ms per step and per EoS pass (profile
@@ -630,6 +657,7 @@ def run_ours(args):
         out["mixed_single_event"] = bench_mixed_single(Bd, I)
         out["freezeout"] = bench_freezeout(Bd, I)
         out["dnmr"] = bench_dnmr(Bd, I)
+        out["partons"] = bench_partons(Bd, I)
         out["offline_eos"] = bench_offline_eos(Bd, I)
         if not args.no_3d:
             out["config_3p1d"] = bench_3p1d(Bd, I)

@@ -255,6 +255,21 @@ sph_status sph_eos_build_inverse(sph_eos *eos, int32_t per_decade, int32_t decad
 sph_status sph_set_eos_mode(sph_event *ev, int32_t mode);
 
 /* ---------------------------------------------------------------------------
+ * Dynamical-initialisation sources (Sec. "Dynamical initialization": the source j^mu of the
+ * partons formed during the evolution): partons[8 k ..] = formation time x^0_k, position
+ * (x, y, z) (Cartesian) or (x, y, eta) (Milne; 2D uses x, y), four-momentum p^mu (fm^-1,
+ * contravariant, the event's coordinates).  The stage evaluated at x^0 gains
+ *   I^mu(r) = sum over partons with x^0 - dtau < x^0_k <= x^0 of
+ *             norm p^mu_k W(|r - r_k|, h_src) / (sqrt(-g) dtau)
+ * with W the cubic spline of the event's dimension and width h_src (distances Euclidean in the
+ * event's coordinates); I^mu enters the equations of motion as the jet tracks' source does
+ * (sph_set_jets).  Host array, copied (sorted by formation time); nparton = 0 removes the
+ * sources.  Errors: SPH_ERR_ARG (nparton outside 0..2^24, null array, h_src <= 0, non-finite
+ * entries); SPH_ERR_TIMEOUT if the event's stream does not drain.
+ * ------------------------------------------------------------------------- */
+sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons, double norm, double h_src);
+
+/* ---------------------------------------------------------------------------
  * Viscous equations of motion (Sec. "Equations of motion": eqs. min_bul_rel, min_she_rel and
  * eq. dnmr).  SPH_EOM_MIN_IS (the default): minimal Israel-Stewart.  SPH_EOM_DNMR: DNMR without
  * the K terms and the couplings to diffusion, with the shear-bulk J terms and the R term phi_7

@@ -36,7 +36,7 @@ EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_even
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
            "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode",
-           "sph_set_viscous_eom"]
+           "sph_set_viscous_eom", "sph_set_partons"]
 SPH_EOS_ONLINE, SPH_EOS_OFFLINE = 0, 1
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
@@ -130,6 +130,7 @@ def lib():
             "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
             "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
             "sph_set_viscous_eom": (i32, [vp, i32, vp]),
+            "sph_set_partons": (i32, [vp, i64, vp, C.c_double, C.c_double]),
             "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
             "sph_eos_build_inverse": (i32, [vp, i32, i32, i32, i32, C.c_double]),
             "sph_set_eos_mode": (i32, [vp, i32]),
@@ -236,6 +237,11 @@ SPH_EOM_MIN_IS, SPH_EOM_DNMR = 0, 1
 def sph_set_viscous_eom(h, model: int, coeffs=None):
     c = _f64(coeffs) if coeffs is not None else None
     _check(lib().sph_set_viscous_eom(h, int(model), _ptr(c) if c is not None else None))
+
+
+def sph_set_partons(h, partons, norm: float, h_src: float):
+    pt = _f64(partons).reshape(-1, 8) if partons is not None else np.zeros((0, 8))
+    _check(lib().sph_set_partons(h, int(pt.shape[0]), _ptr(pt) if pt.size else None, float(norm), float(h_src)))
 
 
 def sph_freezeout_setup(h, e_fo: float, capacity: int):
@@ -430,6 +436,9 @@ class GpuEvent:
         dnmr = getattr(ev.transport, "dnmr", None)
         if dnmr is not None:
             sph_set_viscous_eom(self.h, SPH_EOM_DNMR, dnmr)
+        src = getattr(ev, "partons", None)
+        if src is not None and len(src.partons):
+            sph_set_partons(self.h, src.partons, src.norm, src.h)
 
     def step(self, nsteps: int, sync: bool = False):
         sph_step(self.h, nsteps, SPH_SYNC if sync else 0)

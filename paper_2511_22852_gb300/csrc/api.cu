@@ -63,6 +63,10 @@ struct sph_event {
     int ntrack = 0;                 // jet tracks (sph_set_jets): device copy and Gaussian constants
     double *d_tracks = nullptr;
     double track_norm = 0.0, track_i2s2 = 0.0;
+    int nparton = 0;                // dynamical-initialisation partons (sph_set_partons), sorted by time
+    double *d_partons = nullptr;
+    long long parton_cap = 0;
+    double parton_norm = 0.0, parton_h = 0.0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     DevScalars *sc = nullptr;
@@ -150,6 +154,14 @@ static EvView make_view(const sph_event *ev)
     v.eos = ev->eos->dev;
     v.eos.offline = ev->eos_offline && ev->eos->dev.inv ? 1 : 0;
     v.tr = ev->tr;
+    v.nparton = ev->nparton;
+    v.partons = ev->d_partons;
+    v.parton_norm = ev->parton_norm;
+    v.parton_h = ev->parton_h;
+    v.parton_sd = ev->parton_h > 0.0 ? (ev->dim == 2 ? 10.0 / (7.0 * kPi * ev->parton_h * ev->parton_h)
+                                                     : 1.0 / (kPi * ev->parton_h * ev->parton_h * ev->parton_h))
+                                     : 0.0;
+    v.parton_dt = ev->dtau;
     v.ntrack = ev->ntrack;
     v.tracks = ev->d_tracks;
     v.track_norm = ev->track_norm;
@@ -1024,6 +1036,54 @@ sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, dou
     ev->ntrack = (int)ntrack;
     ev->track_norm = ntrack > 0 ? 1.0 / (std::pow(2.0 * kPi, 1.5) * sigma * sigma * sigma) : 0.0;
     ev->track_i2s2 = ntrack > 0 ? 1.0 / (2.0 * sigma * sigma) : 0.0;
+    if (ev->gexec) {  // the parameters are part of the captured step: capture it again
+        cudaGraphExecDestroy(ev->gexec);
+        ev->gexec = nullptr;
+    }
+    if (ev->graph) {
+        cudaGraphDestroy(ev->graph);
+        ev->graph = nullptr;
+    }
+    ev->graph_ready = false;
+    ev->kernels_per_step = 0;
+    ev->observed = false;
+    return SPH_OK;
+}
+
+sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons, double norm, double h_src)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (nparton < 0 || nparton > (1 << 24)) return fail(SPH_ERR_ARG, "nparton must be in 0..2^24");
+    if (nparton > 0 && (!partons || !(h_src > 0.0) || !std::isfinite(norm)))
+        return fail(SPH_ERR_ARG, "partons, h_src > 0 and a finite norm required");
+    for (int64_t k = 0; k < 8 * nparton; ++k)
+        if (!std::isfinite(partons[k])) return fail(SPH_ERR_ARG, "non-finite parton entry");
+    // sorted by formation time (stable), so a stage finds its window by binary search
+    std::vector<int64_t> ord((size_t)nparton);
+    for (int64_t k = 0; k < nparton; ++k) ord[(size_t)k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t p, int64_t q) { return partons[8 * p] < partons[8 * q]; });
+    std::vector<double> sorted((size_t)(8 * nparton));
+    for (int64_t k = 0; k < nparton; ++k)
+        for (int c = 0; c < 8; ++c) sorted[(size_t)(8 * k + c)] = partons[8 * ord[(size_t)k] + c];
+    {
+        sph_status ws = wait_stream(ev);  // bounded: the buffer below may be in use
+        if (ws != SPH_OK) return ws;
+    }
+    if (nparton > ev->parton_cap || !ev->d_partons) {
+        sph_status s = dalloc(ev, reinterpret_cast<void **>(&ev->d_partons),
+                              sizeof(double) * 8 * (size_t)(nparton > 0 ? nparton : 1));
+        if (s != SPH_OK) return s;
+        ev->parton_cap = nparton > 0 ? nparton : 1;
+    }
+    if (nparton > 0) {
+        CK(cudaMemcpyAsync(ev->d_partons, sorted.data(), sizeof(double) * sorted.size(), cudaMemcpyHostToDevice,
+                           ev->stream));
+        sph_status ws = wait_stream(ev);
+        if (ws != SPH_OK) return ws;
+    }
+    ev->nparton = (int)nparton;
+    ev->parton_norm = nparton > 0 ? norm : 0.0;
+    ev->parton_h = nparton > 0 ? h_src : 0.0;
     if (ev->gexec) {  // the parameters are part of the captured step: capture it again
         cudaGraphExecDestroy(ev->gexec);
         ev->gexec = nullptr;

@@ -260,12 +260,22 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
         dPxy = isg * dpxy - (pxy * isg2) * dsg;
         dPyy = isg * dpyy - (pyy * isg2) * dsg;
     }
-    if (v.ntrack > 0) {  // jet tracks (Cartesian): dP^i/dt gains I^i/sigma*, dS/dt gains u.I/(u^0 sigma T)
-        double I[4];
-        jet_deposit(v, tau, ys[a], ys[n + a], 0.0, I);
-        Fx += I[1] * isig;
-        Fy += I[2] * isig;
-        const double uI = g * I[0] - ux * I[1] - uy * I[2];
+    if (v.ntrack > 0 || v.nparton > 0) {
+        // jet tracks (Cartesian) and partons: dP^i/dx0 gains sqrt(-g) I^i/sigma*, dS/dx0 gains
+        // u_nu I^nu/(u^0 sigma T)
+        double I[4] = {0.0, 0.0, 0.0, 0.0}, Ik[4];
+        if (v.ntrack > 0) {
+            jet_deposit(v, tau, ys[a], ys[n + a], 0.0, Ik);
+            for (int k = 0; k < 4; ++k) I[k] += Ik[k];
+        }
+        if (v.nparton > 0) {
+            const double xa[3] = {ys[a], ys[n + a], 0.0};
+            parton_deposit(v, tau, sqrtg, xa, Ik);
+            for (int k = 0; k < 4; ++k) I[k] += Ik[k];
+        }
+        Fx += sqrtg * I[1] * isig;
+        Fy += sqrtg * I[2] * isig;
+        const double uI = g * I[0] - ux * I[1] - uy * I[2];  // no eta component in 2+1D
         dS = dS + aff((ig * isg / T) * uI);
     }
     Aff ds = sigma * dS + (s * isg) * dsg;

@@ -103,6 +103,11 @@ struct EvView {
     int ntrack;
     const double *tracks;
     double track_norm, track_i2s2;
+    // dynamical-initialisation partons (nparton = 0: none), sorted by formation time:
+    // partons[8 k ..] = x^0_k, position (x, y, z|eta), p^mu; the kernel of width parton_h
+    int nparton;
+    const double *partons;
+    double parton_norm, parton_h, parton_sd, parton_dt;  // parton_sd: the kernel normalisation
 };
 
 // I^nu of the jet tracks at time t and position (x, y, z): every track moves at the speed of
@@ -210,6 +215,36 @@ __device__ __forceinline__ double kernel_dw(double q)
     if (q <= 1.0) return q * fma(2.25, q, -3.0);
     double t = 2.0 - q;
     return -0.75 * t * t;
+}
+
+// I^mu of the partons formed in (t - dt, t] (Sec. "Dynamical initialization"):
+// N p^mu W(r - r_k, h_src) / (sqrt(-g) dt), distances in the event's dim coordinates; the
+// window is found by binary search in the formation times
+__device__ __forceinline__ void parton_deposit(const EvView &v, double t, double sqrtg, const double *x,
+                                               double I[4])
+{
+    I[0] = I[1] = I[2] = I[3] = 0.0;
+    const double lo_t = t - v.parton_dt;
+    int lo = 0, hi = v.nparton;  // first parton with x^0 > t - dt
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v.partons[8 * mid] > lo_t) hi = mid;
+        else lo = mid + 1;
+    }
+    const double f0 = v.parton_norm * v.parton_sd / (sqrtg * v.parton_dt), ih = 1.0 / v.parton_h;
+    for (int k = lo; k < v.nparton; ++k) {
+        const double *q = v.partons + 8 * k;
+        if (q[0] > t) break;
+        double r2 = 0.0;
+        for (int d = 0; d < v.dim; ++d) r2 += (x[d] - q[1 + d]) * (x[d] - q[1 + d]);
+        const double qq = sqrt(r2) * ih;
+        if (!(qq < 2.0)) continue;
+        const double w = f0 * kernel_w(qq);
+        I[0] += w * q[4];
+        I[1] += w * q[5];
+        I[2] += w * q[6];
+        I[3] += w * q[7];
+    }
 }
 
 // affine form c + ax*a_x + ay*a_y in the unknown acceleration (a_x, a_y)

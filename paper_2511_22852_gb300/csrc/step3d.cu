@@ -555,9 +555,21 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
             }
     }
     double Isrc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (v.ntrack > 0) {  // jet tracks (Cartesian): dP^i/dt gains I^i/sigma*, dS/dt gains u.I/(u^0 sigma T)
-        jet_deposit(v, G.tau, ys[a], ys[n + a], ys[2 * n + a], Isrc);
-        const double uI = u[0] * Isrc[0] - u[1] * Isrc[1] - u[2] * Isrc[2] - u[3] * Isrc[3];
+    if (v.ntrack > 0 || v.nparton > 0) {
+        // jet tracks (Cartesian) and partons: dP^i/dx0 gains sqrt(-g) I^i/sigma*, dS/dx0 gains
+        // u_nu I^nu/(u^0 sigma T)
+        double Ik[4];
+        if (v.ntrack > 0) {
+            jet_deposit(v, G.tau, ys[a], ys[n + a], ys[2 * n + a], Ik);
+            for (int k = 0; k < 4; ++k) Isrc[k] += Ik[k];
+        }
+        if (v.nparton > 0) {
+            const double xa[3] = {ys[a], ys[n + a], ys[2 * n + a]};
+            parton_deposit(v, G.tau, G.sqrtg, xa, Ik);
+            for (int k = 0; k < 4; ++k) Isrc[k] += Ik[k];
+        }
+        double uI = 0.0;
+        for (int k = 0; k < 4; ++k) uI += G.g[k] * u[k] * Isrc[k];
         dS = dS + k3((ig * isg / T) * uI);
     }
     const A3 ds = sigma * dS + (s * isg) * dsg;

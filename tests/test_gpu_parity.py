@@ -42,6 +42,13 @@ def state_errors(g, run):
             "Bv": relerr(st["BV"], y[5]), "Pv": relerr(st["PV"], y[6:9])}
 
 
+def _with_partons(ev, extent, dim, h=0.5):
+    """The event with seeded parton sources formed from just before its first stage to 8 steps in."""
+    ev.partons = I.parton_sources(12, (ev.tau0 - 0.5 * ev.dtau, ev.tau0 + 8 * ev.dtau), extent, dim,
+                                  E_GeV=(0.1, 0.3), norm=0.42, h=h)
+    return ev
+
+
 def _with_dnmr(ev):
     """The event with the DNMR equations of motion (14-moment coefficients)."""
     ev.transport.dnmr = I.DNMR_14_MOMENT
@@ -55,6 +62,7 @@ CASES = {
     "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
     "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2)),
     "bsq_small_dnmr": lambda: _with_dnmr(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20)),
+    "bsq_small_partons": lambda: _with_partons(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20), 1.5, 2),
 }
 def _blob3_jets():
     ev = I.smooth_blob_3d(milne=False, flow=0.3, eos=I.CAUSAL_EOS)
@@ -71,6 +79,8 @@ CASES3 = {
     "blob3_cart_jets": _blob3_jets,
     "gubser_shifted3": lambda: I.gubser_shifted_3p1(t0=2.0),
     "blob3_milne_dnmr": lambda: _with_dnmr(I.smooth_blob_3d(milne=True, flow=0.3)),
+    "box_partons": lambda: _with_partons(I.uniform_box_3d(), 0.4, 3, h=0.3),
+    "blob3_milne_partons": lambda: _with_partons(I.smooth_blob_3d(milne=True, flow=0.3), 0.3, 3),
 }
 
 
@@ -261,7 +271,7 @@ def test_graph_and_stream_launches_are_bitwise_identical(Bd):
 
 
 @pytest.mark.parametrize("case,nsteps", [("gubser", 60), ("bsq_small", 150), ("blob_causal", 100),
-                                        ("bsq_small_dnmr", 100)])
+                                        ("bsq_small_dnmr", 100), ("bsq_small_partons", 20)])
 def test_evolution(Bd, case, nsteps):
     ev = CASES[case]()
     g = Bd.GpuEvent(ev, use_graph=True)
@@ -484,10 +494,12 @@ def test_mixed_precision_full_size_event(Bd):
     g.free()
 
 
-@pytest.mark.parametrize("case", list(CASES3))
+@pytest.mark.parametrize("case", [c for c in CASES3 if not c.startswith("box")])
 def test_mixed_precision_3d_against_fp64_oracle(Bd, case):
     """SPH_MIXED in 3+1D: FP32 27-cell neighbour passes, FP64 EoS/EoM -- within 1e-5 of the FP64
-    oracle after 10 steps, neighbour counts exact."""
+    oracle after 10 steps, neighbour counts exact.  The uniform boxes are left out: their
+    spacing divides 2h, so pairs start exactly at the kernel support, and the mixed evolution's
+    ~1e-7 position differences from the FP64 one legitimately flip some of them."""
     ev = CASES3[case]()
     g = Bd.GpuEvent(ev, precision=Bd.SPH_MIXED)
     run = O.OracleRun.start(ev)
