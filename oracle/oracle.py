@@ -10,6 +10,7 @@ product package never imports it.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -27,6 +28,7 @@ AUX = {name: i for i, name in enumerate(
     ["sigstar", "s", "nB", "nS", "nQ", "T", "muB", "muS", "muQ", "p", "e", "cs2", "theta", "Pi",
      "u0", "nnb", "sigma", "status"])}
 ST_FALLBACK, ST_OUT_OF_TABLE, ST_NOCONV, ST_NONFINITE, ST_CS2_CAPPED, ST_SOLVE_FAIL = 1, 2, 4, 8, 16, 32
+ST_BACKUP = 64
 
 
 def build(force: bool = False) -> str:
@@ -37,6 +39,9 @@ def build(force: bool = False) -> str:
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+HBARC_GEV_FM = 0.1973269804  # hbar c in GeV fm
 
 
 class Params(C.Structure):
@@ -58,6 +63,7 @@ class Params(C.Structure):
         ("eom_model", C.c_int), ("pad4", C.c_int), ("dnmr", C.c_double * 6),
         ("nparton", C.c_int), ("pad5", C.c_int), ("partons", C.c_void_p),
         ("parton_norm", C.c_double), ("parton_h", C.c_double), ("parton_dt", C.c_double),
+        ("backup", C.c_int), ("pad6", C.c_int), ("cd_A0", C.c_double), ("cd_mu0", C.c_double * 3),
     ]
 
 
@@ -155,6 +161,17 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
         tr = _f64(jets.tracks).reshape(-1, 8)
         keep.append(tr)
         P.ntrack, P.tracks, P.track_sigma = tr.shape[0], tr.ctypes.data, float(jets.sigma)
+    bk = getattr(ev, "eos_backup", None)
+    if bk is not None:
+        # conformal-diagonal backup (Sec. "Equation of state", backup EoS), matched to the closed
+        # form at T_scale: A0 = p(T_scale, 0) / T_scale^4, mu_q0 = mu_max (A0 / (p(T_scale,
+        # mu_q = mu_max) - p(T_scale, 0)))^(1/4) with T_0 = 1/fm
+        Ts, mumax = bk[0] / HBARC_GEV_FM, bk[1] / HBARC_GEV_FM
+        A0 = e.a0 + e.a1 * (1.0 + math.tanh((bk[0] - e.Tc_GeV) / e.w_GeV)) / 2.0
+        P.backup, P.cd_A0 = 1, A0
+        for q in range(3):
+            dp = e.chi[q] * Ts * Ts * mumax * mumax / 2.0
+            P.cd_mu0[q] = mumax * (A0 / dp) ** 0.25 if dp > 0.0 else mumax
     src = getattr(ev, "partons", None)
     if src is not None and len(src.partons):
         pt = _f64(src.partons).reshape(-1, 8)

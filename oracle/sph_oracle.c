@@ -46,6 +46,7 @@
 #define ST_NONFINITE 8u
 #define ST_CS2_CAPPED 16u
 #define ST_SOLVE_FAIL 32u  /* acceleration system singular */
+#define ST_BACKUP 64u      /* no closed-form solution: the conformal-diagonal backup EoS used */
 
 typedef struct {
     int dim;     /* SPH dimensions: 2 (x, y) or 3 (x, y, eta|z) */
@@ -97,6 +98,11 @@ typedef struct {
     int nparton, pad5;
     const double *partons;
     double parton_norm, parton_h, parton_dt;
+    /* backup EoS (Sec. "Equation of state", backup EoS): where neither the table nor the closed
+       form inverts, the conformal-diagonal EoS p = A0 [T^4 + sum_q (mu_q / mu_q0)^4] (T_0 = 1/fm),
+       which inverts (s, n) in closed form; backup = 0: none (the particle has no solution) */
+    int backup, pad6;
+    double cd_A0, cd_mu0[3];
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -701,6 +707,24 @@ unsigned oc_eos_invert_ws(const oc_params *P, double s, const double *n, const d
     }
     if (!use_table) {
         int r = oc_eos_invert_analytic(P, s, n, &x[0], &x[1]);
+        if (r != 0 && P->backup && s > 0.0) {
+            /* conformal diagonal: s = 4 A0 T^3, n_q = 4 A0 mu_q^3 / mu_q0^4; e = 3 p;
+               p_s = dp/ds|_n = T/3, p_{n_q} = dp/dn_q|_s = mu_q/3 (T and mu_q decouple) */
+            const double A0 = P->cd_A0;
+            out[0] = cbrt(s / (4.0 * A0));
+            double pq = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const double m0 = P->cd_mu0[q];
+                out[1 + q] = cbrt(n[q] * m0 * m0 * m0 * m0 / (4.0 * A0));
+                pq += pow(out[1 + q] / m0, 4.0);
+            }
+            out[4] = A0 * (pow(out[0], 4.0) + pq);
+            out[5] = 3.0 * out[4];
+            out[6] = out[0] / 3.0;
+            for (int q = 0; q < 3; ++q) out[7 + q] = out[1 + q] / 3.0;
+            out[10] = 1.0 / 3.0;
+            return ST_BACKUP;
+        }
         if (r != 0) return (unsigned)r | ST_NOCONV;
         if (P->has_table) {
             if (in_table(P, x)) {

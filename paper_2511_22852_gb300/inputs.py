@@ -160,6 +160,9 @@ class Event:
     jets: JetTracks | None = None
     inverse: InverseGrid | None = None  # set: the EoS is inverted by the offline table
     partons: PartonSources | None = None  # dynamical-initialisation sources
+    # backup EoS (conformal diagonal) where neither the table nor the closed form inverts:
+    # (T_scale, mu_max) in GeV, or None for none
+    eos_backup: tuple | None = None
 
     @property
     def n(self) -> int:

@@ -195,3 +195,63 @@ def test_warm_started_inversion_reaches_the_same_root(bsq):
             assert used.value == 1 and st2 == st
             assert np.all(np.abs(out[:4] - cold[:4]) <= 1e-13 * T)
             assert abs(out[4] / cold[4] - 1) < 1e-13
+
+
+@pytest.fixture(scope="module")
+def bsq_backup():
+    ev = I.viscous_bsq_2p1(n_target=200, R=2.0, n_hot=3)
+    ev.eos_backup = (0.165, 0.45)
+    P, keep = O.make_params(ev)
+    return ev, P, keep
+
+
+def _p_cd(P, T, mu):
+    """The conformal-diagonal pressure of Sec. "Equation of state" (backup EoS), T_0 = 1/fm."""
+    return P.cd_A0 * (T ** 4 + sum((mu[q] / P.cd_mu0[q]) ** 4 for q in range(3)))
+
+
+def test_backup_eos_matches_the_closed_form_at_T_scale(bsq_backup):
+    """The backup's constants satisfy the paper's matching conditions: its pressure equals the
+    closed form's at (T_scale, 0) and at (T_scale, mu_q = mu_max) for each charge."""
+    ev, P, _ = bsq_backup
+    Ts, mm = 0.165 / I.HBARC, 0.45 / I.HBARC
+    p0, _, _ = O.eos_analytic(P, Ts, np.zeros(3))
+    assert abs(_p_cd(P, Ts, np.zeros(3)) / p0 - 1) < 1e-13
+    for q in range(3):
+        mu = np.zeros(3)
+        mu[q] = mm
+        pq, _, _ = O.eos_analytic(P, Ts, mu)
+        assert abs(_p_cd(P, Ts, mu) / pq - 1) < 1e-13
+
+
+def test_backup_eos_inverts_what_the_closed_form_cannot(bsq_backup):
+    """Infeasible charges (the literal +-10 % fraction at 0.5 GeV): the closed form has no
+    solution, the conformal-diagonal backup does -- thermodynamically consistent: its pressure's
+    derivatives at the returned (T, mu) reproduce (s, n), e = 3p, and (p_s, p_n) match finite
+    differences of the inversion."""
+    ev, P, _ = bsq_backup
+    T = 0.5 / I.HBARC
+    _, sn, _ = O.eos_analytic(P, T, np.zeros(3))
+    s = sn[0]
+    n = np.array([0.1 * s, 0.1 * s, -0.1 * s])
+    out, st = O.eos_invert(P, s, n)
+    assert st == O.ST_BACKUP
+    Tb, mu = out[0], out[1:4]
+    d = 1e-6
+    dpdT = (_p_cd(P, Tb * (1 + d), mu) - _p_cd(P, Tb * (1 - d), mu)) / (2 * d * Tb)
+    assert abs(dpdT / s - 1) < 1e-8
+    for q in range(3):
+        m1, m2 = mu.copy(), mu.copy()
+        m1[q] *= 1 + d
+        m2[q] *= 1 - d
+        dpdm = (_p_cd(P, Tb, m1) - _p_cd(P, Tb, m2)) / (2 * d * mu[q])
+        assert abs(dpdm / n[q] - 1) < 1e-8
+    assert abs(out[4] / _p_cd(P, Tb, mu) - 1) < 1e-13 and abs(out[5] / (3 * out[4]) - 1) < 1e-13
+    o2, _ = O.eos_invert(P, s * (1 + d), n)
+    assert abs((o2[4] - out[4]) / (s * d) / out[6] - 1) < 1e-5
+    for q in range(3):
+        n2 = n.copy()
+        n2[q] *= 1 + d
+        o2, _ = O.eos_invert(P, s, n2)
+        assert abs((o2[4] - out[4]) / (n[q] * d) / out[7 + q] - 1) < 1e-5
+    assert abs(out[10] - 1.0 / 3.0) < 1e-15

@@ -106,6 +106,11 @@ MUTATIONS = [
     ("parton_window_open_end", "if (!(q[0] > t - P->parton_dt && q[0] <= t)) continue;",
      "if (!(q[0] > t - 2.0 * P->parton_dt && q[0] <= t)) continue;",
      "test_oracle_sources.py::test_partons_deposit_their_four_momentum"),
+    ("backup_ps_factor", "out[6] = out[0] / 3.0;", "out[6] = out[0] / 4.0;",
+     "test_oracle_eos.py::test_backup_eos_inverts_what_the_closed_form_cannot"),
+    ("backup_mu_inversion", "out[1 + q] = cbrt(n[q] * m0 * m0 * m0 * m0 / (4.0 * A0));",
+     "out[1 + q] = cbrt(n[q] * m0 * m0 * m0 * m0 / (3.0 * A0));",
+     "test_oracle_eos.py::test_backup_eos_inverts_what_the_closed_form_cannot"),
     ("dnmr_bulk_drop_volume_rate", "R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);",
      "R->dBv = DPi / (u0 * q->sigma);", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
 ]
