@@ -59,6 +59,7 @@ typedef enum {
 #define SPH_PST_NOCONV 4u       /* no EoS solution at all */
 #define SPH_PST_NONFINITE 8u    /* non-finite density or state */
 #define SPH_PST_CS2_CAPPED 16u  /* c_s^2 > cap: dp/ds, dp/dn scaled down in the acceleration system */
+#define SPH_PST_BACKUP 64u      /* neither table nor closed form inverts: the conformal-diagonal backup EoS used */
 #define SPH_PST_SOLVE_FAIL 32u  /* the acceleration system was singular */
 /* A particle with NOCONV or NONFINITE from the EoS is frozen for that stage: it moves
  * ballistically (dx/dt = v), every other rate is zero, and it contributes p = e = 0 to its
@@ -253,6 +254,19 @@ sph_status sph_kernel_times(sph_event *ev, int32_t max, char *names, double *ms,
 sph_status sph_eos_build_inverse(sph_eos *eos, int32_t per_decade, int32_t decade_lo, int32_t decades, int32_t nx,
                                  double xmax);
 sph_status sph_set_eos_mode(sph_event *ev, int32_t mode);
+
+/* ---------------------------------------------------------------------------
+ * Backup EoS (Sec. "Equation of state": backup EoS tried in turn when a point lies outside the
+ * others' reach): with enable = 1, a particle that neither the table Newton nor the closed-form
+ * EoS inverts takes the conformal-diagonal EoS p = A0 [T^4 + sum_q (mu_q / mu_q0)^4] (T_0 =
+ * 1/fm), which inverts (s, n) in closed form for every s > 0: T = (s / 4 A0)^(1/3),
+ * mu_q = (n_q mu_q0^4 / 4 A0)^(1/3), e = 3 p, c_s^2 = 1/3; flagged SPH_PST_BACKUP.  A0 and
+ * mu_q0 match the closed form at T_scale: p equal at (T_scale, 0) and at (T_scale, mu_q = mu_max)
+ * (T_scale = 1.1 T_FO in the paper).  enable = 0 (the default): no backup; such particles have
+ * no solution (SPH_PST_NOCONV) and are frozen for the stage.  Errors: SPH_ERR_ARG for
+ * non-positive T_scale or mu_max; SPH_ERR_TIMEOUT if the event's stream does not drain.
+ * ------------------------------------------------------------------------- */
+sph_status sph_set_eos_backup(sph_event *ev, int32_t enable, double T_scale_GeV, double mu_max_GeV);
 
 /* ---------------------------------------------------------------------------
  * Dynamical-initialisation sources (Sec. "Dynamical initialization": the source j^mu of the

@@ -24,6 +24,7 @@ SPH_OK, SPH_ERR_ARG, SPH_ERR_OOM, SPH_ERR_CUDA, SPH_ERR_EOS_RANGE, SPH_ERR_EOS_N
 STATUS_NAMES = ["SPH_OK", "SPH_ERR_ARG", "SPH_ERR_OOM", "SPH_ERR_CUDA", "SPH_ERR_EOS_RANGE", "SPH_ERR_EOS_NOCONV",
                 "SPH_ERR_NONFINITE", "SPH_ERR_TIMEOUT", "SPH_ERR_STATE"]
 PST_FALLBACK, PST_OUT_OF_TABLE, PST_NOCONV, PST_NONFINITE, PST_CS2_CAPPED, PST_SOLVE_FAIL = 1, 2, 4, 8, 16, 32
+PST_BACKUP = 64
 SPH_SYNC = 1
 SPH_FP64, SPH_MIXED = 0, 1
 
@@ -36,7 +37,7 @@ EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_even
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
            "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode",
-           "sph_set_viscous_eom", "sph_set_partons"]
+           "sph_set_viscous_eom", "sph_set_partons", "sph_set_eos_backup"]
 SPH_EOS_ONLINE, SPH_EOS_OFFLINE = 0, 1
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
@@ -131,6 +132,7 @@ def lib():
             "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
             "sph_set_viscous_eom": (i32, [vp, i32, vp]),
             "sph_set_partons": (i32, [vp, i64, vp, C.c_double, C.c_double]),
+            "sph_set_eos_backup": (i32, [vp, i32, C.c_double, C.c_double]),
             "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
             "sph_eos_build_inverse": (i32, [vp, i32, i32, i32, i32, C.c_double]),
             "sph_set_eos_mode": (i32, [vp, i32]),
@@ -242,6 +244,10 @@ def sph_set_viscous_eom(h, model: int, coeffs=None):
 def sph_set_partons(h, partons, norm: float, h_src: float):
     pt = _f64(partons).reshape(-1, 8) if partons is not None else np.zeros((0, 8))
     _check(lib().sph_set_partons(h, int(pt.shape[0]), _ptr(pt) if pt.size else None, float(norm), float(h_src)))
+
+
+def sph_set_eos_backup(h, enable: bool, T_scale_GeV: float = 0.165, mu_max_GeV: float = 0.45):
+    _check(lib().sph_set_eos_backup(h, int(bool(enable)), float(T_scale_GeV), float(mu_max_GeV)))
 
 
 def sph_freezeout_setup(h, e_fo: float, capacity: int):
@@ -439,6 +445,9 @@ class GpuEvent:
         src = getattr(ev, "partons", None)
         if src is not None and len(src.partons):
             sph_set_partons(self.h, src.partons, src.norm, src.h)
+        bk = getattr(ev, "eos_backup", None)
+        if bk is not None:
+            sph_set_eos_backup(self.h, True, bk[0], bk[1])
 
     def step(self, nsteps: int, sync: bool = False):
         sph_step(self.h, nsteps, SPH_SYNC if sync else 0)

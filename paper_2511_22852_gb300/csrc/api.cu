@@ -63,6 +63,8 @@ struct sph_event {
     int ntrack = 0;                 // jet tracks (sph_set_jets): device copy and Gaussian constants
     double *d_tracks = nullptr;
     double track_norm = 0.0, track_i2s2 = 0.0;
+    int backup = 0;                 // conformal-diagonal backup EoS (sph_set_eos_backup)
+    double cd_A0 = 0.0, cd_mu0[3] = {0.0, 0.0, 0.0};
     int nparton = 0;                // dynamical-initialisation partons (sph_set_partons), sorted by time
     double *d_partons = nullptr;
     long long parton_cap = 0;
@@ -154,6 +156,9 @@ static EvView make_view(const sph_event *ev)
     v.eos = ev->eos->dev;
     v.eos.offline = ev->eos_offline && ev->eos->dev.inv ? 1 : 0;
     v.tr = ev->tr;
+    v.eos.backup = ev->backup;
+    v.eos.cd_A0 = ev->cd_A0;
+    for (int q = 0; q < 3; ++q) v.eos.cd_mu0[q] = ev->cd_mu0[q];
     v.nparton = ev->nparton;
     v.partons = ev->d_partons;
     v.parton_norm = ev->parton_norm;
@@ -1036,6 +1041,41 @@ sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, dou
     ev->ntrack = (int)ntrack;
     ev->track_norm = ntrack > 0 ? 1.0 / (std::pow(2.0 * kPi, 1.5) * sigma * sigma * sigma) : 0.0;
     ev->track_i2s2 = ntrack > 0 ? 1.0 / (2.0 * sigma * sigma) : 0.0;
+    if (ev->gexec) {  // the parameters are part of the captured step: capture it again
+        cudaGraphExecDestroy(ev->gexec);
+        ev->gexec = nullptr;
+    }
+    if (ev->graph) {
+        cudaGraphDestroy(ev->graph);
+        ev->graph = nullptr;
+    }
+    ev->graph_ready = false;
+    ev->kernels_per_step = 0;
+    ev->observed = false;
+    return SPH_OK;
+}
+
+sph_status sph_set_eos_backup(sph_event *ev, int32_t enable, double T_scale_GeV, double mu_max_GeV)
+{
+    if (!ev) return fail(SPH_ERR_ARG, "null event");
+    if (enable && (!(T_scale_GeV > 0.0) || !(mu_max_GeV > 0.0)))
+        return fail(SPH_ERR_ARG, "T_scale and mu_max must be positive");
+    {
+        sph_status ws = wait_stream(ev);
+        if (ws != SPH_OK) return ws;
+    }
+    ev->backup = enable ? 1 : 0;
+    if (enable) {
+        // matched to the closed form at T_scale (T_0 = 1/fm): A0 = p(T_scale, 0) / T_scale^4,
+        // mu_q0 = mu_max (A0 / (p(T_scale, mu_q = mu_max) - p(T_scale, 0)))^(1/4)
+        const EosDev &E = ev->eos->dev;
+        const double Ts = T_scale_GeV / kHbarc, mm = mu_max_GeV / kHbarc;
+        ev->cd_A0 = E.a0 + E.a1 * (1.0 + std::tanh((T_scale_GeV - E.Tc_GeV) / E.w_GeV)) / 2.0;
+        for (int q = 0; q < 3; ++q) {
+            const double dp = E.chi[q] * Ts * Ts * mm * mm / 2.0;
+            ev->cd_mu0[q] = dp > 0.0 ? mm * std::pow(ev->cd_A0 / dp, 0.25) : mm;
+        }
+    }
     if (ev->gexec) {  // the parameters are part of the captured step: capture it again
         cudaGraphExecDestroy(ev->gexec);
         ev->gexec = nullptr;

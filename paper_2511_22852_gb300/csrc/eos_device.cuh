@@ -405,6 +405,31 @@ struct EosOut {
     uint32_t st;
 };
 
+// the conformal-diagonal backup EoS (Sec. "Equation of state", backup EoS) inverted in closed
+// form: s = 4 A0 T^3, n_q = 4 A0 mu_q^3 / mu_q0^4; e = 3 p; p_s = T/3, p_{n_q} = mu_q/3
+__device__ __forceinline__ EosOut backup_eos(const EosDev &E, double s, const double *n)
+{
+    EosOut o;
+    const double A0 = E.cd_A0;
+    o.T = cbrt(s / (4.0 * A0));
+    double pq = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double m0 = E.cd_mu0[q], m02 = m0 * m0;
+        o.mu[q] = cbrt(n[q] * m02 * m02 / (4.0 * A0));
+        const double r = o.mu[q] / m0, r2 = r * r;
+        pq += r2 * r2;
+        o.pn[q] = o.mu[q] / 3.0;
+    }
+    const double T2 = o.T * o.T;
+    o.p = A0 * (T2 * T2 + pq);
+    o.e = 3.0 * o.p;
+    o.ps = o.T / 3.0;
+    o.cs2 = 1.0 / 3.0;
+    o.st = PST_BACKUP;
+    return o;
+}
+
 __device__ __forceinline__ bool inside_table(const EosDev &E, const double *x)
 {
     bool in = x[0] >= E.T0 && x[0] <= E.Tmax;
@@ -443,6 +468,7 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
     }
     if (!use_table) {
         o.st = an_invert(E, s, n, x[0], x + 1, w);
+        if (o.st && E.backup && s > 0.0) return backup_eos(E, s, n);
         if (o.st) return o;
         if (E.has_table) {
             if (inside_table(E, x)) {

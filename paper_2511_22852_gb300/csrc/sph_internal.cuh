@@ -26,7 +26,7 @@ constexpr double kPi = 3.14159265358979323846;
 
 // per-particle status bits (same values as SPH_PST_* in the public header)
 constexpr uint32_t PST_FALLBACK = 1u, PST_OUT_OF_TABLE = 2u, PST_NOCONV = 4u, PST_NONFINITE = 8u,
-                   PST_CS2_CAPPED = 16u, PST_SOLVE_FAIL = 32u;
+                   PST_CS2_CAPPED = 16u, PST_SOLVE_FAIL = 32u, PST_BACKUP = 64u;
 // event-level device error bits
 constexpr uint32_t ERR_CELL_OVERFLOW = 1u;
 constexpr uint32_t ERR_PAIR_LIST = 2u;  // a backward pair missing from its partner's forward list
@@ -61,6 +61,10 @@ struct EosDev {
     // table: sn[node] = {s, nB, nS, nQ}, p[node]; node = ((iT*n1 + iB)*n2 + iS)*n3 + iQ
     int has_table, nT, nmu[3], maxit;
     int polish;  // 1: one Newton step after convergence (the plain form); 0: stop at the tolerance
+    // backup EoS where neither the table nor the closed form inverts: the conformal diagonal
+    // p = cd_A0 [T^4 + sum_q (mu_q / cd_mu0[q])^4] (backup = 0: none)
+    int backup;
+    double cd_A0, cd_mu0[3];
     double T0, dT, mu0[3], dmu[3], inv_dT, inv_dmu[3], Tmax, mumax[3];
     const double *sn;
     const double *p;

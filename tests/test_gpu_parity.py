@@ -454,6 +454,30 @@ def test_infeasible_charges_are_flagged(Bd):
     g.free()
 
 
+def test_backup_eos_takes_the_infeasible_particles(Bd):
+    """With the conformal-diagonal backup on, the particles neither the table nor the closed form
+    inverts get the backup's solution (flagged BACKUP, not NOCONV) and evolve; every field follows
+    the oracle over the steps, T and mu included."""
+    ev = I.viscous_bsq_2p1(n_target=1500, R=2.2, n_hot=12, charge_frac=0.1, coherent_charges=True)
+    ev.eos_backup = (0.165, 0.45)
+    g = Bd.GpuEvent(ev)
+    f = g.read(("STATUS", "T", "MU"))
+    run = O.OracleRun.start(ev)
+    aux, st = run.observe()
+    assert np.any(st & O.ST_BACKUP) and not np.any(st & O.ST_NOCONV)
+    assert np.array_equal(f["STATUS"] & Bd.PST_BACKUP, st & O.ST_BACKUP)
+    assert relerr(f["T"], aux[O.AUX["T"]]) < TOL_STEP and relerr(f["MU"], aux[O.AUX["muB"]:O.AUX["muQ"] + 1]) < TOL_STEP
+    g.step(1, sync=True)
+    run.step(1)
+    errs = state_errors(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    g.step(9, sync=True)
+    run.step(9)
+    errs = state_errors(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    g.free()
+
+
 TOL_MIXED = 1e-5  # the mixed-precision form against the FP64 oracle (T, mu, densities)
 
 
