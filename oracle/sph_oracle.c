@@ -559,7 +559,7 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
     double rn = resid_inf(P, x, s, n, r, J);
     for (int it = 0; it < P->newton_maxit; ++it) {
         if (rn <= P->newton_tol) {
-            /* one polishing step, taken only if it does not increase the residual */
+            /* one polishing step, kept when its point still meets the tolerance */
             double A[16], d[4], xn[4], rr[4];
             memcpy(A, J, sizeof(A));
             for (int k = 0; k < 4; ++k) d[k] = -r[k];
@@ -567,7 +567,7 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
                 for (int k = 0; k < 4; ++k) xn[k] = x[k] + d[k];
                 clamp_table(P, xn);
                 double rnn = resid_inf(P, xn, s, n, rr, NULL);
-                if (rnn <= rn) memcpy(x, xn, sizeof(xn));
+                if (rnn <= P->newton_tol) memcpy(x, xn, sizeof(xn));
             }
             return 0;
         }

@@ -288,11 +288,11 @@ __device__ bool tab_newton(const EosDev &E, double s, const double *n, double *x
                 return true;
             }
             ++w.solve;
-            if (solve4(J, d)) {  // one polishing step if it does not increase the residual
+            if (solve4(J, d)) {  // one polishing step, kept when its point still meets the tolerance
                 double xn[4] = {x[0] + d[0], x[1] + d[1], x[2] + d[2], x[3] + d[3]};
                 clamp4(E, xn);
                 ++w.resid;
-                if (resid(E, xn, s, inv_s, n, r, J) <= rn) {
+                if (resid(E, xn, s, inv_s, n, r, J) <= E.tol) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) x[k] = xn[k];
                     *jx = true;
