@@ -641,7 +641,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     return SPH_OK;
 }
 
-// Sizes (or grows) the half-pair lists of the plain 2D passes.  Each stage gives particle a a row
+// Sizes (or grows) the half-pair lists of the plain passes (2D and 3D).  Each stage gives particle a a row
 // of (its previous neighbour count - 1 + margin) entries; the allocation holds 1.5 x those rows
 // for the current state (at least 1.5 x the old allocation when growing), margin = 32.  Counts
 // are carried from stage to stage in the state order (pcnt[0] with Y[0], pcnt[1] with Y1[0]);
@@ -651,7 +651,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
 // margin and the first allocation (tests of the overflow paths).
 static sph_status size_pair_lists(sph_event *ev)
 {
-    if (ev->pairs_off || ev->dim != 2 || ev->mixed || ev->n == 0) return SPH_OK;
+    if (ev->pairs_off || ev->mixed || ev->n == 0) return SPH_OK;
     if (ev->cb.pl.total > 0 && ev->pair_ovf_host && *ev->pair_ovf_host > ev->pair_ovf_seen) {
         ev->pair_ovf_seen = *ev->pair_ovf_host;
         ev->pairs_grow = true;
@@ -683,7 +683,9 @@ static sph_status size_pair_lists(sph_event *ev)
     if (ev->pairs_grow) total = std::max<long long>(total, ev->cb.pl.total * 3 / 2);
     else if (const char *t = getenv("SPH_PAIR_TOTAL")) total = std::max<long long>(1, atoll(t));
     const int nparts = (n + 2047) / 2048;
-    const size_t bytes = (size_t)total * (3 * sizeof(double) + 2 * sizeof(int)) + (size_t)(n + 1) * sizeof(long long) +
+    // per entry: L, P (int), W and the kernel gradient (2 or 3 doubles)
+    const size_t per_entry = 2 * sizeof(int) + (1 + (size_t)ev->dim) * sizeof(double);
+    const size_t bytes = (size_t)total * per_entry + (size_t)(n + 1) * sizeof(long long) +
                          (size_t)nparts * sizeof(unsigned long long) + 4 * sizeof(int) * (size_t)n + 1024;
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
@@ -709,8 +711,10 @@ static sph_status size_pair_lists(sph_event *ev)
     PairBufs pl{};
     pl.total = total;
     pl.margin = margin;
-    pl.G = static_cast<double2 *>(m);
-    pl.W = reinterpret_cast<double *>(pl.G + total);
+    double *gbuf = static_cast<double *>(m);  // the kernel gradients first (16-byte aligned)
+    if (ev->dim == 2) pl.G = reinterpret_cast<double2 *>(gbuf);
+    else pl.G3 = gbuf;
+    pl.W = gbuf + (size_t)ev->dim * total;
     pl.off = reinterpret_cast<long long *>(pl.W + total);
     pl.part = reinterpret_cast<unsigned long long *>(pl.off + (n + 1));
     pl.L = reinterpret_cast<int *>(pl.part + nparts);

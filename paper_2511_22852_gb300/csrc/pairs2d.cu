@@ -394,13 +394,18 @@ inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
 
-void launch_pairs_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
-                          cudaStream_t st)
+void launch_pair_rows(const EvView &v, CellBufs cb, cudaStream_t st)
 {
     const int nparts = (v.n + kScanTile - 1) / kScanTile;
     k_rows_part<<<nparts, kScanThreads, 0, st>>>(v.n, cb.perm, cb.pl);
     k_rows_top<<<1, 1024, 0, st>>>(v.n, nparts, cb.pl, v.sc);
     k_rows_apply<<<nparts, kScanThreads, 0, st>>>(v.n, cb.perm, cb.pl);
+}
+
+void launch_pairs_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                          cudaStream_t st)
+{
+    launch_pair_rows(v, cb, st);
     // the forward partials go to the density rows, which the backward pass completes in place
     k_pairs_density_fwd<<<nblk(v.n, kWarps), 32 * kWarps, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, cb.pl,
                                                                    dens);

@@ -176,6 +176,18 @@ __device__ __forceinline__ int cell_coord(double x, double xmin, double inv_cell
 // neighbour decision r^2 < (2h)^2 is bit-for-bit reproducible
 __device__ __forceinline__ double dist2_2d(double dx, double dy) { return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)); }
 
+// the same in three dimensions
+__device__ __forceinline__ double dist2_3d(double dx, double dy, double dz)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// 3D cell key: the generalized Morton interleave of the per-axis bits (spread tables)
+__device__ __forceinline__ uint32_t key3(const EvView &v, int cx, int cy, int cz)
+{
+    return v.spread[cx] | v.spread[1024 + cy] | v.spread[2048 + cz];
+}
+
 // 1/sqrt(x) for x > 0 in double precision: CUDA's rsqrt (at most 1 ulp of error)
 __device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
 
@@ -293,7 +305,8 @@ struct PairBufs {
     unsigned long long *part;     // scan partial sums
     int *L, *P, *cntF, *cntB;
     double *W;
-    double2 *G;
+    double2 *G;   // 2D
+    double *G3;   // 3D: three components per entry
 };
 
 struct CellBufs {
@@ -347,6 +360,13 @@ void launch_pairs_density(const EvView &v, const double *y, const double *Nq, Ce
                           cudaStream_t st);
 void launch_pairs_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb,
                            double *gout, cudaStream_t st);
+// the per-stage row offsets of the pair lists (prefix scan of the carried counts)
+void launch_pair_rows(const EvView &v, CellBufs cb, cudaStream_t st);
+// plain 3D neighbour passes over the half-pair lists (after k_fpos3 and the row offsets)
+void launch_pairs3_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
+                           cudaStream_t st);
+void launch_pairs3_gradient(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb,
+                            double *gout, cudaStream_t st);
 void launch_density(const EvView &v, const double *y, const double *Nq, CellBufs cb, double *dens, int *nnb,
                     cudaStream_t st);
 void launch_eos(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,

@@ -11,6 +11,8 @@
 // State rows (nv = 13): x^1..3, u^1..3, S, Pi/sigma, pi^{ij}/sigma for (11, 12, 13, 22, 23);
 // pi^{33} follows from tracelessness, pi^{0 mu} from transversality.
 #include "eos_device.cuh"
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace sphg {
@@ -18,16 +20,6 @@ namespace sphg {
 namespace {
 
 constexpr int kWarps3 = 4;
-
-__device__ __forceinline__ double dist2_3d(double dx, double dy, double dz)
-{
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
-
-__device__ __forceinline__ uint32_t key3(const EvView &v, int cx, int cy, int cz)
-{
-    return v.spread[cx] | v.spread[1024 + cy] | v.spread[2048 + cz];
-}
 
 // ---------------------------------------------------------------------------
 // a1: cell coordinates, keys and bucket counts
@@ -132,49 +124,58 @@ __global__ void __launch_bounds__(32 * kWarps3) k_density3(EvView v, const doubl
                                                            const double *__restrict__ Nq,
                                                            const uint32_t *__restrict__ start,
                                                            const uint32_t *__restrict__ cnt, double *__restrict__ dens,
-                                                           int *__restrict__ nnb)
+                                                           int *__restrict__ nnb, int fallback, int *__restrict__ cnt_dst)
 {
+    // fallback = 1: the pair-list passes ran first; this pass only runs if one of their lists
+    // overflowed (and counts such stages)
+    if (fallback) {
+        if (!v.sc->pair_flag) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&v.sc->pair_ovf, 1u);
+    }
     __shared__ int queue[kWarps3][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarps3 + wid;
-    if (a >= v.n) return;
-    const size_t n = (size_t)v.n;
-    const double *X = y, *Y = y + n, *Z = y + 2 * n, *S = y + 6 * n;
-    const double xa[3] = {X[a], Y[a], Z[a]};
-    double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
-    int c = 0;
-    auto pair = [&](int qb) {
-        const int b = qb & 0x7FFFFFFF;
-        const double dx = xa[0] - X[b], dy = xa[1] - Y[b], dz = xa[2] - Z[b];
-        if (qb < 0 && !(dist2_3d(dx, dy, dz) < v.supp2)) return;
-        {
-            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            double q = r2 > 0.0 ? r2 * inv_sqrt(r2) * v.inv_h : 0.0;
-            double w = kernel_w(q);
-            sg += w;
-            ss = fma(S[b], w, ss);
-            sb = fma(Nq[b], w, sb);
-            sS = fma(Nq[n + b], w, sS);
-            sq = fma(Nq[2 * n + b], w, sq);
-            ++c;
+    // grid-stride over particles (one warp each): launched at a few blocks per SM when it is
+    // only the fallback of the pair-list passes
+    for (int a = blockIdx.x * kWarps3 + wid; a < v.n; a += gridDim.x * kWarps3) {  // warp-uniform
+        const size_t n = (size_t)v.n;
+        const double *X = y, *Y = y + n, *Z = y + 2 * n, *S = y + 6 * n;
+        const double xa[3] = {X[a], Y[a], Z[a]};
+        double sg = 0.0, ss = 0.0, sb = 0.0, sS = 0.0, sq = 0.0;
+        int c = 0;
+        auto pair = [&](int qb) {
+            const int b = qb & 0x7FFFFFFF;
+            const double dx = xa[0] - X[b], dy = xa[1] - Y[b], dz = xa[2] - Z[b];
+            if (qb < 0 && !(dist2_3d(dx, dy, dz) < v.supp2)) return;
+            {
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                double q = r2 > 0.0 ? r2 * inv_sqrt(r2) * v.inv_h : 0.0;
+                double w = kernel_w(q);
+                sg += w;
+                ss = fma(S[b], w, ss);
+                sb = fma(Nq[b], w, sb);
+                sS = fma(Nq[n + b], w, sS);
+                sq = fma(Nq[2 * n + b], w, sq);
+                ++c;
+            }
+        };
+        walk27(v, start, cnt, fpos, a, xa, queue[wid], pair);
+        sg = warp_sum(sg);
+        ss = warp_sum(ss);
+        sb = warp_sum(sb);
+        sS = warp_sum(sS);
+        sq = warp_sum(sq);
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0) {
+            const double sd = v.sigma_d;
+            dens[a] = sd * sg;
+            dens[n + a] = sd * ss;
+            dens[2 * n + a] = sd * sb;
+            dens[3 * n + a] = sd * sS;
+            dens[4 * n + a] = sd * sq;
+            nnb[a] = c;
+            if (cnt_dst) cnt_dst[a] = c;  // sizes the pair-list rows of the next stage
+            atomicAdd(&v.sc->pairs, (unsigned long long)c);
         }
-    };
-    walk27(v, start, cnt, fpos, a, xa, queue[wid], pair);
-    sg = warp_sum(sg);
-    ss = warp_sum(ss);
-    sb = warp_sum(sb);
-    sS = warp_sum(sS);
-    sq = warp_sum(sq);
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-    if (lane == 0) {
-        const double sd = v.sigma_d;
-        dens[a] = sd * sg;
-        dens[n + a] = sd * ss;
-        dens[2 * n + a] = sd * sb;
-        dens[3 * n + a] = sd * sS;
-        dens[4 * n + a] = sd * sq;
-        nnb[a] = c;
-        atomicAdd(&v.sc->pairs, (unsigned long long)c);
     }
 }
 
@@ -321,67 +322,70 @@ __global__ void __launch_bounds__(32 * kWarps3) k_gradient3(EvView v, int stage,
                                                             const double *__restrict__ gin,
                                                             const uint32_t *__restrict__ start,
                                                             const uint32_t *__restrict__ cnt,
-                                                            double *__restrict__ gout)
+                                                            double *__restrict__ gout, int fallback)
 {
+    if (fallback && !v.sc->pair_flag) return;  // the pair-list pass did the work
     __shared__ int queue[kWarps3][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarps3 + wid;
-    if (a >= v.n) return;
-    const size_t n = (size_t)v.n;
-    const double *X = y, *Y = y + n, *Z = y + 2 * n;
-    const double xa[3] = {X[a], Y[a], Z[a]};
-    double G[3] = {0, 0, 0}, H[3] = {0, 0, 0}, du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    auto pair = [&](int qb) {
-        const int b = qb & 0x7FFFFFFF;
-        const double d[3] = {xa[0] - X[b], xa[1] - Y[b], xa[2] - Z[b]};
-        if (qb < 0 && !(dist2_3d(d[0], d[1], d[2]) < v.supp2)) return;
-        const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
-        if (r2 > 0.0) {
-            const double ir = inv_sqrt(r2);
-            const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;
-            double gw[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                gw[k] = fac * d[k];
-                G[k] += gw[k];
+    // grid-stride over particles (one warp each): launched at a few blocks per SM when it is
+    // only the fallback of the pair-list passes
+    for (int a = blockIdx.x * kWarps3 + wid; a < v.n; a += gridDim.x * kWarps3) {  // warp-uniform
+        const size_t n = (size_t)v.n;
+        const double *X = y, *Y = y + n, *Z = y + 2 * n;
+        const double xa[3] = {X[a], Y[a], Z[a]};
+        double G[3] = {0, 0, 0}, H[3] = {0, 0, 0}, du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        auto pair = [&](int qb) {
+            const int b = qb & 0x7FFFFFFF;
+            const double d[3] = {xa[0] - X[b], xa[1] - Y[b], xa[2] - Z[b]};
+            if (qb < 0 && !(dist2_3d(d[0], d[1], d[2]) < v.supp2)) return;
+            const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+            if (r2 > 0.0) {
+                const double ir = inv_sqrt(r2);
+                const double fac = kernel_dw(r2 * ir * v.inv_h) * ir;
+                double gw[3];
+    #pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    gw[k] = fac * d[k];
+                    G[k] += gw[k];
+                }
+    #pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    double h = H[i];
+    #pragma unroll
+                    for (int j = 0; j < 3; ++j) h = fma(gin[(size_t)(3 * j + i) * n + b], gw[j], h);
+                    H[i] = h;
+                }
+    #pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const double ub = gin[(size_t)(9 + j) * n + b];
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) du[k][j] = fma(ub, gw[k], du[k][j]);
+                }
             }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                double h = H[i];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) h = fma(gin[(size_t)(3 * j + i) * n + b], gw[j], h);
-                H[i] = h;
-            }
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const double ub = gin[(size_t)(9 + j) * n + b];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) du[k][j] = fma(ub, gw[k], du[k][j]);
-            }
+        };
+        walk27(v, start, cnt, fpos, a, xa, queue[wid], pair);
+    #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G[k] = warp_sum(G[k]);
+            H[k] = warp_sum(H[k]);
+    #pragma unroll
+            for (int j = 0; j < 3; ++j) du[k][j] = warp_sum(du[k][j]);
         }
-    };
-    walk27(v, start, cnt, fpos, a, xa, queue[wid], pair);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        G[k] = warp_sum(G[k]);
-        H[k] = warp_sum(H[k]);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) du[k][j] = warp_sum(du[k][j]);
-    }
-    if (lane == 0) {
-        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-        const double sqrtg = v.milne ? tau : 1.0;
-        const double c = v.sigma_d * v.inv_h;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gout[(size_t)(3 * k + j) * n + a] = c * du[k][j];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            double F = H[i];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) F = fma(gin[(size_t)(3 * j + i) * n + a], G[j], F);
-            gout[(size_t)(9 + i) * n + a] = -sqrtg * c * F;
+        if (lane == 0) {
+            const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+            const double sqrtg = v.milne ? tau : 1.0;
+            const double c = v.sigma_d * v.inv_h;
+    #pragma unroll
+            for (int k = 0; k < 3; ++k)
+    #pragma unroll
+                for (int j = 0; j < 3; ++j) gout[(size_t)(3 * k + j) * n + a] = c * du[k][j];
+    #pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                double F = H[i];
+    #pragma unroll
+                for (int j = 0; j < 3; ++j) F = fma(gin[(size_t)(3 * j + i) * n + a], G[j], F);
+                gout[(size_t)(9 + i) * n + a] = -sqrtg * c * F;
+            }
         }
     }
 }
@@ -770,7 +774,12 @@ void launch_density3(const EvView &v, const double *y, const double *Nq, CellBuf
         return;
     }
     k_fpos3<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos3);
-    k_density3<<<nblk(v.n, kWarps3), 32 * kWarps3, 0, st>>>(v, y, cb.fpos3, Nq, cb.start, cb.cnt, dens, nnb);
+    const int lists = cb.pl.total > 0;
+    if (lists) launch_pairs3_density(v, y, Nq, cb, dens, nnb, st);
+    // as the fallback of the pair-list passes it usually exits at once: a few blocks per SM
+    const int grid = lists ? std::min(nblk(v.n, kWarps3), 8 * device_sm_count()) : nblk(v.n, kWarps3);
+    k_density3<<<grid, 32 * kWarps3, 0, st>>>(v, y, cb.fpos3, Nq, cb.start, cb.cnt, dens, nnb, lists,
+                                              lists ? cb.pl.cnt_dst : nullptr);
 }
 
 void launch_eos3(const EvView &v, int stage, const double *y, const double *dens, double *eos, double *gin,
@@ -787,7 +796,10 @@ void launch_gradient3(const EvView &v, int stage, const double *y, const double 
         launch_gradient3m(v, stage, y, gin, cb, gout, st);
         return;
     }
-    k_gradient3<<<nblk(v.n, kWarps3), 32 * kWarps3, 0, st>>>(v, stage, y, cb.fpos3, gin, cb.start, cb.cnt, gout);
+    const int lists = cb.pl.total > 0;
+    if (lists) launch_pairs3_gradient(v, stage, y, gin, cb, gout, st);
+    const int grid = lists ? std::min(nblk(v.n, kWarps3), 8 * device_sm_count()) : nblk(v.n, kWarps3);
+    k_gradient3<<<grid, 32 * kWarps3, 0, st>>>(v, stage, y, cb.fpos3, gin, cb.start, cb.cnt, gout, lists);
 }
 
 void launch_eom3(const EvView &v, int stage, int mode, const double *ys, const double *dens, const double *eos,

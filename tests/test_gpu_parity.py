@@ -739,3 +739,50 @@ def test_pair_list_rows_resize_on_the_device(Bd, monkeypatch):
     t = g.totals()
     assert t["pair_overflows"] <= 21  # at most every stage and the read-out
     g.free()
+
+
+def test_pair_lists_3d_match_per_particle_passes(Bd, monkeypatch):
+    """Plain 3D: the half-pair-list passes against the per-particle passes (SPH_PAIR_LISTS=0):
+    the same sums in another order -- states within rounding, equal pair counts per step, and
+    both on the oracle."""
+    ev = CASES3["blob3_milne"]()
+    g = Bd.GpuEvent(ev)
+    g.step(4, sync=True)
+    monkeypatch.setenv("SPH_PAIR_LISTS", "0")
+    g0 = Bd.GpuEvent(ev)
+    g0.step(4, sync=True)
+    names = ("X", "U", "S", "BV", "PV", "T", "SIGMA_STAR")
+    a, b = g.read(names), g0.read(names)
+    for k in names:
+        assert relerr(a[k], b[k]) < 1e-13, (k, relerr(a[k], b[k]))
+    t, t0 = g.totals(), g0.totals()
+    assert t["pair_overflows"] == 0
+    g.step(1, sync=True)
+    g0.step(1, sync=True)
+    assert g.totals()["pairs"] - t["pairs"] == g0.totals()["pairs"] - t0["pairs"] > 0
+    run = O.OracleRun.start(ev)
+    run.step(5)
+    errs = state_errors3(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    g.free()
+    g0.free()
+
+
+def test_pair_lists_3d_overflow_falls_back_then_grows(Bd, monkeypatch):
+    """3D lists allocated far too small: per-particle passes for the stage (the step still
+    matches the oracle), then the allocation grows and the stages run on the lists."""
+    monkeypatch.setenv("SPH_PAIR_TOTAL", "64")
+    ev = CASES3["blob3_milne"]()
+    g = Bd.GpuEvent(ev)
+    run = O.OracleRun.start(ev)
+    g.step(1, sync=True)
+    run.step(1)
+    assert g.totals()["pair_overflows"] >= 2
+    errs = state_errors3(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    seen = []
+    for _ in range(3):
+        g.step(1, sync=True)
+        seen.append(g.totals()["pair_overflows"])
+    assert seen[-1] == seen[-2], seen
+    g.free()
