@@ -190,7 +190,9 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     }
     bool used = false;
     EosOut o = eos_invert(E, v.tr.cs2_cap, s, nq, gs, used, w);
-    guess_out[a] = used ? o.T : 0.0;
+    // warm start of the next stage: the table solution, or minus the closed-form T (none after
+    // the backup EoS or without a solution)
+    guess_out[a] = used ? o.T : ((o.st & (PST_NOCONV | PST_NONFINITE | PST_BACKUP)) ? 0.0 : -o.T);
 #pragma unroll
     for (int q = 0; q < 3; ++q) guess_out[(1 + q) * n + a] = used ? o.mu[q] : 0.0;
     status[a] = o.st;

@@ -51,7 +51,10 @@ __device__ __forceinline__ void an_g(const EosDev &E, double T, double s, double
     gp = 12.0 * T2 * f + 8.0 * T3 * fp + T4 * fpp - 3.0 * c / T4;
 }
 
-__device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double &T, double *mu, EosWork &w)
+// Tguess > 0: the particle's closed-form T of its previous stage (warm start of the bracket and of
+// the Newton iteration; the root is the same)
+__device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double &T, double *mu, EosWork &w,
+                              double Tguess = 0.0)
 {
     if (!isfinite(s) || !isfinite(n[0]) || !isfinite(n[1]) || !isfinite(n[2])) return PST_NONFINITE | PST_NOCONV;
     if (!(s > 0.0)) return PST_NOCONV;
@@ -61,15 +64,20 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
         else if (n[q] != 0.0) return PST_NOCONV;
     }
     double Thi = cbrt(s / (4.0 * E.a0));
+    // start: the bound cbrt(s / 4 a0) >= T, or a warm start below it
+    const bool warm = Tguess > 0.0 && Tguess < Thi;
+    const double t0 = warm ? Tguess : Thi;
     double g, gp;
-    an_g(E, Thi, s, c, g, gp);
+    an_g(E, t0, s, c, g, gp);
     ++w.g;
-    double Tlo = Thi;
-    if (g > 0.0) {
+    double Tlo = t0;
+    if (g > 0.0) {  // the root lies below t0: step down to a lower bracket
+        Thi = t0;
+        const double f = warm ? 0.99 : 0.8;  // fine steps from a warm start
         double gprev = g;
         bool found = false;
         for (int k = 0; k < 400; ++k) {
-            Tlo *= 0.8;
+            Tlo *= f;
             double gl, gpl;
             an_g(E, Tlo, s, c, gl, gpl);
             ++w.g;
@@ -82,7 +90,7 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
         }
         if (!found) return PST_NOCONV;
     }
-    double t = Thi;
+    double t = t0;
     for (int it = 0; it < 200; ++it) {
         an_g(E, t, s, c, g, gp);
         ++w.g;
@@ -467,7 +475,8 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
         }
     }
     if (!use_table) {
-        o.st = an_invert(E, s, n, x[0], x + 1, w);
+        // a negative guess is the particle's previous closed-form T
+        o.st = an_invert(E, s, n, x[0], x + 1, w, guess[0] < 0.0 ? -guess[0] : 0.0);
         if (o.st && E.backup && s > 0.0) return backup_eos(E, s, n);
         if (o.st) return o;
         if (E.has_table) {

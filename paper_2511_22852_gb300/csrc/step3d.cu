@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(64, 6) k_eos3(EvView v, int stage, const doubl
         wres = w.resid;
         wsol = w.solve;
         wg = w.g;
-        guess_out[a] = used ? o.T : 0.0;
+        guess_out[a] = used ? o.T : ((o.st & (PST_NOCONV | PST_NONFINITE | PST_BACKUP)) ? 0.0 : -o.T);
         for (int q = 0; q < 3; ++q) guess_out[(size_t)(1 + q) * n + a] = used ? o.mu[q] : 0.0;
         status[a] = o.st;
         warp_or(&v.sc->status_or, o.st);
