@@ -15,10 +15,11 @@
 // from device memory and loop over the arena (or its cells) with a fixed grid, so the
 // whole step is captured once as a CUDA graph and replayed for every composition.
 //
-// The neighbour passes are cell-tiled: one block per cell stages the particles of the 3x3
-// neighbouring cells (three contiguous runs of the sorted arena, one per cell row) in
-// shared memory as positions relative to the centre cell's origin, and every particle of
-// the cell scans them (1, 2 or 4 lanes per particle, by occupancy of the cell).  A proven
+// The neighbour passes are cell-tiled over cells of side h: one block per cell stages the
+// particles of the 5x5 neighbouring cells (five contiguous runs of the sorted arena, one per
+// cell row; every pair closer than 2h lies in it) in shared memory as positions relative to
+// the centre cell's origin, and every particle of the cell scans them with L lanes (by the
+// cell's occupancy, up to 16).  A proven
 // bound on the float r^2 decides all but a thin shell of candidates; inside the shell the
 // FP64 test r^2 < (2h)^2 with separately rounded products decides, so the neighbour sets
 // are exactly those of the FP64 form.  Sums are Neumaier-compensated per lane and combined
@@ -53,14 +54,15 @@ namespace {
 
 constexpr int kScanBlocks = 256;
 constexpr int kTTDefault = 128;  // threads of a tiled neighbour block (the autotuner may pick another)
-constexpr int kTile = 512;  // candidates staged in shared memory at a time
+constexpr int kTile = 640;  // candidates staged in shared memory at a time (a 5x5 block of ~23-particle cells)
+constexpr int kRows = 5;    // cell rows (and columns) of the search block: cells of side h, pairs closer than 2h
 // Accumulation: each lane sums runs of kRun candidates in plain FP32 (at most kRun terms, so a
 // run's sum errs by <= kRun u times the sum of its terms' magnitudes, u = 2^-24) and folds
 // every run into Neumaier-compensated FP32 sums; the lanes of a particle are combined in FP64.
 constexpr int kRun = 16;
 
 // ---------------------------------------------------------------------------
-// single-precision helpers (Neumaier two-sum accumulation, cubic spline kernel)
+// single-precision helpers (Neumaier two-sum accumulation)
 struct CSum {
     float hi, lo;
 };
@@ -72,18 +74,6 @@ __device__ __forceinline__ void cadd(CSum &s, float x)
     s.hi = t;
 }
 __device__ __forceinline__ double cval(CSum s) { return (double)s.hi + (double)s.lo; }
-__device__ __forceinline__ float kernel_wf(float q)
-{
-    if (q <= 1.0f) return fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
-    float t = 2.0f - q;
-    return 0.25f * t * t * t;
-}
-__device__ __forceinline__ float kernel_dwf(float q)
-{
-    if (q <= 1.0f) return q * fmaf(2.25f, q, -3.0f);
-    float t = 2.0f - q;
-    return -0.75f * t * t;
-}
 __device__ __forceinline__ double inf_d() { return __longlong_as_double(0x7FF0000000000000LL); }
 
 // ---------------------------------------------------------------------------
@@ -125,7 +115,7 @@ __global__ void k_seg_bbox(Arena A, int stage, const double *__restrict__ y)
     }
 }
 
-// number of cells of side 2h from the minimum to v, clamped to [1, kMaxCellsAxis]
+// number of cells of side h from the minimum to v, clamped to [1, kMaxCellsAxis]
 __device__ __forceinline__ int cells_to(double v, double v0, double inv_cell)
 {
     if (!(v >= v0)) return 1;
@@ -142,7 +132,7 @@ __global__ void __launch_bounds__(kMaxSlots) k_seg_grid(Arena A, int stage)
     int nc = 0;
     if (s < T->nslots && seg_active(T, s, stage, false)) {
         SegGrid &g = A.grid[s];
-        const double ic = A.segv[s].inv_cell;
+        const double ic = A.segv[s].inv_h;  // cells of side h
         const double x0 = dec_double(g.bb[0]), y0 = dec_double(g.bb[1]);
         const int nx = cells_to(dec_double(g.bb[2]), x0, ic), ny = cells_to(dec_double(g.bb[3]), y0, ic);
         g.x0 = x0;
@@ -184,7 +174,7 @@ __global__ void k_seg_keys(Arena A, int stage, const double *__restrict__ y)
         const int s = A.segid[a];
         if (s < 0 || !seg_active(T, s, stage, false) || a - T->slots[s].off >= T->slots[s].n) continue;
         const SegGrid &g = A.grid[s];
-        const double ic = A.segv[s].inv_cell;
+        const double ic = A.segv[s].inv_h;
         const int cx = clampi(cell_coord(y[a], g.x0, ic), 0, g.nx - 1);
         const int cy = clampi(cell_coord(y[P + a], g.y0, ic), 0, g.ny - 1);
         const uint32_t k = (uint32_t)(g.base + cy * g.nx + cx);
@@ -328,7 +318,7 @@ __global__ void k_seg_permute(Arena A, int stage, SegPerm pa)
         const SegGrid &g = A.grid[s];
         const int lc = (int)A.key[p] - g.base;
         const int cx = lc % g.nx, cy = lc / g.nx;
-        const double cs = 2.0 * A.segv[s].h;
+        const double cs = A.segv[s].h;
         const double *X = pa.src[0];
         A.fpos[j] = make_float2((float)(X[p] - (g.x0 + (double)cx * cs)), (float)(X[P + p] - (g.y0 + (double)cy * cs)));
         A.fq[j] = make_float4((float)X[4 * P + p], (float)pa.nq[p], (float)pa.nq[P + p], (float)pa.nq[2 * P + p]);
@@ -339,9 +329,10 @@ __global__ void k_seg_permute(Arena A, int stage, SegPerm pa)
 // cell-tiled neighbour passes (rows a3, a5)
 struct CellCtx {
     int s, first, na, M, clamped;
-    int rs[3], rl[3];  // the three candidate runs (one per cell row): start, length
-    int rm0[3], rm1[3];  // positions where the centre column of each row starts and ends
-    float cs;            // cell side 2h in single precision
+    int rs[kRows];       // the candidate run of each cell row: its first arena position
+    int cum[kRows + 1];  // candidates of the rows before: row o holds candidates [cum[o], cum[o + 1])
+    int bnd[kRows][4];   // arena positions where the row's columns cx-1, cx, cx+1, cx+2 begin
+    float cs;            // cell side h in single precision
 };
 
 // last slot whose first cell is <= c (slots without cells share the next slot's base)
@@ -356,61 +347,119 @@ __device__ __forceinline__ int find_slot(const int *base, int ns, int c)
     return lo;
 }
 
-__device__ void cell_setup(const Arena &A, const int *s_base, int ns, int c, CellCtx &cc)
+// The context of cell c, built by one warp: every lane reads the cell's scalars (broadcast
+// loads), lanes 0..4 the bounds of one cell row each; the row lengths are scanned across lanes.
+// Rows and columns outside the grid are empty runs.
+__device__ void cell_setup(const Arena &A, const int *s_base, int ns, int c, CellCtx &cc, int lane)
 {
     const int s = find_slot(s_base, ns, c);
-    const SegGrid g = A.grid[s];
+    const SegGrid &g = A.grid[s];
+    const int nx = g.nx, ny = g.ny, base = g.base;
     const int off = A.tab->slots[s].off;
-    const uint32_t S0 = A.start[g.base];
-    const int lc = c - g.base, cx = lc % g.nx, cy = lc / g.nx;
-    cc.s = s;
-    cc.clamped = g.nx >= kMaxCellsAxis || g.ny >= kMaxCellsAxis;
-    cc.first = off + (int)(A.start[c] - S0);
-    cc.na = (int)A.cnt[c];
-    cc.cs = (float)(2.0 * A.segv[s].h);
-    int M = 0;
-    for (int o = 0; o < 3; ++o) {
-        const int r = cy - 1 + o;
-        int st = 0, ln = 0, m0 = 0, m1 = 0;
-        if (r >= 0 && r < g.ny) {
-            const int kc = g.base + r * g.nx + cx;
-            const int k0 = g.base + r * g.nx + max(cx - 1, 0);
-            const int k1 = g.base + r * g.nx + min(cx + 1, g.nx - 1);
-            st = off + (int)(A.start[k0] - S0);
-            ln = (int)(A.start[k1] + A.cnt[k1] - A.start[k0]);
-            m0 = off + (int)(A.start[kc] - S0);
-            m1 = m0 + (int)A.cnt[kc];
-        }
-        cc.rs[o] = st;
-        cc.rl[o] = ln;
-        cc.rm0[o] = m0;
-        cc.rm1[o] = m1;
-        M += ln;
+    const uint32_t S0 = A.start[base];
+    const int lc = c - base, cx = lc % nx, cy = lc / nx;
+    const int r = cy - 2 + lane;
+    int st = 0, ln = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    if (lane < kRows && r >= 0 && r < ny) {
+        const int row = base + r * nx;
+        const int cl = max(cx - 2, 0), cr = min(cx + 2, nx - 1);
+        st = off + (int)(A.start[row + cl] - S0);
+        const int en = off + (int)(A.start[row + cr] + A.cnt[row + cr] - S0);
+        ln = en - st;
+        // start of column col of the row; before the grid: the run's start, past it: its end
+        auto col0 = [&](int col) { return col < 0 ? st : (col >= nx ? en : off + (int)(A.start[row + col] - S0)); };
+        e0 = col0(cx - 1);
+        e1 = col0(cx);
+        e2 = col0(cx + 1);
+        e3 = col0(cx + 2);
     }
-    cc.M = M;
+    int inc = ln;  // inclusive scan of the row lengths over lanes 0..4
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane < kRows) {
+        cc.rs[lane] = st;
+        cc.cum[lane + 1] = inc;
+        cc.bnd[lane][0] = e0;
+        cc.bnd[lane][1] = e1;
+        cc.bnd[lane][2] = e2;
+        cc.bnd[lane][3] = e3;
+    }
+    const int M = __shfl_sync(0xFFFFFFFFu, inc, kRows - 1);
+    if (lane == 0) {
+        cc.cum[0] = 0;
+        cc.s = s;
+        cc.clamped = nx >= kMaxCellsAxis || ny >= kMaxCellsAxis;
+        cc.first = off + (int)(A.start[c] - S0);
+        cc.na = (int)A.cnt[c];
+        cc.cs = (float)A.segv[s].h;
+        cc.M = M;
+    }
 }
 
-// candidate q of the 3x3 block: its arena position and its position relative to the
-// centre cell's origin (own-cell-relative float position + the cell offset)
+// arena position of candidate q of the 5x5 block
+__device__ __forceinline__ int cand_arena(const CellCtx &cc, int q)
+{
+    int o = 0;
+#pragma unroll
+    for (int k = 1; k < kRows; ++k) o += q >= cc.cum[k];
+    return cc.rs[o] + (q - cc.cum[o]);
+}
+
+// candidate q of the 5x5 block: its arena position and its position relative to the
+// centre cell's origin (own-cell-relative float position + the cell offset, an exact
+// multiple of the float cell side)
 __device__ __forceinline__ int cand_index(const CellCtx &cc, int q, const float2 *__restrict__ fpos, float2 &rel)
 {
     int o = 0;
-    if (q >= cc.rl[0]) {
-        q -= cc.rl[0];
-        o = 1;
-        if (q >= cc.rl[1]) {
-            q -= cc.rl[1];
-            o = 2;
-        }
-    }
-    const int b = cc.rs[o] + q;
-    const float ox = b < cc.rm0[o] ? -cc.cs : (b < cc.rm1[o] ? 0.0f : cc.cs);
-    const float oy = (float)(o - 1) * cc.cs;
+#pragma unroll
+    for (int k = 1; k < kRows; ++k) o += q >= cc.cum[k];
+    const int b = cc.rs[o] + (q - cc.cum[o]);
+    const int dc = (b >= cc.bnd[o][0]) + (b >= cc.bnd[o][1]) + (b >= cc.bnd[o][2]) + (b >= cc.bnd[o][3]) - 2;
     const float2 f = fpos[b];
-    rel = make_float2(f.x + ox, f.y + oy);
+    rel = make_float2(f.x + (float)dc * cc.cs, f.y + (float)(o - 2) * cc.cs);
     return b;
 }
 
+// lanes per particle: the most (up to 16) for which kLaneWarps warps hold all na particles in
+// one pass (floor(32 / L) particles per warp, a particle's lanes inside one warp), else 1.  It
+// depends on the cell alone, not on the block size, so the summation order (and the results)
+// do not change with the launch shape.
+constexpr int kLaneWarps = 4;
+__device__ __forceinline__ int lanes_per_particle(int na)
+{
+    for (int L = 16; L > 1; --L)
+        if (kLaneWarps * (32 / L) >= na) return L;
+    return 1;
+}
+
+// fixed-order sum over the L lanes of a particle (lanes [p L, p L + L) of a warp); the total
+// lands in the particle's first lane
+__device__ __forceinline__ double seg_sum(double v, int l, int L)
+{
+    for (int o = 1; o < L; o <<= 1) {
+        const double t = __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if ((l & (2 * o - 1)) == 0 && l + o < L) v += t;
+    }
+    return v;
+}
+
+// cubic spline in single precision without branches: w(q) = (2-q)^3/4 - max(1-q,0)^3 and
+// dw/dq = 3 max(1-q,0)^2 - 3 (2-q)^2 / 4 on 0 <= q <= 2 (the two pieces of the spline)
+__device__ __forceinline__ void spline_terms(float qq, float &t2, float &t, float &u2, float &u)
+{
+    t = 2.0f - qq;
+    u = fmaxf(1.0f - qq, 0.0f);
+    t2 = t * t;
+    u2 = u * u;
+}
+
+// Inner loops of the tiled passes: every candidate of a lane's run is evaluated without
+// branches (the accept decision zeroes its terms; adding +0 is exact), since the lanes of a
+// warp accept different candidates and a branch would cost the same issue slots.  Only the
+// thin shell takes a branch, to the exact FP64 test.
 template <int TT>
 __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__restrict__ y,
                                                      const double *__restrict__ Nq)
@@ -418,120 +467,129 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
     __shared__ int s_base[kMaxSlots];
     __shared__ float2 cpos[kTile];
     __shared__ float4 cq[kTile];
-    __shared__ int cidx[kTile];
     __shared__ CellCtx cc;
+    __shared__ int s_cell, s_cur;
+    __shared__ unsigned long long s_acc[2];  // pairs and shell tests of slot s_cur, flushed when it changes
     const BatchTable *T = A.tab;
     const int ns = T->nslots;
     for (int i = threadIdx.x; i < ns; i += TT) s_base[i] = A.grid[i].base;
-    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_cur = -1;
+        s_acc[0] = s_acc[1] = 0ull;
+    }
     const int ncells = *A.ncells;
     const size_t P = (size_t)A.P;
-    const int tid = threadIdx.x;
-    __shared__ int s_cell;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = TT / 32;
     for (;;) {
-        if (tid == 0) {
-            s_cell = (int)atomicAdd(&A.claim[CLAIM_DENSITY], 1u);
-            if (s_cell < ncells) cell_setup(A, s_base, ns, s_cell, cc);
+        __syncthreads();  // the previous cell's context and tile are no longer read
+        if (warp == 0) {
+            int c = lane == 0 ? (int)atomicAdd(&A.claim[CLAIM_DENSITY], 1u) : 0;
+            c = __shfl_sync(0xFFFFFFFFu, c, 0);
+            if (lane == 0) s_cell = c;
+            if (c < ncells && A.cnt[c] > 0u) cell_setup(A, s_base, ns, c, cc, lane);
+            else if (lane == 0) cc.na = 0;
+            const int snew = c < ncells ? (cc.na > 0 ? cc.s : s_cur) : -1;
+            if (lane == 0 && snew != s_cur) {
+                if (s_cur >= 0) {
+                    if (s_acc[0]) atomicAdd(&A.sc[s_cur].pairs, s_acc[0]);
+                    if (s_acc[1]) atomicAdd(&A.sc[s_cur].shell_tests, s_acc[1]);
+                }
+                s_acc[0] = s_acc[1] = 0ull;
+                s_cur = snew;
+            }
         }
         __syncthreads();
         if (s_cell >= ncells) break;
         const int na = cc.na;
-        if (na > 0) {
-            const EvView &V = A.segv[cc.s];
-            const float ih = (float)V.inv_h;
-            const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
-            const double supp2 = V.supp2, sd = V.sigma_d;
-            int L = 1;  // lanes per particle: as many as the block holds, up to 8
-            while (L < 8 && na * 2 * L <= TT) L *= 2;
-            const int l = tid & (L - 1);
-            unsigned long long pairs = 0ull, shell = 0ull;
-            for (int g0 = 0; g0 < na; g0 += TT / L) {
-                const int my = g0 + tid / L;
-                const bool valid = my < na;
-                const int a = cc.first + (valid ? my : 0);
-                const double xa = y[a], ya = y[P + a];
-                const float2 fa = A.fpos[a];
-                const float fax = fa.x, fay = fa.y;
-                CSum sg = {0.f, 0.f}, ss = {0.f, 0.f}, sb = {0.f, 0.f}, sS = {0.f, 0.f}, sq = {0.f, 0.f};
-                int nacc = 0;
-                for (int t0 = 0; t0 < cc.M; t0 += kTile) {
-                    const int mt = min(kTile, cc.M - t0);
-                    __syncthreads();
+        if (na == 0) continue;
+        const EvView &V = A.segv[cc.s];
+        const float ih = (float)V.inv_h;
+        const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
+        const double supp2 = V.supp2, sd = V.sigma_d;
+        const int L = lanes_per_particle(na), ppw = 32 / L;
+        const int pl = lane / L, l = lane - pl * L;
+        const int M = cc.M;
+        unsigned pairs = 0u, shell = 0u;
+        for (int g0 = 0; g0 < na; g0 += NW * ppw) {
+            const int my = g0 + warp * ppw + pl;
+            const bool valid = pl < ppw && my < na;
+            const int a = cc.first + (valid ? my : 0);
+            const double xa = y[a], ya = y[P + a];
+            const float2 fa = A.fpos[a];
+            CSum sg = {0.f, 0.f}, ss = {0.f, 0.f}, sb = {0.f, 0.f}, sS = {0.f, 0.f}, sq = {0.f, 0.f};
+            int nacc = 0;
+            for (int t0 = 0; t0 < M; t0 += kTile) {
+                const int mt = min(kTile, M - t0);
+                if (g0 == 0 || M > kTile) {  // one tile serves every pass of the cell
+                    if (t0 > 0 || g0 > 0) __syncthreads();
                     for (int i = tid; i < mt; i += TT) {
                         float2 rel;
                         const int b = cand_index(cc, t0 + i, A.fpos, rel);
                         cpos[i] = rel;
                         cq[i] = A.fq[b];
-                        cidx[i] = b;
                     }
                     __syncthreads();
-                    if (valid) {
-                        // runs of kRun candidates summed in plain FP32, each run folded into the
-                        // compensated sums
-                        for (int jb = l; jb < mt; jb += kRun * L) {
-                            const int je = min(mt, jb + kRun * L);
-                            float pg = 0.f, ps = 0.f, pB = 0.f, pS = 0.f, pQ = 0.f;
-                            for (int j = jb; j < je; j += L) {
-                                const float2 pb = cpos[j];
-                                const float dx = fax - pb.x, dy = fay - pb.y;
-                                const float r2 = fmaf(dx, dx, dy * dy);
-                                if (r2 <= shi) {
-                                    bool acc = r2 < slo;
-                                    if (!acc) {  // thin shell: the exact FP64 decision
-                                        const int b = cidx[j];
-                                        acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
-                                        ++shell;
-                                    }
-                                    if (acc) {
-                                        const float q = r2 > 0.0f ? r2 * rsqrtf(r2) * ih : 0.0f;
-                                        const float w = kernel_wf(q);
-                                        const float4 v = cq[j];
-                                        pg += w;
-                                        ps = fmaf(v.x, w, ps);
-                                        pB = fmaf(v.y, w, pB);
-                                        pS = fmaf(v.z, w, pS);
-                                        pQ = fmaf(v.w, w, pQ);
-                                        ++nacc;
-                                    }
-                                }
+                }
+                if (valid) {
+                    // runs of kRun candidates summed in plain FP32, each run folded into the
+                    // compensated sums
+                    for (int jb = l; jb < mt; jb += kRun * L) {
+                        const int je = min(mt, jb + kRun * L);
+                        float pg = 0.f, ps = 0.f, pB = 0.f, pS = 0.f, pQ = 0.f;
+#pragma unroll 4
+                        for (int j = jb; j < je; j += L) {
+                            const float2 pb = cpos[j];
+                            const float dx = fa.x - pb.x, dy = fa.y - pb.y;
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            bool acc = r2 < slo;
+                            if (r2 >= slo && r2 <= shi) {  // thin shell: the exact FP64 decision
+                                const int b = cand_arena(cc, t0 + j);
+                                acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                                ++shell;
                             }
-                            cadd(sg, pg);
-                            cadd(ss, ps);
-                            cadd(sb, pB);
-                            cadd(sS, pS);
-                            cadd(sq, pQ);
+                            const float qq = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * ih;
+                            float t2, t, u2, u;
+                            spline_terms(qq, t2, t, u2, u);
+                            const float w = acc ? fmaf(0.25f * t2, t, -(u2 * u)) : 0.0f;
+                            const float4 v = cq[j];
+                            pg += w;
+                            ps = fmaf(v.x, w, ps);
+                            pB = fmaf(v.y, w, pB);
+                            pS = fmaf(v.z, w, pS);
+                            pQ = fmaf(v.w, w, pQ);
+                            nacc += acc;
                         }
+                        cadd(sg, pg);
+                        cadd(ss, ps);
+                        cadd(sb, pB);
+                        cadd(sS, pS);
+                        cadd(sq, pQ);
                     }
                 }
-                double tg = cval(sg), ts = cval(ss), tb = cval(sb), tS = cval(sS), tq = cval(sq);
-                for (int o = 1; o < L; o <<= 1) {
-                    tg += __shfl_xor_sync(0xFFFFFFFFu, tg, o);
-                    ts += __shfl_xor_sync(0xFFFFFFFFu, ts, o);
-                    tb += __shfl_xor_sync(0xFFFFFFFFu, tb, o);
-                    tS += __shfl_xor_sync(0xFFFFFFFFu, tS, o);
-                    tq += __shfl_xor_sync(0xFFFFFFFFu, tq, o);
-                    nacc += __shfl_xor_sync(0xFFFFFFFFu, nacc, o);
-                }
-                if (valid && l == 0) {
-                    const double ux = y[2 * P + a], uy = y[3 * P + a];
-                    A.dens[a] = sd * tg;
-                    A.dens[P + a] = sd * ts;
-                    A.dens[2 * P + a] = sd * tb;
-                    A.dens[3 * P + a] = sd * tS;
-                    A.dens[4 * P + a] = sd * tq;
-                    A.dens[5 * P + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
-                    A.nnb[a] = nacc;
-                    pairs += (unsigned long long)nacc;
-                }
             }
-            pairs = __reduce_add_sync(0xFFFFFFFFu, (unsigned)pairs);
-            shell = __reduce_add_sync(0xFFFFFFFFu, (unsigned)shell);
-            if ((tid & 31) == 0) {
-                if (pairs) atomicAdd(&A.sc[cc.s].pairs, pairs);
-                if (shell) atomicAdd(&A.sc[cc.s].shell_tests, shell);
+            const double tg = seg_sum(cval(sg), l, L), ts = seg_sum(cval(ss), l, L);
+            const double tb = seg_sum(cval(sb), l, L), tS = seg_sum(cval(sS), l, L);
+            const double tq = seg_sum(cval(sq), l, L);
+            nacc = (int)seg_sum((double)nacc, l, L);
+            if (valid && l == 0) {
+                const double ux = y[2 * P + a], uy = y[3 * P + a];
+                A.dens[a] = sd * tg;
+                A.dens[P + a] = sd * ts;
+                A.dens[2 * P + a] = sd * tb;
+                A.dens[3 * P + a] = sd * tS;
+                A.dens[4 * P + a] = sd * tq;
+                A.dens[5 * P + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+                A.nnb[a] = nacc;
+                pairs += (unsigned)nacc;
             }
         }
-        __syncthreads();
+        pairs = __reduce_add_sync(0xFFFFFFFFu, pairs);
+        shell = __reduce_add_sync(0xFFFFFFFFu, shell);
+        if (lane == 0) {
+            if (pairs) atomicAdd(&s_acc[0], (unsigned long long)pairs);
+            if (shell) atomicAdd(&s_acc[1], (unsigned long long)shell);
+        }
     }
 }
 
@@ -542,130 +600,126 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
     __shared__ float2 cpos[kTile];
     __shared__ float4 cX[kTile];
     __shared__ float2 cU[kTile];
-    __shared__ int cidx[kTile];
     __shared__ CellCtx cc;
+    __shared__ int s_cell;
     const BatchTable *T = A.tab;
     const int ns = T->nslots;
     for (int i = threadIdx.x; i < ns; i += TT) s_base[i] = A.grid[i].base;
-    __syncthreads();
     const int ncells = *A.ncells;
     const size_t P = (size_t)A.P;
     const double *gin = A.gin;
-    const int tid = threadIdx.x;
-    __shared__ int s_cell;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = TT / 32;
     for (;;) {
-        if (tid == 0) {
-            s_cell = (int)atomicAdd(&A.claim[CLAIM_GRADIENT], 1u);
-            if (s_cell < ncells) cell_setup(A, s_base, ns, s_cell, cc);
+        __syncthreads();
+        if (warp == 0) {
+            int c = lane == 0 ? (int)atomicAdd(&A.claim[CLAIM_GRADIENT], 1u) : 0;
+            c = __shfl_sync(0xFFFFFFFFu, c, 0);
+            if (lane == 0) s_cell = c;
+            bool work = c < ncells && A.cnt[c] > 0u;
+            if (work) work = T->slots[find_slot(s_base, ns, c)].mode == SLOT_STEP;
+            if (work) cell_setup(A, s_base, ns, c, cc, lane);
+            else if (lane == 0) cc.na = 0;
         }
         __syncthreads();
         if (s_cell >= ncells) break;
         const int na = cc.na;
-        if (na > 0 && T->slots[cc.s].mode == SLOT_STEP) {
-            const EvView &V = A.segv[cc.s];
-            const float ih = (float)V.inv_h;
-            const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
-            const double supp2 = V.supp2;
-            int L = 1;  // lanes per particle: as many as the block holds, up to 8
-            while (L < 8 && na * 2 * L <= TT) L *= 2;
-            const int l = tid & (L - 1);
-            for (int g0 = 0; g0 < na; g0 += TT / L) {
-                const int my = g0 + tid / L;
-                const bool valid = my < na;
-                const int a = cc.first + (valid ? my : 0);
-                const double xa = y[a], ya = y[P + a];
-                const float2 fa = A.fpos[a];
-                const float fax = fa.x, fay = fa.y;
-                CSum Gx = {0.f, 0.f}, Gy = {0.f, 0.f}, Hx = {0.f, 0.f}, Hy = {0.f, 0.f};
-                CSum xx = {0.f, 0.f}, xy = {0.f, 0.f}, yx = {0.f, 0.f}, yy = {0.f, 0.f};
-                for (int t0 = 0; t0 < cc.M; t0 += kTile) {
-                    const int mt = min(kTile, cc.M - t0);
-                    __syncthreads();
+        if (na == 0) continue;
+        const EvView &V = A.segv[cc.s];
+        const float ih = (float)V.inv_h;
+        const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
+        const double supp2 = V.supp2;
+        const int L = lanes_per_particle(na), ppw = 32 / L;
+        const int pl = lane / L, l = lane - pl * L;
+        const int M = cc.M;
+        for (int g0 = 0; g0 < na; g0 += NW * ppw) {
+            const int my = g0 + warp * ppw + pl;
+            const bool valid = pl < ppw && my < na;
+            const int a = cc.first + (valid ? my : 0);
+            const double xa = y[a], ya = y[P + a];
+            const float2 fa = A.fpos[a];
+            CSum Gx = {0.f, 0.f}, Gy = {0.f, 0.f}, Hx = {0.f, 0.f}, Hy = {0.f, 0.f};
+            CSum xx = {0.f, 0.f}, xy = {0.f, 0.f}, yx = {0.f, 0.f}, yy = {0.f, 0.f};
+            for (int t0 = 0; t0 < M; t0 += kTile) {
+                const int mt = min(kTile, M - t0);
+                if (g0 == 0 || M > kTile) {  // one tile serves every pass of the cell
+                    if (t0 > 0 || g0 > 0) __syncthreads();
                     for (int i = tid; i < mt; i += TT) {
                         float2 rel;
                         const int b = cand_index(cc, t0 + i, A.fpos, rel);
                         cpos[i] = rel;
                         cX[i] = A.fX[b];
                         cU[i] = A.fU[b];
-                        cidx[i] = b;
                     }
                     __syncthreads();
-                    if (valid) {
-                        for (int jb = l; jb < mt; jb += kRun * L) {
-                            const int je = min(mt, jb + kRun * L);
-                            float pGx = 0.f, pGy = 0.f, pHx = 0.f, pHy = 0.f;
-                            float pxx = 0.f, pxy = 0.f, pyx = 0.f, pyy = 0.f;
-                            for (int j = jb; j < je; j += L) {
-                                const float2 pb = cpos[j];
-                                const float dx = fax - pb.x, dy = fay - pb.y;
-                                const float r2 = fmaf(dx, dx, dy * dy);
-                                if (r2 <= shi && r2 > 0.0f) {
-                                    bool acc = r2 < slo;
-                                    if (!acc) {
-                                        const int b = cidx[j];
-                                        acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
-                                    }
-                                    if (acc) {
-                                        const float ir = rsqrtf(r2);
-                                        const float fac = kernel_dwf(r2 * ir * ih) * ir;
-                                        const float gx = fac * dx, gy = fac * dy;
-                                        const float4 X = cX[j];
-                                        const float2 U = cU[j];
-                                        pGx += gx;
-                                        pGy += gy;
-                                        pHx = fmaf(X.x, gx, fmaf(X.z, gy, pHx));
-                                        pHy = fmaf(X.y, gx, fmaf(X.w, gy, pHy));
-                                        pxx = fmaf(U.x, gx, pxx);
-                                        pxy = fmaf(U.y, gx, pxy);
-                                        pyx = fmaf(U.x, gy, pyx);
-                                        pyy = fmaf(U.y, gy, pyy);
-                                    }
-                                }
+                }
+                if (valid) {
+                    for (int jb = l; jb < mt; jb += kRun * L) {
+                        const int je = min(mt, jb + kRun * L);
+                        float pGx = 0.f, pGy = 0.f, pHx = 0.f, pHy = 0.f;
+                        float pxx = 0.f, pxy = 0.f, pyx = 0.f, pyy = 0.f;
+#pragma unroll 4
+                        for (int j = jb; j < je; j += L) {
+                            const float2 pb = cpos[j];
+                            const float dx = fa.x - pb.x, dy = fa.y - pb.y;
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            bool acc = r2 < slo;
+                            if (r2 >= slo && r2 <= shi) {  // thin shell: the exact FP64 decision
+                                const int b = cand_arena(cc, t0 + j);
+                                acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
                             }
-                            cadd(Gx, pGx);
-                            cadd(Gy, pGy);
-                            cadd(Hx, pHx);
-                            cadd(Hy, pHy);
-                            cadd(xx, pxx);
-                            cadd(xy, pxy);
-                            cadd(yx, pyx);
-                            cadd(yy, pyy);
+                            // r = 0 (the particle itself) gives dw/dq = 0: a zero term
+                            const float ir = rsqrtf(fmaxf(r2, 1e-30f));
+                            float t2, t, u2, u;
+                            spline_terms(r2 * ir * ih, t2, t, u2, u);
+                            const float fac = acc ? fmaf(-0.75f, t2, 3.0f * u2) * ir : 0.0f;
+                            const float gx = fac * dx, gy = fac * dy;
+                            const float4 X = cX[j];
+                            const float2 U = cU[j];
+                            pGx += gx;
+                            pGy += gy;
+                            pHx = fmaf(X.x, gx, fmaf(X.z, gy, pHx));
+                            pHy = fmaf(X.y, gx, fmaf(X.w, gy, pHy));
+                            pxx = fmaf(U.x, gx, pxx);
+                            pxy = fmaf(U.y, gx, pxy);
+                            pyx = fmaf(U.x, gy, pyx);
+                            pyy = fmaf(U.y, gy, pyy);
                         }
+                        cadd(Gx, pGx);
+                        cadd(Gy, pGy);
+                        cadd(Hx, pHx);
+                        cadd(Hy, pHy);
+                        cadd(xx, pxx);
+                        cadd(xy, pxy);
+                        cadd(yx, pyx);
+                        cadd(yy, pyy);
                     }
                 }
-                double tGx = cval(Gx), tGy = cval(Gy), tHx = cval(Hx), tHy = cval(Hy);
-                double t00 = cval(xx), t01 = cval(xy), t10 = cval(yx), t11 = cval(yy);
-                for (int o = 1; o < L; o <<= 1) {
-                    tGx += __shfl_xor_sync(0xFFFFFFFFu, tGx, o);
-                    tGy += __shfl_xor_sync(0xFFFFFFFFu, tGy, o);
-                    tHx += __shfl_xor_sync(0xFFFFFFFFu, tHx, o);
-                    tHy += __shfl_xor_sync(0xFFFFFFFFu, tHy, o);
-                    t00 += __shfl_xor_sync(0xFFFFFFFFu, t00, o);
-                    t01 += __shfl_xor_sync(0xFFFFFFFFu, t01, o);
-                    t10 += __shfl_xor_sync(0xFFFFFFFFu, t10, o);
-                    t11 += __shfl_xor_sync(0xFFFFFFFFu, t11, o);
-                }
-                if (valid && l == 0) {
-                    const double tau = A.sc[cc.s].tau + (stage == 2 ? V.dtau : 0.0);
-                    const double sqrtg = V.milne ? tau : 1.0;
-                    const double cf = V.sigma_d * V.inv_h;
-                    double *go = A.gout;
-                    go[a] = cf * t00;
-                    go[P + a] = cf * t01;
-                    go[2 * P + a] = cf * t10;
-                    go[3 * P + a] = cf * t11;
-                    const double Fx = gin[a] * tGx + gin[2 * P + a] * tGy + tHx;
-                    const double Fy = gin[P + a] * tGx + gin[3 * P + a] * tGy + tHy;
-                    go[4 * P + a] = -sqrtg * cf * Fx;
-                    go[5 * P + a] = -sqrtg * cf * Fy;
-                }
+            }
+            const double tGx = seg_sum(cval(Gx), l, L), tGy = seg_sum(cval(Gy), l, L);
+            const double tHx = seg_sum(cval(Hx), l, L), tHy = seg_sum(cval(Hy), l, L);
+            const double t00 = seg_sum(cval(xx), l, L), t01 = seg_sum(cval(xy), l, L);
+            const double t10 = seg_sum(cval(yx), l, L), t11 = seg_sum(cval(yy), l, L);
+            if (valid && l == 0) {
+                const double tau = A.sc[cc.s].tau + (stage == 2 ? V.dtau : 0.0);
+                const double sqrtg = V.milne ? tau : 1.0;
+                const double cf = V.sigma_d * V.inv_h;
+                double *go = A.gout;
+                go[a] = cf * t00;
+                go[P + a] = cf * t01;
+                go[2 * P + a] = cf * t10;
+                go[3 * P + a] = cf * t11;
+                const double Fx = gin[a] * tGx + gin[2 * P + a] * tGy + tHx;
+                const double Fy = gin[P + a] * tGx + gin[3 * P + a] * tGy + tHy;
+                go[4 * P + a] = -sqrtg * cf * Fx;
+                go[5 * P + a] = -sqrtg * cf * Fy;
             }
         }
-        __syncthreads();
     }
 }
 
-// launch shapes of the tiled passes the autotuner chooses among (threads per block)
+// launch shapes of the tiled passes the autotuner chooses among (threads per block; the
+// results do not depend on the choice)
 constexpr int kTTChoices[] = {64, 96, 128, 192, 256};
 
 template <int TT>

@@ -511,16 +511,17 @@ __device__ __forceinline__ bool seg_active(const BatchTable *t, int s, int stage
     return m == SLOT_STEP || (m == SLOT_OBSERVE && stage == 1 && !rates);
 }
 
-// Shell of the cell-tiled mixed-form decision.  Coordinates are taken relative to the
-// origin of the centre cell in FP64 and rounded to float: |x_a - o| <= 2h, |x_b - o| <= 4h,
-// so each carries an error <= 4h u (u = 2^-24) and the float separation of a pair with
-// |dx_d| <= 2h errs by e <= 8h u = 4 (2h) u per axis (the subtraction included; candidates
-// up to 3 cells away err by at most 6 (2h) u).  The float r^2 (fmaf) then errs by at most
-// 4 (2h) e + 2 e^2 + 3 u (2h)^2 <= 27 (2h)^2 u near r = 2h, and the margin r^2 - (2h)^2
-// grows faster than the error beyond it.  The shell is +-64 (2h)^2 u: outside it the float
-// decision equals the exact one.  A grid clamped at kMaxCellsAxis cells puts far particles
-// into its edge cells, where the bound does not hold; such cells use the FP64 test for
-// every candidate.
+// Shell of the cell-tiled mixed-form decision (cells of side h, a 5x5 search block).  A
+// particle's position relative to its own cell's origin, in [0, h) per axis, is rounded to
+// float (error <= h u, u = 2^-24); a candidate k cells away (|k| <= 2) adds k times the
+// float cell side (error <= 2h u) in one float addition (result <= 3h: error <= 3h u).  So
+// x_a carries <= h u, x_b <= 6h u, and the float separation of a pair with |dx_d| <= 2h errs
+// by e <= 9h u = 4.5 (2h) u per axis (the subtraction included).  The float r^2 (fmaf) then
+// errs by at most 4 (2h) e + 2 e^2 + 3 u (2h)^2 <= 22 (2h)^2 u near r = 2h, and the margin
+// r^2 - (2h)^2 grows faster than the error beyond it.  The shell is +-64 (2h)^2 u: outside it
+// the float decision equals the exact one.  A grid clamped at kMaxCellsAxis cells puts far
+// particles into its edge cells, where the bound does not hold; such cells use the FP64 test
+// for every candidate.
 inline void tiled_shell(double h, float &lo, float &hi)
 {
     const double u = 1.0 / 16777216.0;
