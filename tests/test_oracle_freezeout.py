@@ -7,7 +7,14 @@
 * Every element is consistent with its definition: |n_mu n^mu| = 1, sigma |u.n| |dsigma| = 1,
   dsigma_mu = |dsigma| n_mu, each particle crosses once while cooling, and T at the element lies
   just below T_FO (the step's end).
+* In 3+1D Milne coordinates the isotherms of the Gubser flow shifted in Minkowski time (Sec.
+  "Code validation", eqs. tau_prime and shifted_viscous_Gubser_T with H0 = 0) depend on eta_s and
+  the flow has a u^eta component: the four-component normals (the eta derivative by the SPH sum
+  over Euclidean (x, y, eta) distances, advection along u^eta) follow the closed-form -d_mu T and
+  converge under refinement; |n_mu n^mu| = 1 holds with g^{eta eta} = -1/tau^2.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -91,3 +98,94 @@ def test_dsigma_is_inverse_sigma_u_dot_n():
     un = np.sum(recs[:, 4:8] * recs[:, 15:19], axis=1)
     prod = np.array([recs[j, 19] * sig_at[j] * abs(un[j]) for j in range(len(ids))])
     assert np.allclose(prod, 1.0, rtol=1e-12, atol=0)
+
+
+# shifted Gubser flow (t0 = 0.5 fm, the paper's value): T falls from 0.253 GeV (tau = 1 fm, r = 0,
+# eta = 0) to 0.233 GeV at tau = 1.1 fm, so the isotherm at 0.245 GeV sweeps through the box
+T_FO3 = 0.245 / I.HBARC
+E_FO3 = I.GUBSER_FSTAR * T_FO3 ** 4
+T0_SHIFT = 0.5
+
+
+@functools.lru_cache(maxsize=None)
+def _surface3(half_widths, spacings, h, dtau, nsteps, t0=T0_SHIFT, e_fo=E_FO3):
+    ev = I.gubser_shifted_3p1(half_widths=half_widths, spacings=spacings, h=h, t0=t0, dtau=dtau,
+                              nsteps=nsteps)
+    run = O.OracleRun.start(ev)
+    recs, ids = run.evolve_freezeout(nsteps, e_fo)
+    return ev, recs, ids
+
+
+def _directions3(recs, half_widths, h, t0=T0_SHIFT):
+    """Euclidean-normalised (tau, x, y, eta) directions of the SPH normal and of the closed-form
+    -d_mu T, for elements at least 2h inside the lattice (the edges lack neighbours)."""
+    tau, x, y, eta = recs[:, 0], recs[:, 1], recs[:, 2], recs[:, 3]
+    d = 1e-6
+
+    def T(t, xx, yy, ee):
+        return I.gubser_shifted_T_u(t, xx, yy, ee, t0=t0)[0]
+
+    N = -np.stack([(T(tau + d, x, y, eta) - T(tau - d, x, y, eta)) / (2 * d),
+                   (T(tau, x + d, y, eta) - T(tau, x - d, y, eta)) / (2 * d),
+                   (T(tau, x, y + d, eta) - T(tau, x, y - d, eta)) / (2 * d),
+                   (T(tau, x, y, eta + d) - T(tau, x, y, eta - d)) / (2 * d)])
+    Ne = N / np.linalg.norm(N, axis=0)
+    S = recs[:, 15:19].T
+    Se = S / np.linalg.norm(S, axis=0)
+    inner = (np.abs(x) <= half_widths[0] - 2 * h) & (np.abs(y) <= half_widths[1] - 2 * h) & \
+        (np.abs(eta) <= half_widths[2] - 2 * h)
+    return Se[:, inner], Ne[:, inner]
+
+
+def _direction_error3(recs, half_widths, h):
+    Se, Ne = _directions3(recs, half_widths, h)
+    return np.linalg.norm(Se - Ne, axis=0), np.sign(Se[0]) == np.sign(Ne[0]), np.abs(Ne[3])
+
+
+COARSE3 = ((2.4, 2.4, 1.5), (0.2, 0.2, 0.1), 0.4, 0.01, 10)
+FINE3 = ((1.6, 1.6, 1.0), (0.1, 0.1, 0.05), 0.2, 0.005, 20)
+
+
+def test_3d_normals_follow_the_shifted_gubser_isotherm():
+    _, coarse, _ = _surface3(*COARSE3)
+    _, fine, _ = _surface3(*FINE3)
+    e1, s1, eta1 = _direction_error3(coarse, COARSE3[0], COARSE3[2])
+    e2, s2, eta2 = _direction_error3(fine, FINE3[0], FINE3[2])
+    assert len(e1) > 1000 and len(e2) > 4000
+    assert eta1.max() > 0.15 and eta2.max() > 0.15  # the eta component of the normal is exercised
+    assert s1.all() and s2.all()
+    # measured: max 0.17, mean 0.060 (coarse); max 0.043, mean 0.016 (h, spacings, dtau halved)
+    assert e1.max() < 0.25 and e1.mean() < 0.08
+    assert e2.max() < 0.07 and e2.mean() < 0.025
+    assert e2.mean() < 0.35 * e1.mean()
+
+
+def test_3d_elements_satisfy_their_definition():
+    _, recs, ids = _surface3(*COARSE3)
+    assert len(np.unique(ids)) == len(ids)
+    tau = recs[:, 0]
+    u = recs[:, 4:8]
+    n = recs[:, 15:19]
+    g = np.stack([np.ones_like(tau), -np.ones_like(tau), -np.ones_like(tau), -tau * tau])  # Milne g_mu mu
+    assert np.allclose(np.abs(np.sum(n * n / g.T, axis=1)), 1.0, rtol=0, atol=1e-12)
+    # u^mu normalised with the same metric: g_mu nu u^mu u^nu = 1
+    assert np.allclose(np.sum(u * u * g.T, axis=1), 1.0, rtol=0, atol=1e-12)
+    assert np.allclose(recs[:, 20:24], recs[:, 19:20] * n, rtol=1e-14, atol=0)
+    assert np.all(recs[:, 19] > 0) and np.all(np.abs(np.sum(u * n, axis=1)) > 0)
+    assert np.abs(recs[:, 3]).max() > 0.5 and np.abs(u[:, 3]).max() > 0.05  # off the eta = 0 plane, with u^eta
+    T = recs[:, 8]
+    assert np.all(T <= T_FO3 * (1 + 1e-12)) and np.all(T > 0.98 * T_FO3)
+
+
+def test_3d_normals_with_longitudinal_flow():
+    """t0 = 2 fm: u^eta reaches 0.16 fm^-1 where d_eta T is large, so the advection of e along
+    eta enters the time component of the normal at the 10 % level (at t0 = 0.5 fm it is ~2 %).
+    Per component: time 0.0086, transverse 0.016, eta 0.029 (max errors measured); without the
+    eta advection the time and transverse errors grow to 0.022 and 0.043."""
+    t0, t_fo = 2.0, 0.09 / I.HBARC
+    _, recs, _ = _surface3((2.4, 2.4, 1.5), (0.2, 0.2, 0.1), 0.4, 0.01, 10, t0=t0,
+                           e_fo=I.GUBSER_FSTAR * t_fo ** 4)
+    Se, Ne = _directions3(recs, (2.4, 2.4, 1.5), 0.4, t0=t0)
+    assert Se.shape[1] > 300 and np.abs(Ne[3]).max() > 0.3
+    err = np.abs(Se - Ne).max(axis=1)
+    assert err[0] < 0.013 and max(err[1], err[2]) < 0.025 and err[3] < 0.04, err

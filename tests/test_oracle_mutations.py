@@ -70,6 +70,11 @@ MUTATIONS = [
     ("fo_dsigma_lab_density", "double dsig = 1.0 / (aux[16 * n + a] * fabs(un));",
      "double dsig = 1.0 / (aux[0 * n + a] * fabs(un));",
      "test_oracle_freezeout.py::test_dsigma_is_inverse_sigma_u_dot_n"),
+    ("fo_drop_eta_advection", "for (int i = 0; i < dim; ++i) adv += (u[1 + i] / u[0]) * de[i];",
+     "for (int i = 0; i < 2; ++i) adv += (u[1 + i] / u[0]) * de[i];",
+     "test_oracle_freezeout.py::test_3d_normals_with_longitudinal_flow"),
+    ("fo_norm_covariant_metric", "NN += N[mu] * N[mu] / G.g[mu];", "NN += N[mu] * N[mu] * G.g[mu];",
+     "test_oracle_freezeout.py::test_3d_elements_satisfy_their_definition"),
     ("src_drop_momentum", "for (int i = 0; i < dim; ++i) F[1 + i] += G.sqrtg * I[1 + i] / aux[0 * n + a];", "",
      "test_oracle_sources.py::test_track_deposits_its_energy_and_momentum"),
     ("src_drop_heat", "for (int mu = 0; mu < 4; ++mu) q.uI += G.g[mu] * q.u[mu] * I[mu];", "",
