@@ -46,8 +46,9 @@ FLOPS_EOS = (352.0, 64.0, 26.0)
 # FP64 vector peak of GB300 (nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock)
 FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes (read + write) per launch of the FP64 40k-event kernels, from one ncu capture of
-# the current kernels (profiles/ncu_fp64_kernels_viscous_bsq_40k.md); None once a kernel changes
-DRAM_BYTES_PER_LAUNCH = {"gradient": None, "density": None, "eos": 7.291e6, "eom": 13.04e6}
+# the current kernels (profiles/ncu_fp64_kernels_viscous_bsq_40k.md; "density" is the forward
+# plus the backward pair pass: 6.85 + 130.7 + 104.6 + 14.59 MB); None once a kernel changes
+DRAM_BYTES_PER_LAUNCH = {"gradient": 180.3e6, "density": 256.7e6, "eos": 7.33e6, "eom": None}
 
 
 def dist_env():
@@ -443,12 +444,22 @@ def bench_3p1d(Bd, I, steps: int = 3):
     the plain FP64 form next to the mixed form (FP32 neighbour sums, FP64 EoS and equations of
     motion), CUDA events on the event's stream after one untimed step."""
     import torch
+    import numpy as np
     ev = I.viscous_bsq_3p1()
     out = {"workload": f"3+1D Milne viscous BSQ event, {ev.n} particles, dx = dy = 0.124 fm, d_eta = 0.1, "
                        f"h = 0.3 fm, dtau = 0.005 fm, 64x32^3 EoS table", "steps": steps}
-    for name, prec in (("fp64", Bd.SPH_FP64), ("mixed", Bd.SPH_MIXED)):
+    e_fo = None
+    for name, prec in (("fp64", Bd.SPH_FP64), ("mixed", Bd.SPH_MIXED), ("fp64_freezeout", Bd.SPH_FP64)):
         st = torch.cuda.Stream()
         g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream, precision=prec)
+        if name == "fp64":  # a freeze-out surface at the 20 % quantile of the initial e (cooling edge)
+            se = np.sort(g.read(("E",))["E"])
+            k = int(0.2 * len(se))
+            while se[k + 1] - se[k] < 1e-6 * se[k]:
+                k += 1
+            e_fo = 0.5 * float(se[k] + se[k + 1])
+        if name == "fp64_freezeout":
+            g.freezeout_setup(e_fo, 400000)
         g.step(1, sync=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(st):
@@ -460,8 +471,12 @@ def bench_3p1d(Bd, I, steps: int = 3):
         out[name] = {"ms_per_step": ms, "particle_steps_per_s": ev.n / (ms / 1e3)}
         if prec == Bd.SPH_MIXED:
             out[name]["shell_tests"] = g.totals()["shell_tests"]
+        if name == "fp64_freezeout":
+            out[name]["e_fo"] = e_fo
+            out[name]["elements"] = int(len(g.read_freezeout()[1]))
         g.free()
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["freezeout_overhead"] = out["fp64_freezeout"]["ms_per_step"] / out["fp64"]["ms_per_step"] - 1.0
     return out
 
 

@@ -316,20 +316,22 @@ sph_status sph_set_viscous_eom(sph_event *ev, int32_t model, const double *coeff
 sph_status sph_set_jets(sph_event *ev, int64_t ntrack, const double *tracks, double sigma);
 
 /* ---------------------------------------------------------------------------
- * Freeze-out hypersurface (Sec. "Freeze-out hypersurface construction"), dim = 2.
+ * Freeze-out hypersurface (Sec. "Freeze-out hypersurface construction"), dim = 2 or 3.
  * After sph_freezeout_setup, the first stage of every step finds the particles whose energy
  * density fell through e_fo since the previous step's first stage and records one surface
  * element each, evaluated at the current state (the end of the step in which it crossed):
- *   n_mu = N_mu / sqrt(|N_mu N^mu|), N_mu = -d_mu e (covariant, pointing outwards), with the
+ *   n_mu = N_mu / sqrt(|N_mu N^mu|), N_mu = -d_mu e (covariant, pointing outwards; in 3+1D
+ *   Milne coordinates N_mu N^mu = N_0^2 - N_x^2 - N_y^2 - N_eta^2/tau^2), with the
  *   spatial derivatives by the SPH sum d_i e_a = sum_b (e_b/sigma*_b) d_i W_ab and
  *   d_tau e = (e - e_prev)/dtau - v^i d_i e (the particle's rate minus advection);
  *   |dsigma| = m/(sigma |u^mu n_mu|) with unit SPH mass and the rest-frame density sigma;
  *   dsigma_mu = |dsigma| n_mu.
  * A record holds SPH_FO_NREC doubles: tau, x^1..3, u^0..3, T, mu_B, mu_S, mu_Q, e, p, s,
- * n_0..3, |dsigma|, dsigma_0..3 (entries of the third spatial axis are 0 in 2+1D).  The
+ * n_0..3, |dsigma|, dsigma_0..3 (entries of the third spatial axis are 0 in 2+1D; in 3+1D Milne
+ * coordinates x^3 = eta_s, u^3 = u^eta, n_3 = n_eta).  The
  * crossings of the step that ends at tau are found by the next step's first stage.
  * Setup (again) clears the recorded elements; the first step after it only records e.
- * Errors: SPH_ERR_ARG (dim != 2, e_fo <= 0, capacity < 1), SPH_ERR_OOM. */
+ * Errors: SPH_ERR_ARG (e_fo <= 0, capacity < 1), SPH_ERR_OOM. */
 #define SPH_FO_NREC 24
 sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity);
 /* Elements recorded so far, sorted by (tau, particle id): min(count, capacity, cap) records to

@@ -226,7 +226,7 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_EOS, 1, 0);
     launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
     if (ev->fo_on)
-        launch_freezeout2(v, ev->e_fo, ev->Y[1], ev->id[1], ev->dens, ev->eosf, ev->eprev[1], ev->cb, ev->fo, st);
+        launch_freezeout(v, ev->e_fo, ev->Y[1], ev->id[1], ev->dens, ev->eosf, ev->eprev[1], ev->cb, ev->fo, st);
     mark(ev, G_EOS, 1, 1);
     mark(ev, G_GRADIENT, 1, 0);
     launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
@@ -1174,7 +1174,6 @@ sph_status sph_set_viscous_eom(sph_event *ev, int32_t model, const double *coeff
 sph_status sph_freezeout_setup(sph_event *ev, double e_fo, int64_t capacity)
 {
     if (!ev) return fail(SPH_ERR_ARG, "null event");
-    if (ev->dim != 2) return fail(SPH_ERR_ARG, "the freeze-out surface is implemented for dim = 2");
     if (!(e_fo > 0.0) || capacity < 1) return fail(SPH_ERR_ARG, "e_fo > 0 and capacity >= 1 required");
     {
         sph_status ws = wait_stream(ev);  // bounded: the buffers below may be in use

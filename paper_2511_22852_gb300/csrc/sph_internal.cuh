@@ -554,8 +554,8 @@ struct FoBuf {
     unsigned long long *count;
     unsigned long long cap;
 };
-void launch_freezeout2(const EvView &v, double e_fo, const double *y, const int *id, const double *dens,
-                       const double *eosf, double *eprev, CellBufs cb, FoBuf fo, cudaStream_t st);
+void launch_freezeout(const EvView &v, double e_fo, const double *y, const int *id, const double *dens,
+                      const double *eosf, double *eprev, CellBufs cb, FoBuf fo, cudaStream_t st);
 
 // sets the message returned by sph_last_error() for the calling thread
 void set_last_error(const char *msg);

@@ -601,6 +601,44 @@ def test_freezeout_surface_matches_oracle(Bd, case):
     g.free()
 
 
+def _gap_e_fo(e0, quantile=0.6):
+    """A surface value in the middle of a clear gap between particles' initial values, so that no
+    particle sits within rounding of it."""
+    se = np.sort(e0)
+    k = int(quantile * len(se))
+    while se[k + 1] - se[k] < 1e-6 * se[k]:
+        k += 1
+    return 0.5 * float(se[k] + se[k + 1])
+
+
+@pytest.mark.parametrize("case", ["gubser_shifted3", "blob3_milne", "blob3_cart"])
+def test_freezeout_surface_3d_matches_oracle(Bd, case):
+    """3+1D freeze-out elements (Milne: eta_s and u^eta components, n_eta normalised with
+    g^{eta eta} = -1/tau^2; Cartesian): the same particles cross in the same steps, with the
+    oracle's four-component normals and element sizes."""
+    ev = CASES3[case]()
+    run = O.OracleRun.start(ev)
+    aux0, _ = run.observe()
+    e_fo = _gap_e_fo(aux0[O.AUX["e"]])
+    nsteps = 20
+    orecs, oids = run.evolve_freezeout(nsteps, e_fo)
+    assert len(oids) > 100
+    g = Bd.GpuEvent(ev)
+    g.freezeout_setup(e_fo, 100000)
+    g.step(nsteps + 1, sync=True)  # crossings of step k are found by step k + 1's first stage
+    recs, ids = g.read_freezeout()
+    g.free()
+    assert np.array_equal(ids, oids)
+    for c in range(0, 15):  # tau, x^1..3, u^0..3, T, mu, e, p, s
+        assert relerr(recs[:, c], orecs[:, c]) < TOL_STEP, c
+    assert np.abs(orecs[:, 3]).max() > 0 and np.abs(orecs[:, 7]).max() > 0  # third axis exercised
+    N = recs[:, 15:19] / np.linalg.norm(recs[:, 15:19], axis=1)[:, None]
+    ON = orecs[:, 15:19] / np.linalg.norm(orecs[:, 15:19], axis=1)[:, None]
+    assert np.max(np.abs(N - ON)) < 1e-9
+    assert relerr(recs[:, 19], orecs[:, 19]) < 1e-8
+    assert relerr(recs[:, 20:24], orecs[:, 20:24]) < 1e-8
+
+
 def test_stress_event_fp64_and_mixed(Bd):
     """The stress configuration at full size (about 8 10^6 particles, Cartesian 3+1D, 10 jet
     tracks, 128 x 64^3 table), one Heun step in each form: the same neighbour counts, T and u
