@@ -53,38 +53,62 @@ __global__ void k_cells(EvView v, const double *__restrict__ y, uint32_t *key, u
     atomicAdd(&cnt[k], 1u);
 }
 
-// exclusive scan of nb counts with one block of 1024 threads
+// exclusive scan of nb counts with one block of 1024 threads, in tiles of 4096 buckets: thread t
+// takes buckets 4t .. 4t + 3 of a tile (one 16-byte load and store when the arrays are 16-byte
+// aligned), a warp-shuffle scan of the thread sums, and a carry from tile to tile
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ cnt, uint32_t *start, uint32_t *cursor, int nb)
 {
     __shared__ uint32_t warp_tot[32];
-    int t = threadIdx.x;
-    int per = (nb + blockDim.x - 1) / blockDim.x;
-    int b0 = min(t * per, nb), b1 = min(b0 + per, nb);
-    uint32_t local = 0;
-    for (int b = b0; b < b1; ++b) local += cnt[b];
-    // block-wide exclusive scan of the per-thread totals
-    uint32_t incl = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t up = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if ((t & 31) >= o) incl += up;
-    }
-    if ((t & 31) == 31) warp_tot[t >> 5] = incl;
-    __syncthreads();
-    if (t < 32) {
-        uint32_t w = warp_tot[t];
-        uint32_t wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t up = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (t >= o) wi += up;
+    __shared__ uint32_t tile_tot;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const bool vec = ((reinterpret_cast<uintptr_t>(cnt) | reinterpret_cast<uintptr_t>(start) |
+                       reinterpret_cast<uintptr_t>(cursor)) & 15u) == 0;
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += 4096) {
+        const int i0 = base + 4 * t;
+        uint32_t v[4];
+        if (vec && i0 + 3 < nb) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(cnt + i0);
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = i0 + k < nb ? cnt[i0 + k] : 0u;
         }
-        warp_tot[t] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = warp_tot[t >> 5] + incl - local;
-    for (int b = b0; b < b1; ++b) {
-        start[b] = run;
-        cursor[b] = run;
-        run += cnt[b];
+        const uint32_t local = v[0] + v[1] + v[2] + v[3];
+        uint32_t incl = local;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t up = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += up;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (t < 32) {
+            const uint32_t w = warp_tot[t];
+            uint32_t wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t up = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (t >= o) wi += up;
+            }
+            warp_tot[t] = wi - w;
+            if (t == 31) tile_tot = wi;
+        }
+        __syncthreads();
+        uint32_t r[4];
+        r[0] = carry + warp_tot[wid] + incl - local;
+        r[1] = r[0] + v[0];
+        r[2] = r[1] + v[1];
+        r[3] = r[2] + v[2];
+        if (vec && i0 + 3 < nb) {
+            const uint4 q = make_uint4(r[0], r[1], r[2], r[3]);
+            *reinterpret_cast<uint4 *>(start + i0) = q;
+            *reinterpret_cast<uint4 *>(cursor + i0) = q;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (i0 + k < nb) start[i0 + k] = cursor[i0 + k] = r[k];
+        }
+        carry += tile_tot;
+        __syncthreads();  // warp_tot and tile_tot are rewritten by the next tile
     }
 }
 

@@ -190,14 +190,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_pairs_density_fwd(EvView v, con
         if (acc) {
             const double r2 = fma(dx, dx, dy * dy);
             double w = kernel_w(0.0), fac = 0.0;  // coincident particles: W(0), no gradient
-            if (r2 > 0.0) {
+            if (nonzero_nonneg(r2)) {
                 // the cubic spline without a branch on q: w = (2-q)^3/4 - max(1-q, 0)^3,
                 // w' = -3/4 (2-q)^2 + 3 max(1-q, 0)^2 (the same polynomials on both pieces)
+                // (the sign tests and the factor 1/4 on the integer pipe: t^2 is 0 or >= 2^-104)
                 const double ir = inv_sqrt(r2);
                 const double qq = r2 * ir * v.inv_h;
-                const double t = 2.0 - qq, u = fmax(1.0 - qq, 0.0);
+                const double t = 2.0 - qq, u = pos_part(1.0 - qq);
                 const double t2 = t * t, u2 = u * u;
-                w = fma(0.25 * t2, t, -(u2 * u));
+                w = fma(quarter_nonneg(t2), t, -(u2 * u));
                 fac = fma(-0.75, t2, 3.0 * u2) * ir;
             }
             const int slot = nf + __popc(m & lt);

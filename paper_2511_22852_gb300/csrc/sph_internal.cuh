@@ -191,6 +191,21 @@ __device__ __forceinline__ uint32_t key3(const EvView &v, int cx, int cy, int cz
 // 1/sqrt(x) for x > 0 in double precision: CUDA's rsqrt (at most 1 ulp of error)
 __device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
 
+// Exact bit-level helpers that keep work off the FP64 pipe (1/64 of the FP32 rate on GB300):
+// x != 0 for x >= 0 (true when any bit is set; +0 is all zero bits)
+__device__ __forceinline__ bool nonzero_nonneg(double x) { return __double_as_longlong(x) != 0LL; }
+// max(x, 0) for finite x, from the sign bit
+__device__ __forceinline__ double pos_part(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(b & ~(b >> 63));
+}
+// x / 4 for x = 0 or x >= 2^-1020, by lowering the exponent field by 2 (exact)
+__device__ __forceinline__ double quarter_nonneg(double x)
+{
+    return __hiloint2double(max(__double2hiint(x) - 0x00200000, 0), __double2loint(x));
+}
+
 // Warp sum of up to 8 per-lane values by recursive halving (a reduce-scatter): at each of the
 // first three levels a lane keeps half of its values and adds its partner's copy of them, then
 // two butterfly levels finish one value.  9 additions per lane instead of 5 per value for a full
