@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(32 * kWarpsM) k_density2m(EvView v, const doub
     unsigned shell = 0;
     auto pair = [&](int b, float2 d) {
         const float r2 = fmaf(d.x, d.x, d.y * d.y);
-        const float q = r2 > 0.0f ? r2 * rsqrtf(r2) * ih : 0.0f;
+        const float q = sqrt_apx(r2) * ih;
         const float w = kernel_wf(q);
         cadd(sg, w);
         cadd(ss, (float)S[b] * w);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(32 * kWarpsM) k_gradient2m(EvView v, int stage
     auto pair = [&](int b, float2 d) {
         const float r2 = fmaf(d.x, d.x, d.y * d.y);
         if (r2 > 0.0f) {
-            const float ir = rsqrtf(r2);
+            const float ir = rsqrt_apx(fmaxf(r2, 1e-30f));  // a denormal r2 flushed to 0 would give inf
             const float fac = kernel_dwf(r2 * ir * ih) * ir;
             const float gx = fac * d.x, gy = fac * d.y;
             cadd(Gx, gx);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(32 * kW3) k_density3m(EvView v, const double *
     unsigned shell = 0;
     auto pair = [&](int b, float4 d, bool ok) {
         if (!ok) return;
-        const float q = d.w > 0.0f ? d.w * rsqrtf(d.w) * ih : 0.0f;
+        const float q = sqrt_apx(d.w) * ih;
         const float w = kernel_wf(q);
         pg += w;
         ps = fmaf((float)S[b], w, ps);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(32 * kW3) k_gradient3m(EvView v, int stage, co
     unsigned shell = 0;
     auto pair = [&](int b, float4 d, bool ok) {
         if (!ok || !(d.w > 0.0f)) return;
-        const float ir = rsqrtf(d.w);
+        const float ir = rsqrt_apx(fmaxf(d.w, 1e-30f));  // a denormal r2 flushed to 0 would give inf
         const float fac = kernel_dwf(d.w * ir * ih) * ir;
         const float gw[3] = {fac * d.x, fac * d.y, fac * d.z};
 #pragma unroll

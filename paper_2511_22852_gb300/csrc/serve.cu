@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
                                 acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
                                 ++shell;
                             }
-                            const float qq = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * ih;
+                            const float qq = sqrt_apx(r2) * ih;  // r = 0 (the particle itself): q = 0
                             float t2, t, u2, u;
                             spline_terms(qq, t2, t, u2, u);
                             const float w = acc ? fmaf(0.25f * t2, t, -(u2 * u)) : 0.0f;
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
                                 acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
                             }
                             // r = 0 (the particle itself) gives dw/dq = 0: a zero term
-                            const float ir = rsqrtf(fmaxf(r2, 1e-30f));
+                            const float ir = rsqrt_apx(fmaxf(r2, 1e-30f));
                             float t2, t, u2, u;
                             spline_terms(r2 * ir * ih, t2, t, u2, u);
                             const float fac = acc ? fmaf(-0.75f, t2, 3.0f * u2) * ir : 0.0f;

@@ -191,6 +191,22 @@ __device__ __forceinline__ uint32_t key3(const EvView &v, int cx, int cy, int cz
 // 1/sqrt(x) for x > 0 in double precision: CUDA's rsqrt (at most 1 ulp of error)
 __device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
 
+// Single-precision square root and reciprocal square root as the approximate PTX instructions
+// with denormal inputs flushed to zero: one MUFU operation each, relative error about 2^-22
+// (the FP32 neighbour passes, whose kernel values carry that error anyway)
+__device__ __forceinline__ float sqrt_apx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_apx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Exact bit-level helpers that keep work off the FP64 pipe (1/64 of the FP32 rate on GB300):
 // x != 0 for x >= 0 (true when any bit is set; +0 is all zero bits)
 __device__ __forceinline__ bool nonzero_nonneg(double x) { return __double_as_longlong(x) != 0LL; }
