@@ -134,37 +134,51 @@ __device__ void tab_eval_steps(const EosDev &E, const double *x, double sn[4], d
     locate(x[3], E.mu0[2], E.inv_dmu[2], E.nmu[2], iQ, tQ);
     const int n3 = E.nmu[2], n23 = E.nmu[1] * E.nmu[2], n123 = E.nmu[0] * n23;
     const size_t node0 = (size_t)iT * n123 + (size_t)iB * n23 + (size_t)iS * n3 + iQ;
+    // a node's four fields are 32 contiguous bytes: (s, n_B) and (n_S, n_Q) as two 16-byte loads
+    // (the table is a cudaMalloc allocation, 256-byte aligned)
+    const double2 *sn2 = reinterpret_cast<const double2 *>(E.sn);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {  // one field at a time: its 16 corner values
-        double lv[2], lb[2], ls[2], lq[2];  // [bT]: after the mu_B reduction
+    for (int fp = 0; fp < 2; ++fp) {  // a pair of fields at a time: their 16 corner values
+        double lv[2][2], lb[2][2], ls[2][2], lq[2][2];  // [field][bT]: after the mu_B reduction
 #pragma unroll
         for (int bT = 0; bT < 2; ++bT) {
-            double pv[2], ps[2], pq[2];  // [bB]: (mu_S, mu_Q) patch value, d/dS, d/dQ
+            double pv[2][2], ps[2][2], pq[2][2];  // [field][bB]: (mu_S, mu_Q) patch value, d/dS, d/dQ
 #pragma unroll
             for (int bB = 0; bB < 2; ++bB) {
                 const size_t base = node0 + (size_t)bT * n123 + (size_t)bB * n23;
-                const double *c = E.sn + f;
-                const double c00 = __ldg(c + 4 * base), c01 = __ldg(c + 4 * (base + 1));
-                const double c10 = __ldg(c + 4 * (base + n3)), c11 = __ldg(c + 4 * (base + n3 + 1));
-                const double d0 = c01 - c00, d1 = c11 - c10;  // along mu_Q
-                const double a0 = fma(tQ, d0, c00), a1 = fma(tQ, d1, c10);
-                const double ds = a1 - a0;  // along mu_S
-                pv[bB] = fma(tS, ds, a0);
-                ps[bB] = ds;
-                pq[bB] = fma(tS, d1 - d0, d0);
+                const double2 q00 = __ldg(sn2 + 2 * base + fp), q01 = __ldg(sn2 + 2 * (base + 1) + fp);
+                const double2 q10 = __ldg(sn2 + 2 * (base + n3) + fp), q11 = __ldg(sn2 + 2 * (base + n3 + 1) + fp);
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const double c00 = g ? q00.y : q00.x, c01 = g ? q01.y : q01.x;
+                    const double c10 = g ? q10.y : q10.x, c11 = g ? q11.y : q11.x;
+                    const double d0 = c01 - c00, d1 = c11 - c10;  // along mu_Q
+                    const double a0 = fma(tQ, d0, c00), a1 = fma(tQ, d1, c10);
+                    const double ds = a1 - a0;  // along mu_S
+                    pv[g][bB] = fma(tS, ds, a0);
+                    ps[g][bB] = ds;
+                    pq[g][bB] = fma(tS, d1 - d0, d0);
+                }
             }
-            const double db = pv[1] - pv[0];  // along mu_B
-            lv[bT] = fma(tB, db, pv[0]);
-            lb[bT] = db;
-            ls[bT] = fma(tB, ps[1] - ps[0], ps[0]);
-            lq[bT] = fma(tB, pq[1] - pq[0], pq[0]);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const double db = pv[g][1] - pv[g][0];  // along mu_B
+                lv[g][bT] = fma(tB, db, pv[g][0]);
+                lb[g][bT] = db;
+                ls[g][bT] = fma(tB, ps[g][1] - ps[g][0], ps[g][0]);
+                lq[g][bT] = fma(tB, pq[g][1] - pq[g][0], pq[g][0]);
+            }
         }
-        const double dt = lv[1] - lv[0];  // along T
-        sn[f] = fma(tT, dt, lv[0]);
-        J[f][0] = dt;
-        J[f][1] = fma(tT, lb[1] - lb[0], lb[0]);
-        J[f][2] = fma(tT, ls[1] - ls[0], ls[0]);
-        J[f][3] = fma(tT, lq[1] - lq[0], lq[0]);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int f = 2 * fp + g;
+            const double dt = lv[g][1] - lv[g][0];  // along T
+            sn[f] = fma(tT, dt, lv[g][0]);
+            J[f][0] = dt;
+            J[f][1] = fma(tT, lb[g][1] - lb[g][0], lb[g][0]);
+            J[f][2] = fma(tT, ls[g][1] - ls[g][0], ls[g][0]);
+            J[f][3] = fma(tT, lq[g][1] - lq[g][0], lq[g][0]);
+        }
     }
     if (p) {
         double lp[2];

@@ -84,3 +84,23 @@ def gubser_viscous_2p1(ode: GubserODE, n_side=51, half_width=5.0, h=0.5, tau0=1.
                    transport=I.Transport(viscous=True, eta_over_s=ode.eta_over_s, zeta_peak=0.0,
                                          tau_pi_coef=ode.C, tau_Pi_ratio=1.0),
                    meta={"dx": dx})
+
+
+def gubser_viscous_3p1(ode: GubserODE, n_side=51, half_width=5.0, eta_half=1.5, deta=0.2, h=0.5, tau0=1.0,
+                       dtau=0.01, nsteps=60):
+    """The same boost-invariant flow on a 3+1D Milne lattice: the transverse lattice of
+    gubser_viscous_2p1 repeated on eta layers |eta| <= eta_half (spacing deta), u^eta = 0, shear
+    stored as (xx, xy, x eta, yy, y eta) / sigma with the eta components zero."""
+    ev2 = gubser_viscous_2p1(ode, n_side=n_side, half_width=half_width, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps)
+    etas = deta * np.arange(-round(eta_half / deta), round(eta_half / deta) + 1)
+    m, n2 = etas.size, ev2.x.shape[1]
+    x = np.concatenate([np.stack([ev2.x[0], ev2.x[1], np.full(n2, e)]) for e in etas], axis=1)
+    u = np.concatenate([np.stack([ev2.u[0], ev2.u[1], np.zeros(n2)]) for _ in etas], axis=1)
+    # per particle 1/sigma gains the eta spacing; the stored shear is pi / sigma
+    S = np.tile(ev2.S, m) * deta
+    P2 = ev2.Pv * deta
+    z = np.zeros(n2)
+    Pv = np.tile(np.stack([P2[0], P2[1], z, P2[2], z]), (1, m))
+    return I.Event(name="gubser_viscous_3p1", dim=3, milne=True, h=h, tau0=tau0, dtau=dtau, nsteps=nsteps,
+                   x=x, u=u, S=S, Nq=np.zeros((3, n2 * m)), Bv=np.zeros(n2 * m), Pv=Pv, eos=ev2.eos, table=None,
+                   transport=ev2.transport, meta={"dx": ev2.meta["dx"], "deta": deta})

@@ -86,6 +86,9 @@ MUTATIONS = [
     ("inv_node_spacing", "double s = P->inv_p10[i / K] * (1.0 + 9.0 * (double)(i % K) / K);",
      "double s = P->inv_p10[i / K] * (1.0 + 9.5 * (double)(i % K) / K);",
      "test_oracle_offline_inverter.py::test_nodes_reproduce_the_online_inversion"),
+    ("pi3_slot_swap", "static const int PI3[5][2] = {{1, 1}, {1, 2}, {1, 3}, {2, 2}, {2, 3}};",
+     "static const int PI3[5][2] = {{1, 1}, {1, 2}, {2, 2}, {1, 3}, {2, 3}};",
+     "test_oracle_physics.py::test_viscous_gubser_in_3p1_milne"),
     ("milne_drop_gamma_eta_tau_eta", "G->G[3][0][3] = 1.0 / tau;", "G->G[3][0][3] = 0.0;",
      "test_oracle_physics.py::test_shifted_gubser_3p1_against_closed_form"),
     ("milne_du0_drop_metric_rate", "acc += 2.0 * G->g[i] * u[i] * a[i] + u[i] * u[i] * G->dg[i];",
