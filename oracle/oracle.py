@@ -64,6 +64,7 @@ class Params(C.Structure):
         ("nparton", C.c_int), ("pad5", C.c_int), ("partons", C.c_void_p),
         ("parton_norm", C.c_double), ("parton_h", C.c_double), ("parton_dt", C.c_double),
         ("backup", C.c_int), ("pad6", C.c_int), ("cd_A0", C.c_double), ("cd_mu0", C.c_double * 3),
+        ("parton_q", C.c_void_p),
     ]
 
 
@@ -91,7 +92,7 @@ def lib():
             "oc_eos_table": (None, [P, p, p, p, p]),
             "oc_eos_invert": (C.c_uint, [P, d, p, p]),
             "oc_eos_invert_ws": (C.c_uint, [P, d, p, p, p, p]),
-            "oc_stage": (i, [P, l, d, p, p, p, p, p, p, p, p, p]),
+            "oc_stage": (i, [P, l, d, p, p, p, p, p, p, p, p, p, p]),
             "oc_observe": (None, [P, l, d, p, p, p, p, p]),
             "oc_heun": (i, [P, l, p, d, i, p, p, p, p, p, p, p, p]),
             "oc_totals": (None, [P, l, d, p, p, p, p]),
@@ -178,6 +179,11 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
         keep.append(pt)
         P.nparton, P.partons = pt.shape[0], pt.ctypes.data
         P.parton_norm, P.parton_h, P.parton_dt = float(src.norm), float(src.h), float(ev.dtau)
+        if getattr(src, "charges", None) is not None:
+            qc = _f64(src.charges).reshape(-1, 3)
+            assert qc.shape[0] == pt.shape[0]
+            keep.append(qc)
+            P.parton_q = qc.ctypes.data
     return P, keep
 
 
@@ -296,7 +302,8 @@ class OracleRun:
     @classmethod
     def start(cls, ev, **kw):
         P, keep = make_params(ev, **kw)
-        return cls(ev=ev, P=P, keep=keep, y=pack_state(ev), Nq=_f64(ev.Nq), tau=float(ev.tau0),
+        # Nq is integrated in place under charge sources: the run owns a copy
+        return cls(ev=ev, P=P, keep=keep, y=pack_state(ev), Nq=_f64(ev.Nq).copy(), tau=float(ev.tau0),
                    guess=np.zeros((4, ev.n)))
 
     @property
@@ -329,8 +336,10 @@ class OracleRun:
         st = np.zeros(n, dtype=np.uint32)
         wr = C.c_double(0.0)
         gout = np.zeros((4, n))
+        dNq = np.zeros((3, n))
         lib().oc_stage(C.byref(self.P), n, float(tau), _ptr(y), _ptr(self.Nq), _ptr(dydt), _ptr(aux), _ptr(grad),
-                       _ptr(st), C.byref(wr), _ptr(self.guess), _ptr(gout))
+                       _ptr(st), C.byref(wr), _ptr(self.guess), _ptr(gout), _ptr(dNq))
+        self.last_dNq = dNq  # the charge rates (zero without charge sources)
         return dydt, aux, grad, st, wr.value
 
     def observe(self):

@@ -103,6 +103,9 @@ typedef struct {
        which inverts (s, n) in closed form; backup = 0: none (the particle has no solution) */
     int backup, pad6;
     double cd_A0, cd_mu0[3];
+    /* charges of the dynamical-initialisation partons (eq. charge_conservation with I_q != 0):
+       parton_q[3 k ..] = (B, S, Q) of parton k, smeared like its four-momentum (NULL: none) */
+    const double *parton_q;
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -877,9 +880,10 @@ static void jet_source(const oc_params *P, int dim, double t, const double *x, d
 
 /* I^mu of the partons formed in (t - dt, t], smeared with the SPH kernel of width h_src in the
    event's dimensions (distances Euclidean in the event's spatial coordinates) */
-static void parton_source(const oc_params *P, int dim, int milne, double t, const double *x, double *I)
+static void parton_source(const oc_params *P, int dim, int milne, double t, const double *x, double *I, double *Iq)
 {
     for (int mu = 0; mu < 4; ++mu) I[mu] = 0.0;
+    for (int c = 0; c < 3; ++c) Iq[c] = 0.0;
     const double sqrtg = milne ? t : 1.0;
     for (int k = 0; k < P->nparton; ++k) {
         const double *q = P->partons + 8 * k;
@@ -888,6 +892,9 @@ static void parton_source(const oc_params *P, int dim, int milne, double t, cons
         for (int d = 0; d < dim; ++d) r2 += (x[d] - q[1 + d]) * (x[d] - q[1 + d]);
         const double f = P->parton_norm * oc_W(sqrt(r2), P->parton_h, dim) / (sqrtg * P->parton_dt);
         for (int mu = 0; mu < 4; ++mu) I[mu] += f * q[4 + mu];
+        /* the charge source I_q: the parton's (B, S, Q) smeared with the same weight */
+        if (P->parton_q)
+            for (int c = 0; c < 3; ++c) Iq[c] += f * P->parton_q[3 * k + c];
     }
 }
 
@@ -1140,7 +1147,8 @@ typedef struct {
 } eosder_t;
 
 int oc_stage(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *dydt, double *aux,
-             double *grad, unsigned *status, double *work_rate, const double *guess_in, double *guess_out)
+             double *grad, unsigned *status, double *work_rate, const double *guess_in, double *guess_out,
+             double *dNq)
 {
     int dim = P->dim, np = npi_of(dim), nv = nv_of(dim);
     double two_h = 2.0 * P->h;
@@ -1275,20 +1283,29 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
             F[1 + i] = grad[(dim * dim + i) * n + a] - G.sqrtg * src / aux[0 * n + a];
         }
         /* jet and parton sources: dP^i/dx0 gains sqrt(-g) I^i / sigma*, dS/dx0 gains
-           u_nu I^nu / (u^0 sigma T) */
+           u_nu I^nu / (u^0 sigma T); parton charges: dN_q/dx0 = sqrt(-g) I_q / sigma* (the lab
+           charge of the particle's volume 1/sigma*), and dS/dx0 gains R^S_q dN_q/dx0 with
+           R^S_q = -mu_q / T (eq. dsdnrewr), i.e. -mu_q I_q / (u^0 sigma T) */
+        if (dNq)
+            for (int c = 0; c < 3; ++c) dNq[c * n + a] = 0.0;
         if (P->ntrack > 0 || P->nparton > 0) {
-            double xa[3] = {0, 0, 0}, I[4] = {0, 0, 0, 0}, Ik[4];
+            double xa[3] = {0, 0, 0}, I[4] = {0, 0, 0, 0}, Ik[4], Iq[3] = {0, 0, 0};
             for (int d = 0; d < dim; ++d) xa[d] = y[d * n + a];
             if (P->ntrack > 0) {
                 jet_source(P, dim, tau, xa, Ik);
                 for (int mu = 0; mu < 4; ++mu) I[mu] += Ik[mu];
             }
             if (P->nparton > 0) {
-                parton_source(P, dim, P->milne, tau, xa, Ik);
+                parton_source(P, dim, P->milne, tau, xa, Ik, Iq);
                 for (int mu = 0; mu < 4; ++mu) I[mu] += Ik[mu];
             }
             for (int i = 0; i < dim; ++i) F[1 + i] += G.sqrtg * I[1 + i] / aux[0 * n + a];
             for (int mu = 0; mu < 4; ++mu) q.uI += G.g[mu] * q.u[mu] * I[mu];
+            if (P->parton_q) {
+                for (int c = 0; c < 3; ++c) q.uI -= q.mu[c] * Iq[c];
+                if (dNq)
+                    for (int c = 0; c < 3; ++c) dNq[c * n + a] = G.sqrtg * Iq[c] / aux[0 * n + a];
+            }
         }
         /* M_ij = dP^i(e_j) - dP^i(0), c^i = dP^i(0); solve M a = F - c */
         double zero[4] = {0, 0, 0, 0};
@@ -1353,7 +1370,7 @@ void oc_observe(const oc_params *P, long n, double tau, const double *y, const d
 
 /* Heun: y1 = y0 + dt f(t, y0); y = ((y0 + y1) + dt f(t + dt, y1)) / 2.
    work accumulates the longitudinal work integral with the same quadrature. */
-int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, double *y, const double *Nq, double *aux,
+int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, double *y, double *Nq, double *aux,
             double *grad, unsigned *status, unsigned *status_or, double *work, double *guess)
 {
     int nv = nv_of(P->dim);
@@ -1361,15 +1378,24 @@ int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, do
     double *k = (double *)malloc(sz);
     double *y1 = (double *)malloc(sz);
     double *g1 = (double *)calloc((size_t)4 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    /* charges change only under charge sources; then they take the same Heun steps */
+    const int charged = P->parton_q != NULL && P->nparton > 0;
+    size_t szq = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
+    double *kq = charged ? (double *)malloc(szq) : NULL;
+    double *Nq1 = charged ? (double *)malloc(szq) : NULL;
     unsigned acc = 0;
     for (int step = 0; step < nsteps; ++step) {
         double wr0, wr1;
-        oc_stage(P, n, *tau, y, Nq, k, aux, grad, status, &wr0, guess, g1);
+        oc_stage(P, n, *tau, y, Nq, k, aux, grad, status, &wr0, guess, g1, kq);
         for (long a = 0; a < n; ++a) acc |= status[a];
         for (long i = 0; i < (long)nv * n; ++i) y1[i] = y[i] + dtau * k[i];
-        oc_stage(P, n, *tau + dtau, y1, Nq, k, aux, grad, status, &wr1, g1, guess);
+        if (charged)
+            for (long i = 0; i < 3 * n; ++i) Nq1[i] = Nq[i] + dtau * kq[i];
+        oc_stage(P, n, *tau + dtau, y1, charged ? Nq1 : Nq, k, aux, grad, status, &wr1, g1, guess, kq);
         for (long a = 0; a < n; ++a) acc |= status[a];
         for (long i = 0; i < (long)nv * n; ++i) y[i] = 0.5 * ((y[i] + y1[i]) + dtau * k[i]);
+        if (charged)
+            for (long i = 0; i < 3 * n; ++i) Nq[i] = 0.5 * ((Nq[i] + Nq1[i]) + dtau * kq[i]);
         *work += 0.5 * dtau * (wr0 + wr1);
         *tau = *tau + dtau;
     }
@@ -1377,6 +1403,8 @@ int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, do
     free(k);
     free(y1);
     free(g1);
+    free(kq);
+    free(Nq1);
     return 0;
 }
 

@@ -123,6 +123,9 @@ class PartonSources:
     partons: np.ndarray
     norm: float = 1.0
     h: float = 1.4
+    # [N][3] charges (B, S, Q) of the partons, smeared like their four-momenta (None: no charge
+    # sources, the particles' charges stay constant)
+    charges: np.ndarray | None = None
 
 
 @dataclass
@@ -556,3 +559,15 @@ def parton_sources(n: int, t_range, half_extent, dim: int, E_GeV=(1.0, 3.0), nor
     p = np.concatenate([E[None, :], E[None, :] * nvec])
     partons = np.concatenate([t[None, :], x, p]).T.copy()
     return PartonSources(partons=partons, norm=norm, h=h)
+
+
+# (B, S, Q) of the light quarks u, d, s and their antiquarks
+QUARK_CHARGES = np.array([[1 / 3, 0, 2 / 3], [1 / 3, 0, -1 / 3], [1 / 3, -1, -1 / 3],
+                          [-1 / 3, 0, -2 / 3], [-1 / 3, 0, 1 / 3], [-1 / 3, 1, 1 / 3]])
+
+
+def parton_quark_charges(n: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """[n][3] seeded parton charges: each parton a light quark or antiquark (uniform choice of
+    the six), its (B, S, Q) times scale."""
+    u = uniform01(seed, n)
+    return scale * QUARK_CHARGES[np.minimum((u * 6).astype(int), 5)]

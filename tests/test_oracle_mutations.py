@@ -114,6 +114,10 @@ MUTATIONS = [
     ("parton_window_open_end", "if (!(q[0] > t - P->parton_dt && q[0] <= t)) continue;",
      "if (!(q[0] > t - 2.0 * P->parton_dt && q[0] <= t)) continue;",
      "test_oracle_sources.py::test_partons_deposit_their_four_momentum"),
+    ("charge_drop_entropy_term", "for (int c = 0; c < 3; ++c) q.uI -= q.mu[c] * Iq[c];", "",
+     "test_oracle_sources.py::test_charge_deposit_changes_entropy_by_minus_mu_over_T"),
+    ("charge_rate_drop_sqrtg", "dNq[c * n + a] = G.sqrtg * Iq[c] / aux[0 * n + a];",
+     "dNq[c * n + a] = Iq[c] / aux[0 * n + a];", "test_oracle_sources.py::test_parton_charges_are_deposited"),
     ("backup_ps_factor", "out[6] = out[0] / 3.0;", "out[6] = out[0] / 4.0;",
      "test_oracle_eos.py::test_backup_eos_inverts_what_the_closed_form_cannot"),
     ("backup_mu_inversion", "out[1 + q] = cbrt(n[q] * m0 * m0 * m0 * m0 / (4.0 * A0));",
