@@ -910,6 +910,7 @@ typedef struct {
     double pi[4][4], Pv[4][4]; /* pi^{mu nu} and pi^{mu nu}/sigma */
     double eta, zeta, taupi, tauPi;
     double uI; /* u_nu I^nu: energy deposited in the local rest frame per unit time and volume */
+    double dN[3]; /* d N_q / dx0 of the particle's charges (charge sources; else 0) */
     int model;      /* viscous equations of motion (oc_params.eom_model) */
     double cs2;     /* speed of sound squared (DNMR lambda_Pipi) */
     double dnmr[6]; /* DNMR coefficient ratios (oc_params.dnmr) */
@@ -1063,7 +1064,8 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
     double ds = q->sigma * R->dS + (q->s / q->sigma) * dsig;
     double dPi = q->sigma * R->dBv + q->Bv * dsig;
     double dw = (q->T + q->ps) * ds + dPi;
-    for (int c = 0; c < 3; ++c) dw += (q->mu[c] + q->pn[c]) * (q->n[c] / q->sigma) * dsig;
+    /* dn_q = N_q dsigma + sigma dN_q with N_q = n_q / sigma (dN_q != 0 under charge sources) */
+    for (int c = 0; c < 3; ++c) dw += (q->mu[c] + q->pn[c]) * ((q->n[c] / q->sigma) * dsig + q->sigma * q->dN[c]);
     double w = q->e + q->p + q->Pi;
     for (int i = 1; i < 4; ++i) {
         double t1 = 0.0, t2 = 0.0;
@@ -1303,8 +1305,9 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
             for (int mu = 0; mu < 4; ++mu) q.uI += G.g[mu] * q.u[mu] * I[mu];
             if (P->parton_q) {
                 for (int c = 0; c < 3; ++c) q.uI -= q.mu[c] * Iq[c];
+                for (int c = 0; c < 3; ++c) q.dN[c] = G.sqrtg * Iq[c] / aux[0 * n + a];
                 if (dNq)
-                    for (int c = 0; c < 3; ++c) dNq[c * n + a] = G.sqrtg * Iq[c] / aux[0 * n + a];
+                    for (int c = 0; c < 3; ++c) dNq[c * n + a] = q.dN[c];
             }
         }
         /* M_ij = dP^i(e_j) - dP^i(0), c^i = dP^i(0); solve M a = F - c */
