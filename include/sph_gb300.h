@@ -277,11 +277,18 @@ sph_status sph_set_eos_backup(sph_event *ev, int32_t enable, double T_scale_GeV,
  *             norm p^mu_k W(|r - r_k|, h_src) / (sqrt(-g) dtau)
  * with W the cubic spline of the event's dimension and width h_src (distances Euclidean in the
  * event's coordinates); I^mu enters the equations of motion as the jet tracks' source does
- * (sph_set_jets).  Host array, copied (sorted by formation time); nparton = 0 removes the
- * sources.  Errors: SPH_ERR_ARG (nparton outside 0..2^24, null array, h_src <= 0, non-finite
- * entries); SPH_ERR_TIMEOUT if the event's stream does not drain.
+ * (sph_set_jets).  charges (may be NULL): charges[3 k ..] = (B, S, Q) of parton k, smeared with
+ * the same weight into the charge source I_q of eq. charge_conservation (the paper prints the
+ * smearing for p^mu; the charges take the same kernel).  The particles' charges then evolve,
+ * dN_q/dx0 = sqrt(-g) I_q / sigma* with the step's Heun quadrature, the entropy rate gains
+ * -mu_q/T dN_q/dx0 (eq. dsdnrewr) and the momentum equation's enthalpy rate the charges'
+ * (mu_q + dp/dn_q) sigma dN_q; without charges they stay constant.  Host arrays, copied (sorted
+ * by formation time); nparton = 0 removes the sources.  Errors: SPH_ERR_ARG (nparton outside
+ * 0..2^24, null partons, h_src <= 0, non-finite entries), SPH_ERR_OOM; SPH_ERR_TIMEOUT if the
+ * event's stream does not drain.
  * ------------------------------------------------------------------------- */
-sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons, double norm, double h_src);
+sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons, const double *charges, double norm,
+                           double h_src);
 
 /* ---------------------------------------------------------------------------
  * Viscous equations of motion (Sec. "Equations of motion": eqs. min_bul_rel, min_she_rel and

@@ -1237,8 +1237,11 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     /* equations of motion */
 #pragma omp parallel for schedule(static)
     for (long a = 0; a < n; ++a) {
+        if (dNq)
+            for (int c = 0; c < 3; ++c) dNq[c * n + a] = 0.0;
         if (status[a] & (ST_NOCONV | ST_NONFINITE)) {
-            /* no EoS solution: the particle is frozen for this stage, moving ballistically */
+            /* no EoS solution: the particle is frozen for this stage, moving ballistically
+               (its charges too stay as they are) */
             double u0 = aux[14 * n + a];
             for (int k = 0; k < nv; ++k) dydt[k * n + a] = 0.0;
             for (int i = 0; i < dim; ++i) dydt[i * n + a] = y[(dim + i) * n + a] / u0;
@@ -1288,8 +1291,6 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
            u_nu I^nu / (u^0 sigma T); parton charges: dN_q/dx0 = sqrt(-g) I_q / sigma* (the lab
            charge of the particle's volume 1/sigma*), and dS/dx0 gains R^S_q dN_q/dx0 with
            R^S_q = -mu_q / T (eq. dsdnrewr), i.e. -mu_q I_q / (u^0 sigma T) */
-        if (dNq)
-            for (int c = 0; c < 3; ++c) dNq[c * n + a] = 0.0;
         if (P->ntrack > 0 || P->nparton > 0) {
             double xa[3] = {0, 0, 0}, I[4] = {0, 0, 0, 0}, Ik[4], Iq[3] = {0, 0, 0};
             for (int d = 0; d < dim; ++d) xa[d] = y[d * n + a];

@@ -131,7 +131,7 @@ def lib():
             "sph_freezeout_setup": (i32, [vp, C.c_double, i64]),
             "sph_set_jets": (i32, [vp, i64, vp, C.c_double]),
             "sph_set_viscous_eom": (i32, [vp, i32, vp]),
-            "sph_set_partons": (i32, [vp, i64, vp, C.c_double, C.c_double]),
+            "sph_set_partons": (i32, [vp, i64, vp, vp, C.c_double, C.c_double]),
             "sph_set_eos_backup": (i32, [vp, i32, C.c_double, C.c_double]),
             "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
             "sph_eos_build_inverse": (i32, [vp, i32, i32, i32, i32, C.c_double]),
@@ -241,9 +241,13 @@ def sph_set_viscous_eom(h, model: int, coeffs=None):
     _check(lib().sph_set_viscous_eom(h, int(model), _ptr(c) if c is not None else None))
 
 
-def sph_set_partons(h, partons, norm: float, h_src: float):
+def sph_set_partons(h, partons, norm: float, h_src: float, charges=None):
     pt = _f64(partons).reshape(-1, 8) if partons is not None else np.zeros((0, 8))
-    _check(lib().sph_set_partons(h, int(pt.shape[0]), _ptr(pt) if pt.size else None, float(norm), float(h_src)))
+    qc = None if charges is None else np.ascontiguousarray(charges, dtype=np.float64).reshape(-1, 3)
+    if qc is not None and qc.shape[0] != pt.shape[0]:
+        raise ValueError("one (B, S, Q) row per parton")
+    _check(lib().sph_set_partons(h, int(pt.shape[0]), _ptr(pt) if pt.size else None,
+                                 _ptr(qc) if qc is not None and qc.size else None, float(norm), float(h_src)))
 
 
 def sph_set_eos_backup(h, enable: bool, T_scale_GeV: float = 0.165, mu_max_GeV: float = 0.45):
@@ -444,7 +448,7 @@ class GpuEvent:
             sph_set_viscous_eom(self.h, SPH_EOM_DNMR, dnmr)
         src = getattr(ev, "partons", None)
         if src is not None and len(src.partons):
-            sph_set_partons(self.h, src.partons, src.norm, src.h)
+            sph_set_partons(self.h, src.partons, src.norm, src.h, getattr(src, "charges", None))
         bk = getattr(ev, "eos_backup", None)
         if bk is not None:
             sph_set_eos_backup(self.h, True, bk[0], bk[1])

@@ -69,6 +69,11 @@ struct sph_event {
     double *d_partons = nullptr;
     long long parton_cap = 0;
     double parton_norm = 0.0, parton_h = 0.0;
+    // charge sources of the partons (sph_set_partons with charges): their (B, S, Q) in the
+    // partons' order, and the charges of the stage state (ping-pong with the sorts)
+    bool charges = false;
+    double *d_parton_q = nullptr;
+    double *NqS[2] = {nullptr, nullptr};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     DevScalars *sc = nullptr;
@@ -167,6 +172,9 @@ static EvView make_view(const sph_event *ev)
                                                      : 1.0 / (kPi * ev->parton_h * ev->parton_h * ev->parton_h))
                                      : 0.0;
     v.parton_dt = ev->dtau;
+    v.parton_q = ev->charges ? ev->d_parton_q : nullptr;
+    v.nq_cur = nullptr;  // set for the equations-of-motion launches under charge sources
+    v.nq_out = nullptr;
     v.ntrack = ev->ntrack;
     v.tracks = ev->d_tracks;
     v.track_norm = ev->track_norm;
@@ -232,7 +240,11 @@ static void enqueue_step(sph_event *ev)
     launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
     mark(ev, G_GRADIENT, 1, 1);
     mark(ev, G_EOM, 1, 0);
-    launch_eom(v, 1, 0, ev->Y[1], ev->dens, ev->eosf, ev->gout, ev->Y1[0], nullptr, ev->status, st);
+    {
+        EvView ve = v;  // under charge sources the stage-1 charges: NqS = Nq + dt dN
+        if (ev->charges) ve.nq_cur = ev->Nq[1], ve.nq_out = ev->NqS[0];
+        launch_eom(ve, 1, 0, ev->Y[1], ev->dens, ev->eosf, ev->gout, ev->Y1[0], nullptr, ev->status, st);
+    }
     mark(ev, G_EOM, 1, 1);
     mark(ev, G_WORK, 1, 0);
     launch_work_finish(v, 1, ev->wpart, ev->nwblk, st);
@@ -243,14 +255,18 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_CELLS, 2, 1);
     mark(ev, G_PERMUTE, 2, 0);
     {
-        const double *src[5] = {ev->Y1[0], ev->Y[1], ev->Nq[1], ev->wguess, ev->eprev[1]};
-        double *dst[5] = {ev->Y1[1], ev->Y[0], ev->Nq[0], ev->guess_in, ev->eprev[0]};
-        int rows[5] = {ev->nv, ev->nv, 3, 4, 1};
-        launch_permute(v, ev->cb.perm, src, dst, rows, ev->fo_on ? 5 : 4, ev->id[1], ev->id[0], st);
+        const double *src[6] = {ev->Y1[0], ev->Y[1], ev->Nq[1], ev->wguess};
+        double *dst[6] = {ev->Y1[1], ev->Y[0], ev->Nq[0], ev->guess_in};
+        int rows[6] = {ev->nv, ev->nv, 3, 4};
+        int ng = 4;
+        if (ev->charges) src[ng] = ev->NqS[0], dst[ng] = ev->NqS[1], rows[ng++] = 3;
+        if (ev->fo_on) src[ng] = ev->eprev[1], dst[ng] = ev->eprev[0], rows[ng++] = 1;
+        launch_permute(v, ev->cb.perm, src, dst, rows, ng, ev->id[1], ev->id[0], st);
     }
     mark(ev, G_PERMUTE, 2, 1);
     mark(ev, G_DENSITY, 2, 0);
-    launch_density(v, ev->Y1[1], ev->Nq[0], stage_cb(ev, 1, 0), ev->dens, ev->nnb, st);
+    // the stage state's charges: the stage-1 update under charge sources, else the constant ones
+    launch_density(v, ev->Y1[1], ev->charges ? ev->NqS[1] : ev->Nq[0], stage_cb(ev, 1, 0), ev->dens, ev->nnb, st);
     mark(ev, G_DENSITY, 2, 1);
     mark(ev, G_EOS, 2, 0);
     launch_eos(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
@@ -259,7 +275,11 @@ static void enqueue_step(sph_event *ev)
     launch_gradient(v, 2, ev->Y1[1], ev->gin, ev->cb, ev->gout, st);
     mark(ev, G_GRADIENT, 2, 1);
     mark(ev, G_EOM, 2, 0);
-    launch_eom(v, 2, 1, ev->Y1[1], ev->dens, ev->eosf, ev->gout, ev->Y[0], nullptr, ev->status, st);
+    {
+        EvView ve = v;  // under charge sources: Nq = ((Nq + NqS) + dt dN) / 2 in the stage-2 order
+        if (ev->charges) ve.nq_cur = ev->NqS[1], ve.nq_out = ev->Nq[0];
+        launch_eom(ve, 2, 1, ev->Y1[1], ev->dens, ev->eosf, ev->gout, ev->Y[0], nullptr, ev->status, st);
+    }
     mark(ev, G_EOM, 2, 1);
     mark(ev, G_WORK, 2, 0);
     launch_work_finish(v, 2, ev->wpart, ev->nwblk, st);
@@ -1094,7 +1114,8 @@ sph_status sph_set_eos_backup(sph_event *ev, int32_t enable, double T_scale_GeV,
     return SPH_OK;
 }
 
-sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons, double norm, double h_src)
+sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons, const double *charges, double norm,
+                           double h_src)
 {
     if (!ev) return fail(SPH_ERR_ARG, "null event");
     if (nparton < 0 || nparton > (1 << 24)) return fail(SPH_ERR_ARG, "nparton must be in 0..2^24");
@@ -1102,13 +1123,19 @@ sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons
         return fail(SPH_ERR_ARG, "partons, h_src > 0 and a finite norm required");
     for (int64_t k = 0; k < 8 * nparton; ++k)
         if (!std::isfinite(partons[k])) return fail(SPH_ERR_ARG, "non-finite parton entry");
+    if (charges)
+        for (int64_t k = 0; k < 3 * nparton; ++k)
+            if (!std::isfinite(charges[k])) return fail(SPH_ERR_ARG, "non-finite parton charge");
     // sorted by formation time (stable), so a stage finds its window by binary search
     std::vector<int64_t> ord((size_t)nparton);
     for (int64_t k = 0; k < nparton; ++k) ord[(size_t)k] = k;
     std::stable_sort(ord.begin(), ord.end(), [&](int64_t p, int64_t q) { return partons[8 * p] < partons[8 * q]; });
-    std::vector<double> sorted((size_t)(8 * nparton));
-    for (int64_t k = 0; k < nparton; ++k)
+    std::vector<double> sorted((size_t)(8 * nparton)), sq(charges ? (size_t)(3 * nparton) : 0);
+    for (int64_t k = 0; k < nparton; ++k) {
         for (int c = 0; c < 8; ++c) sorted[(size_t)(8 * k + c)] = partons[8 * ord[(size_t)k] + c];
+        if (charges)
+            for (int c = 0; c < 3; ++c) sq[(size_t)(3 * k + c)] = charges[3 * ord[(size_t)k] + c];
+    }
     {
         sph_status ws = wait_stream(ev);  // bounded: the buffer below may be in use
         if (ws != SPH_OK) return ws;
@@ -1117,14 +1144,28 @@ sph_status sph_set_partons(sph_event *ev, int64_t nparton, const double *partons
         sph_status s = dalloc(ev, reinterpret_cast<void **>(&ev->d_partons),
                               sizeof(double) * 8 * (size_t)(nparton > 0 ? nparton : 1));
         if (s != SPH_OK) return s;
+        s = dalloc(ev, reinterpret_cast<void **>(&ev->d_parton_q), sizeof(double) * 3 * (size_t)(nparton > 0 ? nparton : 1));
+        if (s != SPH_OK) return s;
         ev->parton_cap = nparton > 0 ? nparton : 1;
+    }
+    const bool charged = charges && nparton > 0;
+    if (charged && !ev->NqS[0]) {
+        const size_t N = (size_t)(ev->n > 0 ? ev->n : 1);
+        for (int k = 0; k < 2; ++k) {
+            sph_status s = dalloc(ev, reinterpret_cast<void **>(&ev->NqS[k]), sizeof(double) * 3 * N);
+            if (s != SPH_OK) return s;
+        }
     }
     if (nparton > 0) {
         CK(cudaMemcpyAsync(ev->d_partons, sorted.data(), sizeof(double) * sorted.size(), cudaMemcpyHostToDevice,
                            ev->stream));
+        if (charged)
+            CK(cudaMemcpyAsync(ev->d_parton_q, sq.data(), sizeof(double) * sq.size(), cudaMemcpyHostToDevice,
+                               ev->stream));
         sph_status ws = wait_stream(ev);
         if (ws != SPH_OK) return ws;
     }
+    ev->charges = charged;
     ev->nparton = (int)nparton;
     ev->parton_norm = nparton > 0 ? norm : 0.0;
     ev->parton_h = nparton > 0 ? h_src : 0.0;

@@ -183,6 +183,8 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
             else if (mode == 1) yout[k * n + a] = 0.5 * ((yout[k * n + a] + ys[k * n + a]) + dt * fk);
             else rates[k * n + a] = fk;
         }
+        const double dN0[3] = {0.0, 0.0, 0.0};  // frozen: the charges stay as they are
+        heun_charges(v, mode, n, a, dN0);
         return;
     }
 
@@ -260,27 +262,33 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
         dPxy = isg * dpxy - (pxy * isg2) * dsg;
         dPyy = isg * dpyy - (pyy * isg2) * dsg;
     }
+    double dN[3] = {0.0, 0.0, 0.0};  // charge rates dN_q/dx0 (charge sources only)
     if (v.ntrack > 0 || v.nparton > 0) {
         // jet tracks (Cartesian) and partons: dP^i/dx0 gains sqrt(-g) I^i/sigma*, dS/dx0 gains
-        // u_nu I^nu/(u^0 sigma T)
-        double I[4] = {0.0, 0.0, 0.0, 0.0}, Ik[4];
+        // u_nu I^nu/(u^0 sigma T); parton charges: dN_q/dx0 = sqrt(-g) I_q/sigma*, and dS/dx0
+        // gains -mu_q/T dN_q/dx0 (eq. dsdnrewr, R^S_q = -mu_q/T)
+        double I[4] = {0.0, 0.0, 0.0, 0.0}, Ik[4], Iq[3] = {0.0, 0.0, 0.0};
         if (v.ntrack > 0) {
             jet_deposit(v, tau, ys[a], ys[n + a], 0.0, Ik);
             for (int k = 0; k < 4; ++k) I[k] += Ik[k];
         }
         if (v.nparton > 0) {
             const double xa[3] = {ys[a], ys[n + a], 0.0};
-            parton_deposit(v, tau, sqrtg, xa, Ik);
+            parton_deposit(v, tau, sqrtg, xa, Ik, Iq);
             for (int k = 0; k < 4; ++k) I[k] += Ik[k];
         }
         Fx += sqrtg * I[1] * isig;
         Fy += sqrtg * I[2] * isig;
-        const double uI = g * I[0] - ux * I[1] - uy * I[2];  // no eta component in 2+1D
+        // no eta component in 2+1D
+        const double uI = g * I[0] - ux * I[1] - uy * I[2] - (mu0 * Iq[0] + mu1 * Iq[1] + mu2 * Iq[2]);
         dS = dS + aff((ig * isg / T) * uI);
+        for (int c = 0; c < 3; ++c) dN[c] = sqrtg * Iq[c] * isig;
     }
     Aff ds = sigma * dS + (s * isg) * dsg;
     Aff dPi = sigma * dBv + Bv * dsg;
-    Aff dw = (T + ps) * ds + (((mu0 + pn0) * nq0 + (mu1 + pn1) * nq1 + (mu2 + pn2) * nq2) * isg) * dsg + dPi;
+    // dn_q = N_q dsigma + sigma dN_q
+    Aff dw = (T + ps) * ds + (((mu0 + pn0) * nq0 + (mu1 + pn1) * nq1 + (mu2 + pn2) * nq2) * isg) * dsg + dPi +
+             aff(sigma * ((mu0 + pn0) * dN[0] + (mu1 + pn1) * dN[1] + (mu2 + pn2) * dN[2]));
     double w = e + p + Pi;
     double ig2 = ig * ig, ig3 = ig2 * ig;
     double Px0 = ux * Pvxx + uy * Pvxy, Py0 = ux * Pvxy + uy * Pvyy;
@@ -323,6 +331,7 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
     } else {
         for (int k = 0; k < nv; ++k) rates[k * n + a] = f[k];
     }
+    heun_charges(v, mode, n, a, dN);
 }
 
 __global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, const double *__restrict__ ys,

@@ -112,6 +112,13 @@ struct EvView {
     int nparton;
     const double *partons;
     double parton_norm, parton_h, parton_sd, parton_dt;  // parton_sd: the kernel normalisation
+    // charge sources: the partons' (B, S, Q) in the partons' order (nullptr: none; the
+    // particles' charges then stay constant).  With them the equations of motion integrate the
+    // charges: nq_cur (the stage state's) -> nq_out, stage 1 nq_out = nq_cur + dt dN_q/dx0,
+    // stage 2 nq_out = ((nq_out + nq_cur) + dt dN_q/dx0) / 2 (nq_out holding the step's start)
+    const double *parton_q;
+    const double *nq_cur;
+    double *nq_out;
 };
 
 // I^nu of the jet tracks at time t and position (x, y, z): every track moves at the speed of
@@ -264,13 +271,14 @@ __device__ __forceinline__ double kernel_dw(double q)
     return -0.75 * t * t;
 }
 
-// I^mu of the partons formed in (t - dt, t] (Sec. "Dynamical initialization"):
+// I^mu (and I_q) of the partons formed in (t - dt, t] (Sec. "Dynamical initialization"):
 // N p^mu W(r - r_k, h_src) / (sqrt(-g) dt), distances in the event's dim coordinates; the
 // window is found by binary search in the formation times
 __device__ __forceinline__ void parton_deposit(const EvView &v, double t, double sqrtg, const double *x,
-                                               double I[4])
+                                               double I[4], double Iq[3])
 {
     I[0] = I[1] = I[2] = I[3] = 0.0;
+    Iq[0] = Iq[1] = Iq[2] = 0.0;
     const double lo_t = t - v.parton_dt;
     int lo = 0, hi = v.nparton;  // first parton with x^0 > t - dt
     while (lo < hi) {
@@ -291,6 +299,25 @@ __device__ __forceinline__ void parton_deposit(const EvView &v, double t, double
         I[1] += w * q[5];
         I[2] += w * q[6];
         I[3] += w * q[7];
+        if (v.parton_q) {  // the charge source I_q: the parton's (B, S, Q) with the same weight
+            const double *c = v.parton_q + 3 * k;
+            Iq[0] += w * c[0];
+            Iq[1] += w * c[1];
+            Iq[2] += w * c[2];
+        }
+    }
+}
+
+// Heun step of the particle's charges under charge sources (v.nq_out set): stage 1 (mode 0)
+// nq_out = nq_cur + dt dN, stage 2 (mode 1) nq_out = ((nq_out + nq_cur) + dt dN) / 2
+__device__ __forceinline__ void heun_charges(const EvView &v, int mode, size_t n, size_t a, const double dN[3])
+{
+    if (!v.nq_out || mode > 1) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double cur = v.nq_cur[c * n + a];
+        double *o = v.nq_out + c * n + a;
+        *o = mode == 0 ? cur + v.dtau * dN[c] : 0.5 * ((*o + cur) + v.dtau * dN[c]);
     }
 }
 

@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
             else if (mode == 1) yout[k * n + a] = 0.5 * ((yout[k * n + a] + ys[k * n + a]) + dt * fk);
             else rates[k * n + a] = fk;
         }
+        const double dN0[3] = {0.0, 0.0, 0.0};  // frozen: the charges stay as they are
+        heun_charges(v, mode, n, a, dN0);
         return;
     }
     double Bv = 0.0, stv[5] = {0, 0, 0, 0, 0};
@@ -559,26 +561,32 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
             }
     }
     double Isrc[4] = {0.0, 0.0, 0.0, 0.0};
+    double dN[3] = {0.0, 0.0, 0.0};  // charge rates dN_q/dx0 (charge sources only)
     if (v.ntrack > 0 || v.nparton > 0) {
         // jet tracks (Cartesian) and partons: dP^i/dx0 gains sqrt(-g) I^i/sigma*, dS/dx0 gains
-        // u_nu I^nu/(u^0 sigma T)
-        double Ik[4];
+        // u_nu I^nu/(u^0 sigma T); parton charges: dN_q/dx0 = sqrt(-g) I_q/sigma*, and dS/dx0
+        // gains -mu_q/T dN_q/dx0 (eq. dsdnrewr, R^S_q = -mu_q/T)
+        double Ik[4], Iq[3] = {0.0, 0.0, 0.0};
         if (v.ntrack > 0) {
             jet_deposit(v, G.tau, ys[a], ys[n + a], ys[2 * n + a], Ik);
             for (int k = 0; k < 4; ++k) Isrc[k] += Ik[k];
         }
         if (v.nparton > 0) {
             const double xa[3] = {ys[a], ys[n + a], ys[2 * n + a]};
-            parton_deposit(v, G.tau, G.sqrtg, xa, Ik);
+            parton_deposit(v, G.tau, G.sqrtg, xa, Ik, Iq);
             for (int k = 0; k < 4; ++k) Isrc[k] += Ik[k];
         }
         double uI = 0.0;
         for (int k = 0; k < 4; ++k) uI += G.g[k] * u[k] * Isrc[k];
+        uI -= mu[0] * Iq[0] + mu[1] * Iq[1] + mu[2] * Iq[2];
         dS = dS + k3((ig * isg / T) * uI);
+        for (int c = 0; c < 3; ++c) dN[c] = G.sqrtg * Iq[c] / sig_star;
     }
     const A3 ds = sigma * dS + (s * isg) * dsg;
     const A3 dPi = sigma * dBv + Bv * dsg;
-    const A3 dw = (T + ps) * ds + (((mu[0] + pn[0]) * nq[0] + (mu[1] + pn[1]) * nq[1] + (mu[2] + pn[2]) * nq[2]) * isg) * dsg + dPi;
+    // dn_q = N_q dsigma + sigma dN_q
+    const A3 dw = (T + ps) * ds + (((mu[0] + pn[0]) * nq[0] + (mu[1] + pn[1]) * nq[1] + (mu[2] + pn[2]) * nq[2]) * isg) * dsg + dPi +
+                  k3(sigma * ((mu[0] + pn[0]) * dN[0] + (mu[1] + pn[1]) * dN[1] + (mu[2] + pn[2]) * dN[2]));
     const double w = e + p + Pi;
     const double ig2 = ig * ig, ig3 = ig2 * ig;
     // T^{mu nu} for the Christoffel source of the momentum rate (i = eta in Milne)
@@ -684,6 +692,7 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
     } else {
         for (int k = 0; k < nv; ++k) rates[k * n + a] = f[k];
     }
+    heun_charges(v, mode, n, a, dN);
 }
 
 // a8: totals contributions in original order: [0] sqrt(-g) T^{00}/sigma*, [1] S
