@@ -116,8 +116,8 @@ MUTATIONS = [
      "test_oracle_sources.py::test_partons_deposit_their_four_momentum"),
     ("charge_drop_entropy_term", "for (int c = 0; c < 3; ++c) q.uI -= q.mu[c] * Iq[c];", "",
      "test_oracle_sources.py::test_charge_deposit_changes_entropy_by_minus_mu_over_T"),
-    ("charge_rate_drop_sqrtg", "dNq[c * n + a] = G.sqrtg * Iq[c] / aux[0 * n + a];",
-     "dNq[c * n + a] = Iq[c] / aux[0 * n + a];", "test_oracle_sources.py::test_parton_charges_are_deposited"),
+    ("charge_rate_drop_sqrtg", "q.dN[c] = G.sqrtg * Iq[c] / aux[0 * n + a];",
+     "q.dN[c] = Iq[c] / aux[0 * n + a];", "test_oracle_sources.py::test_parton_charges_are_deposited"),
     ("charge_drop_enthalpy_term", "((q->n[c] / q->sigma) * dsig + q->sigma * q->dN[c]);", "((q->n[c] / q->sigma) * dsig);",
      "test_oracle_sources.py::test_charge_deposit_into_moving_fluid_keeps_energy_and_momentum"),
     ("backup_ps_factor", "out[6] = out[0] / 3.0;", "out[6] = out[0] / 4.0;",
