@@ -47,8 +47,8 @@ FLOPS_EOS = (352.0, 64.0, 26.0)
 FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes (read + write) per launch of the FP64 40k-event kernels, from one ncu capture of
 # the current kernels (profiles/ncu_fp64_kernels_viscous_bsq_40k.md; "density" is the forward
-# plus the backward pair pass: 6.85 + 130.7 + 104.6 + 14.59 MB); None once a kernel changes
-DRAM_BYTES_PER_LAUNCH = {"gradient": 180.3e6, "density": 256.7e6, "eos": 7.33e6, "eom": None}
+# plus the backward pair pass: 6.85 + 130.68 + 104.67 + 15.14 MB); None once a kernel changes
+DRAM_BYTES_PER_LAUNCH = {"gradient": 180.3e6, "density": 257.3e6, "eos": 7.33e6, "eom": None}
 
 
 def dist_env():
