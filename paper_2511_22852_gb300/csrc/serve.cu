@@ -59,7 +59,9 @@ constexpr int kRows = 5;    // cell rows (and columns) of the search block: cell
 // Accumulation: each lane sums runs of kRun candidates in plain FP32 (at most kRun terms, so a
 // run's sum errs by <= kRun u times the sum of its terms' magnitudes, u = 2^-24) and folds
 // every run into Neumaier-compensated FP32 sums; the lanes of a particle are combined in FP64.
-constexpr int kRun = 16;
+// 32 terms per run (<= 2e-6 of the run's magnitudes, within the form's 1e-5) fold half as often
+// as 16 (+1.5 % serving throughput measured).
+constexpr int kRun = 32;
 
 // ---------------------------------------------------------------------------
 // single-precision helpers (Neumaier two-sum accumulation)
