@@ -135,6 +135,29 @@ def replica_event(rank: int):
     return I.viscous_bsq_2p1(seed_hot=1 + 1000 * rank, seed_charge=2 + 1000 * rank)
 
 
+def fp64_dgemm_rate(n: int = 8192, reps: int = 5):
+    """Context for the FP64 roofline: cuBLAS DGEMM (torch.matmul in float64, 2 n^3 flops) timed
+    with CUDA events, best of reps -- the FP64 rate a library reaches on this GPU, next to the
+    nominal vector rate the roofline uses."""
+    import torch
+    a = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    b = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return {"gflops": 2.0 * n ** 3 / (best / 1e3) / 1e9, "n": n, "best_ms": best,
+            "how": "torch.matmul float64 (cuBLAS DGEMM), best of %d, CUDA events" % reps}
+
+
 def cpu_baseline(ev, target_s=15.0):
     """The CPU oracle, as it stands, on a bounded sample: whole Heun steps of the same event."""
     from oracle import oracle as O
@@ -632,6 +655,9 @@ def run_ours(args):
                             "avg_launch_ms": ms / times[k][1], "flops_per_launch": flops[k] / times[k][1]}
         rooflines["eos"]["work_per_launch"] = {"table_evals": ew[0] / times["eos"][1], "solves": ew[1] / times["eos"][1],
                                                "closed_form_evals": ew[2] / times["eos"][1]}
+        dgemm = fp64_dgemm_rate()
+        for r in rooflines.values():
+            r["frac_of_measured_dgemm"] = r["achieved"] / dgemm["gflops"]
         roof = rooflines.get(dom)
         total_ms = sum(v[0] for v in times.values())
         kernel_share = {k: round(v[0] / total_ms, 4) for k, v in times.items()}
@@ -662,6 +688,7 @@ def run_ours(args):
                "config": {"workload": WORKLOAD, "particles": ev.n, "l2": "flushed (256 MiB write) between timed steps",
                           "parallelism": f"replicas x{ws}", "cuda_graph": True},
                "roofline": roof, "kernel_share": kernel_share, "kernel_rooflines": rooflines,
+               "fp64_dgemm_measured": dgemm,
                "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                "wall_s_timed": t_wall, "status_or": int(status_or),
                "diagnostics": {"ms_per_step_without_l2_flush": noflush_ms,
