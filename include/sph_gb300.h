@@ -359,10 +359,15 @@ sph_status sph_read_freezeout(sph_event *ev, int64_t cap, double *elems, int64_t
  * Every temporary lives in one fixed file-scope device array (10,223,872 bytes, held by
  * every GPU that loads the library until exit); the call allocates nothing and frees
  * nothing.  Limits: n <= SPH_NOALLOC_MAX_PARTICLES (else SPH_ERR_ARG) and at most 256
- * cells of side 2h per axis (else SPH_ERR_STATE).  Work runs on `stream` (NULL: the
- * legacy default stream) and the call returns after it finished.  All calls share the
- * array: calls that overlap on the GPU race and must be serialised by the caller.  The
- * first call on a device looks up the array's address; make it before any stream capture. */
+ * cells of side 2h per axis (else SPH_ERR_STATE).  Work runs on `stream` and the call
+ * returns after it finished; the wait is bounded (SPH_WAIT_LIMIT_S seconds, default 600,
+ * then SPH_ERR_TIMEOUT).  stream = NULL is the legacy default stream, which synchronises with
+ * every other stream of the device and may not be used while any thread captures a CUDA
+ * graph in global mode: such callers pass a stream they created.  A launch failure returns
+ * SPH_ERR_CUDA.  All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  The first call on a device (and the first after its context
+ * was destroyed and recreated, e.g. by cudaDeviceReset) looks up the array's address; make
+ * it before any stream capture. */
 #define SPH_NOALLOC_MAX_PARTICLES 65536
 sph_status sph_density_noalloc(const double *x, const double *u, const double *S, const double *Nq, int64_t n,
                                double h, double tau, int32_t milne, double *out, void *stream);

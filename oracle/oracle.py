@@ -56,7 +56,7 @@ class Params(C.Structure):
         ("eta_over_s", C.c_double), ("zeta_peak", C.c_double), ("zeta_T_GeV", C.c_double),
         ("zeta_w_GeV", C.c_double), ("tau_pi_coef", C.c_double), ("tau_Pi_ratio", C.c_double),
         ("cs2_cap", C.c_double),
-        ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("pad", C.c_int),
+        ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("newton_no_polish", C.c_int),
         ("ntrack", C.c_int), ("pad2", C.c_int), ("tracks", C.c_void_p), ("track_sigma", C.c_double),
         ("inv", C.c_void_p), ("inv_p10", C.c_void_p), ("inv_K", C.c_int), ("inv_nd", C.c_int), ("inv_nx", C.c_int),
         ("pad3", C.c_int), ("inv_xmax", C.c_double),
@@ -118,7 +118,7 @@ def _f64(a) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
+def make_params(ev, newton_tol=1e-12, newton_maxit=30, newton_polish=True) -> tuple[Params, list]:
     """Params for an inputs.Event; returns (params, keep-alive list of table arrays)."""
     P = Params()
     P.dim, P.milne, P.viscous = ev.dim, int(ev.milne), int(ev.transport.viscous)
@@ -149,6 +149,7 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30) -> tuple[Params, list]:
         for k in range(6):
             P.dnmr[k] = float(dn[k])
     P.newton_tol, P.newton_maxit = newton_tol, newton_maxit
+    P.newton_no_polish = 0 if newton_polish else 1
     inv = getattr(ev, "inverse", None)
     if inv is not None:
         table, p10 = inverse_table(P, inv)

@@ -69,7 +69,7 @@ typedef struct {
     /* Newton */
     double newton_tol;
     int newton_maxit;
-    int pad;
+    int newton_no_polish; /* 1: stop at the first iterate that meets the tolerance (no polishing step) */
     /* energy-momentum source I^nu of straight jet tracks (Cartesian coordinates only):
        tracks[8 k ..]: x0, y0, z0, direction n (unit), start time t0, dE/dx (fm^-2) */
     int ntrack;
@@ -562,7 +562,11 @@ static int table_newton(const oc_params *P, double s, const double *n, double *x
     double rn = resid_inf(P, x, s, n, r, J);
     for (int it = 0; it < P->newton_maxit; ++it) {
         if (rn <= P->newton_tol) {
-            /* one polishing step, kept when its point still meets the tolerance */
+            /* one polishing step, kept when its point still meets the tolerance: both points are
+               solutions under the stopping rule; the polished one lies at the interpolant's root to
+               rounding (quadratic convergence), so the result no longer depends on which iterate
+               first crossed the tolerance */
+            if (P->newton_no_polish) return 0;
             double A[16], d[4], xn[4], rr[4];
             memcpy(A, J, sizeof(A));
             for (int k = 0; k < 4; ++k) d[k] = -r[k];

@@ -15,9 +15,16 @@
 //   * all calls share the one array: calls that overlap on the GPU (two streams,
 //     two host threads) race on it -- serialise them;
 //   * the first call on a device looks up the array's device address (once per
-//     device); make that first call before any stream capture begins.
+//     device, and again after the device's context was destroyed and recreated);
+//     make that first call before any stream capture begins;
+//   * the waits for the device are bounded (SPH_WAIT_LIMIT_S seconds, default 600):
+//     a stream that does not drain gives SPH_ERR_TIMEOUT instead of blocking.
+#include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <thread>
 
 #include "sph_gb300.h"
 #include "sph_internal.cuh"
@@ -51,13 +58,63 @@ constexpr size_t kScratchBytes = align256(kOffFpos + sizeof(float2) * kMaxPartic
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
+// per device: the array's device address and the id of the context it was looked up in
 void *g_base[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 std::mutex g_mu;
 
 sph_status nfail(sph_status s, const char *msg)
 {
     sphg::set_last_error(msg);
     return s;
+}
+
+// Id of the calling thread's current context (driver entry points reached through the
+// runtime, so the library needs no link-time dependence on the driver library).  A context
+// that is destroyed and recreated (cudaDeviceReset) gets a new id; 0 when unavailable.
+unsigned long long current_context_id()
+{
+    typedef int (*get_current_t)(void **);
+    typedef int (*get_id_t)(void *, unsigned long long *);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<get_current_t>(f1);
+            get_id = reinterpret_cast<get_id_t>(f2);
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// waits for the stream with the library's bound on host waits
+sph_status bounded_wait(cudaStream_t st)
+{
+    double limit = 600.0;
+    if (const char *t = getenv("SPH_WAIT_LIMIT_S")) limit = atof(t);
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return SPH_OK;
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            return nfail(SPH_ERR_CUDA, cudaGetErrorString(e));
+        }
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit) return nfail(SPH_ERR_TIMEOUT, "device did not finish within the wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 20 : 500));
+    }
 }
 
 __global__ void k_iota(int *id, int n)
@@ -96,8 +153,10 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_base[dev]) {
+        unsigned long long ctx = current_context_id();
+        if (!g_base[dev] || ctx != g_ctx_id[dev]) {
             // the array's name is a host-side stand-in: its device address comes from the runtime
+            // (looked up again when the device's context was recreated)
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess || !p) {
@@ -105,6 +164,7 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
                 return nfail(SPH_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
             }
             g_base[dev] = p;
+            g_ctx_id[dev] = ctx;
         }
         base = g_base[dev];
     }
@@ -145,7 +205,11 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     v.sc = sc;
 
     // the array keeps the previous call's contents: reset the flags and counters
-    cudaMemsetAsync(sc, 0, sizeof(DevScalars), st);
+    cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nfail(SPH_ERR_CUDA, cudaGetErrorString(e));
+    }
     k_iota<<<(nn + 255) / 256, 256, 0, st>>>(id_in, nn);
     launch_bbox(v, x, st);
     launch_cells(v, x, id_in, cb, st);
@@ -157,13 +221,18 @@ extern "C" sph_status sph_density_noalloc(const double *x, const double *u, cons
     }
     launch_density(v, ys, nqs, cb, dens, nnb, st);
     k_unsort<<<(nn + 255) / 256, 256, 0, st>>>(dens, id_out, nn, milne ? tau : 1.0, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return nfail(SPH_ERR_CUDA, cudaGetErrorString(e));
+    // the copy below goes to pageable memory, which blocks the host until the stream drained:
+    // wait first, with the bound
+    sph_status ws = bounded_wait(st);
+    if (ws != SPH_OK) return ws;
     DevScalars hs;
-    cudaError_t e = cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    e = cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return nfail(SPH_ERR_CUDA, cudaGetErrorString(e));
     }
+    if ((ws = bounded_wait(st)) != SPH_OK) return ws;
     if (hs.err_flags & ERR_CELL_OVERFLOW)
         return nfail(SPH_ERR_STATE, "particles span more than 256 cells of side 2h along an axis");
     return SPH_OK;

@@ -495,6 +495,35 @@ def uniform_box_3d(T_GeV=0.3, half_widths=(1.2, 1.2, 1.2), spacing=0.12, h=0.3, 
                  meta={"dx": spacing}, jets=jets)
 
 
+def boosted_sound_wave_2d(T_GeV=0.3, v=0.5, amp=1e-3, wavelength=4.0, half_widths=(5.6, 3.4), spacing=0.1,
+                          h=0.3, t0=0.0, dtau=0.01, nsteps=300, zeta_over_s=0.2, eta_over_s=1e-4,
+                          tau_pi_coef=5000.0, tau_Pi_ratio=1.0) -> Event:
+    """A uniform conformal fluid (e = 11 T^4, no charges) moving with velocity v along x in a
+    Cartesian 2D box, carrying a small sound wave: e(x) = e0 (1 + amp cos(2 pi x / wavelength)),
+    u^i = (gamma v, 0), Pi = pi = 0 at t0.  Bulk viscosity zeta/s constant (a Gaussian of
+    essentially infinite width), a small shear viscosity whose relaxation time
+    tau_pi = tau_pi_coef eta/(e + p) sets tau_Pi = tau_Pi_ratio tau_pi."""
+    eos = AnalyticEoS(a0=GUBSER_FSTAR / 3.0)
+    gx = spacing * (np.arange(int(round(2 * half_widths[0] / spacing)) + 1) - round(half_widths[0] / spacing))
+    gy = spacing * (np.arange(int(round(2 * half_widths[1] / spacing)) + 1) - round(half_widths[1] / spacing))
+    X, Y = np.meshgrid(gx, gy, indexing="ij")
+    x, y = X.ravel().copy(), Y.ravel().copy()
+    n = x.size
+    k = 2.0 * math.pi / wavelength
+    T = (T_GeV / HBARC) * (1.0 + amp * np.cos(k * x)) ** 0.25
+    _, s, _ = _analytic_p_s_n(eos, T, np.zeros((3, n)))
+    gam = 1.0 / math.sqrt(1.0 - v * v)
+    u = np.zeros((2, n))
+    u[0] = gam * v
+    return Event(name="boosted_sound_wave_2d", dim=2, milne=False, h=h, tau0=t0, dtau=dtau, nsteps=nsteps,
+                 x=np.stack([x, y]), u=u, S=s * gam * spacing * spacing, Nq=np.zeros((3, n)), Bv=np.zeros(n),
+                 Pv=np.zeros((3, n)), eos=eos, table=None,
+                 transport=Transport(viscous=True, eta_over_s=eta_over_s, zeta_peak=zeta_over_s,
+                                     zeta_T_GeV=T_GeV, zeta_w_GeV=1.0e6, tau_pi_coef=tau_pi_coef,
+                                     tau_Pi_ratio=tau_Pi_ratio),
+                 meta={"dx": spacing, "k": k, "v": v, "T0": T_GeV / HBARC, "amp": amp})
+
+
 def stress_cartesian_3d(n_target=8_000_000, R=7.0, z_sigma=1.5, z_max=5.0, h=0.15, n_hot=200, sigma_hot=0.4,
                         T_max_GeV=0.5, charge_frac=0.1, t0=0.6, dtau=0.005, n_tracks=10, seed_hot=1,
                         seed_charge=2, seed_tracks=5, table_shape=(128, 64), with_table=True) -> Event:

@@ -255,3 +255,40 @@ def test_backup_eos_inverts_what_the_closed_form_cannot(bsq_backup):
         o2, _ = O.eos_invert(P, s, n2)
         assert abs((o2[4] - out[4]) / (n[q] * d) / out[7 + q] - 1) < 1e-5
     assert abs(out[10] - 1.0 / 3.0) < 1e-15
+
+
+def test_newton_polish_stays_within_the_stopping_rule(bsq):
+    """The table Newton's polishing step (one Newton step past the first iterate that meets the
+    tolerance, kept when its point meets the tolerance too) only chooses between points the
+    stopping rule of Sec. "EoS inverter" accepts.  So with and without it the inversion agrees
+    within the image of the tolerance: T to 1e-12 relative (s ~ T^3), each mu_q within
+    tol s / (chi_q T^2) (n_q = chi_q T^2 mu_q in the closed form the table samples), p within
+    s dT + n.dmu of those differences;
+    and the evolved state of a viscous event after 20 Heun steps to 1e-12 normwise."""
+    ev, P, _ = bsq
+    Pn, _ = O.make_params(ev, newton_polish=False)
+    t = ev.table
+    tol = P.newton_tol
+    rng = np.random.default_rng(21)
+    for _ in range(400):
+        T = t.T0 + rng.uniform(1, t.nT - 2) * t.dT
+        mu = np.clip(rng.uniform(-0.3, 0.3, 3) * T, t.mu0[0] + t.dmu[0], -t.mu0[0] - t.dmu[0])
+        _, sn, _ = O.eos_table(P, np.array([T, *mu]))
+        a, sa = O.eos_invert(P, sn[0], sn[1:])
+        b, sb = O.eos_invert(Pn, sn[0], sn[1:])
+        assert sa == sb
+        assert abs(a[0] - b[0]) <= 1e-12 * a[0]
+        for q in range(3):
+            assert abs(a[1 + q] - b[1 + q]) <= 2.0 * tol * sn[0] / (ev.eos.chi[q] * a[0] ** 2)
+        # dp = s dT + n.dmu (Gibbs-Duhem) to first order
+        dp = sn[0] * abs(a[0] - b[0]) + float(np.dot(np.abs(sn[1:]), np.abs(a[1:4] - b[1:4])))
+        assert abs(a[4] - b[4]) <= 2.0 * dp + 1e-14 * abs(a[4])
+    small = I.viscous_bsq_2p1(n_target=1200, R=2.0, n_hot=8)
+    ys = []
+    for pol in (True, False):
+        r = O.OracleRun.start(small, newton_polish=pol)
+        r.step(20)
+        ys.append(r.y.copy())
+    for k in range(ys[0].shape[0]):
+        scale = max(np.max(np.abs(ys[0][k])), 1e-300)
+        assert np.max(np.abs(ys[0][k] - ys[1][k])) <= 1e-12 * scale

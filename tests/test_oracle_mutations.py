@@ -125,6 +125,10 @@ MUTATIONS = [
     ("backup_mu_inversion", "out[1 + q] = cbrt(n[q] * m0 * m0 * m0 * m0 / (4.0 * A0));",
      "out[1 + q] = cbrt(n[q] * m0 * m0 * m0 * m0 / (3.0 * A0));",
      "test_oracle_eos.py::test_backup_eos_inverts_what_the_closed_form_cannot"),
+    ("enthalpy_drop_bulk_rate", "double dw = (q->T + q->ps) * ds + dPi;", "double dw = (q->T + q->ps) * ds;",
+     "test_oracle_bulk_flow.py::test_bulk_sound_wave_in_moving_fluid"),
+    ("stress_drop_bulk", "double X = -(p + Pi) * (j == i", "double X = -(p) * (j == i",
+     "test_oracle_bulk_flow.py::test_bulk_sound_wave_in_moving_fluid"),
     ("dnmr_bulk_drop_volume_rate", "R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);",
      "R->dBv = DPi / (u0 * q->sigma);", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
 ]
