@@ -138,6 +138,20 @@ typedef struct {
     void *stream;
     int32_t profile;   /* 1: time every kernel group with CUDA events (no graph; see sph_kernel_times) */
     int32_t precision; /* SPH_FP64 or SPH_MIXED (see below) */
+    double T_stop_GeV; /* > 0: a particle whose temperature is below it has left the fluid (the matter
+                          below the freeze-out surface of Sec. "Freeze-out hypersurface construction"):
+                          in that stage it streams freely (dx/dx0 = v, its other variables and charges
+                          unchanged) while its neighbours still see its kernel sums and pressure;
+                          0: off */
+    /* BSQ diffusion (Sec. "Equations of motion", eq. min_dif_rel; constant kappa/T^2 and tau T,
+     * Sec. "Transport coefficients"), dim = 2 only, single-event forms: with kappaT2 != NULL
+     * (kappaT2[3 q + q'] = kappa_{qq'} / T^2, q = B, S, Q; tauJT[q] = tau_q T > 0) the charges
+     * diffuse: tau_q Delta^mu_nu D J^nu_q + J^mu_q = kappa_{qq'} nabla^<mu> (mu_{q'} / T) (metric
+     * (+,-,-,-): the current runs down the gradient of mu/T); the state gains J^i_q / sigma
+     * (Jv[6 n]: (x, y) of B, then S, then Q; NULL: zero) and Nq becomes the particles' lab charge
+     * N_q + J^0_q / (sigma u^0), whose sum over the particles is conserved (read with SPH_F_JV,
+     * SPH_F_NQ).  kappaT2 = NULL: no diffusion (the charges are constant). */
+    const double *kappaT2, *tauJT, *Jv;
 } sph_event_desc;
 
 /* Precision of the step.  SPH_FP64: every operation in double precision.  SPH_MIXED (dim 2 or 3):
@@ -189,6 +203,7 @@ sph_status sph_step(sph_event *ev, int32_t nsteps, uint32_t flags);
 #define SPH_F_STATUS (1ull << 14)    /* status[n] (uint32) */
 #define SPH_F_NNB (1ull << 15)       /* neighbour count including self, nnb[n] (int32) */
 #define SPH_F_CELL (1ull << 16)      /* cell coordinates cell[dim*n] (int32) */
+#define SPH_F_JV (1ull << 18)        /* diffusion currents Jv[6*n]: J^i_q / sigma (x, y of B, S, Q) */
 #define SPH_F_GUESS (1ull << 17)     /* EoS warm start guess[4*n]: the previous stage's table solution
                                         (T, mu_B, mu_S, mu_Q), T = 0 where the table was not used;
                                         part of the evolved state (read it and write it back for a
@@ -201,6 +216,7 @@ typedef struct {
     int32_t *nnb, *cell;
     double *guess;
     int32_t on_device;
+    double *Jv; /* SPH_F_JV */
 } sph_field_bufs;
 
 typedef struct {
@@ -457,6 +473,27 @@ sph_status sph_server_drain(sph_server *srv, double timeout_s);
  * composition for a fixed shape).  Errors: SPH_ERR_STATE (no batch has run a step). */
 sph_status sph_server_autotune(sph_server *srv, int32_t trials, int32_t *chosen);
 
+/* Sampled per-kernel-group timing of the batch step (measurement support): with every > 0,
+ * every every-th batch step launches the same kernels eagerly instead of through the step graph,
+ * with CUDA events between its kernel groups (per stage: sort = bounding boxes, cell keys, scans
+ * and permutation; density; eos; gradient; eom; work), on the server's stream.  every = 0 turns
+ * the sampling off (the sums are kept).  sph_server_kernel_times: for group k < *count (count <=
+ * max), names[32*k ..] gets its name, ms[k] the summed milliseconds of the sampled stages and
+ * launches[k] their number (two per sampled step).  Errors: SPH_ERR_ARG; SPH_ERR_STATE when
+ * sampling was never enabled. */
+sph_status sph_server_profile(sph_server *srv, int32_t every);
+sph_status sph_server_kernel_times(sph_server *srv, int32_t max, char *names, double *ms, int64_t *launches,
+                                   int32_t *count);
+
+/* Measurement support (not part of the stepping interface): the device's fused multiply-add
+ * rate in FP64 (fp64 = 1) or FP32 (fp64 = 0), the denominator of the arithmetic rooflines of the
+ * step's kernels.  Eight independent multiply-add chains per thread, eight resident blocks of 256
+ * threads on every SM, about 40 ms per launch; *gflops = 2 x multiply-adds / the best of reps
+ * launches timed with CUDA events (*best_ms, may be NULL, its duration).  Allocates a small
+ * buffer and a stream, freed before returning.  Errors: SPH_ERR_ARG (null gflops, reps < 1),
+ * SPH_ERR_OOM, SPH_ERR_CUDA. */
+sph_status sph_measure_fma_peak(int32_t fp64, int32_t reps, double *gflops, double *best_ms);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *sph_last_error(void);
 
@@ -466,7 +503,7 @@ const char *sph_last_error(void);
 sph_status sph_debug_neighbors(sph_event *ev, int64_t cap, int32_t *pa, int32_t *pb, int64_t *count);
 
 /* Test support: one right-hand-side evaluation at the current state, without
- * advancing it.  rates[nv*n] (nv = 2 dim + 2 + npi) and grad[(dim*dim + dim)*n]
+ * advancing it.  rates[nv*n] (nv = 2 dim + 2 + npi, plus 6 with diffusion) and grad[(dim*dim + dim)*n]
  * (d_k u^j with k major, then F^i) in original order, host buffers; either may be NULL. */
 sph_status sph_debug_rates(sph_event *ev, double *rates, double *grad);
 

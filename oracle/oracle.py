@@ -65,6 +65,8 @@ class Params(C.Structure):
         ("parton_norm", C.c_double), ("parton_h", C.c_double), ("parton_dt", C.c_double),
         ("backup", C.c_int), ("pad6", C.c_int), ("cd_A0", C.c_double), ("cd_mu0", C.c_double * 3),
         ("parton_q", C.c_void_p),
+        ("T_stop_GeV", C.c_double),
+        ("diffusion", C.c_int), ("pad8", C.c_int), ("kappaT2", C.c_double * 9), ("tauJT", C.c_double * 3),
     ]
 
 
@@ -150,6 +152,15 @@ def make_params(ev, newton_tol=1e-12, newton_maxit=30, newton_polish=True) -> tu
             P.dnmr[k] = float(dn[k])
     P.newton_tol, P.newton_maxit = newton_tol, newton_maxit
     P.newton_no_polish = 0 if newton_polish else 1
+    P.T_stop_GeV = float(getattr(tr, "T_stop_GeV", 0.0) or 0.0)
+    df = getattr(ev, "diffusion", None)
+    if df is not None:
+        P.diffusion = 1
+        kap = np.asarray(df.kappaT2, dtype=np.float64).reshape(9)
+        for k in range(9):
+            P.kappaT2[k] = float(kap[k])
+        for q in range(3):
+            P.tauJT[q] = float(df.tauJT[q])
     inv = getattr(ev, "inverse", None)
     if inv is not None:
         table, p10 = inverse_table(P, inv)
@@ -218,8 +229,13 @@ def nv(dim: int) -> int:
 
 
 def pack_state(ev) -> np.ndarray:
-    """y[nv][N]: x^i, u^i, S, Pi/sigma, pi^{ij}/sigma."""
-    return np.ascontiguousarray(np.vstack([ev.x, ev.u, ev.S[None], ev.Bv[None], ev.Pv]), dtype=np.float64)
+    """y[nv][N]: x^i, u^i, S, Pi/sigma, pi^{ij}/sigma, and with diffusion J^i_q/sigma (charge major)."""
+    rows = [ev.x, ev.u, ev.S[None], ev.Bv[None], ev.Pv]
+    df = getattr(ev, "diffusion", None)
+    if df is not None:
+        jv = df.Jv if df.Jv is not None else np.zeros((3 * ev.dim, ev.n))
+        rows.append(np.asarray(jv, dtype=np.float64).reshape(3 * ev.dim, ev.n))
+    return np.ascontiguousarray(np.vstack(rows), dtype=np.float64)
 
 
 def W(r, h, dim):

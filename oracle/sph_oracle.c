@@ -106,6 +106,21 @@ typedef struct {
     /* charges of the dynamical-initialisation partons (eq. charge_conservation with I_q != 0):
        parton_q[3 k ..] = (B, S, Q) of parton k, smeared like its four-momentum (NULL: none) */
     const double *parton_q;
+    /* temperature (GeV) below which a particle has left the fluid: it streams freely
+       (dx/dx0 = v, its other variables and charges constant) while its neighbours still see its
+       kernel sums and pressure (0: off) */
+    double T_stop_GeV;
+    /* BSQ diffusion (eq. min_dif_rel, minimal Israel-Stewart): tau_q Delta^mu_nu D J^nu_q + J^mu_q
+       = kappa_{qq'} nabla^<mu> alpha_{q'} (metric (+,-,-,-)), alpha_q = mu_q / T, with
+       kappa_{qq'} = kappaT2[3 q + q'] T^2
+       and the diagonal relaxation times tau_q = tauJT[q] / T (constant kappa/T^2 and tau T, Sec.
+       "Transport coefficients").  The state then carries J^i_q / sigma (contravariant spatial
+       components, charge major) after the shear rows, and the charges Nq are the particles' lab
+       charges sqrt(-g) N^0_q / sigma* = N_q + J^0_q / (sigma u^0) (see oc_stage). */
+    int diffusion;
+    int pad8;
+    double kappaT2[9];
+    double tauJT[3];
 } oc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -918,6 +933,15 @@ typedef struct {
     int model;      /* viscous equations of motion (oc_params.eom_model) */
     double cs2;     /* speed of sound squared (DNMR lambda_Pipi) */
     double dnmr[6]; /* DNMR coefficient ratios (oc_params.dnmr) */
+    /* BSQ diffusion */
+    int diff;
+    double Jc[3][4];  /* J^mu_q, contravariant (J^0 from transversality) */
+    double Jh[3][4];  /* J^i_q / sigma, the stored variables */
+    double ga[3][4];  /* d_i alpha_q */
+    double kap[3][3]; /* kappa_{qq'} */
+    double tJ[3];     /* tau_q */
+    double dNt[3];    /* rate of the lab charge from the flux divergence of the currents */
+    double dal[3][4]; /* d alpha_q / d(s, n_B, n_S, n_Q) */
 } ppart;
 
 typedef struct {
@@ -925,7 +949,60 @@ typedef struct {
     double dS, dBv;
     double dPv[4][4];
     double theta;
+    double dJ[3][4];    /* d/dx0 of J^i_q / sigma */
+    double dNl[3];      /* d/dx0 of the lab charges */
 } prates;
+
+/* The diffusion rates for a given D alpha_q (the comoving derivative of alpha_q = mu_q / T),
+   at a trial acceleration: from eq. min_dif_rel, tau_q Delta^i_nu D J^nu_q + J^i_q =
+   kappa_{qq'} nabla^<i> alpha_{q'} (the sign for the metric (+,-,-,-): the current runs down the
+   gradient of mu/T, and the entropy production kappa (nabla alpha)^2 is non-negative), with
+   Delta^i_nu D J^nu = D J^i + u^i J^nu Du_nu (u_nu J^nu = 0) and
+   nabla^<i> alpha = g^{ii} d_i alpha - u^i D alpha:
+     D J^i = (-J^i + kappa nabla^<i> alpha) / tau - u^i J^nu Du_nu,
+     dJ^i/dx0 = (D J^i - u^mu Gamma^i_{mu lambda} J^lambda) / u^0,  d(J^i/sigma) = dJ^i/sigma - J^i dsigma/sigma^2;
+   the rest-frame charge N_q = lab charge - Z_q with Z_q = J^0_q / (sigma u^0), so
+   dN_q = dNt_q - dZ_q; the entropy rate gains -mu_q dN_q / T (eq. dsdnrewr); and D alpha_q
+   implied by those rates, u^0 (alpha_{q,s} ds + alpha_{q,n} . dn) with s = sigma S and
+   n = sigma N, is returned in Dal_out (the caller solves for its fixed point). */
+static void diff_chain(const ppart *q, const geom_t *G, const double *a, double du0, const double *alow, double dsig,
+                       double dS0, const double *Dal_in, double dJh[3][4], double *dNd, double *Dal_out)
+{
+    const double *u = q->u;
+    const int dim = q->dim;
+    double dN[3];
+    for (int c = 0; c < 3; ++c) {
+        double jDu = 0.0;
+        for (int nu = 0; nu < 4; ++nu) jDu += q->Jc[c][nu] * alow[nu];
+        double dZ = 0.0;
+        for (int i = 1; i <= dim; ++i) {
+            double src = 0.0; /* kappa_{qq'} nabla^<i> alpha_{q'} */
+            for (int c2 = 0; c2 < 3; ++c2)
+                src += q->kap[c][c2] * (G->gi[i] * q->ga[c2][i] - u[i] * Dal_in[c2]);
+            const double DJ = (-q->Jc[c][i] + src) / q->tJ[c] - u[i] * jDu;
+            double chr = 0.0;
+            for (int m = 0; m < 4; ++m)
+                for (int l = 0; l < 4; ++l) chr += u[m] * G->G[i][m][l] * q->Jc[c][l];
+            const double dJ = (DJ - chr) / u[0];
+            const double dj = dJ / q->sigma - q->Jc[c][i] * dsig / (q->sigma * q->sigma);
+            if (dJh) dJh[c][i] = dj;
+            dZ += -(G->dg[i] * u[i] * q->Jh[c][i] + G->g[i] * a[i] * q->Jh[c][i] + G->g[i] * u[i] * dj) / (u[0] * u[0]) +
+                  2.0 * G->g[i] * u[i] * q->Jh[c][i] * du0 / (u[0] * u[0] * u[0]);
+        }
+        dN[c] = q->dNt[c] - dZ;
+        if (dNd) dNd[c] = dN[c];
+    }
+    double dS = dS0;
+    for (int c = 0; c < 3; ++c) dS -= q->mu[c] * dN[c] / q->T;
+    const double ds = q->sigma * dS + (q->s / q->sigma) * dsig;
+    double dn[3];
+    for (int c = 0; c < 3; ++c) dn[c] = q->sigma * (q->dN[c] + dN[c]) + (q->n[c] / q->sigma) * dsig;
+    for (int c = 0; c < 3; ++c) {
+        double d = q->dal[c][0] * ds;
+        for (int r = 0; r < 3; ++r) d += q->dal[c][1 + r] * dn[r];
+        Dal_out[c] = u[0] * d;
+    }
+}
 
 /* every rate as a function of a trial acceleration a^i = du^i/dx0 (linear in a) */
 static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
@@ -1065,11 +1142,41 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
         R->dS = q->uI / (u0 * q->sigma * q->T);
         R->dBv = 0.0;
     }
+    /* rest-frame charge rates: the charge sources', plus the diffusion currents' */
+    double dNq[3] = {q->dN[0], q->dN[1], q->dN[2]};
+    memset(R->dJ, 0, sizeof(R->dJ));
+    for (int c = 0; c < 3; ++c) R->dNl[c] = q->dN[c];
+    if (q->diff) {
+        double alow_d[4];
+        for (int al = 0; al < 4; ++al) alow_d[al] = G->g[al] * Du[al];
+        /* the chain is affine in D alpha: its fixed point from the chain at 0 and the unit vectors */
+        const double z3[3] = {0.0, 0.0, 0.0};
+        double f0[3], Fm[9], rhs[3];
+        diff_chain(q, G, a, du0, alow_d, dsig, R->dS, z3, NULL, NULL, f0);
+        for (int k = 0; k < 3; ++k) {
+            double e[3] = {0.0, 0.0, 0.0}, fk[3];
+            e[k] = 1.0;
+            diff_chain(q, G, a, du0, alow_d, dsig, R->dS, e, NULL, NULL, fk);
+            for (int c = 0; c < 3; ++c) Fm[c * 3 + k] = (c == k ? 1.0 : 0.0) - (fk[c] - f0[c]);
+        }
+        for (int c = 0; c < 3; ++c) rhs[c] = f0[c];
+        double Dal[3] = {0.0, 0.0, 0.0};
+        if (gauss_solve(3, Fm, rhs) == 0)
+            for (int c = 0; c < 3; ++c) Dal[c] = rhs[c];
+        double dNd[3], Dchk[3];
+        diff_chain(q, G, a, du0, alow_d, dsig, R->dS, Dal, R->dJ, dNd, Dchk);
+        for (int c = 0; c < 3; ++c) {
+            R->dS -= q->mu[c] * dNd[c] / q->T;
+            dNq[c] += dNd[c];
+            R->dNl[c] += q->dNt[c];
+        }
+    }
     double ds = q->sigma * R->dS + (q->s / q->sigma) * dsig;
     double dPi = q->sigma * R->dBv + q->Bv * dsig;
     double dw = (q->T + q->ps) * ds + dPi;
-    /* dn_q = N_q dsigma + sigma dN_q with N_q = n_q / sigma (dN_q != 0 under charge sources) */
-    for (int c = 0; c < 3; ++c) dw += (q->mu[c] + q->pn[c]) * ((q->n[c] / q->sigma) * dsig + q->sigma * q->dN[c]);
+    /* dn_q = N_q dsigma + sigma dN_q with N_q = n_q / sigma (dN_q != 0 under charge sources and
+       diffusion) */
+    for (int c = 0; c < 3; ++c) dw += (q->mu[c] + q->pn[c]) * ((q->n[c] / q->sigma) * dsig + q->sigma * dNq[c]);
     double w = q->e + q->p + q->Pi;
     for (int i = 1; i < 4; ++i) {
         double t1 = 0.0, t2 = 0.0;
@@ -1086,6 +1193,17 @@ static void lhs_of(const ppart *q, const geom_t *G, const double *a, prates *R)
 /* one stage: neighbours, densities, EoS, gradients, rates                   */
 /* ------------------------------------------------------------------------ */
 static int nv_of(int dim) { return 2 * dim + 2 + npi_of(dim); }
+/* state rows: the diffusion currents J^i_q / sigma follow the shear rows */
+static int nvp_of(const oc_params *P) { return nv_of(P->dim) + (P->diffusion ? 3 * P->dim : 0); }
+static int jrow(const oc_params *P, int q, int i) { return nv_of(P->dim) + q * P->dim + i; }
+
+/* J^0 of a transverse current from its spatial components: u_mu J^mu = 0 with g_00 = 1 */
+static double j0_of(const geom_t *G, int dim, const double *u, const double *J)
+{
+    double acc = 0.0;
+    for (int i = 1; i <= dim; ++i) acc += G->g[i] * u[i] * J[i];
+    return -acc / u[0];
+}
 
 /* y layout [nv][n]: x^1..x^dim, u^1..u^dim, S, Pi/sigma, pi^{ij}/sigma (stored comps)
    aux layout [NAUX][n]: sigma*, s, nB, nS, nQ, T, muB, muS, muQ, p, e, cs2, theta, Pi,
@@ -1124,6 +1242,16 @@ static void densities_eos(const oc_params *P, long n, double tau, const double *
             aux[0 * n + a] = sig;
             aux[1 * n + a] = ss / vol;
             for (int c = 0; c < 3; ++c) aux[(2 + c) * n + a] = nn[c] / vol;
+            if (P->diffusion) {
+                /* the kernel sum of the lab charges is the lab density sqrt(-g) N^0 = sqrt(-g)
+                   (n u^0 + J^0): the rest-frame n_q = (sum / sqrt(-g) - J^0_q) / u^0 */
+                double u[4] = {u0, 0, 0, 0}, J[4] = {0, 0, 0, 0};
+                for (int i = 0; i < dim; ++i) u[1 + i] = y[(dim + i) * n + a];
+                for (int c = 0; c < 3; ++c) {
+                    for (int i = 0; i < dim; ++i) J[1 + i] = (sig / vol) * y[jrow(P, c, i) * n + a];
+                    aux[(2 + c) * n + a] = (nn[c] / G.sqrtg - j0_of(&G, dim, u, J)) / u0;
+                }
+            }
             aux[14 * n + a] = u0;
             aux[15 * n + a] = (double)m;
             aux[16 * n + a] = sig / vol;
@@ -1152,11 +1280,50 @@ typedef struct {
     double ps, pn[3], cs2;
 } eosder_t;
 
+/* d alpha_q / d(s, n_B, n_S, n_Q), alpha_q = mu_q / T, at an inversion's solution x = (T, mu):
+   (dT, dmu) = H^-1 (ds, dn) with H = d(s, n)/d(T, mu) of the EoS that produced it (the table,
+   the closed form, or the conformal-diagonal backup); charge directions the closed form does
+   not couple (chi_q = 0, no table) get zero derivatives.  Returns -1 for a singular H. */
+static int dalpha_of(const oc_params *P, const double *x, int used_table, unsigned st, double dal[3][4])
+{
+    double H[16], p, sn[4];
+    memset(dal, 0, sizeof(double) * 12);
+    if (st & ST_BACKUP) {
+        memset(H, 0, sizeof(H));
+        H[0] = 12.0 * P->cd_A0 * x[0] * x[0];
+        for (int q = 0; q < 3; ++q) {
+            const double m0 = P->cd_mu0[q];
+            H[(1 + q) * 4 + 1 + q] = 12.0 * P->cd_A0 * x[1 + q] * x[1 + q] / (m0 * m0 * m0 * m0);
+        }
+    } else if (used_table) {
+        oc_eos_table(P, x, &p, sn, H);
+    } else {
+        oc_eos_analytic(P, x[0], &x[1], &p, sn, H);
+    }
+    int act[4], m = 0;
+    for (int k = 0; k < 4; ++k)
+        if (k == 0 || used_table || (st & ST_BACKUP) || P->chi[k - 1] > 0.0) act[m++] = k;
+    double Hi[16];
+    memset(Hi, 0, sizeof(Hi));
+    for (int f = 0; f < m; ++f) { /* column f of the inverse over the active directions */
+        double A[16], b[4];
+        for (int i = 0; i < m; ++i) {
+            b[i] = i == f ? 1.0 : 0.0;
+            for (int j = 0; j < m; ++j) A[i * m + j] = H[act[i] * 4 + act[j]];
+        }
+        if (gauss_solve(m, A, b) != 0) return -1;
+        for (int i = 0; i < m; ++i) Hi[act[i] * 4 + act[f]] = b[i];
+    }
+    for (int q = 0; q < 3; ++q)
+        for (int f = 0; f < 4; ++f) dal[q][f] = (Hi[(1 + q) * 4 + f] - (x[1 + q] / x[0]) * Hi[0 * 4 + f]) / x[0];
+    return 0;
+}
+
 int oc_stage(const oc_params *P, long n, double tau, const double *y, const double *Nq, double *dydt, double *aux,
              double *grad, unsigned *status, double *work_rate, const double *guess_in, double *guess_out,
              double *dNq)
 {
-    int dim = P->dim, np = npi_of(dim), nv = nv_of(dim);
+    int dim = P->dim, np = npi_of(dim), nv = nvp_of(P);
     double two_h = 2.0 * P->h;
     double supp2 = two_h * two_h;
     geom_t G;
@@ -1164,6 +1331,16 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     grid_t g;
     grid_build(&g, n, dim, y, P->h);
     densities_eos(P, n, tau, y, Nq, &g, aux, status, guess_in, guess_out);
+    /* diffusion: per particle alpha_q, d alpha_q / d(s, n), J^mu_q, and the flux
+       (J^k - v^k J^0) / sigma*^2 of the lab charge; per particle from the gradient pass
+       d_k alpha_q and the flux divergence */
+    const size_t nz = (size_t)(n > 0 ? n : 1);
+    double *alph = P->diffusion ? (double *)calloc(3 * nz, sizeof(double)) : NULL;
+    double *dalp = P->diffusion ? (double *)calloc(12 * nz, sizeof(double)) : NULL;
+    double *Jmu = P->diffusion ? (double *)calloc(12 * nz, sizeof(double)) : NULL;
+    double *Fls = P->diffusion ? (double *)calloc(9 * nz, sizeof(double)) : NULL;
+    double *galp = P->diffusion ? (double *)calloc(9 * nz, sizeof(double)) : NULL;
+    double *dNt = P->diffusion ? (double *)calloc(3 * nz, sizeof(double)) : NULL;
 
     /* EoS derivatives again (kept out of aux), transport, full pi, X^{ji}/sigma*^2 */
     eosder_t *ed = (eosder_t *)malloc(sizeof(eosder_t) * (size_t)(n > 0 ? n : 1));
@@ -1178,7 +1355,14 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
         double gs[4] = {0, 0, 0, 0};
         if (guess_in)
             for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
-        oc_eos_invert_ws(P, aux[1 * n + a], nr, gs, out, NULL);
+        int used = 0;
+        unsigned est = oc_eos_invert_ws(P, aux[1 * n + a], nr, gs, out, &used);
+        if (P->diffusion) {
+            double dal[3][4];
+            if (!(est & (ST_NOCONV | ST_NONFINITE)) && out[0] > 0.0 && dalpha_of(P, out, used, est, dal) == 0)
+                memcpy(&dalp[12 * a], dal, sizeof(dal));
+            for (int c = 0; c < 3; ++c) alph[3 * a + c] = out[0] > 0.0 ? out[1 + c] / out[0] : 0.0;
+        }
         ed[a].ps = out[6];
         for (int c = 0; c < 3; ++c) ed[a].pn[c] = out[7 + c];
         ed[a].cs2 = out[10];
@@ -1201,6 +1385,14 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
                 Xs[9 * a + 3 * j + i] = X / (sstar * sstar);
             }
         for (int j = 0; j < 3; ++j) us[3 * a + j] = u[1 + j] / sstar;
+        if (P->diffusion)
+            for (int c = 0; c < 3; ++c) {
+                double J[4] = {0, 0, 0, 0};
+                for (int i = 0; i < dim; ++i) J[1 + i] = sigma * y[jrow(P, c, i) * n + a];
+                J[0] = j0_of(&G, dim, u, J);
+                for (int m = 0; m < 4; ++m) Jmu[12 * a + 4 * c + m] = J[m];
+                for (int k = 0; k < 3; ++k) Fls[9 * a + 3 * c + k] = (J[1 + k] - (u[1 + k] / u[0]) * J[0]) / (sstar * sstar);
+            }
         for (int m = 0; m < 4; ++m)
             for (int l = 0; l < 4; ++l) {
                 double Delta = (m == l ? G.gi[m] : 0.0) - u[m] * u[l];
@@ -1215,9 +1407,11 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
 #pragma omp for schedule(dynamic, 64)
         for (long a = 0; a < n; ++a) {
             long m = grid_neighbors(&g, y, supp2, a, buf);
-            double du[3][3], F[3];
+            double du[3][3], F[3], ga[3][3], dv[3];
             memset(du, 0, sizeof(du));
             memset(F, 0, sizeof(F));
+            memset(ga, 0, sizeof(ga));
+            memset(dv, 0, sizeof(dv));
             for (long k = 0; k < m; ++k) {
                 long b = buf[k];
                 double r2 = r2_of(dim, y, n, a, b);
@@ -1230,7 +1424,22 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
                     for (int j = 0; j < dim; ++j) du[kk][j] += us[3 * b + j] * gw[kk];
                 for (int i = 0; i < dim; ++i)
                     for (int j = 0; j < dim; ++j) F[i] += (Xs[9 * a + 3 * j + i] + Xs[9 * b + 3 * j + i]) * gw[j];
+                if (P->diffusion)
+                    for (int c = 0; c < 3; ++c) {
+                        /* d_k alpha: the difference form (the general SPH derivative with n = 1,
+                           zero for a uniform alpha); the flux divergence: the n = -1 form */
+                        const double da = alph[3 * b + c] - alph[3 * a + c];
+                        for (int kk = 0; kk < dim; ++kk) {
+                            ga[c][kk] += da * gw[kk];
+                            dv[c] += (Fls[9 * a + 3 * c + kk] + Fls[9 * b + 3 * c + kk]) * gw[kk];
+                        }
+                    }
             }
+            if (P->diffusion)
+                for (int c = 0; c < 3; ++c) {
+                    for (int kk = 0; kk < dim; ++kk) galp[9 * a + 3 * c + kk] = ga[c][kk] / aux[0 * n + a];
+                    dNt[3 * a + c] = -G.sqrtg * dv[c];
+                }
             for (int kk = 0; kk < dim; ++kk)
                 for (int j = 0; j < dim; ++j) grad[(kk * dim + j) * n + a] = du[kk][j];
             for (int i = 0; i < dim; ++i) grad[(dim * dim + i) * n + a] = -G.sqrtg * F[i];
@@ -1243,9 +1452,10 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     for (long a = 0; a < n; ++a) {
         if (dNq)
             for (int c = 0; c < 3; ++c) dNq[c * n + a] = 0.0;
-        if (status[a] & (ST_NOCONV | ST_NONFINITE)) {
-            /* no EoS solution: the particle is frozen for this stage, moving ballistically
-               (its charges too stay as they are) */
+        if ((status[a] & (ST_NOCONV | ST_NONFINITE)) ||
+            (P->T_stop_GeV > 0.0 && aux[5 * n + a] * HBARC < P->T_stop_GeV)) {
+            /* no EoS solution, or below the stop temperature: the particle is frozen for this
+               stage, moving ballistically (its charges too stay as they are) */
             double u0 = aux[14 * n + a];
             for (int k = 0; k < nv; ++k) dydt[k * n + a] = 0.0;
             for (int i = 0; i < dim; ++i) dydt[i * n + a] = y[(dim + i) * n + a] / u0;
@@ -1315,6 +1525,21 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
                     for (int c = 0; c < 3; ++c) dNq[c * n + a] = q.dN[c];
             }
         }
+        if (P->diffusion) {
+            q.diff = 1;
+            const double T = q.T;
+            for (int c = 0; c < 3; ++c) {
+                for (int m = 0; m < 4; ++m) q.Jc[c][m] = Jmu[12 * a + 4 * c + m];
+                for (int i = 0; i < dim; ++i) {
+                    q.Jh[c][1 + i] = y[jrow(P, c, i) * n + a];
+                    q.ga[c][1 + i] = galp[9 * a + 3 * c + i];
+                }
+                for (int c2 = 0; c2 < 3; ++c2) q.kap[c][c2] = P->kappaT2[3 * c + c2] * T * T;
+                q.tJ[c] = P->tauJT[c] / T;
+                q.dNt[c] = dNt[3 * a + c];
+                for (int f = 0; f < 4; ++f) q.dal[c][f] = dalp[12 * a + 4 * c + f];
+            }
+        }
         /* M_ij = dP^i(e_j) - dP^i(0), c^i = dP^i(0); solve M a = F - c */
         double zero[4] = {0, 0, 0, 0};
         prates R0;
@@ -1346,6 +1571,12 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
             int i = dim == 2 ? PI2[k][0] : PI3[k][0], j = dim == 2 ? PI2[k][1] : PI3[k][1];
             dydt[(2 * dim + 2 + k) * n + a] = P->viscous ? R.dPv[i][j] : 0.0;
         }
+        if (P->diffusion) {
+            for (int c = 0; c < 3; ++c)
+                for (int i = 0; i < dim; ++i) dydt[jrow(P, c, i) * n + a] = R.dJ[c][1 + i];
+            if (dNq)
+                for (int c = 0; c < 3; ++c) dNq[c * n + a] = R.dNl[c];
+        }
     }
     /* longitudinal work rate: sum_a sqrt(-g) Gamma^0_{mu nu} T^{mu nu} / sigma* (serial, fixed order) */
     double wr = 0.0;
@@ -1361,6 +1592,12 @@ int oc_stage(const oc_params *P, long n, double tau, const double *y, const doub
     free(us);
     free(pif);
     free(Tfull);
+    free(alph);
+    free(dalp);
+    free(Jmu);
+    free(Fls);
+    free(galp);
+    free(dNt);
     grid_free(&g);
     return 0;
 }
@@ -1381,13 +1618,13 @@ void oc_observe(const oc_params *P, long n, double tau, const double *y, const d
 int oc_heun(const oc_params *P, long n, double *tau, double dtau, int nsteps, double *y, double *Nq, double *aux,
             double *grad, unsigned *status, unsigned *status_or, double *work, double *guess)
 {
-    int nv = nv_of(P->dim);
+    int nv = nvp_of(P);
     size_t sz = sizeof(double) * (size_t)nv * (size_t)(n > 0 ? n : 1);
     double *k = (double *)malloc(sz);
     double *y1 = (double *)malloc(sz);
     double *g1 = (double *)calloc((size_t)4 * (size_t)(n > 0 ? n : 1), sizeof(double));
-    /* charges change only under charge sources; then they take the same Heun steps */
-    const int charged = P->parton_q != NULL && P->nparton > 0;
+    /* charges change only under charge sources or diffusion; then they take the same Heun steps */
+    const int charged = (P->parton_q != NULL && P->nparton > 0) || P->diffusion;
     size_t szq = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
     double *kq = charged ? (double *)malloc(szq) : NULL;
     double *Nq1 = charged ? (double *)malloc(szq) : NULL;

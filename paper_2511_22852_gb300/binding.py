@@ -30,14 +30,15 @@ SPH_FP64, SPH_MIXED = 0, 1
 
 F = {name: 1 << i for i, name in enumerate(
     ["X", "U", "S", "NQ", "BV", "PV", "SIGMA_STAR", "S_DENS", "N_DENS", "T", "MU", "P", "E", "PI_BULK", "STATUS",
-     "NNB", "CELL", "GUESS"])}
+     "NNB", "CELL", "GUESS", "JV"])}
 
 EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_event", "sph_step", "sph_read_fields",
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
            "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode",
-           "sph_set_viscous_eom", "sph_set_partons", "sph_set_eos_backup"]
+           "sph_set_viscous_eom", "sph_set_partons", "sph_set_eos_backup", "sph_server_profile",
+           "sph_server_kernel_times", "sph_measure_fma_peak"]
 SPH_EOS_ONLINE, SPH_EOS_OFFLINE = 0, 1
 SPH_FO_NREC = 24
 SPH_TICKET_QUEUED, SPH_TICKET_RUNNING, SPH_TICKET_DONE = 0, 1, 2
@@ -64,12 +65,14 @@ class EventDesc(C.Structure):
                 ("Pv", C.c_void_p), ("eta_over_s", C.c_double), ("zeta_peak", C.c_double),
                 ("zeta_T_GeV", C.c_double), ("zeta_w_GeV", C.c_double), ("tau_pi_coef", C.c_double),
                 ("tau_Pi_ratio", C.c_double), ("cs2_cap", C.c_double), ("fatal_mask", C.c_uint32),
-                ("use_graph", C.c_int32), ("stream", C.c_void_p), ("profile", C.c_int32), ("precision", C.c_int32)]
+                ("use_graph", C.c_int32), ("stream", C.c_void_p), ("profile", C.c_int32), ("precision", C.c_int32),
+                ("T_stop_GeV", C.c_double), ("kappaT2", C.c_void_p), ("tauJT", C.c_void_p), ("Jv", C.c_void_p)]
 
 
 class FieldBufs(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ["x", "u", "S", "Nq", "Bv", "Pv", "sigstar", "s", "nq", "T", "mu", "p",
-                                          "e", "Pi", "status", "nnb", "cell", "guess"]] + [("on_device", C.c_int32)]
+                                          "e", "Pi", "status", "nnb", "cell", "guess"]] + [("on_device", C.c_int32),
+                                                                                          ("Jv", C.c_void_p)]
 
 
 class Totals(C.Structure):
@@ -134,6 +137,9 @@ def lib():
             "sph_set_partons": (i32, [vp, i64, vp, vp, C.c_double, C.c_double]),
             "sph_set_eos_backup": (i32, [vp, i32, C.c_double, C.c_double]),
             "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
+            "sph_server_profile": (i32, [vp, i32]),
+            "sph_measure_fma_peak": (i32, [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "sph_server_kernel_times": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32)]),
             "sph_eos_build_inverse": (i32, [vp, i32, i32, i32, i32, C.c_double]),
             "sph_set_eos_mode": (i32, [vp, i32]),
             "sph_read_freezeout": (i32, [vp, i64, vp, vp, C.POINTER(i64)]),
@@ -216,6 +222,24 @@ def sph_kernel_times(h):
     _check(lib().sph_kernel_times(h, 16, names, ms.ctypes.data, nl.ctypes.data, C.byref(cnt)))
     raw = names.raw
     return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
+
+
+def sph_server_kernel_times(h):
+    """{group: (milliseconds, stages timed)} of the server's sampled batch steps."""
+    names = C.create_string_buffer(32 * 16)
+    ms = np.zeros(16)
+    nl = np.zeros(16, dtype=np.int64)
+    cnt = C.c_int32(0)
+    _check(lib().sph_server_kernel_times(h, 16, names, ms.ctypes.data, nl.ctypes.data, C.byref(cnt)))
+    raw = names.raw
+    return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(nl[k])) for k in range(cnt.value)}
+
+
+def sph_measure_fma_peak(fp64: bool, reps: int = 5):
+    """(GFLOP/s, best launch ms) of the device's FP64 or FP32 multiply-add chains."""
+    g, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().sph_measure_fma_peak(int(bool(fp64)), int(reps), C.byref(g), C.byref(ms)))
+    return g.value, ms.value
 
 
 def sph_eos_build_inverse(eos, grid):
@@ -337,6 +361,17 @@ def event_desc(ev):
     tr = ev.transport
     d.eta_over_s, d.zeta_peak, d.zeta_T_GeV, d.zeta_w_GeV = tr.eta_over_s, tr.zeta_peak, tr.zeta_T_GeV, tr.zeta_w_GeV
     d.tau_pi_coef, d.tau_Pi_ratio, d.cs2_cap = tr.tau_pi_coef, tr.tau_Pi_ratio, tr.cs2_cap
+    d.T_stop_GeV = float(getattr(tr, "T_stop_GeV", 0.0) or 0.0)
+    df = getattr(ev, "diffusion", None)
+    if df is not None:
+        kap = _f64(np.asarray(df.kappaT2, dtype=np.float64).reshape(9))
+        tj = _f64(np.asarray(df.tauJT, dtype=np.float64).reshape(3))
+        keep += [kap, tj]
+        d.kappaT2, d.tauJT = kap.ctypes.data, tj.ctypes.data
+        if df.Jv is not None:
+            jv = _f64(np.asarray(df.Jv, dtype=np.float64).reshape(6, ev.n))
+            keep.append(jv)
+            d.Jv = jv.ctypes.data
     return d, keep
 
 
@@ -401,6 +436,13 @@ class GpuServer:
     def drain(self, timeout_s: float = 0.0):
         sph_server_drain(self.h, timeout_s)
 
+    def profile(self, every: int):
+        """Sampled per-kernel-group timing of every every-th batch step (0: off)."""
+        _check(lib().sph_server_profile(self.h, int(every)))
+
+    def kernel_times(self):
+        return sph_server_kernel_times(self.h)
+
     def free(self):
         if self.h is not None:
             sph_server_free(self.h)
@@ -461,7 +503,8 @@ class GpuEvent:
         shapes = {"X": (self.dim, "x"), "U": (self.dim, "u"), "S": (1, "S"), "NQ": (3, "Nq"), "BV": (1, "Bv"),
                   "PV": (self.npi, "Pv"), "SIGMA_STAR": (1, "sigstar"), "S_DENS": (1, "s"), "N_DENS": (3, "nq"),
                   "T": (1, "T"), "MU": (3, "mu"), "P": (1, "p"), "E": (1, "e"), "PI_BULK": (1, "Pi"),
-                  "STATUS": (1, "status"), "NNB": (1, "nnb"), "CELL": (self.dim, "cell"), "GUESS": (4, "guess")}
+                  "STATUS": (1, "status"), "NNB": (1, "nnb"), "CELL": (self.dim, "cell"), "GUESS": (4, "guess"),
+                  "JV": (6, "Jv")}
         b = FieldBufs()
         out, mask = {}, 0
         for nm in names:

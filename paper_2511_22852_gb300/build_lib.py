@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsph_gb300.so")
 SOURCES = ["cells.cu", "density_eos.cu", "gradient_eom.cu", "step3d.cu", "mixed2d.cu", "api.cu", "noalloc.cu",
-           "serve.cu", "mixed3d.cu", "freezeout.cu", "pairs2d.cu", "pairs3d.cu"]
+           "serve.cu", "mixed3d.cu", "freezeout.cu", "pairs2d.cu", "pairs3d.cu", "peak.cu", "diffusion.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

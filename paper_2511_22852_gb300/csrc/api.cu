@@ -74,6 +74,10 @@ struct sph_event {
     bool charges = false;
     double *d_parton_q = nullptr;
     double *NqS[2] = {nullptr, nullptr};
+    // BSQ diffusion (2+1D): kappa/T^2, tau T, and the per-stage scratch of the diffusion passes
+    int diff = 0;
+    double kapT2[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tauJT[3] = {0, 0, 0};
+    double *dinp = nullptr, *dal = nullptr, *dout = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     DevScalars *sc = nullptr;
@@ -179,6 +183,12 @@ static EvView make_view(const sph_event *ev)
     v.tracks = ev->d_tracks;
     v.track_norm = ev->track_norm;
     v.track_i2s2 = ev->track_i2s2;
+    v.diff = ev->diff;
+    for (int k = 0; k < 9; ++k) v.kapT2[k] = ev->kapT2[k];
+    for (int q = 0; q < 3; ++q) v.tauJT[q] = ev->tauJT[q];
+    v.dinp = ev->dinp;
+    v.dal = ev->dal;
+    v.dout = ev->dout;
     return v;
 }
 
@@ -235,6 +245,7 @@ static void enqueue_step(sph_event *ev)
     launch_eos(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
     if (ev->fo_on)
         launch_freezeout(v, ev->e_fo, ev->Y[1], ev->id[1], ev->dens, ev->eosf, ev->eprev[1], ev->cb, ev->fo, st);
+    launch_diffusion(v, 1, ev->Y[1], ev->dens, ev->eosf, ev->status, ev->cb, st);
     mark(ev, G_EOS, 1, 1);
     mark(ev, G_GRADIENT, 1, 0);
     launch_gradient(v, 1, ev->Y[1], ev->gin, ev->cb, ev->gout, st);
@@ -270,6 +281,7 @@ static void enqueue_step(sph_event *ev)
     mark(ev, G_DENSITY, 2, 1);
     mark(ev, G_EOS, 2, 0);
     launch_eos(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->gin, ev->status, ev->wpart, ev->guess_in, ev->wguess, st);
+    launch_diffusion(v, 2, ev->Y1[1], ev->dens, ev->eosf, ev->status, ev->cb, st);
     mark(ev, G_EOS, 2, 1);
     mark(ev, G_GRADIENT, 2, 0);
     launch_gradient(v, 2, ev->Y1[1], ev->gin, ev->cb, ev->gout, st);
@@ -483,6 +495,19 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     ev->viscous = d->viscous ? 1 : 0;
     ev->npi = ev->dim == 2 ? 3 : 5;
     ev->nv = 2 * ev->dim + 2 + ev->npi;
+    if (d->kappaT2) {
+        bool ok = ev->dim == 2 && d->tauJT != nullptr;
+        for (int k = 0; ok && k < 9; ++k) ok = std::isfinite(d->kappaT2[k]);
+        for (int q = 0; ok && q < 3; ++q) ok = std::isfinite(d->tauJT[q]) && d->tauJT[q] > 0.0;
+        if (!ok) {
+            sph_free_event(ev);
+            return fail(SPH_ERR_ARG, "diffusion needs dim = 2, finite kappa/T^2 and positive tau T");
+        }
+        ev->diff = 1;
+        for (int k = 0; k < 9; ++k) ev->kapT2[k] = d->kappaT2[k];
+        for (int q = 0; q < 3; ++q) ev->tauJT[q] = d->tauJT[q];
+        ev->nv += 6;  // J^i_q / sigma
+    }
     ev->ngin = ev->dim == 2 ? kNGin : 12;
     ev->ngout = ev->dim == 2 ? kNGout : 12;
     ev->h = d->h;
@@ -514,6 +539,7 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     ev->tr.tau_pi_coef = d->tau_pi_coef;
     ev->tr.tau_Pi_ratio = d->tau_Pi_ratio;
     ev->tr.cs2_cap = d->cs2_cap > 0.0 ? d->cs2_cap : 1.0;
+    ev->tr.T_stop_GeV = d->T_stop_GeV > 0.0 ? d->T_stop_GeV : 0.0;
     if (const char *t = getenv("SPH_WAIT_LIMIT_S")) ev->timeout_s = atof(t);
     auto bail = [&](sph_status s) {
         std::string keep = g_err;
@@ -623,6 +649,13 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
     ev->nwblk = eos_block_count(n > 0 ? n : 1, ev->dim);
     AL(ev->wpart, sizeof(double) * (size_t)ev->nwblk);
     AL(ev->scratch, dv * std::max(std::max(ev->nv, kNEos), ev->ngout));
+    if (ev->diff) {  // the charges evolve (the lab charges); the diffusion passes' scratch
+        for (int k = 0; k < 2; ++k) AL(ev->NqS[k], dv * 3);
+        AL(ev->dinp, dv * 9);
+        AL(ev->dal, dv * 12);
+        AL(ev->dout, dv * 9);
+        ev->charges = true;
+    }
     AL(ev->ntot, sizeof(double) * (8 + 3 * 256));
     AL(ev->tot, sizeof(double) * (8 + 3 * 256));
 #undef AL
@@ -637,6 +670,10 @@ sph_status sph_init_event(sph_event **out, const sph_event_desc *d, const sph_eo
         else CK(cudaMemsetAsync(ev->Y[0] + (size_t)(2 * ev->dim + 1) * n, 0, dn, st));
         if (d->Pv) CK(cudaMemcpyAsync(ev->Y[0] + (size_t)(2 * ev->dim + 2) * n, d->Pv, dn * ev->npi, k, st));
         else CK(cudaMemsetAsync(ev->Y[0] + (size_t)(2 * ev->dim + 2) * n, 0, dn * ev->npi, st));
+        if (ev->diff) {
+            if (d->Jv) CK(cudaMemcpyAsync(ev->Y[0] + (size_t)kJRow * n, d->Jv, dn * 6, k, st));
+            else CK(cudaMemsetAsync(ev->Y[0] + (size_t)kJRow * n, 0, dn * 6, st));
+        }
         CK(cudaMemcpyAsync(ev->Nq[0], d->Nq, dn * 3, k, st));
         CK(cudaMemcpyAsync(ev->Nq_orig, d->Nq, dn * 3, k, st));
         CK(cudaMemsetAsync(ev->wguess, 0, dn * 4, st));
@@ -888,6 +925,7 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         {SPH_F_BV, o ? o->Bv : nullptr, ev->Y[0] + (2 * ev->dim + 1) * N, 1, 1},
         {SPH_F_PV, o ? o->Pv : nullptr, ev->Y[0] + (2 * ev->dim + 2) * N, ev->npi, 1},
         {SPH_F_GUESS, o ? o->guess : nullptr, ev->wguess, 4, 1},
+        {SPH_F_JV, o ? o->Jv : nullptr, ev->Y[0] + (size_t)kJRow * N, ev->diff ? 6 : 0, 1},
         {SPH_F_SIGMA_STAR, o ? o->sigstar : nullptr, dens, 1, 0},
         {SPH_F_S_DENS, o ? o->s : nullptr, dens + N, 1, 0},
         {SPH_F_N_DENS, o ? o->nq : nullptr, dens + 2 * N, 3, 0},
@@ -896,6 +934,7 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
         {SPH_F_P, o ? o->p : nullptr, eo + 4 * N, 1, 0},
         {SPH_F_E, o ? o->e : nullptr, eo + 5 * N, 1, 0},
     };
+    if ((mask & SPH_F_JV) && !ev->diff) return fail(SPH_ERR_ARG, "the event has no diffusion currents");
     for (auto &r : rows) {
         if (!(mask & r.bit)) continue;
         if (!r.dst) return fail(SPH_ERR_ARG, "requested field has a null destination");
@@ -1339,7 +1378,9 @@ sph_status sph_write_state(sph_event *ev, uint64_t mask, const sph_field_bufs *i
         {SPH_F_S, in->S, (size_t)2 * ev->dim, 1},
         {SPH_F_BV, in->Bv, (size_t)2 * ev->dim + 1, 1},
         {SPH_F_PV, in->Pv, (size_t)2 * ev->dim + 2, ev->npi},
+        {SPH_F_JV, in->Jv, (size_t)kJRow, ev->diff ? 6 : 0},
     };
+    if ((mask & SPH_F_JV) && !ev->diff) return fail(SPH_ERR_ARG, "the event has no diffusion currents");
     for (auto &r : rows) {
         if (!(mask & r.bit)) continue;
         if (!r.src) return fail(SPH_ERR_ARG, "masked field has a null source");

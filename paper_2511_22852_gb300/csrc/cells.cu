@@ -20,7 +20,10 @@ namespace {
 __global__ void k_bbox_init(DevScalars *sc)
 {
     if (threadIdx.x < 3) sc->xmin_enc[threadIdx.x] = 0x7FF0000000000000LL;  // +inf
-    if (threadIdx.x == 0) sc->pair_flag = 0u;
+    if (threadIdx.x == 0) {
+        sc->pair_flag = 0u;
+        sc->eos_claim = 0u;
+    }
 }
 
 __global__ void k_bbox(EvView v, const double *__restrict__ y)

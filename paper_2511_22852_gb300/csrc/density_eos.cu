@@ -153,33 +153,39 @@ __global__ void __launch_bounds__(32 * kWarps) k_density2(EvView v, const double
     }
 }
 
-// EoS pass, 2+1D, one particle: rest-frame densities, inversion, and the per-particle inputs
-// of the gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} - v^j pi^{tau i},
-// and u^j / sigma*; returns the particle's longitudinal work rate (p + Pi + tau^2 pi^{eta eta}) / sigma*.
-// Rows are n apart; the EoS work done is added to w.
-// gprev (may be NULL): an earlier table solution, one step before guess_in; when both are table
-// solutions the guess is extrapolated linearly, 2 guess_in - gprev (kept if inside the table)
-__device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E, int stage, size_t n, size_t a,
-                                                const double *__restrict__ y, double *__restrict__ dens,
-                                                double *__restrict__ eos, double *__restrict__ gin,
-                                                uint32_t *__restrict__ status, const double *__restrict__ guess_in,
-                                                double *__restrict__ guess_out, EosWork &w,
-                                                const double *__restrict__ gprev = nullptr)
+// EoS pass, 2+1D, one particle, in two halves around the inversion.
+// eos2_load: the rest-frame densities (written back to dens) and the warm start of the Newton
+// iteration: this particle's previous-stage table solution; with gprev (an earlier table
+// solution, one step before guess_in) both table solutions extrapolate linearly to
+// 2 guess_in - gprev (kept if inside the table).  keep receives guess_in as read.
+__device__ __forceinline__ void eos2_load(const EvView &v, const EosDev &E, int stage, size_t n, size_t a,
+                                          double *__restrict__ dens, const double *__restrict__ guess_in,
+                                          const double *__restrict__ gprev, double &s, double nq[3], double gs[4],
+                                          double keep[4], const double *__restrict__ y)
 {
-    double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-    double sqrtg = v.milne ? tau : 1.0;
-    double sig_star = dens[a];
-    double u0 = dens[5 * n + a];
-    double vol = u0 * sqrtg;
-    // one reciprocal per shared denominator (an FP64 division is a multi-instruction sequence)
-    const double ivol = 1.0 / vol, isig = 1.0 / sig_star;
-    double s = dens[n + a] * ivol;
-    double nq[3] = {dens[2 * n + a] * ivol, dens[3 * n + a] * ivol, dens[4 * n + a] * ivol};
-    dens[n + a] = s;
-    for (int q = 0; q < 3; ++q) dens[(2 + q) * n + a] = nq[q];
-    double gs[4];
+    const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+    const double sqrtg = v.milne ? tau : 1.0;
+    const double vol = dens[5 * n + a] * sqrtg;
+    const double ivol = 1.0 / vol;
+    s = dens[n + a] * ivol;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) gs[k] = guess_in[k * n + a];
+    for (int q = 0; q < 3; ++q) nq[q] = dens[(2 + q) * n + a] * ivol;
+    if (v.diff) {
+        // the kernel sums of the lab charges give the lab density sqrt(-g) (n u^0 + J^0): the rest
+        // frame n_q = (sum / sqrt(-g) - J^0_q) / u^0 with J^0 = u.J / u^0 and J^i = sigma J^i/sigma
+        const double u0 = dens[5 * n + a], sigma = dens[a] * ivol;
+        const double ux = y[2 * n + a], uy = y[3 * n + a];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double J0 = (ux * sigma * y[(kJRow + 2 * q) * n + a] + uy * sigma * y[(kJRow + 2 * q + 1) * n + a]) / u0;
+            nq[q] = (dens[(2 + q) * n + a] / sqrtg - J0) / u0;
+        }
+    }
+    dens[n + a] = s;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dens[(2 + q) * n + a] = nq[q];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) keep[k] = gs[k] = guess_in[k * n + a];
     if (gprev && gs[0] > 0.0 && gprev[a] > 0.0) {
         double ge[4];
 #pragma unroll
@@ -188,10 +194,24 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
 #pragma unroll
             for (int k = 0; k < 4; ++k) gs[k] = ge[k];
     }
-    bool used = false;
-    EosOut o = eos_invert(E, v.tr.cs2_cap, s, nq, gs, used, w);
-    // warm start of the next stage: the table solution, or minus the closed-form T (none after
-    // the backup EoS or without a solution)
+}
+
+// eos2_store: the EoS outputs, the next stage's warm start (the table solution, or minus the
+// closed-form T; none after the backup EoS or without a solution), and the per-particle inputs
+// of the gradient pass: X^{ji} / sigma*^2 with X^{ji} = (p + Pi) delta^{ji} + pi^{ji} -
+// v^j pi^{tau i}, and u^j / sigma*.  Returns the particle's longitudinal work rate
+// (p + Pi + tau^2 pi^{eta eta}) / sigma*.
+__device__ __forceinline__ double eos2_store(const EvView &v, int stage, size_t n, size_t a,
+                                             const double *__restrict__ y, const double *__restrict__ dens,
+                                             double *__restrict__ eos, double *__restrict__ gin,
+                                             uint32_t *__restrict__ status, double *__restrict__ guess_out,
+                                             const EosOut &o, bool used)
+{
+    const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+    const double sqrtg = v.milne ? tau : 1.0;
+    const double sig_star = dens[a];
+    const double u0 = dens[5 * n + a];
+    const double ivol = 1.0 / (u0 * sqrtg), isig = 1.0 / sig_star;
     guess_out[a] = used ? o.T : ((o.st & (PST_NOCONV | PST_NONFINITE | PST_BACKUP)) ? 0.0 : -o.T);
 #pragma unroll
     for (int q = 0; q < 3; ++q) guess_out[(1 + q) * n + a] = used ? o.mu[q] : 0.0;
@@ -203,10 +223,10 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
     eos[6 * n + a] = o.ps;
     for (int q = 0; q < 3; ++q) eos[(7 + q) * n + a] = o.pn[q];
     eos[10 * n + a] = o.cs2;
-    double ux = y[2 * n + a], uy = y[3 * n + a];
+    const double ux = y[2 * n + a], uy = y[3 * n + a];
     const double iu0 = ivol * sqrtg;
-    double vx = ux * iu0, vy = uy * iu0;
-    double sigma = sig_star * ivol;
+    const double vx = ux * iu0, vy = uy * iu0;
+    const double sigma = sig_star * ivol;
     double Pi = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
     if (v.tr.viscous) {
         Pi = sigma * y[5 * n + a];
@@ -214,103 +234,146 @@ __device__ __forceinline__ double eos2_particle(const EvView &v, const EosDev &E
         pxy = sigma * y[7 * n + a];
         pyy = sigma * y[8 * n + a];
     }
-    double ptx = vx * pxx + vy * pxy;  // pi^{tau x}
-    double pty = vx * pxy + vy * pyy;  // pi^{tau y}
-    double inv2 = isig * isig;
-    double P = o.p + Pi;
-    gin[a] = (P + pxx - vx * ptx) * inv2;                 // X^{xx}
-    gin[n + a] = (pxy - vx * pty) * inv2;                 // X^{xy}  (j = x, i = y)
-    gin[2 * n + a] = (pxy - vy * ptx) * inv2;             // X^{yx}  (j = y, i = x)
-    gin[3 * n + a] = (P + pyy - vy * pty) * inv2;         // X^{yy}
+    const double ptx = vx * pxx + vy * pxy;  // pi^{tau x}
+    const double pty = vx * pxy + vy * pyy;  // pi^{tau y}
+    const double inv2 = isig * isig;
+    const double P = o.p + Pi;
+    gin[a] = (P + pxx - vx * ptx) * inv2;          // X^{xx}
+    gin[n + a] = (pxy - vx * pty) * inv2;          // X^{xy}  (j = x, i = y)
+    gin[2 * n + a] = (pxy - vy * ptx) * inv2;      // X^{yx}  (j = y, i = x)
+    gin[3 * n + a] = (P + pyy - vy * pty) * inv2;  // X^{yy}
     gin[4 * n + a] = ux * isig;
     gin[5 * n + a] = uy * isig;
     double wcontrib = 0.0;
     if (v.milne) {
-        double ptt = vx * ptx + vy * pty;
-        double t2pee = ptt - pxx - pyy;  // tau^2 pi^{eta eta} from tracelessness
+        const double ptt = vx * ptx + vy * pty;
+        const double t2pee = ptt - pxx - pyy;  // tau^2 pi^{eta eta} from tracelessness
         wcontrib = (P + t2pee) * isig;
     }
-    warp_or(&v.sc->status_or, o.st);
     return wcontrib;
 }
 
-// One warp per block: the pass holds 40k-particle events in a fraction of a wave, and with
-// blocks of one warp the blocks (and the varying Newton work) spread more evenly over the SMs.
-__global__ void __launch_bounds__(32, 12) k_eos2(EvView v, int stage, const double *__restrict__ y,
-                                             double *__restrict__ dens, double *__restrict__ eos,
-                                             double *__restrict__ gin, uint32_t *__restrict__ status,
-                                             double *__restrict__ wpart, const double *__restrict__ guess_in,
-                                             double *__restrict__ guess_out)
+// Plain and mixed single-event forms: persistent blocks of kEosWarps warps run the lane-refill
+// pass (eos_lanes) over the event's particles; the work rate goes to wpart[a] (summed in a fixed
+// order by the work kernel), the work counters and the status bits are warp-aggregated.
+constexpr int kEosWarps = 4;
+#ifndef SPH_EOS_BLOCKS_PER_SM
+#define SPH_EOS_BLOCKS_PER_SM 3
+#endif
+constexpr int kEosBlocksPerSM = SPH_EOS_BLOCKS_PER_SM;  // resident blocks per SM (the register budget)
+
+struct Eos2Ctx {
+    const EvView &v;
+    int stage;
+    size_t n;
+    const double *__restrict__ y;
+    double *__restrict__ dens, *__restrict__ eos, *__restrict__ gin, *__restrict__ wpart, *__restrict__ guess_out;
+    uint32_t *__restrict__ status;
+    const double *__restrict__ guess_in;
+    unsigned st_or;
+    __device__ bool load(int a, double &s, double nq[3], double g[4], double &cap)
+    {
+        double keep[4];
+        cap = v.tr.cs2_cap;
+        eos2_load(v, v.eos, stage, n, (size_t)a, dens, guess_in, nullptr, s, nq, g, keep, y);
+        return true;
+    }
+    __device__ void store(int a, const EosOut &o, bool used)
+    {
+        wpart[a] = eos2_store(v, stage, n, (size_t)a, y, dens, eos, gin, status, guess_out, o, used);
+        st_or |= o.st;
+    }
+};
+
+__global__ void __launch_bounds__(32 * kEosWarps, kEosBlocksPerSM) k_eos2(EvView v, int stage, const double *__restrict__ y,
+                                                         double *__restrict__ dens, double *__restrict__ eos,
+                                                         double *__restrict__ gin, uint32_t *__restrict__ status,
+                                                         double *__restrict__ wpart,
+                                                         const double *__restrict__ guess_in,
+                                                         double *__restrict__ guess_out)
 {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    double wcontrib = 0.0;
+    Eos2Ctx ctx{v, stage, (size_t)v.n, y, dens, eos, gin, wpart, guess_out, status, guess_in, 0u};
     EosWork w = {0u, 0u, 0u};
-    if (a < v.n)
-        wcontrib = eos2_particle(v, v.eos, stage, (size_t)v.n, (size_t)a, y, dens, eos, gin, status, guess_in,
-                                 guess_out, w);
-    // work counters (warp-aggregated) and the deterministic block sum of the work rate
-    unsigned wres = __reduce_add_sync(0xFFFFFFFFu, w.resid);
-    unsigned wsol = __reduce_add_sync(0xFFFFFFFFu, w.solve);
-    unsigned wg = __reduce_add_sync(0xFFFFFFFFu, w.g);
+    eos_lanes(v.eos, &v.sc->eos_claim, v.n, ctx, w);
+    const unsigned wres = __reduce_add_sync(0xFFFFFFFFu, w.resid);
+    const unsigned wsol = __reduce_add_sync(0xFFFFFFFFu, w.solve);
+    const unsigned wg = __reduce_add_sync(0xFFFFFFFFu, w.g);
+    const unsigned sor = __reduce_or_sync(0xFFFFFFFFu, ctx.st_or);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&v.sc->eos_resid, (unsigned long long)wres);
         atomicAdd(&v.sc->eos_solve, (unsigned long long)wsol);
         atomicAdd(&v.sc->eos_g, (unsigned long long)wg);
+        if (sor) atomicOr(&v.sc->status_or, sor);
     }
-    for (int o = 16; o > 0; o >>= 1) wcontrib += __shfl_xor_sync(0xFFFFFFFFu, wcontrib, o);
-    if (threadIdx.x == 0) wpart[blockIdx.x] = wcontrib;
 }
 
-// Serving form: the same EoS pass over the segmented arena.  Persistent one-warp blocks claim
-// chunks of 32 particles from a counter (the Newton work per particle varies, so a static split,
-// or coarser chunks, leave a tail).  A warp never straddles two events, so the work-rate partial
-// of every warp of an event's range goes to wpart[a / 32] and the per-event counters are
-// warp-aggregated.
-__global__ void __launch_bounds__(32, 12) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
+// Serving form: the same pass over the segmented arena (particles of every event active in this
+// stage; padding and inactive slots are skipped).  A lane's particles may belong to different
+// events: the per-event work counters and status bits are gathered per block in shared memory
+// and flushed once.  Stage 2 starts from the stage-1 solutions of this and the previous step,
+// extrapolated to the later time, and keeps this step's for the next.
+struct SegEosCtx {
+    const Arena &A;
+    const BatchTable *T;
+    int stage;
+    size_t P;
+    const double *__restrict__ y;
+    unsigned int *sh;  // [kMaxSlots][4]: table evaluations, solves, closed-form evaluations, status bits
+    EosWork *w;
+    EosWork w0;
+    int slot;
+    double keep[4];
+    __device__ bool load(int a, double &s, double nq[3], double g[4], double &cap)
+    {
+        const int sl = A.segid[a];
+        if (sl < 0 || !seg_active(T, sl, stage, false)) return false;
+        const SegSlot q = T->slots[sl];
+        if (a - q.off >= q.n) return false;
+        slot = sl;
+        w0 = *w;
+        cap = A.segv[sl].tr.cs2_cap;
+        eos2_load(A.segv[sl], A.segv[sl].eos, stage, P, (size_t)a, A.dens, A.guess_in,
+                  stage == 2 ? A.xs1[0] : nullptr, s, nq, g, keep, y);
+        return true;
+    }
+    __device__ void store(int a, const EosOut &o, bool used)
+    {
+        A.wpart[a] = eos2_store(A.segv[slot], stage, P, (size_t)a, y, A.dens, A.eosf, A.gin, A.status, A.wguess, o,
+                                used);
+        if (stage == 2)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) A.xs1[0][k * P + a] = keep[k];
+        if (T->slots[slot].mode == SLOT_STEP) {  // float copies of the gradient-pass inputs
+            const double *g = A.gin;
+            A.fX[a] = make_float4((float)g[a], (float)g[P + a], (float)g[2 * P + a], (float)g[3 * P + a]);
+            A.fU[a] = make_float2((float)g[4 * P + a], (float)g[5 * P + a]);
+        }
+        unsigned int *c = sh + 4 * slot;
+        atomicAdd_block(c, w->resid - w0.resid);
+        atomicAdd_block(c + 1, w->solve - w0.solve);
+        atomicAdd_block(c + 2, w->g - w0.g);
+        if (o.st) atomicOr_block(c + 3, o.st);
+    }
+};
+
+__global__ void __launch_bounds__(32 * kEosWarps, kEosBlocksPerSM) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
 {
+    __shared__ unsigned int sh[kMaxSlots * 4];
+    for (int i = threadIdx.x; i < kMaxSlots * 4; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
     const BatchTable *T = A.tab;
-    const int hi = T->hi;
-    const size_t P = (size_t)A.P;
-    for (;;) {
-        int chunk = 0;
-        if (threadIdx.x == 0) chunk = (int)atomicAdd(&A.claim[CLAIM_EOS], 1u);
-        const int base = __shfl_sync(0xFFFFFFFFu, chunk, 0) * 32;
-        if (base >= hi) break;
-        const int a = base + threadIdx.x;
-        const int s = A.segid[a];  // warp-uniform: ranges are multiples of 256 and hi is a range end
-        if (s < 0 || !seg_active(T, s, stage, false)) continue;
-        const SegSlot sl = T->slots[s];
-        double wc = 0.0;
-        EosWork w = {0u, 0u, 0u};
-        if (a - sl.off < sl.n) {
-            // stage 2 starts from the stage-1 solutions of this and the previous step,
-            // extrapolated to the later time; then keeps this step's for the next
-            const double *gp = stage == 2 ? A.xs1[0] : nullptr;
-            double keep[4];
-            if (stage == 2)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) keep[k] = A.guess_in[k * P + a];
-            wc = eos2_particle(A.segv[s], E, stage, P, (size_t)a, y, A.dens, A.eosf, A.gin, A.status, A.guess_in,
-                               A.wguess, w, gp);
-            if (stage == 2)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) A.xs1[0][k * P + a] = keep[k];
-            if (T->slots[s].mode == SLOT_STEP) {  // float copies of the gradient-pass inputs
-                const double *g = A.gin;
-                A.fX[a] = make_float4((float)g[a], (float)g[P + a], (float)g[2 * P + a], (float)g[3 * P + a]);
-                A.fU[a] = make_float2((float)g[4 * P + a], (float)g[5 * P + a]);
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xFFFFFFFFu, wc, o);
-        const unsigned wres = __reduce_add_sync(0xFFFFFFFFu, w.resid);
-        const unsigned wsol = __reduce_add_sync(0xFFFFFFFFu, w.solve);
-        const unsigned wg = __reduce_add_sync(0xFFFFFFFFu, w.g);
-        if ((threadIdx.x & 31) == 0) {
-            A.wpart[a >> 5] = wc;
-            atomicAdd(&A.sc[s].eos_resid, (unsigned long long)wres);
-            atomicAdd(&A.sc[s].eos_solve, (unsigned long long)wsol);
-            atomicAdd(&A.sc[s].eos_g, (unsigned long long)wg);
-        }
+    EosWork w = {0u, 0u, 0u};
+    SegEosCtx ctx{A, T, stage, (size_t)A.P, y, sh, &w, w, -1, {0.0, 0.0, 0.0, 0.0}};
+    // E is the server's EoS (every event's view carries the same)
+    eos_lanes(E, &A.claim[CLAIM_EOS], T->hi, ctx, w);
+    __syncthreads();
+    const int ns = T->nslots;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const unsigned int *c = sh + 4 * s;
+        if (c[0]) atomicAdd(&A.sc[s].eos_resid, (unsigned long long)c[0]);
+        if (c[1]) atomicAdd(&A.sc[s].eos_solve, (unsigned long long)c[1]);
+        if (c[2]) atomicAdd(&A.sc[s].eos_g, (unsigned long long)c[2]);
+        if (c[3]) atomicOr(&A.sc[s].status_or, c[3]);
     }
 }
 
@@ -345,11 +408,15 @@ void launch_eos(const EvView &v, int stage, const double *y, const double *dens,
         launch_eos3(v, stage, y, dens, eos, gin, status, wpart, guess_in, guess_out, st);
         return;
     }
-    k_eos2<<<nblk(v.n, 32), 32, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart, guess_in,
-                                         guess_out);
+    // persistent: resident blocks on every SM, or fewer for a small event (a lane per particle)
+    const int grid = std::max(1, std::min(nblk(v.n, 32 * kEosWarps), kEosBlocksPerSM * device_sm_count()));
+    k_eos2<<<grid, 32 * kEosWarps, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart,
+                                              guess_in, guess_out);
 }
 
-int eos_block_count(int n, int dim) { return nblk(n, dim == 2 ? 32 : 64); }
+// entries of the work-rate partials: one per particle in 2D (the lane-refill pass), one per
+// 64-particle block in 3D
+int eos_block_count(int n, int dim) { return dim == 2 ? n : nblk(n, 64); }
 
 int device_sm_count()
 {
@@ -404,7 +471,9 @@ void launch_inverse_build(const EosDev &E, double *inv, long long nnodes, cudaSt
 
 void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st)
 {
-    k_eos2_seg<<<grid, 32, 0, st>>>(A, E, stage, y);
+    k_eos2_seg<<<grid, 32 * kEosWarps, 0, st>>>(A, E, stage, y);
 }
+
+int eos_seg_grid(int sms) { return kEosBlocksPerSM * sms; }
 
 }  // namespace sphg

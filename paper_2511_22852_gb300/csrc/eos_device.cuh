@@ -115,9 +115,10 @@ __device__ uint32_t an_invert(const EosDev &E, double s, const double *n, double
 // four (T, mu_B) corner patches, then mu_B, then T), carrying the partial derivatives along
 __device__ __forceinline__ void locate(double x, double x0, double inv, int nx, int &i, double &t)
 {
-    double r = (x - x0) * inv;
-    int k = (int)floor(r);
-    k = max(0, min(k, nx - 2));
+    const double r = (x - x0) * inv;
+    // the cell below r: truncation toward zero is the floor for r >= 0, and the clamp to
+    // [0, nx - 2] takes every r < 0 to cell 0 as the floor would (no rounding instruction)
+    const int k = max(0, min(__double2int_rz(r), nx - 2));
     i = k;
     t = r - (double)k;
 }
@@ -215,22 +216,27 @@ __device__ void tab_eval(const EosDev &E, const double *x, double sn[4], double 
 // moves; each pivot is inverted once (FP64 division is a multi-instruction sequence on
 // the 1:64 FP64 pipe) and the back substitution multiplies by it.  Returns false on a
 // zero or non-finite pivot.
+// magnitude of a double as an integer: for non-negative doubles the IEEE bit patterns order as
+// the values do (NaN above infinity), so the pivot search compares integers
+__device__ __forceinline__ long long mag_bits(double v) { return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL; }
+constexpr long long kInfBits = 0x7FF0000000000000LL;
+
 __device__ __forceinline__ bool solve4(double A[4][4], double b[4])
 {
     double ipv[4];  // reciprocal pivots, reused by the back substitution
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int piv = c;
-        double best = fabs(A[c][c]);
+        long long best = mag_bits(A[c][c]);
 #pragma unroll
         for (int r = c + 1; r < 4; ++r) {
-            double v = fabs(A[r][c]);
+            const long long v = mag_bits(A[r][c]);
             if (v > best) {
                 best = v;
                 piv = r;
             }
         }
-        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (best == 0 || best >= kInfBits) return false;  // zero, infinite or NaN pivot
 #pragma unroll
         for (int r = c + 1; r < 4; ++r) {
             if (piv == r) {
@@ -265,10 +271,25 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4])
     return true;
 }
 
+// order-preserving integer key of a double (its own inverse): negative values have their
+// magnitude bits flipped, so signed integer comparisons order keys as the values
+__device__ __forceinline__ long long okey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double clamp_key(double v, double lo, double hi)
+{
+    const long long k = min(max(okey(v), okey(lo)), okey(hi));
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+}
+
+// the point into the table's box (exact: a comparison and a selection per bound, on integers)
 __device__ __forceinline__ void clamp4(const EosDev &E, double *x)
 {
-    x[0] = fmin(fmax(x[0], E.T0), E.Tmax);
-    for (int q = 0; q < 3; ++q) x[1 + q] = fmin(fmax(x[1 + q], E.mu0[q]), E.mumax[q]);
+    x[0] = clamp_key(x[0], E.T0, E.Tmax);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) x[1 + q] = clamp_key(x[1 + q], E.mu0[q], E.mumax[q]);
 }
 
 __device__ double resid(const EosDev &E, const double *x, double s, double inv_s, const double *n, double r[4],
@@ -558,6 +579,242 @@ __device__ EosOut eos_invert(const EosDev &E, double cs2_cap, double s, const do
     return o;
 }
 
+// ---------------------------------------------------------------------------
+// Lane-refill EoS pass.  The table Newton's work varies from particle to particle (iterations,
+// line-search trials, the polishing step), so a warp that inverts 32 particles together leaves
+// its finished lanes idle until the slowest is done, and every FP64 instruction of the 1:64 pipe
+// costs the whole warp.  Here each lane holds its own particle and claims the next one as soon
+// as its own is done.  One trip through the loop is, for every lane that holds a particle, one
+// table evaluation at its trial point (s, n_q, their Jacobian and p) and at most one 4x4 solve:
+// the Newton step, the polishing step, or, once converged, the transposed system of the EoS
+// derivatives (p_s, p_n) = H^-T (s, n) -- so the warp's lanes evaluate and solve together
+// whatever stage of the iteration their particles are at.  The iteration per particle is the
+// damped Newton of tab_newton (the same iterates, with the residual and the step in grid-step
+// units: the scaling changes rounding only) followed by the derivative solve of eos_invert.
+// Particles whose warm start is not a table solution inside the table, whose table Newton
+// fails, or when the offline inverter is on, take eos_invert inline (a divergent, rarer path).
+//
+// Ctx supplies  __device__ bool load(int a, double &s, double n[3], double g[4], double &cs2_cap)
+// (false: not a particle of this pass), and  __device__ void store(int a, const EosOut &o, bool
+// used_table).
+// claim: the pass's particle counter (indices 0 .. limit-1, claimed one lane at a time).
+enum { LANE_NONE = 0, LANE_NEWTON = 1, LANE_POLISH = 2, LANE_REEVAL = 3 };
+
+// the general inversion as a call of its own: the lane loop keeps its registers for the table
+// Newton, the common path
+__device__ __noinline__ EosOut eos_invert_call(const EosDev &E, double cs2_cap, double s, const double *n,
+                                               const double *guess, bool &used_table, EosWork &w)
+{
+    return eos_invert(E, cs2_cap, s, n, guess, used_table, w);
+}
+
+template <class Ctx>
+__device__ void eos_lanes(const EosDev &E, unsigned int *claim, int limit, Ctx &ctx, EosWork &w)
+{
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    // grid steps of the table axes: the iteration works in grid-step units with the residual
+    // unscaled (the Newton step is the same: scaling the residual and the Jacobian's rows by
+    // 1/s, or its columns by the steps, does not change it), and converges when
+    // max |residual| <= tol s
+    const double step[4] = {E.dT, E.dmu[0], E.dmu[1], E.dmu[2]};
+    const double istep[4] = {E.inv_dT, E.inv_dmu[0], E.inv_dmu[1], E.inv_dmu[2]};
+    int a = -1, phase = LANE_NONE, it = 0, ls = 0;
+    bool more = true, first = false;
+    long long rn = 0, tolb = 0;  // max-norms of the residual as integer magnitudes
+    double x[4], xt[4], d[4], r[4], J[4][4], p = 0.0, lam = 1.0, s = 0.0, nq[3];
+    double cs2_cap = 1.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = xt[k] = d[k] = r[k] = 0.0;
+    nq[0] = nq[1] = nq[2] = 0.0;
+    for (;;) {
+        // lanes without a particle claim the next ones (one atomic per warp)
+        const unsigned need = __ballot_sync(FULL, a < 0 && more);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned base = 0u;
+            if (lane == leader) base = atomicAdd(claim, (unsigned)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (a < 0 && more) {
+                const long long idx = (long long)base + __popc(need & ((1u << lane) - 1u));
+                if (idx >= limit) more = false;
+                else a = (int)idx;
+            }
+        }
+        if (__ballot_sync(FULL, a >= 0 || more) == 0u) break;
+        // a new particle: the table Newton from its warm start, or the general inversion
+        if (a >= 0 && phase == LANE_NONE) {
+            double g[4];
+            if (!ctx.load(a, s, nq, g, cs2_cap)) {
+                a = -1;
+            } else if (E.has_table && !E.offline && g[0] > 0.0 && inside_table(E, g) && isfinite(s) && s > 0.0 &&
+                       isfinite(nq[0]) && isfinite(nq[1]) && isfinite(nq[2])) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xt[k] = g[k];
+                phase = LANE_NEWTON;
+                first = true;
+                it = 0;
+                ls = 0;
+                tolb = __double_as_longlong(E.tol * s);
+            } else {
+                bool used = false;
+                const EosOut o = eos_invert_call(E, cs2_cap, s, nq, g, used, w);
+                ctx.store(a, o, used);
+                a = -1;
+            }
+        }
+        // one table evaluation at the trial point: (s, n) - target and the Jacobian per grid
+        // step, and p
+        const bool evl = a >= 0 && phase != LANE_NONE;
+        long long rnn = 0;
+        if (evl) {
+            double sn[4];
+            tab_eval_steps(E, xt, sn, J, &p);
+            const double tgt[4] = {s, nq[0], nq[1], nq[2]};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                r[k] = sn[k] - tgt[k];
+                rnn = max(rnn, min(mag_bits(r[k]), kInfBits));  // a non-finite residual counts as infinite
+            }
+            ++w.resid;
+        }
+        // what this trip solves: 0 nothing, 1 a Newton step (J d = -r, also the polishing
+        // step), 2 the EoS derivatives at the converged point (H^T z = (s, n), H = d(s, n)/d(T, mu))
+        int act = 0;
+        bool fail = false;
+        if (evl) {
+            bool accepted = false;
+            if (phase == LANE_NEWTON) {
+                if (first || rnn < rn) {
+                    accepted = true;
+                    if (!first) ++it;
+                    first = false;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x[k] = xt[k];
+                    rn = rnn;
+                } else if (++ls > 8) {
+                    fail = true;  // no decrease along the Newton direction: stalled
+                } else {
+                    lam *= 0.5;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xt[k] = fma(lam, d[k], x[k]);
+                    clamp4(E, xt);
+                }
+                if (accepted) {
+                    if (it >= E.maxit) {
+                        if (rn <= tolb) act = 2;
+                        else fail = true;
+                    } else if (rn <= tolb) {
+                        act = E.polish ? 1 : 2;
+                        if (E.polish) phase = LANE_POLISH;
+                    } else {
+                        act = 1;
+                    }
+                }
+            } else if (phase == LANE_POLISH) {
+                if (rnn <= tolb) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x[k] = xt[k];
+                    act = 2;
+                } else {  // the polished point is refused: J and p again at the kept point
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xt[k] = x[k];
+                    phase = LANE_REEVAL;
+                }
+            } else {  // LANE_REEVAL
+                act = 2;
+            }
+        }
+        double b[4];
+        if (act == 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = -r[k];
+        } else if (act == 2) {  // A = H^T, H[f][j] = J[f][j] / step_j
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = i + 1; j < 4; ++j) {
+                    const double t = J[i][j];
+                    J[i][j] = J[j][i];
+                    J[j][i] = t;
+                }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) J[i][j] *= istep[i];
+            b[0] = s;
+            b[1] = nq[0];
+            b[2] = nq[1];
+            b[3] = nq[2];
+        }
+        bool ok = true;
+        if (act) {
+            ++w.solve;
+            ok = solve4(J, b);
+        }
+        if (act == 1) {
+            if (phase == LANE_POLISH) {
+                if (ok) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xt[k] = fma(b[k], step[k], x[k]);
+                    clamp4(E, xt);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xt[k] = x[k];
+                    phase = LANE_REEVAL;
+                }
+            } else if (!ok) {
+                fail = true;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    d[k] = b[k] * step[k];
+                    xt[k] = x[k] + d[k];
+                }
+                clamp4(E, xt);
+                lam = 1.0;
+                ls = 0;
+            }
+        } else if (act == 2) {
+            EosOut o;
+            o.st = 0u;
+            if (!ok) {
+                o.T = o.p = o.e = o.ps = o.cs2 = 0.0;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) o.mu[q] = o.pn[q] = 0.0;
+                o.st = PST_NOCONV;
+            } else {
+                const double e = x[0] * s + x[1] * nq[0] + x[2] * nq[1] + x[3] * nq[2] - p;
+                double cs2 = (s * b[0] + nq[0] * b[1] + nq[1] * b[2] + nq[2] * b[3]) / (e + p);
+                if (cs2 > cs2_cap) {
+                    const double f = cs2_cap / cs2;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) b[k] *= f;
+                    cs2 = cs2_cap;
+                    o.st |= PST_CS2_CAPPED;
+                }
+                o.T = x[0];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) o.mu[q] = x[1 + q], o.pn[q] = b[1 + q];
+                o.p = p;
+                o.e = e;
+                o.ps = b[0];
+                o.cs2 = cs2;
+            }
+            ctx.store(a, o, true);
+            a = -1;
+            phase = LANE_NONE;
+        }
+        if (fail) {  // the table Newton from the warm start failed: the general inversion
+            const double g0[4] = {0.0, 0.0, 0.0, 0.0};
+            bool used = false;
+            const EosOut o = eos_invert_call(E, cs2_cap, s, nq, g0, used, w);
+            ctx.store(a, o, used);
+            a = -1;
+            phase = LANE_NONE;
+        }
+    }
+}
 
 }  // namespace
 }  // namespace sphg

@@ -175,8 +175,9 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
     double Pi = sigma * Bv, pxx = sigma * Pvxx, pxy = sigma * Pvxy, pyy = sigma * Pvyy;
     const double dt = v.dtau;
     const int nv = v.nv;
-    if (status[a] & (PST_NOCONV | PST_NONFINITE)) {
-        // no EoS solution: the particle is frozen for this stage (ballistic motion only)
+    if ((status[a] & (PST_NOCONV | PST_NONFINITE)) || (v.tr.T_stop_GeV > 0.0 && eos[a] * kHbarc < v.tr.T_stop_GeV)) {
+        // no EoS solution, or below the stop temperature: the particle is frozen for this stage
+        // (ballistic motion only)
         for (int k = 0; k < nv; ++k) {
             double fk = k == 0 ? vx : (k == 1 ? vy : 0.0);
             if (mode == 0) yout[k * n + a] = ys[k * n + a] + dt * fk;
@@ -284,11 +285,102 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
         dS = dS + aff((ig * isg / T) * uI);
         for (int c = 0; c < 3; ++c) dN[c] = sqrtg * Iq[c] * isig;
     }
+    // BSQ diffusion (eq. min_dif_rel, metric (+,-,-,-)): tau_q Delta^i_nu D J^nu_q + J^i_q =
+    // kappa_{qq'} nabla^<i> alpha_{q'}, with Delta^i_nu D J^nu = D J^i + u^i J^nu Du_nu and
+    // nabla^<i> alpha = -d_i alpha - u^i D alpha (no Christoffel terms for the transverse
+    // components).  The particle's lab charge N_q + Z_q, Z_q = J^0_q / (sigma u^0), changes by the
+    // flux divergence (dout); the rest-frame charge rate dN_q = d(lab) - dZ_q enters the entropy
+    // rate (-mu_q/T dN_q, eq. dsdnrewr) and the enthalpy rate.  D alpha_q = u^0 (alpha_{q,s} ds +
+    // alpha_{q,n} . dn) depends on those rates, linearly: its fixed point is solved exactly (the
+    // coefficient matrix is the state's; the right-hand side is affine in the acceleration).
+    Aff dNd[3] = {aff(0.0), aff(0.0), aff(0.0)}, dJhx[3], dJhy[3];
+    double dNt[3] = {0.0, 0.0, 0.0};
+    if (v.diff) {
+        const double qn[3] = {nq0, nq1, nq2}, qmu[3] = {mu0, mu1, mu2};
+        double Jhx[3], Jhy[3], Jx[3], Jy[3], kap[3][3], itJ[3], gax[3], gay[3], dal[3][4];
+        Aff jDu[3];
+        for (int q = 0; q < 3; ++q) {
+            Jhx[q] = ys[(kJRow + 2 * q) * n + a];
+            Jhy[q] = ys[(kJRow + 2 * q + 1) * n + a];
+            Jx[q] = sigma * Jhx[q];
+            Jy[q] = sigma * Jhy[q];
+            const double J0 = (ux * Jx[q] + uy * Jy[q]) * ig;
+            jDu[q] = g * (J0 * dg - (Jx[q] * ax + Jy[q] * ay));  // J^nu Du_nu
+            for (int q2 = 0; q2 < 3; ++q2) kap[q][q2] = v.kapT2[3 * q + q2] * T * T;
+            itJ[q] = T / v.tauJT[q];
+            gax[q] = v.dout[(2 * q) * n + a];
+            gay[q] = v.dout[(2 * q + 1) * n + a];
+            dNt[q] = v.dout[(6 + q) * n + a];
+            for (int f = 0; f < 4; ++f) dal[q][f] = v.dal[(4 * q + f) * n + a];
+        }
+        const double ig2 = ig * ig, ig3 = ig2 * ig, isg2 = isg * isg;
+        // the rates for a given D alpha; returns D alpha implied by them
+        auto chain = [&](const Aff *Dal, Aff *dNq_o, Aff &dS_o, Aff *Dal_o) {
+            Aff ds_l = aff(0.0);
+            for (int q = 0; q < 3; ++q) {
+                Aff sx = aff(0.0), sy = aff(0.0);  // kappa nabla^<i> alpha
+                for (int q2 = 0; q2 < 3; ++q2) {
+                    sx = sx + kap[q][q2] * (aff(-gax[q2]) - ux * Dal[q2]);
+                    sy = sy + kap[q][q2] * (aff(-gay[q2]) - uy * Dal[q2]);
+                }
+                const Aff DJx = itJ[q] * (sx + (-Jx[q])) - ux * jDu[q];
+                const Aff DJy = itJ[q] * (sy + (-Jy[q])) - uy * jDu[q];
+                dJhx[q] = (ig * isg) * DJx - (Jx[q] * isg2) * dsg;
+                dJhy[q] = (ig * isg) * DJy - (Jy[q] * isg2) * dsg;
+                const Aff dZ = ig2 * (Jhx[q] * ax + Jhy[q] * ay + ux * dJhx[q] + uy * dJhy[q]) -
+                               (2.0 * (ux * Jhx[q] + uy * Jhy[q]) * ig3) * dg;
+                dNq_o[q] = aff(dNt[q]) - dZ;
+            }
+            dS_o = dS;
+            for (int q = 0; q < 3; ++q) dS_o = dS_o - (qmu[q] / T) * dNq_o[q];
+            ds_l = sigma * dS_o + (s * isg) * dsg;
+            for (int q = 0; q < 3; ++q) {
+                Aff d = dal[q][0] * ds_l;
+                for (int r = 0; r < 3; ++r) d = d + dal[q][1 + r] * (sigma * (dNq_o[r] + aff(dN[r])) + (qn[r] * isg) * dsg);
+                Dal_o[q] = g * d;
+            }
+        };
+        const Aff z3[3] = {aff(0.0), aff(0.0), aff(0.0)};
+        Aff f0[3], dNq0[3], dS0;
+        chain(z3, dNq0, dS0, f0);
+        // d dN_q / d D alpha_{q2} = kappa_{qq2} |u|^2 / (tau_q u0^3 sigma), through dZ
+        const double uu = ux * ux + uy * uy;
+        double K[3][3], Fm[3][3];
+        for (int q = 0; q < 3; ++q)
+            for (int q2 = 0; q2 < 3; ++q2) K[q][q2] = itJ[q] * kap[q][q2] * uu * ig3 * isg;
+        for (int c = 0; c < 3; ++c)
+            for (int q2 = 0; q2 < 3; ++q2) {
+                double dSd = 0.0;
+                for (int q = 0; q < 3; ++q) dSd -= (qmu[q] / T) * K[q][q2];
+                double d = dal[c][0] * sigma * dSd;
+                for (int r = 0; r < 3; ++r) d += dal[c][1 + r] * sigma * K[r][q2];
+                Fm[c][q2] = (c == q2 ? 1.0 : 0.0) - g * d;  // I - F
+            }
+        // (I - F) D alpha = f0 by Cramer's rule, component by component of the affine forms
+        const double det = Fm[0][0] * (Fm[1][1] * Fm[2][2] - Fm[1][2] * Fm[2][1]) -
+                           Fm[0][1] * (Fm[1][0] * Fm[2][2] - Fm[1][2] * Fm[2][0]) +
+                           Fm[0][2] * (Fm[1][0] * Fm[2][1] - Fm[1][1] * Fm[2][0]);
+        const double id = 1.0 / det;
+        double Mi[3][3];
+        Mi[0][0] = (Fm[1][1] * Fm[2][2] - Fm[1][2] * Fm[2][1]) * id;
+        Mi[0][1] = (Fm[0][2] * Fm[2][1] - Fm[0][1] * Fm[2][2]) * id;
+        Mi[0][2] = (Fm[0][1] * Fm[1][2] - Fm[0][2] * Fm[1][1]) * id;
+        Mi[1][0] = (Fm[1][2] * Fm[2][0] - Fm[1][0] * Fm[2][2]) * id;
+        Mi[1][1] = (Fm[0][0] * Fm[2][2] - Fm[0][2] * Fm[2][0]) * id;
+        Mi[1][2] = (Fm[0][2] * Fm[1][0] - Fm[0][0] * Fm[1][2]) * id;
+        Mi[2][0] = (Fm[1][0] * Fm[2][1] - Fm[1][1] * Fm[2][0]) * id;
+        Mi[2][1] = (Fm[0][1] * Fm[2][0] - Fm[0][0] * Fm[2][1]) * id;
+        Mi[2][2] = (Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0]) * id;
+        Aff Dal[3], Dchk[3];
+        for (int c = 0; c < 3; ++c) Dal[c] = Mi[c][0] * f0[0] + Mi[c][1] * f0[1] + Mi[c][2] * f0[2];
+        chain(Dal, dNd, dS, Dchk);
+    }
     Aff ds = sigma * dS + (s * isg) * dsg;
     Aff dPi = sigma * dBv + Bv * dsg;
     // dn_q = N_q dsigma + sigma dN_q
     Aff dw = (T + ps) * ds + (((mu0 + pn0) * nq0 + (mu1 + pn1) * nq1 + (mu2 + pn2) * nq2) * isg) * dsg + dPi +
-             aff(sigma * ((mu0 + pn0) * dN[0] + (mu1 + pn1) * dN[1] + (mu2 + pn2) * dN[2]));
+             aff(sigma * ((mu0 + pn0) * dN[0] + (mu1 + pn1) * dN[1] + (mu2 + pn2) * dN[2])) +
+             sigma * ((mu0 + pn0) * dNd[0] + (mu1 + pn1) * dNd[1] + (mu2 + pn2) * dNd[2]);
     double w = e + p + Pi;
     double ig2 = ig * ig, ig3 = ig2 * ig;
     double Px0 = ux * Pvxx + uy * Pvxy, Py0 = ux * Pvxy + uy * Pvyy;
@@ -307,7 +399,7 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
     } else {
         st |= PST_SOLVE_FAIL;
     }
-    double f[9];
+    double f[kJRow + 6];
     f[0] = vx;
     f[1] = vy;
     f[2] = acx;
@@ -317,8 +409,15 @@ __device__ __forceinline__ void eom2_particle(const EvView &v, int stage, int mo
     f[6] = at(dPxx, acx, acy);
     f[7] = at(dPxy, acx, acy);
     f[8] = at(dPyy, acx, acy);
+    if (v.diff) {
+        for (int q = 0; q < 3; ++q) {
+            f[kJRow + 2 * q] = at(dJhx[q], acx, acy);
+            f[kJRow + 2 * q + 1] = at(dJhy[q], acx, acy);
+            dN[q] += dNt[q];  // the lab charges: sources and the flux divergence
+        }
+    }
     bool fin = true;
-    for (int k = 0; k < 9; ++k) fin = fin && isfinite(f[k]);
+    for (int k = 0; k < nv; ++k) fin = fin && isfinite(f[k]);
     if (!fin) st |= PST_NONFINITE;
     if (st) {
         status[a] |= st;

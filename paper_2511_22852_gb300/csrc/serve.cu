@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -768,16 +769,24 @@ void tiled_gradient(int tt, int grid, cudaStream_t st, const Arena &A, int stage
 
 // stage work rate per stepping event: fixed-order sum over the warps of its range; stage 2
 // closes the step (Heun quadrature of the work integral, tau += dtau)
-__global__ void k_seg_work(Arena A, int stage)
+// per event: the stage's work rate, a fixed-order sum of its particles' rates (thread t takes
+// particles t, t + 256, ...; then a tree), independent of the rest of the batch
+__global__ void __launch_bounds__(256) k_seg_work(Arena A, int stage)
 {
+    __shared__ double sh[256];
     const int s = blockIdx.x;
     const BatchTable *T = A.tab;
     if (s >= T->nslots || T->slots[s].mode != SLOT_STEP) return;
     const SegSlot sl = T->slots[s];
-    const int w0 = sl.off >> 5, w1 = (sl.off + sl.n + 31) >> 5;
     double acc = 0.0;
-    for (int w = w0 + (int)threadIdx.x; w < w1; w += 32) acc += A.wpart[w];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    for (int a = sl.off + (int)threadIdx.x; a < sl.off + sl.n; a += 256) acc += A.wpart[a];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    acc = sh[0];
     if (threadIdx.x == 0) {
         DevScalars &sc = A.sc[s];
         const EvView &V = A.segv[s];
@@ -918,6 +927,11 @@ struct RangeAlloc {
 
 enum { TK_QUEUED = 0, TK_RUNNING = 1, TK_RETIRING = 2, TK_DONE = 3 };
 
+// kernel groups of a stage for the sampled timing, and the events that delimit them
+constexpr int kProfGroups = 6;
+constexpr int kProfMarks = 2 * (kProfGroups + 1);
+const char *const kProfNames[kProfGroups] = {"sort", "density", "eos", "gradient", "eom", "work"};
+
 struct Ticket {
     int64_t id = 0;
     int state = TK_QUEUED;
@@ -982,6 +996,14 @@ struct sph_server {
     // statistics
     long long particle_steps = 0, launches = 0;
     double timeout_s = 60.0;
+    // sampled per-kernel-group timing: every prof_every-th batch step runs eagerly with CUDA
+    // events between its kernel groups (same kernels, same stream); prof_step[i] is the batch
+    // step whose marks ring entry i holds (-1: none)
+    int prof_every = 0;
+    std::vector<cudaEvent_t> prof_ev;  // ring of kProfMarks events per entry
+    std::vector<long long> prof_step;
+    double prof_ms[kProfGroups] = {};
+    long long prof_n[kProfGroups] = {};
 };
 
 namespace {
@@ -1000,15 +1022,20 @@ sph_status dmalloc(sph_server *S, void **p, size_t bytes)
 
 constexpr int kKernelsPerBatchStep = 2 * 14;
 
-// one batch step (both stages) on the server's stream; captured once into a graph
-void enqueue_batch_step(sph_server *S)
+// one batch step (both stages) on the server's stream; captured once into a graph.  marks (the
+// sampled timing, eager launches only): kProfMarks events recorded between the kernel groups
+void enqueue_batch_step(sph_server *S, const cudaEvent_t *marks = nullptr)
 {
     const Arena &A = S->A;
     cudaStream_t st = S->st;
     const size_t P = (size_t)A.P;
+    auto mark = [&](int stage, int j) {
+        if (marks) cudaEventRecord(marks[(stage - 1) * (kProfGroups + 1) + j], st);
+    };
     for (int stage = 1; stage <= 2; ++stage) {
         const double *ysrc = stage == 1 ? A.Y[0] : A.Y1[0];
         const int *idsrc = stage == 1 ? A.id[0] : A.id[1];
+        mark(stage, 0);
         k_seg_reset<<<1, 256, 0, st>>>(A);
         k_seg_bbox<<<S->grid_p, 256, 0, st>>>(A, stage, ysrc);
         k_seg_grid<<<1, kMaxSlots, 0, st>>>(A, stage);
@@ -1039,14 +1066,20 @@ void enqueue_batch_step(sph_server *S)
             pa.nq = A.Nq[1];
         }
         k_seg_permute<<<S->grid_p, 256, 0, st>>>(A, stage, pa);
+        mark(stage, 1);
         const double *ys = stage == 1 ? A.Y[1] : A.Y1[1];
         const double *nq = stage == 1 ? A.Nq[1] : A.Nq[0];
         tiled_density(S->tt, S->grid_c, st, A, ys, nq);
+        mark(stage, 2);
         launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st);
+        mark(stage, 3);
         tiled_gradient(S->tt, S->grid_c, st, A, stage, ys);
+        mark(stage, 4);
         if (stage == 1) launch_eom2_seg(A, 1, 0, ys, A.Y1[0], S->grid_p, st);
         else launch_eom2_seg(A, 2, 1, ys, A.Y[0], S->grid_p, st);
-        k_seg_work<<<S->max_events, 32, 0, st>>>(A, stage);
+        mark(stage, 5);
+        k_seg_work<<<S->max_events, 256, 0, st>>>(A, stage);
+        mark(stage, 6);
     }
     (void)P;
 }
@@ -1208,6 +1241,21 @@ void account_steps(sph_server *S)
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, S->step_t0[i], S->step_ev[i]) == cudaSuccess) S->device_ms += ms;
         else cudaGetLastError();
+        if (!S->prof_step.empty() && S->prof_step[i] == S->steps_timed) {
+            const cudaEvent_t *mk = S->prof_ev.data() + i * kProfMarks;
+            for (int stage = 0; stage < 2; ++stage)
+                for (int g = 0; g < kProfGroups; ++g) {
+                    float gm = 0.0f;
+                    const int b = stage * (kProfGroups + 1) + g;
+                    if (cudaEventElapsedTime(&gm, mk[b], mk[b + 1]) == cudaSuccess) {
+                        S->prof_ms[g] += gm;
+                        S->prof_n[g] += 1;
+                    } else {
+                        cudaGetLastError();
+                    }
+                }
+            S->prof_step[i] = -1;
+        }
         ++S->steps_timed;
     }
 }
@@ -1240,7 +1288,15 @@ sph_status batch_step(sph_server *S)
         SCK(cudaGraphInstantiate(&S->gexec, g, 0));
     }
     SCK(cudaEventRecord(ev0, S->st));
-    SCK(cudaGraphLaunch(S->gexec, S->st));
+    const size_t ring_i = (size_t)(k % (long long)S->step_ev.size());
+    if (S->prof_every > 0 && k % S->prof_every == 0 && !S->prof_step.empty()) {
+        // a sampled step: the same kernels launched eagerly, with events between the groups
+        enqueue_batch_step(S, S->prof_ev.data() + ring_i * kProfMarks);
+        S->prof_step[ring_i] = k;
+    } else {
+        if (!S->prof_step.empty()) S->prof_step[ring_i] = -1;
+        SCK(cudaGraphLaunch(S->gexec, S->st));
+    }
     SCK(cudaEventRecord(ev, S->st));
     S->steps_launched += 1;
     S->launches += kKernelsPerBatchStep;
@@ -1360,7 +1416,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     SAL(A.gout, sizeof(double) * kNGout * Pz);
     SAL(A.status, sizeof(uint32_t) * Pz);
     SAL(A.nnb, sizeof(int) * Pz);
-    SAL(A.wpart, sizeof(double) * (Pz / 32 + 1));
+    SAL(A.wpart, sizeof(double) * Pz);
     SAL(A.key, sizeof(uint32_t) * Pz);
     SAL(A.rnk, sizeof(uint32_t) * Pz);
     SAL(A.tmp, sizeof(uint32_t) * Pz);
@@ -1420,14 +1476,14 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
                 return bail(sfail(SPH_ERR_CUDA, "cudaEventCreate failed"));
             }
     // launch shapes: persistent grids of resident blocks on every SM
-    int dev = 0, sms = 0, occ_e = 12;  // EoS pass: one-warp blocks, 12 per SM (168 registers)
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::max(sms, 1);
     S->sms = sms;
     S->grid_p = sms * 8;
     S->grid_c = tiled_grid_for(S->tt, sms);
-    S->grid_e = sms * occ_e;
+    S->grid_e = eos_seg_grid(sms);
     // host/device clock reference for completion times
     if (cudaEventCreate(&S->ref_ev) != cudaSuccess || cudaEventRecord(S->ref_ev, S->st) != cudaSuccess ||
         cudaEventSynchronize(S->ref_ev) != cudaSuccess) {
@@ -1458,6 +1514,8 @@ void sph_server_free(sph_server *S)
         if (e) cudaEventDestroy(e);
     for (auto e : S->step_t0)
         if (e) cudaEventDestroy(e);
+    for (auto e : S->prof_ev)
+        if (e) cudaEventDestroy(e);
     if (S->ref_ev) cudaEventDestroy(S->ref_ev);
     for (void *p : S->allocs) cudaFree(p);
     if (S->pool) cudaFreeHost(S->pool);
@@ -1472,6 +1530,7 @@ sph_status sph_submit(sph_server *S, const sph_event_desc *d, int32_t nsteps, in
     if (!S || !d || !ticket) return sfail(SPH_ERR_ARG, "null argument");
     *ticket = 0;
     if (d->dim != 2) return sfail(SPH_ERR_ARG, "the serving form runs 2+1D events (dim = 2)");
+    if (d->kappaT2) return sfail(SPH_ERR_ARG, "the serving form runs without diffusion currents");
     if (nsteps < 0) return sfail(SPH_ERR_ARG, "nsteps < 0");
     if (d->n < 1 || d->n > S->A.P) return sfail(d->n < 1 ? SPH_ERR_ARG : SPH_ERR_OOM,
                                                 d->n < 1 ? "the serving form needs n >= 1"
@@ -1546,6 +1605,7 @@ sph_status sph_submit(sph_server *S, const sph_event_desc *d, int32_t nsteps, in
     v.tr.tau_pi_coef = d->tau_pi_coef;
     v.tr.tau_Pi_ratio = d->tau_Pi_ratio;
     v.tr.cs2_cap = d->cs2_cap > 0.0 ? d->cs2_cap : 1.0;
+    v.tr.T_stop_GeV = d->T_stop_GeV > 0.0 ? d->T_stop_GeV : 0.0;
     t->sc0 = DevScalars{};
     t->sc0.tau = d->tau0;
     t->id = S->next_id++;
@@ -1741,6 +1801,41 @@ sph_status sph_server_autotune(sph_server *S, int32_t trials, int32_t *chosen)
         S->graph = nullptr;
     }
     if (chosen) *chosen = S->tt;
+    return SPH_OK;
+}
+
+sph_status sph_server_profile(sph_server *S, int32_t every)
+{
+    if (!S || every < 0) return sfail(SPH_ERR_ARG, "bad argument");
+    if (every > 0 && S->prof_ev.empty()) {
+        // the ring of marks follows the step ring (its entries are read when a step completes)
+        SCK(cudaStreamSynchronize(S->st));
+        S->prof_ev.assign(S->step_ev.size() * kProfMarks, nullptr);
+        for (auto &e : S->prof_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                e = nullptr;
+                return sfail(SPH_ERR_CUDA, "cudaEventCreate failed");
+            }
+        S->prof_step.assign(S->step_ev.size(), -1);
+    }
+    S->prof_every = every;
+    return SPH_OK;
+}
+
+sph_status sph_server_kernel_times(sph_server *S, int32_t max, char *names, double *ms, int64_t *launches,
+                                   int32_t *count)
+{
+    if (!S || !count || (max > 0 && (!names || !ms || !launches))) return sfail(SPH_ERR_ARG, "null argument");
+    if (S->prof_ev.empty()) return sfail(SPH_ERR_STATE, "sampled timing is off (sph_server_profile)");
+    account_steps(S);
+    const int m = std::min<int>(max, kProfGroups);
+    for (int g = 0; g < m; ++g) {
+        std::snprintf(names + 32 * g, 32, "%s", kProfNames[g]);
+        ms[g] = S->prof_ms[g];
+        launches[g] = S->prof_n[g];
+    }
+    *count = kProfGroups;
     return SPH_OK;
 }
 

@@ -53,6 +53,8 @@ struct DevScalars {
     // passes), and the number of stages that did so
     unsigned int pair_flag;
     unsigned int pair_ovf;
+    unsigned int eos_claim;  // particle counter of the lane-refill EoS pass (reset with the bounding box)
+    unsigned int pad_;
 };
 
 struct EosDev {
@@ -81,6 +83,8 @@ struct EosDev {
 struct TransportDev {
     int viscous;
     double eta_over_s, zeta_peak, zeta_T_GeV, zeta_w_GeV, tau_pi_coef, tau_Pi_ratio, cs2_cap;
+    // temperature (GeV) below which a particle leaves the fluid and streams freely (0: off)
+    double T_stop_GeV;
     // viscous equations of motion: 0 minimal Israel-Stewart, 1 DNMR (shear and bulk J terms,
     // phi_7) with the ratios delta_PiPi/tau_Pi, lambda_Pipi/(tau_Pi (1/3 - c_s^2)),
     // delta_pipi/tau_pi, tau_pipi/tau_pi, lambda_piPi/tau_pi, phi_7 p
@@ -119,7 +123,17 @@ struct EvView {
     const double *parton_q;
     const double *nq_cur;
     double *nq_out;
+    // BSQ diffusion (2+1D; diff = 0: none): kappa_{qq'} / T^2 (row q), tau_q T; per stage, in the
+    // stage's sorted order: dinp[9][n] = alpha_q = mu_q / T (rows 0-2) and the lab-charge flux
+    // (J^i_q - v^i J^0_q) / sigma*^2 (rows 3 + 2 q + i); dal[12][n] = d alpha_q / d(s, n_B, n_S,
+    // n_Q) (row 4 q + k); dout[9][n] = d_i alpha_q (rows 2 q + i, the SPH difference form) and
+    // the lab-charge rate of the flux divergence (rows 6 + q).  The state carries J^i_q / sigma
+    // in rows 9 + 2 q + i.
+    int diff;
+    double kapT2[9], tauJT[3];
+    double *dinp, *dal, *dout;
 };
+constexpr int kJRow = 9;  // first state row of the diffusion currents (2+1D)
 
 // I^nu of the jet tracks at time t and position (x, y, z): every track moves at the speed of
 // light from x0 along n from t0 and deposits dE/dx per unit path length into a normalised
@@ -544,7 +558,7 @@ struct Arena {
     double *dens, *eosf, *gin, *gout;
     uint32_t *status;
     int *nnb;
-    double *wpart;  // per 32 particles: work-rate partial sums of the EoS pass
+    double *wpart;  // per particle: work rate of the EoS pass (summed per event in a fixed order)
     uint32_t *key, *rnk, *tmp, *perm;
     uint32_t *cnt, *start, *scan_part;
     // single-precision copies for the neighbour passes, written once per particle and stage:
@@ -600,6 +614,10 @@ EosDev eos_params(const ::sph_eos *e);
 void eos_retain(::sph_eos *e);
 
 void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st);
+int eos_seg_grid(int sms);  // persistent grid of the serving EoS pass
+// BSQ diffusion inputs and neighbour sums of a stage (2+1D; after the EoS pass)
+void launch_diffusion(const EvView &v, int stage, const double *y, const double *dens, const double *eos,
+                      const uint32_t *status, CellBufs cb, cudaStream_t st);
 void launch_eom2_seg(const Arena &A, int stage, int mode, const double *ys, double *yout, int grid,
                      cudaStream_t st);
 

@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(64) k_eom3(EvView v, int stage, int mode, cons
     const bool visc = v.tr.viscous != 0;
     const double dt = v.dtau;
     const int nv = v.nv;
-    if (status[a] & (PST_NOCONV | PST_NONFINITE)) {
+    if ((status[a] & (PST_NOCONV | PST_NONFINITE)) || (v.tr.T_stop_GeV > 0.0 && eos[a] * kHbarc < v.tr.T_stop_GeV)) {
+        // no EoS solution, or below the stop temperature: ballistic motion only
         for (int k = 0; k < nv; ++k) {
             double fk = k < 3 ? vv[1 + k] : 0.0;
             if (mode == 0) yout[k * n + a] = ys[k * n + a] + dt * fk;

@@ -96,6 +96,8 @@ class Transport:
     tau_pi_coef: float = 5.0      # tau_pi = coef * eta / (eps + p)
     tau_Pi_ratio: float = 1.0     # tau_Pi = ratio * tau_pi
     cs2_cap: float = 1.0          # causal cap on c_s^2 in the acceleration system
+    # temperature (GeV) below which a particle leaves the fluid and streams freely (0: off)
+    T_stop_GeV: float = 0.0
     # None: minimal Israel-Stewart; else DNMR with the coefficient ratios (delta_PiPi / tau_Pi,
     # lambda_Pipi / (tau_Pi (1/3 - c_s^2)), delta_pipi / tau_pi, tau_pipi / tau_pi,
     # lambda_piPi / tau_pi, phi_7 p), e.g. DNMR_14_MOMENT
@@ -104,6 +106,20 @@ class Transport:
 
 # DNMR coefficient ratios of the 14-moment approximation for a massless Boltzmann gas
 DNMR_14_MOMENT = (2.0 / 3.0, 8.0 / 5.0, 4.0 / 3.0, 10.0 / 7.0, 6.0 / 5.0, 9.0 / 70.0)
+
+
+@dataclass
+class Diffusion:
+    """BSQ diffusion (minimal Israel-Stewart): constant kappa_{qq'}/T^2 (3 x 3, row q = B, S, Q)
+    and relaxation times tau_q = tauJT[q] / T; Jv (3 dim x N, charge major, or None for zero):
+    the initial J^i_q / sigma."""
+    kappaT2: tuple
+    tauJT: tuple = (0.2, 0.2, 0.2)
+    Jv: np.ndarray | None = None
+
+
+# the full BSQ matrix of the paper's diffusion study (Sec. "BSQ Diffusion and the Beam Energy Scan")
+KAPPA_BSQ = ((0.0482, -0.0482, 0.0), (-0.0482, 0.1447, 0.0147), (0.0, 0.0147, 0.0880))
 
 
 @dataclass
@@ -166,6 +182,7 @@ class Event:
     # backup EoS (conformal diagonal) where neither the table nor the closed form inverts:
     # (T_scale, mu_max) in GeV, or None for none
     eos_backup: tuple | None = None
+    diffusion: Diffusion | None = None  # BSQ diffusion currents
 
     @property
     def n(self) -> int:
@@ -522,6 +539,35 @@ def boosted_sound_wave_2d(T_GeV=0.3, v=0.5, amp=1e-3, wavelength=4.0, half_width
                                      zeta_T_GeV=T_GeV, zeta_w_GeV=1.0e6, tau_pi_coef=tau_pi_coef,
                                      tau_Pi_ratio=tau_Pi_ratio),
                  meta={"dx": spacing, "k": k, "v": v, "T0": T_GeV / HBARC, "amp": amp})
+
+
+def diffusion_box_2d(T_GeV=0.3, v=0.0, amps=(1e-3, -7e-4, 5e-4), wavelength=4.0, half_widths=(6.0, 3.4),
+                     spacing=0.1, h=0.3, t0=0.0, dtau=0.01, nsteps=200, kappaT2=None, tauJT=(0.2, 0.2, 0.2)) -> Event:
+    """A uniform fluid at zero chemical potentials (e = 11 T^4 plus the charges' chi_q T^2 mu_q^2 / 2,
+    chi = (0.3, 0.5, 0.4)) moving with velocity v along x in a Cartesian 2D box, carrying small
+    charge waves n_q = chi_q T^3 amps[q] cos(2 pi x / wavelength) (alpha_q = mu_q / T = amps[q]
+    cos(...)), ideal apart from BSQ diffusion with constant kappaT2 (3 x 3) and tau_q = tauJT[q] / T,
+    J = 0 at t0."""
+    eos = AnalyticEoS(a0=GUBSER_FSTAR / 3.0, chi=(0.3, 0.5, 0.4))
+    gx = spacing * (np.arange(int(round(2 * half_widths[0] / spacing)) + 1) - round(half_widths[0] / spacing))
+    gy = spacing * (np.arange(int(round(2 * half_widths[1] / spacing)) + 1) - round(half_widths[1] / spacing))
+    X, Y = np.meshgrid(gx, gy, indexing="ij")
+    x, y = X.ravel().copy(), Y.ravel().copy()
+    n = x.size
+    k = 2.0 * math.pi / wavelength
+    T = T_GeV / HBARC
+    mu = np.stack([T * amps[q] * np.cos(k * x) for q in range(3)])
+    _, s, nq = _analytic_p_s_n(eos, np.full(n, T), mu)
+    gam = 1.0 / math.sqrt(1.0 - v * v)
+    u = np.zeros((2, n))
+    u[0] = gam * v
+    vol = gam * spacing * spacing
+    kap = KAPPA_BSQ if kappaT2 is None else kappaT2
+    return Event(name="diffusion_box_2d", dim=2, milne=False, h=h, tau0=t0, dtau=dtau, nsteps=nsteps,
+                 x=np.stack([x, y]), u=u, S=s * vol, Nq=nq * vol, Bv=np.zeros(n), Pv=np.zeros((3, n)), eos=eos,
+                 table=None, transport=Transport(viscous=False),
+                 meta={"dx": spacing, "k": k, "v": v, "T0": T, "amps": amps},
+                 diffusion=Diffusion(kappaT2=kap, tauJT=tauJT))
 
 
 def stress_cartesian_3d(n_target=8_000_000, R=7.0, z_sigma=1.5, z_max=5.0, h=0.15, n_hot=200, sigma_hot=0.4,

@@ -39,7 +39,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_sizes_match_the_header_layout():
     # the ctypes mirrors follow the C layout (natural alignment, 64-bit pointers)
     assert C.sizeof(Bd.EosDesc) == 8 * 7 + 4 * 6 + 8 * 8 + 8 * 5 + 8
-    assert C.sizeof(Bd.EventDesc) == 4 * 4 + 8 * 4 + 8 * 6 + 8 * 7 + 4 * 2 + 8 + 4 * 2
+    assert C.sizeof(Bd.EventDesc) == 4 * 4 + 8 * 4 + 8 * 6 + 8 * 7 + 4 * 2 + 8 + 4 * 2 + 8 + 8 * 3
+    assert C.sizeof(Bd.FieldBufs) == 8 * 18 + 8 + 8
     assert C.sizeof(Bd.Totals) == 8 * 7 + 4 * 2 + 8 * 7
     assert C.sizeof(Bd.ServerDesc) == 4 * 2 + 8 * 4 + 4 * 2 + 8
     assert C.sizeof(Bd.ServerStats) == 8 * 8 + 4 * 2 + 8 + 8

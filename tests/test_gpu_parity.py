@@ -52,6 +52,12 @@ def _with_partons(ev, extent, dim, h=0.5, charges=0.0):
     return ev
 
 
+def _with_stop(ev, T_GeV):
+    """The event with the stop temperature: particles colder than T_GeV stream freely."""
+    ev.transport.T_stop_GeV = T_GeV
+    return ev
+
+
 def _with_dnmr(ev):
     """The event with the DNMR equations of motion (14-moment coefficients)."""
     ev.transport.dnmr = I.DNMR_14_MOMENT
@@ -66,6 +72,7 @@ CASES = {
     "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2)),
     "bsq_small_dnmr": lambda: _with_dnmr(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20)),
     "bsq_small_partons": lambda: _with_partons(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20), 1.5, 2),
+    "bsq_small_stop": lambda: _with_stop(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20), 0.2),
 }
 def _blob3_jets():
     ev = I.smooth_blob_3d(milne=False, flow=0.3, eos=I.CAUSAL_EOS)
@@ -274,7 +281,7 @@ def test_graph_and_stream_launches_are_bitwise_identical(Bd):
 
 
 @pytest.mark.parametrize("case,nsteps", [("gubser", 60), ("bsq_small", 150), ("blob_causal", 100),
-                                        ("bsq_small_dnmr", 100), ("bsq_small_partons", 20)])
+                                        ("bsq_small_dnmr", 100), ("bsq_small_partons", 20), ("bsq_small_stop", 100)])
 def test_evolution(Bd, case, nsteps):
     ev = CASES[case]()
     g = Bd.GpuEvent(ev, use_graph=True)

@@ -69,10 +69,15 @@ def check_against_oracle(out, ev, nsteps):
     return run
 
 
+def _stopped(ev, T_GeV):
+    ev.transport.T_stop_GeV = T_GeV
+    return ev
+
+
 @pytest.mark.parametrize("case,nsteps", [("bsq", 20), ("gubser", 30), ("blob_causal", 20), ("bjorken", 10),
-                                        ("gubser_viscous", 30)])
+                                        ("gubser_viscous", 30), ("bsq_stop", 40)])
 def test_server_event_matches_fp64_oracle(Bd, case, nsteps):
-    ev = {"bsq": lambda: bsq(3000), "gubser": lambda: I.gubser_ideal_2p1(),
+    ev = {"bsq": lambda: bsq(3000), "bsq_stop": lambda: _stopped(bsq(3000), 0.2), "gubser": lambda: I.gubser_ideal_2p1(),
           "blob_causal": lambda: I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS),
           "bjorken": lambda: I.bjorken_lattice_2p1(n_side=21),
           "gubser_viscous": lambda: VG.gubser_viscous_2p1(VG.GubserODE(eta_over_s=0.2))}[case]()

@@ -1,7 +1,7 @@
 """The multi-rank (replica) path of the benchmark on CPU: world size 2 over gloo.
 
-Every rank advances its own event; the job's time is the slowest rank's and its work the
-sum of the ranks' particle-steps, with no collective on the data path.
+Every rank serves its own stream of events (rank-shifted seeds); the job's time is the slowest
+rank's and its work the sum of the ranks' particle-steps, with no collective on the data path.
 """
 import os
 import socket
@@ -27,7 +27,8 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     ws, r, local = bench.dist_env()
-    ev = bench.replica_event(rank)
+    sizes, arrivals, offset = bench.replica_stream(rank, nevents=3)
+    ev = bench.c4_event(0 + offset, int(sizes[0]))
     ms, units = bench.combine_ranks(100.0 + 50.0 * rank, float(ev.n * 10))
     out[rank] = (ws, r, ms, units, ev.n, float(ev.S.sum()))
     dist.barrier()
@@ -58,7 +59,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
 
     class A:
-        steps, warmup = 1, 0
+        steps, warmup, events = 1, 0, 3
 
     assert bench.run_reference(A()) == 0
     assert capsys.readouterr().out == ""

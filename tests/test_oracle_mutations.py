@@ -118,7 +118,7 @@ MUTATIONS = [
      "test_oracle_sources.py::test_charge_deposit_changes_entropy_by_minus_mu_over_T"),
     ("charge_rate_drop_sqrtg", "q.dN[c] = G.sqrtg * Iq[c] / aux[0 * n + a];",
      "q.dN[c] = Iq[c] / aux[0 * n + a];", "test_oracle_sources.py::test_parton_charges_are_deposited"),
-    ("charge_drop_enthalpy_term", "((q->n[c] / q->sigma) * dsig + q->sigma * q->dN[c]);", "((q->n[c] / q->sigma) * dsig);",
+    ("charge_drop_enthalpy_term", "((q->n[c] / q->sigma) * dsig + q->sigma * dNq[c]);", "((q->n[c] / q->sigma) * dsig);",
      "test_oracle_sources.py::test_charge_deposit_into_moving_fluid_keeps_energy_and_momentum"),
     ("backup_ps_factor", "out[6] = out[0] / 3.0;", "out[6] = out[0] / 4.0;",
      "test_oracle_eos.py::test_backup_eos_inverts_what_the_closed_form_cannot"),
@@ -129,6 +129,27 @@ MUTATIONS = [
      "test_oracle_bulk_flow.py::test_bulk_sound_wave_in_moving_fluid"),
     ("stress_drop_bulk", "double X = -(p + Pi) * (j == i", "double X = -(p) * (j == i",
      "test_oracle_bulk_flow.py::test_bulk_sound_wave_in_moving_fluid"),
+    ("diffusion_density_drop_J0", "aux[(2 + c) * n + a] = (nn[c] / G.sqrtg - j0_of(&G, dim, u, J)) / u0;",
+     "aux[(2 + c) * n + a] = (nn[c] / G.sqrtg) / u0;", "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_flux_drop_vJ0", "Fls[9 * a + 3 * c + k] = (J[1 + k] - (u[1 + k] / u[0]) * J[0]) / (sstar * sstar);",
+     "Fls[9 * a + 3 * c + k] = (J[1 + k]) / (sstar * sstar);",
+     "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_projection_drop_Dalpha",
+     "src += q->kap[c][c2] * (G->gi[i] * q->ga[c2][i] - u[i] * Dal_in[c2]);",
+     "src += q->kap[c][c2] * (G->gi[i] * q->ga[c2][i]);",
+     "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_kappa_transposed", "q.kap[c][c2] = P->kappaT2[3 * c + c2] * T * T;",
+     "q.kap[c][c2] = P->kappaT2[3 * c2 + c] * T * T;",
+     "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_drop_u0", "const double dJ = (DJ - chr) / u[0];", "const double dJ = (DJ - chr);",
+     "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_flux_sign", "dNt[3 * a + c] = -G.sqrtg * dv[c];", "dNt[3 * a + c] = G.sqrtg * dv[c];",
+     "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_source_sign", "const double DJ = (-q->Jc[c][i] + src) / q->tJ[c] - u[i] * jDu;",
+     "const double DJ = (-q->Jc[c][i] - src) / q->tJ[c] - u[i] * jDu;",
+     "test_oracle_diffusion.py::test_charge_waves_against_linear_diffusion"),
+    ("diffusion_flux_not_antisymmetric", "dv[c] += (Fls[9 * a + 3 * c + kk] + Fls[9 * b + 3 * c + kk]) * gw[kk];",
+     "dv[c] += (2.0 * Fls[9 * b + 3 * c + kk]) * gw[kk];", "test_oracle_diffusion.py::test_lab_charge_conserved_exactly"),
     ("dnmr_bulk_drop_volume_rate", "R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);",
      "R->dBv = DPi / (u0 * q->sigma);", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
 ]

@@ -394,3 +394,28 @@ def test_bjorken_3p1_dnmr_against_ode():
     assert abs(sigma * run.y[8][c] - Phiode / 2) < 1e-3 * abs(Phiode)
     assert abs(sigma * run.y[11][c] - Phiode / 2) < 1e-3 * abs(Phiode)
     assert max(abs(run.y[9][c]), abs(run.y[10][c]), abs(run.y[12][c])) < 1e-9 * abs(run.y[8][c])
+
+
+def test_stop_temperature_freezes_cold_particles():
+    """A particle colder than the stop temperature has left the fluid: its rates are those of free
+    streaming (dx/dtau = v, every other rate zero, charges constant), while every warmer particle
+    evolves as without the rule, except through the frozen ones' unchanged contributions."""
+    ev = I.viscous_bsq_2p1(n_target=2000, R=2.5, n_hot=10)
+    ref = O.OracleRun.start(ev)
+    ref.step(3)
+    dy0, aux0, _, st0, _ = ref.stage()
+    T_stop = float(np.quantile(aux0[O.AUX["T"]], 0.3)) * I.HBARC  # about a third of the particles
+    ev.transport.T_stop_GeV = T_stop
+    run = O.OracleRun.start(ev)
+    run.y, run.tau, run.guess = ref.y.copy(), ref.tau, ref.guess.copy()
+    dy, aux, _, st, _ = run.stage()
+    cold = aux[O.AUX["T"]] * I.HBARC < T_stop
+    assert 0.2 < cold.mean() < 0.4
+    u0 = aux[O.AUX["u0"]]
+    assert np.array_equal(dy[0][cold], run.y[2][cold] / u0[cold]) and np.array_equal(dy[1][cold], run.y[3][cold] / u0[cold])
+    assert not np.any(dy[2:, cold])
+    assert not np.any(run.last_dNq[:, cold])
+    # the densities and EoS are the state's, with or without the rule
+    assert np.array_equal(aux[O.AUX["T"]], aux0[O.AUX["T"]])
+    # warm particles keep their rates (they see the same neighbours' state)
+    assert np.array_equal(dy[:, ~cold], dy0[:, ~cold])
