@@ -998,6 +998,10 @@ sph_status sph_read_fields(sph_event *ev, uint64_t mask, const sph_field_bufs *o
             double h2[2], hn[3];
             sph_status s = fetch(ev, h2, ev->tot, sizeof(h2));
             if (s != SPH_OK) return s;
+            if (ev->charges) {  // the charges evolve: their current fixed-order sums (original order)
+                launch_scatter_orig(ev->Nq[0], ev->scratch, ev->id[0], n, 3, st);
+                launch_sum_fixed(ev->scratch, n, 3, ev->ntot, st);
+            }
             if ((s = fetch(ev, hn, ev->ntot, sizeof(hn))) != SPH_OK) return s;
             s = check_device_flags(ev, &hs);
             if (s != SPH_OK && s != SPH_ERR_EOS_RANGE && s != SPH_ERR_EOS_NOCONV && s != SPH_ERR_NONFINITE) return s;

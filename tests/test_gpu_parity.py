@@ -903,3 +903,77 @@ def test_pair_lists_3d_overflow_falls_back_then_grows(Bd, monkeypatch):
         seen.append(g.totals()["pair_overflows"])
     assert seen[-1] == seen[-2], seen
     g.free()
+
+
+def _diffusing(ev, kap=None, tauJT=(0.2, 0.2, 0.2)):
+    """The event with BSQ diffusion (the paper's full matrix unless kap is given)."""
+    ev.diffusion = I.Diffusion(kappaT2=kap if kap is not None else I.KAPPA_BSQ, tauJT=tauJT)
+    return ev
+
+
+DIFF_CASES = {
+    "bsq_small_diff": lambda: _diffusing(I.viscous_bsq_2p1(n_target=3000, R=3.0, n_hot=20)),
+    "diffusion_box_moving": lambda: I.diffusion_box_2d(v=0.7, half_widths=(3.0, 1.5),
+                                                      kappaT2=((0.05, 0.02, 0.0), (-0.01, 0.14, 0.015), (0.0, 0.03, 0.09))),
+    "blob_causal_diff": lambda: _diffusing(I.smooth_blob_2p1(half_width=2.0, eos=I.CAUSAL_EOS)),
+}
+
+
+def _diff_state(g, run, dim=2):
+    st = g.read(("X", "U", "S", "BV", "PV", "JV", "NQ"))
+    y = run.y
+    k = 2 * dim
+    return {"x": relerr(st["X"], y[0:dim]), "u": relerr(st["U"], y[dim:k]), "S": relerr(st["S"], y[k]),
+            "Bv": relerr(st["BV"], y[k + 1]), "Pv": relerr(st["PV"], y[k + 2:k + 5]), "J": relerr(st["JV"], y[9:15]),
+            "Nq": relerr(st["NQ"], run.Nq)}
+
+
+@pytest.mark.parametrize("case", list(DIFF_CASES))
+def test_diffusion_step_and_evolution(Bd, case):
+    """BSQ diffusion (2+1D, plain FP64): the densities with the currents' J^0, the inversion, the
+    currents' relaxation and the lab-charge fluxes match the oracle: 1e-11 after one Heun step,
+    1e-8 over 40; the lab charges' totals stay constant."""
+    ev = DIFF_CASES[case]()
+    g = Bd.GpuEvent(ev, use_graph=True)
+    run = O.OracleRun.start(ev)
+    f = g.read(("N_DENS", "T", "MU"))
+    aux, _ = run.observe()
+    assert relerr(f["N_DENS"], aux[O.AUX["nB"]:O.AUX["nQ"] + 1]) < TOL_STEP
+    g.step(1, sync=True)
+    run.step(1)
+    errs = _diff_state(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    g.step(39, sync=True)
+    run.step(39)
+    errs = _diff_state(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    jv = g.read(("JV",))["JV"]
+    assert np.max(np.abs(jv)) > 0.0
+    t = g.totals()
+    N0 = np.array([np.sum(ev.Nq[q]) for q in range(3)])
+    assert np.allclose(t["N"], N0, rtol=1e-12, atol=1e-12 * np.max(np.abs(ev.Nq)) * ev.n)
+    g.free()
+
+
+def test_diffusion_mixed_form_against_oracle(Bd):
+    """The mixed single-event form (FP32 neighbour sums) with diffusion: within 1e-5 over 40 steps."""
+    ev = DIFF_CASES["bsq_small_diff"]()
+    g = Bd.GpuEvent(ev, use_graph=True, precision=Bd.SPH_MIXED)
+    g.step(40, sync=True)
+    run = O.OracleRun.start(ev)
+    run.step(40)
+    errs = _diff_state(g, run)
+    assert all(v < TOL_MIXED for v in errs.values()), errs
+    g.free()
+
+
+def test_diffusion_rejected_where_not_built(Bd):
+    """3+1D events and the serving form run without diffusion currents: asking for them is an error."""
+    ev3 = _diffusing(I.smooth_blob_3d(milne=True, flow=0.3))
+    with pytest.raises(Bd.SphError):
+        Bd.GpuEvent(ev3)
+    ev = DIFF_CASES["bsq_small_diff"]()
+    srv = Bd.GpuServer(ev.eos, ev.table, max_events=2, max_particles=1 << 13)
+    with pytest.raises(Bd.SphError):
+        srv.submit(ev, 1)
+    srv.free()
