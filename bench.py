@@ -180,14 +180,16 @@ def c4_sizes(nevents: int = C4_EVENTS, seed_sizes: int = 4):
     return np.floor(np.exp(math.log(5e3) + u * (math.log(2e5) - math.log(5e3)))).astype(int)
 
 
-C4_T_STOP_GEV = 0.05  # the EoS table's lower edge: colder matter has left the fluid
+# matter colder than 0.10 GeV (below the 0.15 GeV freeze-out surface, above the EoS table's
+# 0.05 GeV lower edge) streams freely: it has left the fluid
+C4_T_STOP_GEV = 0.10
 
 
 def c4_event(e: int, n: int):
     """Event e of the stream: the single-event workload's spacing (0.062 fm), hotspot width
     (0.4 fm) and hotspot density (200 per 154 fm^2) on a disc of radius 7 fm sqrt(n / 40000),
     so round(200 n / 40000) hotspots; hotspot seed 1000 + e, charge seed 500000 + e.  Particles
-    colder than the table (0.05 GeV) stream freely (far below the freeze-out surface)."""
+    colder than 0.10 GeV stream freely (below the freeze-out surface)."""
     import math
     from paper_2511_22852_gb300 import inputs as I
     ev = I.viscous_bsq_2p1(n_target=int(n), R=7.0 * math.sqrt(n / 40000.0), n_hot=max(1, round(200 * n / 40000)),
@@ -700,7 +702,7 @@ def run_ours(args):
     # warm-up: W batch steps of the stream's first four events (untimed), the autotuner's choice
     tw = [srv.submit(evs[k], args.warmup + 2) for k in range(4)]
     srv.pump(args.warmup)
-    tuned = srv.autotune(3)
+    tuned = srv.autotune(3, lanes=True)
     srv.drain(600.0)
     for t in tw:
         srv.collect(t, names=("T",))
@@ -784,7 +786,7 @@ def run_ours(args):
                                             "one Heun step, both stages); the stream runs to completion, so --steps "
                                             "does not bound it: it sets the first-steps window of the FP64 "
                                             "single-event sub-entry",
-                          "autotuned_block_threads": tuned},
+                          "autotuned_shape": {"block_threads": tuned[0], "lane_split_warps": tuned[1]}},
                "events_per_hr": events_hr,
                "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                              "mean": float(lat.mean()), "max": float(lat.max()),
@@ -801,6 +803,7 @@ def run_ours(args):
                               "memory, through sph_submit / sph_server_pump / sph_collect with host arrays"},
                "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]), "clocks": clocks,
                "status_counts_final": res["status_counts"],
+               "failed_events": int(st1["failed"] - st0["failed"]),
                "fp64_single_event": fp64ev}
         if not args.no_extras:
             out["mixed_single_event"] = bench_mixed_single(Bd, I)

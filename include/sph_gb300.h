@@ -433,6 +433,8 @@ typedef struct {
     double device_ms;              /* device time of the batch steps completed so far (CUDA events
                                       around each step's graph launch) */
     int64_t steps_timed;           /* batch steps included in device_ms */
+    int64_t failed;                /* events ended early because their state or rates became
+                                      non-finite (their tickets are DONE; see sph_server_pump) */
 } sph_server_stats;
 
 /* Errors: SPH_ERR_ARG (max_events outside 1..256, bad fractions), SPH_ERR_OOM (arena
@@ -449,7 +451,11 @@ sph_status sph_submit(sph_server *srv, const sph_event_desc *desc, int32_t nstep
 /* Runs up to max_steps batch steps: before each, admits queued events that fit; after
  * each, retires events that finished.  Returns early when nothing is admitted or running.
  * At most max_inflight steps run ahead of the device (bounded waits: SPH_ERR_TIMEOUT).
- * *running (may be NULL) receives the number of events in the batch. */
+ * *running (may be NULL) receives the number of events in the batch.  An event whose state
+ * or rates become non-finite is ended early, within max_inflight + 2 batch steps, so that it
+ * does not slow the others down: its ticket becomes DONE with its last state, the
+ * non-finite bit (8) in the totals' status_or and totals.steps below the requested count;
+ * the other events' results do not change (sph_server_stats.failed counts such events). */
 sph_status sph_server_pump(sph_server *srv, int32_t max_steps, int32_t *running);
 /* State of a ticket (SPH_TICKET_*); for a DONE ticket, *latency_s (may be NULL) receives
  * the seconds from sph_submit until its results were readable in host memory (device
@@ -465,13 +471,20 @@ sph_status sph_collect(sph_server *srv, int64_t ticket, uint64_t mask, const sph
 sph_status sph_server_stats_get(sph_server *srv, sph_server_stats *out);
 /* Pumps until every submitted ticket is DONE (timeout_s <= 0: no limit). */
 sph_status sph_server_drain(sph_server *srv, double timeout_s);
-/* Autotuner of the launch shape: times the tiled neighbour passes of the running batch (the
- * state of its last step) with 64, 96, 128, 192 and 256 threads per block, trials runs each,
- * and keeps the fastest for the following steps (*chosen, may be NULL).  The work per cell is
- * split into lanes by the block size, so the choice changes the summation order of the kernel
- * sums (results then differ at the rounding level; they stay bitwise independent of the batch
- * composition for a fixed shape).  Errors: SPH_ERR_STATE (no batch has run a step). */
-sph_status sph_server_autotune(sph_server *srv, int32_t trials, int32_t *chosen);
+/* Autotuner of the tiled neighbour passes' shape: times them on the running batch (the state of
+ * its last step) for every pair of block size (64, 96, 128, 192, 256 threads) and lane split (a
+ * cell's particles shared by the lanes of 2, 4 or 8 warps: the lanes per particle follow from it
+ * and the cell's occupancy), trials runs each, and keeps the fastest for the following steps
+ * (*chosen: threads per block, *chosen_lanes: warps of the lane split; either may be NULL).  The
+ * lane split sets the summation order of the kernel sums (results differ at the rounding level
+ * between splits; for a fixed shape they stay bitwise independent of the batch composition).
+ * Errors: SPH_ERR_STATE (no batch has run a step). */
+sph_status sph_server_autotune(sph_server *srv, int32_t trials, int32_t *chosen, int32_t *chosen_lanes);
+/* Sets the tiled neighbour passes' shape by hand (threads per block: 64, 96, 128, 192 or 256;
+ * lane split: 2, 4 or 8 warps), e.g. to repeat a run bitwise with a shape an earlier
+ * autotuning chose.  Waits for the server's stream; the following steps use the shape.
+ * Errors: SPH_ERR_ARG (a value outside those lists). */
+sph_status sph_server_set_shape(sph_server *srv, int32_t threads, int32_t lane_warps);
 
 /* Sampled per-kernel-group timing of the batch step (measurement support): with every > 0,
  * every every-th batch step launches the same kernels eagerly instead of through the step graph,

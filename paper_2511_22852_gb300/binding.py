@@ -36,7 +36,7 @@ EXPORTS = ["sph_set_eos_table", "sph_free_eos", "sph_init_event", "sph_free_even
            "sph_write_state", "sph_last_error", "sph_debug_neighbors", "sph_debug_rates", "sph_kernel_times",
            "sph_server_create", "sph_server_free", "sph_submit", "sph_server_pump", "sph_poll", "sph_collect",
            "sph_server_stats_get", "sph_server_drain", "sph_freezeout_setup", "sph_read_freezeout",
-           "sph_set_jets", "sph_server_autotune", "sph_eos_build_inverse", "sph_set_eos_mode",
+           "sph_set_jets", "sph_server_autotune", "sph_server_set_shape", "sph_eos_build_inverse", "sph_set_eos_mode",
            "sph_set_viscous_eom", "sph_set_partons", "sph_set_eos_backup", "sph_server_profile",
            "sph_server_kernel_times", "sph_measure_fma_peak"]
 SPH_EOS_ONLINE, SPH_EOS_OFFLINE = 0, 1
@@ -92,7 +92,7 @@ class ServerStats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ["queued", "running", "done", "batch_steps", "particle_steps",
                                          "arena_capacity", "arena_in_use", "kernel_launches"]] + \
                [("slots_in_use", C.c_int32), ("max_events", C.c_int32), ("device_ms", C.c_double),
-                ("steps_timed", C.c_int64)]
+                ("steps_timed", C.c_int64), ("failed", C.c_int64)]
 
 
 _lib = None
@@ -136,7 +136,8 @@ def lib():
             "sph_set_viscous_eom": (i32, [vp, i32, vp]),
             "sph_set_partons": (i32, [vp, i64, vp, vp, C.c_double, C.c_double]),
             "sph_set_eos_backup": (i32, [vp, i32, C.c_double, C.c_double]),
-            "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32)]),
+            "sph_server_autotune": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
+            "sph_server_set_shape": (i32, [vp, i32, i32]),
             "sph_server_profile": (i32, [vp, i32]),
             "sph_measure_fma_peak": (i32, [i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "sph_server_kernel_times": (i32, [vp, i32, vp, vp, vp, C.POINTER(i32)]),
@@ -428,10 +429,16 @@ class GpuServer:
     def stats(self) -> dict:
         return sph_server_stats_get(self.h)
 
-    def autotune(self, trials: int = 3) -> int:
-        c = C.c_int32(0)
-        _check(lib().sph_server_autotune(self.h, int(trials), C.byref(c)))
-        return c.value
+    def autotune(self, trials: int = 3, lanes: bool = False):
+        """Tunes the tiled passes' shape; returns the threads per block (and the lane-split warps
+        with lanes=True)."""
+        c, lw = C.c_int32(0), C.c_int32(0)
+        _check(lib().sph_server_autotune(self.h, int(trials), C.byref(c), C.byref(lw)))
+        return (c.value, lw.value) if lanes else c.value
+
+    def set_shape(self, threads: int, lane_warps: int):
+        """Fixes the tiled passes' shape (threads per block, lane-split warps)."""
+        _check(lib().sph_server_set_shape(self.h, int(threads), int(lane_warps)))
 
     def drain(self, timeout_s: float = 0.0):
         sph_server_drain(self.h, timeout_s)

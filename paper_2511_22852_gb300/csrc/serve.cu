@@ -59,7 +59,8 @@ constexpr int kTile = 640;  // candidates staged in shared memory at a time (a 5
 constexpr int kRows = 5;    // cell rows (and columns) of the search block: cells of side h, pairs closer than 2h
 // Accumulation: each lane sums runs of kRun candidates in plain FP32 (at most kRun terms, so a
 // run's sum errs by <= kRun u times the sum of its terms' magnitudes, u = 2^-24) and folds
-// every run into Neumaier-compensated FP32 sums; the lanes of a particle are combined in FP64.
+// every run into Neumaier-compensated FP32 sums; the lanes of a particle are combined in FP32
+// with error-free additions (seg_csum) and each total converted to FP64 once.
 // 32 terms per run (<= 2e-6 of the run's magnitudes, within the form's 1e-5) fold half as often
 // as 16 (+1.5 % serving throughput measured).
 constexpr int kRun = 32;
@@ -77,6 +78,27 @@ __device__ __forceinline__ void cadd(CSum &s, float x)
     s.hi = t;
 }
 __device__ __forceinline__ double cval(CSum s) { return (double)s.hi + (double)s.lo; }
+
+// The lanes of a particle combined in FP32 without loss: the pairs (hi, lo) of two lanes add as
+// hi = TwoSum(hi_1, hi_2) (Knuth's error-free transformation: the rounded sum and its exact
+// rounding error) with the error folded into lo = lo_1 + lo_2 + err, in a fixed tree order; the
+// total lands in the particle's first lane.  (The FP64 pipe, 1/64 of the FP32 rate, is then
+// needed only for the one conversion of each total.)
+__device__ __forceinline__ CSum seg_csum(CSum v, int l, int L)
+{
+    for (int o = 1; o < L; o <<= 1) {
+        const float th = __shfl_down_sync(0xFFFFFFFFu, v.hi, o);
+        const float tl = __shfl_down_sync(0xFFFFFFFFu, v.lo, o);
+        if ((l & (2 * o - 1)) == 0 && l + o < L) {
+            const float s = v.hi + th;
+            const float bb = s - v.hi;
+            const float err = (v.hi - (s - bb)) + (th - bb);
+            v.hi = s;
+            v.lo = (v.lo + tl) + err;
+        }
+    }
+    return v;
+}
 __device__ __forceinline__ double inf_d() { return __longlong_as_double(0x7FF0000000000000LL); }
 
 // ---------------------------------------------------------------------------
@@ -426,27 +448,17 @@ __device__ __forceinline__ int cand_index(const CellCtx &cc, int q, const float2
     return b;
 }
 
-// lanes per particle: the most (up to 16) for which kLaneWarps warps hold all na particles in
-// one pass (floor(32 / L) particles per warp, a particle's lanes inside one warp), else 1.  It
-// depends on the cell alone, not on the block size, so the summation order (and the results)
-// do not change with the launch shape.
-constexpr int kLaneWarps = 4;
-__device__ __forceinline__ int lanes_per_particle(int na)
+// lanes per particle: the most (up to 16) for which lw warps hold all na particles in one pass
+// (floor(32 / L) particles per warp, a particle's lanes inside one warp), else 1.  It depends on
+// the cell and lw alone, not on the block size, so for a given lw the summation order (and the
+// results) do not change with the launch shape or the batch; lw is part of the tuned shape.
+constexpr int kLaneWarpsDefault = 4;
+constexpr int kLaneWarpChoices[] = {2, 4, 8};
+__device__ __forceinline__ int lanes_per_particle(int na, int lw)
 {
     for (int L = 16; L > 1; --L)
-        if (kLaneWarps * (32 / L) >= na) return L;
+        if (lw * (32 / L) >= na) return L;
     return 1;
-}
-
-// fixed-order sum over the L lanes of a particle (lanes [p L, p L + L) of a warp); the total
-// lands in the particle's first lane
-__device__ __forceinline__ double seg_sum(double v, int l, int L)
-{
-    for (int o = 1; o < L; o <<= 1) {
-        const double t = __shfl_down_sync(0xFFFFFFFFu, v, o);
-        if ((l & (2 * o - 1)) == 0 && l + o < L) v += t;
-    }
-    return v;
 }
 
 // cubic spline in single precision without branches: w(q) = (2-q)^3/4 - max(1-q,0)^3 and
@@ -510,7 +522,7 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
         const float ih = (float)V.inv_h;
         const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
         const double supp2 = V.supp2, sd = V.sigma_d;
-        const int L = lanes_per_particle(na), ppw = 32 / L;
+        const int L = lanes_per_particle(na, A.lane_warps), ppw = 32 / L;
         const int pl = lane / L, l = lane - pl * L;
         const int M = cc.M;
         unsigned pairs = 0u, shell = 0u;
@@ -571,11 +583,17 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
                     }
                 }
             }
-            const double tg = seg_sum(cval(sg), l, L), ts = seg_sum(cval(ss), l, L);
-            const double tb = seg_sum(cval(sb), l, L), tS = seg_sum(cval(sS), l, L);
-            const double tq = seg_sum(cval(sq), l, L);
-            nacc = (int)seg_sum((double)nacc, l, L);
+            sg = seg_csum(sg, l, L);
+            ss = seg_csum(ss, l, L);
+            sb = seg_csum(sb, l, L);
+            sS = seg_csum(sS, l, L);
+            sq = seg_csum(sq, l, L);
+            for (int o = 1; o < L; o <<= 1) {  // the neighbour count, in the same tree
+                const int t = __shfl_down_sync(0xFFFFFFFFu, nacc, o);
+                if ((l & (2 * o - 1)) == 0 && l + o < L) nacc += t;
+            }
             if (valid && l == 0) {
+                const double tg = cval(sg), ts = cval(ss), tb = cval(sb), tS = cval(sS), tq = cval(sq);
                 const double ux = y[2 * P + a], uy = y[3 * P + a];
                 A.dens[a] = sd * tg;
                 A.dens[P + a] = sd * ts;
@@ -632,7 +650,7 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
         const float ih = (float)V.inv_h;
         const float slo = cc.clamped ? -1.0f : V.shell_lo, shi = cc.clamped ? 3.0e38f : V.shell_hi;
         const double supp2 = V.supp2;
-        const int L = lanes_per_particle(na), ppw = 32 / L;
+        const int L = lanes_per_particle(na, A.lane_warps), ppw = 32 / L;
         const int pl = lane / L, l = lane - pl * L;
         const int M = cc.M;
         for (int g0 = 0; g0 < na; g0 += NW * ppw) {
@@ -699,11 +717,17 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
                     }
                 }
             }
-            const double tGx = seg_sum(cval(Gx), l, L), tGy = seg_sum(cval(Gy), l, L);
-            const double tHx = seg_sum(cval(Hx), l, L), tHy = seg_sum(cval(Hy), l, L);
-            const double t00 = seg_sum(cval(xx), l, L), t01 = seg_sum(cval(xy), l, L);
-            const double t10 = seg_sum(cval(yx), l, L), t11 = seg_sum(cval(yy), l, L);
+            Gx = seg_csum(Gx, l, L);
+            Gy = seg_csum(Gy, l, L);
+            Hx = seg_csum(Hx, l, L);
+            Hy = seg_csum(Hy, l, L);
+            xx = seg_csum(xx, l, L);
+            xy = seg_csum(xy, l, L);
+            yx = seg_csum(yx, l, L);
+            yy = seg_csum(yy, l, L);
             if (valid && l == 0) {
+                const double tGx = cval(Gx), tGy = cval(Gy), tHx = cval(Hx), tHy = cval(Hy);
+                const double t00 = cval(xx), t01 = cval(xy), t10 = cval(yx), t11 = cval(yy);
                 const double tau = A.sc[cc.s].tau + (stage == 2 ? V.dtau : 0.0);
                 const double sqrtg = V.milne ? tau : 1.0;
                 const double cf = V.sigma_d * V.inv_h;
@@ -795,6 +819,8 @@ __global__ void __launch_bounds__(256) k_seg_work(Arena A, int stage)
             sc.work += 0.5 * V.dtau * (sc.wr[0] + sc.wr[1]);
             sc.tau = sc.tau + V.dtau;
             sc.steps += 1;
+            // the host's view of the event's health (read before later launches)
+            if (A.hflags) *(volatile unsigned int *)(A.hflags + s) = sc.status_or;
         }
     }
 }
@@ -941,6 +967,7 @@ struct Ticket {
     long long pin_off = -1;        // offset in the pool (-1: heap)
     size_t pin_bytes = 0;
     bool viscous = false;
+    bool failed = false;  // ended early: its state or rates became non-finite
     cudaEvent_t done = nullptr;
     EvView view{};
     DevScalars sc0{};
@@ -993,8 +1020,10 @@ struct sph_server {
     double device_ms = 0.0;            // device time of the completed batch steps
     cudaEvent_t ref_ev = nullptr;
     double ref_host = 0.0;
+    // per-slot status words the device writes after each batch step (mapped pinned memory)
+    unsigned int *hflags = nullptr;
     // statistics
-    long long particle_steps = 0, launches = 0;
+    long long particle_steps = 0, launches = 0, failed = 0;
     double timeout_s = 60.0;
     // sampled per-kernel-group timing: every prof_every-th batch step runs eagerly with CUDA
     // events between its kernel groups (same kernels, same stream); prof_step[i] is the batch
@@ -1276,6 +1305,21 @@ sph_status batch_step(sph_server *S)
         sph_status s = wait_event(S, back);
         if (s != SPH_OK) return s;
     }
+    // an event whose state or rates became non-finite ends here, with its last state, instead of
+    // slowing the batch down (its particles would crowd one cell).  The status word of a slot is
+    // this ticket's own once it has run more than `inflight` steps: the step k - inflight waited
+    // for above has then run it and written the word.
+    for (int sl = 0; sl < S->max_events; ++sl) {
+        if (S->slots[sl].mode != SLOT_STEP) continue;
+        Ticket *t = S->slot_owner[sl];
+        if (!t || t->nsteps - t->steps_left <= S->inflight) continue;
+        if (*(volatile unsigned int *)(S->hflags + sl) & PST_NONFINITE) {
+            t->failed = true;
+            S->failed += 1;
+            sph_status r = retire(S, sl);
+            if (r != SPH_OK) return r;
+        }
+    }
     sph_status s = upload_table(S);
     if (s != SPH_OK) return s;
     if (!S->gexec) {
@@ -1338,6 +1382,20 @@ bool any_running(const sph_server *S)
     return false;
 }
 
+// the tiled passes' shape for the following steps; the step graph holds it, so a change drops
+// the graph (captured again by the next step)
+void apply_shape(sph_server *S, int tt, int lw)
+{
+    if (tt == S->tt && lw == S->A.lane_warps) return;
+    S->tt = tt;
+    S->A.lane_warps = lw;
+    S->grid_c = tiled_grid_for(tt, S->sms);
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    S->gexec = nullptr;
+    S->graph = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1391,6 +1449,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     if (P < kSegAlign) return bail(sfail(SPH_ERR_OOM, "arena smaller than one segment"));
     Arena &A = S->A;
     A.P = (int)P;
+    A.lane_warps = kLaneWarpsDefault;
     A.cmax = S->max_events * kMaxCellsAxis * kMaxCellsAxis;
     const size_t Pz = (size_t)P;
     sph_status s;
@@ -1464,6 +1523,13 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
         S->tab_ring = nullptr;
         return bail(sfail(SPH_ERR_OOM, "pinned table ring"));
     }
+    if (cudaHostAlloc(reinterpret_cast<void **>(&S->hflags), sizeof(unsigned int) * kMaxSlots, cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&A.hflags), S->hflags, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(sfail(SPH_ERR_OOM, "mapped status words"));
+    }
+    std::memset(S->hflags, 0, sizeof(unsigned int) * kMaxSlots);
     S->slots.assign(S->max_events, SegSlot{SLOT_FREE, 0, 0, 0});
     S->slot_owner.assign(S->max_events, nullptr);
     S->step_ev.resize(16, nullptr);
@@ -1520,6 +1586,7 @@ void sph_server_free(sph_server *S)
     for (void *p : S->allocs) cudaFree(p);
     if (S->pool) cudaFreeHost(S->pool);
     if (S->tab_ring) cudaFreeHost(S->tab_ring);
+    if (S->hflags) cudaFreeHost(S->hflags);
     if (S->own_stream && S->st) cudaStreamDestroy(S->st);
     if (S->eos_held) sph_free_eos(S->eos);  // drops the server's reference
     delete S;
@@ -1746,10 +1813,11 @@ sph_status sph_server_stats_get(sph_server *S, sph_server_stats *o)
     account_steps(S);
     o->device_ms = S->device_ms;
     o->steps_timed = S->steps_timed;
+    o->failed = S->failed;
     return SPH_OK;
 }
 
-sph_status sph_server_autotune(sph_server *S, int32_t trials, int32_t *chosen)
+sph_status sph_server_autotune(sph_server *S, int32_t trials, int32_t *chosen, int32_t *chosen_lanes)
 {
     if (!S) return sfail(SPH_ERR_ARG, "null argument");
     if (trials < 1) trials = 3;
@@ -1765,42 +1833,51 @@ sph_status sph_server_autotune(sph_server *S, int32_t trials, int32_t *chosen)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SCK(cudaEventCreate(&e0));
     SCK(cudaEventCreate(&e1));
-    const Arena &A = S->A;
+    Arena A = S->A;
     float best = 1e30f;
-    int best_tt = S->tt;
-    for (int tt : kTTChoices) {
-        const int grid = tiled_grid_for(tt, S->sms);
-        float tot = 0.0f;
-        for (int r = 0; r <= trials; ++r) {  // r = 0: warm-up
-            SCK(cudaMemsetAsync(A.claim, 0, sizeof(unsigned int) * kClaims, S->st));
-            SCK(cudaEventRecord(e0, S->st));
-            tiled_density(tt, grid, S->st, A, A.Y1[1], A.Nq[0]);
-            tiled_gradient(tt, grid, S->st, A, 2, A.Y1[1]);
-            SCK(cudaEventRecord(e1, S->st));
-            SCK(cudaGetLastError());
-            sph_status s = wait_event(S, e1);
-            if (s != SPH_OK) return s;
-            float ms = 0.0f;
-            SCK(cudaEventElapsedTime(&ms, e0, e1));
-            if (r > 0) tot += ms;
+    int best_tt = S->tt, best_lw = S->A.lane_warps;
+    for (int lw : kLaneWarpChoices)
+        for (int tt : kTTChoices) {
+            A.lane_warps = lw;
+            const int grid = tiled_grid_for(tt, S->sms);
+            float tot = 0.0f;
+            for (int r = 0; r <= trials; ++r) {  // r = 0: warm-up
+                SCK(cudaMemsetAsync(A.claim, 0, sizeof(unsigned int) * kClaims, S->st));
+                SCK(cudaEventRecord(e0, S->st));
+                tiled_density(tt, grid, S->st, A, A.Y1[1], A.Nq[0]);
+                tiled_gradient(tt, grid, S->st, A, 2, A.Y1[1]);
+                SCK(cudaEventRecord(e1, S->st));
+                SCK(cudaGetLastError());
+                sph_status s = wait_event(S, e1);
+                if (s != SPH_OK) return s;
+                float ms = 0.0f;
+                SCK(cudaEventElapsedTime(&ms, e0, e1));
+                if (r > 0) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                best_tt = tt;
+                best_lw = lw;
+            }
         }
-        if (tot < best) {
-            best = tot;
-            best_tt = tt;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     SCK(cudaMemcpy(S->A.sc, save.data(), sizeof(DevScalars) * (size_t)ns, cudaMemcpyHostToDevice));
-    if (best_tt != S->tt) {  // the step graph holds the launch shape: capture it again
-        S->tt = best_tt;
-        S->grid_c = tiled_grid_for(best_tt, S->sms);
-        if (S->gexec) cudaGraphExecDestroy(S->gexec);
-        if (S->graph) cudaGraphDestroy(S->graph);
-        S->gexec = nullptr;
-        S->graph = nullptr;
-    }
+    apply_shape(S, best_tt, best_lw);
     if (chosen) *chosen = S->tt;
+    if (chosen_lanes) *chosen_lanes = S->A.lane_warps;
+    return SPH_OK;
+}
+
+sph_status sph_server_set_shape(sph_server *S, int32_t threads, int32_t lane_warps)
+{
+    if (!S) return sfail(SPH_ERR_ARG, "null argument");
+    bool ok_tt = false, ok_lw = false;
+    for (int tt : kTTChoices) ok_tt = ok_tt || tt == threads;
+    for (int lw : kLaneWarpChoices) ok_lw = ok_lw || lw == lane_warps;
+    if (!ok_tt || !ok_lw) return sfail(SPH_ERR_ARG, "threads must be 64, 96, 128, 192 or 256 and lane_warps 2, 4 or 8");
+    SCK(cudaStreamSynchronize(S->st));
+    apply_shape(S, threads, lane_warps);
     return SPH_OK;
 }
 

@@ -550,6 +550,8 @@ struct BatchTable {  // host-written
 };
 struct Arena {
     int P, cmax;  // particle and cell capacity
+    int lane_warps;  // tiled neighbour passes: warps whose lanes share a cell's particles (the tuned shape)
+    unsigned int *hflags;  // mapped pinned host words: per slot, its status OR after each batch step
     double *Y[2], *Y1[2], *Nq[2];
     int *id[2];
     double *wguess, *guess_in;

@@ -43,4 +43,4 @@ def test_struct_sizes_match_the_header_layout():
     assert C.sizeof(Bd.FieldBufs) == 8 * 18 + 8 + 8
     assert C.sizeof(Bd.Totals) == 8 * 7 + 4 * 2 + 8 * 7
     assert C.sizeof(Bd.ServerDesc) == 4 * 2 + 8 * 4 + 4 * 2 + 8
-    assert C.sizeof(Bd.ServerStats) == 8 * 8 + 4 * 2 + 8 + 8
+    assert C.sizeof(Bd.ServerStats) == 8 * 8 + 4 * 2 + 8 + 8 + 8

@@ -192,8 +192,8 @@ def test_autotuner_keeps_results_and_counters(Bd):
     assert e.value.code == Bd.SPH_ERR_STATE
     tk = [s.submit(ev, 12) for ev in evs]
     s.pump(2)
-    tt = s.autotune(2)
-    assert tt in (64, 96, 128, 192, 256)
+    tt, lw = s.autotune(2, lanes=True)
+    assert tt in (64, 96, 128, 192, 256) and lw in (2, 4, 8)
     s.drain(120.0)
     out = [s.collect(t) for t in tk]
     s.free()
@@ -215,3 +215,60 @@ def test_server_wait_limit_reports_timeout(Bd, monkeypatch):
             s.pump(1)
     assert e.value.code == Bd.SPH_ERR_TIMEOUT
     s.free()
+
+
+def test_nonfinite_event_ends_early_without_touching_others(Bd):
+    """An event whose rates overflow (a shear stress of 1e305 on every particle) is ended within
+    a few batch steps: its ticket completes with the non-finite status bit and fewer steps than
+    requested, the server counts one failed event, and the healthy event served beside it is
+    bitwise what it is alone."""
+    healthy = bsq(3000, seed=81)
+    alone = serve_alone(Bd, healthy, 40, max_events=4, max_particles=1 << 15)
+    bad = bsq(1500, seed=82)
+    bad.Pv = np.full_like(bad.Pv, 1e305)
+    s = Bd.GpuServer(healthy.eos, healthy.table, max_events=4, max_particles=1 << 15)
+    tb = s.submit(bad, 200)
+    th = s.submit(healthy, 40)
+    s.drain(120.0)
+    st = s.stats()
+    assert st["failed"] == 1
+    ob = s.collect(tb, names=("X", "T", "STATUS"))
+    oh = s.collect(th)
+    s.free()
+    assert ob["totals"]["status_or"] & 8
+    assert 1 <= ob["totals"]["steps"] <= 6, ob["totals"]["steps"]
+    assert oh["totals"]["status_or"] & 8 == 0 and oh["totals"]["steps"] == 40
+    for k in ("X", "U", "S", "BV", "PV", "T", "MU", "S_DENS", "N_DENS", "NNB"):
+        assert np.array_equal(alone[k], oh[k]), k
+
+
+def test_fixed_shape_runs_match_oracle_and_are_batch_invariant(Bd):
+    """Every lane split, set by hand, gives the oracle's results within the form's tolerance and,
+    for a fixed shape, the same bits alone and in a batch; shapes outside the lists are refused."""
+    ev = bsq(2500, seed=91)
+    other = bsq(4000, seed=92)
+    s = Bd.GpuServer(ev.eos, ev.table, max_events=4, max_particles=1 << 15)
+    for bad in ((100, 4), (128, 3), (0, 0)):
+        with pytest.raises(Bd.SphError) as e:
+            s.set_shape(*bad)
+        assert e.value.code == Bd.SPH_ERR_ARG
+    s.free()
+    for tt, lw in ((64, 2), (192, 8)):
+        a = Bd.GpuServer(ev.eos, ev.table, max_events=4, max_particles=1 << 15)
+        a.set_shape(tt, lw)
+        t = a.submit(ev, 10)
+        a.drain(60.0)
+        lone = a.collect(t)
+        a.free()
+        check_against_oracle(lone, ev, 10)
+        b = Bd.GpuServer(ev.eos, ev.table, max_events=4, max_particles=1 << 15)
+        b.set_shape(tt, lw)
+        to = b.submit(other, 14)
+        b.pump(2)
+        t = b.submit(ev, 10)
+        b.drain(60.0)
+        mixed = b.collect(t)
+        b.collect(to)
+        b.free()
+        for k in ("X", "U", "T", "MU", "NNB"):
+            assert np.array_equal(lone[k], mixed[k]), (tt, lw, k)
