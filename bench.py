@@ -14,6 +14,8 @@ wall-clock figures of the whole stream.  The plain FP64 form, one event at a tim
 a sample of whole events and extrapolated to the stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --profile-case serving|fp64|diffusion [--events E] [--profile-steps K]
+        (a short fixed run of the timed kernels for profiler captures; measures nothing)
 
 N > 1 runs under torchrun, one independent stream per rank (replicas, weak scaling, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference times the CPU
@@ -598,20 +600,29 @@ def _with_table(ev):
     return ev
 
 
-def traffic_of(kernel: str):
-    """DRAM bytes (read + write) per launch of a kernel from the committed ncu summary, or None
-    when the kernel's source file changed since the capture (the counters then no longer
-    describe it)."""
+def traffic_of(kernel: str, particles_per_launch: float | None = None):
+    """DRAM bytes (read + write) per launch of a kernel from the committed ncu summary
+    (profiles/traffic.json: bytes per particle of one captured launch), scaled to the launch's
+    particle count when it differs from the capture's; None when a source file of the kernel
+    changed since the capture (the counters then no longer describe it)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[kernel]
-        src = open(os.path.join(ROOT, "paper_2511_22852_gb300", "csrc", rec["source"]), "rb").read()
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2511_22852_gb300", "csrc", f), "rb").read())
     except (OSError, KeyError, ValueError):
         return None
-    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha16"]:
+    if h.hexdigest()[:16] != rec["source_sha16"]:
         return None
-    return {"bytes_per_launch": rec["bytes_per_launch"], "capture": rec["capture"]}
+    n = float(particles_per_launch) if particles_per_launch else float(rec["particles"])
+    out = {"bytes_per_launch": rec["bytes_per_particle"] * n, "bytes_per_particle": rec["bytes_per_particle"],
+           "capture": rec["capture"], "captured_particles": rec["particles"]}
+    if abs(n - rec["particles"]) > 0.5:
+        out["scaled"] = (f"captured on {rec['particles']} particles, scaled to {n:.0f} per launch "
+                         "(DRAM bytes taken proportional to the particles processed)")
+    return out
 
 
 def bench_fp64_event(Bd, I, stream, flush, first_k: int):
@@ -669,7 +680,8 @@ def bench_fp64_event(Bd, I, stream, flush, first_k: int):
 def alu_roof(name, flops, ms, launches, peak, peak_name, kernel, traffic=None):
     achieved = flops / (ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": kernel, "group": name, "peak_source": peak_name,
+            "traffic": traffic["bytes_per_launch"] if traffic else None, "traffic_source": traffic,
+            "kernel": kernel, "group": name, "peak_source": peak_name,
             "avg_launch_ms": ms / max(1, launches), "flops_per_launch": flops / max(1, launches)}
 
 
@@ -744,13 +756,14 @@ def run_ours(args):
                  "gradient": FLOPS_PER_PAIR["gradient"] * res["pairs"]}
         peak64 = f"measured FP64 FMA rate of this GPU ({fp64_gflops:.0f} GFLOP/s, sph_measure_fma_peak)"
         peak32 = f"measured FP32 FMA rate of this GPU ({fp32_gflops:.0f} GFLOP/s, sph_measure_fma_peak)"
+        ppl = psteps / max(1, batch_steps)  # mean particles per launch (resident per batch step)
         rooflines = {
             "eos": alu_roof("eos", flops["eos"], g_ms["eos"], launches_g, fp64_gflops, peak64, "k_eos2_seg",
-                            traffic_of("k_eos2_seg")),
+                            traffic_of("k_eos2_seg", ppl)),
             "density": alu_roof("density", flops["density"], g_ms["density"], launches_g, fp32_gflops, peak32,
-                                "k_seg_density", traffic_of("k_seg_density")),
+                                "k_seg_density", traffic_of("k_seg_density", ppl)),
             "gradient": alu_roof("gradient", flops["gradient"], g_ms["gradient"], launches_g, fp32_gflops, peak32,
-                                 "k_seg_gradient", traffic_of("k_seg_gradient")),
+                                 "k_seg_gradient", traffic_of("k_seg_gradient", ppl)),
         }
         rooflines["eos"]["work_per_particle_stage"] = {
             "table_evals": float(ew[0] / (2.0 * psteps)), "solves": float(ew[1] / (2.0 * psteps)),
@@ -827,6 +840,48 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A short, fixed run of the timed kernels for profiler captures (no timing, no reference
+    legs): 'serving' -- the stream's first --events events resident at once in the serving
+    arena, --profile-steps batch steps in the tiled-pass shape --profile-shape; 'fp64' -- the
+    40k-particle viscous BSQ event in the plain FP64 form, --profile-steps Heun steps (kernels
+    launched one by one); 'diffusion' -- the same event with BSQ diffusion.  Prints one JSON
+    line describing what ran."""
+    import numpy as np
+    import torch
+    from paper_2511_22852_gb300 import binding as Bd
+    from paper_2511_22852_gb300 import build_lib
+    from paper_2511_22852_gb300 import inputs as I
+
+    build_lib.build()
+    k = args.profile_steps
+    if args.profile_case == "serving":
+        sizes = c4_sizes(C4_EVENTS)[:args.events]
+        evs = c4_events(sizes)
+        tt, lw = (int(v) for v in args.profile_shape.split(","))
+        srv = Bd.GpuServer(I.BJ_EOS, I.synthetic_eos_table(I.BJ_EOS), max_events=max(4, len(evs)),
+                           max_particles=C4_ARENA)
+        srv.set_shape(tt, lw)
+        for ev in evs:
+            srv.submit(ev, C4_STEPS)
+        srv.pump(k)
+        st = srv.stats()
+        srv.free()
+        desc = {"events": len(evs), "particles": int(np.sum(sizes)), "batch_steps": int(st["batch_steps"]),
+                "shape": [tt, lw], "kernel_launches": int(st["kernel_launches"])}
+    else:
+        ev = I.viscous_bsq_2p1()
+        if args.profile_case == "diffusion":
+            ev.diffusion = I.Diffusion(kappaT2=I.KAPPA_BSQ)
+        g = Bd.GpuEvent(ev, use_graph=False)
+        g.step(k, sync=True)
+        g.free()
+        desc = {"particles": ev.n, "steps": k}
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, **desc}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -839,7 +894,13 @@ def main():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--events", type=int, default=C4_EVENTS,
                     help="events of the stream (the configuration has 512; fewer only for quick checks)")
+    ap.add_argument("--profile-case", choices=["serving", "fp64", "diffusion"], default=None,
+                    help="a short fixed run of the timed kernels for profiler captures (no measurement)")
+    ap.add_argument("--profile-steps", type=int, default=40)
+    ap.add_argument("--profile-shape", default="64,2", help="threads,lane-split warps of the tiled passes")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     return run_reference(args) if args.impl == "reference" else run_ours(args)
