@@ -109,14 +109,90 @@ __global__ void __launch_bounds__(128) k_diff_prep(EvView v, int stage, const do
         for (int f = 0; f < 4; ++f) v.dal[(4 * q + f) * n + a] = dal[q][f];
 }
 
+// the sums of particle a (lane 0 of its warp writes them): S = sum grad W, ga = sum (alpha_b -
+// alpha_a) grad W, dv = sum F_b . grad W, lane partials reduced in a fixed butterfly order
+__device__ __forceinline__ void diff_finish(const EvView &v, int stage, const double *__restrict__ dens, int a,
+                                            int lane, double Gx, double Gy, double (&ga)[3][2], double (&dv)[3])
+{
+    const size_t n = (size_t)v.n;
+    const double *F = v.dinp + 3 * n;
+    for (int o = 16; o > 0; o >>= 1) {
+        Gx += __shfl_xor_sync(0xFFFFFFFFu, Gx, o);
+        Gy += __shfl_xor_sync(0xFFFFFFFFu, Gy, o);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            ga[q][0] += __shfl_xor_sync(0xFFFFFFFFu, ga[q][0], o);
+            ga[q][1] += __shfl_xor_sync(0xFFFFFFFFu, ga[q][1], o);
+            dv[q] += __shfl_xor_sync(0xFFFFFFFFu, dv[q], o);
+        }
+    }
+    if (lane == 0) {
+        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+        const double sqrtg = v.milne ? tau : 1.0;
+        const double c = v.sigma_d * v.inv_h;
+        const double isig = 1.0 / dens[a];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            v.dout[(2 * q) * n + a] = c * ga[q][0] * isig;
+            v.dout[(2 * q + 1) * n + a] = c * ga[q][1] * isig;
+            const double div = F[(2 * q) * n + a] * Gx + F[(2 * q + 1) * n + a] * Gy + dv[q];
+            v.dout[(6 + q) * n + a] = -sqrtg * c * div;
+        }
+    }
+}
+
+// pair-list form (plain 2D events): one warp per particle over its accepted pairs, with the
+// kernel gradient the density pass stored per pair (grad_a W_ab h / sigma_d: b > a forward in
+// a's row, b < a as minus the entry in b's row), so no distance or kernel is evaluated again
+__global__ void __launch_bounds__(32 * kDiffWarps) k_diff_pairs(EvView v, int stage, const double *__restrict__ dens,
+                                                                PairBufs pl)
+{
+    if (v.sc->pair_flag) return;  // a list overflowed: the cell pass runs instead
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * kDiffWarps + wid;
+    if (a >= v.n) return;  // warp-uniform
+    const size_t n = (size_t)v.n;
+    const double *al = v.dinp, *F = v.dinp + 3 * n;
+    const double aa[3] = {al[a], al[n + a], al[2 * n + a]};
+    const long long r0 = pl.off[a], rend = pl.off[a + 1] - 1;
+    const int nf = pl.cntF[a], nt = nf + pl.cntB[a];
+    double ga[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}}, dv[3] = {0.0, 0.0, 0.0}, Gx = 0.0, Gy = 0.0;
+    for (int j = lane; j < nt; j += 32) {
+        int b;
+        double gx, gy;
+        if (j < nf) {
+            b = pl.L[r0 + j];
+            const double2 g = pl.G[r0 + j];
+            gx = g.x;
+            gy = g.y;
+        } else {
+            b = pl.L[rend - (j - nf)];
+            const double2 g = pl.G[pl.off[b] + pl.P[rend - (j - nf)]];
+            gx = -g.x;
+            gy = -g.y;
+        }
+        Gx += gx;
+        Gy += gy;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double da = al[q * n + b] - aa[q];
+            ga[q][0] = fma(da, gx, ga[q][0]);
+            ga[q][1] = fma(da, gy, ga[q][1]);
+            dv[q] = fma(F[(2 * q) * n + b], gx, fma(F[(2 * q + 1) * n + b], gy, dv[q]));
+        }
+    }
+    diff_finish(v, stage, dens, a, lane, Gx, Gy, ga, dv);
+}
+
 // one warp per particle: the 3x3 cells of side 2h around its own, the exact FP64 test r < 2h on
-// every candidate (the neighbour set of the other passes), lane partial sums reduced in a fixed
-// butterfly order
+// every candidate (the neighbour set of the other passes).  The mixed-precision form's pass,
+// and the plain form's when a pair list overflowed (fallback: it returns at once otherwise).
 __global__ void __launch_bounds__(32 * kDiffWarps) k_diff2(EvView v, int stage, const double *__restrict__ y,
                                                            const double *__restrict__ dens,
                                                            const uint32_t *__restrict__ start,
-                                                           const uint32_t *__restrict__ cnt)
+                                                           const uint32_t *__restrict__ cnt, int fallback)
 {
+    if (fallback && !v.sc->pair_flag) return;  // the pair-list pass did the work
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t n = (size_t)v.n;
     const double xmin0 = dec_double(v.sc->xmin_enc[0]), xmin1 = dec_double(v.sc->xmin_enc[1]);
@@ -155,29 +231,7 @@ __global__ void __launch_bounds__(32 * kDiffWarps) k_diff2(EvView v, int stage, 
                 }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            Gx += __shfl_xor_sync(0xFFFFFFFFu, Gx, o);
-            Gy += __shfl_xor_sync(0xFFFFFFFFu, Gy, o);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                ga[q][0] += __shfl_xor_sync(0xFFFFFFFFu, ga[q][0], o);
-                ga[q][1] += __shfl_xor_sync(0xFFFFFFFFu, ga[q][1], o);
-                dv[q] += __shfl_xor_sync(0xFFFFFFFFu, dv[q], o);
-            }
-        }
-        if (lane == 0) {
-            const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-            const double sqrtg = v.milne ? tau : 1.0;
-            const double c = v.sigma_d * v.inv_h;
-            const double isig = 1.0 / dens[a];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                v.dout[(2 * q) * n + a] = c * ga[q][0] * isig;
-                v.dout[(2 * q + 1) * n + a] = c * ga[q][1] * isig;
-                const double div = F[(2 * q) * n + a] * Gx + F[(2 * q + 1) * n + a] * Gy + dv[q];
-                v.dout[(6 + q) * n + a] = -sqrtg * c * div;
-            }
-        }
+        diff_finish(v, stage, dens, a, lane, Gx, Gy, ga, dv);
     }
 }
 
@@ -190,7 +244,12 @@ void launch_diffusion(const EvView &v, int stage, const double *y, const double 
 {
     if (!v.diff || v.n <= 0) return;
     k_diff_prep<<<nblk(v.n, 128), 128, 0, st>>>(v, stage, y, dens, eos, status);
-    k_diff2<<<nblk(v.n, kDiffWarps), 32 * kDiffWarps, 0, st>>>(v, stage, y, dens, cb.start, cb.cnt);
+    // the plain form keeps pair lists: the pass over them, with the cell pass standing by (at a
+    // few blocks per SM) for a stage whose lists overflowed
+    const int lists = !v.mixed && cb.pl.total > 0;
+    if (lists) k_diff_pairs<<<nblk(v.n, kDiffWarps), 32 * kDiffWarps, 0, st>>>(v, stage, dens, cb.pl);
+    const int grid = lists ? std::min(nblk(v.n, kDiffWarps), 8 * device_sm_count()) : nblk(v.n, kDiffWarps);
+    k_diff2<<<grid, 32 * kDiffWarps, 0, st>>>(v, stage, y, dens, cb.start, cb.cnt, lists);
 }
 
 }  // namespace sphg

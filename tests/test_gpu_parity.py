@@ -967,6 +967,26 @@ def test_diffusion_mixed_form_against_oracle(Bd):
     g.free()
 
 
+def test_diffusion_pair_list_overflow_uses_the_cell_pass(Bd, monkeypatch):
+    """Pair lists far too small: the stages whose lists overflowed take the diffusion sums from
+    the cell pass (distances and kernel gradients evaluated again), the others from the lists;
+    both follow the oracle."""
+    monkeypatch.setenv("SPH_PAIR_TOTAL", "64")
+    ev = DIFF_CASES["bsq_small_diff"]()
+    g = Bd.GpuEvent(ev)
+    run = O.OracleRun.start(ev)
+    g.step(1, sync=True)
+    run.step(1)
+    assert g.totals()["pair_overflows"] >= 2
+    errs = _diff_state(g, run)
+    assert all(v < TOL_STEP for v in errs.values()), errs
+    g.step(9, sync=True)
+    run.step(9)
+    errs = _diff_state(g, run)
+    assert all(v < TOL_EVOL for v in errs.values()), errs
+    g.free()
+
+
 def test_diffusion_rejected_where_not_built(Bd):
     """3+1D events and the serving form run without diffusion currents: asking for them is an error."""
     ev3 = _diffusing(I.smooth_blob_3d(milne=True, flow=0.3))
