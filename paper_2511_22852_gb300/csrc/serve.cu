@@ -22,9 +22,10 @@
 // cell's occupancy, up to 16).  A proven
 // bound on the float r^2 decides all but a thin shell of candidates; inside the shell the
 // FP64 test r^2 < (2h)^2 with separately rounded products decides, so the neighbour sets
-// are exactly those of the FP64 form.  Sums are Neumaier-compensated per lane and combined
-// across lanes in FP64 in a fixed order: an event's results do not depend on what else is
-// in the batch or where its range lies.
+// are exactly those of the FP64 form.  A lane evaluates two candidates per packed two-wide
+// FP32 instruction.  Sums are Neumaier-compensated per lane and combined across a particle's
+// lanes with error-free FP32 additions in a fixed order: an event's results do not depend on
+// what else is in the batch or where its range lies.
 //
 // Host side.  sph_submit copies an event into pinned staging and queues it; each
 // sph_server_pump step admits queued events while a slot and an arena range are free
@@ -461,14 +462,34 @@ __device__ __forceinline__ int lanes_per_particle(int na, int lw)
     return 1;
 }
 
-// cubic spline in single precision without branches: w(q) = (2-q)^3/4 - max(1-q,0)^3 and
-// dw/dq = 3 max(1-q,0)^2 - 3 (2-q)^2 / 4 on 0 <= q <= 2 (the two pieces of the spline)
-__device__ __forceinline__ void spline_terms(float qq, float &t2, float &t, float &u2, float &u)
+// Candidates of a staged tile go in pairs (2k, 2k + 1), laid out so that every operand of the
+// packed two-wide FP32 operations (one instruction for both candidates) loads as one register
+// pair: a float4 per pair holds (a_0, a_1, b_0, b_1) for two per-candidate values a and b.
+// Positions are stored negated (x_a + (-x_b) rounds exactly as x_a - x_b).  An odd tile is
+// padded with a candidate kFar away (its r^2 overflows to +inf: never accepted, never in the
+// shell; its terms are selected away before use, and its carried values are zero).
+constexpr float kFar = 3.0e19f;
+
+__device__ __forceinline__ void put_pair(float4 *arr, int i, float a, float b)
 {
-    t = 2.0f - qq;
-    u = fmaxf(1.0f - qq, 0.0f);
-    t2 = t * t;
-    u2 = u * u;
+    float *p = reinterpret_cast<float *>(arr + (i >> 1));
+    p[i & 1] = a;
+    p[2 + (i & 1)] = b;
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// the cubic spline in single precision without branches, for both candidates: w(q) = (2-q)^3/4
+// - max(1-q,0)^3 and dw/dq = 3 max(1-q,0)^2 - 3 (2-q)^2 / 4 on 0 <= q <= 2 take t = 2 - q,
+// u = max(1 - q, 0) and their squares
+__device__ __forceinline__ void spline_terms2(float2 q, float2 &t2, float2 &t, float2 &u2, float2 &u)
+{
+    const float2 nq = make_float2(-q.x, -q.y);
+    t = __fadd2_rn(make_float2(2.0f, 2.0f), nq);
+    const float2 v = __fadd2_rn(make_float2(1.0f, 1.0f), nq);
+    u = make_float2(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f));
+    t2 = __fmul2_rn(t, t);
+    u2 = __fmul2_rn(u, u);
 }
 
 // Inner loops of the tiled passes: every candidate of a lane's run is evaluated without
@@ -480,8 +501,9 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
                                                      const double *__restrict__ Nq)
 {
     __shared__ int s_base[kMaxSlots];
-    __shared__ float2 cpos[kTile];
-    __shared__ float4 cq[kTile];
+    __shared__ float4 cP[kTile / 2];   // (-x_0, -x_1, -y_0, -y_1) relative to the centre cell
+    __shared__ float4 cQa[kTile / 2];  // (S_0, S_1, N_B0, N_B1)
+    __shared__ float4 cQb[kTile / 2];  // (N_S0, N_S1, N_Q0, N_Q1)
     __shared__ CellCtx cc;
     __shared__ int s_cell, s_cur;
     __shared__ unsigned long long s_acc[2];  // pairs and shell tests of slot s_cur, flushed when it changes
@@ -541,45 +563,64 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
                     for (int i = tid; i < mt; i += TT) {
                         float2 rel;
                         const int b = cand_index(cc, t0 + i, A.fpos, rel);
-                        cpos[i] = rel;
-                        cq[i] = A.fq[b];
+                        put_pair(cP, i, -rel.x, -rel.y);
+                        const float4 q = A.fq[b];
+                        put_pair(cQa, i, q.x, q.y);
+                        put_pair(cQb, i, q.z, q.w);
+                    }
+                    if ((mt & 1) && tid == 0) {
+                        put_pair(cP, mt, kFar, kFar);
+                        put_pair(cQa, mt, 0.0f, 0.0f);
+                        put_pair(cQb, mt, 0.0f, 0.0f);
                     }
                     __syncthreads();
                 }
                 if (valid) {
-                    // runs of kRun candidates summed in plain FP32, each run folded into the
-                    // compensated sums
-                    for (int jb = l; jb < mt; jb += kRun * L) {
-                        const int je = min(mt, jb + kRun * L);
-                        float pg = 0.f, ps = 0.f, pB = 0.f, pS = 0.f, pQ = 0.f;
-#pragma unroll 4
-                        for (int j = jb; j < je; j += L) {
-                            const float2 pb = cpos[j];
-                            const float dx = fa.x - pb.x, dy = fa.y - pb.y;
-                            const float r2 = fmaf(dx, dx, dy * dy);
-                            bool acc = r2 < slo;
-                            if (r2 >= slo && r2 <= shi) {  // thin shell: the exact FP64 decision
-                                const int b = cand_arena(cc, t0 + j);
-                                acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                    // runs of kRun candidates (kRun / 2 pairs) summed in plain FP32, each half of a
+                    // packed sum over kRun / 2 terms, each run folded into the compensated sums
+                    const float2 fx = make_float2(fa.x, fa.x), fy = make_float2(fa.y, fa.y), ih2 = make_float2(ih, ih);
+                    const int np = (mt + 1) >> 1;
+                    for (int kb = l; kb < np; kb += (kRun / 2) * L) {
+                        const int ke = min(np, kb + (kRun / 2) * L);
+                        float2 pg = make_float2(0.f, 0.f), ps = pg, pB = pg, pS = pg, pQ = pg;
+#pragma unroll 2
+                        for (int k = kb; k < ke; k += L) {
+                            const float4 pk = cP[k];
+                            const float2 dx = __fadd2_rn(fx, lo2(pk)), dy = __fadd2_rn(fy, hi2(pk));
+                            const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                            bool a0 = r2.x < slo, a1 = r2.y < slo;
+                            if (r2.x >= slo && r2.x <= shi) {  // thin shell: the exact FP64 decision
+                                const int b = cand_arena(cc, t0 + 2 * k);
+                                a0 = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
                                 ++shell;
                             }
-                            const float qq = sqrt_apx(r2) * ih;  // r = 0 (the particle itself): q = 0
-                            float t2, t, u2, u;
-                            spline_terms(qq, t2, t, u2, u);
-                            const float w = acc ? fmaf(0.25f * t2, t, -(u2 * u)) : 0.0f;
-                            const float4 v = cq[j];
-                            pg += w;
-                            ps = fmaf(v.x, w, ps);
-                            pB = fmaf(v.y, w, pB);
-                            pS = fmaf(v.z, w, pS);
-                            pQ = fmaf(v.w, w, pQ);
-                            nacc += acc;
+                            if (r2.y >= slo && r2.y <= shi) {
+                                const int b = cand_arena(cc, t0 + 2 * k + 1);
+                                a1 = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                                ++shell;
+                            }
+                            // r = 0 (the particle itself): q = 0
+                            const float2 qq = __fmul2_rn(make_float2(sqrt_apx(r2.x), sqrt_apx(r2.y)), ih2);
+                            float2 t2, t, u2, u;
+                            spline_terms2(qq, t2, t, u2, u);
+                            // w = t^3 / 4 - u^3, rounded as fmaf(0.25 t2, t, -(u2 u))
+                            float2 w = __ffma2_rn(__fmul2_rn(make_float2(0.25f, 0.25f), t2), t,
+                                                  __fmul2_rn(u2, make_float2(-u.x, -u.y)));
+                            w.x = a0 ? w.x : 0.0f;
+                            w.y = a1 ? w.y : 0.0f;
+                            const float4 qa = cQa[k], qb = cQb[k];
+                            pg = __fadd2_rn(pg, w);
+                            ps = __ffma2_rn(lo2(qa), w, ps);
+                            pB = __ffma2_rn(hi2(qa), w, pB);
+                            pS = __ffma2_rn(lo2(qb), w, pS);
+                            pQ = __ffma2_rn(hi2(qb), w, pQ);
+                            nacc += (int)a0 + (int)a1;
                         }
-                        cadd(sg, pg);
-                        cadd(ss, ps);
-                        cadd(sb, pB);
-                        cadd(sS, pS);
-                        cadd(sq, pQ);
+                        cadd(sg, pg.x + pg.y);
+                        cadd(ss, ps.x + ps.y);
+                        cadd(sb, pB.x + pB.y);
+                        cadd(sS, pS.x + pS.y);
+                        cadd(sq, pQ.x + pQ.y);
                     }
                 }
             }
@@ -618,9 +659,10 @@ template <int TT>
 __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const double *__restrict__ y)
 {
     __shared__ int s_base[kMaxSlots];
-    __shared__ float2 cpos[kTile];
-    __shared__ float4 cX[kTile];
-    __shared__ float2 cU[kTile];
+    __shared__ float4 cP[kTile / 2];   // (-x_0, -x_1, -y_0, -y_1) relative to the centre cell
+    __shared__ float4 cXa[kTile / 2];  // (X^xx_0, X^xx_1, X^xy_0, X^xy_1) / sigma*^2
+    __shared__ float4 cXb[kTile / 2];  // (X^yx_0, X^yx_1, X^yy_0, X^yy_1) / sigma*^2
+    __shared__ float4 cU2[kTile / 2];  // (u^x_0, u^x_1, u^y_0, u^y_1) / sigma*
     __shared__ CellCtx cc;
     __shared__ int s_cell;
     const BatchTable *T = A.tab;
@@ -668,52 +710,70 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
                     for (int i = tid; i < mt; i += TT) {
                         float2 rel;
                         const int b = cand_index(cc, t0 + i, A.fpos, rel);
-                        cpos[i] = rel;
-                        cX[i] = A.fX[b];
-                        cU[i] = A.fU[b];
+                        put_pair(cP, i, -rel.x, -rel.y);
+                        const float4 X = A.fX[b];
+                        const float2 U = A.fU[b];
+                        put_pair(cXa, i, X.x, X.y);
+                        put_pair(cXb, i, X.z, X.w);
+                        put_pair(cU2, i, U.x, U.y);
+                    }
+                    if ((mt & 1) && tid == 0) {
+                        put_pair(cP, mt, kFar, kFar);
+                        put_pair(cXa, mt, 0.0f, 0.0f);
+                        put_pair(cXb, mt, 0.0f, 0.0f);
+                        put_pair(cU2, mt, 0.0f, 0.0f);
                     }
                     __syncthreads();
                 }
                 if (valid) {
-                    for (int jb = l; jb < mt; jb += kRun * L) {
-                        const int je = min(mt, jb + kRun * L);
-                        float pGx = 0.f, pGy = 0.f, pHx = 0.f, pHy = 0.f;
-                        float pxx = 0.f, pxy = 0.f, pyx = 0.f, pyy = 0.f;
-#pragma unroll 4
-                        for (int j = jb; j < je; j += L) {
-                            const float2 pb = cpos[j];
-                            const float dx = fa.x - pb.x, dy = fa.y - pb.y;
-                            const float r2 = fmaf(dx, dx, dy * dy);
-                            bool acc = r2 < slo;
-                            if (r2 >= slo && r2 <= shi) {  // thin shell: the exact FP64 decision
-                                const int b = cand_arena(cc, t0 + j);
-                                acc = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                    const float2 fx = make_float2(fa.x, fa.x), fy = make_float2(fa.y, fa.y), ih2 = make_float2(ih, ih);
+                    const int np = (mt + 1) >> 1;
+                    for (int kb = l; kb < np; kb += (kRun / 2) * L) {
+                        const int ke = min(np, kb + (kRun / 2) * L);
+                        float2 pGx = make_float2(0.f, 0.f), pGy = pGx, pHx = pGx, pHy = pGx;
+                        float2 pxx = pGx, pxy = pGx, pyx = pGx, pyy = pGx;
+#pragma unroll 2
+                        for (int k = kb; k < ke; k += L) {
+                            const float4 pk = cP[k];
+                            const float2 dx = __fadd2_rn(fx, lo2(pk)), dy = __fadd2_rn(fy, hi2(pk));
+                            const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                            bool a0 = r2.x < slo, a1 = r2.y < slo;
+                            if (r2.x >= slo && r2.x <= shi) {  // thin shell: the exact FP64 decision
+                                const int b = cand_arena(cc, t0 + 2 * k);
+                                a0 = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
+                            }
+                            if (r2.y >= slo && r2.y <= shi) {
+                                const int b = cand_arena(cc, t0 + 2 * k + 1);
+                                a1 = dist2_2d(xa - y[b], ya - y[P + b]) < supp2;
                             }
                             // r = 0 (the particle itself) gives dw/dq = 0: a zero term
-                            const float ir = rsqrt_apx(fmaxf(r2, 1e-30f));
-                            float t2, t, u2, u;
-                            spline_terms(r2 * ir * ih, t2, t, u2, u);
-                            const float fac = acc ? fmaf(-0.75f, t2, 3.0f * u2) * ir : 0.0f;
-                            const float gx = fac * dx, gy = fac * dy;
-                            const float4 X = cX[j];
-                            const float2 U = cU[j];
-                            pGx += gx;
-                            pGy += gy;
-                            pHx = fmaf(X.x, gx, fmaf(X.z, gy, pHx));
-                            pHy = fmaf(X.y, gx, fmaf(X.w, gy, pHy));
-                            pxx = fmaf(U.x, gx, pxx);
-                            pxy = fmaf(U.y, gx, pxy);
-                            pyx = fmaf(U.x, gy, pyx);
-                            pyy = fmaf(U.y, gy, pyy);
+                            const float2 ir = make_float2(rsqrt_apx(fmaxf(r2.x, 1e-30f)), rsqrt_apx(fmaxf(r2.y, 1e-30f)));
+                            float2 t2, t, u2, u;
+                            spline_terms2(__fmul2_rn(__fmul2_rn(r2, ir), ih2), t2, t, u2, u);
+                            // fac = (3 u^2 - 3 t^2 / 4) / r, rounded as fmaf(-0.75, t2, 3 u2) * ir
+                            float2 fac = __fmul2_rn(__ffma2_rn(make_float2(-0.75f, -0.75f), t2,
+                                                               __fmul2_rn(make_float2(3.0f, 3.0f), u2)), ir);
+                            fac.x = a0 ? fac.x : 0.0f;
+                            fac.y = a1 ? fac.y : 0.0f;
+                            const float2 gx = __fmul2_rn(fac, dx), gy = __fmul2_rn(fac, dy);
+                            const float4 xa4 = cXa[k], xb4 = cXb[k], u4 = cU2[k];
+                            pGx = __fadd2_rn(pGx, gx);
+                            pGy = __fadd2_rn(pGy, gy);
+                            pHx = __ffma2_rn(lo2(xa4), gx, __ffma2_rn(lo2(xb4), gy, pHx));
+                            pHy = __ffma2_rn(hi2(xa4), gx, __ffma2_rn(hi2(xb4), gy, pHy));
+                            pxx = __ffma2_rn(lo2(u4), gx, pxx);
+                            pxy = __ffma2_rn(hi2(u4), gx, pxy);
+                            pyx = __ffma2_rn(lo2(u4), gy, pyx);
+                            pyy = __ffma2_rn(hi2(u4), gy, pyy);
                         }
-                        cadd(Gx, pGx);
-                        cadd(Gy, pGy);
-                        cadd(Hx, pHx);
-                        cadd(Hy, pHy);
-                        cadd(xx, pxx);
-                        cadd(xy, pxy);
-                        cadd(yx, pyx);
-                        cadd(yy, pyy);
+                        cadd(Gx, pGx.x + pGx.y);
+                        cadd(Gy, pGy.x + pGy.y);
+                        cadd(Hx, pHx.x + pHx.y);
+                        cadd(Hy, pHy.x + pHy.y);
+                        cadd(xx, pxx.x + pxx.y);
+                        cadd(xy, pxy.x + pxy.y);
+                        cadd(yx, pyx.x + pyx.y);
+                        cadd(yy, pyy.x + pyy.y);
                     }
                 }
             }
@@ -749,16 +809,23 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
 // results do not depend on the choice)
 constexpr int kTTChoices[] = {64, 96, 128, 192, 256};
 
+// persistent grids of the two tiled passes: each fills every SM with as many blocks as its own
+// registers and shared memory allow (the cells are claimed dynamically, so the grid size does
+// not change the results)
+struct TiledGrid {
+    int d = 0, g = 0;  // density, gradient
+};
+
 template <int TT>
-int tiled_grid(int sms)
+TiledGrid tiled_grid(int sms)
 {
     int o1 = 0, o2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_seg_density<TT>, TT, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_seg_gradient<TT>, TT, 0);
-    return sms * std::max(1, std::min(o1, o2));
+    return TiledGrid{sms * std::max(1, o1), sms * std::max(1, o2)};
 }
 
-int tiled_grid_for(int tt, int sms)
+TiledGrid tiled_grid_for(int tt, int sms)
 {
     switch (tt) {
     case 64: return tiled_grid<64>(sms);
@@ -791,37 +858,54 @@ void tiled_gradient(int tt, int grid, cudaStream_t st, const Arena &A, int stage
     }
 }
 
-// stage work rate per stepping event: fixed-order sum over the warps of its range; stage 2
-// closes the step (Heun quadrature of the work integral, tau += dtau)
-// per event: the stage's work rate, a fixed-order sum of its particles' rates (thread t takes
-// particles t, t + 256, ...; then a tree), independent of the rest of the batch
-__global__ void __launch_bounds__(256) k_seg_work(Arena A, int stage)
+// The work integral's rate per event: the sum of its particles' (p + Pi + tau^2 pi^{eta eta}) /
+// sigma* in a fixed order that depends on the event alone.  Its range splits into kWorkChunks
+// chunks of a size set by its particle count (a multiple of 256); block (c, s) sums chunk c of
+// slot s, and k_seg_work adds the chunks in order.
+constexpr int kWorkChunks = 16;
+
+__device__ __forceinline__ double block_sum_fixed(double acc, double *sh)
 {
-    __shared__ double sh[256];
-    const int s = blockIdx.x;
-    const BatchTable *T = A.tab;
-    if (s >= T->nslots || T->slots[s].mode != SLOT_STEP) return;
-    const SegSlot sl = T->slots[s];
-    double acc = 0.0;
-    for (int a = sl.off + (int)threadIdx.x; a < sl.off + sl.n; a += 256) acc += A.wpart[a];
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
-    acc = sh[0];
-    if (threadIdx.x == 0) {
-        DevScalars &sc = A.sc[s];
-        const EvView &V = A.segv[s];
-        sc.wr[stage - 1] = V.milne ? acc : 0.0;
-        if (stage == 2) {
-            sc.work += 0.5 * V.dtau * (sc.wr[0] + sc.wr[1]);
-            sc.tau = sc.tau + V.dtau;
-            sc.steps += 1;
-            // the host's view of the event's health (read before later launches)
-            if (A.hflags) *(volatile unsigned int *)(A.hflags + s) = sc.status_or;
-        }
+    return sh[0];
+}
+
+__global__ void __launch_bounds__(256) k_seg_work_part(Arena A)
+{
+    __shared__ double sh[256];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const BatchTable *T = A.tab;
+    if (s >= T->nslots || T->slots[s].mode != SLOT_STEP) return;
+    const SegSlot sl = T->slots[s];
+    const int cs = ((sl.n + kWorkChunks - 1) / kWorkChunks + 255) & ~255;
+    const int b0 = c * cs, b1 = min(sl.n, b0 + cs);
+    double acc = 0.0;
+    for (int i = b0 + (int)threadIdx.x; i < b1; i += 256) acc += A.wpart[sl.off + i];
+    acc = block_sum_fixed(acc, sh);  // every block reaches it: the return above is block-uniform
+    if (threadIdx.x == 0) A.wchunk[s * kWorkChunks + c] = acc;
+}
+
+__global__ void k_seg_work(Arena A, int stage)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const BatchTable *T = A.tab;
+    if (s >= T->nslots || T->slots[s].mode != SLOT_STEP) return;
+    double acc = 0.0;
+    for (int c = 0; c < kWorkChunks; ++c) acc += A.wchunk[s * kWorkChunks + c];
+    DevScalars &sc = A.sc[s];
+    const EvView &V = A.segv[s];
+    sc.wr[stage - 1] = V.milne ? acc : 0.0;
+    if (stage == 2) {
+        sc.work += 0.5 * V.dtau * (sc.wr[0] + sc.wr[1]);
+        sc.tau = sc.tau + V.dtau;
+        sc.steps += 1;
+        // the host's view of the event's health (read before later launches)
+        if (A.hflags) *(volatile unsigned int *)(A.hflags + s) = sc.status_or;
     }
 }
 
@@ -990,7 +1074,8 @@ struct sph_server {
     std::vector<void *> allocs;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    int max_events = 0, inflight = 2, grid_p = 0, grid_e = 0, grid_c = 0, sms = 1;
+    int max_events = 0, inflight = 2, grid_p = 0, grid_e = 0, sms = 1;
+    TiledGrid grid_c;  // persistent grids of the tiled passes
     int tt = kTTDefault;  // threads per block of the tiled passes
     int polish = 0;
     // pinned staging pool
@@ -1049,7 +1134,9 @@ sph_status dmalloc(sph_server *S, void **p, size_t bytes)
     return SPH_OK;
 }
 
-constexpr int kKernelsPerBatchStep = 2 * 14;
+// kernels a batch step launches: per stage 11 for the cell list and permutation, then the
+// density, EoS, gradient and equations-of-motion passes and the two of the work sum
+constexpr int kKernelsPerBatchStep = 2 * 17;
 
 // one batch step (both stages) on the server's stream; captured once into a graph.  marks (the
 // sampled timing, eager launches only): kProfMarks events recorded between the kernel groups
@@ -1098,16 +1185,17 @@ void enqueue_batch_step(sph_server *S, const cudaEvent_t *marks = nullptr)
         mark(stage, 1);
         const double *ys = stage == 1 ? A.Y[1] : A.Y1[1];
         const double *nq = stage == 1 ? A.Nq[1] : A.Nq[0];
-        tiled_density(S->tt, S->grid_c, st, A, ys, nq);
+        tiled_density(S->tt, S->grid_c.d, st, A, ys, nq);
         mark(stage, 2);
         launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st);
         mark(stage, 3);
-        tiled_gradient(S->tt, S->grid_c, st, A, stage, ys);
+        tiled_gradient(S->tt, S->grid_c.g, st, A, stage, ys);
         mark(stage, 4);
         if (stage == 1) launch_eom2_seg(A, 1, 0, ys, A.Y1[0], S->grid_p, st);
         else launch_eom2_seg(A, 2, 1, ys, A.Y[0], S->grid_p, st);
         mark(stage, 5);
-        k_seg_work<<<S->max_events, 256, 0, st>>>(A, stage);
+        k_seg_work_part<<<dim3(kWorkChunks, S->max_events), 256, 0, st>>>(A);
+        k_seg_work<<<(S->max_events + 127) / 128, 128, 0, st>>>(A, stage);
         mark(stage, 6);
     }
     (void)P;
@@ -1476,6 +1564,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     SAL(A.status, sizeof(uint32_t) * Pz);
     SAL(A.nnb, sizeof(int) * Pz);
     SAL(A.wpart, sizeof(double) * Pz);
+    SAL(A.wchunk, sizeof(double) * kMaxSlots * kWorkChunks);
     SAL(A.key, sizeof(uint32_t) * Pz);
     SAL(A.rnk, sizeof(uint32_t) * Pz);
     SAL(A.tmp, sizeof(uint32_t) * Pz);
@@ -1839,13 +1928,13 @@ sph_status sph_server_autotune(sph_server *S, int32_t trials, int32_t *chosen, i
     for (int lw : kLaneWarpChoices)
         for (int tt : kTTChoices) {
             A.lane_warps = lw;
-            const int grid = tiled_grid_for(tt, S->sms);
+            const TiledGrid grid = tiled_grid_for(tt, S->sms);
             float tot = 0.0f;
             for (int r = 0; r <= trials; ++r) {  // r = 0: warm-up
                 SCK(cudaMemsetAsync(A.claim, 0, sizeof(unsigned int) * kClaims, S->st));
                 SCK(cudaEventRecord(e0, S->st));
-                tiled_density(tt, grid, S->st, A, A.Y1[1], A.Nq[0]);
-                tiled_gradient(tt, grid, S->st, A, 2, A.Y1[1]);
+                tiled_density(tt, grid.d, S->st, A, A.Y1[1], A.Nq[0]);
+                tiled_gradient(tt, grid.g, S->st, A, 2, A.Y1[1]);
                 SCK(cudaEventRecord(e1, S->st));
                 SCK(cudaGetLastError());
                 sph_status s = wait_event(S, e1);

@@ -552,6 +552,7 @@ struct Arena {
     int P, cmax;  // particle and cell capacity
     int lane_warps;  // tiled neighbour passes: warps whose lanes share a cell's particles (the tuned shape)
     unsigned int *hflags;  // mapped pinned host words: per slot, its status OR after each batch step
+    double *wchunk;        // per slot, partial sums of the work rates over fixed chunks of its range
     double *Y[2], *Y1[2], *Nq[2];
     int *id[2];
     double *wguess, *guess_in;
