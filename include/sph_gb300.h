@@ -414,7 +414,12 @@ typedef struct {
     int64_t pinned_bytes;  /* pinned host staging pool (0: 256 bytes per arena particle) */
     void *stream;          /* cudaStream_t of all server work, NULL: library-created */
     int32_t polish;        /* 1: a Newton polishing step after convergence, as the plain form */
-    int32_t reserved;
+    int32_t groups;        /* 1: every pass over all events in turn; 0 or 2: the events split into
+                              two groups of about equal particle counts, the second group's passes
+                              one pass behind the first's on a second branch of the step graph,
+                              so that the passes of one group fill the tails of the other's (the
+                              FP64-bound EoS and equations of motion beside the FP32 neighbour
+                              passes); results are bitwise the same either way */
     double newton_tol;     /* EoS Newton tolerance on max |residual|/s (<= 0: 1e-10; the plain form
                               uses the EoS handle's, 1e-12 by default) */
 } sph_server_desc;

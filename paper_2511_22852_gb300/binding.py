@@ -85,7 +85,7 @@ class Totals(C.Structure):
 class ServerDesc(C.Structure):
     _fields_ = [("max_events", C.c_int32), ("max_inflight", C.c_int32), ("max_particles", C.c_int64),
                 ("hbm_fraction", C.c_double), ("pinned_bytes", C.c_int64), ("stream", C.c_void_p),
-                ("polish", C.c_int32), ("reserved", C.c_int32), ("newton_tol", C.c_double)]
+                ("polish", C.c_int32), ("groups", C.c_int32), ("newton_tol", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -386,13 +386,14 @@ class GpuServer:
     """The serving form: events submitted from ``inputs.Event`` objects, batched on the GPU."""
 
     def __init__(self, eos, table=None, max_events=32, max_particles=0, hbm_fraction=0.0, pinned_bytes=0,
-                 polish=False, max_inflight=2, stream=None, newton_tol=0.0):
+                 polish=False, max_inflight=2, stream=None, newton_tol=0.0, groups=0):
         ed, self._keep_eos = eos_desc(eos, table)
         self.eos = sph_set_eos_table(ed)
         d = ServerDesc()
         d.max_events, d.max_inflight, d.max_particles = int(max_events), int(max_inflight), int(max_particles)
         d.hbm_fraction, d.pinned_bytes, d.stream, d.polish = float(hbm_fraction), int(pinned_bytes), stream, int(polish)
         d.newton_tol = float(newton_tol)
+        d.groups = int(groups)
         self.h = sph_server_create(d, self.eos)
         self.n_of = {}
 

@@ -316,6 +316,7 @@ struct SegEosCtx {
     const Arena &A;
     const BatchTable *T;
     int stage;
+    int grp;  // event group (-1: every event)
     size_t P;
     const double *__restrict__ y;
     unsigned int *sh;  // [kMaxSlots][4]: table evaluations, solves, closed-form evaluations, status bits
@@ -326,7 +327,7 @@ struct SegEosCtx {
     __device__ bool load(int a, double &s, double nq[3], double g[4], double &cap)
     {
         const int sl = A.segid[a];
-        if (sl < 0 || !seg_active(T, sl, stage, false)) return false;
+        if (sl < 0 || !seg_active(T, sl, stage, false) || !in_group(T, sl, grp)) return false;
         const SegSlot q = T->slots[sl];
         if (a - q.off >= q.n) return false;
         slot = sl;
@@ -356,16 +357,17 @@ struct SegEosCtx {
     }
 };
 
-__global__ void __launch_bounds__(32 * kEosWarps, kEosBlocksPerSM) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y)
+__global__ void __launch_bounds__(32 * kEosWarps, kEosBlocksPerSM) k_eos2_seg(Arena A, EosDev E, int stage, const double *__restrict__ y,
+                                                                             int grp)
 {
     __shared__ unsigned int sh[kMaxSlots * 4];
     for (int i = threadIdx.x; i < kMaxSlots * 4; i += blockDim.x) sh[i] = 0u;
     __syncthreads();
     const BatchTable *T = A.tab;
     EosWork w = {0u, 0u, 0u};
-    SegEosCtx ctx{A, T, stage, (size_t)A.P, y, sh, &w, w, -1, {0.0, 0.0, 0.0, 0.0}};
+    SegEosCtx ctx{A, T, stage, grp, (size_t)A.P, y, sh, &w, w, -1, {0.0, 0.0, 0.0, 0.0}};
     // E is the server's EoS (every event's view carries the same)
-    eos_lanes(E, &A.claim[CLAIM_EOS], T->hi, ctx, w);
+    eos_lanes(E, &A.claim[claim_of(CLAIM_EOS, grp)], T->hi, ctx, w);
     __syncthreads();
     const int ns = T->nslots;
     for (int s = threadIdx.x; s < ns; s += blockDim.x) {
@@ -469,9 +471,9 @@ void launch_inverse_build(const EosDev &E, double *inv, long long nnodes, cudaSt
     k_inverse_build<<<grid, 128, 0, st>>>(online, inv, nnodes);
 }
 
-void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st)
+void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st, int grp)
 {
-    k_eos2_seg<<<grid, 32 * kEosWarps, 0, st>>>(A, E, stage, y);
+    k_eos2_seg<<<grid, 32 * kEosWarps, 0, st>>>(A, E, stage, y, grp);
 }
 
 int eos_seg_grid(int sms) { return kEosBlocksPerSM * sms; }

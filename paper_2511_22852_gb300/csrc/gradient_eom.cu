@@ -445,13 +445,13 @@ __global__ void __launch_bounds__(128) k_eom2(EvView v, int stage, int mode, con
 
 // Serving form: the equations of motion over the segmented arena (persistent grid)
 __global__ void __launch_bounds__(128) k_eom2_seg(Arena A, int stage, int mode, const double *__restrict__ ys,
-                                                  double *__restrict__ yout)
+                                                  double *__restrict__ yout, int grp)
 {
     const BatchTable *T = A.tab;
     const int hi = T->hi;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < hi; a += gridDim.x * blockDim.x) {
         const int s = A.segid[a];
-        if (s < 0 || !seg_active(T, s, stage, true)) continue;
+        if (s < 0 || !seg_active(T, s, stage, true) || !in_group(T, s, grp)) continue;
         if (a - T->slots[s].off >= T->slots[s].n) continue;
         eom2_particle(A.segv[s], stage, mode, (size_t)A.P, (size_t)a, ys, A.dens, A.eosf, A.gout, yout, nullptr,
                       A.status);
@@ -570,9 +570,9 @@ void launch_eom(const EvView &v, int stage, int mode, const double *ys, const do
 }
 
 void launch_eom2_seg(const Arena &A, int stage, int mode, const double *ys, double *yout, int grid,
-                     cudaStream_t st)
+                     cudaStream_t st, int grp)
 {
-    k_eom2_seg<<<grid, 128, 0, st>>>(A, stage, mode, ys, yout);
+    k_eom2_seg<<<grid, 128, 0, st>>>(A, stage, mode, ys, yout, grp);
 }
 
 void launch_work_finish(const EvView &v, int stage, const double *wpart, int nb, cudaStream_t st)

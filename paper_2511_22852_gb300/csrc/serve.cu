@@ -37,6 +37,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -178,8 +179,12 @@ __global__ void __launch_bounds__(kMaxSlots) k_seg_grid(Arena A, int stage)
     if (s < T->nslots) {
         A.grid[s].base = sh[s] - nc;
         A.grid[s].ncell = nc;
+        if (s == T->split) A.ncells[1] = sh[s] - nc;  // group 1's cells start at its first slot's
     }
-    if (s == kMaxSlots - 1) *A.ncells = sh[s];
+    if (s == kMaxSlots - 1) {
+        A.ncells[0] = sh[s];
+        if (T->split >= T->nslots) A.ncells[1] = sh[s];  // group 1 is empty
+    }
     if (s < kClaims) A.claim[s] = 0u;
 }
 
@@ -498,7 +503,7 @@ __device__ __forceinline__ void spline_terms2(float2 q, float2 &t2, float2 &t, f
 // thin shell takes a branch, to the exact FP64 test.
 template <int TT>
 __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__restrict__ y,
-                                                     const double *__restrict__ Nq)
+                                                     const double *__restrict__ Nq, int grp)
 {
     __shared__ int s_base[kMaxSlots];
     __shared__ float4 cP[kTile / 2];   // (-x_0, -x_1, -y_0, -y_1) relative to the centre cell
@@ -514,19 +519,20 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
         s_cur = -1;
         s_acc[0] = s_acc[1] = 0ull;
     }
-    const int ncells = *A.ncells;
+    // the cells of the event group (grp < 0: all): group 0's come first
+    const int c_lo = grp > 0 ? A.ncells[1] : 0, c_hi = grp == 0 ? A.ncells[1] : A.ncells[0];
     const size_t P = (size_t)A.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = TT / 32;
     for (;;) {
         __syncthreads();  // the previous cell's context and tile are no longer read
         if (warp == 0) {
-            int c = lane == 0 ? (int)atomicAdd(&A.claim[CLAIM_DENSITY], 1u) : 0;
+            int c = lane == 0 ? c_lo + (int)atomicAdd(&A.claim[claim_of(CLAIM_DENSITY, grp)], 1u) : 0;
             c = __shfl_sync(0xFFFFFFFFu, c, 0);
             if (lane == 0) s_cell = c;
-            if (c < ncells && A.cnt[c] > 0u) cell_setup(A, s_base, ns, c, cc, lane);
+            if (c < c_hi && A.cnt[c] > 0u) cell_setup(A, s_base, ns, c, cc, lane);
             else if (lane == 0) cc.na = 0;
-            const int snew = c < ncells ? (cc.na > 0 ? cc.s : s_cur) : -1;
+            const int snew = c < c_hi ? (cc.na > 0 ? cc.s : s_cur) : -1;
             if (lane == 0 && snew != s_cur) {
                 if (s_cur >= 0) {
                     if (s_acc[0]) atomicAdd(&A.sc[s_cur].pairs, s_acc[0]);
@@ -537,7 +543,7 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
             }
         }
         __syncthreads();
-        if (s_cell >= ncells) break;
+        if (s_cell >= c_hi) break;
         const int na = cc.na;
         if (na == 0) continue;
         const EvView &V = A.segv[cc.s];
@@ -656,7 +662,7 @@ __global__ void __launch_bounds__(TT) k_seg_density(Arena A, const double *__res
 }
 
 template <int TT>
-__global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const double *__restrict__ y)
+__global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const double *__restrict__ y, int grp)
 {
     __shared__ int s_base[kMaxSlots];
     __shared__ float4 cP[kTile / 2];   // (-x_0, -x_1, -y_0, -y_1) relative to the centre cell
@@ -668,7 +674,7 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
     const BatchTable *T = A.tab;
     const int ns = T->nslots;
     for (int i = threadIdx.x; i < ns; i += TT) s_base[i] = A.grid[i].base;
-    const int ncells = *A.ncells;
+    const int c_lo = grp > 0 ? A.ncells[1] : 0, c_hi = grp == 0 ? A.ncells[1] : A.ncells[0];
     const size_t P = (size_t)A.P;
     const double *gin = A.gin;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -676,16 +682,16 @@ __global__ void __launch_bounds__(TT) k_seg_gradient(Arena A, int stage, const d
     for (;;) {
         __syncthreads();
         if (warp == 0) {
-            int c = lane == 0 ? (int)atomicAdd(&A.claim[CLAIM_GRADIENT], 1u) : 0;
+            int c = lane == 0 ? c_lo + (int)atomicAdd(&A.claim[claim_of(CLAIM_GRADIENT, grp)], 1u) : 0;
             c = __shfl_sync(0xFFFFFFFFu, c, 0);
             if (lane == 0) s_cell = c;
-            bool work = c < ncells && A.cnt[c] > 0u;
+            bool work = c < c_hi && A.cnt[c] > 0u;
             if (work) work = T->slots[find_slot(s_base, ns, c)].mode == SLOT_STEP;
             if (work) cell_setup(A, s_base, ns, c, cc, lane);
             else if (lane == 0) cc.na = 0;
         }
         __syncthreads();
-        if (s_cell >= ncells) break;
+        if (s_cell >= c_hi) break;
         const int na = cc.na;
         if (na == 0) continue;
         const EvView &V = A.segv[cc.s];
@@ -836,25 +842,25 @@ TiledGrid tiled_grid_for(int tt, int sms)
     }
 }
 
-void tiled_density(int tt, int grid, cudaStream_t st, const Arena &A, const double *ys, const double *nq)
+void tiled_density(int tt, int grid, cudaStream_t st, const Arena &A, const double *ys, const double *nq, int grp = -1)
 {
     switch (tt) {
-    case 64: k_seg_density<64><<<grid, 64, 0, st>>>(A, ys, nq); break;
-    case 96: k_seg_density<96><<<grid, 96, 0, st>>>(A, ys, nq); break;
-    case 192: k_seg_density<192><<<grid, 192, 0, st>>>(A, ys, nq); break;
-    case 256: k_seg_density<256><<<grid, 256, 0, st>>>(A, ys, nq); break;
-    default: k_seg_density<128><<<grid, 128, 0, st>>>(A, ys, nq); break;
+    case 64: k_seg_density<64><<<grid, 64, 0, st>>>(A, ys, nq, grp); break;
+    case 96: k_seg_density<96><<<grid, 96, 0, st>>>(A, ys, nq, grp); break;
+    case 192: k_seg_density<192><<<grid, 192, 0, st>>>(A, ys, nq, grp); break;
+    case 256: k_seg_density<256><<<grid, 256, 0, st>>>(A, ys, nq, grp); break;
+    default: k_seg_density<128><<<grid, 128, 0, st>>>(A, ys, nq, grp); break;
     }
 }
 
-void tiled_gradient(int tt, int grid, cudaStream_t st, const Arena &A, int stage, const double *ys)
+void tiled_gradient(int tt, int grid, cudaStream_t st, const Arena &A, int stage, const double *ys, int grp = -1)
 {
     switch (tt) {
-    case 64: k_seg_gradient<64><<<grid, 64, 0, st>>>(A, stage, ys); break;
-    case 96: k_seg_gradient<96><<<grid, 96, 0, st>>>(A, stage, ys); break;
-    case 192: k_seg_gradient<192><<<grid, 192, 0, st>>>(A, stage, ys); break;
-    case 256: k_seg_gradient<256><<<grid, 256, 0, st>>>(A, stage, ys); break;
-    default: k_seg_gradient<128><<<grid, 128, 0, st>>>(A, stage, ys); break;
+    case 64: k_seg_gradient<64><<<grid, 64, 0, st>>>(A, stage, ys, grp); break;
+    case 96: k_seg_gradient<96><<<grid, 96, 0, st>>>(A, stage, ys, grp); break;
+    case 192: k_seg_gradient<192><<<grid, 192, 0, st>>>(A, stage, ys, grp); break;
+    case 256: k_seg_gradient<256><<<grid, 256, 0, st>>>(A, stage, ys, grp); break;
+    default: k_seg_gradient<128><<<grid, 128, 0, st>>>(A, stage, ys, grp); break;
     }
 }
 
@@ -1076,6 +1082,15 @@ struct sph_server {
     bool own_stream = false;
     int max_events = 0, inflight = 2, grid_p = 0, grid_e = 0, sms = 1;
     TiledGrid grid_c;  // persistent grids of the tiled passes
+    // Two-group schedule: the events split into two groups of about equal particle counts
+    // (contiguous slot ranges); group 1's passes run on a second branch of the step graph one
+    // pass behind group 0's, so that one group's FP64-bound passes (EoS, equations of motion)
+    // and the other's FP32 neighbour passes fill each other's tails.  Each pass keeps its full
+    // persistent grid: splitting the register file between a FP64 and a FP32 pass (fewer
+    // blocks for each) measured slower, since both need most of it.
+    int groups = 2;
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t fk[2] = {nullptr, nullptr};
     int tt = kTTDefault;  // threads per block of the tiled passes
     int polish = 0;
     // pinned staging pool
@@ -1097,8 +1112,9 @@ struct sph_server {
     int *ires_d = nullptr;
     int res_cap = 0;
     // step graph and pacing
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // the step graph: [0] all events in turn, [1] overlapped groups
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    bool split_ok = false;  // the current table has two non-empty event groups
     std::vector<cudaEvent_t> step_ev;
     std::vector<cudaEvent_t> step_t0;  // timing events at the start of each batch step (same ring)
     long long steps_launched = 0, steps_timed = 0;
@@ -1140,7 +1156,7 @@ constexpr int kKernelsPerBatchStep = 2 * 17;
 
 // one batch step (both stages) on the server's stream; captured once into a graph.  marks (the
 // sampled timing, eager launches only): kProfMarks events recorded between the kernel groups
-void enqueue_batch_step(sph_server *S, const cudaEvent_t *marks = nullptr)
+void enqueue_batch_step(sph_server *S, const cudaEvent_t *marks = nullptr, bool overlap = false)
 {
     const Arena &A = S->A;
     cudaStream_t st = S->st;
@@ -1185,15 +1201,34 @@ void enqueue_batch_step(sph_server *S, const cudaEvent_t *marks = nullptr)
         mark(stage, 1);
         const double *ys = stage == 1 ? A.Y[1] : A.Y1[1];
         const double *nq = stage == 1 ? A.Nq[1] : A.Nq[0];
-        tiled_density(S->tt, S->grid_c.d, st, A, ys, nq);
-        mark(stage, 2);
-        launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st);
-        mark(stage, 3);
-        tiled_gradient(S->tt, S->grid_c.g, st, A, stage, ys);
-        mark(stage, 4);
-        if (stage == 1) launch_eom2_seg(A, 1, 0, ys, A.Y1[0], S->grid_p, st);
-        else launch_eom2_seg(A, 2, 1, ys, A.Y[0], S->grid_p, st);
-        mark(stage, 5);
+        double *yout = stage == 1 ? A.Y1[0] : A.Y[0];
+        const int mode = stage == 1 ? 0 : 1;
+        if (overlap && !marks) {
+            // group 0 on st; group 1 on st2 from the end of group 0's densities, so its density
+            // pass meets group 0's EoS, its EoS group 0's gradient, its gradient group 0's
+            // equations of motion; then st waits for group 1
+            tiled_density(S->tt, S->grid_c.d, st, A, ys, nq, 0);
+            cudaEventRecord(S->fk[0], st);
+            cudaStreamWaitEvent(S->st2, S->fk[0], 0);
+            launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st, 0);
+            tiled_density(S->tt, S->grid_c.d, S->st2, A, ys, nq, 1);
+            tiled_gradient(S->tt, S->grid_c.g, st, A, stage, ys, 0);
+            launch_eos2_seg(A, S->E, stage, ys, S->grid_e, S->st2, 1);
+            launch_eom2_seg(A, stage, mode, ys, yout, S->grid_p, st, 0);
+            tiled_gradient(S->tt, S->grid_c.g, S->st2, A, stage, ys, 1);
+            launch_eom2_seg(A, stage, mode, ys, yout, S->grid_p, S->st2, 1);
+            cudaEventRecord(S->fk[1], S->st2);
+            cudaStreamWaitEvent(st, S->fk[1], 0);
+        } else {
+            tiled_density(S->tt, S->grid_c.d, st, A, ys, nq);
+            mark(stage, 2);
+            launch_eos2_seg(A, S->E, stage, ys, S->grid_e, st);
+            mark(stage, 3);
+            tiled_gradient(S->tt, S->grid_c.g, st, A, stage, ys);
+            mark(stage, 4);
+            launch_eom2_seg(A, stage, mode, ys, yout, S->grid_p, st);
+            mark(stage, 5);
+        }
         k_seg_work_part<<<dim3(kWorkChunks, S->max_events), 256, 0, st>>>(A);
         k_seg_work<<<(S->max_events + 127) / 128, 128, 0, st>>>(A, stage);
         mark(stage, 6);
@@ -1248,6 +1283,23 @@ sph_status upload_table(sph_server *S)
     S->tab_ring_i = (S->tab_ring_i + 1) % S->tab_ring_n;
     b.hi = S->hi;
     b.nslots = S->nslots;
+    // the event groups: the slot boundary closest to half the particles (group 1 empty with one
+    // schedule or a single event)
+    b.split = S->nslots;
+    if (S->groups == 2) {
+        long long tot = 0, cum = 0, best = -1;
+        for (int s = 0; s < S->nslots; ++s)
+            if (S->slots[s].mode != SLOT_FREE) tot += S->slots[s].n;
+        for (int s = 1; s < S->nslots; ++s) {
+            if (S->slots[s - 1].mode != SLOT_FREE) cum += S->slots[s - 1].n;
+            const long long d = std::llabs(2 * cum - tot);
+            if (cum > 0 && cum < tot && (best < 0 || d < best)) {
+                best = d;
+                b.split = s;
+            }
+        }
+    }
+    S->split_ok = b.split < S->nslots;
     for (int s = 0; s < S->nslots; ++s) b.slots[s] = S->slots[s];
     const size_t bytes = offsetof(BatchTable, slots) + sizeof(SegSlot) * (size_t)std::max(S->nslots, 1);
     SCK(cudaMemcpyAsync(S->A.tab, &b, bytes, cudaMemcpyHostToDevice, S->st));
@@ -1410,14 +1462,16 @@ sph_status batch_step(sph_server *S)
     }
     sph_status s = upload_table(S);
     if (s != SPH_OK) return s;
-    if (!S->gexec) {
+    // the overlapped graph when the table has two non-empty event groups
+    const int gi = (S->groups == 2 && S->split_ok) ? 1 : 0;
+    if (!S->gexec[gi]) {
         SCK(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
-        enqueue_batch_step(S);
+        enqueue_batch_step(S, nullptr, gi == 1);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(S->st, &g);
         if (e != cudaSuccess) return sfail(SPH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-        S->graph = g;
-        SCK(cudaGraphInstantiate(&S->gexec, g, 0));
+        S->graph[gi] = g;
+        SCK(cudaGraphInstantiate(&S->gexec[gi], g, 0));
     }
     SCK(cudaEventRecord(ev0, S->st));
     const size_t ring_i = (size_t)(k % (long long)S->step_ev.size());
@@ -1427,7 +1481,7 @@ sph_status batch_step(sph_server *S)
         S->prof_step[ring_i] = k;
     } else {
         if (!S->prof_step.empty()) S->prof_step[ring_i] = -1;
-        SCK(cudaGraphLaunch(S->gexec, S->st));
+        SCK(cudaGraphLaunch(S->gexec[gi], S->st));
     }
     SCK(cudaEventRecord(ev, S->st));
     S->steps_launched += 1;
@@ -1478,10 +1532,12 @@ void apply_shape(sph_server *S, int tt, int lw)
     S->tt = tt;
     S->A.lane_warps = lw;
     S->grid_c = tiled_grid_for(tt, S->sms);
-    if (S->gexec) cudaGraphExecDestroy(S->gexec);
-    if (S->graph) cudaGraphDestroy(S->graph);
-    S->gexec = nullptr;
-    S->graph = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (S->gexec[i]) cudaGraphExecDestroy(S->gexec[i]);
+        if (S->graph[i]) cudaGraphDestroy(S->graph[i]);
+        S->gexec[i] = nullptr;
+        S->graph[i] = nullptr;
+    }
 }
 
 }  // namespace
@@ -1576,7 +1632,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     SAL(A.cnt, sizeof(uint32_t) * (size_t)A.cmax);
     SAL(A.start, sizeof(uint32_t) * (size_t)A.cmax);
     SAL(A.scan_part, sizeof(uint32_t) * kScanBlocks);
-    SAL(A.ncells, sizeof(int));
+    SAL(A.ncells, sizeof(int) * 2);
     SAL(A.claim, sizeof(unsigned int) * kClaims);
     SAL(A.tab, sizeof(BatchTable));
     SAL(A.grid, sizeof(SegGrid) * kMaxSlots);
@@ -1585,7 +1641,7 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     if (cudaMemsetAsync(A.segid, 0xFF, sizeof(int) * Pz, S->st) != cudaSuccess ||
         cudaMemsetAsync(A.tab, 0, sizeof(BatchTable), S->st) != cudaSuccess ||
         cudaMemsetAsync(A.grid, 0, sizeof(SegGrid) * kMaxSlots, S->st) != cudaSuccess ||
-        cudaMemsetAsync(A.ncells, 0, sizeof(int), S->st) != cudaSuccess ||
+        cudaMemsetAsync(A.ncells, 0, sizeof(int) * 2, S->st) != cudaSuccess ||
         cudaMemsetAsync(A.claim, 0, sizeof(unsigned int) * kClaims, S->st) != cudaSuccess) {
         cudaGetLastError();
         return bail(sfail(SPH_ERR_CUDA, "cudaMemsetAsync failed"));
@@ -1639,6 +1695,15 @@ sph_status sph_server_create(sph_server **out, const sph_server_desc *d, const s
     S->grid_p = sms * 8;
     S->grid_c = tiled_grid_for(S->tt, sms);
     S->grid_e = eos_seg_grid(sms);
+    S->groups = d->groups == 1 ? 1 : 2;
+    if (S->groups == 2) {
+        if (cudaStreamCreateWithFlags(&S->st2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&S->fk[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&S->fk[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(sfail(SPH_ERR_CUDA, "second stream of the overlapped schedule"));
+        }
+    }
     // host/device clock reference for completion times
     if (cudaEventCreate(&S->ref_ev) != cudaSuccess || cudaEventRecord(S->ref_ev, S->st) != cudaSuccess ||
         cudaEventSynchronize(S->ref_ev) != cudaSuccess) {
@@ -1663,8 +1728,10 @@ void sph_server_free(sph_server *S)
         delete t;
     }
     S->tickets.clear();
-    if (S->gexec) cudaGraphExecDestroy(S->gexec);
-    if (S->graph) cudaGraphDestroy(S->graph);
+    for (int i = 0; i < 2; ++i) {
+        if (S->gexec[i]) cudaGraphExecDestroy(S->gexec[i]);
+        if (S->graph[i]) cudaGraphDestroy(S->graph[i]);
+    }
     for (auto e : S->step_ev)
         if (e) cudaEventDestroy(e);
     for (auto e : S->step_t0)
@@ -1677,6 +1744,9 @@ void sph_server_free(sph_server *S)
     if (S->tab_ring) cudaFreeHost(S->tab_ring);
     if (S->hflags) cudaFreeHost(S->hflags);
     if (S->own_stream && S->st) cudaStreamDestroy(S->st);
+    if (S->st2) cudaStreamDestroy(S->st2);
+    for (cudaEvent_t e : S->fk)
+        if (e) cudaEventDestroy(e);
     if (S->eos_held) sph_free_eos(S->eos);  // drops the server's reference
     delete S;
 }

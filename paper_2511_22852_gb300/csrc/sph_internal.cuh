@@ -545,7 +545,8 @@ struct SegGrid {  // device-written, per slot and stage: bounding box and cell g
 struct BatchTable {  // host-written
     int hi;          // arena high-water mark: every kernel loops over [0, hi)
     int nslots;      // slots in use (table length)
-    int pad[2];
+    int split;       // first slot of event group 1 (groups: slots [0, split) and [split, nslots))
+    int pad;
     SegSlot slots[kMaxSlots];
 };
 struct Arena {
@@ -570,14 +571,21 @@ struct Arena {
     float2 *fpos;
     float4 *fq, *fX;
     float2 *fU;
-    int *ncells;  // device-written total of the active slots' cells
+    int *ncells;  // device-written: [0] the active slots' cells, [1] those of event group 0
     unsigned int *claim;  // work counters of the dynamically scheduled passes (reset per stage)
     BatchTable *tab;
     SegGrid *grid;
     EvView *segv;
     DevScalars *sc;
 };
-constexpr int CLAIM_EOS = 0, CLAIM_DENSITY = 1, CLAIM_GRADIENT = 2, kClaims = 4;
+// work counters of the dynamically scheduled passes; event group g (0 or 1) uses index + 4 g
+constexpr int CLAIM_EOS = 0, CLAIM_DENSITY = 1, CLAIM_GRADIENT = 2, kClaims = 8;
+__device__ __forceinline__ int claim_of(int which, int grp) { return which + (grp > 0 ? 4 : 0); }
+// slot s in event group grp (grp < 0: every slot)
+__device__ __forceinline__ bool in_group(const BatchTable *t, int s, int grp)
+{
+    return grp < 0 || ((s >= t->split) == (grp > 0));
+}
 // slot s takes part in this stage's pass: stage 1 evaluates STEP and OBSERVE slots, stage 2
 // and the rate passes (gradient, equations of motion, work) only STEP slots
 __device__ __forceinline__ bool seg_active(const BatchTable *t, int s, int stage, bool rates)
@@ -616,13 +624,15 @@ void launch_inverse_build(const EosDev &E, double *inv, long long nnodes, cudaSt
 EosDev eos_params(const ::sph_eos *e);
 void eos_retain(::sph_eos *e);
 
-void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st);
+// grp: the event group the pass covers (-1: every event)
+void launch_eos2_seg(const Arena &A, const EosDev &E, int stage, const double *y, int grid, cudaStream_t st,
+                     int grp = -1);
 int eos_seg_grid(int sms);  // persistent grid of the serving EoS pass
 // BSQ diffusion inputs and neighbour sums of a stage (2+1D; after the EoS pass)
 void launch_diffusion(const EvView &v, int stage, const double *y, const double *dens, const double *eos,
                       const uint32_t *status, CellBufs cb, cudaStream_t st);
 void launch_eom2_seg(const Arena &A, int stage, int mode, const double *ys, double *yout, int grid,
-                     cudaStream_t st);
+                     cudaStream_t st, int grp = -1);
 
 // freeze-out surface elements (freezeout.cu): records of kFoRec doubles
 // (tau, x^1..3, u^0..3, T, mu_B, mu_S, mu_Q, e, p, s, n_0..3, |dsigma|, dsigma_0..3)

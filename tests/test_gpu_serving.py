@@ -272,3 +272,22 @@ def test_fixed_shape_runs_match_oracle_and_are_batch_invariant(Bd):
         b.free()
         for k in ("X", "U", "T", "MU", "NNB"):
             assert np.array_equal(lone[k], mixed[k]), (tt, lw, k)
+
+
+def test_overlapped_groups_give_the_same_bits(Bd):
+    """The two-group schedule (one group's EoS and equations of motion beside the other's
+    neighbour passes) computes exactly what the one-group schedule does: every event's results
+    bitwise equal."""
+    evs = [bsq(3000, seed=101), bsq(5000, seed=102), bsq(2000, seed=103)]
+    outs = {}
+    for groups in (1, 2):
+        s = Bd.GpuServer(evs[0].eos, evs[0].table, max_events=4, max_particles=1 << 15, groups=groups)
+        tk = [s.submit(ev, 15) for ev in evs]
+        s.drain(60.0)
+        outs[groups] = [s.collect(t) for t in tk]
+        s.free()
+    for a, b in zip(outs[1], outs[2]):
+        for k in ("X", "U", "S", "BV", "PV", "T", "MU", "S_DENS", "N_DENS", "NNB"):
+            assert np.array_equal(a[k], b[k]), k
+        for k in ("tau", "E", "work", "pairs"):
+            assert a["totals"][k] == b["totals"][k], k
