@@ -154,7 +154,10 @@ def cpu_baseline(ev, served, nsteps):
                "mu": nrm(served["MU"], np.stack([aux[O.AUX[k]] for k in ("muB", "muS", "muQ")])),
                "s": nrm(served["S_DENS"], aux[O.AUX["s"]]),
                "n_q": nrm(served["N_DENS"], np.stack([aux[O.AUX[k]] for k in ("nB", "nS", "nQ")])),
-               "tolerance": 1e-5}
+               "parity_tolerance_300_steps": 1e-5,
+               "note": "whole evolution (1480 steps): the served form's error against the oracle grows with "
+                       "the evolution; the parity tests hold 1e-5 over 300 steps, and the FP64 form stays "
+                       "within 1e-13 of the oracle over the whole evolution"}
     return {"value": ev.n * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one whole event of the stream (its smallest, {ev.n} particles): all {nsteps} Heun steps, "
                       f"tau 0.6 -> 8 fm/c ({dt:.1f} s, FP64 C oracle, OpenMP over particles)"}, err
@@ -843,7 +846,7 @@ def run_ours(args):
 def run_profile_case(args):
     """A short, fixed run of the timed kernels for profiler captures (no timing, no reference
     legs): 'serving' -- the stream's first --events events resident at once in the serving
-    arena, --profile-steps batch steps in the tiled-pass shape --profile-shape; 'fp64' -- the
+    arena (one event group), --profile-steps batch steps in the tiled-pass shape --profile-shape; 'fp64' -- the
     40k-particle viscous BSQ event in the plain FP64 form, --profile-steps Heun steps (kernels
     launched one by one); 'diffusion' -- the same event with BSQ diffusion.  Prints one JSON
     line describing what ran."""
@@ -859,8 +862,10 @@ def run_profile_case(args):
         sizes = c4_sizes(C4_EVENTS)[:args.events]
         evs = c4_events(sizes)
         tt, lw = (int(v) for v in args.profile_shape.split(","))
+        # one event group: every launch covers every event (the stream's two-group schedule runs
+        # the same kernels over about half the events each)
         srv = Bd.GpuServer(I.BJ_EOS, I.synthetic_eos_table(I.BJ_EOS), max_events=max(4, len(evs)),
-                           max_particles=C4_ARENA)
+                           max_particles=C4_ARENA, groups=1)
         srv.set_shape(tt, lw)
         for ev in evs:
             srv.submit(ev, C4_STEPS)
