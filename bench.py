@@ -321,10 +321,25 @@ def fp64_one_at_a_time(Bd, I, evs, sizes, nsteps):
                    f"its {len(sizes)} events of the least-squares line through them"}
 
 
+def mixed_vs_fp64(fm, f64):
+    """Normwise error (max |d| / max |ref|) of the mixed form's fields against the FP64 form's
+    after the same steps (the FP64 form follows the oracle to 1e-11 per step, tests/)."""
+    import numpy as np
+    out = {}
+    for k in ("T", "MU", "S_DENS", "N_DENS"):
+        a, b = np.asarray(fm[k], dtype=np.float64), np.asarray(f64[k], dtype=np.float64)
+        den = float(np.max(np.abs(b)))
+        if den > 0:
+            out[k] = float(np.max(np.abs(a - b)) / den)
+    return out
+
+
 def bench_mixed_single(Bd, I, steps: int = 50):
-    """The 40k-particle event in the mixed-precision forms: the per-event SPH_MIXED path (warp
-    per particle neighbour passes) and the serving form holding this one event (cell-tiled
-    passes, one CUDA graph per batch step); device or wall ms per step after warm-up."""
+    """The 40k-particle event in the mixed-precision forms: the per-event SPH_MIXED path (cell-tiled
+    passes over the 2h-cells, one CUDA graph per step) and the serving form holding this one
+    event (cell-tiled passes over h-cells, one CUDA graph per batch step); device or wall ms per
+    step after warm-up, and the per-event form's error against the FP64 form after the same
+    steps."""
     import torch
     ev = I.viscous_bsq_2p1()
     st = torch.cuda.Stream()
@@ -337,7 +352,13 @@ def bench_mixed_single(Bd, I, steps: int = 50):
         b.record(st)
     torch.cuda.synchronize()
     per_event = a.elapsed_time(b) / steps
+    names = ("T", "MU", "S_DENS", "N_DENS")
+    fm = g.read(names)
     g.free()
+    g64 = Bd.GpuEvent(ev, use_graph=True, precision=Bd.SPH_FP64)
+    g64.step(3 + steps, sync=True)
+    err = mixed_vs_fp64(fm, g64.read(names))
+    g64.free()
     srv = Bd.GpuServer(ev.eos, ev.table, max_events=2, max_particles=1 << 17)
     t = srv.submit(ev, steps + 8)
     srv.pump(4)
@@ -354,6 +375,7 @@ def bench_mixed_single(Bd, I, steps: int = 50):
             "per_event_particle_steps_per_s": ev.n / (per_event / 1e3),
             "serving_one_event_ms_per_step": served,
             "serving_one_event_particle_steps_per_s": ev.n / (served / 1e3),
+            "per_event_vs_fp64": {**err, "steps": 3 + steps},
             "note": "per-event: CUDA events; serving: wall clock over pumped batch steps (host pacing included)"}
 
 
@@ -501,6 +523,7 @@ def bench_3p1d(Bd, I, steps: int = 3):
     out = {"workload": f"3+1D Milne viscous BSQ event, {ev.n} particles, dx = dy = 0.124 fm, d_eta = 0.1, "
                        f"h = 0.3 fm, dtau = 0.005 fm, 64x32^3 EoS table", "steps": steps}
     e_fo = None
+    fields = {}
     for name, prec in (("fp64", Bd.SPH_FP64), ("mixed", Bd.SPH_MIXED), ("fp64_freezeout", Bd.SPH_FP64)):
         st = torch.cuda.Stream()
         g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream, precision=prec)
@@ -523,11 +546,14 @@ def bench_3p1d(Bd, I, steps: int = 3):
         out[name] = {"ms_per_step": ms, "particle_steps_per_s": ev.n / (ms / 1e3)}
         if prec == Bd.SPH_MIXED:
             out[name]["shell_tests"] = g.totals()["shell_tests"]
+        if name in ("fp64", "mixed"):
+            fields[name] = g.read(("T", "MU", "S_DENS", "N_DENS"))
         if name == "fp64_freezeout":
             out[name]["e_fo"] = e_fo
             out[name]["elements"] = int(len(g.read_freezeout()[1]))
         g.free()
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["mixed_vs_fp64"] = {**mixed_vs_fp64(fields["mixed"], fields["fp64"]), "steps": 1 + steps}
     out["freezeout_overhead"] = out["fp64_freezeout"]["ms_per_step"] / out["fp64"]["ms_per_step"] - 1.0
     return out
 
@@ -541,6 +567,7 @@ def bench_stress(Bd, I, steps: int = 3):
     out = {"workload": f"3+1D Cartesian viscous BSQ event with 10 jet tracks (5 GeV/fm, sigma 0.3 fm), "
                        f"{ev.n} particles, spacing {ev.meta['dx']:.4f} fm, h = 0.15 fm, dt = 0.005 fm, "
                        f"128x64^3 EoS table", "steps": steps}
+    fields = {}
     for name, prec in (("fp64", Bd.SPH_FP64), ("mixed", Bd.SPH_MIXED)):
         st = torch.cuda.Stream()
         g = Bd.GpuEvent(ev, use_graph=True, stream=st.cuda_stream, precision=prec)
@@ -554,8 +581,10 @@ def bench_stress(Bd, I, steps: int = 3):
         ms = e0.elapsed_time(e1) / steps
         out[name] = {"ms_per_step": ms, "particle_steps_per_s": ev.n / (ms / 1e3),
                      "status_or": g.totals()["status_or"]}
+        fields[name] = g.read(("T", "MU", "S_DENS", "N_DENS"))
         g.free()
     out["mixed_speedup"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["mixed_vs_fp64"] = {**mixed_vs_fp64(fields["mixed"], fields["fp64"]), "steps": 1 + steps}
     return out
 
 

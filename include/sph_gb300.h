@@ -156,10 +156,12 @@ typedef struct {
 
 /* Precision of the step.  SPH_FP64: every operation in double precision.  SPH_MIXED (dim 2 or 3):
  * the neighbour passes (kernel sums and gradients) run in single precision with positions
- * relative to their cell's origin and compensated (two-sum) accumulation, combined in double
- * precision per particle; the neighbour set stays exactly that of the FP64 test (a proven float
- * error band, the FP64 test inside it); the EoS inversion, equations of motion, Heun update and
- * reductions stay FP64.  Results differ from SPH_FP64 at the ~1e-7 relative level. */
+ * relative to their cell's origin and compensated (two-sum) accumulation, combined per particle
+ * without loss (2+1D: cell-tiled, two candidates per packed FP32 instruction); the neighbour set
+ * stays exactly that of the FP64 test (a proven float error band, the FP64 test inside it); the
+ * EoS inversion (to max(newton_tol, 1e-10) without the polishing step, as its inputs carry the
+ * single-precision sums' rounding), equations of motion, Heun update and reductions stay FP64.
+ * Results differ from SPH_FP64 at the ~1e-7 relative level. */
 #define SPH_FP64 0
 #define SPH_MIXED 1
 

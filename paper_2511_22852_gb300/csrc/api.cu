@@ -164,6 +164,12 @@ static EvView make_view(const sph_event *ev)
     v.sc = ev->sc;
     v.eos = ev->eos->dev;
     v.eos.offline = ev->eos_offline && ev->eos->dev.inv ? 1 : 0;
+    if (ev->mixed) {
+        // the mixed form's densities carry the FP32 sums' rounding (about 1e-7 of s): its
+        // inversion stops at the serving form's tolerance, without the polishing step
+        v.eos.polish = 0;
+        v.eos.tol = std::max(v.eos.tol, 1e-10);
+    }
     v.tr = ev->tr;
     v.eos.backup = ev->backup;
     v.eos.cd_A0 = ev->cd_A0;

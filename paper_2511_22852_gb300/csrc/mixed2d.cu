@@ -9,47 +9,18 @@
 //     candidates as certainly inside (r2f < (2h)^2 - err), certainly outside
 //     (r2f > (2h)^2 + err), or in the thin shell between, where the FP64 test r^2 < (2h)^2
 //     with separately rounded products decides -- the same set as the FP64 path;
-//   * sums are compensated (Neumaier two-sum) per lane in float, then each lane's
-//     (hi + lo) is combined across the warp in FP64 in a fixed butterfly order.
+//   * candidates are staged per cell in shared memory and evaluated two per packed two-wide
+//     FP32 instruction; sums are compensated (Neumaier two-sum) per lane in float, and a
+//     particle's lanes are combined with error-free FP32 additions in a fixed tree order.
 // The EoS inversion, equations of motion and conservation reductions stay FP64.
+#include <algorithm>
+
 #include "sph_internal.cuh"
+#include "tiled_common.cuh"
 
 namespace sphg {
 
 namespace {
-
-constexpr int kWarpsM = 4;
-
-// Neumaier compensated accumulation in single precision
-struct CSum {
-    float hi, lo;
-};
-__device__ __forceinline__ void cadd(CSum &s, float x)
-{
-    float t = s.hi + x;
-    if (fabsf(s.hi) >= fabsf(x)) s.lo += (s.hi - t) + x;
-    else s.lo += (x - t) + s.hi;
-    s.hi = t;
-}
-__device__ __forceinline__ double cwarp(CSum s)
-{
-    double v = (double)s.hi + (double)s.lo;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float kernel_wf(float q)
-{
-    if (q <= 1.0f) return fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
-    float t = 2.0f - q;
-    return 0.25f * t * t * t;
-}
-__device__ __forceinline__ float kernel_dwf(float q)
-{
-    if (q <= 1.0f) return q * fmaf(2.25f, q, -3.0f);
-    float t = 2.0f - q;
-    return -0.75f * t * t;
-}
 
 // cell-relative single-precision positions of the sorted particles
 __global__ void k_relpos2(EvView v, const double *__restrict__ y, float2 *__restrict__ rel)
@@ -68,177 +39,346 @@ __global__ void k_relpos2(EvView v, const double *__restrict__ y, float2 *__rest
     rel[j] = make_float2(__double2float_rn(r[0]), __double2float_rn(r[1]));
 }
 
-// candidate walk of one warp over the 3x3 cells with the three-way classification;
-// accepted candidates (with their float separation) go to the per-warp queue
-template <class Pair>
-__device__ __forceinline__ void walk9m(const EvView &v, const uint32_t *__restrict__ start,
-                                      const uint32_t *__restrict__ cnt, const float2 *__restrict__ rel,
-                                      const double *__restrict__ y, int a, int *qb, float2 *qd, Pair &pair,
-                                      unsigned &shell)
+// Cell-tiled passes: one block per occupied cell (grid-stride over the cell grid) stages the
+// candidates of the 3x3 block of 2h-cells around it -- nine runs of the Morton-sorted order --
+// in shared memory, in tiles of kTile2, two candidates per float4 entry (packed two-wide FP32
+// arithmetic), and every particle of the cell scans them with L lanes (lanes_per_particle).  A
+// candidate carries its own-cell-relative position and its cell's offset separately, so the
+// separation (r_a - r_b) - o (2h) rounds exactly as the shell bound assumes.
+constexpr int kTT2 = 256;      // threads of a tiled block; all its warps share a cell's particles
+constexpr int kTile2 = 896;    // candidates staged at a time (about the 3x3 block of a C2 cell)
+
+struct Runs9 {
+    int rs[9];     // first sorted index of each neighbour cell (row-major over (oy, ox))
+    int cum[10];   // candidates before run o
+    float ox[9], oy[9];  // the run's cell offset times the float cell side
+};
+
+// the runs of cell (cx, cy), built by the first nine threads; thread 0 scans the lengths
+__device__ __forceinline__ void runs9_setup(const EvView &v, const uint32_t *__restrict__ start,
+                                            const uint32_t *__restrict__ cnt, int cx, int cy, Runs9 &R)
 {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int n = v.n;
-    const double xa = y[a], ya = y[n + a];
-    const float2 ra = rel[a];
-    const int cx = cell_coord(xa, dec_double(v.sc->xmin_enc[0]), v.inv_cell);
-    const int cy = cell_coord(ya, dec_double(v.sc->xmin_enc[1]), v.inv_cell);
-    const int lim = 1 << v.B;
-    const float cs = v.cell_f;
-    int qn = 0;
-    for (int oy = -1; oy <= 1; ++oy) {
-        const int ny = cy + oy;
-        if (ny < 0 || ny >= lim) continue;
-        for (int ox = -1; ox <= 1; ++ox) {
-            const int nx = cx + ox;
-            if (nx < 0 || nx >= lim) continue;
+    const int t = threadIdx.x, lim = 1 << v.B;
+    if (t < 9) {
+        const int dy = t / 3 - 1, dx = t % 3 - 1, nx = cx + dx, ny = cy + dy;
+        int len = 0, st = 0;
+        if (nx >= 0 && nx < lim && ny >= 0 && ny < lim) {
             const uint32_t k = morton2((uint32_t)nx, (uint32_t)ny);
-            const uint32_t b0 = start[k], b1 = b0 + cnt[k];
-            const float offx = (float)ox * cs, offy = (float)oy * cs;
-            for (uint32_t base = b0; base < b1; base += 32) {
-                const uint32_t b = base + lane;
-                bool acc = false;
-                float dx = 0.0f, dy = 0.0f;
-                if (b < b1) {
-                    const float2 rb = rel[b];
-                    dx = (ra.x - rb.x) - offx;
-                    dy = (ra.y - rb.y) - offy;
-                    const float r2 = fmaf(dx, dx, dy * dy);
-                    if (r2 < v.shell_lo) {
-                        acc = true;
-                    } else if (r2 <= v.shell_hi) {  // thin shell: the exact FP64 decision
-                        acc = dist2_2d(xa - y[b], ya - y[n + b]) < v.supp2;
-                        ++shell;
+            st = (int)start[k];
+            len = (int)cnt[k];
+        }
+        R.rs[t] = st;
+        R.cum[t + 1] = len;
+        R.ox[t] = (float)dx * v.cell_f;
+        R.oy[t] = (float)dy * v.cell_f;
+    }
+    __syncthreads();
+    if (t == 0) {
+        R.cum[0] = 0;
+        for (int o = 0; o < 9; ++o) R.cum[o + 1] += R.cum[o];
+    }
+    __syncthreads();
+}
+
+// sorted index of candidate q and its run
+__device__ __forceinline__ int run_of(const Runs9 &R, int q)
+{
+    int o = 0;
+#pragma unroll
+    for (int k = 1; k < 9; ++k) o += q >= R.cum[k];
+    return o;
+}
+
+template <int TT>
+__global__ void __launch_bounds__(TT) k_tiled_density2m(EvView v, const double *__restrict__ y,
+                                                          const float2 *__restrict__ rel,
+                                                          const double *__restrict__ Nq,
+                                                          const uint32_t *__restrict__ start,
+                                                          const uint32_t *__restrict__ cnt,
+                                                          double *__restrict__ dens, int *__restrict__ nnb)
+{
+    __shared__ float4 cP[kTile2 / 2];   // (-x_0, -x_1, -y_0, -y_1): own-cell-relative positions
+    __shared__ float4 cO[kTile2 / 2];   // (-ox_0, -ox_1, -oy_0, -oy_1): their cells' offsets
+    __shared__ float4 cQa[kTile2 / 2];  // (S_0, S_1, N_B0, N_B1)
+    __shared__ float4 cQb[kTile2 / 2];  // (N_S0, N_S1, N_Q0, N_Q1)
+    __shared__ Runs9 R;
+    __shared__ unsigned long long s_acc[2];
+    const size_t n = (size_t)v.n;
+    const int lim = 1 << v.B, ncell = lim * lim;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = TT / 32;
+    const float ih = (float)v.inv_h, slo = v.shell_lo, shi = v.shell_hi;
+    const double supp2 = v.supp2, sd = v.sigma_d;
+    if (tid == 0) s_acc[0] = s_acc[1] = 0ull;
+    for (int ci = blockIdx.x; ci < ncell; ci += gridDim.x) {  // block-uniform
+        const int cx = ci % lim, cy = ci / lim;
+        const uint32_t kc = morton2((uint32_t)cx, (uint32_t)cy);
+        const int na = (int)cnt[kc];
+        if (na == 0) continue;
+        __syncthreads();  // the previous cell's runs and tiles are no longer read
+        runs9_setup(v, start, cnt, cx, cy, R);
+        const int M = R.cum[9], first = (int)start[kc];
+        const int L = lanes_per_particle(na, NW), ppw = 32 / L;
+        const int pl = lane / L, l = lane - pl * L;
+        unsigned pairs = 0u, shell = 0u;
+        for (int g0 = 0; g0 < na; g0 += NW * ppw) {
+            const int my = g0 + warp * ppw + pl;
+            const bool valid = pl < ppw && my < na;
+            const int a = first + (valid ? my : 0);
+            const double xa = y[a], ya = y[n + a];
+            const float2 ra = rel[a];
+            CSum sg = {0.f, 0.f}, ss = {0.f, 0.f}, sb = {0.f, 0.f}, sS = {0.f, 0.f}, sq = {0.f, 0.f};
+            int nacc = 0;
+            for (int t0 = 0; t0 < M; t0 += kTile2) {
+                const int mt = min(kTile2, M - t0);
+                if (g0 == 0 || M > kTile2) {  // one tile serves every pass of the cell
+                    if (t0 > 0 || g0 > 0) __syncthreads();
+                    for (int i = tid; i < mt; i += TT) {
+                        const int q = t0 + i, o = run_of(R, q), b = R.rs[o] + (q - R.cum[o]);
+                        const float2 rb = rel[b];
+                        put_pair(cP, i, -rb.x, -rb.y);
+                        put_pair(cO, i, -R.ox[o], -R.oy[o]);
+                        put_pair(cQa, i, (float)y[4 * n + b], (float)Nq[b]);
+                        put_pair(cQb, i, (float)Nq[n + b], (float)Nq[2 * n + b]);
                     }
-                }
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, acc);
-                if (acc) {
-                    const int slot = qn + __popc(m & lt);
-                    qb[slot] = (int)b;
-                    qd[slot] = make_float2(dx, dy);
-                }
-                qn += __popc(m);
-                __syncwarp();
-                if (qn >= 32) {
-                    pair(qb[lane], qd[lane]);
-                    qn -= 32;
-                    __syncwarp();
-                    if (lane < qn) {
-                        qb[lane] = qb[32 + lane];
-                        qd[lane] = qd[32 + lane];
+                    if ((mt & 1) && tid == 0) {
+                        put_pair(cP, mt, kFar, kFar);
+                        put_pair(cO, mt, 0.0f, 0.0f);
+                        put_pair(cQa, mt, 0.0f, 0.0f);
+                        put_pair(cQb, mt, 0.0f, 0.0f);
                     }
-                    __syncwarp();
+                    __syncthreads();
+                }
+                if (valid) {
+                    const float2 fx = make_float2(ra.x, ra.x), fy = make_float2(ra.y, ra.y), ih2 = make_float2(ih, ih);
+                    const int np = (mt + 1) >> 1;
+                    for (int kb = l; kb < np; kb += (kRun / 2) * L) {
+                        const int ke = min(np, kb + (kRun / 2) * L);
+                        float2 pg = make_float2(0.f, 0.f), ps = pg, pB = pg, pS = pg, pQ = pg;
+#pragma unroll 2
+                        for (int k = kb; k < ke; k += L) {
+                            const float4 pk = cP[k], po = cO[k];
+                            // (r_a - r_b) - o (2h), rounded step by step as the shell bound assumes
+                            const float2 dx = __fadd2_rn(__fadd2_rn(fx, lo2(pk)), lo2(po));
+                            const float2 dy = __fadd2_rn(__fadd2_rn(fy, hi2(pk)), hi2(po));
+                            const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                            bool a0 = r2.x < slo, a1 = r2.y < slo;
+                            if (r2.x >= slo && r2.x <= shi) {  // thin shell: the exact FP64 decision
+                                const int q = t0 + 2 * k, o = run_of(R, q), b = R.rs[o] + (q - R.cum[o]);
+                                a0 = dist2_2d(xa - y[b], ya - y[n + b]) < supp2;
+                                ++shell;
+                            }
+                            if (r2.y >= slo && r2.y <= shi) {
+                                const int q = t0 + 2 * k + 1, o = run_of(R, q), b = R.rs[o] + (q - R.cum[o]);
+                                a1 = dist2_2d(xa - y[b], ya - y[n + b]) < supp2;
+                                ++shell;
+                            }
+                            const float2 qq = __fmul2_rn(make_float2(sqrt_apx(r2.x), sqrt_apx(r2.y)), ih2);
+                            float2 t2, t, u2, u;
+                            spline_terms2(qq, t2, t, u2, u);
+                            float2 w = __ffma2_rn(__fmul2_rn(make_float2(0.25f, 0.25f), t2), t,
+                                                  __fmul2_rn(u2, make_float2(-u.x, -u.y)));
+                            w.x = a0 ? w.x : 0.0f;
+                            w.y = a1 ? w.y : 0.0f;
+                            const float4 qa = cQa[k], qb = cQb[k];
+                            pg = __fadd2_rn(pg, w);
+                            ps = __ffma2_rn(lo2(qa), w, ps);
+                            pB = __ffma2_rn(hi2(qa), w, pB);
+                            pS = __ffma2_rn(lo2(qb), w, pS);
+                            pQ = __ffma2_rn(hi2(qb), w, pQ);
+                            nacc += (int)a0 + (int)a1;
+                        }
+                        cadd(sg, pg.x + pg.y);
+                        cadd(ss, ps.x + ps.y);
+                        cadd(sb, pB.x + pB.y);
+                        cadd(sS, pS.x + pS.y);
+                        cadd(sq, pQ.x + pQ.y);
+                    }
                 }
             }
+            sg = seg_csum(sg, l, L);
+            ss = seg_csum(ss, l, L);
+            sb = seg_csum(sb, l, L);
+            sS = seg_csum(sS, l, L);
+            sq = seg_csum(sq, l, L);
+            for (int o = 1; o < L; o <<= 1) {  // the neighbour count, in the same tree
+                const int t = __shfl_down_sync(0xFFFFFFFFu, nacc, o);
+                if ((l & (2 * o - 1)) == 0 && l + o < L) nacc += t;
+            }
+            if (valid && l == 0) {
+                const double ux = y[2 * n + a], uy = y[3 * n + a];
+                dens[a] = sd * cval(sg);
+                dens[n + a] = sd * cval(ss);
+                dens[2 * n + a] = sd * cval(sb);
+                dens[3 * n + a] = sd * cval(sS);
+                dens[4 * n + a] = sd * cval(sq);
+                dens[5 * n + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
+                nnb[a] = nacc;
+                pairs += (unsigned)nacc;
+            }
+        }
+        pairs = __reduce_add_sync(0xFFFFFFFFu, pairs);
+        shell = __reduce_add_sync(0xFFFFFFFFu, shell);
+        if (lane == 0) {
+            if (pairs) atomicAdd(&s_acc[0], (unsigned long long)pairs);
+            if (shell) atomicAdd(&s_acc[1], (unsigned long long)shell);
         }
     }
-    if (lane < qn) pair(qb[lane], qd[lane]);
-}
-
-__global__ void __launch_bounds__(32 * kWarpsM) k_density2m(EvView v, const double *__restrict__ y,
-                                                            const float2 *__restrict__ rel,
-                                                            const double *__restrict__ Nq,
-                                                            const uint32_t *__restrict__ start,
-                                                            const uint32_t *__restrict__ cnt,
-                                                            double *__restrict__ dens, int *__restrict__ nnb)
-{
-    __shared__ int qb_s[kWarpsM][64];
-    __shared__ float2 qd_s[kWarpsM][64];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarpsM + wid;
-    if (a >= v.n) return;
-    const size_t n = (size_t)v.n;
-    const double *S = y + 4 * n;
-    const float ih = (float)v.inv_h;
-    CSum sg = {0, 0}, ss = {0, 0}, sb = {0, 0}, sS = {0, 0}, sq = {0, 0};
-    int c = 0;
-    unsigned shell = 0;
-    auto pair = [&](int b, float2 d) {
-        const float r2 = fmaf(d.x, d.x, d.y * d.y);
-        const float q = sqrt_apx(r2) * ih;
-        const float w = kernel_wf(q);
-        cadd(sg, w);
-        cadd(ss, (float)S[b] * w);
-        cadd(sb, (float)Nq[b] * w);
-        cadd(sS, (float)Nq[n + b] * w);
-        cadd(sq, (float)Nq[2 * n + b] * w);
-        ++c;
-    };
-    walk9m(v, start, cnt, rel, y, a, qb_s[wid], qd_s[wid], pair, shell);
-    const double tsg = cwarp(sg), tss = cwarp(ss), tsb = cwarp(sb), tsS = cwarp(sS), tsq = cwarp(sq);
-    for (int o = 16; o > 0; o >>= 1) {
-        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-        shell += __shfl_xor_sync(0xFFFFFFFFu, shell, o);
-    }
-    if (lane == 0) {
-        const double ux = y[2 * n + a], uy = y[3 * n + a];
-        const double sd = v.sigma_d;
-        dens[a] = sd * tsg;
-        dens[n + a] = sd * tss;
-        dens[2 * n + a] = sd * tsb;
-        dens[3 * n + a] = sd * tsS;
-        dens[4 * n + a] = sd * tsq;
-        dens[5 * n + a] = sqrt(fma(ux, ux, fma(uy, uy, 1.0)));
-        nnb[a] = c;
-        atomicAdd(&v.sc->pairs, (unsigned long long)c);
-        if (shell) atomicAdd(&v.sc->shell_tests, (unsigned long long)shell);
+    __syncthreads();
+    if (tid == 0) {
+        if (s_acc[0]) atomicAdd(&v.sc->pairs, s_acc[0]);
+        if (s_acc[1]) atomicAdd(&v.sc->shell_tests, s_acc[1]);
     }
 }
 
-__global__ void __launch_bounds__(32 * kWarpsM) k_gradient2m(EvView v, int stage, const double *__restrict__ y,
-                                                             const float2 *__restrict__ rel,
-                                                             const double *__restrict__ gin,
-                                                             const uint32_t *__restrict__ start,
-                                                             const uint32_t *__restrict__ cnt,
-                                                             double *__restrict__ gout)
+template <int TT>
+__global__ void __launch_bounds__(TT) k_tiled_gradient2m(EvView v, int stage, const double *__restrict__ y,
+                                                           const float2 *__restrict__ rel,
+                                                           const double *__restrict__ gin,
+                                                           const uint32_t *__restrict__ start,
+                                                           const uint32_t *__restrict__ cnt, double *__restrict__ gout)
 {
-    __shared__ int qb_s[kWarpsM][64];
-    __shared__ float2 qd_s[kWarpsM][64];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarpsM + wid;
-    if (a >= v.n) return;
+    __shared__ float4 cP[kTile2 / 2];
+    __shared__ float4 cO[kTile2 / 2];
+    __shared__ float4 cXa[kTile2 / 2];  // (X^xx_0, X^xx_1, X^xy_0, X^xy_1) / sigma*^2
+    __shared__ float4 cXb[kTile2 / 2];  // (X^yx_0, X^yx_1, X^yy_0, X^yy_1) / sigma*^2
+    __shared__ float4 cU2[kTile2 / 2];  // (u^x_0, u^x_1, u^y_0, u^y_1) / sigma*
+    __shared__ Runs9 R;
     const size_t n = (size_t)v.n;
     const double *Xxx = gin, *Xxy = gin + n, *Xyx = gin + 2 * n, *Xyy = gin + 3 * n;
     const double *Ux = gin + 4 * n, *Uy = gin + 5 * n;
-    const float ih = (float)v.inv_h;
-    CSum Gx = {0, 0}, Gy = {0, 0}, Hx = {0, 0}, Hy = {0, 0}, dxux = {0, 0}, dxuy = {0, 0}, dyux = {0, 0}, dyuy = {0, 0};
-    unsigned shell = 0;
-    auto pair = [&](int b, float2 d) {
-        const float r2 = fmaf(d.x, d.x, d.y * d.y);
-        if (r2 > 0.0f) {
-            const float ir = rsqrt_apx(fmaxf(r2, 1e-30f));  // a denormal r2 flushed to 0 would give inf
-            const float fac = kernel_dwf(r2 * ir * ih) * ir;
-            const float gx = fac * d.x, gy = fac * d.y;
-            cadd(Gx, gx);
-            cadd(Gy, gy);
-            cadd(Hx, fmaf((float)Xxx[b], gx, (float)Xyx[b] * gy));
-            cadd(Hy, fmaf((float)Xxy[b], gx, (float)Xyy[b] * gy));
-            const float ubx = (float)Ux[b], uby = (float)Uy[b];
-            cadd(dxux, ubx * gx);
-            cadd(dxuy, uby * gx);
-            cadd(dyux, ubx * gy);
-            cadd(dyuy, uby * gy);
+    const int lim = 1 << v.B, ncell = lim * lim;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = TT / 32;
+    const float ih = (float)v.inv_h, slo = v.shell_lo, shi = v.shell_hi;
+    const double supp2 = v.supp2;
+    for (int ci = blockIdx.x; ci < ncell; ci += gridDim.x) {  // block-uniform
+        const int cx = ci % lim, cy = ci / lim;
+        const uint32_t kc = morton2((uint32_t)cx, (uint32_t)cy);
+        const int na = (int)cnt[kc];
+        if (na == 0) continue;
+        __syncthreads();
+        runs9_setup(v, start, cnt, cx, cy, R);
+        const int M = R.cum[9], first = (int)start[kc];
+        const int L = lanes_per_particle(na, NW), ppw = 32 / L;
+        const int pl = lane / L, l = lane - pl * L;
+        for (int g0 = 0; g0 < na; g0 += NW * ppw) {
+            const int my = g0 + warp * ppw + pl;
+            const bool valid = pl < ppw && my < na;
+            const int a = first + (valid ? my : 0);
+            const double xa = y[a], ya = y[n + a];
+            const float2 ra = rel[a];
+            CSum Gx = {0.f, 0.f}, Gy = {0.f, 0.f}, Hx = {0.f, 0.f}, Hy = {0.f, 0.f};
+            CSum xx = {0.f, 0.f}, xy = {0.f, 0.f}, yx = {0.f, 0.f}, yy = {0.f, 0.f};
+            for (int t0 = 0; t0 < M; t0 += kTile2) {
+                const int mt = min(kTile2, M - t0);
+                if (g0 == 0 || M > kTile2) {
+                    if (t0 > 0 || g0 > 0) __syncthreads();
+                    for (int i = tid; i < mt; i += TT) {
+                        const int q = t0 + i, o = run_of(R, q), b = R.rs[o] + (q - R.cum[o]);
+                        const float2 rb = rel[b];
+                        put_pair(cP, i, -rb.x, -rb.y);
+                        put_pair(cO, i, -R.ox[o], -R.oy[o]);
+                        put_pair(cXa, i, (float)Xxx[b], (float)Xxy[b]);
+                        put_pair(cXb, i, (float)Xyx[b], (float)Xyy[b]);
+                        put_pair(cU2, i, (float)Ux[b], (float)Uy[b]);
+                    }
+                    if ((mt & 1) && tid == 0) {
+                        put_pair(cP, mt, kFar, kFar);
+                        put_pair(cO, mt, 0.0f, 0.0f);
+                        put_pair(cXa, mt, 0.0f, 0.0f);
+                        put_pair(cXb, mt, 0.0f, 0.0f);
+                        put_pair(cU2, mt, 0.0f, 0.0f);
+                    }
+                    __syncthreads();
+                }
+                if (valid) {
+                    const float2 fx = make_float2(ra.x, ra.x), fy = make_float2(ra.y, ra.y), ih2 = make_float2(ih, ih);
+                    const int np = (mt + 1) >> 1;
+                    for (int kb = l; kb < np; kb += (kRun / 2) * L) {
+                        const int ke = min(np, kb + (kRun / 2) * L);
+                        float2 pGx = make_float2(0.f, 0.f), pGy = pGx, pHx = pGx, pHy = pGx;
+                        float2 pxx = pGx, pxy = pGx, pyx = pGx, pyy = pGx;
+#pragma unroll 2
+                        for (int k = kb; k < ke; k += L) {
+                            const float4 pk = cP[k], po = cO[k];
+                            const float2 dx = __fadd2_rn(__fadd2_rn(fx, lo2(pk)), lo2(po));
+                            const float2 dy = __fadd2_rn(__fadd2_rn(fy, hi2(pk)), hi2(po));
+                            const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                            bool a0 = r2.x < slo, a1 = r2.y < slo;
+                            if (r2.x >= slo && r2.x <= shi) {  // thin shell: the exact FP64 decision
+                                const int q = t0 + 2 * k, o = run_of(R, q), b = R.rs[o] + (q - R.cum[o]);
+                                a0 = dist2_2d(xa - y[b], ya - y[n + b]) < supp2;
+                            }
+                            if (r2.y >= slo && r2.y <= shi) {
+                                const int q = t0 + 2 * k + 1, o = run_of(R, q), b = R.rs[o] + (q - R.cum[o]);
+                                a1 = dist2_2d(xa - y[b], ya - y[n + b]) < supp2;
+                            }
+                            // r = 0 (the particle itself) gives dw/dq = 0: a zero term
+                            const float2 ir = make_float2(rsqrt_apx(fmaxf(r2.x, 1e-30f)), rsqrt_apx(fmaxf(r2.y, 1e-30f)));
+                            float2 t2, t, u2, u;
+                            spline_terms2(__fmul2_rn(__fmul2_rn(r2, ir), ih2), t2, t, u2, u);
+                            float2 fac = __fmul2_rn(__ffma2_rn(make_float2(-0.75f, -0.75f), t2,
+                                                               __fmul2_rn(make_float2(3.0f, 3.0f), u2)), ir);
+                            fac.x = a0 ? fac.x : 0.0f;
+                            fac.y = a1 ? fac.y : 0.0f;
+                            const float2 gx = __fmul2_rn(fac, dx), gy = __fmul2_rn(fac, dy);
+                            const float4 xa4 = cXa[k], xb4 = cXb[k], u4 = cU2[k];
+                            pGx = __fadd2_rn(pGx, gx);
+                            pGy = __fadd2_rn(pGy, gy);
+                            pHx = __ffma2_rn(lo2(xa4), gx, __ffma2_rn(lo2(xb4), gy, pHx));
+                            pHy = __ffma2_rn(hi2(xa4), gx, __ffma2_rn(hi2(xb4), gy, pHy));
+                            pxx = __ffma2_rn(lo2(u4), gx, pxx);
+                            pxy = __ffma2_rn(hi2(u4), gx, pxy);
+                            pyx = __ffma2_rn(lo2(u4), gy, pyx);
+                            pyy = __ffma2_rn(hi2(u4), gy, pyy);
+                        }
+                        cadd(Gx, pGx.x + pGx.y);
+                        cadd(Gy, pGy.x + pGy.y);
+                        cadd(Hx, pHx.x + pHx.y);
+                        cadd(Hy, pHy.x + pHy.y);
+                        cadd(xx, pxx.x + pxx.y);
+                        cadd(xy, pxy.x + pxy.y);
+                        cadd(yx, pyx.x + pyx.y);
+                        cadd(yy, pyy.x + pyy.y);
+                    }
+                }
+            }
+            Gx = seg_csum(Gx, l, L);
+            Gy = seg_csum(Gy, l, L);
+            Hx = seg_csum(Hx, l, L);
+            Hy = seg_csum(Hy, l, L);
+            xx = seg_csum(xx, l, L);
+            xy = seg_csum(xy, l, L);
+            yx = seg_csum(yx, l, L);
+            yy = seg_csum(yy, l, L);
+            if (valid && l == 0) {
+                const double tGx = cval(Gx), tGy = cval(Gy), tHx = cval(Hx), tHy = cval(Hy);
+                const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
+                const double sqrtg = v.milne ? tau : 1.0;
+                const double c = v.sigma_d * v.inv_h;
+                gout[a] = c * cval(xx);
+                gout[n + a] = c * cval(xy);
+                gout[2 * n + a] = c * cval(yx);
+                gout[3 * n + a] = c * cval(yy);
+                const double Fx = Xxx[a] * tGx + Xyx[a] * tGy + tHx;
+                const double Fy = Xxy[a] * tGx + Xyy[a] * tGy + tHy;
+                gout[4 * n + a] = -sqrtg * c * Fx;
+                gout[5 * n + a] = -sqrtg * c * Fy;
+            }
         }
-    };
-    walk9m(v, start, cnt, rel, y, a, qb_s[wid], qd_s[wid], pair, shell);
-    const double tGx = cwarp(Gx), tGy = cwarp(Gy), tHx = cwarp(Hx), tHy = cwarp(Hy);
-    const double t00 = cwarp(dxux), t01 = cwarp(dxuy), t10 = cwarp(dyux), t11 = cwarp(dyuy);
-    if (lane == 0) {
-        const double tau = v.sc->tau + (stage == 2 ? v.dtau : 0.0);
-        const double sqrtg = v.milne ? tau : 1.0;
-        const double c = v.sigma_d * v.inv_h;
-        gout[a] = c * t00;
-        gout[n + a] = c * t01;
-        gout[2 * n + a] = c * t10;
-        gout[3 * n + a] = c * t11;
-        const double Fx = Xxx[a] * tGx + Xyx[a] * tGy + tHx;
-        const double Fy = Xxy[a] * tGx + Xyy[a] * tGy + tHy;
-        gout[4 * n + a] = -sqrtg * c * Fx;
-        gout[5 * n + a] = -sqrtg * c * Fy;
     }
 }
 
 inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+// blocks of the tiled passes: one per cell of the 2^B x 2^B grid, at most 8 per SM (the rest
+// grid-stride)
+inline int tiled_grid2(const EvView &v)
+{
+    const long long ncell = 1ll << (2 * v.B);
+    return (int)std::min<long long>(ncell, 8ll * device_sm_count());
+}
 
 }  // namespace
 
@@ -246,13 +386,13 @@ void launch_density2m(const EvView &v, const double *y, const double *Nq, CellBu
                       cudaStream_t st)
 {
     k_relpos2<<<nblk(v.n, 256), 256, 0, st>>>(v, y, cb.fpos);
-    k_density2m<<<nblk(v.n, kWarpsM), 32 * kWarpsM, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb);
+    k_tiled_density2m<kTT2><<<tiled_grid2(v), kTT2, 0, st>>>(v, y, cb.fpos, Nq, cb.start, cb.cnt, dens, nnb);
 }
 
 void launch_gradient2m(const EvView &v, int stage, const double *y, const double *gin, CellBufs cb, double *gout,
                        cudaStream_t st)
 {
-    k_gradient2m<<<nblk(v.n, kWarpsM), 32 * kWarpsM, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout);
+    k_tiled_gradient2m<kTT2><<<tiled_grid2(v), kTT2, 0, st>>>(v, stage, y, cb.fpos, gin, cb.start, cb.cnt, gout);
 }
 
 }  // namespace sphg
