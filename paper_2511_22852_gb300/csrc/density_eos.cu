@@ -410,8 +410,11 @@ void launch_eos(const EvView &v, int stage, const double *y, const double *dens,
         launch_eos3(v, stage, y, dens, eos, gin, status, wpart, guess_in, guess_out, st);
         return;
     }
-    // persistent: resident blocks on every SM, or fewer for a small event (a lane per particle)
-    const int grid = std::max(1, std::min(nblk(v.n, 32 * kEosWarps), kEosBlocksPerSM * device_sm_count()));
+    // persistent: resident blocks on every SM; an event with fewer particles than that many lanes
+    // takes a whole number of blocks per SM (the lanes claim the rest, so no SM holds a block
+    // more than another), or a lane per particle when it is smaller than one block per SM
+    const int sms = device_sm_count(), need = nblk(v.n, 32 * kEosWarps);
+    const int grid = need >= kEosBlocksPerSM * sms ? kEosBlocksPerSM * sms : (need >= sms ? (need / sms) * sms : std::max(1, need));
     k_eos2<<<grid, 32 * kEosWarps, 0, st>>>(v, stage, y, const_cast<double *>(dens), eos, gin, status, wpart,
                                               guess_in, guess_out);
 }
