@@ -14,7 +14,7 @@ wall-clock figures of the whole stream.  The plain FP64 form, one event at a tim
 a sample of whole events and extrapolated to the stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --profile-case serving|fp64|diffusion [--events E] [--profile-steps K]
+    python bench.py --profile-case serving|fp64|mixed|diffusion [--events E] [--profile-steps K]
         (a short fixed run of the timed kernels for profiler captures; measures nothing)
 
 N > 1 runs under torchrun, one independent stream per rank (replicas, weak scaling, no
@@ -877,7 +877,8 @@ def run_profile_case(args):
     legs): 'serving' -- the stream's first --events events resident at once in the serving
     arena (one event group), --profile-steps batch steps in the tiled-pass shape --profile-shape; 'fp64' -- the
     40k-particle viscous BSQ event in the plain FP64 form, --profile-steps Heun steps (kernels
-    launched one by one); 'diffusion' -- the same event with BSQ diffusion.  Prints one JSON
+    launched one by one); 'mixed' -- the same event in the per-event mixed form; 'diffusion' --
+    the same event with BSQ diffusion (FP64).  Prints one JSON
     line describing what ran."""
     import numpy as np
     import torch
@@ -907,7 +908,8 @@ def run_profile_case(args):
         ev = I.viscous_bsq_2p1()
         if args.profile_case == "diffusion":
             ev.diffusion = I.Diffusion(kappaT2=I.KAPPA_BSQ)
-        g = Bd.GpuEvent(ev, use_graph=False)
+        prec = Bd.SPH_MIXED if args.profile_case == "mixed" else Bd.SPH_FP64
+        g = Bd.GpuEvent(ev, use_graph=False, precision=prec)
         g.step(k, sync=True)
         g.free()
         desc = {"particles": ev.n, "steps": k}
@@ -928,7 +930,7 @@ def main():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--events", type=int, default=C4_EVENTS,
                     help="events of the stream (the configuration has 512; fewer only for quick checks)")
-    ap.add_argument("--profile-case", choices=["serving", "fp64", "diffusion"], default=None,
+    ap.add_argument("--profile-case", choices=["serving", "fp64", "mixed", "diffusion"], default=None,
                     help="a short fixed run of the timed kernels for profiler captures (no measurement)")
     ap.add_argument("--profile-steps", type=int, default=40)
     ap.add_argument("--profile-shape", default="64,2", help="threads,lane-split warps of the tiled passes")
