@@ -651,6 +651,10 @@ def traffic_of(kernel: str, particles_per_launch: float | None = None):
     n = float(particles_per_launch) if particles_per_launch else float(rec["particles"])
     out = {"bytes_per_launch": rec["bytes_per_particle"] * n, "bytes_per_particle": rec["bytes_per_particle"],
            "capture": rec["capture"], "captured_particles": rec["particles"]}
+    if "counters" in rec:  # pipe and issue activity of the captured launch (ncu)
+        out["counters"] = rec["counters"]
+    if "note" in rec:
+        out["note"] = rec["note"]
     if abs(n - rec["particles"]) > 0.5:
         out["scaled"] = (f"captured on {rec['particles']} particles, scaled to {n:.0f} per launch "
                          "(DRAM bytes taken proportional to the particles processed)")
