@@ -152,6 +152,12 @@ MUTATIONS = [
      "dv[c] += (2.0 * Fls[9 * b + 3 * c + kk]) * gw[kk];", "test_oracle_diffusion.py::test_lab_charge_conserved_exactly"),
     ("dnmr_bulk_drop_volume_rate", "R->dBv = (DPi + q->Pi * theta) / (u0 * q->sigma);",
      "R->dBv = DPi / (u0 * q->sigma);", "test_oracle_physics.py::test_bjorken_dnmr_against_ode"),
+    ("stop_rule_inverted", "(P->T_stop_GeV > 0.0 && aux[5 * n + a] * HBARC < P->T_stop_GeV)",
+     "(P->T_stop_GeV > 0.0 && aux[5 * n + a] * HBARC > P->T_stop_GeV)",
+     "test_oracle_physics.py::test_stop_temperature_freezes_cold_particles"),
+    ("stop_rule_frozen_at_rest", "for (int i = 0; i < dim; ++i) dydt[i * n + a] = y[(dim + i) * n + a] / u0;",
+     "for (int i = 0; i < dim; ++i) dydt[i * n + a] = 0.0 * u0;",
+     "test_oracle_physics.py::test_stop_temperature_freezes_cold_particles"),
 ]
 
 
